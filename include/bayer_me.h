@@ -1,0 +1,192 @@
+/*
+ * bayer_me.h -- C ABI of the B300 (sm_103a) Bayer-domain block motion
+ * estimation and motion-vector feature propagation library (libbayer_me.so).
+ *
+ * Method: arXiv 2508.05990, "Efficient Bayer-Domain Video Computer Vision with
+ * Fast Motion Estimation and Learned Perception Residual".
+ *   Sec. 2.2 "Definition":   MV = ME(F_R, F_C)
+ *   Sec. 3.2 "Fast Motion Estimation": block pyramid, coarse-to-fine stages,
+ *                            SAD matching criterion, argmin = MV
+ *   Sec. 3.3 equation:       z_pred = Warp(z_R, MV)
+ *   Sec. 4.1 "CUDA Settings": (2R+1)^2 candidates per block per stage; the MV
+ *                            field is h x w; a Batch dimension of frame pairs.
+ *
+ * Conventions (all entry points)
+ *   Frames: uint16 row-major H x W (row pitch in elements), RGGB mosaic with
+ *     R at (0, 0), values 0..4095 (12 bit).  Larger values give undefined MVs.
+ *   MV sign: the current block at (x, y) matches the reference block at
+ *     (x + dx, y + dy).
+ *   MV field: h = ceil(H / block) rows x w = ceil(W / block) columns of
+ *     bayer_mv_t (8 bytes, row-major), one field per frame pair.
+ *   Candidate set of a stage centred on p with radius R (in steps) and step s:
+ *     { p + (u*s, v*s) : u, v in [-R, R] }; a candidate whose displaced block
+ *     leaves the frame is skipped; partial edge blocks are clipped to the frame.
+ *   Tie-break: lexicographic minimum of (sad, |dx|+|dy|, dy, dx).
+ *   Phase: EVEN uses even offsets only (same-colour CFA samples); RAW uses all.
+ *   |dx|, |dy| of any MV are at most 511.
+ *
+ * Ownership: every frame, feature, proposal and MV buffer is owned by the
+ *   caller and is a DEVICE pointer unless the entry point's name ends in _host.
+ *   The handle owns only its workspace.  All device entry points are
+ *   asynchronous on the caller's CUDA stream (NULL = legacy default stream);
+ *   the caller keeps buffers alive until the stream reaches the call.
+ *
+ * Errors: argument errors are returned synchronously and launch nothing.
+ *   BAYER_ERR_CUDA reports a failed launch or CUDA runtime call; device-side
+ *   conditions are read back with bayer_me_sync_status.  One handle per host
+ *   thread; the library keeps no global mutable state.
+ */
+#ifndef BAYER_ME_H
+#define BAYER_ME_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bayer_me_s* bayer_me_t;
+
+/* One motion vector record: 8 bytes. */
+typedef struct {
+  int16_t dx;
+  int16_t dy;
+  uint32_t sad;
+} bayer_mv_t;
+
+typedef enum {
+  BAYER_OK = 0,
+  BAYER_ERR_INVALID_ARG = 1,
+  BAYER_ERR_UNSUPPORTED = 2,
+  BAYER_ERR_CUDA = 3,
+  BAYER_ERR_OOM = 4,
+  BAYER_ERR_TIMEOUT = 5
+} bayer_status_t;
+
+enum { BAYER_MODE_FULL = 0, BAYER_MODE_C2F = 1, BAYER_MODE_SEEDED = 2 };
+enum { BAYER_PHASE_EVEN = 0, BAYER_PHASE_RAW = 1 };
+enum { BAYER_INTERP_NEAREST = 0, BAYER_INTERP_BILINEAR = 1 };
+enum { BAYER_LAYOUT_NCHW = 0, BAYER_LAYOUT_NHWC = 1 };
+
+#define BAYER_MAX_LEVELS 4
+#define BAYER_MAX_STAGES 4
+
+/* Search parameters for bayer_me_estimate_ex.
+ *   mode FULL:   exhaustive search |dx|, |dy| <= range around the zero MV
+ *                (EVEN: step 2, RAW: step 1) -- the plain definition of block
+ *                matching (Sec. 2.2, "Block Matching-based ME").
+ *   mode C2F:    the paper's block pyramid (Sec. 3.2): levels[0..n_levels-1]
+ *                block sizes, large to small; every level runs the stages
+ *                (stage_radius[k], stage_step[k]) in order, each centred on
+ *                the previous stage's best; level 0 starts at the zero MV,
+ *                level l > 0 at the MV of the level l-1 block holding the
+ *                child's top-left pixel.  Standard setting: levels {64, 32},
+ *                stages (8, 8), (4, 4), (2, 1) (FME-settings table).  In EVEN
+ *                phase an odd step s becomes s + 1 with radius R*s/(s+1)
+ *                (integer division).  The output is the last level's field.
+ *   mode SEEDED: per block, confidence < conf_thresh -> FULL search with
+ *                `range`; otherwise the proposal (dx, dy) is rounded to the
+ *                nearest even integer (half away from zero), clamped to
+ *                [-range, range] and to the block's valid displacements, and
+ *                one stage R = 2, step 2 (+-4) is searched around it with
+ *                |dx|, |dy| <= range.  EVEN phase only.
+ * batch pairs are processed in one launch: pair b uses ref + b*ref_batch_stride
+ * and cur + b*cur_batch_stride (elements, >= 0; frames may overlap, they are
+ * only read) and writes field b of mv_out. */
+typedef struct {
+  int mode;          /* BAYER_MODE_* */
+  int phase;         /* BAYER_PHASE_* */
+  int block;         /* FULL, SEEDED: block size, one of 8, 16, 32, 64 */
+  int range;         /* FULL, SEEDED: maximum |dx|, |dy| in pixels (EVEN: even) */
+  int n_levels;      /* C2F: 1..BAYER_MAX_LEVELS */
+  int levels[BAYER_MAX_LEVELS];
+  int n_stages;      /* C2F: 1..BAYER_MAX_STAGES */
+  int stage_radius[BAYER_MAX_STAGES];
+  int stage_step[BAYER_MAX_STAGES];
+  float conf_thresh; /* SEEDED: confidence threshold (0.5 by default) */
+  int batch;         /* number of frame pairs, >= 1 */
+  long long ref_batch_stride; /* elements between reference frames of consecutive pairs */
+  long long cur_batch_stride; /* elements between current frames of consecutive pairs */
+} bayer_me_params_t;
+
+/* Create a handle bound to CUDA device `device` (makes it current).
+ * *out receives the handle.  Returns BAYER_ERR_CUDA if the device cannot be
+ * used, BAYER_ERR_OOM if the workspace cannot be allocated. */
+bayer_status_t bayer_me_init(bayer_me_t* out, int device);
+
+/* Release the handle and its workspace (synchronises the device first). */
+bayer_status_t bayer_me_destroy(bayer_me_t h);
+
+/* Static, NUL-terminated description of a status code. */
+const char* bayer_status_string(bayer_status_t s);
+
+/* Exhaustive EVEN-phase block matching of one frame pair (Sec. 2.2, Sec. 3.2
+ * "Matching Criterion"): for every block, the SAD of every candidate offset
+ * (dx, dy) with even |dx|, |dy| <= range, argmin by the tie-break above.
+ *   ref, cur: device frames H x W, pitch W.  block in {8, 16, 32, 64};
+ *   W, H even and >= block; range even, 0 <= range <= 510.
+ *   mv_out: device array of ceil(H/block) * ceil(W/block) records. */
+bayer_status_t bayer_me_estimate(bayer_me_t h, const uint16_t* ref, const uint16_t* cur, int W, int H,
+                                 int block, int range, bayer_mv_t* mv_out, void* stream);
+
+/* General form: FULL / C2F / SEEDED, EVEN or RAW, batched pairs, row pitch.
+ *   pitch: elements per frame row (>= W).
+ *   prop_dxdy: SEEDED only, device float array [batch][h][w][2] (dx, dy);
+ *   conf: SEEDED only, device float array [batch][h][w].
+ *   mv_out: device array [batch][h][w] for the output level's block size.
+ *   fallback_out: optional (SEEDED), device uint8 [batch][h][w], 1 where the
+ *     full search was used.
+ * Workspace for C2F's intermediate levels is taken from the handle. */
+bayer_status_t bayer_me_estimate_ex(bayer_me_t h, const uint16_t* ref, const uint16_t* cur, int W, int H,
+                                    int pitch, const bayer_me_params_t* params, const float* prop_dxdy,
+                                    const float* conf, bayer_mv_t* mv_out, uint8_t* fallback_out,
+                                    void* stream);
+
+/* Motion-vector feature propagation z_pred = Warp(z_R, MV) (Sec. 3.3).
+ * Feature cell (fy, fx) takes the MV of block (fy*stride/block, fx*stride/block)
+ * and samples z_R at (fy + dy/stride, fx + dx/stride):
+ *   NEAREST: offsets dy/stride, dx/stride rounded half away from zero; a copy.
+ *   BILINEAR: y0 = floor, wy = fraction (likewise x);
+ *     out = (1-wy)*((1-wx)*a + wx*b) + wy*((1-wx)*c + wx*d), each product and
+ *     sum rounded to float in this order (no fused multiply-add).
+ *   Indices are clamped to the map.
+ *   feat: device float32, n maps of C x Hf x Wf (NCHW) or Hf x Wf x C (NHWC),
+ *     contiguous; out: same shape, must not overlap feat.
+ *   mv: device, n fields of mv_h x mv_w; stride divides block;
+ *     mv_h == ceil(Hf*stride/block), mv_w == ceil(Wf*stride/block). */
+bayer_status_t bayer_feat_propagate(bayer_me_t h, const float* feat, int n, int C, int Hf, int Wf, int layout,
+                                    int interp, const bayer_mv_t* mv, int mv_h, int mv_w, int block, int stride,
+                                    float* out, void* stream);
+
+/* The whole per-clip path with HOST buffers (the end-to-end form of
+ * Sec. 3.1's inference: ME of each consecutive frame pair (F_{t-1}, F_t),
+ * then propagation of that pair's reference features):
+ *   frames: host uint16 [n_frames][H][W]; feats: host float32
+ *   [n_frames-1][C][Hf][Wf] (NCHW); mv_out: host [n_frames-1][h][w];
+ *   feat_out: host float32 like feats.  Full EVEN search with block, range;
+ *   interp as in bayer_feat_propagate.  Copies run on the handle's streams,
+ *   overlapped with compute across pairs; returns after the last copy
+ *   completes.  Page-locked host buffers give full copy bandwidth. */
+bayer_status_t bayer_clip_process_host(bayer_me_t h, const uint16_t* frames, int n_frames, int W, int H,
+                                       int block, int range, const float* feats, int C, int Hf, int Wf,
+                                       int stride, int interp, bayer_mv_t* mv_out, float* feat_out);
+
+/* Read and clear the handle's device status word after synchronising
+ * `stream`: BAYER_OK, or the first device-side error raised since the last
+ * call (e.g. BAYER_ERR_TIMEOUT from a bounded wait). */
+bayer_status_t bayer_me_sync_status(bayer_me_t h, void* stream);
+
+/* Roofline probe: throughput of the exact SAD primitive on this device.
+ * Runs a register-only loop of `variant` (0 = sad.u32 integer, 1 = float
+ * subtract + absolute add, 2 = both interleaved) on every SM and returns the
+ * pixel-candidates per clock per SM and the SM clock (MHz) seen during the
+ * run.  Synchronous. */
+bayer_status_t bayer_probe_alu(bayer_me_t h, int variant, double* pc_per_clk_per_sm, double* sm_mhz,
+                               int* sm_count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BAYER_ME_H */

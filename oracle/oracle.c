@@ -248,8 +248,13 @@ long long oracle_me_seeded(const uint16_t* ref, const uint16_t* cur, int W, int 
       stage_one_block(ref, cur, W, H, pitch, x0, y0, bw, bh, 0, 0, range / 2, 2, range, &out[b], &cnt);
     } else {
       fallback[b] = 0;
-      int cx = 2 * (int)roundf(prop_dx[b] * 0.5f);
-      int cy = 2 * (int)roundf(prop_dy[b] * 0.5f);
+      /* proposals beyond +-1024 are first limited to +-1024 (the centre is
+       * clamped to +-range <= 510 below anyway); this keeps the float-to-int
+       * conversion defined for any input */
+      float px = fminf(fmaxf(prop_dx[b], -1024.f), 1024.f);
+      float py = fminf(fmaxf(prop_dy[b], -1024.f), 1024.f);
+      int cx = 2 * (int)roundf(px * 0.5f);
+      int cy = 2 * (int)roundf(py * 0.5f);
       if (cx < -range) cx = -range;
       if (cx > range) cx = range;
       if (cy < -range) cy = -range;

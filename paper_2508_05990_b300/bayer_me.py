@@ -1,0 +1,255 @@
+"""Thin ctypes binding of libbayer_me.so (C ABI in include/bayer_me.h).
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels.  Device buffers are torch CUDA tensors (PyTorch provides device memory
+and streams); calls are asynchronous on the current torch stream unless a
+stream is given.  If the library is missing this module raises on use -- there
+is no fallback.
+
+Names follow the C ABI: ``init``/``destroy`` create and release a handle;
+``estimate``, ``estimate_ex``, ``feat_propagate``, ``clip_process_host``,
+``sync_status`` and ``probe_alu`` wrap the entry points of the same name.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbayer_me.so")
+
+MV_DTYPE = np.dtype([("dx", "<i2"), ("dy", "<i2"), ("sad", "<u4")])
+
+OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_OOM, ERR_TIMEOUT = range(6)
+MODE_FULL, MODE_C2F, MODE_SEEDED = 0, 1, 2
+PHASE_EVEN, PHASE_RAW = 0, 1
+INTERP_NEAREST, INTERP_BILINEAR = 0, 1
+LAYOUT_NCHW, LAYOUT_NHWC = 0, 1
+MAX_LEVELS = MAX_STAGES = 4
+
+# Every function the header declares (checked against include/bayer_me.h by the tests).
+EXPORTS = ("bayer_me_init", "bayer_me_destroy", "bayer_status_string", "bayer_me_estimate",
+           "bayer_me_estimate_ex", "bayer_feat_propagate", "bayer_clip_process_host", "bayer_me_sync_status",
+           "bayer_probe_alu")
+
+
+class BayerError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {status_string(status)} (status {status})")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("phase", ctypes.c_int), ("block", ctypes.c_int), ("range", ctypes.c_int),
+                ("n_levels", ctypes.c_int), ("levels", ctypes.c_int * MAX_LEVELS),
+                ("n_stages", ctypes.c_int), ("stage_radius", ctypes.c_int * MAX_STAGES),
+                ("stage_step", ctypes.c_int * MAX_STAGES), ("conf_thresh", ctypes.c_float),
+                ("batch", ctypes.c_int), ("ref_batch_stride", ctypes.c_longlong),
+                ("cur_batch_stride", ctypes.c_longlong)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libbayer_me.so not built at {path}; run `python -m paper_2508_05990_b300.build`")
+    lib = ctypes.CDLL(path)
+    P, I, F, LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_longlong
+    lib.bayer_me_init.argtypes = [ctypes.POINTER(P), I]
+    lib.bayer_me_destroy.argtypes = [P]
+    lib.bayer_status_string.argtypes = [I]
+    lib.bayer_status_string.restype = ctypes.c_char_p
+    lib.bayer_me_estimate.argtypes = [P, P, P, I, I, I, I, P, P]
+    lib.bayer_me_estimate_ex.argtypes = [P, P, P, I, I, I, ctypes.POINTER(Params), P, P, P, P, P]
+    lib.bayer_feat_propagate.argtypes = [P, P, I, I, I, I, I, I, P, I, I, I, I, P, P]
+    lib.bayer_clip_process_host.argtypes = [P, P, I, I, I, I, I, P, I, I, I, I, I, P, P]
+    lib.bayer_me_sync_status.argtypes = [P, P]
+    lib.bayer_probe_alu.argtypes = [P, I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_int)]
+    for name in EXPORTS:
+        if name != "bayer_status_string":
+            getattr(lib, name).restype = I
+    _lib = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    return load().bayer_status_string(int(status)).decode()
+
+
+def _check(status: int, what: str) -> None:
+    if status != OK:
+        raise BayerError(status, what)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    if t is None:
+        return ctypes.c_void_p(None)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def grid_shape(H: int, W: int, block: int):
+    return (H + block - 1) // block, (W + block - 1) // block
+
+
+@dataclass
+class C2FSetting:
+    """Pyramid levels (block sizes, large to small) x stages (radius in steps, step)."""
+    levels: tuple = (64, 32)
+    stages: tuple = ((8, 8), (4, 4), (2, 1))
+
+
+class Handle:
+    """A library handle bound to one CUDA device (``bayer_me_init``)."""
+
+    def __init__(self, device: int = 0):
+        self._lib = load()
+        self._h = ctypes.c_void_p()
+        _check(self._lib.bayer_me_init(ctypes.byref(self._h), int(device)), "bayer_me_init")
+        self.device = device
+
+    def close(self):
+        if self._h:
+            _check(self._lib.bayer_me_destroy(self._h), "bayer_me_destroy")
+            self._h = ctypes.c_void_p()
+
+    destroy = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- motion estimation ---------------------------------------------------
+    def estimate(self, ref, cur, block: int = 16, search_range: int = 32, out=None, stream=None):
+        """Exhaustive EVEN search of one pair; returns an int32 tensor [h, w, 2] view of the records."""
+        import torch
+        H, W = ref.shape[-2:]
+        h, w = grid_shape(H, W, block)
+        if out is None:
+            out = torch.empty((h, w, 2), dtype=torch.int32, device=ref.device)
+        _check(self._lib.bayer_me_estimate(self._h, _ptr(ref), _ptr(cur), W, H, block, search_range, _ptr(out),
+                                           _stream(stream)), "bayer_me_estimate")
+        return out
+
+    def estimate_ex(self, ref, cur, mode=MODE_FULL, phase=PHASE_EVEN, block=16, search_range=32, c2f=None,
+                    prop_dxdy=None, conf=None, conf_thresh=0.5, batch=1, ref_batch_stride=0, cur_batch_stride=0,
+                    out=None, fallback=None, stream=None, W=None, H=None, pitch=None):
+        """General search (FULL / C2F / SEEDED; EVEN / RAW; batched).  ``ref``/``cur`` are uint16
+        tensors whose first frame is the first pair's; returns the [batch, h, w, 2] int32 record tensor."""
+        import torch
+        if H is None or W is None:
+            H, W = ref.shape[-2:]
+        if pitch is None:
+            pitch = W
+        p = Params()
+        p.mode, p.phase, p.block, p.range = mode, phase, block, search_range
+        out_block = block
+        if mode == MODE_C2F:
+            c2f = c2f or C2FSetting()
+            p.n_levels = len(c2f.levels)
+            for i, b in enumerate(c2f.levels):
+                p.levels[i] = b
+            p.n_stages = len(c2f.stages)
+            for i, (r, s) in enumerate(c2f.stages):
+                p.stage_radius[i] = r
+                p.stage_step[i] = s
+            out_block = c2f.levels[-1]
+        p.conf_thresh = conf_thresh
+        p.batch = batch
+        p.ref_batch_stride = ref_batch_stride
+        p.cur_batch_stride = cur_batch_stride
+        h, w = grid_shape(H, W, out_block)
+        if out is None:
+            out = torch.empty((batch, h, w, 2), dtype=torch.int32, device=ref.device)
+        _check(self._lib.bayer_me_estimate_ex(self._h, _ptr(ref), _ptr(cur), W, H, pitch, ctypes.byref(p),
+                                              _ptr(prop_dxdy), _ptr(conf), _ptr(out), _ptr(fallback),
+                                              _stream(stream)), "bayer_me_estimate_ex")
+        return out
+
+    # -- propagation ---------------------------------------------------------
+    def feat_propagate(self, feat, mv, block: int, stride: int, interp=INTERP_BILINEAR, layout=LAYOUT_NCHW,
+                       out=None, stream=None):
+        """z_pred = Warp(z_R, MV).  feat: float32 [n, C, Hf, Wf] (NCHW) or [n, Hf, Wf, C] (NHWC);
+        mv: int32 records [n, mv_h, mv_w, 2]."""
+        import torch
+        if feat.dim() == 3:
+            feat = feat.unsqueeze(0)
+        if mv.dim() == 3:
+            mv = mv.unsqueeze(0)
+        n = feat.shape[0]
+        if layout == LAYOUT_NCHW:
+            C, Hf, Wf = feat.shape[1:]
+        else:
+            Hf, Wf, C = feat.shape[1:]
+        if out is None:
+            out = torch.empty_like(feat)
+        _check(self._lib.bayer_feat_propagate(self._h, _ptr(feat), n, C, Hf, Wf, layout, interp, _ptr(mv),
+                                              mv.shape[1], mv.shape[2], block, stride, _ptr(out),
+                                              _stream(stream)), "bayer_feat_propagate")
+        return out
+
+    # -- host-buffer end-to-end path -----------------------------------------
+    def clip_process_host(self, frames: np.ndarray, feats: np.ndarray, block=16, search_range=32, stride=8,
+                          interp=INTERP_BILINEAR, mv_out=None, feat_out=None):
+        """frames: host uint16 [T, H, W]; feats: host float32 [T-1, C, Hf, Wf].  Returns
+        (mv records [T-1, h, w] MV_DTYPE, propagated features [T-1, C, Hf, Wf])."""
+        T, H, W = frames.shape
+        _, C, Hf, Wf = feats.shape
+        h, w = grid_shape(H, W, block)
+        if mv_out is None:
+            mv_out = np.empty((T - 1, h, w), MV_DTYPE)
+        if feat_out is None:
+            feat_out = np.empty_like(feats)
+        for a in (frames, feats, mv_out, feat_out):
+            if not a.flags["C_CONTIGUOUS"]:
+                raise ValueError("host buffers must be C-contiguous")
+        _check(self._lib.bayer_clip_process_host(self._h, frames.ctypes.data, T, W, H, block, search_range,
+                                                 feats.ctypes.data, C, Hf, Wf, stride, interp,
+                                                 mv_out.ctypes.data, feat_out.ctypes.data),
+               "bayer_clip_process_host")
+        return mv_out, feat_out
+
+    def sync_status(self, stream=None) -> int:
+        return int(self._lib.bayer_me_sync_status(self._h, _stream(stream)))
+
+    def probe_alu(self, variant: int = 0):
+        """(pixel-candidates per clock per SM, SM MHz during the probe, SM count)."""
+        a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+        _check(self._lib.bayer_probe_alu(self._h, variant, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+               "bayer_probe_alu")
+        return a.value, b.value, c.value
+
+
+def init(device: int = 0) -> Handle:
+    return Handle(device)
+
+
+def records_to_numpy(t) -> np.ndarray:
+    """int32 [..., 2] record tensor -> numpy structured MV_DTYPE array [...]."""
+    a = t.detach().cpu().contiguous().numpy()
+    return a.view(MV_DTYPE).reshape(a.shape[:-1])

@@ -1,0 +1,418 @@
+// C ABI of libbayer_me.so (declarations and contracts in include/bayer_me.h).
+//
+// Host-side argument validation (no launch on error), kernel selection, the
+// handle's workspace (coarse-to-fine intermediate fields, host-pipeline
+// staging buffers, the device status word) and the host-buffer clip pipeline.
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+struct bayer_me_s {
+  int device = 0;
+  int* d_status = nullptr;       // device status word (bayer_status_t)
+  void* scratch = nullptr;       // coarse-to-fine intermediate fields
+  size_t scratch_bytes = 0;
+  // host pipeline (bayer_clip_process_host)
+  cudaStream_t s_in = nullptr, s_comp = nullptr, s_out = nullptr;
+  uint16_t* d_frames = nullptr;
+  size_t frames_bytes = 0;
+  float* d_feat = nullptr;
+  size_t feat_bytes = 0;
+  float* d_fout = nullptr;
+  size_t fout_bytes = 0;
+  bayer_mv_t* d_mv = nullptr;
+  size_t mv_bytes = 0;
+};
+
+namespace {
+
+using bme::GenericArgs;
+
+bool is_block(int b) { return b == 8 || b == 16 || b == 32 || b == 64; }
+
+bayer_status_t cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return BAYER_OK;
+  if (e == cudaErrorMemoryAllocation) return BAYER_ERR_OOM;
+  return BAYER_ERR_CUDA;
+}
+
+// Grow a device buffer to at least `bytes` (contents not kept).  Synchronises
+// the device first, because work queued earlier may still use the old buffer.
+template <typename T>
+bayer_status_t grow(T** p, size_t* cap, size_t bytes) {
+  if (*cap >= bytes) return BAYER_OK;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_status(e);
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  e = cudaMalloc(reinterpret_cast<void**>(p), bytes);
+  if (e != cudaSuccess) return cuda_status(e);
+  *cap = bytes;
+  return BAYER_OK;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int now = -1;
+    if (prev >= 0 && cudaGetDevice(&now) == cudaSuccess && now != prev) cudaSetDevice(prev);
+  }
+};
+
+bayer_status_t check_frames(const void* ref, const void* cur, int W, int H, int pitch, int block) {
+  if (!ref || !cur) return BAYER_ERR_INVALID_ARG;
+  if (!is_block(block)) return BAYER_ERR_INVALID_ARG;
+  if (W <= 0 || H <= 0 || (W & 1) || (H & 1)) return BAYER_ERR_INVALID_ARG;
+  if (W < block || H < block) return BAYER_ERR_INVALID_ARG;
+  if (pitch < W) return BAYER_ERR_INVALID_ARG;
+  if (W > 32767 || H > 32767) return BAYER_ERR_INVALID_ARG;
+  return BAYER_OK;
+}
+
+// Full search dispatch: the specialised 16x16 EVEN kernel where it applies,
+// the generic stage kernel otherwise.
+bayer_status_t full_search(const uint16_t* ref, const uint16_t* cur, int W, int H, int pitch, long long rbs,
+                           long long cbs, int batch, int block, int range, int phase, bayer_mv_t* out,
+                           cudaStream_t st) {
+  const int h = (H + block - 1) / block, w = (W + block - 1) / block;
+  if (phase == BAYER_PHASE_EVEN && block == 16 && (W % 16) == 0 && (H % 16) == 0 &&
+      bme::full16_even_supported(range)) {
+    return cuda_status(bme::launch_full16_even(ref, cur, W, H, pitch, rbs, cbs, batch, range, out, st));
+  }
+  GenericArgs a{};
+  a.ref = ref;
+  a.cur = cur;
+  a.W = W;
+  a.H = H;
+  a.pitch = pitch;
+  a.ref_bs = rbs;
+  a.cur_bs = cbs;
+  a.B = block;
+  a.h = h;
+  a.w = w;
+  a.nst = 1;
+  a.S[0] = phase == BAYER_PHASE_EVEN ? 2 : 1;
+  a.R[0] = range / a.S[0];
+  a.lim = range;
+  a.center_mode = 0;
+  a.out = out;
+  return cuda_status(bme::launch_generic(a, batch, st));
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* bayer_status_string(bayer_status_t s) {
+  switch (s) {
+    case BAYER_OK: return "ok";
+    case BAYER_ERR_INVALID_ARG: return "invalid argument";
+    case BAYER_ERR_UNSUPPORTED: return "unsupported configuration";
+    case BAYER_ERR_CUDA: return "CUDA error";
+    case BAYER_ERR_OOM: return "out of device memory";
+    case BAYER_ERR_TIMEOUT: return "device-side wait timed out";
+  }
+  return "unknown status";
+}
+
+bayer_status_t bayer_me_init(bayer_me_t* out, int device) {
+  if (!out) return BAYER_ERR_INVALID_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return BAYER_ERR_CUDA;
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) return cuda_status(e);
+  bayer_me_s* h = new (std::nothrow) bayer_me_s();
+  if (!h) return BAYER_ERR_OOM;
+  h->device = device;
+  e = bme::configure_full16();
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_comp, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_out, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    bayer_me_destroy(h);
+    return cuda_status(e);
+  }
+  *out = h;
+  return BAYER_OK;
+}
+
+bayer_status_t bayer_me_destroy(bayer_me_t h) {
+  if (!h) return BAYER_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  cudaDeviceSynchronize();
+  if (h->d_status) cudaFree(h->d_status);
+  if (h->scratch) cudaFree(h->scratch);
+  if (h->d_frames) cudaFree(h->d_frames);
+  if (h->d_feat) cudaFree(h->d_feat);
+  if (h->d_fout) cudaFree(h->d_fout);
+  if (h->d_mv) cudaFree(h->d_mv);
+  if (h->s_in) cudaStreamDestroy(h->s_in);
+  if (h->s_comp) cudaStreamDestroy(h->s_comp);
+  if (h->s_out) cudaStreamDestroy(h->s_out);
+  delete h;
+  return BAYER_OK;
+}
+
+bayer_status_t bayer_me_estimate(bayer_me_t h, const uint16_t* ref, const uint16_t* cur, int W, int H, int block,
+                                 int range, bayer_mv_t* mv_out, void* stream) {
+  if (!h || !mv_out) return BAYER_ERR_INVALID_ARG;
+  bayer_status_t s = check_frames(ref, cur, W, H, W, block);
+  if (s != BAYER_OK) return s;
+  if (range < 0 || (range & 1) || range > 510) return BAYER_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  return full_search(ref, cur, W, H, W, 0, 0, 1, block, range, BAYER_PHASE_EVEN, mv_out,
+                     static_cast<cudaStream_t>(stream));
+}
+
+bayer_status_t bayer_me_estimate_ex(bayer_me_t h, const uint16_t* ref, const uint16_t* cur, int W, int H,
+                                    int pitch, const bayer_me_params_t* p, const float* prop_dxdy,
+                                    const float* conf, bayer_mv_t* mv_out, uint8_t* fallback_out, void* stream) {
+  if (!h || !p || !mv_out) return BAYER_ERR_INVALID_ARG;
+  if (p->batch < 1 || p->batch > 65535) return BAYER_ERR_INVALID_ARG;
+  if (p->phase != BAYER_PHASE_EVEN && p->phase != BAYER_PHASE_RAW) return BAYER_ERR_INVALID_ARG;
+  if (p->ref_batch_stride < 0 || p->cur_batch_stride < 0) return BAYER_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  DeviceGuard g(h->device);
+
+  if (p->mode == BAYER_MODE_FULL) {
+    bayer_status_t s = check_frames(ref, cur, W, H, pitch, p->block);
+    if (s != BAYER_OK) return s;
+    if (p->range < 0 || p->range > 510) return BAYER_ERR_INVALID_ARG;
+    if (p->phase == BAYER_PHASE_EVEN && (p->range & 1)) return BAYER_ERR_INVALID_ARG;
+    return full_search(ref, cur, W, H, pitch, p->ref_batch_stride, p->cur_batch_stride, p->batch, p->block,
+                       p->range, p->phase, mv_out, st);
+  }
+
+  if (p->mode == BAYER_MODE_SEEDED) {
+    bayer_status_t s = check_frames(ref, cur, W, H, pitch, p->block);
+    if (s != BAYER_OK) return s;
+    if (p->phase != BAYER_PHASE_EVEN) return BAYER_ERR_UNSUPPORTED;
+    if (p->range < 4 || p->range > 510 || (p->range & 1)) return BAYER_ERR_INVALID_ARG;
+    if (!prop_dxdy || !conf) return BAYER_ERR_INVALID_ARG;
+    GenericArgs a{};
+    a.ref = ref;
+    a.cur = cur;
+    a.W = W;
+    a.H = H;
+    a.pitch = pitch;
+    a.ref_bs = p->ref_batch_stride;
+    a.cur_bs = p->cur_batch_stride;
+    a.B = p->block;
+    a.h = (H + p->block - 1) / p->block;
+    a.w = (W + p->block - 1) / p->block;
+    a.nst = 1;
+    a.lim = p->range;
+    a.center_mode = 2;
+    a.prop = prop_dxdy;
+    a.conf = conf;
+    a.thresh = p->conf_thresh;
+    a.range = p->range;
+    a.fallback = fallback_out;
+    a.out = mv_out;
+    return cuda_status(bme::launch_generic(a, p->batch, st));
+  }
+
+  if (p->mode == BAYER_MODE_C2F) {
+    if (p->n_levels < 1 || p->n_levels > BAYER_MAX_LEVELS) return BAYER_ERR_INVALID_ARG;
+    if (p->n_stages < 1 || p->n_stages > BAYER_MAX_STAGES) return BAYER_ERR_INVALID_ARG;
+    int R[BAYER_MAX_STAGES], S[BAYER_MAX_STAGES];
+    int reach = 0;
+    for (int k = 0; k < p->n_stages; ++k) {
+      R[k] = p->stage_radius[k];
+      S[k] = p->stage_step[k];
+      if (R[k] < 0 || S[k] < 1 || R[k] > 64 || S[k] > 64) return BAYER_ERR_INVALID_ARG;
+      if (p->phase == BAYER_PHASE_EVEN && (S[k] & 1)) {
+        R[k] = (R[k] * S[k]) / (S[k] + 1);
+        S[k] = S[k] + 1;
+      }
+      reach += R[k] * S[k];
+    }
+    for (int l = 0; l < p->n_levels; ++l) {
+      bayer_status_t s = check_frames(ref, cur, W, H, pitch, p->levels[l]);
+      if (s != BAYER_OK) return s;
+      if (l > 0 && p->levels[l] > p->levels[l - 1]) return BAYER_ERR_INVALID_ARG;
+    }
+    if (reach * p->n_levels > 511) return BAYER_ERR_INVALID_ARG;  // |dx|, |dy| <= 511
+    // two intermediate fields, ping-pong
+    size_t need = 0;
+    for (int l = 0; l + 1 < p->n_levels; ++l) {
+      const int B = p->levels[l];
+      const size_t n = (size_t)p->batch * ((H + B - 1) / B) * ((W + B - 1) / B) * sizeof(bayer_mv_t);
+      need = n > need ? n : need;
+    }
+    if (need) {
+      bayer_status_t s = grow(reinterpret_cast<char**>(&h->scratch), &h->scratch_bytes, 2 * need);
+      if (s != BAYER_OK) return s;
+    }
+    bayer_mv_t* buf[2] = {static_cast<bayer_mv_t*>(h->scratch),
+                          reinterpret_cast<bayer_mv_t*>(static_cast<char*>(h->scratch) + need)};
+    const bayer_mv_t* parent = nullptr;
+    int parent_B = 0;
+    for (int l = 0; l < p->n_levels; ++l) {
+      const int B = p->levels[l];
+      GenericArgs a{};
+      a.ref = ref;
+      a.cur = cur;
+      a.W = W;
+      a.H = H;
+      a.pitch = pitch;
+      a.ref_bs = p->ref_batch_stride;
+      a.cur_bs = p->cur_batch_stride;
+      a.B = B;
+      a.h = (H + B - 1) / B;
+      a.w = (W + B - 1) / B;
+      a.nst = p->n_stages;
+      for (int k = 0; k < p->n_stages; ++k) {
+        a.R[k] = R[k];
+        a.S[k] = S[k];
+      }
+      a.lim = 1 << 20;
+      a.center_mode = parent ? 1 : 0;
+      a.parent = parent;
+      a.parent_B = parent_B;
+      a.parent_h = parent ? (H + parent_B - 1) / parent_B : 0;
+      a.parent_w = parent ? (W + parent_B - 1) / parent_B : 0;
+      a.out = (l == p->n_levels - 1) ? mv_out : buf[l & 1];
+      cudaError_t e = bme::launch_generic(a, p->batch, st);
+      if (e != cudaSuccess) return cuda_status(e);
+      parent = a.out;
+      parent_B = B;
+    }
+    return BAYER_OK;
+  }
+  return BAYER_ERR_INVALID_ARG;
+}
+
+bayer_status_t bayer_feat_propagate(bayer_me_t h, const float* feat, int n, int C, int Hf, int Wf, int layout,
+                                    int interp, const bayer_mv_t* mv, int mv_h, int mv_w, int block, int stride,
+                                    float* out, void* stream) {
+  if (!h || !feat || !mv || !out) return BAYER_ERR_INVALID_ARG;
+  if (n < 1 || C < 1 || Hf < 1 || Wf < 1) return BAYER_ERR_INVALID_ARG;
+  if (layout != BAYER_LAYOUT_NCHW && layout != BAYER_LAYOUT_NHWC) return BAYER_ERR_INVALID_ARG;
+  if (interp != BAYER_INTERP_NEAREST && interp != BAYER_INTERP_BILINEAR) return BAYER_ERR_INVALID_ARG;
+  if (!is_block(block) || stride < 1 || stride > block || block % stride != 0) return BAYER_ERR_INVALID_ARG;
+  const long long eh = ((long long)Hf * stride + block - 1) / block;
+  const long long ew = ((long long)Wf * stride + block - 1) / block;
+  if (mv_h != eh || mv_w != ew) return BAYER_ERR_INVALID_ARG;
+  const size_t bytes = (size_t)n * C * Hf * Wf * sizeof(float);
+  const char* fb = reinterpret_cast<const char*>(feat);
+  const char* ob = reinterpret_cast<const char*>(out);
+  if (ob < fb + bytes && fb < ob + bytes) return BAYER_ERR_INVALID_ARG;  // out overlaps feat
+  DeviceGuard g(h->device);
+  bme::PropArgs a{feat, out, n, C, Hf, Wf, mv, mv_h, mv_w, block / stride, stride};
+  return cuda_status(bme::launch_propagate(a, layout, interp, static_cast<cudaStream_t>(stream)));
+}
+
+bayer_status_t bayer_clip_process_host(bayer_me_t h, const uint16_t* frames, int n_frames, int W, int H, int block,
+                                       int range, const float* feats, int C, int Hf, int Wf, int stride, int interp,
+                                       bayer_mv_t* mv_out, float* feat_out) {
+  if (!h || !frames || !feats || !mv_out || !feat_out || n_frames < 2) return BAYER_ERR_INVALID_ARG;
+  bayer_status_t s = check_frames(frames, frames, W, H, W, block);
+  if (s != BAYER_OK) return s;
+  if (range < 0 || (range & 1) || range > 510) return BAYER_ERR_INVALID_ARG;
+  if (interp != BAYER_INTERP_NEAREST && interp != BAYER_INTERP_BILINEAR) return BAYER_ERR_INVALID_ARG;
+  if (C < 1 || Hf < 1 || Wf < 1 || stride < 1 || block % stride != 0) return BAYER_ERR_INVALID_ARG;
+  const int h_ = (H + block - 1) / block, w_ = (W + block - 1) / block;
+  if (((long long)Hf * stride + block - 1) / block != h_ || ((long long)Wf * stride + block - 1) / block != w_)
+    return BAYER_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  const int npairs = n_frames - 1;
+  const size_t frame_elems = (size_t)W * H;
+  const size_t map_elems = (size_t)C * Hf * Wf;
+  const size_t field = (size_t)h_ * w_;
+  if ((s = grow(&h->d_frames, &h->frames_bytes, frame_elems * n_frames * sizeof(uint16_t))) != BAYER_OK) return s;
+  if ((s = grow(&h->d_feat, &h->feat_bytes, map_elems * npairs * sizeof(float))) != BAYER_OK) return s;
+  if ((s = grow(&h->d_fout, &h->fout_bytes, map_elems * npairs * sizeof(float))) != BAYER_OK) return s;
+  if ((s = grow(&h->d_mv, &h->mv_bytes, field * npairs * sizeof(bayer_mv_t))) != BAYER_OK) return s;
+
+  // Stream plan: s_in copies the frames, then each pair's features; s_comp
+  // runs the batched search once the frames are in, then each pair's
+  // propagation once its features are in; s_out returns the MV fields and
+  // each propagated map as soon as it is done.
+  cudaEvent_t ev_frames, ev_me;
+  cudaEventCreateWithFlags(&ev_frames, cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&ev_me, cudaEventDisableTiming);
+  cudaEvent_t* ev_in = new cudaEvent_t[npairs];
+  cudaEvent_t* ev_done = new cudaEvent_t[npairs];
+  for (int t = 0; t < npairs; ++t) {
+    cudaEventCreateWithFlags(&ev_in[t], cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&ev_done[t], cudaEventDisableTiming);
+  }
+  cudaError_t e = cudaMemcpyAsync(h->d_frames, frames, frame_elems * n_frames * sizeof(uint16_t),
+                                  cudaMemcpyHostToDevice, h->s_in);
+  if (e == cudaSuccess) e = cudaEventRecord(ev_frames, h->s_in);
+  for (int t = 0; t < npairs && e == cudaSuccess; ++t) {
+    e = cudaMemcpyAsync(h->d_feat + map_elems * t, feats + map_elems * t, map_elems * sizeof(float),
+                        cudaMemcpyHostToDevice, h->s_in);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_in[t], h->s_in);
+  }
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_comp, ev_frames, 0);
+  if (e == cudaSuccess) {
+    s = full_search(h->d_frames, h->d_frames + frame_elems, W, H, W, (long long)frame_elems,
+                    (long long)frame_elems, npairs, block, range, BAYER_PHASE_EVEN, h->d_mv, h->s_comp);
+    if (s != BAYER_OK) e = cudaErrorLaunchFailure;
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(ev_me, h->s_comp);
+  for (int t = 0; t < npairs && e == cudaSuccess; ++t) {
+    e = cudaStreamWaitEvent(h->s_comp, ev_in[t], 0);
+    bme::PropArgs a{h->d_feat + map_elems * t, h->d_fout + map_elems * t, 1, C, Hf, Wf, h->d_mv + field * t,
+                    h_, w_, block / stride, stride};
+    if (e == cudaSuccess) e = bme::launch_propagate(a, BAYER_LAYOUT_NCHW, interp, h->s_comp);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_done[t], h->s_comp);
+  }
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_out, ev_me, 0);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(mv_out, h->d_mv, field * npairs * sizeof(bayer_mv_t), cudaMemcpyDeviceToHost, h->s_out);
+  for (int t = 0; t < npairs && e == cudaSuccess; ++t) {
+    e = cudaStreamWaitEvent(h->s_out, ev_done[t], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(feat_out + map_elems * t, h->d_fout + map_elems * t, map_elems * sizeof(float),
+                          cudaMemcpyDeviceToHost, h->s_out);
+  }
+  cudaError_t e2 = cudaStreamSynchronize(h->s_in);
+  cudaError_t e3 = cudaStreamSynchronize(h->s_comp);
+  cudaError_t e4 = cudaStreamSynchronize(h->s_out);
+  if (e == cudaSuccess) e = e2 != cudaSuccess ? e2 : (e3 != cudaSuccess ? e3 : e4);
+  cudaEventDestroy(ev_frames);
+  cudaEventDestroy(ev_me);
+  for (int t = 0; t < npairs; ++t) {
+    cudaEventDestroy(ev_in[t]);
+    cudaEventDestroy(ev_done[t]);
+  }
+  delete[] ev_in;
+  delete[] ev_done;
+  return cuda_status(e);
+}
+
+bayer_status_t bayer_me_sync_status(bayer_me_t h, void* stream) {
+  if (!h) return BAYER_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_status, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_status(e);
+  return static_cast<bayer_status_t>(v);
+}
+
+bayer_status_t bayer_probe_alu(bayer_me_t h, int variant, double* pc_per_clk_per_sm, double* sm_mhz,
+                               int* sm_count) {
+  if (!h || !pc_per_clk_per_sm || !sm_mhz || !sm_count || variant < 0 || variant > 2)
+    return BAYER_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  return cuda_status(bme::run_probe_alu(variant, pc_per_clk_per_sm, sm_mhz, sm_count));
+}
+
+}  // extern "C"

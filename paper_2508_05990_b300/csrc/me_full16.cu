@@ -1,0 +1,207 @@
+// Exhaustive EVEN-phase block matching for 16 x 16 blocks (Sec. 2.2 "Block
+// Matching-based ME"; Sec. 3.2 "Matching Criterion": SAD, argmin = MV).
+//
+// Mapping (B300: 148 SMs, INT32 sad.u32 at 64 lanes/clk/SM):
+//   * one CTA = NW warps = NW horizontally adjacent blocks of one block row of
+//     one frame pair; the CTA stages the union of their search windows
+//     ((16*NW + 4R) x (16 + 4R) pixels) and their current blocks into shared
+//     memory as 32-bit pixel words;
+//   * one warp = one block; lane v owns candidate row v (dy = 2v - 2R) and all
+//     2R+1 candidates of that row (dx = 2u - 2R).  Adjacent candidates of a
+//     row are one 32-bit word apart (EVEN offsets), so every reference word a
+//     lane loads feeds up to 8 accumulators (register-blocked sliding SAD);
+//   * for R = 16 the 33rd row (dy = +32) is spread one candidate per lane and
+//     the corner candidate (+32, +32) is split over 16 lanes and summed with a
+//     warp reduction, so the 1089 candidates divide evenly over 32 lanes;
+//   * half the lanes walk the block rows rotated by one, which together with a
+//     window pitch of 4*(odd) words makes every 128-bit shared load
+//     conflict-free;
+//   * argmin: each lane folds its candidates into a uint64 key
+//     (sad, |dx|+|dy|, dy, dx), then a 5-step shuffle minimum.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace bme {
+
+namespace {
+
+constexpr int kNW = 4;  // warps (blocks) per CTA
+
+template <int R>
+struct Full16 {
+  static constexpr int NU = 2 * R + 1;         // candidates per row
+  static constexpr int REACH = 2 * R;          // pixels each side
+  static constexpr int WIN_W = 16 * kNW + 2 * REACH;
+  static constexpr int WIN_H = 16 + 2 * REACH;
+  static constexpr int P0 = (WIN_W + 3) / 4 * 4;
+  static constexpr int P = ((P0 / 4) % 2 == 0) ? P0 + 4 : P0;  // 4 * odd words
+  static constexpr int PC = 16 * kNW + 4;      // current-tile pitch (words)
+  static constexpr int SPAN = 16 + 2 * REACH;  // window pixels one block reads per row
+  static constexpr size_t SMEM = (size_t)(WIN_H * P + 16 * PC) * sizeof(uint32_t);
+  static_assert(NU <= 33, "at most 33 candidate rows");
+  static_assert(SPAN % 4 == 0, "span must be a multiple of 4 words");
+};
+
+template <int R>
+__global__ void __launch_bounds__(kNW * 32) me_full16_even_kernel(const uint16_t* __restrict__ ref_base,
+                                                                   const uint16_t* __restrict__ cur_base, int W,
+                                                                   int H, int pitch, long long ref_bs,
+                                                                   long long cur_bs, int h, int w,
+                                                                   bayer_mv_t* __restrict__ out) {
+  using C = Full16<R>;
+  extern __shared__ __align__(16) uint32_t smem[];
+  uint32_t* win = smem;                 // WIN_H x P
+  uint32_t* curt = smem + C::WIN_H * C::P;  // 16 x PC
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int pair = blockIdx.z;
+  const uint16_t* ref = ref_base + (long long)pair * ref_bs;
+  const uint16_t* cur = cur_base + (long long)pair * cur_bs;
+  const int x0 = blockIdx.x * kNW * 16, y0 = blockIdx.y * 16;
+
+  // ---- stage the reference window and the current tile (out-of-frame = 0)
+  for (int ry = warp; ry < C::WIN_H; ry += kNW) {
+    const int gy = y0 - C::REACH + ry;
+    const bool row_in = gy >= 0 && gy < H;
+    for (int rx = lane; rx < C::WIN_W; rx += 32) {
+      const int gx = x0 - C::REACH + rx;
+      uint32_t v = 0;
+      if (row_in && gx >= 0 && gx < W) v = __ldg(ref + (long long)gy * pitch + gx);
+      win[ry * C::P + rx] = pix_word(v);
+    }
+  }
+  for (int ry = warp; ry < 16; ry += kNW) {
+    const int gy = y0 + ry;
+    for (int rx = lane; rx < 16 * kNW; rx += 32) {
+      const int gx = x0 + rx;
+      uint32_t v = 0;
+      if (gy < H && gx < W) v = __ldg(cur + (long long)gy * pitch + gx);
+      curt[ry * C::PC + rx] = pix_word(v);
+    }
+  }
+  __syncthreads();
+
+  const int bx = blockIdx.x * kNW + warp;
+  if (bx >= w) return;
+
+  const int v = lane < C::NU ? lane : C::NU - 1;  // lanes past the last row repeat it
+  const int eps = (lane >> 2) & 1;                // row rotation for conflict-free loads
+  const uint32_t* wbase = win + 16 * warp;
+  const uint32_t* cbase = curt + 16 * warp;
+
+  uint32_t acc[C::NU];
+#pragma unroll
+  for (int k = 0; k < C::NU; ++k) acc[k] = 0;
+  uint32_t accx = 0, accc = 0;
+
+#pragma unroll 1
+  for (int i = 0; i < 16; ++i) {
+    const int r = (i + eps) & 15;
+    uint32_t c[16];
+    const uint4* cp = reinterpret_cast<const uint4*>(cbase + r * C::PC);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint4 t = cp[q];
+      c[4 * q + 0] = t.x;
+      c[4 * q + 1] = t.y;
+      c[4 * q + 2] = t.z;
+      c[4 * q + 3] = t.w;
+    }
+    const uint4* wp = reinterpret_cast<const uint4*>(wbase + (2 * v + r) * C::P);
+#pragma unroll
+    for (int q = 0; q < C::SPAN / 4; ++q) {
+      const uint4 t = wp[q];
+      const uint32_t rr[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const int p = 4 * q + s;
+#pragma unroll
+        for (int k = 0; k < C::NU; ++k) {
+          const int cc = p - 2 * k;
+          if (cc >= 0 && cc < 16) acc[k] = sad_u32(rr[s], c[cc], acc[k]);
+        }
+      }
+    }
+    if constexpr (C::NU == 33) {
+      // row v = 32: candidate u = lane at window pixel 2*lane
+      const uint2* xp = reinterpret_cast<const uint2*>(wbase + (64 + r) * C::P + 2 * lane);
+#pragma unroll
+      for (int t2 = 0; t2 < 8; ++t2) {
+        const uint2 e2 = xp[t2];
+        accx = sad_u32(e2.x, c[2 * t2], accx);
+        accx = sad_u32(e2.y, c[2 * t2 + 1], accx);
+      }
+      // corner candidate (u, v) = (32, 32): lane l < 16 takes column l
+      if (lane < 16) accc = sad_u32(wbase[(64 + r) * C::P + 64 + lane], cbase[r * C::PC + lane], accc);
+    }
+  }
+
+  // ---- argmin with the (sad, |mv|_1, dy, dx) key
+  const int xb = bx * 16, yb = y0;
+  const int dy = 2 * v - C::REACH;
+  const bool row_ok = lane < C::NU && yb + dy >= 0 && yb + dy + 16 <= H;
+  uint64_t best = kInvalidKey;
+#pragma unroll
+  for (int k = 0; k < C::NU; ++k) {
+    const int dx = 2 * k - C::REACH;
+    const bool ok = row_ok && xb + dx >= 0 && xb + dx + 16 <= W;
+    const uint64_t key = ok ? make_key(acc[k], dx, dy) : kInvalidKey;
+    best = key < best ? key : best;
+  }
+  if constexpr (C::NU == 33) {
+    {
+      const int dx = 2 * lane - C::REACH;
+      const bool ok = yb + 48 <= H && xb + dx >= 0 && xb + dx + 16 <= W;
+      const uint64_t key = ok ? make_key(accx, dx, 32) : kInvalidKey;
+      best = key < best ? key : best;
+    }
+    const uint32_t corner = __reduce_add_sync(0xffffffffu, accc);
+    if (lane == 0 && xb + 48 <= W && yb + 48 <= H) {
+      const uint64_t key = make_key(corner, 32, 32);
+      best = key < best ? key : best;
+    }
+  }
+  best = warp_min_u64(best);
+  if (lane == 0) out[((long long)pair * h + blockIdx.y) * w + bx] = key_to_mv(best);
+}
+
+template <int R>
+cudaError_t launch_r(const uint16_t* ref, const uint16_t* cur, int W, int H, int pitch, long long ref_bs,
+                     long long cur_bs, int batch, bayer_mv_t* out, cudaStream_t st) {
+  using C = Full16<R>;
+  const int h = H / 16, w = W / 16;
+  dim3 grid((w + kNW - 1) / kNW, h, batch);
+  me_full16_even_kernel<R><<<grid, kNW * 32, C::SMEM, st>>>(ref, cur, W, H, pitch, ref_bs, cur_bs, h, w, out);
+  return cudaGetLastError();
+}
+
+template <int R>
+cudaError_t configure_r() {
+  return cudaFuncSetAttribute(me_full16_even_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)Full16<R>::SMEM);
+}
+
+}  // namespace
+
+cudaError_t configure_full16() {
+  cudaError_t e;
+  if ((e = configure_r<4>()) != cudaSuccess) return e;
+  if ((e = configure_r<8>()) != cudaSuccess) return e;
+  if ((e = configure_r<12>()) != cudaSuccess) return e;
+  return configure_r<16>();
+}
+
+bool full16_even_supported(int range) { return range == 8 || range == 16 || range == 24 || range == 32; }
+
+cudaError_t launch_full16_even(const uint16_t* ref, const uint16_t* cur, int W, int H, int pitch, long long ref_bs,
+                               long long cur_bs, int batch, int range, bayer_mv_t* out, cudaStream_t st) {
+  switch (range) {
+    case 8: return launch_r<4>(ref, cur, W, H, pitch, ref_bs, cur_bs, batch, out, st);
+    case 16: return launch_r<8>(ref, cur, W, H, pitch, ref_bs, cur_bs, batch, out, st);
+    case 24: return launch_r<12>(ref, cur, W, H, pitch, ref_bs, cur_bs, batch, out, st);
+    case 32: return launch_r<16>(ref, cur, W, H, pitch, ref_bs, cur_bs, batch, out, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace bme

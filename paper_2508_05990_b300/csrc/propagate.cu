@@ -1,0 +1,182 @@
+// Motion-vector feature propagation z_pred = Warp(z_R, MV) (Sec. 3.3).
+//
+// Feature cell (fy, fx) takes the MV of the block holding raw pixel
+// (fy*s, fx*s) and samples z_R at (fy + dy/s, fx + dx/s).  NEAREST rounds the
+// offsets half away from zero (a pure copy, bit-exact); BILINEAR evaluates
+//   (1-wy)*((1-wx)*a + wx*b) + wy*((1-wx)*c + wx*d)
+// with every product and sum rounded separately (__fmul_rn/__fadd_rn), so the
+// result is reproducible bit for bit by any IEEE float evaluation in the same
+// order.  Indices are clamped to the map.
+//
+// HBM-bound: per map C*Hf*Wf*4 bytes read once and written once.
+//   NCHW: one thread per output cell (fy, fx) loops over the C planes, so the
+//         MV lookup and tap arithmetic are paid once per cell and every plane's
+//         store is a coalesced 128-byte warp row.
+//   NHWC: one thread per (cell, 4 channels) moves float4 vectors (taps are
+//         contiguous C-vectors), fully coalesced.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace bme {
+
+namespace {
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+__device__ __forceinline__ int floordiv(int a, int b) {
+  int q = a / b;
+  if ((a % b != 0) && (a < 0)) --q;
+  return q;
+}
+
+__device__ __forceinline__ int rounddiv(int a, int b) {
+  return a >= 0 ? (2 * a + b) / (2 * b) : -((2 * (-a) + b) / (2 * b));
+}
+
+struct Taps {
+  int y0, y1, x0, x1;
+  float wy, wx, owy, owx;
+};
+
+__device__ __forceinline__ Taps bilinear_taps(const PropArgs& a, int fy, int fx, bayer_mv_t m) {
+  Taps t;
+  const int qy = floordiv(m.dy, a.s), qx = floordiv(m.dx, a.s);
+  t.wy = __fdiv_rn((float)(m.dy - qy * a.s), (float)a.s);
+  t.wx = __fdiv_rn((float)(m.dx - qx * a.s), (float)a.s);
+  t.owy = __fsub_rn(1.0f, t.wy);
+  t.owx = __fsub_rn(1.0f, t.wx);
+  t.y0 = clampi(fy + qy, 0, a.Hf - 1);
+  t.y1 = clampi(fy + qy + 1, 0, a.Hf - 1);
+  t.x0 = clampi(fx + qx, 0, a.Wf - 1);
+  t.x1 = clampi(fx + qx + 1, 0, a.Wf - 1);
+  return t;
+}
+
+__device__ __forceinline__ float blend(const Taps& t, float va, float vb, float vc, float vd) {
+  const float top = __fadd_rn(__fmul_rn(t.owx, va), __fmul_rn(t.wx, vb));
+  const float bot = __fadd_rn(__fmul_rn(t.owx, vc), __fmul_rn(t.wx, vd));
+  return __fadd_rn(__fmul_rn(t.owy, top), __fmul_rn(t.wy, bot));
+}
+
+template <int INTERP>
+__global__ void __launch_bounds__(256) prop_nchw_kernel(const PropArgs a) {
+  const long long cells = (long long)a.Hf * a.Wf;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)a.n * cells) return;
+  const int m = (int)(t / cells);
+  const int rem = (int)(t - (long long)m * cells);
+  const int fy = rem / a.Wf, fx = rem - fy * a.Wf;
+  const bayer_mv_t mv = a.mv[((long long)m * a.mv_h + fy / a.cells) * a.mv_w + fx / a.cells];
+  const float* in = a.feat + (long long)m * a.C * cells;
+  float* out = a.out + (long long)m * a.C * cells + rem;
+  if (INTERP == BAYER_INTERP_NEAREST) {
+    const int sy = clampi(fy + rounddiv(mv.dy, a.s), 0, a.Hf - 1);
+    const int sx = clampi(fx + rounddiv(mv.dx, a.s), 0, a.Wf - 1);
+    const float* src = in + (long long)sy * a.Wf + sx;
+#pragma unroll 8
+    for (int c = 0; c < a.C; ++c) __stcs(out + c * cells, __ldg(src + c * cells));
+  } else {
+    const Taps tp = bilinear_taps(a, fy, fx, mv);
+    const float* pa = in + (long long)tp.y0 * a.Wf + tp.x0;
+    const float* pb = in + (long long)tp.y0 * a.Wf + tp.x1;
+    const float* pc = in + (long long)tp.y1 * a.Wf + tp.x0;
+    const float* pd = in + (long long)tp.y1 * a.Wf + tp.x1;
+#pragma unroll 4
+    for (int c = 0; c < a.C; ++c) {
+      const long long o = c * cells;
+      __stcs(out + o, blend(tp, __ldg(pa + o), __ldg(pb + o), __ldg(pc + o), __ldg(pd + o)));
+    }
+  }
+}
+
+// NHWC with C % 4 == 0: one thread per (map, cell, 4 channels).
+template <int INTERP>
+__global__ void __launch_bounds__(256) prop_nhwc4_kernel(const PropArgs a) {
+  const int c4n = a.C >> 2;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long cells = (long long)a.Hf * a.Wf;
+  if (t >= (long long)a.n * cells * c4n) return;
+  const int c4 = (int)(t % c4n);
+  const long long cell = t / c4n;
+  const int m = (int)(cell / cells);
+  const int rem = (int)(cell - (long long)m * cells);
+  const int fy = rem / a.Wf, fx = rem - fy * a.Wf;
+  const bayer_mv_t mv = a.mv[((long long)m * a.mv_h + fy / a.cells) * a.mv_w + fx / a.cells];
+  const float4* in = reinterpret_cast<const float4*>(a.feat + (long long)m * cells * a.C);
+  float4* out = reinterpret_cast<float4*>(a.out) + t;
+  if (INTERP == BAYER_INTERP_NEAREST) {
+    const int sy = clampi(fy + rounddiv(mv.dy, a.s), 0, a.Hf - 1);
+    const int sx = clampi(fx + rounddiv(mv.dx, a.s), 0, a.Wf - 1);
+    __stcs(out, __ldg(in + ((long long)sy * a.Wf + sx) * c4n + c4));
+  } else {
+    const Taps tp = bilinear_taps(a, fy, fx, mv);
+    const float4 va = __ldg(in + ((long long)tp.y0 * a.Wf + tp.x0) * c4n + c4);
+    const float4 vb = __ldg(in + ((long long)tp.y0 * a.Wf + tp.x1) * c4n + c4);
+    const float4 vc = __ldg(in + ((long long)tp.y1 * a.Wf + tp.x0) * c4n + c4);
+    const float4 vd = __ldg(in + ((long long)tp.y1 * a.Wf + tp.x1) * c4n + c4);
+    float4 r;
+    r.x = blend(tp, va.x, vb.x, vc.x, vd.x);
+    r.y = blend(tp, va.y, vb.y, vc.y, vd.y);
+    r.z = blend(tp, va.z, vb.z, vc.z, vd.z);
+    r.w = blend(tp, va.w, vb.w, vc.w, vd.w);
+    __stcs(out, r);
+  }
+}
+
+// NHWC, any C: one thread per (map, cell, channel).
+template <int INTERP>
+__global__ void __launch_bounds__(256) prop_nhwc1_kernel(const PropArgs a) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long cells = (long long)a.Hf * a.Wf;
+  if (t >= (long long)a.n * cells * a.C) return;
+  const int c = (int)(t % a.C);
+  const long long cell = t / a.C;
+  const int m = (int)(cell / cells);
+  const int rem = (int)(cell - (long long)m * cells);
+  const int fy = rem / a.Wf, fx = rem - fy * a.Wf;
+  const bayer_mv_t mv = a.mv[((long long)m * a.mv_h + fy / a.cells) * a.mv_w + fx / a.cells];
+  const float* in = a.feat + (long long)m * cells * a.C;
+  if (INTERP == BAYER_INTERP_NEAREST) {
+    const int sy = clampi(fy + rounddiv(mv.dy, a.s), 0, a.Hf - 1);
+    const int sx = clampi(fx + rounddiv(mv.dx, a.s), 0, a.Wf - 1);
+    a.out[t] = __ldg(in + ((long long)sy * a.Wf + sx) * a.C + c);
+  } else {
+    const Taps tp = bilinear_taps(a, fy, fx, mv);
+    a.out[t] = blend(tp, __ldg(in + ((long long)tp.y0 * a.Wf + tp.x0) * a.C + c),
+                     __ldg(in + ((long long)tp.y0 * a.Wf + tp.x1) * a.C + c),
+                     __ldg(in + ((long long)tp.y1 * a.Wf + tp.x0) * a.C + c),
+                     __ldg(in + ((long long)tp.y1 * a.Wf + tp.x1) * a.C + c));
+  }
+}
+
+inline unsigned blocks_for(long long threads, int per) { return (unsigned)((threads + per - 1) / per); }
+
+}  // namespace
+
+cudaError_t launch_propagate(const PropArgs& a, int layout, int interp, cudaStream_t st) {
+  const long long cells = (long long)a.n * a.Hf * a.Wf;
+  if (cells == 0 || a.C == 0) return cudaSuccess;
+  if (layout == BAYER_LAYOUT_NCHW) {
+    const unsigned g = blocks_for(cells, 256);
+    if (interp == BAYER_INTERP_NEAREST)
+      prop_nchw_kernel<BAYER_INTERP_NEAREST><<<g, 256, 0, st>>>(a);
+    else
+      prop_nchw_kernel<BAYER_INTERP_BILINEAR><<<g, 256, 0, st>>>(a);
+  } else if ((a.C & 3) == 0 && (reinterpret_cast<uintptr_t>(a.feat) & 15) == 0 &&
+             (reinterpret_cast<uintptr_t>(a.out) & 15) == 0) {
+    const unsigned g = blocks_for(cells * (a.C >> 2), 256);
+    if (interp == BAYER_INTERP_NEAREST)
+      prop_nhwc4_kernel<BAYER_INTERP_NEAREST><<<g, 256, 0, st>>>(a);
+    else
+      prop_nhwc4_kernel<BAYER_INTERP_BILINEAR><<<g, 256, 0, st>>>(a);
+  } else {
+    const unsigned g = blocks_for(cells * a.C, 256);
+    if (interp == BAYER_INTERP_NEAREST)
+      prop_nhwc1_kernel<BAYER_INTERP_NEAREST><<<g, 256, 0, st>>>(a);
+    else
+      prop_nhwc1_kernel<BAYER_INTERP_BILINEAR><<<g, 256, 0, st>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace bme
