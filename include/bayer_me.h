@@ -185,6 +185,31 @@ bayer_status_t bayer_me_sync_status(bayer_me_t h, void* stream);
 bayer_status_t bayer_probe_alu(bayer_me_t h, int variant, double* pc_per_clk_per_sm, double* sm_mhz,
                                int* sm_count);
 
+/* Allocation-free coarse-to-fine search.  The paper has no counterpart: this
+ * entry point serves callers that cannot call cudaMalloc -- for example a
+ * real-time frame loop, where an allocation can synchronise the device and
+ * stall every stream, or a host that commits all device memory to a fixed
+ * budget at start-up and forbids later allocations.  It takes no handle (a
+ * handle allocates its workspace) and runs the same search as
+ * bayer_me_estimate_ex with mode BAYER_MODE_C2F, on the current device.
+ *   Scratch: the intermediate pyramid fields live in one static device array
+ *     of BAYER_NOALLOC_SCRATCH_BYTES (1 MiB), which every GPU that loads the
+ *     library holds until the process exits.  2 x the largest intermediate
+ *     field (batch x h x w records of every level but the last) must fit in
+ *     it; larger requests return BAYER_ERR_UNSUPPORTED and launch nothing.
+ *   Set-up: the first call on a device looks the array's device address up
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   Sharing: all calls share the array, which keeps the last call's contents.
+ *     Every intermediate field is written before it is read, so nothing needs
+ *     clearing; calls whose work overlaps on the GPU (several streams or host
+ *     threads) race on the array and must be serialised by the caller.
+ *   Calls no cudaMalloc, cudaFree or other allocating routine.
+ *   Arguments as in bayer_me_estimate_ex (params->mode must be C2F). */
+#define BAYER_NOALLOC_SCRATCH_BYTES (1u << 20)
+bayer_status_t bayer_me_estimate_c2f_noalloc(const uint16_t* ref, const uint16_t* cur, int W, int H, int pitch,
+                                             const bayer_me_params_t* params, bayer_mv_t* mv_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -33,7 +33,7 @@ MAX_LEVELS = MAX_STAGES = 4
 # Every function the header declares (checked against include/bayer_me.h by the tests).
 EXPORTS = ("bayer_me_init", "bayer_me_destroy", "bayer_status_string", "bayer_me_estimate",
            "bayer_me_estimate_ex", "bayer_feat_propagate", "bayer_clip_process_host", "bayer_me_sync_status",
-           "bayer_probe_alu")
+           "bayer_probe_alu", "bayer_me_estimate_c2f_noalloc")
 
 
 class BayerError(RuntimeError):
@@ -74,6 +74,7 @@ def load(path: str = LIB_PATH):
     lib.bayer_me_sync_status.argtypes = [P, P]
     lib.bayer_probe_alu.argtypes = [P, I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                     ctypes.POINTER(ctypes.c_int)]
+    lib.bayer_me_estimate_c2f_noalloc.argtypes = [P, P, I, I, I, ctypes.POINTER(Params), P, P]
     for name in EXPORTS:
         if name != "bayer_status_string":
             getattr(lib, name).restype = I
@@ -243,6 +244,39 @@ class Handle:
         _check(self._lib.bayer_probe_alu(self._h, variant, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
                "bayer_probe_alu")
         return a.value, b.value, c.value
+
+
+def estimate_c2f_noalloc(ref, cur, c2f=None, phase=PHASE_EVEN, batch=1, ref_batch_stride=0, cur_batch_stride=0,
+                         out=None, stream=None, W=None, H=None, pitch=None):
+    """Coarse-to-fine search without any device allocation (no handle): the
+    intermediate pyramid fields use the library's static 1 MiB device scratch.
+    For callers that must not allocate after start-up.  ``out`` must be given
+    by such callers (allocating it here would defeat the purpose); it is only
+    created when omitted, for convenience in tests.  Calls that overlap on the
+    GPU share the scratch and must be serialised."""
+    import torch
+    lib = load()
+    if H is None or W is None:
+        H, W = ref.shape[-2:]
+    if pitch is None:
+        pitch = W
+    c2f = c2f or C2FSetting()
+    p = Params()
+    p.mode, p.phase = MODE_C2F, phase
+    p.n_levels = len(c2f.levels)
+    for i, b in enumerate(c2f.levels):
+        p.levels[i] = b
+    p.n_stages = len(c2f.stages)
+    for i, (r, s) in enumerate(c2f.stages):
+        p.stage_radius[i] = r
+        p.stage_step[i] = s
+    p.batch, p.ref_batch_stride, p.cur_batch_stride = batch, ref_batch_stride, cur_batch_stride
+    h, w = grid_shape(H, W, c2f.levels[-1])
+    if out is None:
+        out = torch.empty((batch, h, w, 2), dtype=torch.int32, device=ref.device)
+    _check(lib.bayer_me_estimate_c2f_noalloc(_ptr(ref), _ptr(cur), W, H, pitch, ctypes.byref(p), _ptr(out),
+                                             _stream(stream)), "bayer_me_estimate_c2f_noalloc")
+    return out
 
 
 def init(device: int = 0) -> Handle:
