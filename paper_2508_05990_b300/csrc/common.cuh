@@ -14,6 +14,11 @@ namespace bme {
 // difference of two words is exact too.  One copy serves both pipes.
 __device__ __forceinline__ uint32_t pix_word(uint32_t v) { return 0x4B000000u | v; }
 
+// Pixel words of the low / high 16-bit sample of a 32-bit word (one byte
+// permute each: bytes [v.b0, v.b1, 0x00, 0x4B] and [v.b2, v.b3, 0x00, 0x4B]).
+__device__ __forceinline__ uint32_t pix_lo(uint32_t two) { return __byte_perm(two, 0x4B000000u, 0x7610); }
+__device__ __forceinline__ uint32_t pix_hi(uint32_t two) { return __byte_perm(two, 0x4B000000u, 0x7632); }
+
 // |a - b| + c on the integer pipe (PTX sad.u32).
 __device__ __forceinline__ uint32_t sad_u32(uint32_t a, uint32_t b, uint32_t c) {
   uint32_t d;

@@ -2,10 +2,11 @@
 // Matching-based ME"; Sec. 3.2 "Matching Criterion": SAD, argmin = MV).
 //
 // Mapping (B300: 148 SMs, INT32 sad.u32 at 64 lanes/clk/SM):
-//   * one CTA = NW warps = NW horizontally adjacent blocks of one block row of
-//     one frame pair; the CTA stages the union of their search windows
+//   * one CTA = NW (8) warps = NW horizontally adjacent blocks of one block
+//     row of one frame pair; the CTA stages the union of their search windows
 //     ((16*NW + 4R) x (16 + 4R) pixels) and their current blocks into shared
-//     memory as 32-bit pixel words;
+//     memory as 32-bit pixel words, 8 pixels per 16-byte load with every load
+//     of a thread in flight before the first conversion;
 //   * one warp = one block; lane v owns candidate row v (dy = 2v - 2R) and all
 //     2R+1 candidates of that row (dx = 2u - 2R).  Adjacent candidates of a
 //     row are one 32-bit word apart (EVEN offsets), so every reference word a
@@ -17,7 +18,9 @@
 //     window pitch of 4*(odd) words makes every 128-bit shared load
 //     conflict-free;
 //   * argmin: each lane folds its candidates into a uint64 key
-//     (sad, |dx|+|dy|, dy, dx), then a 5-step shuffle minimum.
+//     (sad, |dx|+|dy|, dy, dx) -- on interior blocks through a 32-bit
+//     sad*64 + rank key, rank being the tie-break order within the lane's row
+//     -- then a 5-step shuffle minimum.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -25,7 +28,7 @@ namespace bme {
 
 namespace {
 
-constexpr int kNW = 4;  // warps (blocks) per CTA
+constexpr int kNW = 8;  // warps (blocks) per CTA
 
 template <int R>
 struct Full16 {
@@ -47,7 +50,7 @@ __global__ void __launch_bounds__(kNW * 32) me_full16_even_kernel(const uint16_t
                                                                    const uint16_t* __restrict__ cur_base, int W,
                                                                    int H, int pitch, long long ref_bs,
                                                                    long long cur_bs, int h, int w,
-                                                                   bayer_mv_t* __restrict__ out) {
+                                                                   bayer_mv_t* __restrict__ out, bool vec_ok) {
   using C = Full16<R>;
   extern __shared__ __align__(16) uint32_t smem[];
   uint32_t* win = smem;                 // WIN_H x P
@@ -60,23 +63,65 @@ __global__ void __launch_bounds__(kNW * 32) me_full16_even_kernel(const uint16_t
   const int x0 = blockIdx.x * kNW * 16, y0 = blockIdx.y * 16;
 
   // ---- stage the reference window and the current tile (out-of-frame = 0)
-  for (int ry = warp; ry < C::WIN_H; ry += kNW) {
-    const int gy = y0 - C::REACH + ry;
-    const bool row_in = gy >= 0 && gy < H;
-    for (int rx = lane; rx < C::WIN_W; rx += 32) {
-      const int gx = x0 - C::REACH + rx;
-      uint32_t v = 0;
-      if (row_in && gx >= 0 && gx < W) v = __ldg(ref + (long long)gy * pitch + gx);
-      win[ry * C::P + rx] = pix_word(v);
+  if (vec_ok) {
+    // 8 pixels (16 bytes) per load: the window origin x0 - 2R and the tile
+    // origin x0 are multiples of 8 and W is a multiple of 16, so every 8-pixel
+    // chunk lies wholly inside or wholly outside the frame.  All loads of a
+    // thread are issued before any conversion.
+    constexpr int WCH = C::WIN_W / 8, NWCH = WCH * C::WIN_H;
+    constexpr int TCH = 2 * kNW, NTCH = TCH * 16;
+    constexpr int PER = (NWCH + NTCH + kNW * 32 - 1) / (kNW * 32);
+    uint4 raw[PER];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int e = threadIdx.x + i * kNW * 32;
+      raw[i] = make_uint4(0, 0, 0, 0);
+      if (e < NWCH) {
+        const int ry = e / WCH, cx = e - ry * WCH;
+        const int gy = y0 - C::REACH + ry, gx = x0 - C::REACH + 8 * cx;
+        if (gy >= 0 && gy < H && gx >= 0 && gx < W)
+          raw[i] = __ldg(reinterpret_cast<const uint4*>(ref + (long long)gy * pitch + gx));
+      } else if (e < NWCH + NTCH) {
+        const int f = e - NWCH, ry = f / TCH, cx = f - ry * TCH;
+        const int gx = x0 + 8 * cx;
+        if (gx < W) raw[i] = __ldg(reinterpret_cast<const uint4*>(cur + (long long)(y0 + ry) * pitch + gx));
+      }
     }
-  }
-  for (int ry = warp; ry < 16; ry += kNW) {
-    const int gy = y0 + ry;
-    for (int rx = lane; rx < 16 * kNW; rx += 32) {
-      const int gx = x0 + rx;
-      uint32_t v = 0;
-      if (gy < H && gx < W) v = __ldg(cur + (long long)gy * pitch + gx);
-      curt[ry * C::PC + rx] = pix_word(v);
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int e = threadIdx.x + i * kNW * 32;
+      uint32_t* dst;
+      if (e < NWCH) {
+        const int ry = e / WCH, cx = e - ry * WCH;
+        dst = win + ry * C::P + 8 * cx;
+      } else if (e < NWCH + NTCH) {
+        const int f = e - NWCH, ry = f / TCH, cx = f - ry * TCH;
+        dst = curt + ry * C::PC + 8 * cx;
+      } else {
+        continue;
+      }
+      reinterpret_cast<uint4*>(dst)[0] = make_uint4(pix_lo(raw[i].x), pix_hi(raw[i].x), pix_lo(raw[i].y), pix_hi(raw[i].y));
+      reinterpret_cast<uint4*>(dst)[1] = make_uint4(pix_lo(raw[i].z), pix_hi(raw[i].z), pix_lo(raw[i].w), pix_hi(raw[i].w));
+    }
+  } else {
+    for (int ry = warp; ry < C::WIN_H; ry += kNW) {
+      const int gy = y0 - C::REACH + ry;
+      const bool row_in = gy >= 0 && gy < H;
+      for (int rx = lane; rx < C::WIN_W; rx += 32) {
+        const int gx = x0 - C::REACH + rx;
+        uint32_t v = 0;
+        if (row_in && gx >= 0 && gx < W) v = __ldg(ref + (long long)gy * pitch + gx);
+        win[ry * C::P + rx] = pix_word(v);
+      }
+    }
+    for (int ry = warp; ry < 16; ry += kNW) {
+      const int gy = y0 + ry;
+      for (int rx = lane; rx < 16 * kNW; rx += 32) {
+        const int gx = x0 + rx;
+        uint32_t v = 0;
+        if (gy < H && gx < W) v = __ldg(cur + (long long)gy * pitch + gx);
+        curt[ry * C::PC + rx] = pix_word(v);
+      }
     }
   }
   __syncthreads();
@@ -139,14 +184,31 @@ __global__ void __launch_bounds__(kNW * 32) me_full16_even_kernel(const uint16_t
   // ---- argmin with the (sad, |mv|_1, dy, dx) key
   const int xb = bx * 16, yb = y0;
   const int dy = 2 * v - C::REACH;
-  const bool row_ok = lane < C::NU && yb + dy >= 0 && yb + dy + 16 <= H;
   uint64_t best = kInvalidKey;
+  const bool interior = xb >= C::REACH && xb + 16 + C::REACH <= W && yb >= C::REACH && yb + 16 + C::REACH <= H;
+  if (interior) {
+    // Every candidate is valid.  Within a lane dy is fixed, so the tie-break
+    // (|dx|+|dy|, dy, dx) orders the row by rank = 0 for dx = 0, then -2, +2,
+    // -4, +4, ...; sad * 64 + rank is a 32-bit key (sad < 2^25, rank <= 32).
+    uint32_t m = 0xFFFFFFFFu;
 #pragma unroll
-  for (int k = 0; k < C::NU; ++k) {
-    const int dx = 2 * k - C::REACH;
-    const bool ok = row_ok && xb + dx >= 0 && xb + dx + 16 <= W;
-    const uint64_t key = ok ? make_key(acc[k], dx, dy) : kInvalidKey;
-    best = key < best ? key : best;
+    for (int k = 0; k < C::NU; ++k) {
+      const uint32_t rank = k == R ? 0u : (k < R ? (uint32_t)(2 * (R - k) - 1) : (uint32_t)(2 * (k - R)));
+      const uint32_t key = acc[k] * 64u + rank;
+      m = key < m ? key : m;
+    }
+    const uint32_t rank = m & 63u;
+    const int k = rank == 0 ? R : ((rank & 1u) ? R - (int)((rank + 1) >> 1) : R + (int)(rank >> 1));
+    if (lane < C::NU) best = make_key(m >> 6, 2 * k - C::REACH, dy);
+  } else {
+    const bool row_ok = lane < C::NU && yb + dy >= 0 && yb + dy + 16 <= H;
+#pragma unroll
+    for (int k = 0; k < C::NU; ++k) {
+      const int dx = 2 * k - C::REACH;
+      const bool ok = row_ok && xb + dx >= 0 && xb + dx + 16 <= W;
+      const uint64_t key = ok ? make_key(acc[k], dx, dy) : kInvalidKey;
+      best = key < best ? key : best;
+    }
   }
   if constexpr (C::NU == 33) {
     {
@@ -171,7 +233,10 @@ cudaError_t launch_r(const uint16_t* ref, const uint16_t* cur, int W, int H, int
   using C = Full16<R>;
   const int h = H / 16, w = W / 16;
   dim3 grid((w + kNW - 1) / kNW, h, batch);
-  me_full16_even_kernel<R><<<grid, kNW * 32, C::SMEM, st>>>(ref, cur, W, H, pitch, ref_bs, cur_bs, h, w, out);
+  // 16-byte loads need 16-byte aligned rows in every frame of the batch
+  const bool vec_ok = (reinterpret_cast<uintptr_t>(ref) % 16) == 0 && (reinterpret_cast<uintptr_t>(cur) % 16) == 0 &&
+                      pitch % 8 == 0 && ref_bs % 8 == 0 && cur_bs % 8 == 0;
+  me_full16_even_kernel<R><<<grid, kNW * 32, C::SMEM, st>>>(ref, cur, W, H, pitch, ref_bs, cur_bs, h, w, out, vec_ok);
   return cudaGetLastError();
 }
 

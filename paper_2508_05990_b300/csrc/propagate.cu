@@ -9,9 +9,10 @@
 // order.  Indices are clamped to the map.
 //
 // HBM-bound: per map C*Hf*Wf*4 bytes read once and written once.
-//   NCHW: one thread per output cell (fy, fx) loops over the C planes, so the
-//         MV lookup and tap arithmetic are paid once per cell and every plane's
-//         store is a coalesced 128-byte warp row.
+//   NCHW: one thread per output cell (fy, fx) and chunk of 8 channels; the
+//         MV lookup and tap arithmetic are paid once per chunk, all tap loads
+//         of the chunk are in flight together, and every plane's store is a
+//         coalesced 128-byte warp row.
 //   NHWC: one thread per (cell, 4 channels) moves float4 vectors (taps are
 //         contiguous C-vectors), fully coalesced.
 #include "common.cuh"
@@ -58,33 +59,58 @@ __device__ __forceinline__ float blend(const Taps& t, float va, float vb, float 
   return __fadd_rn(__fmul_rn(t.owy, top), __fmul_rn(t.wy, bot));
 }
 
+// NCHW: one thread per output cell (fy, fx) and chunk of kCK channels
+// (grid.y = map x channel chunk).  The MV lookup and tap arithmetic are paid
+// once per chunk; all kCK x 4 tap loads are issued before any arithmetic, and
+// each plane's store is a coalesced warp row.
+constexpr int kCK = 8;
+
 template <int INTERP>
-__global__ void __launch_bounds__(256) prop_nchw_kernel(const PropArgs a) {
-  const long long cells = (long long)a.Hf * a.Wf;
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long long)a.n * cells) return;
-  const int m = (int)(t / cells);
-  const int rem = (int)(t - (long long)m * cells);
-  const int fy = rem / a.Wf, fx = rem - fy * a.Wf;
+__global__ void __launch_bounds__(256) prop_nchw_kernel(const PropArgs a, int nchunks) {
+  const int cells = a.Hf * a.Wf;
+  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= cells) return;
+  const int m = blockIdx.y / nchunks;
+  const int c0 = (blockIdx.y - m * nchunks) * kCK;
+  const int fy = cell / a.Wf, fx = cell - fy * a.Wf;
   const bayer_mv_t mv = a.mv[((long long)m * a.mv_h + fy / a.cells) * a.mv_w + fx / a.cells];
-  const float* in = a.feat + (long long)m * a.C * cells;
-  float* out = a.out + (long long)m * a.C * cells + rem;
+  const float* in = a.feat + ((long long)m * a.C + c0) * cells;
+  float* out = a.out + ((long long)m * a.C + c0) * cells + cell;
+  const int nc = min(kCK, a.C - c0);
   if (INTERP == BAYER_INTERP_NEAREST) {
     const int sy = clampi(fy + rounddiv(mv.dy, a.s), 0, a.Hf - 1);
     const int sx = clampi(fx + rounddiv(mv.dx, a.s), 0, a.Wf - 1);
-    const float* src = in + (long long)sy * a.Wf + sx;
-#pragma unroll 8
-    for (int c = 0; c < a.C; ++c) __stcs(out + c * cells, __ldg(src + c * cells));
+    const float* src = in + sy * a.Wf + sx;
+    if (nc == kCK) {
+      float v[kCK];
+#pragma unroll
+      for (int c = 0; c < kCK; ++c) v[c] = __ldg(src + (long long)c * cells);
+#pragma unroll
+      for (int c = 0; c < kCK; ++c) __stcs(out + (long long)c * cells, v[c]);
+    } else {
+      for (int c = 0; c < nc; ++c) __stcs(out + (long long)c * cells, __ldg(src + (long long)c * cells));
+    }
   } else {
     const Taps tp = bilinear_taps(a, fy, fx, mv);
-    const float* pa = in + (long long)tp.y0 * a.Wf + tp.x0;
-    const float* pb = in + (long long)tp.y0 * a.Wf + tp.x1;
-    const float* pc = in + (long long)tp.y1 * a.Wf + tp.x0;
-    const float* pd = in + (long long)tp.y1 * a.Wf + tp.x1;
-#pragma unroll 4
-    for (int c = 0; c < a.C; ++c) {
-      const long long o = c * cells;
-      __stcs(out + o, blend(tp, __ldg(pa + o), __ldg(pb + o), __ldg(pc + o), __ldg(pd + o)));
+    const int oa = tp.y0 * a.Wf + tp.x0, ob = tp.y0 * a.Wf + tp.x1;
+    const int oc = tp.y1 * a.Wf + tp.x0, od = tp.y1 * a.Wf + tp.x1;
+    if (nc == kCK) {
+      float va[kCK], vb[kCK], vc[kCK], vd[kCK];
+#pragma unroll
+      for (int c = 0; c < kCK; ++c) {
+        const float* pl = in + (long long)c * cells;
+        va[c] = __ldg(pl + oa);
+        vb[c] = __ldg(pl + ob);
+        vc[c] = __ldg(pl + oc);
+        vd[c] = __ldg(pl + od);
+      }
+#pragma unroll
+      for (int c = 0; c < kCK; ++c) __stcs(out + (long long)c * cells, blend(tp, va[c], vb[c], vc[c], vd[c]));
+    } else {
+      for (int c = 0; c < nc; ++c) {
+        const float* pl = in + (long long)c * cells;
+        __stcs(out + (long long)c * cells, blend(tp, __ldg(pl + oa), __ldg(pl + ob), __ldg(pl + oc), __ldg(pl + od)));
+      }
     }
   }
 }
@@ -157,11 +183,13 @@ cudaError_t launch_propagate(const PropArgs& a, int layout, int interp, cudaStre
   const long long cells = (long long)a.n * a.Hf * a.Wf;
   if (cells == 0 || a.C == 0) return cudaSuccess;
   if (layout == BAYER_LAYOUT_NCHW) {
-    const unsigned g = blocks_for(cells, 256);
+    const int nchunks = (a.C + kCK - 1) / kCK;
+    if ((long long)a.n * nchunks > 65535 || (long long)a.Hf * a.Wf > (1ll << 31) - 256) return cudaErrorInvalidValue;
+    dim3 g(blocks_for((long long)a.Hf * a.Wf, 256), a.n * nchunks);
     if (interp == BAYER_INTERP_NEAREST)
-      prop_nchw_kernel<BAYER_INTERP_NEAREST><<<g, 256, 0, st>>>(a);
+      prop_nchw_kernel<BAYER_INTERP_NEAREST><<<g, 256, 0, st>>>(a, nchunks);
     else
-      prop_nchw_kernel<BAYER_INTERP_BILINEAR><<<g, 256, 0, st>>>(a);
+      prop_nchw_kernel<BAYER_INTERP_BILINEAR><<<g, 256, 0, st>>>(a, nchunks);
   } else if ((a.C & 3) == 0 && (reinterpret_cast<uintptr_t>(a.feat) & 15) == 0 &&
              (reinterpret_cast<uintptr_t>(a.out) & 15) == 0) {
     const unsigned g = blocks_for(cells * (a.C >> 2), 256);
