@@ -55,6 +55,28 @@ def prop_bytes_per_pair() -> int:
     return 2 * C * HF * WF * 4 + (H // BLOCK) * (W // BLOCK) * 8
 
 
+ME_SOURCES = ("paper_2508_05990_b300/csrc/me_full16.cu", "paper_2508_05990_b300/csrc/common.cuh")
+PROP_SOURCES = ("paper_2508_05990_b300/csrc/propagate.cu", "paper_2508_05990_b300/csrc/common.cuh")
+
+
+def profiled_traffic(summary: str, sources) -> int | None:
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from an ncu
+    summary under profiles/, or None once the kernel's source differs from the one the
+    counters were taken on (the summary records a hash of it)."""
+    import hashlib
+    import re
+    try:
+        text = open(os.path.join(ROOT, "profiles", summary)).read()
+        blob = b"".join(open(os.path.join(ROOT, f), "rb").read() for f in sources)
+    except OSError:
+        return None
+    m_sha = re.search(r"source_sha256_16:\s*([0-9a-f]{16})", text)
+    m_bytes = re.search(r"traffic_bytes_per_launch:\s*(\d+)", text)
+    if not m_sha or not m_bytes or m_sha.group(1) != hashlib.sha256(blob).hexdigest()[:16]:
+        return None
+    return int(m_bytes.group(1))
+
+
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
@@ -93,7 +115,7 @@ def make_inputs(rank: int):
 
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons while running."""
-    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+    Q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
@@ -104,7 +126,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                          "-lms", "100", "-i", str(self.index)], stdout=subprocess.PIPE,
+                                          "-lms", "20", "-i", str(self.index)], stdout=subprocess.PIPE,
                                          stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -121,25 +143,30 @@ class ClockSampler:
                 out, _ = self.proc.communicate()
             self.lines = [l for l in out.splitlines() if l.strip()]
 
-    def summary(self):
-        sm, mx, reasons = [], [], set()
+    def summary(self, t0=None, t1=None):
+        """Median SM clock and active throttle reasons over the samples taken
+        between host times t0 and t1 (all samples if none fall inside)."""
+        import datetime
+        parsed = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for l in self.lines:
             f = [x.strip() for x in l.split(",")]
-            if len(f) < 8:
+            if len(f) < 9:
                 continue
             try:
-                sm.append(float(f[0]))
-                mx.append(float(f[1]))
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                sm, mx = float(f[1]), float(f[2])
             except ValueError:
                 continue
-            for n, v in zip(names, f[4:8]):
-                if v.lower().startswith("active"):
-                    reasons.add(n)
-        if not sm:
+            reasons = {n for n, v in zip(names, f[5:9]) if v.lower().startswith("active")}
+            parsed.append((ts, sm, mx, reasons))
+        inside = [p for p in parsed if t0 is not None and t0 - 0.05 <= p[0] <= t1 + 0.05]
+        use = inside or parsed
+        if not use:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return {"sm_mhz": statistics.median(p[1] for p in use), "sm_max_mhz": max(p[2] for p in use),
+                "reasons": sorted(set().union(*(p[3] for p in use))), "samples": len(use),
+                "window": "timed region" if inside else "whole run"}
 
 
 def cpu_baseline_sample(frames, feats):
@@ -194,12 +221,14 @@ def run_ours(args):
     barrier(world)
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        time.sleep(0.3)  # let the sampler start
+        time.sleep(0.5)  # let the sampler start
+        t_host0 = time.time()
         start.record(stream)
         for k in range(args.steps):
             step(evs[k])
         end.record(stream)
         torch.cuda.synchronize()
+        t_host1 = time.time()
     barrier(world)
     ms_total = start.elapsed_time(end)
     ms_total = max_over_ranks(ms_total, world, device="cuda")
@@ -226,7 +255,7 @@ def run_ours(args):
     pc_clk_sm, probe_mhz, nsm = h.probe_alu(0)
     result = None
     if rank == 0:
-        clocks = clk.summary()
+        clocks = clk.summary(t_host0, t_host1)
         sm_mhz = clocks["sm_mhz"] or probe_mhz
         me_avg_s = statistics.mean(me_ms) / 1e3
         achieved = PAIRS * pc_per_pair() / me_avg_s / 1e9
@@ -252,9 +281,14 @@ def run_ours(args):
                          "peak": round(peak, 1), "unit": "G pixel-candidates/s", "frac": round(achieved / peak, 4),
                          "peak_source": f"measured sad.u32 loop: {pc_clk_sm:.1f} pc/clk/SM x {nsm} SMs x "
                                         f"{sm_mhz:.0f} MHz (median SM clock under load)",
-                         "traffic": None, "avg_launch_ms": round(me_avg_s * 1e3, 4)},
+                         "traffic": profiled_traffic("me_full16_even_1080p_clip.md", ME_SOURCES),
+                         "traffic_unit": "DRAM bytes per launch (ncu)",
+                         "algorithmic_per_launch": f"{PAIRS * pc_per_pair()} pixel-candidates",
+                         "avg_launch_ms": round(me_avg_s * 1e3, 4)},
             "propagation": {"bound": "hbm", "achieved": round(prop_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                             "frac": round(prop_gbs / hbm_peak, 4), "avg_launch_ms": round(prop_avg_s * 1e3, 4),
+                            "traffic": profiled_traffic("prop_nchw_bilinear_1080p_clip.md", PROP_SOURCES),
+                            "algorithmic_bytes_per_launch": PAIRS * prop_bytes_per_pair(),
                             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
             "mblocks_per_s": round(value * hb * wb / 1e6, 3),
             "e2e": {"value": round(world * PAIRS * args.steps / e2e_s, 2), "unit": UNIT,
@@ -309,7 +343,7 @@ def run_reference(args):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
