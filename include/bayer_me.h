@@ -185,6 +185,76 @@ bayer_status_t bayer_me_sync_status(bayer_me_t h, void* stream);
 bayer_status_t bayer_probe_alu(bayer_me_t h, int variant, double* pc_per_clk_per_sm, double* sm_mhz,
                                int* sm_count);
 
+/* ---------------------------------------------------------------------------
+ * Learned-seeded search (not in the paper).  A small CNN proposes an MV and a
+ * confidence per 16x16 block; confident blocks are refined by one +-4 stage
+ * (R = 2, step 2) around the proposal, the others fall back to the exhaustive
+ * +-range search -- the SEEDED mode of bayer_me_estimate_ex with the proposals
+ * computed on the device.  The network follows the paper's recipe for its own
+ * learned module where one exists: AdamW with a cosine schedule (Sec. 4.1
+ * "Training Details") and the BerHu loss (Sec. 3.3).
+ *
+ * Network, parameters as one flat vector (float32 master, bfloat16 copy, both
+ * caller-owned device arrays of BAYER_CNN_NPARAMS elements, the bf16 copy
+ * passed as uint16_t):
+ *   x0 = 8 channels: the R, G (R row), G (B row), B planes of ref, then of cur,
+ *        at half resolution, each sample v / 2048 - 1
+ *   x_l = ReLU(conv3x3(x_{l-1}, stride 2, zero pad 1) + b_l), 32 channels,
+ *        l = 1..4; weights w_l[co][ci][ky][kx]
+ *   z = head 1x1 conv 32 -> 12 + bias; channel 3*(2*sy + sx) + q of L4 cell
+ *       (i, k) is quantity q of block (2i + sy, 2k + sx)
+ *   dx = range * tanh(z_0), dy = range * tanh(z_1), conf = sigmoid(z_2)
+ * Activations are bfloat16, accumulation float32.  W and H must be multiples
+ * of 32 (the L4 grid is then exactly half the 16x16 block grid).
+ * Loss (mean over the blocks of the batch): BerHu_4(dx - dx*) +
+ * BerHu_4(dy - dy*) + BCE(conf, t), BerHu_c(e) = |e| for |e| <= c, else
+ * (e^2 + c^2) / (2c); t = 1 where the proposal rounded to the nearest even
+ * integer lies within +-4 of the label (dx*, dy*) in both components. */
+#define BAYER_CNN_W1 0
+#define BAYER_CNN_B1 2304
+#define BAYER_CNN_W2 2336
+#define BAYER_CNN_B2 11552
+#define BAYER_CNN_W3 11584
+#define BAYER_CNN_B3 20800
+#define BAYER_CNN_W4 20832
+#define BAYER_CNN_B4 30048
+#define BAYER_CNN_WH 30080
+#define BAYER_CNN_BH 30464
+#define BAYER_CNN_NPARAMS 30476
+
+/* Network forward on `batch` frame pairs (strides as in bayer_me_params_t):
+ * prop_dxdy [batch][H/16][W/16][2] and conf [batch][H/16][W/16] (device
+ * float32).  Activations use the handle's workspace. */
+bayer_status_t bayer_cnn_forward(bayer_me_t h, const uint16_t* ref, const uint16_t* cur, int W, int H, int pitch,
+                                 int batch, long long ref_batch_stride, long long cur_batch_stride,
+                                 const uint16_t* w_bf16, int range, float* prop_dxdy, float* conf, void* stream);
+
+/* Loss and its gradient w.r.t. all parameters on `batch` pairs labelled by
+ * `labels` [batch][H/16][W/16] (the exhaustive-search fields): grad
+ * [BAYER_CNN_NPARAMS] and loss [1], device float32, overwritten. */
+bayer_status_t bayer_cnn_loss_grad(bayer_me_t h, const uint16_t* ref, const uint16_t* cur, int W, int H, int pitch,
+                                   int batch, long long ref_batch_stride, long long cur_batch_stride,
+                                   const uint16_t* w_bf16, const bayer_mv_t* labels, int range, float* grad,
+                                   float* loss, void* stream);
+
+/* One AdamW step (decoupled weight decay, bias-corrected moments) on the
+ * float32 master w, refreshing the bfloat16 copy; step counts from 1. */
+bayer_status_t bayer_cnn_adamw(bayer_me_t h, float* w, uint16_t* w_bf16, const float* grad, float* m, float* v,
+                               int step, float lr, float beta1, float beta2, float eps, float weight_decay,
+                               void* stream);
+
+/* Learned-seeded search: network forward, +-4 refine of the blocks with
+ * conf >= conf_thresh, exhaustive +-range search of the others (block 16,
+ * EVEN phase, range in {8, 16, 24, 32}).  mv_out [batch][H/16][W/16];
+ * fallback_out (optional) 1 where the full search ran; n_fallback (optional,
+ * device int) the number of such blocks.  The result is exactly the SEEDED
+ * mode of bayer_me_estimate_ex given the network's proposals. */
+bayer_status_t bayer_me_estimate_learned(bayer_me_t h, const uint16_t* ref, const uint16_t* cur, int W, int H,
+                                         int pitch, int batch, long long ref_batch_stride,
+                                         long long cur_batch_stride, const uint16_t* w_bf16, int range,
+                                         float conf_thresh, bayer_mv_t* mv_out, uint8_t* fallback_out,
+                                         int* n_fallback, void* stream);
+
 /* Allocation-free coarse-to-fine search.  The paper has no counterpart: this
  * entry point serves callers that cannot call cudaMalloc -- for example a
  * real-time frame loop, where an allocation can synchronise the device and

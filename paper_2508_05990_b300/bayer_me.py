@@ -33,7 +33,14 @@ MAX_LEVELS = MAX_STAGES = 4
 # Every function the header declares (checked against include/bayer_me.h by the tests).
 EXPORTS = ("bayer_me_init", "bayer_me_destroy", "bayer_status_string", "bayer_me_estimate",
            "bayer_me_estimate_ex", "bayer_feat_propagate", "bayer_clip_process_host", "bayer_me_sync_status",
-           "bayer_probe_alu", "bayer_me_estimate_c2f_noalloc")
+           "bayer_probe_alu", "bayer_me_estimate_c2f_noalloc", "bayer_cnn_forward", "bayer_cnn_loss_grad",
+           "bayer_cnn_adamw", "bayer_me_estimate_learned")
+
+# Flat parameter layout of the proposal network (BAYER_CNN_* in the header).
+CNN_OFFSETS = dict(w1=0, b1=2304, w2=2336, b2=11552, w3=11584, b3=20800, w4=20832, b4=30048, wh=30080, bh=30464)
+CNN_NPARAMS = 30476
+CNN_SHAPES = [("w", (32, 8, 3, 3)), ("b", (32,)), ("w", (32, 32, 3, 3)), ("b", (32,)), ("w", (32, 32, 3, 3)),
+              ("b", (32,)), ("w", (32, 32, 3, 3)), ("b", (32,)), ("w", (12, 32)), ("b", (12,))]
 
 
 class BayerError(RuntimeError):
@@ -75,6 +82,10 @@ def load(path: str = LIB_PATH):
     lib.bayer_probe_alu.argtypes = [P, I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                     ctypes.POINTER(ctypes.c_int)]
     lib.bayer_me_estimate_c2f_noalloc.argtypes = [P, P, I, I, I, ctypes.POINTER(Params), P, P]
+    lib.bayer_cnn_forward.argtypes = [P, P, P, I, I, I, I, LL, LL, P, I, P, P, P]
+    lib.bayer_cnn_loss_grad.argtypes = [P, P, P, I, I, I, I, LL, LL, P, P, I, P, P, P]
+    lib.bayer_cnn_adamw.argtypes = [P, P, P, P, P, P, I, F, F, F, F, F, P]
+    lib.bayer_me_estimate_learned.argtypes = [P, P, P, I, I, I, I, LL, LL, P, I, F, P, P, P, P]
     for name in EXPORTS:
         if name != "bayer_status_string":
             getattr(lib, name).restype = I
@@ -235,6 +246,55 @@ class Handle:
                "bayer_clip_process_host")
         return mv_out, feat_out
 
+    # -- learned proposal network and learned-seeded search -----------------
+    def cnn_forward(self, ref, cur, w_bf16, search_range=32, batch=1, ref_batch_stride=0, cur_batch_stride=0,
+                    prop=None, conf=None, stream=None):
+        """Proposals [batch, h, w, 2] and confidences [batch, h, w] (float32 tensors)."""
+        import torch
+        H, W = ref.shape[-2:]
+        h, w = H // 16, W // 16
+        if prop is None:
+            prop = torch.empty((batch, h, w, 2), dtype=torch.float32, device=ref.device)
+        if conf is None:
+            conf = torch.empty((batch, h, w), dtype=torch.float32, device=ref.device)
+        _check(self._lib.bayer_cnn_forward(self._h, _ptr(ref), _ptr(cur), W, H, W, batch, ref_batch_stride,
+                                           cur_batch_stride, _ptr(w_bf16), search_range, _ptr(prop), _ptr(conf),
+                                           _stream(stream)), "bayer_cnn_forward")
+        return prop, conf
+
+    def cnn_loss_grad(self, ref, cur, w_bf16, labels, search_range=32, batch=1, ref_batch_stride=0,
+                      cur_batch_stride=0, grad=None, loss=None, stream=None):
+        """(grad [CNN_NPARAMS], loss [1]) float32 tensors; labels: int32 records [batch, h, w, 2]."""
+        import torch
+        H, W = ref.shape[-2:]
+        if grad is None:
+            grad = torch.empty(CNN_NPARAMS, dtype=torch.float32, device=ref.device)
+        if loss is None:
+            loss = torch.empty(1, dtype=torch.float32, device=ref.device)
+        _check(self._lib.bayer_cnn_loss_grad(self._h, _ptr(ref), _ptr(cur), W, H, W, batch, ref_batch_stride,
+                                             cur_batch_stride, _ptr(w_bf16), _ptr(labels), search_range, _ptr(grad),
+                                             _ptr(loss), _stream(stream)), "bayer_cnn_loss_grad")
+        return grad, loss
+
+    def cnn_adamw(self, w, w_bf16, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.01,
+                  stream=None):
+        _check(self._lib.bayer_cnn_adamw(self._h, _ptr(w), _ptr(w_bf16), _ptr(grad), _ptr(m), _ptr(v), int(step),
+                                         float(lr), float(beta1), float(beta2), float(eps), float(weight_decay),
+                                         _stream(stream)), "bayer_cnn_adamw")
+
+    def estimate_learned(self, ref, cur, w_bf16, search_range=32, conf_thresh=0.5, batch=1, ref_batch_stride=0,
+                         cur_batch_stride=0, out=None, fallback=None, n_fallback=None, stream=None):
+        """Learned-seeded search; returns the [batch, h, w, 2] int32 record tensor."""
+        import torch
+        H, W = ref.shape[-2:]
+        if out is None:
+            out = torch.empty((batch, H // 16, W // 16, 2), dtype=torch.int32, device=ref.device)
+        _check(self._lib.bayer_me_estimate_learned(self._h, _ptr(ref), _ptr(cur), W, H, W, batch, ref_batch_stride,
+                                                   cur_batch_stride, _ptr(w_bf16), search_range, float(conf_thresh),
+                                                   _ptr(out), _ptr(fallback), _ptr(n_fallback), _stream(stream)),
+               "bayer_me_estimate_learned")
+        return out
+
     def sync_status(self, stream=None) -> int:
         return int(self._lib.bayer_me_sync_status(self._h, _stream(stream)))
 
@@ -277,6 +337,12 @@ def estimate_c2f_noalloc(ref, cur, c2f=None, phase=PHASE_EVEN, batch=1, ref_batc
     _check(lib.bayer_me_estimate_c2f_noalloc(_ptr(ref), _ptr(cur), W, H, pitch, ctypes.byref(p), _ptr(out),
                                              _stream(stream)), "bayer_me_estimate_c2f_noalloc")
     return out
+
+
+def to_bf16_bits(w32):
+    """float32 tensor -> bfloat16 tensor viewed as int16 (the layout the C ABI takes as uint16_t)."""
+    import torch
+    return w32.to(torch.bfloat16).view(torch.int16)
 
 
 def init(device: int = 0) -> Handle:

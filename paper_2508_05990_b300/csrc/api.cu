@@ -25,6 +25,15 @@ struct bayer_me_s {
   size_t fout_bytes = 0;
   bayer_mv_t* d_mv = nullptr;
   size_t mv_bytes = 0;
+  // learned proposal network and seeded search
+  void* cnn_acts = nullptr;
+  size_t cnn_acts_bytes = 0;
+  void* cnn_dpre = nullptr;
+  size_t cnn_dpre_bytes = 0;
+  float* prop = nullptr;  // [blocks][2] proposals, then [blocks] confidences
+  size_t prop_bytes = 0;
+  int* list = nullptr;    // [1 + blocks]: count, then block indices
+  size_t list_bytes = 0;
 };
 
 namespace {
@@ -107,6 +116,57 @@ bayer_status_t full_search(const uint16_t* ref, const uint16_t* cur, int W, int 
   return cuda_status(bme::launch_generic(a, batch, st));
 }
 
+bool seeded16_fast(int block, int phase, int W, int H, int range) {
+  return block == 16 && phase == BAYER_PHASE_EVEN && (W % 16) == 0 && (H % 16) == 0 &&
+         bme::full16_even_supported(range);
+}
+
+// Seeded refine on the fast kernels: warp-per-block +-4 refine, compacted list
+// of low-confidence blocks, list-mode exhaustive search of that list.
+bayer_status_t seeded_fast(bayer_me_s* h, const uint16_t* ref, const uint16_t* cur, int W, int H, int pitch,
+                           long long rbs, long long cbs, int batch, int range, const float* prop, const float* conf,
+                           float thresh, bayer_mv_t* out, uint8_t* fallback, int* n_fallback, cudaStream_t st) {
+  const int hb = H / 16, wb = W / 16;
+  const long long nblk = (long long)batch * hb * wb;
+  bayer_status_t s = grow(&h->list, &h->list_bytes, (size_t)(nblk + 1) * sizeof(int));
+  if (s != BAYER_OK) return s;
+  cudaError_t e = cudaMemsetAsync(h->list, 0, sizeof(int), st);
+  bme::Seeded16Args a{};
+  a.ref = ref;
+  a.cur = cur;
+  a.W = W;
+  a.H = H;
+  a.pitch = pitch;
+  a.ref_bs = rbs;
+  a.cur_bs = cbs;
+  a.h = hb;
+  a.w = wb;
+  a.batch = batch;
+  a.prop = prop;
+  a.conf = conf;
+  a.thresh = thresh;
+  a.range = range;
+  a.out = out;
+  a.fallback = fallback;
+  a.count = h->list;
+  a.list = h->list + 1;
+  if (e == cudaSuccess) e = bme::launch_seeded16(a, st);
+  if (e == cudaSuccess)
+    e = bme::launch_full16_list(ref, cur, W, H, pitch, rbs, cbs, hb, wb, range, h->list + 1, h->list, (int)nblk, out,
+                                st);
+  if (e == cudaSuccess && n_fallback) e = cudaMemcpyAsync(n_fallback, h->list, sizeof(int), cudaMemcpyDeviceToDevice, st);
+  return cuda_status(e);
+}
+
+bayer_status_t check_cnn_frames(const void* ref, const void* cur, int W, int H, int pitch, int batch, long long rbs,
+                                long long cbs) {
+  bayer_status_t s = check_frames(ref, cur, W, H, pitch, 16);
+  if (s != BAYER_OK) return s;
+  if ((W % 32) != 0 || (H % 32) != 0) return BAYER_ERR_UNSUPPORTED;
+  if (batch < 1 || batch > 65535 || rbs < 0 || cbs < 0) return BAYER_ERR_INVALID_ARG;
+  return BAYER_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -134,6 +194,7 @@ bayer_status_t bayer_me_init(bayer_me_t* out, int device) {
   if (!h) return BAYER_ERR_OOM;
   h->device = device;
   e = bme::configure_full16();
+  if (e == cudaSuccess) e = bme::configure_full16_list();
   if (e == cudaSuccess) e = cudaMalloc(&h->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking);
@@ -157,6 +218,10 @@ bayer_status_t bayer_me_destroy(bayer_me_t h) {
   if (h->d_feat) cudaFree(h->d_feat);
   if (h->d_fout) cudaFree(h->d_fout);
   if (h->d_mv) cudaFree(h->d_mv);
+  if (h->cnn_acts) cudaFree(h->cnn_acts);
+  if (h->cnn_dpre) cudaFree(h->cnn_dpre);
+  if (h->prop) cudaFree(h->prop);
+  if (h->list) cudaFree(h->list);
   if (h->s_in) cudaStreamDestroy(h->s_in);
   if (h->s_comp) cudaStreamDestroy(h->s_comp);
   if (h->s_out) cudaStreamDestroy(h->s_out);
@@ -200,6 +265,9 @@ bayer_status_t bayer_me_estimate_ex(bayer_me_t h, const uint16_t* ref, const uin
     if (p->phase != BAYER_PHASE_EVEN) return BAYER_ERR_UNSUPPORTED;
     if (p->range < 4 || p->range > 510 || (p->range & 1)) return BAYER_ERR_INVALID_ARG;
     if (!prop_dxdy || !conf) return BAYER_ERR_INVALID_ARG;
+    if (seeded16_fast(p->block, p->phase, W, H, p->range))
+      return seeded_fast(h, ref, cur, W, H, pitch, p->ref_batch_stride, p->cur_batch_stride, p->batch, p->range,
+                         prop_dxdy, conf, p->conf_thresh, mv_out, fallback_out, nullptr, st);
     GenericArgs a{};
     a.ref = ref;
     a.cur = cur;
@@ -393,6 +461,73 @@ bayer_status_t bayer_clip_process_host(bayer_me_t h, const uint16_t* frames, int
   delete[] ev_in;
   delete[] ev_done;
   return cuda_status(e);
+}
+
+bayer_status_t bayer_cnn_forward(bayer_me_t h, const uint16_t* ref, const uint16_t* cur, int W, int H, int pitch,
+                                 int batch, long long ref_bs, long long cur_bs, const uint16_t* w_bf16, int range,
+                                 float* prop_dxdy, float* conf, void* stream) {
+  if (!h || !w_bf16 || !prop_dxdy || !conf || range < 1 || range > 510) return BAYER_ERR_INVALID_ARG;
+  bayer_status_t s = check_cnn_frames(ref, cur, W, H, pitch, batch, ref_bs, cur_bs);
+  if (s != BAYER_OK) return s;
+  DeviceGuard g(h->device);
+  if ((s = grow(reinterpret_cast<char**>(&h->cnn_acts), &h->cnn_acts_bytes, bme::cnn_act_bytes(W, H, batch))) !=
+      BAYER_OK)
+    return s;
+  bme::CnnFrames fr{ref, cur, W, H, pitch, ref_bs, cur_bs};
+  return cuda_status(bme::cnn_forward(fr, batch, w_bf16, range, h->cnn_acts, prop_dxdy, conf,
+                                      static_cast<cudaStream_t>(stream)));
+}
+
+bayer_status_t bayer_cnn_loss_grad(bayer_me_t h, const uint16_t* ref, const uint16_t* cur, int W, int H, int pitch,
+                                   int batch, long long ref_bs, long long cur_bs, const uint16_t* w_bf16,
+                                   const bayer_mv_t* labels, int range, float* grad, float* loss, void* stream) {
+  if (!h || !w_bf16 || !labels || !grad || !loss || range < 1 || range > 510) return BAYER_ERR_INVALID_ARG;
+  bayer_status_t s = check_cnn_frames(ref, cur, W, H, pitch, batch, ref_bs, cur_bs);
+  if (s != BAYER_OK) return s;
+  DeviceGuard g(h->device);
+  if ((s = grow(reinterpret_cast<char**>(&h->cnn_acts), &h->cnn_acts_bytes, bme::cnn_act_bytes(W, H, batch))) !=
+      BAYER_OK)
+    return s;
+  if ((s = grow(reinterpret_cast<char**>(&h->cnn_dpre), &h->cnn_dpre_bytes, bme::cnn_grad_bytes(W, H, batch))) !=
+      BAYER_OK)
+    return s;
+  bme::CnnFrames fr{ref, cur, W, H, pitch, ref_bs, cur_bs};
+  return cuda_status(bme::cnn_loss_grad(fr, batch, w_bf16, labels, range, h->cnn_acts, h->cnn_dpre, grad, loss,
+                                        static_cast<cudaStream_t>(stream)));
+}
+
+bayer_status_t bayer_cnn_adamw(bayer_me_t h, float* w, uint16_t* w_bf16, const float* grad, float* m, float* v,
+                               int step, float lr, float beta1, float beta2, float eps, float weight_decay,
+                               void* stream) {
+  if (!h || !w || !w_bf16 || !grad || !m || !v || step < 1) return BAYER_ERR_INVALID_ARG;
+  if (!(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f)) return BAYER_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  return cuda_status(bme::cnn_adamw(w, w_bf16, grad, m, v, BAYER_CNN_NPARAMS, step, lr, beta1, beta2, eps,
+                                    weight_decay, static_cast<cudaStream_t>(stream)));
+}
+
+bayer_status_t bayer_me_estimate_learned(bayer_me_t h, const uint16_t* ref, const uint16_t* cur, int W, int H,
+                                         int pitch, int batch, long long ref_bs, long long cur_bs,
+                                         const uint16_t* w_bf16, int range, float conf_thresh, bayer_mv_t* mv_out,
+                                         uint8_t* fallback_out, int* n_fallback, void* stream) {
+  if (!h || !w_bf16 || !mv_out) return BAYER_ERR_INVALID_ARG;
+  bayer_status_t s = check_cnn_frames(ref, cur, W, H, pitch, batch, ref_bs, cur_bs);
+  if (s != BAYER_OK) return s;
+  if (!bme::full16_even_supported(range)) return BAYER_ERR_UNSUPPORTED;
+  DeviceGuard g(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t nblk = (size_t)batch * (H / 16) * (W / 16);
+  if ((s = grow(reinterpret_cast<char**>(&h->cnn_acts), &h->cnn_acts_bytes, bme::cnn_act_bytes(W, H, batch))) !=
+      BAYER_OK)
+    return s;
+  if ((s = grow(reinterpret_cast<char**>(&h->prop), &h->prop_bytes, nblk * 3 * sizeof(float))) != BAYER_OK) return s;
+  float* prop = h->prop;
+  float* conf = h->prop + 2 * nblk;
+  bme::CnnFrames fr{ref, cur, W, H, pitch, ref_bs, cur_bs};
+  cudaError_t e = bme::cnn_forward(fr, batch, w_bf16, range, h->cnn_acts, prop, conf, st);
+  if (e != cudaSuccess) return cuda_status(e);
+  return seeded_fast(h, ref, cur, W, H, pitch, ref_bs, cur_bs, batch, range, prop, conf, conf_thresh, mv_out,
+                     fallback_out, n_fallback, st);
 }
 
 bayer_status_t bayer_me_sync_status(bayer_me_t h, void* stream) {

@@ -1,0 +1,561 @@
+// Learned MV proposal network: forward, loss gradient and AdamW (BF16
+// weights and activations, FP32 accumulation).  Not in the paper: it seeds the
+// +-4 refine of the learned-seeded search.  Training follows the paper's
+// recipe for its learned module (AdamW, cosine schedule; Sec. 4.1 "Training
+// Details") and its BerHu loss (Sec. 3.3).
+//
+// Network (flat parameter order = BAYER_CNN_* offsets in bayer_me.h):
+//   x0 = the four RGGB planes of ref and cur at half resolution, v/2048 - 1
+//   x_l = ReLU(conv3x3(x_{l-1}, stride 2, pad 1) + b_l), 32 channels, l = 1..4
+//   z = 1x1 conv (32 -> 12) + b_h; channel 3*(2*sy + sx) + q of L4 cell (i, k)
+//       is quantity q of block (2i + sy, 2k + sx)
+//   dx = range*tanh(z_0), dy = range*tanh(z_1), conf = sigmoid(z_2)
+// Activations are NHWC bf16 [B][H][W][32]; layer 1 reads the Bayer frames
+// directly (the packing is fused into its gather).  Loss per block:
+//   BerHu_4(dx - dx*) + BerHu_4(dy - dy*) + BCE(conf, t),
+//   t = [round_even(dx) within +-4 of dx* and likewise for dy],
+// averaged over all blocks of the batch.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace bme {
+
+namespace {
+
+constexpr int kC = 32;
+
+__device__ __forceinline__ float bf(const __nv_bfloat16 v) { return __bfloat162float(v); }
+
+// 8 bf16 packed in a uint4 -> 8 floats
+__device__ __forceinline__ void unpack8(const uint4 u, float* f) {
+  const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    f[2 * i] = __uint_as_float(w[i] << 16);
+    f[2 * i + 1] = __uint_as_float(w[i] & 0xFFFF0000u);
+  }
+}
+
+__device__ __forceinline__ uint32_t pack2(float a, float b) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// Layer-1 input sample: channel ci (0..7) at half-resolution (hy, hx), zero
+// outside the half-resolution map.
+__device__ __forceinline__ float l1_input(const uint16_t* ref, const uint16_t* cur, int pitch, int Hh, int Wh, int ci,
+                                          int hy, int hx) {
+  if (hy < 0 || hy >= Hh || hx < 0 || hx >= Wh) return 0.f;
+  const uint16_t* f = ci < 4 ? ref : cur;
+  const int p = ci & 3;
+  const int y = 2 * hy + (p >> 1), x = 2 * hx + (p & 1);
+  return (float)__ldg(f + (long long)y * pitch + x) * (1.0f / 2048.0f) - 1.0f;
+}
+
+// ---------------------------------------------------------------------------
+// forward
+// ---------------------------------------------------------------------------
+
+// Layer 1 from the frames: one thread = 2 horizontally adjacent output pixels x 32 channels.
+__global__ void __launch_bounds__(128) l1_fwd_kernel(CnnFrames fr, const __nv_bfloat16* __restrict__ w,
+                                                     __nv_bfloat16* __restrict__ out, int Ho, int Wo) {
+  __shared__ __align__(16) float ws[72 * kC];  // [ci*9 + tap][co]
+  __shared__ float bs[kC];
+  for (int i = threadIdx.x; i < 72 * kC; i += blockDim.x) {
+    const int k = i / kC, co = i - k * kC;
+    ws[i] = bf(w[co * 72 + k]);
+  }
+  if (threadIdx.x < kC) bs[threadIdx.x] = bf(w[BAYER_CNN_B1 - BAYER_CNN_W1 + threadIdx.x]);
+  __syncthreads();
+  const int b = blockIdx.z, oy = blockIdx.y;
+  const int ox0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  if (ox0 >= Wo) return;
+  const uint16_t* ref = fr.ref + (long long)b * fr.ref_bs;
+  const uint16_t* cur = fr.cur + (long long)b * fr.cur_bs;
+  const int Hh = fr.H / 2, Wh = fr.W / 2;
+  float acc[2][kC];
+#pragma unroll
+  for (int co = 0; co < kC; ++co) acc[0][co] = acc[1][co] = bs[co];
+  for (int ci = 0; ci < 8; ++ci) {
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      const int ky = tap / 3, kx = tap - 3 * (tap / 3);
+      const int hy = 2 * oy + ky - 1;
+      const float x0 = l1_input(ref, cur, fr.pitch, Hh, Wh, ci, hy, 2 * ox0 + kx - 1);
+      const float x1 = ox0 + 1 < Wo ? l1_input(ref, cur, fr.pitch, Hh, Wh, ci, hy, 2 * ox0 + 2 + kx - 1) : 0.f;
+      const float4* wr = reinterpret_cast<const float4*>(ws + (ci * 9 + tap) * kC);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float4 wv = wr[q];
+        acc[0][4 * q + 0] = fmaf(x0, wv.x, acc[0][4 * q + 0]);
+        acc[0][4 * q + 1] = fmaf(x0, wv.y, acc[0][4 * q + 1]);
+        acc[0][4 * q + 2] = fmaf(x0, wv.z, acc[0][4 * q + 2]);
+        acc[0][4 * q + 3] = fmaf(x0, wv.w, acc[0][4 * q + 3]);
+        acc[1][4 * q + 0] = fmaf(x1, wv.x, acc[1][4 * q + 0]);
+        acc[1][4 * q + 1] = fmaf(x1, wv.y, acc[1][4 * q + 1]);
+        acc[1][4 * q + 2] = fmaf(x1, wv.z, acc[1][4 * q + 2]);
+        acc[1][4 * q + 3] = fmaf(x1, wv.w, acc[1][4 * q + 3]);
+      }
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    if (ox0 + p >= Wo) break;
+    uint4* dst = reinterpret_cast<uint4*>(out + (((long long)b * Ho + oy) * Wo + ox0 + p) * kC);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float* a = acc[p] + 8 * q;
+      dst[q] = make_uint4(pack2(fmaxf(a[0], 0.f), fmaxf(a[1], 0.f)), pack2(fmaxf(a[2], 0.f), fmaxf(a[3], 0.f)),
+                          pack2(fmaxf(a[4], 0.f), fmaxf(a[5], 0.f)), pack2(fmaxf(a[6], 0.f), fmaxf(a[7], 0.f)));
+    }
+  }
+}
+
+// Layers 2..4: NHWC bf16 in (32 channels), 2 output pixels x 32 channels per thread.
+__global__ void __launch_bounds__(128) conv_fwd_kernel(const __nv_bfloat16* __restrict__ in, int Hi, int Wi,
+                                                       const __nv_bfloat16* __restrict__ w,
+                                                       const __nv_bfloat16* __restrict__ bias,
+                                                       __nv_bfloat16* __restrict__ out, int Ho, int Wo) {
+  __shared__ __align__(16) float ws[288 * kC];  // [tap*32 + ci][co]
+  __shared__ float bs[kC];
+  for (int i = threadIdx.x; i < 288 * kC; i += blockDim.x) {
+    const int k = i / kC, co = i - k * kC;
+    const int tap = k / kC, ci = k - tap * kC;
+    ws[i] = bf(w[co * 288 + ci * 9 + tap]);
+  }
+  if (threadIdx.x < kC) bs[threadIdx.x] = bf(bias[threadIdx.x]);
+  __syncthreads();
+  const int b = blockIdx.z, oy = blockIdx.y;
+  const int ox0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  if (ox0 >= Wo) return;
+  const __nv_bfloat16* inb = in + (long long)b * Hi * Wi * kC;
+  float acc[2][kC];
+#pragma unroll
+  for (int co = 0; co < kC; ++co) acc[0][co] = acc[1][co] = bs[co];
+#pragma unroll 1
+  for (int tap = 0; tap < 9; ++tap) {
+    const int ky = tap / 3, kx = tap - 3 * (tap / 3);
+    const int iy = 2 * oy + ky - 1;
+    const int ix0 = 2 * ox0 + kx - 1, ix1 = ix0 + 2;
+    const bool r_ok = iy >= 0 && iy < Hi;
+    const bool ok0 = r_ok && ix0 >= 0 && ix0 < Wi;
+    const bool ok1 = r_ok && ox0 + 1 < Wo && ix1 >= 0 && ix1 < Wi;
+    const uint4* p0 = reinterpret_cast<const uint4*>(inb + ((long long)iy * Wi + ix0) * kC);
+    const uint4* p1 = reinterpret_cast<const uint4*>(inb + ((long long)iy * Wi + ix1) * kC);
+#pragma unroll
+    for (int c8 = 0; c8 < 4; ++c8) {
+      float x0[8], x1[8];
+      const uint4 z4 = make_uint4(0, 0, 0, 0);
+      unpack8(ok0 ? __ldg(p0 + c8) : z4, x0);
+      unpack8(ok1 ? __ldg(p1 + c8) : z4, x1);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const float4* wr = reinterpret_cast<const float4*>(ws + (tap * kC + c8 * 8 + c) * kC);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const float4 wv = wr[q];
+          acc[0][4 * q + 0] = fmaf(x0[c], wv.x, acc[0][4 * q + 0]);
+          acc[0][4 * q + 1] = fmaf(x0[c], wv.y, acc[0][4 * q + 1]);
+          acc[0][4 * q + 2] = fmaf(x0[c], wv.z, acc[0][4 * q + 2]);
+          acc[0][4 * q + 3] = fmaf(x0[c], wv.w, acc[0][4 * q + 3]);
+          acc[1][4 * q + 0] = fmaf(x1[c], wv.x, acc[1][4 * q + 0]);
+          acc[1][4 * q + 1] = fmaf(x1[c], wv.y, acc[1][4 * q + 1]);
+          acc[1][4 * q + 2] = fmaf(x1[c], wv.z, acc[1][4 * q + 2]);
+          acc[1][4 * q + 3] = fmaf(x1[c], wv.w, acc[1][4 * q + 3]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    if (ox0 + p >= Wo) break;
+    uint4* dst = reinterpret_cast<uint4*>(out + (((long long)b * Ho + oy) * Wo + ox0 + p) * kC);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float* a = acc[p] + 8 * q;
+      dst[q] = make_uint4(pack2(fmaxf(a[0], 0.f), fmaxf(a[1], 0.f)), pack2(fmaxf(a[2], 0.f), fmaxf(a[3], 0.f)),
+                          pack2(fmaxf(a[4], 0.f), fmaxf(a[5], 0.f)), pack2(fmaxf(a[6], 0.f), fmaxf(a[7], 0.f)));
+    }
+  }
+}
+
+// Head: one thread per L4 cell -> 4 blocks' (dx, dy, conf).
+__global__ void __launch_bounds__(128) head_fwd_kernel(const __nv_bfloat16* __restrict__ x4, int H4, int W4,
+                                                       const __nv_bfloat16* __restrict__ w, int range,
+                                                       float* __restrict__ prop, float* __restrict__ conf) {
+  __shared__ float wh[12 * kC + 12];
+  for (int i = threadIdx.x; i < 12 * kC + 12; i += blockDim.x) wh[i] = bf(w[BAYER_CNN_WH + i]);
+  __syncthreads();
+  const int cells = H4 * W4;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = blockIdx.y;
+  if (t >= cells) return;
+  const int i = t / W4, k = t - i * W4;
+  float x[kC];
+  const uint4* src = reinterpret_cast<const uint4*>(x4 + ((long long)b * cells + t) * kC);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) unpack8(__ldg(src + q), x + 8 * q);
+  const int h = 2 * H4, wb = 2 * W4;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    float z[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const int j = 3 * s + q;
+      float a = wh[12 * kC + j];
+#pragma unroll
+      for (int c = 0; c < kC; ++c) a = fmaf(wh[j * kC + c], x[c], a);
+      z[q] = a;
+    }
+    const long long blk = ((long long)b * h + 2 * i + (s >> 1)) * wb + 2 * k + (s & 1);
+    prop[2 * blk] = (float)range * tanhf(z[0]);
+    prop[2 * blk + 1] = (float)range * tanhf(z[1]);
+    conf[blk] = 1.0f / (1.0f + expf(-z[2]));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// training: loss and gradients
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float round_even(float v) { return 2.0f * roundf(v * 0.5f); }
+__device__ __forceinline__ float berhu(float e) {
+  const float a = fabsf(e);
+  return a <= 4.0f ? a : (e * e + 16.0f) * 0.125f;
+}
+__device__ __forceinline__ float berhu_grad(float e) {
+  return fabsf(e) <= 4.0f ? (e > 0.f ? 1.f : (e < 0.f ? -1.f : 0.f)) : e * 0.25f;
+}
+
+// Head forward + loss + head backward.  One thread per L4 cell.  Writes
+// dpre4 = dL/d(L4 pre-activation) (fp32 NHWC), accumulates dL/d(head w, b)
+// into grad and the loss sum into *loss (both already scaled by 1/n).
+__global__ void __launch_bounds__(128) head_loss_bwd_kernel(const __nv_bfloat16* __restrict__ x4, int H4, int W4,
+                                                            const __nv_bfloat16* __restrict__ w, int range,
+                                                            const bayer_mv_t* __restrict__ labels, float inv_n,
+                                                            float* __restrict__ dpre4, float* __restrict__ grad,
+                                                            float* __restrict__ loss) {
+  __shared__ float wh[12 * kC + 12];
+  __shared__ float gsum[12 * kC + 12];
+  __shared__ float lsum;
+  for (int i = threadIdx.x; i < 12 * kC + 12; i += blockDim.x) {
+    wh[i] = bf(w[BAYER_CNN_WH + i]);
+    gsum[i] = 0.f;
+  }
+  if (threadIdx.x == 0) lsum = 0.f;
+  __syncthreads();
+  const int cells = H4 * W4;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = blockIdx.y;
+  if (t < cells) {
+    const int i = t / W4, k = t - i * W4;
+    float x[kC];
+    const uint4* src = reinterpret_cast<const uint4*>(x4 + ((long long)b * cells + t) * kC);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) unpack8(__ldg(src + q), x + 8 * q);
+    const int h = 2 * H4, wb = 2 * W4;
+    float dz[12];
+    float l = 0.f;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      float z[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const int j = 3 * s + q;
+        float a = wh[12 * kC + j];
+#pragma unroll
+        for (int c = 0; c < kC; ++c) a = fmaf(wh[j * kC + c], x[c], a);
+        z[q] = a;
+      }
+      const long long blk = ((long long)b * h + 2 * i + (s >> 1)) * wb + 2 * k + (s & 1);
+      const bayer_mv_t lab = labels[blk];
+      const float tx = tanhf(z[0]), ty = tanhf(z[1]);
+      const float dx = (float)range * tx, dy = (float)range * ty;
+      const float cf = 1.0f / (1.0f + expf(-z[2]));
+      const float ex = dx - (float)lab.dx, ey = dy - (float)lab.dy;
+      const float tgt = (fabsf(round_even(dx) - (float)lab.dx) <= 4.f && fabsf(round_even(dy) - (float)lab.dy) <= 4.f)
+                            ? 1.f : 0.f;
+      l += berhu(ex) + berhu(ey) - (tgt * logf(cf + 1e-12f) + (1.f - tgt) * logf(1.f - cf + 1e-12f));
+      dz[3 * s + 0] = berhu_grad(ex) * (float)range * (1.f - tx * tx) * inv_n;
+      dz[3 * s + 1] = berhu_grad(ey) * (float)range * (1.f - ty * ty) * inv_n;
+      dz[3 * s + 2] = (cf - tgt) * inv_n;
+    }
+    // d x4, masked by ReLU (x4 > 0 iff its pre-activation > 0)
+    float* dst = dpre4 + ((long long)b * cells + t) * kC;
+#pragma unroll
+    for (int c = 0; c < kC; ++c) {
+      float a = 0.f;
+#pragma unroll
+      for (int j = 0; j < 12; ++j) a = fmaf(wh[j * kC + c], dz[j], a);
+      dst[c] = x[c] > 0.f ? a : 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < 12; ++j) {
+#pragma unroll
+      for (int c = 0; c < kC; ++c) atomicAdd(&gsum[j * kC + c], dz[j] * x[c]);
+      atomicAdd(&gsum[12 * kC + j], dz[j]);
+    }
+    atomicAdd(&lsum, l * inv_n);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 12 * kC + 12; i += blockDim.x) atomicAdd(&grad[BAYER_CNN_WH + i], gsum[i]);
+  if (threadIdx.x == 0) atomicAdd(loss, lsum);
+}
+
+// dX of a stride-2 3x3 conv (32 -> 32), masked by ReLU of the layer below:
+// dpre_in[b, iy, ix, ci] = [x_in > 0] * sum_{taps, co} dpre_out[b, oy, ox, co] * w[co, ci, tap]
+// with iy = 2 oy + ky - 1.  One thread per input pixel.
+__global__ void __launch_bounds__(128) conv_bwd_data_kernel(const float* __restrict__ dout, int Ho, int Wo,
+                                                            const __nv_bfloat16* __restrict__ w,
+                                                            const __nv_bfloat16* __restrict__ xin, int Hi, int Wi,
+                                                            float* __restrict__ din) {
+  __shared__ __align__(16) float wt[9 * kC * kC];  // [tap][co][ci]
+  for (int i = threadIdx.x; i < 9 * kC * kC; i += blockDim.x) {
+    const int tap = i / (kC * kC), r = i - tap * kC * kC, co = r / kC, ci = r - co * kC;
+    wt[i] = bf(w[co * 288 + ci * 9 + tap]);
+  }
+  __syncthreads();
+  const int b = blockIdx.z, iy = blockIdx.y;
+  const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ix >= Wi) return;
+  float acc[kC];
+#pragma unroll
+  for (int c = 0; c < kC; ++c) acc[c] = 0.f;
+  for (int ky = 0; ky < 3; ++ky) {
+    const int ny = iy + 1 - ky;
+    if (ny < 0 || (ny & 1)) continue;
+    const int oy = ny >> 1;
+    if (oy >= Ho) continue;
+    for (int kx = 0; kx < 3; ++kx) {
+      const int nx = ix + 1 - kx;
+      if (nx < 0 || (nx & 1)) continue;
+      const int ox = nx >> 1;
+      if (ox >= Wo) continue;
+      const float4* dr = reinterpret_cast<const float4*>(dout + (((long long)b * Ho + oy) * Wo + ox) * kC);
+      const int tap = ky * 3 + kx;
+#pragma unroll 2
+      for (int q = 0; q < 8; ++q) {
+        const float4 d4 = __ldg(dr + q);
+        const float dv[4] = {d4.x, d4.y, d4.z, d4.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float4* wr = reinterpret_cast<const float4*>(wt + (tap * kC + 4 * q + e) * kC);
+#pragma unroll
+          for (int m = 0; m < 8; ++m) {
+            const float4 wv = wr[m];
+            acc[4 * m + 0] = fmaf(dv[e], wv.x, acc[4 * m + 0]);
+            acc[4 * m + 1] = fmaf(dv[e], wv.y, acc[4 * m + 1]);
+            acc[4 * m + 2] = fmaf(dv[e], wv.z, acc[4 * m + 2]);
+            acc[4 * m + 3] = fmaf(dv[e], wv.w, acc[4 * m + 3]);
+          }
+        }
+      }
+    }
+  }
+  float xv[kC];
+  const uint4* xs = reinterpret_cast<const uint4*>(xin + (((long long)b * Hi + iy) * Wi + ix) * kC);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) unpack8(__ldg(xs + q), xv + 8 * q);
+  float4* dst = reinterpret_cast<float4*>(din + (((long long)b * Hi + iy) * Wi + ix) * kC);
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    dst[q] = make_float4(xv[4 * q] > 0.f ? acc[4 * q] : 0.f, xv[4 * q + 1] > 0.f ? acc[4 * q + 1] : 0.f,
+                         xv[4 * q + 2] > 0.f ? acc[4 * q + 2] : 0.f, xv[4 * q + 3] > 0.f ? acc[4 * q + 3] : 0.f);
+}
+
+// dW, db of a stride-2 3x3 conv: dW[co, k] = sum_pixels dout[p, co] * patch[p, k],
+// k = ci*9 + tap (the flat weight order), db[co] = sum_p dout[p, co].  Each CTA
+// walks output pixels in chunks of 32 (grid-stride), stages the chunk's dout rows
+// and input patches in shared memory, keeps its partial sums in registers (thread
+// = one co and KPT consecutive k) and adds them to grad once at the end.
+template <int CIN, bool FRAMES>
+__global__ void __launch_bounds__(256) conv_bwd_w_kernel(const float* __restrict__ dout, int Ho, int Wo, int B,
+                                                         const __nv_bfloat16* __restrict__ xin, int Hi, int Wi,
+                                                         CnnFrames fr, float* __restrict__ gw, float* __restrict__ gb) {
+  constexpr int K = CIN * 9;
+  constexpr int KPT = K / 8;  // k per thread (8 threads per co)
+  constexpr int PCH = 32;     // pixels per chunk
+  __shared__ __align__(16) float ds[PCH][kC];
+  __shared__ __align__(16) float xs[PCH][K];
+  const int co = threadIdx.x >> 3, kg = threadIdx.x & 7;
+  float acc[KPT];
+#pragma unroll
+  for (int j = 0; j < KPT; ++j) acc[j] = 0.f;
+  float accb = 0.f;
+  const long long npix = (long long)B * Ho * Wo;
+  const int Hh = fr.H / 2, Wh = fr.W / 2;
+  for (long long base = (long long)blockIdx.x * PCH; base < npix; base += (long long)gridDim.x * PCH) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < PCH * kC; i += blockDim.x) {
+      const int p = i / kC, c = i - p * kC;
+      const long long gp = base + p;
+      ds[p][c] = gp < npix ? dout[gp * kC + c] : 0.f;
+    }
+    for (int i = threadIdx.x; i < PCH * K; i += blockDim.x) {
+      const int p = i / K, k = i - p * K;
+      const long long gp = base + p;
+      float v = 0.f;
+      if (gp < npix) {
+        const int b = (int)(gp / ((long long)Ho * Wo));
+        const int r = (int)(gp - (long long)b * Ho * Wo);
+        const int oy = r / Wo, ox = r - oy * Wo;
+        const int ci = k / 9, tap = k - 9 * ci;
+        const int iy = 2 * oy + tap / 3 - 1, ix = 2 * ox + tap % 3 - 1;
+        if (FRAMES) {
+          v = l1_input(fr.ref + (long long)b * fr.ref_bs, fr.cur + (long long)b * fr.cur_bs, fr.pitch, Hh, Wh, ci, iy,
+                       ix);
+        } else if (iy >= 0 && iy < Hi && ix >= 0 && ix < Wi) {
+          v = bf(xin[(((long long)b * Hi + iy) * Wi + ix) * kC + ci]);
+        }
+      }
+      xs[p][k] = v;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int p = 0; p < PCH; ++p) {
+      const float d = ds[p][co];
+      accb += d;
+#pragma unroll
+      for (int j = 0; j < KPT; ++j) acc[j] = fmaf(d, xs[p][kg * KPT + j], acc[j]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < KPT; ++j) atomicAdd(&gw[co * K + kg * KPT + j], acc[j]);
+  if (kg == 0) atomicAdd(&gb[co], accb);
+}
+
+__global__ void adamw_kernel(float* __restrict__ w, __nv_bfloat16* __restrict__ wb, const float* __restrict__ g,
+                             float* __restrict__ m, float* __restrict__ v, int n, float lr, float b1, float b2,
+                             float eps, float wd, float bc1, float bc2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  const float mh = mi / bc1, vh = vi / bc2;
+  const float wi = w[i] - lr * (mh / (sqrtf(vh) + eps) + wd * w[i]);
+  w[i] = wi;
+  wb[i] = __float2bfloat16_rn(wi);
+}
+
+__global__ void f32_to_bf16_kernel(const float* __restrict__ a, __nv_bfloat16* __restrict__ b, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = __float2bfloat16_rn(a[i]);
+}
+
+inline int conv_out(int n) { return (n - 1) / 2 + 1; }
+
+}  // namespace
+
+CnnShapes cnn_shapes(int W, int H) {
+  CnnShapes s;
+  s.H[0] = H / 2;
+  s.W[0] = W / 2;
+  for (int l = 1; l <= 4; ++l) {
+    s.H[l] = conv_out(s.H[l - 1]);
+    s.W[l] = conv_out(s.W[l - 1]);
+  }
+  return s;
+}
+
+size_t cnn_act_bytes(int W, int H, int batch) {
+  const CnnShapes s = cnn_shapes(W, H);
+  size_t n = 0;
+  for (int l = 1; l <= 4; ++l) n += (size_t)s.H[l] * s.W[l] * kC;
+  return n * batch * sizeof(__nv_bfloat16);
+}
+
+size_t cnn_grad_bytes(int W, int H, int batch) {
+  const CnnShapes s = cnn_shapes(W, H);
+  size_t n = 0;
+  for (int l = 1; l <= 4; ++l) n += (size_t)s.H[l] * s.W[l] * kC;
+  return n * batch * sizeof(float);
+}
+
+cudaError_t cnn_forward_acts(const CnnFrames& fr, int batch, const uint16_t* wbf16, void* acts, cudaStream_t st) {
+  const CnnShapes s = cnn_shapes(fr.W, fr.H);
+  const __nv_bfloat16* w = reinterpret_cast<const __nv_bfloat16*>(wbf16);
+  __nv_bfloat16* a[5];
+  a[1] = static_cast<__nv_bfloat16*>(acts);
+  for (int l = 2; l <= 4; ++l) a[l] = a[l - 1] + (size_t)batch * s.H[l - 1] * s.W[l - 1] * kC;
+  {
+    dim3 g((s.W[1] / 2 + 127) / 128 + 1, s.H[1], batch);
+    l1_fwd_kernel<<<g, 128, 0, st>>>(fr, w + BAYER_CNN_W1, a[1], s.H[1], s.W[1]);
+  }
+  const int woff[5] = {0, BAYER_CNN_W1, BAYER_CNN_W2, BAYER_CNN_W3, BAYER_CNN_W4};
+  const int boff[5] = {0, BAYER_CNN_B1, BAYER_CNN_B2, BAYER_CNN_B3, BAYER_CNN_B4};
+  for (int l = 2; l <= 4; ++l) {
+    dim3 g((s.W[l] / 2 + 127) / 128 + 1, s.H[l], batch);
+    conv_fwd_kernel<<<g, 128, 0, st>>>(a[l - 1], s.H[l - 1], s.W[l - 1], w + woff[l], w + boff[l], a[l], s.H[l],
+                                       s.W[l]);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t cnn_forward(const CnnFrames& fr, int batch, const uint16_t* wbf16, int range, void* acts, float* prop,
+                        float* conf, cudaStream_t st) {
+  cudaError_t e = cnn_forward_acts(fr, batch, wbf16, acts, st);
+  if (e != cudaSuccess) return e;
+  const CnnShapes s = cnn_shapes(fr.W, fr.H);
+  const __nv_bfloat16* a4 = static_cast<const __nv_bfloat16*>(acts);
+  for (int l = 1; l <= 3; ++l) a4 += (size_t)batch * s.H[l] * s.W[l] * kC;
+  dim3 g((s.H[4] * s.W[4] + 127) / 128, batch);
+  head_fwd_kernel<<<g, 128, 0, st>>>(a4, s.H[4], s.W[4], reinterpret_cast<const __nv_bfloat16*>(wbf16), range, prop,
+                                     conf);
+  return cudaGetLastError();
+}
+
+cudaError_t cnn_loss_grad(const CnnFrames& fr, int batch, const uint16_t* wbf16, const bayer_mv_t* labels, int range,
+                          void* acts, void* dpre, float* grad, float* loss, cudaStream_t st) {
+  const CnnShapes s = cnn_shapes(fr.W, fr.H);
+  cudaError_t e = cnn_forward_acts(fr, batch, wbf16, acts, st);
+  if (e != cudaSuccess) return e;
+  const __nv_bfloat16* w = reinterpret_cast<const __nv_bfloat16*>(wbf16);
+  const __nv_bfloat16* a[5];
+  a[1] = static_cast<const __nv_bfloat16*>(acts);
+  for (int l = 2; l <= 4; ++l) a[l] = a[l - 1] + (size_t)batch * s.H[l - 1] * s.W[l - 1] * kC;
+  float* d[5];
+  d[1] = static_cast<float*>(dpre);
+  for (int l = 2; l <= 4; ++l) d[l] = d[l - 1] + (size_t)batch * s.H[l - 1] * s.W[l - 1] * kC;
+  if ((e = cudaMemsetAsync(grad, 0, BAYER_CNN_NPARAMS * sizeof(float), st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(loss, 0, sizeof(float), st)) != cudaSuccess) return e;
+  const float inv_n = 1.0f / ((float)batch * (2 * s.H[4]) * (2 * s.W[4]));
+  {
+    dim3 g((s.H[4] * s.W[4] + 127) / 128, batch);
+    head_loss_bwd_kernel<<<g, 128, 0, st>>>(a[4], s.H[4], s.W[4], w, range, labels, inv_n, d[4], grad, loss);
+  }
+  const int woff[5] = {0, BAYER_CNN_W1, BAYER_CNN_W2, BAYER_CNN_W3, BAYER_CNN_W4};
+  const int boff[5] = {0, BAYER_CNN_B1, BAYER_CNN_B2, BAYER_CNN_B3, BAYER_CNN_B4};
+  int nsm = 148;
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  for (int l = 4; l >= 2; --l) {
+    conv_bwd_w_kernel<32, false><<<nsm * 2, 256, 0, st>>>(d[l], s.H[l], s.W[l], batch, a[l - 1], s.H[l - 1],
+                                                           s.W[l - 1], fr, grad + woff[l], grad + boff[l]);
+    dim3 g((s.W[l - 1] + 127) / 128, s.H[l - 1], batch);
+    conv_bwd_data_kernel<<<g, 128, 0, st>>>(d[l], s.H[l], s.W[l], w + woff[l], a[l - 1], s.H[l - 1], s.W[l - 1],
+                                            d[l - 1]);
+  }
+  conv_bwd_w_kernel<8, true><<<nsm * 2, 256, 0, st>>>(d[1], s.H[1], s.W[1], batch, nullptr, 0, 0, fr,
+                                                      grad + BAYER_CNN_W1, grad + BAYER_CNN_B1);
+  return cudaGetLastError();
+}
+
+cudaError_t cnn_adamw(float* w, uint16_t* wbf16, const float* g, float* m, float* v, int n, int step, float lr,
+                      float b1, float b2, float eps, float wd, cudaStream_t st) {
+  const float bc1 = 1.f - powf(b1, (float)step), bc2 = 1.f - powf(b2, (float)step);
+  adamw_kernel<<<(n + 255) / 256, 256, 0, st>>>(w, reinterpret_cast<__nv_bfloat16*>(wbf16), g, m, v, n, lr, b1, b2,
+                                                eps, wd, bc1, bc2);
+  return cudaGetLastError();
+}
+
+cudaError_t cnn_to_bf16(const float* w, uint16_t* wbf16, int n, cudaStream_t st) {
+  f32_to_bf16_kernel<<<(n + 255) / 256, 256, 0, st>>>(w, reinterpret_cast<__nv_bfloat16*>(wbf16), n);
+  return cudaGetLastError();
+}
+
+}  // namespace bme

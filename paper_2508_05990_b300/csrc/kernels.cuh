@@ -52,6 +52,49 @@ struct PropArgs {
 };
 cudaError_t launch_propagate(const PropArgs& a, int layout, int interp, cudaStream_t st);
 
+// Learned proposal network (cnn.cu).
+struct CnnFrames {
+  const uint16_t* ref;
+  const uint16_t* cur;
+  int W, H, pitch;
+  long long ref_bs, cur_bs;
+};
+struct CnnShapes {
+  int H[5], W[5];  // [0] half-resolution input, [1..4] layer outputs
+};
+CnnShapes cnn_shapes(int W, int H);
+size_t cnn_act_bytes(int W, int H, int batch);   // bf16 activations of layers 1..4
+size_t cnn_grad_bytes(int W, int H, int batch);  // fp32 pre-activation gradients of layers 1..4
+cudaError_t cnn_forward(const CnnFrames& fr, int batch, const uint16_t* wbf16, int range, void* acts, float* prop,
+                        float* conf, cudaStream_t st);
+cudaError_t cnn_loss_grad(const CnnFrames& fr, int batch, const uint16_t* wbf16, const bayer_mv_t* labels, int range,
+                          void* acts, void* dpre, float* grad, float* loss, cudaStream_t st);
+cudaError_t cnn_adamw(float* w, uint16_t* wbf16, const float* g, float* m, float* v, int n, int step, float lr,
+                      float b1, float b2, float eps, float wd, cudaStream_t st);
+
+// Seeded +-4 refine of 16x16 blocks (warp per block) with a compacted list of
+// the low-confidence blocks, and the exhaustive search of a block list.
+struct Seeded16Args {
+  const uint16_t* ref;
+  const uint16_t* cur;
+  int W, H, pitch;
+  long long ref_bs, cur_bs;
+  int h, w, batch;
+  const float* prop;  // [batch][h][w][2]
+  const float* conf;  // [batch][h][w]
+  float thresh;
+  int range;
+  bayer_mv_t* out;
+  uint8_t* fallback;  // optional
+  int* list;          // [batch*h*w] global block indices needing the full search
+  int* count;         // number of entries in list (zeroed by the caller)
+};
+cudaError_t launch_seeded16(const Seeded16Args& a, cudaStream_t st);
+cudaError_t launch_full16_list(const uint16_t* ref, const uint16_t* cur, int W, int H, int pitch, long long ref_bs,
+                               long long cur_bs, int h, int w, int range, const int* list, const int* count,
+                               int max_count, bayer_mv_t* out, cudaStream_t st);
+cudaError_t configure_full16_list();
+
 // Roofline probe of the SAD primitive.
 cudaError_t run_probe_alu(int variant, double* pc_per_clk_per_sm, double* sm_mhz, int* sm_count);
 

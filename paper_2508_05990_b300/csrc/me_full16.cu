@@ -45,6 +45,107 @@ struct Full16 {
   static_assert(SPAN % 4 == 0, "span must be a multiple of 4 words");
 };
 
+// SAD of every candidate of one 16x16 block, computed by one warp from a
+// staged window (wbase: the block's window origin, row pitch P words) and
+// current block (cbase, row pitch PC words); returns the lane's best key.
+template <int R, int P, int PC>
+__device__ __forceinline__ uint64_t full16_block(const uint32_t* wbase, const uint32_t* cbase, int lane, int xb, int yb,
+                                                 int W, int H) {
+  constexpr int NU = 2 * R + 1, REACH = 2 * R, SPAN = 16 + 2 * REACH;
+  const int v = lane < NU ? lane : NU - 1;  // lanes past the last row repeat it
+  const int eps = (lane >> 2) & 1;          // row rotation for conflict-free loads
+
+  uint32_t acc[NU];
+#pragma unroll
+  for (int k = 0; k < NU; ++k) acc[k] = 0;
+  uint32_t accx = 0, accc = 0;
+
+#pragma unroll 1
+  for (int i = 0; i < 16; ++i) {
+    const int r = (i + eps) & 15;
+    uint32_t c[16];
+    const uint4* cp = reinterpret_cast<const uint4*>(cbase + r * PC);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint4 t = cp[q];
+      c[4 * q + 0] = t.x;
+      c[4 * q + 1] = t.y;
+      c[4 * q + 2] = t.z;
+      c[4 * q + 3] = t.w;
+    }
+    const uint4* wp = reinterpret_cast<const uint4*>(wbase + (2 * v + r) * P);
+#pragma unroll
+    for (int q = 0; q < SPAN / 4; ++q) {
+      const uint4 t = wp[q];
+      const uint32_t rr[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const int p = 4 * q + s;
+#pragma unroll
+        for (int k = 0; k < NU; ++k) {
+          const int cc = p - 2 * k;
+          if (cc >= 0 && cc < 16) acc[k] = sad_u32(rr[s], c[cc], acc[k]);
+        }
+      }
+    }
+    if constexpr (NU == 33) {
+      // row v = 32: candidate u = lane at window pixel 2*lane
+      const uint2* xp = reinterpret_cast<const uint2*>(wbase + (64 + r) * P + 2 * lane);
+#pragma unroll
+      for (int t2 = 0; t2 < 8; ++t2) {
+        const uint2 e2 = xp[t2];
+        accx = sad_u32(e2.x, c[2 * t2], accx);
+        accx = sad_u32(e2.y, c[2 * t2 + 1], accx);
+      }
+      // corner candidate (u, v) = (32, 32): lane l < 16 takes column l
+      if (lane < 16) accc = sad_u32(wbase[(64 + r) * P + 64 + lane], cbase[r * PC + lane], accc);
+    }
+  }
+
+  // ---- argmin with the (sad, |mv|_1, dy, dx) key
+  const int dy = 2 * v - REACH;
+  uint64_t best = kInvalidKey;
+  const bool interior = xb >= REACH && xb + 16 + REACH <= W && yb >= REACH && yb + 16 + REACH <= H;
+  if (interior) {
+    // Every candidate is valid.  Within a lane dy is fixed, so the tie-break
+    // (|dx|+|dy|, dy, dx) orders the row by rank = 0 for dx = 0, then -2, +2,
+    // -4, +4, ...; sad * 64 + rank is a 32-bit key (sad < 2^25, rank <= 32).
+    uint32_t m = 0xFFFFFFFFu;
+#pragma unroll
+    for (int k = 0; k < NU; ++k) {
+      const uint32_t rank = k == R ? 0u : (k < R ? (uint32_t)(2 * (R - k) - 1) : (uint32_t)(2 * (k - R)));
+      const uint32_t key = acc[k] * 64u + rank;
+      m = key < m ? key : m;
+    }
+    const uint32_t rank = m & 63u;
+    const int k = rank == 0 ? R : ((rank & 1u) ? R - (int)((rank + 1) >> 1) : R + (int)(rank >> 1));
+    if (lane < NU) best = make_key(m >> 6, 2 * k - REACH, dy);
+  } else {
+    const bool row_ok = lane < NU && yb + dy >= 0 && yb + dy + 16 <= H;
+#pragma unroll
+    for (int k = 0; k < NU; ++k) {
+      const int dx = 2 * k - REACH;
+      const bool ok = row_ok && xb + dx >= 0 && xb + dx + 16 <= W;
+      const uint64_t key = ok ? make_key(acc[k], dx, dy) : kInvalidKey;
+      best = key < best ? key : best;
+    }
+  }
+  if constexpr (NU == 33) {
+    {
+      const int dx = 2 * lane - REACH;
+      const bool ok = yb + 48 <= H && xb + dx >= 0 && xb + dx + 16 <= W;
+      const uint64_t key = ok ? make_key(accx, dx, 32) : kInvalidKey;
+      best = key < best ? key : best;
+    }
+    const uint32_t corner = __reduce_add_sync(0xffffffffu, accc);
+    if (lane == 0 && xb + 48 <= W && yb + 48 <= H) {
+      const uint64_t key = make_key(corner, 32, 32);
+      best = key < best ? key : best;
+    }
+  }
+  return best;
+}
+
 template <int R>
 __global__ void __launch_bounds__(kNW * 32) me_full16_even_kernel(const uint16_t* __restrict__ ref_base,
                                                                    const uint16_t* __restrict__ cur_base, int W,
@@ -129,101 +230,8 @@ __global__ void __launch_bounds__(kNW * 32) me_full16_even_kernel(const uint16_t
   const int bx = blockIdx.x * kNW + warp;
   if (bx >= w) return;
 
-  const int v = lane < C::NU ? lane : C::NU - 1;  // lanes past the last row repeat it
-  const int eps = (lane >> 2) & 1;                // row rotation for conflict-free loads
-  const uint32_t* wbase = win + 16 * warp;
-  const uint32_t* cbase = curt + 16 * warp;
-
-  uint32_t acc[C::NU];
-#pragma unroll
-  for (int k = 0; k < C::NU; ++k) acc[k] = 0;
-  uint32_t accx = 0, accc = 0;
-
-#pragma unroll 1
-  for (int i = 0; i < 16; ++i) {
-    const int r = (i + eps) & 15;
-    uint32_t c[16];
-    const uint4* cp = reinterpret_cast<const uint4*>(cbase + r * C::PC);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const uint4 t = cp[q];
-      c[4 * q + 0] = t.x;
-      c[4 * q + 1] = t.y;
-      c[4 * q + 2] = t.z;
-      c[4 * q + 3] = t.w;
-    }
-    const uint4* wp = reinterpret_cast<const uint4*>(wbase + (2 * v + r) * C::P);
-#pragma unroll
-    for (int q = 0; q < C::SPAN / 4; ++q) {
-      const uint4 t = wp[q];
-      const uint32_t rr[4] = {t.x, t.y, t.z, t.w};
-#pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        const int p = 4 * q + s;
-#pragma unroll
-        for (int k = 0; k < C::NU; ++k) {
-          const int cc = p - 2 * k;
-          if (cc >= 0 && cc < 16) acc[k] = sad_u32(rr[s], c[cc], acc[k]);
-        }
-      }
-    }
-    if constexpr (C::NU == 33) {
-      // row v = 32: candidate u = lane at window pixel 2*lane
-      const uint2* xp = reinterpret_cast<const uint2*>(wbase + (64 + r) * C::P + 2 * lane);
-#pragma unroll
-      for (int t2 = 0; t2 < 8; ++t2) {
-        const uint2 e2 = xp[t2];
-        accx = sad_u32(e2.x, c[2 * t2], accx);
-        accx = sad_u32(e2.y, c[2 * t2 + 1], accx);
-      }
-      // corner candidate (u, v) = (32, 32): lane l < 16 takes column l
-      if (lane < 16) accc = sad_u32(wbase[(64 + r) * C::P + 64 + lane], cbase[r * C::PC + lane], accc);
-    }
-  }
-
-  // ---- argmin with the (sad, |mv|_1, dy, dx) key
-  const int xb = bx * 16, yb = y0;
-  const int dy = 2 * v - C::REACH;
-  uint64_t best = kInvalidKey;
-  const bool interior = xb >= C::REACH && xb + 16 + C::REACH <= W && yb >= C::REACH && yb + 16 + C::REACH <= H;
-  if (interior) {
-    // Every candidate is valid.  Within a lane dy is fixed, so the tie-break
-    // (|dx|+|dy|, dy, dx) orders the row by rank = 0 for dx = 0, then -2, +2,
-    // -4, +4, ...; sad * 64 + rank is a 32-bit key (sad < 2^25, rank <= 32).
-    uint32_t m = 0xFFFFFFFFu;
-#pragma unroll
-    for (int k = 0; k < C::NU; ++k) {
-      const uint32_t rank = k == R ? 0u : (k < R ? (uint32_t)(2 * (R - k) - 1) : (uint32_t)(2 * (k - R)));
-      const uint32_t key = acc[k] * 64u + rank;
-      m = key < m ? key : m;
-    }
-    const uint32_t rank = m & 63u;
-    const int k = rank == 0 ? R : ((rank & 1u) ? R - (int)((rank + 1) >> 1) : R + (int)(rank >> 1));
-    if (lane < C::NU) best = make_key(m >> 6, 2 * k - C::REACH, dy);
-  } else {
-    const bool row_ok = lane < C::NU && yb + dy >= 0 && yb + dy + 16 <= H;
-#pragma unroll
-    for (int k = 0; k < C::NU; ++k) {
-      const int dx = 2 * k - C::REACH;
-      const bool ok = row_ok && xb + dx >= 0 && xb + dx + 16 <= W;
-      const uint64_t key = ok ? make_key(acc[k], dx, dy) : kInvalidKey;
-      best = key < best ? key : best;
-    }
-  }
-  if constexpr (C::NU == 33) {
-    {
-      const int dx = 2 * lane - C::REACH;
-      const bool ok = yb + 48 <= H && xb + dx >= 0 && xb + dx + 16 <= W;
-      const uint64_t key = ok ? make_key(accx, dx, 32) : kInvalidKey;
-      best = key < best ? key : best;
-    }
-    const uint32_t corner = __reduce_add_sync(0xffffffffu, accc);
-    if (lane == 0 && xb + 48 <= W && yb + 48 <= H) {
-      const uint64_t key = make_key(corner, 32, 32);
-      best = key < best ? key : best;
-    }
-  }
-  best = warp_min_u64(best);
+  const uint64_t best = warp_min_u64(
+      full16_block<R, C::P, C::PC>(win + 16 * warp, curt + 16 * warp, lane, bx * 16, y0, W, H));
   if (lane == 0) out[((long long)pair * h + blockIdx.y) * w + bx] = key_to_mv(best);
 }
 
@@ -240,6 +248,106 @@ cudaError_t launch_r(const uint16_t* ref, const uint16_t* cur, int W, int H, int
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// List mode: the exhaustive search of the blocks named in a device list (the
+// low-confidence blocks of the learned-seeded search).  Each warp stages its
+// own block's window, so the blocks need not be adjacent; warps loop over the
+// list (grid-stride) up to the count found in device memory.
+constexpr int kLW = 4;  // warps per CTA in list mode
+
+template <int R>
+struct Full16List {
+  static constexpr int REACH = 2 * R;
+  static constexpr int WIN_W = 16 + 2 * REACH;
+  static constexpr int WIN_H = 16 + 2 * REACH;
+  static constexpr int P0 = (WIN_W + 3) / 4 * 4;
+  static constexpr int P = ((P0 / 4) % 2 == 0) ? P0 + 4 : P0;  // 4 * odd words
+  static constexpr int PC = 20;                                // 4 * odd words
+  static constexpr int WARP_WORDS = WIN_H * P + 16 * PC;
+  static constexpr size_t SMEM = (size_t)kLW * WARP_WORDS * sizeof(uint32_t);
+};
+
+template <int R>
+__global__ void __launch_bounds__(kLW * 32) me_full16_list_kernel(const uint16_t* __restrict__ ref_base,
+                                                                   const uint16_t* __restrict__ cur_base, int W,
+                                                                   int H, int pitch, long long ref_bs,
+                                                                   long long cur_bs, int h, int w,
+                                                                   const int* __restrict__ list,
+                                                                   const int* __restrict__ count,
+                                                                   bayer_mv_t* __restrict__ out, bool vec_ok) {
+  using C = Full16List<R>;
+  extern __shared__ __align__(16) uint32_t smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t* win = smem + warp * C::WARP_WORDS;
+  uint32_t* curt = win + C::WIN_H * C::P;
+  const int n = *count;
+  for (int gi = blockIdx.x * kLW + warp; gi < n; gi += gridDim.x * kLW) {
+    const int gb = list[gi];
+    const int pair = gb / (h * w), rem = gb - pair * h * w;
+    const int by = rem / w, bx = rem - by * w;
+    const uint16_t* ref = ref_base + (long long)pair * ref_bs;
+    const uint16_t* cur = cur_base + (long long)pair * cur_bs;
+    const int x0 = bx * 16, y0 = by * 16;
+    __syncwarp();  // the previous block's reads are done
+    if (vec_ok) {
+      constexpr int WCH = C::WIN_W / 8, NW = WCH * C::WIN_H;
+      for (int e = lane; e < NW + 32; e += 32) {
+        uint4 raw = make_uint4(0, 0, 0, 0);
+        uint32_t* dst;
+        if (e < NW) {
+          const int ry = e / WCH, cx = e - ry * WCH;
+          const int gy = y0 - C::REACH + ry, gx = x0 - C::REACH + 8 * cx;
+          if (gy >= 0 && gy < H && gx >= 0 && gx < W)
+            raw = __ldg(reinterpret_cast<const uint4*>(ref + (long long)gy * pitch + gx));
+          dst = win + ry * C::P + 8 * cx;
+        } else {
+          const int f = e - NW, ry = f >> 1, cx = f & 1;
+          raw = __ldg(reinterpret_cast<const uint4*>(cur + (long long)(y0 + ry) * pitch + x0 + 8 * cx));
+          dst = curt + ry * C::PC + 8 * cx;
+        }
+        reinterpret_cast<uint4*>(dst)[0] = make_uint4(pix_lo(raw.x), pix_hi(raw.x), pix_lo(raw.y), pix_hi(raw.y));
+        reinterpret_cast<uint4*>(dst)[1] = make_uint4(pix_lo(raw.z), pix_hi(raw.z), pix_lo(raw.w), pix_hi(raw.w));
+      }
+    } else {
+      for (int e = lane; e < C::WIN_H * C::WIN_W; e += 32) {
+        const int ry = e / C::WIN_W, rx = e - ry * C::WIN_W;
+        const int gy = y0 - C::REACH + ry, gx = x0 - C::REACH + rx;
+        uint32_t v = 0;
+        if (gy >= 0 && gy < H && gx >= 0 && gx < W) v = __ldg(ref + (long long)gy * pitch + gx);
+        win[ry * C::P + rx] = pix_word(v);
+      }
+      for (int e = lane; e < 256; e += 32)
+        curt[(e >> 4) * C::PC + (e & 15)] = pix_word(__ldg(cur + (long long)(y0 + (e >> 4)) * pitch + x0 + (e & 15)));
+    }
+    __syncwarp();
+    const uint64_t best = warp_min_u64(full16_block<R, C::P, C::PC>(win, curt, lane, x0, y0, W, H));
+    if (lane == 0) out[gb] = key_to_mv(best);
+  }
+}
+
+template <int R>
+cudaError_t launch_list_r(const uint16_t* ref, const uint16_t* cur, int W, int H, int pitch, long long ref_bs,
+                          long long cur_bs, int h, int w, const int* list, const int* count, int max_count,
+                          bayer_mv_t* out, cudaStream_t st) {
+  using C = Full16List<R>;
+  int dev = 0, nsm = 148;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  int grid = (max_count + kLW - 1) / kLW;
+  if (grid > 2 * nsm) grid = 2 * nsm;
+  if (grid < 1) grid = 1;
+  const bool vec_ok = (reinterpret_cast<uintptr_t>(ref) % 16) == 0 && (reinterpret_cast<uintptr_t>(cur) % 16) == 0 &&
+                      pitch % 8 == 0 && ref_bs % 8 == 0 && cur_bs % 8 == 0;
+  me_full16_list_kernel<R><<<grid, kLW * 32, C::SMEM, st>>>(ref, cur, W, H, pitch, ref_bs, cur_bs, h, w, list, count,
+                                                             out, vec_ok);
+  return cudaGetLastError();
+}
+
+template <int R>
+cudaError_t configure_list_r() {
+  return cudaFuncSetAttribute(me_full16_list_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)Full16List<R>::SMEM);
+}
+
 template <int R>
 cudaError_t configure_r() {
   return cudaFuncSetAttribute(me_full16_even_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -254,6 +362,26 @@ cudaError_t configure_full16() {
   if ((e = configure_r<8>()) != cudaSuccess) return e;
   if ((e = configure_r<12>()) != cudaSuccess) return e;
   return configure_r<16>();
+}
+
+cudaError_t configure_full16_list() {
+  cudaError_t e;
+  if ((e = configure_list_r<4>()) != cudaSuccess) return e;
+  if ((e = configure_list_r<8>()) != cudaSuccess) return e;
+  if ((e = configure_list_r<12>()) != cudaSuccess) return e;
+  return configure_list_r<16>();
+}
+
+cudaError_t launch_full16_list(const uint16_t* ref, const uint16_t* cur, int W, int H, int pitch, long long ref_bs,
+                               long long cur_bs, int h, int w, int range, const int* list, const int* count,
+                               int max_count, bayer_mv_t* out, cudaStream_t st) {
+  switch (range) {
+    case 8: return launch_list_r<4>(ref, cur, W, H, pitch, ref_bs, cur_bs, h, w, list, count, max_count, out, st);
+    case 16: return launch_list_r<8>(ref, cur, W, H, pitch, ref_bs, cur_bs, h, w, list, count, max_count, out, st);
+    case 24: return launch_list_r<12>(ref, cur, W, H, pitch, ref_bs, cur_bs, h, w, list, count, max_count, out, st);
+    case 32: return launch_list_r<16>(ref, cur, W, H, pitch, ref_bs, cur_bs, h, w, list, count, max_count, out, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 bool full16_even_supported(int range) { return range == 8 || range == 16 || range == 24 || range == 32; }

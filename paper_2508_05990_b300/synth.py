@@ -161,6 +161,21 @@ def proposals(seed: int, h: int, w: int, search_range: int, true_mv=None, jitter
     return p[..., 0].astype(np.float32), p[..., 1].astype(np.float32), conf
 
 
+def he_normal_params(seed: int, shapes) -> np.ndarray:
+    """Initial network parameters, flat float32: for each (kind, shape) in order,
+    kind "w" draws N(0, 2 / fan_in) with fan_in = prod(shape[1:]) (He-normal) and
+    kind "b" gives zeros.  Random draws only; the layout is the caller's."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for kind, shape in shapes:
+        n = int(np.prod(shape))
+        if kind == "b":
+            parts.append(np.zeros(n))
+        else:
+            parts.append(rng.normal(0.0, np.sqrt(2.0 / int(np.prod(shape[1:]))), n))
+    return np.concatenate(parts).astype(np.float32)
+
+
 # Workloads (all synthetic).  Seeds: workload k uses 1000 + k; clips and
 # streams add their index.
 WORKLOADS = {

@@ -1,0 +1,175 @@
+"""Learned proposal network and learned-seeded search on the GPU vs the oracle.
+
+The network's weights and activations are bfloat16 with float32 accumulation.
+The oracle (oracle/cnn.py) evaluates the same bf16 weights in float64, either
+keeping activations exact (act_round=None) or rounding them to bfloat16 at the
+points the network's definition stores them (act_round="bf16").
+
+Tolerances (normwise relative):
+* forward outputs vs the exact float64 oracle: 2e-2 (the BF16 tolerance);
+* gradient vs the bf16-activation oracle: 1e-4 (only float32 accumulation
+  order differs; measured 1.3e-7);
+* gradient vs the exact float64 oracle: 5e-2 -- rounding the activations to
+  bfloat16 (relative 2^-9 each) moves the loss surface itself, and the
+  gradient of four stacked layers moves with it (measured 3.2 %, identical for
+  the GPU and for the bf16-activation oracle).
+Integer outputs (MV fields) are compared bit for bit.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import cnn
+from paper_2508_05990_b300 import bayer_me as bm
+from paper_2508_05990_b300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 2e-2
+
+
+@pytest.fixture(scope="module")
+def handle():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2508_05990_b300 import build
+    build.build()
+    h = bm.Handle(0)
+    yield h
+    h.close()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def weights(seed):
+    theta = synth.he_normal_params(seed, bm.CNN_SHAPES)
+    w32 = torch.from_numpy(theta).cuda()
+    wbf = bm.to_bf16_bits(w32)
+    theta_bf = w32.to(torch.bfloat16).double().cpu().numpy()  # the values the GPU uses, exactly
+    return w32, wbf, theta_bf
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-30))
+
+
+@pytest.mark.parametrize("shape", [(128, 192), (1088, 1920)])
+def test_cnn_forward_matches_oracle(handle, shape):
+    H, W = shape
+    ref, cur = synth.pan_clip(90, H, W, n_frames=2, rect_size=(16, 64))
+    _, wbf, theta = weights(3)
+    prop, conf = handle.cnn_forward(dev(ref), dev(cur), wbf, 32)
+    dx, dy, cf, _ = cnn.forward(theta, ref, cur, 32)
+    p = prop[0].cpu().numpy()
+    assert rel(p[..., 0], dx) < TOL and rel(p[..., 1], dy) < TOL
+    assert rel(conf[0].cpu().numpy(), cf) < TOL
+
+
+def test_cnn_forward_batched_strides(handle):
+    H, W = 96, 128
+    frames = synth.pan_clip(91, H, W, n_frames=4, rect_size=(8, 32))
+    _, wbf, theta = weights(4)
+    d = dev(frames)
+    prop, conf = handle.cnn_forward(d, d[1:], wbf, 16, batch=3, ref_batch_stride=H * W, cur_batch_stride=H * W)
+    for t in range(3):
+        dx, dy, cf, _ = cnn.forward(theta, frames[t], frames[t + 1], 16)
+        assert rel(prop[t, ..., 0].cpu().numpy(), dx) < TOL
+        assert rel(conf[t].cpu().numpy(), cf) < TOL
+
+
+def test_cnn_loss_and_gradient_match_oracle(handle):
+    H, W = 128, 192
+    frames = synth.pan_clip(92, H, W, n_frames=3, rect_size=(16, 48))
+    _, wbf, theta = weights(5)
+    rng = np.random.default_rng(8)
+    h, w = H // 16, W // 16
+    labels = np.zeros((2, h, w), oracle.MV_DTYPE)
+    labels["dx"] = 2 * rng.integers(-16, 17, (2, h, w))
+    labels["dy"] = 2 * rng.integers(-16, 17, (2, h, w))
+    d = dev(frames)
+    lab = dev(labels.view(np.int32).reshape(2, h, w, 2))
+    grad, loss = handle.cnn_loss_grad(d, d[1:], wbf, lab, 32, batch=2, ref_batch_stride=H * W, cur_batch_stride=H * W)
+    g = grad.cpu().numpy()
+    losses, grads = [], []
+    for t in range(2):
+        l, gr = cnn.loss_and_grad(theta, frames[t], frames[t + 1], labels["dx"][t].astype(np.float64),
+                                  labels["dy"][t].astype(np.float64), 32)
+        losses.append(l)
+        grads.append(gr)
+    want_loss, want_grad = np.mean(losses), np.mean(grads, axis=0)
+    assert abs(float(loss.item()) - want_loss) <= TOL * abs(want_loss)
+    assert rel(g, want_grad) < 5e-2
+    # the same network with its bfloat16 activation rounding modelled in the oracle
+    gb = np.mean([cnn.loss_and_grad(theta, frames[t], frames[t + 1], labels["dx"][t].astype(np.float64),
+                                    labels["dy"][t].astype(np.float64), 32, act_round="bf16")[1] for t in range(2)],
+                 axis=0)
+    assert rel(g, gb) < 1e-4
+    for name, (kind, shape) in zip(["w1", "b1", "w2", "b2", "w3", "b3", "w4", "b4", "wh", "bh"], bm.CNN_SHAPES):
+        o = bm.CNN_OFFSETS[name]
+        n = int(np.prod(shape))
+        if np.linalg.norm(gb[o:o + n]) > 1e-6:
+            assert rel(g[o:o + n], gb[o:o + n]) < 1e-3, name
+
+
+def test_adamw_matches_formula(handle):
+    rng = np.random.default_rng(2)
+    n = bm.CNN_NPARAMS
+    w0, g, m0, v0 = (rng.normal(size=n).astype(np.float32) for _ in range(4))
+    v0 = np.abs(v0)
+    w, m, v = dev(w0.copy()), dev(m0.copy()), dev(v0.copy())
+    wb = torch.empty(n, dtype=torch.int16, device="cuda")
+    lr, b1, b2, eps, wd, step = 1e-3, 0.9, 0.999, 1e-8, 0.01, 7
+    handle.cnn_adamw(w, wb, dev(g), m, v, step, lr, b1, b2, eps, wd)
+    mm = b1 * m0.astype(np.float64) + (1 - b1) * g
+    vv = b2 * v0.astype(np.float64) + (1 - b2) * g.astype(np.float64) ** 2
+    ww = w0 - lr * ((mm / (1 - b1 ** step)) / (np.sqrt(vv / (1 - b2 ** step)) + eps) + wd * w0)
+    np.testing.assert_allclose(w.cpu().numpy(), ww, rtol=1e-5, atol=1e-7)
+    np.testing.assert_allclose(m.cpu().numpy(), mm, rtol=1e-5, atol=1e-7)
+    assert torch.equal(wb, bm.to_bf16_bits(w))
+
+
+def test_learned_equals_seeded_mode_on_network_proposals(handle):
+    H, W = 256, 384
+    frames = synth.pan_clip(93, H, W, n_frames=3, rect_size=(16, 64))
+    _, wbf, _ = weights(6)
+    d = dev(frames)
+    kw = dict(batch=2, ref_batch_stride=H * W, cur_batch_stride=H * W)
+    fb = torch.empty((2, H // 16, W // 16), dtype=torch.uint8, device="cuda")
+    nfb = torch.zeros(1, dtype=torch.int32, device="cuda")
+    got = handle.estimate_learned(d, d[1:], wbf, 32, 0.5, fallback=fb, n_fallback=nfb, **kw)
+    prop, conf = handle.cnn_forward(d, d[1:], wbf, 32, **kw)
+    fb2 = torch.empty_like(fb)
+    want = handle.estimate_ex(d, d[1:], mode=bm.MODE_SEEDED, search_range=32, prop_dxdy=prop, conf=conf,
+                              fallback=fb2, **kw)
+    torch.cuda.synchronize()
+    assert torch.equal(got, want) and torch.equal(fb, fb2)
+    assert int(nfb.item()) == int(fb.sum().item())
+
+
+@pytest.mark.parametrize("mode", ["all_fallback", "at_optimum", "mixed"])
+def test_seeded_fast_path_vs_oracle(handle, mode):
+    H, W = 224, 320
+    frames = synth.pan_clip(94, H, W, n_frames=2, rect_size=(16, 64))
+    h, w = H // 16, W // 16
+    full, _ = oracle.me_full(frames[0], frames[1], 16, 32, even=True)
+    if mode == "all_fallback":
+        pdx = pdy = np.zeros((h, w), np.float32)
+        conf = np.zeros((h, w), np.float32)
+    elif mode == "at_optimum":
+        pdx, pdy = full["dx"].astype(np.float32), full["dy"].astype(np.float32)
+        conf = np.ones((h, w), np.float32)
+    else:
+        pdx, pdy, conf = synth.proposals(95, h, w, 32, true_mv=np.stack([full["dx"], full["dy"]], -1), jitter=4.0)
+    prop = np.stack([pdx, pdy], -1)
+    out = handle.estimate_ex(dev(frames[0]), dev(frames[1]), mode=bm.MODE_SEEDED, search_range=32,
+                             prop_dxdy=dev(prop), conf=dev(conf))
+    want, _, _ = oracle.me_seeded(frames[0], frames[1], 16, 32, pdx, pdy, conf)
+    g = bm.records_to_numpy(out[0])
+    for k in ("dx", "dy", "sad"):
+        np.testing.assert_array_equal(g[k], want[k])
+    if mode != "mixed":
+        for k in ("dx", "dy", "sad"):
+            np.testing.assert_array_equal(g[k], full[k])
