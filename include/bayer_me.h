@@ -207,9 +207,11 @@ bayer_status_t bayer_probe_alu(bayer_me_t h, int variant, double* pc_per_clk_per
  * Activations are bfloat16, accumulation float32.  W and H must be multiples
  * of 32 (the L4 grid is then exactly half the 16x16 block grid).
  * Loss (mean over the blocks of the batch): BerHu_4(dx - dx*) +
- * BerHu_4(dy - dy*) + BCE(conf, t), BerHu_c(e) = |e| for |e| <= c, else
- * (e^2 + c^2) / (2c); t = 1 where the proposal rounded to the nearest even
- * integer lies within +-4 of the label (dx*, dy*) in both components. */
+ * BerHu_4(dy - dy*) - t log(conf) - w_neg (1 - t) log(1 - conf), with
+ * BerHu_c(e) = |e| for |e| <= c, else (e^2 + c^2) / (2c); t = 1 where the
+ * proposal rounded to the nearest even integer lies within +-4 of the label
+ * (dx*, dy*) in both components (then the +-4 refine reaches the label).
+ * w_neg > 1 makes a confidence >= 0.5 mean P(t = 1) >= w_neg / (1 + w_neg). */
 #define BAYER_CNN_W1 0
 #define BAYER_CNN_B1 2304
 #define BAYER_CNN_W2 2336
@@ -229,13 +231,13 @@ bayer_status_t bayer_cnn_forward(bayer_me_t h, const uint16_t* ref, const uint16
                                  int batch, long long ref_batch_stride, long long cur_batch_stride,
                                  const uint16_t* w_bf16, int range, float* prop_dxdy, float* conf, void* stream);
 
-/* Loss and its gradient w.r.t. all parameters on `batch` pairs labelled by
- * `labels` [batch][H/16][W/16] (the exhaustive-search fields): grad
+/* Loss (neg_weight = w_neg > 0) and its gradient w.r.t. all parameters on
+ * `batch` pairs labelled by `labels` [batch][H/16][W/16] (the exhaustive-search fields): grad
  * [BAYER_CNN_NPARAMS] and loss [1], device float32, overwritten. */
 bayer_status_t bayer_cnn_loss_grad(bayer_me_t h, const uint16_t* ref, const uint16_t* cur, int W, int H, int pitch,
                                    int batch, long long ref_batch_stride, long long cur_batch_stride,
-                                   const uint16_t* w_bf16, const bayer_mv_t* labels, int range, float* grad,
-                                   float* loss, void* stream);
+                                   const uint16_t* w_bf16, const bayer_mv_t* labels, int range, float neg_weight,
+                                   float* grad, float* loss, void* stream);
 
 /* One AdamW step (decoupled weight decay, bias-corrected moments) on the
  * float32 master w, refreshing the bfloat16 copy; step counts from 1. */

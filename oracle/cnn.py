@@ -19,10 +19,11 @@ definitions below:
   (2 i + sy, 2 k + sx) (depth-to-space x 2);
 * dx = range * tanh(z_0), dy = range * tanh(z_1), conf = sigmoid(z_2);
 * loss (mean over blocks): BerHu_c(dx - dx*) + BerHu_c(dy - dy*) with
-  c = 4 px (|e| below c, (e^2 + c^2) / (2c) above), plus the binary cross
-  entropy of conf against t = 1 if the proposal rounded to the nearest even
-  integer lies within +-4 of the label in both components, else 0 (t is a
-  constant of the prediction, no gradient flows through it).
+  c = 4 px (|e| below c, (e^2 + c^2) / (2c) above), plus the weighted binary
+  cross entropy -t log(conf) - w_neg (1 - t) log(1 - conf) against t = 1 if
+  the proposal rounded to the nearest even integer lies within +-4 of the
+  label in both components, else 0 (t is a constant of the prediction, no
+  gradient flows through it).
 
 Activations: the network's definition stores each post-ReLU activation in
 bfloat16 (weights are bfloat16 too).  ``act_round="bf16"`` applies that
@@ -166,21 +167,21 @@ def berhu_grad(e, c=BERHU_C):
     return np.where(np.abs(e) <= c, np.sign(e), e / c)
 
 
-def loss_and_grad(theta, ref, cur, label_dx, label_dy, search_range: int, act_round=None):
+def loss_and_grad(theta, ref, cur, label_dx, label_dy, search_range: int, act_round=None, neg_weight=1.0):
     """Mean loss over blocks and its gradient w.r.t. theta (float64)."""
     dx, dy, conf, cache = forward(theta, ref, cur, search_range, act_round)
     n = dx.size
     ex, ey = dx - label_dx, dy - label_dy
     t = ((np.abs(round_even(dx) - label_dx) <= 4) & (np.abs(round_even(dy) - label_dy) <= 4)).astype(np.float64)
     eps = 1e-12
-    bce = -(t * np.log(conf + eps) + (1 - t) * np.log(1 - conf + eps))
+    bce = -(t * np.log(conf + eps) + neg_weight * (1 - t) * np.log(1 - conf + eps))
     loss = float((berhu(ex) + berhu(ey) + bce).sum() / n)
     z = cache["z"]
     R = cache["range"]
     dz = np.zeros_like(z)
     dz[0] = berhu_grad(ex) * R * (1 - np.tanh(z[0]) ** 2) / n
     dz[1] = berhu_grad(ey) * R * (1 - np.tanh(z[1]) ** 2) / n
-    dz[2] = (conf - t) / n
+    dz[2] = (conf * (t + neg_weight * (1 - t)) - t) / n
     return loss, backward(cache, dz)
 
 

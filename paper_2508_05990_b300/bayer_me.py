@@ -83,7 +83,7 @@ def load(path: str = LIB_PATH):
                                     ctypes.POINTER(ctypes.c_int)]
     lib.bayer_me_estimate_c2f_noalloc.argtypes = [P, P, I, I, I, ctypes.POINTER(Params), P, P]
     lib.bayer_cnn_forward.argtypes = [P, P, P, I, I, I, I, LL, LL, P, I, P, P, P]
-    lib.bayer_cnn_loss_grad.argtypes = [P, P, P, I, I, I, I, LL, LL, P, P, I, P, P, P]
+    lib.bayer_cnn_loss_grad.argtypes = [P, P, P, I, I, I, I, LL, LL, P, P, I, F, P, P, P]
     lib.bayer_cnn_adamw.argtypes = [P, P, P, P, P, P, I, F, F, F, F, F, P]
     lib.bayer_me_estimate_learned.argtypes = [P, P, P, I, I, I, I, LL, LL, P, I, F, P, P, P, P]
     for name in EXPORTS:
@@ -263,7 +263,7 @@ class Handle:
         return prop, conf
 
     def cnn_loss_grad(self, ref, cur, w_bf16, labels, search_range=32, batch=1, ref_batch_stride=0,
-                      cur_batch_stride=0, grad=None, loss=None, stream=None):
+                      cur_batch_stride=0, grad=None, loss=None, neg_weight=1.0, stream=None):
         """(grad [CNN_NPARAMS], loss [1]) float32 tensors; labels: int32 records [batch, h, w, 2]."""
         import torch
         H, W = ref.shape[-2:]
@@ -272,7 +272,8 @@ class Handle:
         if loss is None:
             loss = torch.empty(1, dtype=torch.float32, device=ref.device)
         _check(self._lib.bayer_cnn_loss_grad(self._h, _ptr(ref), _ptr(cur), W, H, W, batch, ref_batch_stride,
-                                             cur_batch_stride, _ptr(w_bf16), _ptr(labels), search_range, _ptr(grad),
+                                             cur_batch_stride, _ptr(w_bf16), _ptr(labels), search_range,
+                                             float(neg_weight), _ptr(grad),
                                              _ptr(loss), _stream(stream)), "bayer_cnn_loss_grad")
         return grad, loss
 

@@ -480,8 +480,10 @@ bayer_status_t bayer_cnn_forward(bayer_me_t h, const uint16_t* ref, const uint16
 
 bayer_status_t bayer_cnn_loss_grad(bayer_me_t h, const uint16_t* ref, const uint16_t* cur, int W, int H, int pitch,
                                    int batch, long long ref_bs, long long cur_bs, const uint16_t* w_bf16,
-                                   const bayer_mv_t* labels, int range, float* grad, float* loss, void* stream) {
+                                   const bayer_mv_t* labels, int range, float neg_weight, float* grad, float* loss,
+                                   void* stream) {
   if (!h || !w_bf16 || !labels || !grad || !loss || range < 1 || range > 510) return BAYER_ERR_INVALID_ARG;
+  if (!(neg_weight > 0.f)) return BAYER_ERR_INVALID_ARG;
   bayer_status_t s = check_cnn_frames(ref, cur, W, H, pitch, batch, ref_bs, cur_bs);
   if (s != BAYER_OK) return s;
   DeviceGuard g(h->device);
@@ -492,8 +494,8 @@ bayer_status_t bayer_cnn_loss_grad(bayer_me_t h, const uint16_t* ref, const uint
       BAYER_OK)
     return s;
   bme::CnnFrames fr{ref, cur, W, H, pitch, ref_bs, cur_bs};
-  return cuda_status(bme::cnn_loss_grad(fr, batch, w_bf16, labels, range, h->cnn_acts, h->cnn_dpre, grad, loss,
-                                        static_cast<cudaStream_t>(stream)));
+  return cuda_status(bme::cnn_loss_grad(fr, batch, w_bf16, labels, range, neg_weight, h->cnn_acts, h->cnn_dpre, grad,
+                                        loss, static_cast<cudaStream_t>(stream)));
 }
 
 bayer_status_t bayer_cnn_adamw(bayer_me_t h, float* w, uint16_t* w_bf16, const float* grad, float* m, float* v,

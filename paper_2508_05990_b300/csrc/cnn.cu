@@ -12,7 +12,7 @@
 //   dx = range*tanh(z_0), dy = range*tanh(z_1), conf = sigmoid(z_2)
 // Activations are NHWC bf16 [B][H][W][32]; layer 1 reads the Bayer frames
 // directly (the packing is fused into its gather).  Loss per block:
-//   BerHu_4(dx - dx*) + BerHu_4(dy - dy*) + BCE(conf, t),
+//   BerHu_4(dx - dx*) + BerHu_4(dy - dy*) - t log(conf) - w_neg (1 - t) log(1 - conf),
 //   t = [round_even(dx) within +-4 of dx* and likewise for dy],
 // averaged over all blocks of the batch.
 #include <cuda_bf16.h>
@@ -235,7 +235,8 @@ __device__ __forceinline__ float berhu_grad(float e) {
 __global__ void __launch_bounds__(128) head_loss_bwd_kernel(const __nv_bfloat16* __restrict__ x4, int H4, int W4,
                                                             const __nv_bfloat16* __restrict__ w, int range,
                                                             const bayer_mv_t* __restrict__ labels, float inv_n,
-                                                            float* __restrict__ dpre4, float* __restrict__ grad,
+                                                            float neg_w, float* __restrict__ dpre4,
+                                                            float* __restrict__ grad,
                                                             float* __restrict__ loss) {
   __shared__ float wh[12 * kC + 12];
   __shared__ float gsum[12 * kC + 12];
@@ -277,10 +278,10 @@ __global__ void __launch_bounds__(128) head_loss_bwd_kernel(const __nv_bfloat16*
       const float ex = dx - (float)lab.dx, ey = dy - (float)lab.dy;
       const float tgt = (fabsf(round_even(dx) - (float)lab.dx) <= 4.f && fabsf(round_even(dy) - (float)lab.dy) <= 4.f)
                             ? 1.f : 0.f;
-      l += berhu(ex) + berhu(ey) - (tgt * logf(cf + 1e-12f) + (1.f - tgt) * logf(1.f - cf + 1e-12f));
+      l += berhu(ex) + berhu(ey) - (tgt * logf(cf + 1e-12f) + neg_w * (1.f - tgt) * logf(1.f - cf + 1e-12f));
       dz[3 * s + 0] = berhu_grad(ex) * (float)range * (1.f - tx * tx) * inv_n;
       dz[3 * s + 1] = berhu_grad(ey) * (float)range * (1.f - ty * ty) * inv_n;
-      dz[3 * s + 2] = (cf - tgt) * inv_n;
+      dz[3 * s + 2] = (cf * (tgt + neg_w * (1.f - tgt)) - tgt) * inv_n;
     }
     // d x4, masked by ReLU (x4 > 0 iff its pre-activation > 0)
     float* dst = dpre4 + ((long long)b * cells + t) * kC;
@@ -510,7 +511,7 @@ cudaError_t cnn_forward(const CnnFrames& fr, int batch, const uint16_t* wbf16, i
 }
 
 cudaError_t cnn_loss_grad(const CnnFrames& fr, int batch, const uint16_t* wbf16, const bayer_mv_t* labels, int range,
-                          void* acts, void* dpre, float* grad, float* loss, cudaStream_t st) {
+                          float neg_weight, void* acts, void* dpre, float* grad, float* loss, cudaStream_t st) {
   const CnnShapes s = cnn_shapes(fr.W, fr.H);
   cudaError_t e = cnn_forward_acts(fr, batch, wbf16, acts, st);
   if (e != cudaSuccess) return e;
@@ -526,7 +527,8 @@ cudaError_t cnn_loss_grad(const CnnFrames& fr, int batch, const uint16_t* wbf16,
   const float inv_n = 1.0f / ((float)batch * (2 * s.H[4]) * (2 * s.W[4]));
   {
     dim3 g((s.H[4] * s.W[4] + 127) / 128, batch);
-    head_loss_bwd_kernel<<<g, 128, 0, st>>>(a[4], s.H[4], s.W[4], w, range, labels, inv_n, d[4], grad, loss);
+    head_loss_bwd_kernel<<<g, 128, 0, st>>>(a[4], s.H[4], s.W[4], w, range, labels, inv_n, neg_weight, d[4], grad,
+                                            loss);
   }
   const int woff[5] = {0, BAYER_CNN_W1, BAYER_CNN_W2, BAYER_CNN_W3, BAYER_CNN_W4};
   const int boff[5] = {0, BAYER_CNN_B1, BAYER_CNN_B2, BAYER_CNN_B3, BAYER_CNN_B4};

@@ -68,7 +68,7 @@ size_t cnn_grad_bytes(int W, int H, int batch);  // fp32 pre-activation gradient
 cudaError_t cnn_forward(const CnnFrames& fr, int batch, const uint16_t* wbf16, int range, void* acts, float* prop,
                         float* conf, cudaStream_t st);
 cudaError_t cnn_loss_grad(const CnnFrames& fr, int batch, const uint16_t* wbf16, const bayer_mv_t* labels, int range,
-                          void* acts, void* dpre, float* grad, float* loss, cudaStream_t st);
+                          float neg_weight, void* acts, void* dpre, float* grad, float* loss, cudaStream_t st);
 cudaError_t cnn_adamw(float* w, uint16_t* wbf16, const float* g, float* m, float* v, int n, int step, float lr,
                       float b1, float b2, float eps, float wd, cudaStream_t st);
 

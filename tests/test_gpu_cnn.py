@@ -80,7 +80,8 @@ def test_cnn_forward_batched_strides(handle):
         assert rel(conf[t].cpu().numpy(), cf) < TOL
 
 
-def test_cnn_loss_and_gradient_match_oracle(handle):
+@pytest.mark.parametrize("neg_weight", [1.0, 8.0])
+def test_cnn_loss_and_gradient_match_oracle(handle, neg_weight):
     H, W = 128, 192
     frames = synth.pan_clip(92, H, W, n_frames=3, rect_size=(16, 48))
     _, wbf, theta = weights(5)
@@ -91,12 +92,13 @@ def test_cnn_loss_and_gradient_match_oracle(handle):
     labels["dy"] = 2 * rng.integers(-16, 17, (2, h, w))
     d = dev(frames)
     lab = dev(labels.view(np.int32).reshape(2, h, w, 2))
-    grad, loss = handle.cnn_loss_grad(d, d[1:], wbf, lab, 32, batch=2, ref_batch_stride=H * W, cur_batch_stride=H * W)
+    grad, loss = handle.cnn_loss_grad(d, d[1:], wbf, lab, 32, batch=2, ref_batch_stride=H * W, cur_batch_stride=H * W,
+                                      neg_weight=neg_weight)
     g = grad.cpu().numpy()
     losses, grads = [], []
     for t in range(2):
         l, gr = cnn.loss_and_grad(theta, frames[t], frames[t + 1], labels["dx"][t].astype(np.float64),
-                                  labels["dy"][t].astype(np.float64), 32)
+                                  labels["dy"][t].astype(np.float64), 32, neg_weight=neg_weight)
         losses.append(l)
         grads.append(gr)
     want_loss, want_grad = np.mean(losses), np.mean(grads, axis=0)
@@ -104,7 +106,8 @@ def test_cnn_loss_and_gradient_match_oracle(handle):
     assert rel(g, want_grad) < 5e-2
     # the same network with its bfloat16 activation rounding modelled in the oracle
     gb = np.mean([cnn.loss_and_grad(theta, frames[t], frames[t + 1], labels["dx"][t].astype(np.float64),
-                                    labels["dy"][t].astype(np.float64), 32, act_round="bf16")[1] for t in range(2)],
+                                    labels["dy"][t].astype(np.float64), 32, act_round="bf16",
+                                    neg_weight=neg_weight)[1] for t in range(2)],
                  axis=0)
     assert rel(g, gb) < 1e-4
     for name, (kind, shape) in zip(["w1", "b1", "w2", "b2", "w3", "b3", "w4", "b4", "wh", "bh"], bm.CNN_SHAPES):

@@ -65,13 +65,14 @@ def test_forward_and_gradient_match_torch_autograd():
     np.testing.assert_allclose(g, tg, rtol=1e-8, atol=1e-12)
 
 
-def test_gradient_matches_finite_differences():
+@pytest.mark.parametrize("neg_weight", [1.0, 6.0])
+def test_gradient_matches_finite_differences(neg_weight):
     ref, cur = synth.pan_clip(5, 64, 64, n_frames=2, rect_size=(8, 24))
     theta = synth.he_normal_params(12, shapes()).astype(np.float64)
     rng = np.random.default_rng(6)
     ldx = 2.0 * rng.integers(-8, 9, (4, 4))
     ldy = 2.0 * rng.integers(-8, 9, (4, 4))
-    _, g = cnn.loss_and_grad(theta, ref, cur, ldx, ldy, 16)
+    _, g = cnn.loss_and_grad(theta, ref, cur, ldx, ldy, 16, neg_weight=neg_weight)
     idx = np.concatenate([rng.choice(2304, 6, replace=False), 2304 + rng.choice(32, 3, replace=False),
                           rng.choice(np.arange(2336, cnn.n_params()), 12, replace=False)])
     h = 1e-6
@@ -79,7 +80,8 @@ def test_gradient_matches_finite_differences():
         tp, tm = theta.copy(), theta.copy()
         tp[i] += h
         tm[i] -= h
-        fd = (cnn.loss_and_grad(tp, ref, cur, ldx, ldy, 16)[0] - cnn.loss_and_grad(tm, ref, cur, ldx, ldy, 16)[0]) / (2 * h)
+        fd = (cnn.loss_and_grad(tp, ref, cur, ldx, ldy, 16, neg_weight=neg_weight)[0]
+              - cnn.loss_and_grad(tm, ref, cur, ldx, ldy, 16, neg_weight=neg_weight)[0]) / (2 * h)
         assert abs(fd - g[i]) <= 1e-6 + 1e-5 * abs(g[i]), (i, fd, g[i])
 
 
