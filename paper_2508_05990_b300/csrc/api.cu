@@ -195,6 +195,7 @@ bayer_status_t bayer_me_init(bayer_me_t* out, int device) {
   h->device = device;
   e = bme::configure_full16();
   if (e == cudaSuccess) e = bme::configure_full16_list();
+  if (e == cudaSuccess) e = bme::configure_conv_tc();
   if (e == cudaSuccess) e = cudaMalloc(&h->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking);
@@ -474,7 +475,7 @@ bayer_status_t bayer_cnn_forward(bayer_me_t h, const uint16_t* ref, const uint16
       BAYER_OK)
     return s;
   bme::CnnFrames fr{ref, cur, W, H, pitch, ref_bs, cur_bs};
-  return cuda_status(bme::cnn_forward(fr, batch, w_bf16, range, h->cnn_acts, prop_dxdy, conf,
+  return cuda_status(bme::cnn_forward(fr, batch, w_bf16, range, h->cnn_acts, prop_dxdy, conf, h->d_status,
                                       static_cast<cudaStream_t>(stream)));
 }
 
@@ -495,7 +496,7 @@ bayer_status_t bayer_cnn_loss_grad(bayer_me_t h, const uint16_t* ref, const uint
     return s;
   bme::CnnFrames fr{ref, cur, W, H, pitch, ref_bs, cur_bs};
   return cuda_status(bme::cnn_loss_grad(fr, batch, w_bf16, labels, range, neg_weight, h->cnn_acts, h->cnn_dpre, grad,
-                                        loss, static_cast<cudaStream_t>(stream)));
+                                        loss, h->d_status, static_cast<cudaStream_t>(stream)));
 }
 
 bayer_status_t bayer_cnn_adamw(bayer_me_t h, float* w, uint16_t* w_bf16, const float* grad, float* m, float* v,
@@ -526,7 +527,7 @@ bayer_status_t bayer_me_estimate_learned(bayer_me_t h, const uint16_t* ref, cons
   float* prop = h->prop;
   float* conf = h->prop + 2 * nblk;
   bme::CnnFrames fr{ref, cur, W, H, pitch, ref_bs, cur_bs};
-  cudaError_t e = bme::cnn_forward(fr, batch, w_bf16, range, h->cnn_acts, prop, conf, st);
+  cudaError_t e = bme::cnn_forward(fr, batch, w_bf16, range, h->cnn_acts, prop, conf, h->d_status, st);
   if (e != cudaSuccess) return cuda_status(e);
   return seeded_fast(h, ref, cur, W, H, pitch, ref_bs, cur_bs, batch, range, prop, conf, conf_thresh, mv_out,
                      fallback_out, n_fallback, st);

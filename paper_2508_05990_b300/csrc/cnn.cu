@@ -10,8 +10,9 @@
 //   z = 1x1 conv (32 -> 12) + b_h; channel 3*(2*sy + sx) + q of L4 cell (i, k)
 //       is quantity q of block (2i + sy, 2k + sx)
 //   dx = range*tanh(z_0), dy = range*tanh(z_1), conf = sigmoid(z_2)
-// Activations are NHWC bf16 [B][H][W][32]; layer 1 reads the Bayer frames
-// directly (the packing is fused into its gather).  Loss per block:
+// Activations are NHWC bf16 [B][H][W][32].  The four convolutions run on the
+// tensor cores (conv_tc.cu; layer 1 gathers the Bayer frames directly, the
+// packing fused into its operand staging); head, loss and backward are SIMT.  Loss per block:
 //   BerHu_4(dx - dx*) + BerHu_4(dy - dy*) - t log(conf) - w_neg (1 - t) log(1 - conf),
 //   t = [round_even(dx) within +-4 of dx* and likewise for dy],
 // averaged over all blocks of the batch.
@@ -57,129 +58,6 @@ __device__ __forceinline__ float l1_input(const uint16_t* ref, const uint16_t* c
 // ---------------------------------------------------------------------------
 // forward
 // ---------------------------------------------------------------------------
-
-// Layer 1 from the frames: one thread = 2 horizontally adjacent output pixels x 32 channels.
-__global__ void __launch_bounds__(128) l1_fwd_kernel(CnnFrames fr, const __nv_bfloat16* __restrict__ w,
-                                                     __nv_bfloat16* __restrict__ out, int Ho, int Wo) {
-  __shared__ __align__(16) float ws[72 * kC];  // [ci*9 + tap][co]
-  __shared__ float bs[kC];
-  for (int i = threadIdx.x; i < 72 * kC; i += blockDim.x) {
-    const int k = i / kC, co = i - k * kC;
-    ws[i] = bf(w[co * 72 + k]);
-  }
-  if (threadIdx.x < kC) bs[threadIdx.x] = bf(w[BAYER_CNN_B1 - BAYER_CNN_W1 + threadIdx.x]);
-  __syncthreads();
-  const int b = blockIdx.z, oy = blockIdx.y;
-  const int ox0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-  if (ox0 >= Wo) return;
-  const uint16_t* ref = fr.ref + (long long)b * fr.ref_bs;
-  const uint16_t* cur = fr.cur + (long long)b * fr.cur_bs;
-  const int Hh = fr.H / 2, Wh = fr.W / 2;
-  float acc[2][kC];
-#pragma unroll
-  for (int co = 0; co < kC; ++co) acc[0][co] = acc[1][co] = bs[co];
-  for (int ci = 0; ci < 8; ++ci) {
-#pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-      const int ky = tap / 3, kx = tap - 3 * (tap / 3);
-      const int hy = 2 * oy + ky - 1;
-      const float x0 = l1_input(ref, cur, fr.pitch, Hh, Wh, ci, hy, 2 * ox0 + kx - 1);
-      const float x1 = ox0 + 1 < Wo ? l1_input(ref, cur, fr.pitch, Hh, Wh, ci, hy, 2 * ox0 + 2 + kx - 1) : 0.f;
-      const float4* wr = reinterpret_cast<const float4*>(ws + (ci * 9 + tap) * kC);
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const float4 wv = wr[q];
-        acc[0][4 * q + 0] = fmaf(x0, wv.x, acc[0][4 * q + 0]);
-        acc[0][4 * q + 1] = fmaf(x0, wv.y, acc[0][4 * q + 1]);
-        acc[0][4 * q + 2] = fmaf(x0, wv.z, acc[0][4 * q + 2]);
-        acc[0][4 * q + 3] = fmaf(x0, wv.w, acc[0][4 * q + 3]);
-        acc[1][4 * q + 0] = fmaf(x1, wv.x, acc[1][4 * q + 0]);
-        acc[1][4 * q + 1] = fmaf(x1, wv.y, acc[1][4 * q + 1]);
-        acc[1][4 * q + 2] = fmaf(x1, wv.z, acc[1][4 * q + 2]);
-        acc[1][4 * q + 3] = fmaf(x1, wv.w, acc[1][4 * q + 3]);
-      }
-    }
-  }
-#pragma unroll
-  for (int p = 0; p < 2; ++p) {
-    if (ox0 + p >= Wo) break;
-    uint4* dst = reinterpret_cast<uint4*>(out + (((long long)b * Ho + oy) * Wo + ox0 + p) * kC);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float* a = acc[p] + 8 * q;
-      dst[q] = make_uint4(pack2(fmaxf(a[0], 0.f), fmaxf(a[1], 0.f)), pack2(fmaxf(a[2], 0.f), fmaxf(a[3], 0.f)),
-                          pack2(fmaxf(a[4], 0.f), fmaxf(a[5], 0.f)), pack2(fmaxf(a[6], 0.f), fmaxf(a[7], 0.f)));
-    }
-  }
-}
-
-// Layers 2..4: NHWC bf16 in (32 channels), 2 output pixels x 32 channels per thread.
-__global__ void __launch_bounds__(128) conv_fwd_kernel(const __nv_bfloat16* __restrict__ in, int Hi, int Wi,
-                                                       const __nv_bfloat16* __restrict__ w,
-                                                       const __nv_bfloat16* __restrict__ bias,
-                                                       __nv_bfloat16* __restrict__ out, int Ho, int Wo) {
-  __shared__ __align__(16) float ws[288 * kC];  // [tap*32 + ci][co]
-  __shared__ float bs[kC];
-  for (int i = threadIdx.x; i < 288 * kC; i += blockDim.x) {
-    const int k = i / kC, co = i - k * kC;
-    const int tap = k / kC, ci = k - tap * kC;
-    ws[i] = bf(w[co * 288 + ci * 9 + tap]);
-  }
-  if (threadIdx.x < kC) bs[threadIdx.x] = bf(bias[threadIdx.x]);
-  __syncthreads();
-  const int b = blockIdx.z, oy = blockIdx.y;
-  const int ox0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-  if (ox0 >= Wo) return;
-  const __nv_bfloat16* inb = in + (long long)b * Hi * Wi * kC;
-  float acc[2][kC];
-#pragma unroll
-  for (int co = 0; co < kC; ++co) acc[0][co] = acc[1][co] = bs[co];
-#pragma unroll 1
-  for (int tap = 0; tap < 9; ++tap) {
-    const int ky = tap / 3, kx = tap - 3 * (tap / 3);
-    const int iy = 2 * oy + ky - 1;
-    const int ix0 = 2 * ox0 + kx - 1, ix1 = ix0 + 2;
-    const bool r_ok = iy >= 0 && iy < Hi;
-    const bool ok0 = r_ok && ix0 >= 0 && ix0 < Wi;
-    const bool ok1 = r_ok && ox0 + 1 < Wo && ix1 >= 0 && ix1 < Wi;
-    const uint4* p0 = reinterpret_cast<const uint4*>(inb + ((long long)iy * Wi + ix0) * kC);
-    const uint4* p1 = reinterpret_cast<const uint4*>(inb + ((long long)iy * Wi + ix1) * kC);
-#pragma unroll
-    for (int c8 = 0; c8 < 4; ++c8) {
-      float x0[8], x1[8];
-      const uint4 z4 = make_uint4(0, 0, 0, 0);
-      unpack8(ok0 ? __ldg(p0 + c8) : z4, x0);
-      unpack8(ok1 ? __ldg(p1 + c8) : z4, x1);
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        const float4* wr = reinterpret_cast<const float4*>(ws + (tap * kC + c8 * 8 + c) * kC);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const float4 wv = wr[q];
-          acc[0][4 * q + 0] = fmaf(x0[c], wv.x, acc[0][4 * q + 0]);
-          acc[0][4 * q + 1] = fmaf(x0[c], wv.y, acc[0][4 * q + 1]);
-          acc[0][4 * q + 2] = fmaf(x0[c], wv.z, acc[0][4 * q + 2]);
-          acc[0][4 * q + 3] = fmaf(x0[c], wv.w, acc[0][4 * q + 3]);
-          acc[1][4 * q + 0] = fmaf(x1[c], wv.x, acc[1][4 * q + 0]);
-          acc[1][4 * q + 1] = fmaf(x1[c], wv.y, acc[1][4 * q + 1]);
-          acc[1][4 * q + 2] = fmaf(x1[c], wv.z, acc[1][4 * q + 2]);
-          acc[1][4 * q + 3] = fmaf(x1[c], wv.w, acc[1][4 * q + 3]);
-        }
-      }
-    }
-  }
-#pragma unroll
-  for (int p = 0; p < 2; ++p) {
-    if (ox0 + p >= Wo) break;
-    uint4* dst = reinterpret_cast<uint4*>(out + (((long long)b * Ho + oy) * Wo + ox0 + p) * kC);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float* a = acc[p] + 8 * q;
-      dst[q] = make_uint4(pack2(fmaxf(a[0], 0.f), fmaxf(a[1], 0.f)), pack2(fmaxf(a[2], 0.f), fmaxf(a[3], 0.f)),
-                          pack2(fmaxf(a[4], 0.f), fmaxf(a[5], 0.f)), pack2(fmaxf(a[6], 0.f), fmaxf(a[7], 0.f)));
-    }
-  }
-}
 
 // Head: one thread per L4 cell -> 4 blocks' (dx, dy, conf).
 __global__ void __launch_bounds__(128) head_fwd_kernel(const __nv_bfloat16* __restrict__ x4, int H4, int W4,
@@ -477,29 +355,37 @@ size_t cnn_grad_bytes(int W, int H, int batch) {
   return n * batch * sizeof(float);
 }
 
-cudaError_t cnn_forward_acts(const CnnFrames& fr, int batch, const uint16_t* wbf16, void* acts, cudaStream_t st) {
+cudaError_t cnn_forward_acts(const CnnFrames& fr, int batch, const uint16_t* wbf16, void* acts, int* status,
+                             cudaStream_t st) {
   const CnnShapes s = cnn_shapes(fr.W, fr.H);
   const __nv_bfloat16* w = reinterpret_cast<const __nv_bfloat16*>(wbf16);
   __nv_bfloat16* a[5];
   a[1] = static_cast<__nv_bfloat16*>(acts);
   for (int l = 2; l <= 4; ++l) a[l] = a[l - 1] + (size_t)batch * s.H[l - 1] * s.W[l - 1] * kC;
-  {
-    dim3 g((s.W[1] / 2 + 127) / 128 + 1, s.H[1], batch);
-    l1_fwd_kernel<<<g, 128, 0, st>>>(fr, w + BAYER_CNN_W1, a[1], s.H[1], s.W[1]);
-  }
   const int woff[5] = {0, BAYER_CNN_W1, BAYER_CNN_W2, BAYER_CNN_W3, BAYER_CNN_W4};
   const int boff[5] = {0, BAYER_CNN_B1, BAYER_CNN_B2, BAYER_CNN_B3, BAYER_CNN_B4};
-  for (int l = 2; l <= 4; ++l) {
-    dim3 g((s.W[l] / 2 + 127) / 128 + 1, s.H[l], batch);
-    conv_fwd_kernel<<<g, 128, 0, st>>>(a[l - 1], s.H[l - 1], s.W[l - 1], w + woff[l], w + boff[l], a[l], s.H[l],
-                                       s.W[l]);
+  for (int l = 1; l <= 4; ++l) {
+    ConvTcArgs c{};
+    c.in = l == 1 ? nullptr : a[l - 1];
+    c.fr = fr;
+    c.Hi = s.H[l - 1];
+    c.Wi = s.W[l - 1];
+    c.w = w + woff[l];
+    c.bias = w + boff[l];
+    c.out = a[l];
+    c.Ho = s.H[l];
+    c.Wo = s.W[l];
+    c.batch = batch;
+    c.status = status;
+    cudaError_t e = launch_conv_tc(c, l == 1 ? 16 : 32, 32, 2, l == 1 ? 1 : 0, true, st);
+    if (e != cudaSuccess) return e;
   }
-  return cudaGetLastError();
+  return cudaSuccess;
 }
 
 cudaError_t cnn_forward(const CnnFrames& fr, int batch, const uint16_t* wbf16, int range, void* acts, float* prop,
-                        float* conf, cudaStream_t st) {
-  cudaError_t e = cnn_forward_acts(fr, batch, wbf16, acts, st);
+                        float* conf, int* status, cudaStream_t st) {
+  cudaError_t e = cnn_forward_acts(fr, batch, wbf16, acts, status, st);
   if (e != cudaSuccess) return e;
   const CnnShapes s = cnn_shapes(fr.W, fr.H);
   const __nv_bfloat16* a4 = static_cast<const __nv_bfloat16*>(acts);
@@ -511,9 +397,10 @@ cudaError_t cnn_forward(const CnnFrames& fr, int batch, const uint16_t* wbf16, i
 }
 
 cudaError_t cnn_loss_grad(const CnnFrames& fr, int batch, const uint16_t* wbf16, const bayer_mv_t* labels, int range,
-                          float neg_weight, void* acts, void* dpre, float* grad, float* loss, cudaStream_t st) {
+                          float neg_weight, void* acts, void* dpre, float* grad, float* loss, int* status,
+                          cudaStream_t st) {
   const CnnShapes s = cnn_shapes(fr.W, fr.H);
-  cudaError_t e = cnn_forward_acts(fr, batch, wbf16, acts, st);
+  cudaError_t e = cnn_forward_acts(fr, batch, wbf16, acts, status, st);
   if (e != cudaSuccess) return e;
   const __nv_bfloat16* w = reinterpret_cast<const __nv_bfloat16*>(wbf16);
   const __nv_bfloat16* a[5];

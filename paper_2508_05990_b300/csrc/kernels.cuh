@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "../../include/bayer_me.h"
@@ -66,9 +67,25 @@ CnnShapes cnn_shapes(int W, int H);
 size_t cnn_act_bytes(int W, int H, int batch);   // bf16 activations of layers 1..4
 size_t cnn_grad_bytes(int W, int H, int batch);  // fp32 pre-activation gradients of layers 1..4
 cudaError_t cnn_forward(const CnnFrames& fr, int batch, const uint16_t* wbf16, int range, void* acts, float* prop,
-                        float* conf, cudaStream_t st);
+                        float* conf, int* status, cudaStream_t st);
 cudaError_t cnn_loss_grad(const CnnFrames& fr, int batch, const uint16_t* wbf16, const bayer_mv_t* labels, int range,
-                          float neg_weight, void* acts, void* dpre, float* grad, float* loss, cudaStream_t st);
+                          float neg_weight, void* acts, void* dpre, float* grad, float* loss, int* status,
+                          cudaStream_t st);
+
+// 3x3 convolution on the tensor cores (conv_tc.cu): NHWC bf16 in (or, src 1,
+// the Bayer frames of layer 1), NHWC bf16 out, bias + optional ReLU.
+struct ConvTcArgs {
+  const __nv_bfloat16* in;  // src 0: [batch][Hi][Wi][cin]
+  CnnFrames fr;             // src 1: frames; Hi, Wi are the half-resolution dims
+  int Hi, Wi;
+  const __nv_bfloat16* w;     // [cout][cin_w][3][3] (cin_w = cin, or 8 for src 1)
+  const __nv_bfloat16* bias;  // [cout]
+  __nv_bfloat16* out;         // [batch][Ho][Wo][cout]
+  int Ho, Wo, batch;
+  int* status;  // device status word: BAYER_ERR_TIMEOUT if a bounded wait expired
+};
+cudaError_t configure_conv_tc();
+cudaError_t launch_conv_tc(const ConvTcArgs& a, int cin, int cout, int stride, int src, bool relu, cudaStream_t st);
 cudaError_t cnn_adamw(float* w, uint16_t* wbf16, const float* g, float* m, float* v, int n, int step, float lr,
                       float b1, float b2, float eps, float wd, cudaStream_t st);
 
@@ -88,6 +105,7 @@ struct Seeded16Args {
   uint8_t* fallback;  // optional
   int* list;          // [batch*h*w] global block indices needing the full search
   int* count;         // number of entries in list (zeroed by the caller)
+  bool vec2;          // set by launch_seeded16: 32-bit sample-pair loads allowed
 };
 cudaError_t launch_seeded16(const Seeded16Args& a, cudaStream_t st);
 cudaError_t launch_full16_list(const uint16_t* ref, const uint16_t* cur, int W, int H, int pitch, long long ref_bs,

@@ -290,23 +290,38 @@ __global__ void __launch_bounds__(kLW * 32) me_full16_list_kernel(const uint16_t
     const int x0 = bx * 16, y0 = by * 16;
     __syncwarp();  // the previous block's reads are done
     if (vec_ok) {
-      constexpr int WCH = C::WIN_W / 8, NW = WCH * C::WIN_H;
-      for (int e = lane; e < NW + 32; e += 32) {
-        uint4 raw = make_uint4(0, 0, 0, 0);
-        uint32_t* dst;
-        if (e < NW) {
-          const int ry = e / WCH, cx = e - ry * WCH;
-          const int gy = y0 - C::REACH + ry, gx = x0 - C::REACH + 8 * cx;
-          if (gy >= 0 && gy < H && gx >= 0 && gx < W)
-            raw = __ldg(reinterpret_cast<const uint4*>(ref + (long long)gy * pitch + gx));
-          dst = win + ry * C::P + 8 * cx;
-        } else {
-          const int f = e - NW, ry = f >> 1, cx = f & 1;
-          raw = __ldg(reinterpret_cast<const uint4*>(cur + (long long)(y0 + ry) * pitch + x0 + 8 * cx));
-          dst = curt + ry * C::PC + 8 * cx;
+      constexpr int WCH = C::WIN_W / 8, NW = WCH * C::WIN_H, NT = NW + 32, BATCH = 8;
+      for (int e0 = 0; e0 < NT; e0 += 32 * BATCH) {
+        uint4 raw[BATCH];
+#pragma unroll
+        for (int j = 0; j < BATCH; ++j) {
+          const int e = e0 + lane + 32 * j;
+          raw[j] = make_uint4(0, 0, 0, 0);
+          if (e < NW) {
+            const int ry = e / WCH, cx = e - ry * WCH;
+            const int gy = y0 - C::REACH + ry, gx = x0 - C::REACH + 8 * cx;
+            if (gy >= 0 && gy < H && gx >= 0 && gx < W)
+              raw[j] = __ldg(reinterpret_cast<const uint4*>(ref + (long long)gy * pitch + gx));
+          } else if (e < NT) {
+            const int f = e - NW, ry = f >> 1, cx = f & 1;
+            raw[j] = __ldg(reinterpret_cast<const uint4*>(cur + (long long)(y0 + ry) * pitch + x0 + 8 * cx));
+          }
         }
-        reinterpret_cast<uint4*>(dst)[0] = make_uint4(pix_lo(raw.x), pix_hi(raw.x), pix_lo(raw.y), pix_hi(raw.y));
-        reinterpret_cast<uint4*>(dst)[1] = make_uint4(pix_lo(raw.z), pix_hi(raw.z), pix_lo(raw.w), pix_hi(raw.w));
+#pragma unroll
+        for (int j = 0; j < BATCH; ++j) {
+          const int e = e0 + lane + 32 * j;
+          if (e >= NT) continue;
+          uint32_t* dst;
+          if (e < NW) {
+            const int ry = e / WCH, cx = e - ry * WCH;
+            dst = win + ry * C::P + 8 * cx;
+          } else {
+            const int f = e - NW;
+            dst = curt + (f >> 1) * C::PC + 8 * (f & 1);
+          }
+          reinterpret_cast<uint4*>(dst)[0] = make_uint4(pix_lo(raw[j].x), pix_hi(raw[j].x), pix_lo(raw[j].y), pix_hi(raw[j].y));
+          reinterpret_cast<uint4*>(dst)[1] = make_uint4(pix_lo(raw[j].z), pix_hi(raw[j].z), pix_lo(raw[j].w), pix_hi(raw[j].w));
+        }
       }
     } else {
       for (int e = lane; e < C::WIN_H * C::WIN_W; e += 32) {

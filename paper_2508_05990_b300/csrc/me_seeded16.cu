@@ -15,7 +15,7 @@ namespace bme {
 
 namespace {
 
-constexpr int kSW = 4;     // warps per CTA
+constexpr int kSW = 8;     // warps per CTA
 constexpr int kWin = 24;   // window side (16 + 2 * 4)
 constexpr int kWP = 24;    // window pitch (words)
 
@@ -51,14 +51,45 @@ __global__ void __launch_bounds__(kSW * 32) seeded16_kernel(const Seeded16Args a
   uint32_t* win = win_all[warp];
   uint32_t* cb = cur_all[warp];
   const int wx0 = x0 + cx - 4, wy0 = y0 + cy - 4;
-  for (int e = lane; e < kWin * kWin; e += 32) {
-    const int ry = e / kWin, rx = e - ry * kWin;
-    const int gy = wy0 + ry, gx = wx0 + rx;
-    uint32_t v = 0;
-    if (gy >= 0 && gy < a.H && gx >= 0 && gx < a.W) v = __ldg(ref + (long long)gy * a.pitch + gx);
-    win[ry * kWP + rx] = pix_word(v);
+  if (a.vec2) {
+    // pairs of samples: the window starts at an even column (even centre, block
+    // origin a multiple of 16) and W is even, so a pair is wholly in or out
+    uint32_t rw[9], rc[4];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const int e = lane + 32 * i, ry = e / 12, px = e - ry * 12;
+      const int gy = wy0 + ry, gx = wx0 + 2 * px;
+      rw[i] = (gy >= 0 && gy < a.H && gx >= 0 && gx < a.W)
+                  ? __ldg(reinterpret_cast<const uint32_t*>(ref + (long long)gy * a.pitch + gx)) : 0u;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int e = lane + 32 * i;
+      rc[i] = __ldg(reinterpret_cast<const uint32_t*>(cur + (long long)(y0 + (e >> 3)) * a.pitch + x0 + 2 * (e & 7)));
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const int e = lane + 32 * i, ry = e / 12, px = e - ry * 12;
+      win[ry * kWP + 2 * px] = pix_lo(rw[i]);
+      win[ry * kWP + 2 * px + 1] = pix_hi(rw[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int e = lane + 32 * i;
+      cb[(e >> 3) * 16 + 2 * (e & 7)] = pix_lo(rc[i]);
+      cb[(e >> 3) * 16 + 2 * (e & 7) + 1] = pix_hi(rc[i]);
+    }
+  } else {
+    for (int e = lane; e < kWin * kWin; e += 32) {
+      const int ry = e / kWin, rx = e - ry * kWin;
+      const int gy = wy0 + ry, gx = wx0 + rx;
+      uint32_t v = 0;
+      if (gy >= 0 && gy < a.H && gx >= 0 && gx < a.W) v = __ldg(ref + (long long)gy * a.pitch + gx);
+      win[ry * kWP + rx] = pix_word(v);
+    }
+    for (int e = lane; e < 256; e += 32)
+      cb[e] = pix_word(__ldg(cur + (long long)(y0 + (e >> 4)) * a.pitch + x0 + (e & 15)));
   }
-  for (int e = lane; e < 256; e += 32) cb[e] = pix_word(__ldg(cur + (long long)(y0 + (e >> 4)) * a.pitch + x0 + (e & 15)));
   __syncwarp();
 
   uint64_t key = kInvalidKey;
@@ -96,7 +127,10 @@ __global__ void __launch_bounds__(kSW * 32) seeded16_kernel(const Seeded16Args a
 
 }  // namespace
 
-cudaError_t launch_seeded16(const Seeded16Args& a, cudaStream_t st) {
+cudaError_t launch_seeded16(const Seeded16Args& in, cudaStream_t st) {
+  Seeded16Args a = in;
+  a.vec2 = (reinterpret_cast<uintptr_t>(a.ref) % 4) == 0 && (reinterpret_cast<uintptr_t>(a.cur) % 4) == 0 &&
+           a.pitch % 2 == 0 && a.ref_bs % 2 == 0 && a.cur_bs % 2 == 0;
   const long long nblk = (long long)a.batch * a.h * a.w;
   seeded16_kernel<<<(unsigned)((nblk + kSW - 1) / kSW), kSW * 32, 0, st>>>(a);
   return cudaGetLastError();
