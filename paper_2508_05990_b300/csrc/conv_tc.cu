@@ -5,16 +5,16 @@
 //   D[m, n] = sum_k A[m, k] * B[k, n],  m = output pixel, n = output channel,
 //   k = tap * CIN + ci,  A[m, k] = input at (S*oy + ky - 1, S*ox + kx - 1, ci).
 //
-// CTA = 128 threads = 128 output pixels (MMA M = 128, N = COUT); persistent
-// over pixel tiles.  All nine taps' weights stay in shared memory.  Per tile
-// each thread gathers its pixel's 9 x CIN input values into the A tile
-// (canonical no-swizzle K-major layout: 8-row x 16-byte core matrices), three
-// taps' loads in flight at a time; after one barrier thread 0 issues the
-// 9*CIN/16 MMAs (K = 16 each) and commits them to an mbarrier that gates the
-// epilogue (TMEM -> registers -> bias, ReLU, bf16 -> global).  Several CTAs
-// per SM overlap one tile's gather with another's MMAs and epilogue.  Every
-// mbarrier wait is bounded; on expiry the kernel records BAYER_ERR_TIMEOUT in
-// the status word, frees its TMEM and finishes.
+// Tile = 128 consecutive output pixels of one output row (MMA M = 128,
+// N = COUT); CTA = 128 threads, persistent over tiles, all nine taps' weights
+// resident in shared memory.  Per tile the CTA stages the three input rows
+// once (coalesced 16-byte loads; no im2col copy), after one barrier thread 0
+// issues 9 * CIN/16 MMAs whose A operands are shifted views of the staged rows
+// and commits them to an mbarrier that gates the epilogue (TMEM -> registers
+// -> bias, ReLU, bf16 -> global).  Several CTAs per SM overlap one tile's
+// staging with another's MMAs and epilogue.  Every mbarrier wait is bounded;
+// on expiry the kernel records BAYER_ERR_TIMEOUT in the status word, frees its
+// TMEM and finishes.
 //
 // SRC 1 (layer 1 of the proposal network) gathers straight from the Bayer
 // frames: the 8 half-resolution planes x = v/2048 - 1 are split exactly into
@@ -30,17 +30,27 @@ namespace bme {
 
 namespace {
 
-constexpr int kM = 128;
+constexpr int kM = 128;  // output pixels per tile (MMA M)
 constexpr uint32_t kWaitLimit = 1u << 20;
 
-template <int CIN, int COUT>
-struct ConvTcLayout {
-  static constexpr int KC = CIN / 8;            // 16-byte K chunks per tap
-  static constexpr int A_BYTES = kM * 9 * CIN * 2;  // all nine taps of one tile
+// Shared-memory plan of one CTA.  The three input rows a tile needs are staged
+// once, split into S column-parity planes (S = stride) and into 16-byte
+// channel chunks: element (row rho, plane q, chunk kc, pixel p) at
+// (((rho*S + q)*KC + kc)*NP + p)*16.  Output pixel m of tap (ky, kx) then reads
+// plane q = kx % S at pixel m + kx / S, so every tap's A operand is the staged
+// tensor itself at a shifted start address: core matrices of 8 consecutive
+// pixels (SBO = 128 bytes), the next K chunk one plane further (LBO = NP*16).
+template <int CIN, int COUT, int S>
+struct RowConvLayout {
+  static constexpr int KC = CIN / 8;
+  static constexpr int NJ = S * (kM - 1) + 3;       // staged input columns
+  static constexpr int NP = (NJ + S - 1) / S;       // pixels per parity plane
+  static constexpr int STAGE_BYTES = 3 * S * KC * NP * 16;
   static constexpr int B_BYTES = 9 * CIN * COUT * 2;
   static constexpr int TMEM_COLS = COUT < 32 ? 32 : COUT;
-  static constexpr int SMEM = B_BYTES + A_BYTES + 64;
+  static constexpr int SMEM = B_BYTES + STAGE_BYTES + 64;
   static_assert(CIN % 16 == 0 && COUT % 32 == 0 && COUT <= 256, "shape");
+  static_assert(B_BYTES % 128 == 0 && STAGE_BYTES % 16 == 0, "alignment");
 };
 
 __device__ __forceinline__ uint32_t bf2(float a, float b) {
@@ -48,14 +58,19 @@ __device__ __forceinline__ uint32_t bf2(float a, float b) {
   return *reinterpret_cast<const uint32_t*>(&v);
 }
 
-template <int CIN, int COUT, int STRIDE, int SRC, bool RELU>
+// hi/lo bf16 pair of a 12-bit sample (SRC 1): hi = (v >> 4)/128 - 1, lo = (v & 15)/16.
+__device__ __forceinline__ uint32_t split12(uint32_t v) {
+  return bf2((float)(v >> 4) * (1.0f / 128.0f) - 1.0f, (float)(v & 15u) * (1.0f / 16.0f));
+}
+
+template <int CIN, int COUT, int S, int SRC, bool RELU>
 __global__ void __launch_bounds__(kM) conv3x3_tc_kernel(const ConvTcArgs a) {
-  using L = ConvTcLayout<CIN, COUT>;
+  using L = RowConvLayout<CIN, COUT, S>;
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sB = smem;
-  uint8_t* sA = smem + L::B_BYTES;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L::B_BYTES + L::A_BYTES);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 2);
+  uint8_t* sX = smem + L::B_BYTES;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L::B_BYTES + L::STAGE_BYTES);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
   const int tid = threadIdx.x, warp = tid >> 5;
 
   if (tid == 0) {
@@ -82,73 +97,74 @@ __global__ void __launch_bounds__(kM) conv3x3_tc_kernel(const ConvTcArgs a) {
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t sA_addr = tc::smem_addr(sA), sB_addr = tc::smem_addr(sB);
+  const uint32_t sX_addr = tc::smem_addr(sX), sB_addr = tc::smem_addr(sB);
   constexpr uint32_t idesc = tc::idesc_bf16_f32(kM, COUT);
-  constexpr int KCA = 9 * L::KC;  // K chunks of the full A tile
-  const long long npix = (long long)a.batch * a.Ho * a.Wo;
-  const long long ntiles = (npix + kM - 1) / kM;
+  const int segs = (a.Wo + kM - 1) / kM;
+  const long long ntiles = (long long)a.batch * a.Ho * segs;
   uint32_t phase = 0;
   bool ok = true;
-  // A tile (K-major, k = tap*CIN + ci): row m, chunk kc at (m/8)*KCA*128 + kc*128 + (m%8)*16
-  uint8_t* arow = sA + (tid >> 3) * (KCA * 128) + (tid & 7) * 16;
 
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const long long pix = tile * kM + tid;
-    const bool valid = pix < npix;
-    int b = 0, oy = 0, ox = 0;
-    if (valid) {
-      b = (int)(pix / ((long long)a.Ho * a.Wo));
-      const int r = (int)(pix - (long long)b * a.Ho * a.Wo);
-      oy = r / a.Wo;
-      ox = r - oy * a.Wo;
-    }
-    // gather the nine taps, three at a time (all loads of a group in flight together)
-#pragma unroll
-    for (int g = 0; g < 3; ++g) {
+    const int seg = (int)(tile % segs);
+    const long long row = tile / segs;
+    const int b = (int)(row / a.Ho), oy = (int)(row - (long long)b * a.Ho);
+    const int ox0 = seg * kM;
+    const int c0 = S * ox0 - 1;  // input column of staged column 0
+
+    // ---- stage rows S*oy - 1 .. S*oy + 1, columns c0 .. c0 + NJ - 1
+    constexpr int NITEM = 3 * L::NJ;
+    for (int it0 = 0; it0 < NITEM; it0 += 2 * kM) {
       if (SRC == 0) {
-        uint4 v[3][L::KC];
+        uint4 v[2][L::KC];
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          const int tap = 3 * g + j, ky = tap / 3, kx = tap % 3;
-          const int iy = STRIDE * oy + ky - 1, ix = STRIDE * ox + kx - 1;
-          const bool in_ok = valid && iy >= 0 && iy < a.Hi && ix >= 0 && ix < a.Wi;
+        for (int u = 0; u < 2; ++u) {
+          const int it = it0 + u * kM + tid;
+          const int rho = it / L::NJ, j = it - rho * L::NJ;
+          const int iy = S * oy - 1 + rho, ix = c0 + j;
+          const bool in_ok = it < NITEM && iy >= 0 && iy < a.Hi && ix >= 0 && ix < a.Wi;
           const uint4* src = reinterpret_cast<const uint4*>(a.in + (((long long)b * a.Hi + iy) * a.Wi + ix) * CIN);
 #pragma unroll
-          for (int kc = 0; kc < L::KC; ++kc) v[j][kc] = in_ok ? __ldg(src + kc) : make_uint4(0, 0, 0, 0);
+          for (int kc = 0; kc < L::KC; ++kc) v[u][kc] = in_ok ? __ldg(src + kc) : make_uint4(0, 0, 0, 0);
         }
 #pragma unroll
-        for (int j = 0; j < 3; ++j)
+        for (int u = 0; u < 2; ++u) {
+          const int it = it0 + u * kM + tid;
+          if (it >= NITEM) continue;
+          const int rho = it / L::NJ, j = it - rho * L::NJ;
+          const int q = j % S, pp = j / S;
 #pragma unroll
           for (int kc = 0; kc < L::KC; ++kc)
-            *reinterpret_cast<uint4*>(arow + ((3 * g + j) * L::KC + kc) * 128) = v[j][kc];
+            *reinterpret_cast<uint4*>(sX + (((rho * S + q) * L::KC + kc) * L::NP + pp) * 16) = v[u][kc];
+        }
       } else {
-        uint32_t raw[3][8];
+        uint32_t raw[2][8];
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          const int tap = 3 * g + j, ky = tap / 3, kx = tap % 3;
-          const int iy = 2 * oy + ky - 1, ix = 2 * ox + kx - 1;
-          const bool in_ok = valid && iy >= 0 && iy < a.Hi && ix >= 0 && ix < a.Wi;
+        for (int u = 0; u < 2; ++u) {
+          const int it = it0 + u * kM + tid;
+          const int rho = it / L::NJ, j = it - rho * L::NJ;
+          const int iy = S * oy - 1 + rho, ix = c0 + j;
+          const bool in_ok = it < NITEM && iy >= 0 && iy < a.Hi && ix >= 0 && ix < a.Wi;
 #pragma unroll
           for (int c = 0; c < 8; ++c) {
             const uint16_t* f = (c < 4 ? a.fr.ref + (long long)b * a.fr.ref_bs : a.fr.cur + (long long)b * a.fr.cur_bs);
-            const int p = c & 3;
-            raw[j][c] = in_ok ? (uint32_t)__ldg(f + (long long)(2 * iy + (p >> 1)) * a.fr.pitch + 2 * ix + (p & 1))
-                              : 0xFFFFFFFFu;  // marks zero padding
+            const int pl = c & 3;
+            raw[u][c] = in_ok ? (uint32_t)__ldg(f + (long long)(2 * iy + (pl >> 1)) * a.fr.pitch + 2 * ix + (pl & 1))
+                              : 0xFFFFFFFFu;
           }
         }
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
+        for (int u = 0; u < 2; ++u) {
+          const int it = it0 + u * kM + tid;
+          if (it >= NITEM) continue;
+          const int rho = it / L::NJ, j = it - rho * L::NJ;
+          const int q = j % S, pp = j / S;
           uint32_t wd[8];
 #pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            const uint32_t v = raw[j][c];
-            const float hi = v == 0xFFFFFFFFu ? 0.f : (float)(v >> 4) * (1.0f / 128.0f) - 1.0f;
-            const float lo = v == 0xFFFFFFFFu ? 0.f : (float)(v & 15u) * (1.0f / 16.0f);
-            wd[c] = bf2(hi, lo);
-          }
-          const int tap = 3 * g + j;
-          *reinterpret_cast<uint4*>(arow + (tap * 2) * 128) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
-          *reinterpret_cast<uint4*>(arow + (tap * 2 + 1) * 128) = make_uint4(wd[4], wd[5], wd[6], wd[7]);
+          for (int c = 0; c < 8; ++c) wd[c] = raw[u][c] == 0xFFFFFFFFu ? 0u : split12(raw[u][c]);
+          *reinterpret_cast<uint4*>(sX + (((rho * S + q) * L::KC + 0) * L::NP + pp) * 16) =
+              make_uint4(wd[0], wd[1], wd[2], wd[3]);
+          *reinterpret_cast<uint4*>(sX + (((rho * S + q) * L::KC + 1) * L::NP + pp) * 16) =
+              make_uint4(wd[4], wd[5], wd[6], wd[7]);
         }
       }
     }
@@ -157,57 +173,62 @@ __global__ void __launch_bounds__(kM) conv3x3_tc_kernel(const ConvTcArgs a) {
     if (tid == 0) {
       tc::fence_after_sync();
 #pragma unroll
-      for (int s = 0; s < 9 * CIN / 16; ++s) {
-        const uint64_t ad = tc::smem_desc(sA_addr + 2 * s * 128, 128, KCA * 128);
-        const uint64_t bd = tc::smem_desc(sB_addr + 2 * s * 128, 128, KCA * 128);
-        tc::mma_bf16(tmem, ad, bd, idesc, s > 0 ? 1u : 0u);
+      for (int tap = 0; tap < 9; ++tap) {
+        const int ky = tap / 3, kx = tap % 3;
+        const int q = kx % S, dp = kx / S;
+#pragma unroll
+        for (int s2 = 0; s2 < CIN / 16; ++s2) {
+          const uint32_t a_addr = sX_addr + (((ky * S + q) * L::KC + 2 * s2) * L::NP + dp) * 16;
+          const uint64_t ad = tc::smem_desc(a_addr, L::NP * 16, 128);
+          const uint64_t bd = tc::smem_desc(sB_addr + (tap * L::KC + 2 * s2) * 128, 128, 9 * L::KC * 128);
+          tc::mma_bf16(tmem, ad, bd, idesc, (tap > 0 || s2 > 0) ? 1u : 0u);
+        }
       }
       tc::commit(&mbar[0]);
     }
     ok &= tc::mbar_wait(&mbar[0], phase & 1, kWaitLimit);
     ++phase;
     tc::fence_after_sync();
+    const int ox = ox0 + tid;
+    const bool valid = ox < a.Wo;
+    __nv_bfloat16* orow = a.out + (((long long)b * a.Ho + oy) * a.Wo + ox) * COUT;
 #pragma unroll
-    for (int c0 = 0; c0 < COUT; c0 += 32) {
+    for (int cc = 0; cc < COUT; cc += 32) {
       float v[32];
-      tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cc, v);
       if (valid) {
         uint32_t o[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-          float x0 = v[2 * j] + __bfloat162float(a.bias[c0 + 2 * j]);
-          float x1 = v[2 * j + 1] + __bfloat162float(a.bias[c0 + 2 * j + 1]);
+          float x0 = v[2 * j] + __bfloat162float(a.bias[cc + 2 * j]);
+          float x1 = v[2 * j + 1] + __bfloat162float(a.bias[cc + 2 * j + 1]);
           if (RELU) {
             x0 = fmaxf(x0, 0.f);
             x1 = fmaxf(x1, 0.f);
           }
           o[j] = bf2(x0, x1);
         }
-        uint4* dst = reinterpret_cast<uint4*>(a.out + pix * COUT + c0);
+        uint4* dst = reinterpret_cast<uint4*>(orow + cc);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) dst[q] = make_uint4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+        for (int q4 = 0; q4 < 4; ++q4) dst[q4] = make_uint4(o[4 * q4], o[4 * q4 + 1], o[4 * q4 + 2], o[4 * q4 + 3]);
       }
     }
     tc::fence_before_sync();
-    __syncthreads();  // TMEM read and A consumed before the next tile overwrites them
+    __syncthreads();  // TMEM read and staged rows consumed before the next tile
   }
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, L::TMEM_COLS);
   if (!ok && tid == 0 && a.status) atomicExch(a.status, (int)BAYER_ERR_TIMEOUT);
 }
 
-template <int CIN, int COUT, int STRIDE, int SRC, bool RELU>
+template <int CIN, int COUT, int S, int SRC, bool RELU>
 cudaError_t launch_t(const ConvTcArgs& a, cudaStream_t st) {
-  using L = ConvTcLayout<CIN, COUT>;
-  auto kern = conv3x3_tc_kernel<CIN, COUT, STRIDE, SRC, RELU>;
-  int dev = 0, nsm = 148, per_sm = 1;
+  using L = RowConvLayout<CIN, COUT, S>;
+  auto kern = conv3x3_tc_kernel<CIN, COUT, S, SRC, RELU>;
+  int dev = 0, nsm = 148;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kM, L::SMEM);
-  if (e != cudaSuccess) return e;
-  const int tmem_limit = 512 / L::TMEM_COLS;
-  if (per_sm > tmem_limit) per_sm = tmem_limit;
-  if (per_sm < 1) per_sm = 1;
-  const long long ntiles = ((long long)a.batch * a.Ho * a.Wo + kM - 1) / kM;
+  const int per_sm = tc::ctas_per_sm(kern, kM, L::SMEM, L::TMEM_COLS);
+  const long long ntiles = (long long)a.batch * a.Ho * ((a.Wo + kM - 1) / kM);
   long long grid = (long long)nsm * per_sm;
   if (grid > ntiles) grid = ntiles;
   if (grid < 1) return cudaSuccess;
@@ -215,11 +236,15 @@ cudaError_t launch_t(const ConvTcArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <int CIN, int COUT, int STRIDE, int SRC, bool RELU>
+template <int CIN, int COUT, int S, int SRC, bool RELU>
 cudaError_t configure_t() {
-  using L = ConvTcLayout<CIN, COUT>;
-  return cudaFuncSetAttribute(conv3x3_tc_kernel<CIN, COUT, STRIDE, SRC, RELU>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
+  using L = RowConvLayout<CIN, COUT, S>;
+  auto kern = conv3x3_tc_kernel<CIN, COUT, S, SRC, RELU>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
+  // prefer the largest shared-memory carveout so several CTAs fit per SM (the
+  // occupancy query that sizes the persistent grid follows this preference)
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  return e;
 }
 
 }  // namespace

@@ -23,6 +23,7 @@
 //     -- then a 5-step shuffle minimum.
 #include "common.cuh"
 #include "kernels.cuh"
+#include "tc_common.cuh"
 
 namespace bme {
 
@@ -347,8 +348,9 @@ cudaError_t launch_list_r(const uint16_t* ref, const uint16_t* cur, int W, int H
   using C = Full16List<R>;
   int dev = 0, nsm = 148;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int per_sm = tc::ctas_per_sm(me_full16_list_kernel<R>, kLW * 32, (int)C::SMEM, 0);
   int grid = (max_count + kLW - 1) / kLW;
-  if (grid > 2 * nsm) grid = 2 * nsm;
+  if (grid > per_sm * nsm) grid = per_sm * nsm;
   if (grid < 1) grid = 1;
   const bool vec_ok = (reinterpret_cast<uintptr_t>(ref) % 16) == 0 && (reinterpret_cast<uintptr_t>(cur) % 16) == 0 &&
                       pitch % 8 == 0 && ref_bs % 8 == 0 && cur_bs % 8 == 0;
@@ -359,14 +361,20 @@ cudaError_t launch_list_r(const uint16_t* ref, const uint16_t* cur, int W, int H
 
 template <int R>
 cudaError_t configure_list_r() {
-  return cudaFuncSetAttribute(me_full16_list_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)Full16List<R>::SMEM);
+  cudaError_t e = cudaFuncSetAttribute(me_full16_list_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)Full16List<R>::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(me_full16_list_kernel<R>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  return e;
 }
 
 template <int R>
 cudaError_t configure_r() {
-  return cudaFuncSetAttribute(me_full16_even_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)Full16<R>::SMEM);
+  cudaError_t e = cudaFuncSetAttribute(me_full16_even_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)Full16<R>::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(me_full16_even_kernel<R>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  return e;
 }
 
 }  // namespace

@@ -5,8 +5,10 @@
 // rounded to the nearest even integer (half away from zero), clamped to
 // [-range, range] and to the block's valid displacements, and the 25
 // candidates centre + (2u, 2v), u, v in [-2, 2], with |dx|, |dy| <= range and
-// the displaced block inside the frame are evaluated, one per lane, from a
-// 24x24 window and the current block staged in the warp's shared memory.
+// the displaced block inside the frame are evaluated from a 24x24 window and
+// the current block staged in the warp's shared memory: lane (v, g) holds the
+// five candidates of row v over column quarter g (each 128-bit window load
+// feeds five accumulators), and two shuffles sum the quarters.
 // Argmin with the (sad, |dx|+|dy|, dy, dx) key as everywhere else.
 #include "common.cuh"
 #include "kernels.cuh"
@@ -92,30 +94,41 @@ __global__ void __launch_bounds__(kSW * 32) seeded16_kernel(const Seeded16Args a
   }
   __syncwarp();
 
+  // lane = 4 * v + g (v: candidate row, g: column quarter), 20 lanes: each
+  // 128-bit window load (4 samples) feeds the 5 candidates of the row.
   uint64_t key = kInvalidKey;
-  if (lane < 25) {
-    const int u = lane % 5, v = lane / 5;
-    const int dx = cx + 2 * (u - 2), dy = cy + 2 * (v - 2);
-    const bool ok = abs(dx) <= a.range && abs(dy) <= a.range && x0 + dx >= 0 && x0 + dx + 16 <= a.W &&
-                    y0 + dy >= 0 && y0 + dy + 16 <= a.H;
-    if (ok) {
-      uint32_t s = 0;
-      const uint32_t* wr = win + (2 * v) * kWP + 2 * u;
+  const int v = lane >> 2, g = lane & 3;
+  uint32_t acc[5] = {0, 0, 0, 0, 0};
+  if (lane < 20) {
+    const uint32_t* wr = win + (2 * v) * kWP + 4 * g;
+    const uint32_t* cr = cb + 4 * g;
 #pragma unroll 4
-      for (int r = 0; r < 16; ++r) {
-        const uint2* w2 = reinterpret_cast<const uint2*>(wr + r * kWP);
-        const uint4* c4 = reinterpret_cast<const uint4*>(cb + r * 16);
+    for (int r = 0; r < 16; ++r) {
+      const uint4 w0 = *reinterpret_cast<const uint4*>(wr + r * kWP);
+      const uint4 w1 = *reinterpret_cast<const uint4*>(wr + r * kWP + 4);
+      const uint4 w2 = *reinterpret_cast<const uint4*>(wr + r * kWP + 8);
+      const uint4 c4 = *reinterpret_cast<const uint4*>(cr + r * 16);
+      const uint32_t wv[12] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w, w2.x, w2.y, w2.z, w2.w};
+      const uint32_t cv[4] = {c4.x, c4.y, c4.z, c4.w};
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const uint4 cv = c4[q];
-          const uint2 a0 = w2[2 * q], a1 = w2[2 * q + 1];
-          s = sad_u32(a0.x, cv.x, s);
-          s = sad_u32(a0.y, cv.y, s);
-          s = sad_u32(a1.x, cv.z, s);
-          s = sad_u32(a1.y, cv.w, s);
-        }
-      }
-      key = make_key(s, dx, dy);
+      for (int u = 0; u < 5; ++u)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[u] = sad_u32(wv[2 * u + c], cv[c], acc[u]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 5; ++u) {
+    acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], 1);
+    acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], 2);
+  }
+  if (lane < 20 && g == 0) {
+#pragma unroll
+    for (int u = 0; u < 5; ++u) {
+      const int dx = cx + 2 * (u - 2), dy = cy + 2 * (v - 2);
+      const bool ok = abs(dx) <= a.range && abs(dy) <= a.range && x0 + dx >= 0 && x0 + dx + 16 <= a.W &&
+                      y0 + dy >= 0 && y0 + dy + 16 <= a.H;
+      const uint64_t k = ok ? make_key(acc[u], dx, dy) : kInvalidKey;
+      key = k < key ? k : key;
     }
   }
   key = warp_min_u64(key);

@@ -97,5 +97,24 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// CTAs of `kern` that fit on one SM with `threads` threads and `smem` bytes of
+// dynamic shared memory each, also bounded by TMEM columns (512 per SM).
+template <typename K>
+inline int ctas_per_sm(K kern, int threads, int smem, int tmem_cols) {
+  int dev = 0, smem_sm = 0, regs_sm = 0, thr_sm = 0;
+  cudaFuncAttributes fa{};
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return 1;
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+  const int per_cta_smem = smem + (int)fa.sharedSizeBytes + 1024;  // 1 KB reserved per CTA
+  int n = thr_sm / threads;
+  if (per_cta_smem > 0) n = n < smem_sm / per_cta_smem ? n : smem_sm / per_cta_smem;
+  const int regs = ((fa.numRegs + 7) / 8) * 8 * threads;
+  if (regs > 0) n = n < regs_sm / regs ? n : regs_sm / regs;
+  if (tmem_cols > 0) n = n < 512 / tmem_cols ? n : 512 / tmem_cols;
+  return n < 1 ? 1 : n;
+}
+
 }  // namespace tc
 }  // namespace bme
