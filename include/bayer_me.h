@@ -257,6 +257,58 @@ bayer_status_t bayer_me_estimate_learned(bayer_me_t h, const uint16_t* ref, cons
                                          float conf_thresh, bayer_mv_t* mv_out, uint8_t* fallback_out,
                                          int* n_fallback, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Refine convolution of propagated features.  The paper corrects the
+ * propagated features z_pred with a learned residual (Sec. 3.3: z_C = z_pred +
+ * z_Res, PRNet); its dense-convolution core is reduced here to three 3x3
+ * convolutions (stride 1, zero pad 1): C -> hidden (ReLU) -> hidden (ReLU) ->
+ * C (linear), biases added, on NHWC float32 maps.
+ *   precision BAYER_PREC_BF16: inputs, weights and the two hidden activations
+ *     rounded to bfloat16, products accumulated in float32 on the tensor cores
+ *     (tcgen05, accumulators in TMEM); output float32.
+ *   precision BAYER_PREC_FP32: everything in float32 on the SIMT cores.
+ * Supported: C = 128, hidden = 64.  feat, out: device float32
+ * [n][Hf][Wf][C] (must not overlap); w1 [hidden][C][3][3], b1 [hidden],
+ * w2 [hidden][hidden][3][3], b2 [hidden], w3 [C][hidden][3][3], b3 [C]:
+ * device float32.  Hidden activations use the handle's workspace. */
+enum { BAYER_PREC_BF16 = 0, BAYER_PREC_FP32 = 1 };
+bayer_status_t bayer_refine_conv(bayer_me_t h, const float* feat, int n, int Hf, int Wf, int C, int hidden,
+                                 const float* w1, const float* b1, const float* w2, const float* b2, const float* w3,
+                                 const float* b3, int precision, float* out, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Many camera streams at once (not in the paper; its batch dimension, Sec. 4.1
+ * "CUDA Settings", extended to frame pairs of different sizes).  One frame pair
+ * per entry: exhaustive EVEN search (block 16, +-range, range in
+ * {8, 16, 24, 32}; W and H multiples of 16), then, where feat is not NULL,
+ * propagation of that pair's NCHW feature map as in bayer_feat_propagate
+ * (stride divides 16; Hf*stride/16 == H/16 and Wf*stride/16 == W/16).
+ * All searches run in one persistent launch over a work queue of strips of
+ * all pairs, all propagations in a second one; the two are captured as a CUDA
+ * graph and replayed on later calls with the same set of sizes.  The first
+ * call for a set of sizes also runs an autotuner: it times each launch
+ * schedule (blocks per strip 4 or 8; pairs as given or largest first) and
+ * keeps the fastest for that set (the handle's autotune table).
+ *   pairs: HOST array of n descriptors of device buffers (caller-owned).
+ *   end_ns: optional device int64 [n]: per pair, nanoseconds from the start
+ *     of the search launch until that pair's output (propagated features, or
+ *     the MV field without features) was complete.
+ *   schedule: optional host int, receives 10 * blocks per strip + order.
+ * The first call synchronises the device (autotuning); later calls are
+ * asynchronous on `stream`. */
+typedef struct {
+  const uint16_t* ref; /* device frame, H rows of `pitch` elements */
+  const uint16_t* cur;
+  int W, H, pitch;
+  bayer_mv_t* mv_out;  /* device [H/16][W/16] */
+  const float* feat;   /* device NCHW [C][Hf][Wf], or NULL */
+  float* feat_out;     /* device, like feat */
+  int C, Hf, Wf, stride;
+} bayer_pair_t;
+
+bayer_status_t bayer_me_multi_stream(bayer_me_t h, const bayer_pair_t* pairs, int n, int range, int interp,
+                                     long long* end_ns, int* schedule, void* stream);
+
 /* Allocation-free coarse-to-fine search.  The paper has no counterpart: this
  * entry point serves callers that cannot call cudaMalloc -- for example a
  * real-time frame loop, where an allocation can synchronise the device and

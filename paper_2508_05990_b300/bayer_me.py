@@ -34,7 +34,8 @@ MAX_LEVELS = MAX_STAGES = 4
 EXPORTS = ("bayer_me_init", "bayer_me_destroy", "bayer_status_string", "bayer_me_estimate",
            "bayer_me_estimate_ex", "bayer_feat_propagate", "bayer_clip_process_host", "bayer_me_sync_status",
            "bayer_probe_alu", "bayer_me_estimate_c2f_noalloc", "bayer_cnn_forward", "bayer_cnn_loss_grad",
-           "bayer_cnn_adamw", "bayer_me_estimate_learned")
+           "bayer_cnn_adamw", "bayer_me_estimate_learned", "bayer_refine_conv", "bayer_me_multi_stream")
+PREC_BF16, PREC_FP32 = 0, 1
 
 # Flat parameter layout of the proposal network (BAYER_CNN_* in the header).
 CNN_OFFSETS = dict(w1=0, b1=2304, w2=2336, b2=11552, w3=11584, b3=20800, w4=20832, b4=30048, wh=30080, bh=30464)
@@ -47,6 +48,14 @@ class BayerError(RuntimeError):
     def __init__(self, status: int, what: str):
         super().__init__(f"{what}: {status_string(status)} (status {status})")
         self.status = status
+
+
+class PairDesc(ctypes.Structure):
+    """bayer_pair_t: one frame pair (device buffers) of a multi-stream call."""
+    _fields_ = [("ref", ctypes.c_void_p), ("cur", ctypes.c_void_p), ("W", ctypes.c_int), ("H", ctypes.c_int),
+                ("pitch", ctypes.c_int), ("mv_out", ctypes.c_void_p), ("feat", ctypes.c_void_p),
+                ("feat_out", ctypes.c_void_p), ("C", ctypes.c_int), ("Hf", ctypes.c_int), ("Wf", ctypes.c_int),
+                ("stride", ctypes.c_int)]
 
 
 class Params(ctypes.Structure):
@@ -86,6 +95,8 @@ def load(path: str = LIB_PATH):
     lib.bayer_cnn_loss_grad.argtypes = [P, P, P, I, I, I, I, LL, LL, P, P, I, F, P, P, P]
     lib.bayer_cnn_adamw.argtypes = [P, P, P, P, P, P, I, F, F, F, F, F, P]
     lib.bayer_me_estimate_learned.argtypes = [P, P, P, I, I, I, I, LL, LL, P, I, F, P, P, P, P]
+    lib.bayer_refine_conv.argtypes = [P, P, I, I, I, I, I, P, P, P, P, P, P, I, P, P]
+    lib.bayer_me_multi_stream.argtypes = [P, ctypes.POINTER(PairDesc), I, I, I, P, ctypes.POINTER(ctypes.c_int), P]
     for name in EXPORTS:
         if name != "bayer_status_string":
             getattr(lib, name).restype = I
@@ -295,6 +306,39 @@ class Handle:
                                                    _ptr(out), _ptr(fallback), _ptr(n_fallback), _stream(stream)),
                "bayer_me_estimate_learned")
         return out
+
+    def refine_conv(self, feat, weights, precision=PREC_BF16, out=None, stream=None):
+        """Three 3x3 convs C -> hidden -> hidden -> C on NHWC float32 feat [n, Hf, Wf, C];
+        weights = (w1, b1, w2, b2, w3, b3) float32 CUDA tensors."""
+        import torch
+        if feat.dim() == 3:
+            feat = feat.unsqueeze(0)
+        n, Hf, Wf, C = feat.shape
+        hidden = weights[0].shape[0]
+        if out is None:
+            out = torch.empty_like(feat)
+        _check(self._lib.bayer_refine_conv(self._h, _ptr(feat), n, Hf, Wf, C, hidden, *[_ptr(t) for t in weights],
+                                           int(precision), _ptr(out), _stream(stream)), "bayer_refine_conv")
+        return out
+
+    def multi_stream(self, pairs, search_range=32, interp=INTERP_BILINEAR, end_ns=None, stream=None):
+        """pairs: list of dicts with ref, cur (uint16/int16 [H, W] tensors), mv (int32 [H/16, W/16, 2]) and
+        optionally feat, feat_out (float32 [C, Hf, Wf]) and stride.  Returns the schedule the autotuner chose
+        (10 * blocks per strip + order)."""
+        arr = (PairDesc * len(pairs))()
+        for i, q in enumerate(pairs):
+            H, W = q["ref"].shape[-2:]
+            d = arr[i]
+            d.ref, d.cur, d.W, d.H, d.pitch = q["ref"].data_ptr(), q["cur"].data_ptr(), W, H, W
+            d.mv_out = q["mv"].data_ptr()
+            if q.get("feat") is not None:
+                C, Hf, Wf = q["feat"].shape[-3:]
+                d.feat, d.feat_out = q["feat"].data_ptr(), q["feat_out"].data_ptr()
+                d.C, d.Hf, d.Wf, d.stride = C, Hf, Wf, q.get("stride", 8)
+        sched = ctypes.c_int(0)
+        _check(self._lib.bayer_me_multi_stream(self._h, arr, len(pairs), search_range, interp, _ptr(end_ns),
+                                               ctypes.byref(sched), _stream(stream)), "bayer_me_multi_stream")
+        return sched.value
 
     def sync_status(self, stream=None) -> int:
         return int(self._lib.bayer_me_sync_status(self._h, _stream(stream)))

@@ -34,6 +34,12 @@ struct bayer_me_s {
   size_t prop_bytes = 0;
   int* list = nullptr;    // [1 + blocks]: count, then block indices
   size_t list_bytes = 0;
+  // refine convolution
+  void* ref_w = nullptr;  // bf16 weights and biases
+  size_t ref_w_bytes = 0;
+  void* ref_act = nullptr;  // two hidden activation maps
+  size_t ref_act_bytes = 0;
+  bme::MultiStream* ms = nullptr;  // multi-stream tables, autotune table, graphs
 };
 
 namespace {
@@ -223,6 +229,9 @@ bayer_status_t bayer_me_destroy(bayer_me_t h) {
   if (h->cnn_dpre) cudaFree(h->cnn_dpre);
   if (h->prop) cudaFree(h->prop);
   if (h->list) cudaFree(h->list);
+  if (h->ref_w) cudaFree(h->ref_w);
+  if (h->ref_act) cudaFree(h->ref_act);
+  if (h->ms) bme::ms_destroy(h->ms);
   if (h->s_in) cudaStreamDestroy(h->s_in);
   if (h->s_comp) cudaStreamDestroy(h->s_comp);
   if (h->s_out) cudaStreamDestroy(h->s_out);
@@ -531,6 +540,113 @@ bayer_status_t bayer_me_estimate_learned(bayer_me_t h, const uint16_t* ref, cons
   if (e != cudaSuccess) return cuda_status(e);
   return seeded_fast(h, ref, cur, W, H, pitch, ref_bs, cur_bs, batch, range, prop, conf, conf_thresh, mv_out,
                      fallback_out, n_fallback, st);
+}
+
+bayer_status_t bayer_refine_conv(bayer_me_t h, const float* feat, int n, int Hf, int Wf, int C, int hidden,
+                                 const float* w1, const float* b1, const float* w2, const float* b2, const float* w3,
+                                 const float* b3, int precision, float* out, void* stream) {
+  if (!h || !feat || !out || !w1 || !b1 || !w2 || !b2 || !w3 || !b3) return BAYER_ERR_INVALID_ARG;
+  if (n < 1 || Hf < 1 || Wf < 1) return BAYER_ERR_INVALID_ARG;
+  if (precision != BAYER_PREC_BF16 && precision != BAYER_PREC_FP32) return BAYER_ERR_INVALID_ARG;
+  if (C != 128 || hidden != 64) return BAYER_ERR_UNSUPPORTED;
+  const size_t bytes = (size_t)n * Hf * Wf * C * sizeof(float);
+  const char* fb = reinterpret_cast<const char*>(feat);
+  const char* ob = reinterpret_cast<const char*>(out);
+  if (ob < fb + bytes && fb < ob + bytes) return BAYER_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(feat) | reinterpret_cast<uintptr_t>(out)) & 15) return BAYER_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t pix = (size_t)n * Hf * Wf;
+  const size_t esz = precision == BAYER_PREC_BF16 ? 2 : 4;
+  bayer_status_t s = grow(reinterpret_cast<char**>(&h->ref_act), &h->ref_act_bytes, 2 * pix * hidden * esz);
+  if (s != BAYER_OK) return s;
+  cudaError_t e;
+  if (precision == BAYER_PREC_FP32) {
+    float* a1 = static_cast<float*>(h->ref_act);
+    float* a2 = a1 + pix * hidden;
+    e = bme::launch_conv3x3_f32(feat, n, Hf, Wf, C, w1, b1, hidden, true, a1, st);
+    if (e == cudaSuccess) e = bme::launch_conv3x3_f32(a1, n, Hf, Wf, hidden, w2, b2, hidden, true, a2, st);
+    if (e == cudaSuccess) e = bme::launch_conv3x3_f32(a2, n, Hf, Wf, hidden, w3, b3, C, false, out, st);
+    return cuda_status(e);
+  }
+  // bf16 copies of the parameters: w1 b1 w2 b2 w3 b3, each 64-byte aligned
+  const size_t nw[6] = {(size_t)hidden * C * 9, (size_t)hidden, (size_t)hidden * hidden * 9, (size_t)hidden,
+                        (size_t)C * hidden * 9, (size_t)C};
+  const float* src[6] = {w1, b1, w2, b2, w3, b3};
+  size_t off[6], total = 0;
+  for (int i = 0; i < 6; ++i) {
+    off[i] = total;
+    total += (nw[i] + 31) / 32 * 32;
+  }
+  if ((s = grow(reinterpret_cast<char**>(&h->ref_w), &h->ref_w_bytes, total * 2)) != BAYER_OK) return s;
+  uint16_t* wb = static_cast<uint16_t*>(h->ref_w);
+  for (int i = 0; i < 6; ++i) {
+    e = bme::cnn_to_bf16(src[i], wb + off[i], (int)nw[i], st);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  const __nv_bfloat16* W[6];
+  for (int i = 0; i < 6; ++i) W[i] = reinterpret_cast<const __nv_bfloat16*>(wb + off[i]);
+  __nv_bfloat16* a1 = static_cast<__nv_bfloat16*>(h->ref_act);
+  __nv_bfloat16* a2 = a1 + pix * hidden;
+  bme::ConvTcArgs c{};
+  c.Hi = Hf;
+  c.Wi = Wf;
+  c.Ho = Hf;
+  c.Wo = Wf;
+  c.batch = n;
+  c.status = h->d_status;
+  c.in_f32 = feat;
+  c.w = W[0];
+  c.bias = W[1];
+  c.out = a1;
+  c.cout = hidden;
+  e = bme::launch_conv_tc(c, C, 1, 2, 0, true, st);
+  if (e != cudaSuccess) return cuda_status(e);
+  c.in = a1;
+  c.w = W[2];
+  c.bias = W[3];
+  c.out = a2;
+  e = bme::launch_conv_tc(c, hidden, 1, 0, 0, true, st);
+  if (e != cudaSuccess) return cuda_status(e);
+  c.in = a2;
+  c.w = W[4];
+  c.bias = W[5];
+  c.out = nullptr;
+  c.out_f32 = out;
+  c.cout = C;
+  e = bme::launch_conv_tc(c, hidden, 1, 0, 1, false, st);
+  return cuda_status(e);
+}
+
+bayer_status_t bayer_me_multi_stream(bayer_me_t h, const bayer_pair_t* pairs, int n, int range, int interp,
+                                     long long* end_ns, int* schedule, void* stream) {
+  if (!h || !pairs || n < 1) return BAYER_ERR_INVALID_ARG;
+  if (!bme::full16_even_supported(range)) return BAYER_ERR_UNSUPPORTED;
+  if (interp != BAYER_INTERP_NEAREST && interp != BAYER_INTERP_BILINEAR) return BAYER_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) {
+    const bayer_pair_t& q = pairs[i];
+    if (!q.ref || !q.cur || !q.mv_out) return BAYER_ERR_INVALID_ARG;
+    if (q.W < 16 || q.H < 16 || (q.W % 16) || (q.H % 16) || q.pitch < q.W || q.W > 32767 || q.H > 32767)
+      return BAYER_ERR_INVALID_ARG;
+    if (q.feat) {
+      if (!q.feat_out || q.C < 1 || q.stride < 1 || 16 % q.stride) return BAYER_ERR_INVALID_ARG;
+      if (q.Hf * q.stride / 16 != q.H / 16 || q.Wf * q.stride / 16 != q.W / 16 || (q.Hf * q.stride) % 16 ||
+          (q.Wf * q.stride) % 16)
+        return BAYER_ERR_INVALID_ARG;
+      const size_t bytes = (size_t)q.C * q.Hf * q.Wf * sizeof(float);
+      const char* fb = reinterpret_cast<const char*>(q.feat);
+      const char* ob = reinterpret_cast<const char*>(q.feat_out);
+      if (ob < fb + bytes && fb < ob + bytes) return BAYER_ERR_INVALID_ARG;
+    }
+  }
+  DeviceGuard g(h->device);
+  if (!h->ms) {
+    h->ms = bme::ms_create(h->device);
+    if (!h->ms) return BAYER_ERR_CUDA;
+  }
+  cudaError_t e = bme::ms_run(h->ms, pairs, n, range, interp, end_ns, static_cast<cudaStream_t>(stream));
+  if (e == cudaSuccess && schedule) *schedule = bme::ms_config_nw(h->ms, pairs, n, range, interp);
+  return cuda_status(e);
 }
 
 bayer_status_t bayer_me_sync_status(bayer_me_t h, void* stream) {

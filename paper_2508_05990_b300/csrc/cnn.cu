@@ -39,11 +39,6 @@ __device__ __forceinline__ void unpack8(const uint4 u, float* f) {
   }
 }
 
-__device__ __forceinline__ uint32_t pack2(float a, float b) {
-  const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
-  return *reinterpret_cast<const uint32_t*>(&v);
-}
-
 // Layer-1 input sample: channel ci (0..7) at half-resolution (hy, hx), zero
 // outside the half-resolution map.
 __device__ __forceinline__ float l1_input(const uint16_t* ref, const uint16_t* cur, int pitch, int Hh, int Wh, int ci,
@@ -376,8 +371,9 @@ cudaError_t cnn_forward_acts(const CnnFrames& fr, int batch, const uint16_t* wbf
     c.Ho = s.H[l];
     c.Wo = s.W[l];
     c.batch = batch;
+    c.cout = 32;
     c.status = status;
-    cudaError_t e = launch_conv_tc(c, l == 1 ? 16 : 32, 32, 2, l == 1 ? 1 : 0, true, st);
+    cudaError_t e = launch_conv_tc(c, l == 1 ? 16 : 32, 2, l == 1 ? 1 : 0, 0, true, st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

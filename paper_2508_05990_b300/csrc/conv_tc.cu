@@ -40,17 +40,18 @@ constexpr uint32_t kWaitLimit = 1u << 20;
 // plane q = kx % S at pixel m + kx / S, so every tap's A operand is the staged
 // tensor itself at a shifted start address: core matrices of 8 consecutive
 // pixels (SBO = 128 bytes), the next K chunk one plane further (LBO = NP*16).
-template <int CIN, int COUT, int S>
+template <int CIN, int NB, int S>
 struct RowConvLayout {
   static constexpr int KC = CIN / 8;
   static constexpr int NJ = S * (kM - 1) + 3;       // staged input columns
   static constexpr int NP = (NJ + S - 1) / S;       // pixels per parity plane
   static constexpr int STAGE_BYTES = 3 * S * KC * NP * 16;
-  static constexpr int B_BYTES = 9 * CIN * COUT * 2;
-  static constexpr int TMEM_COLS = COUT < 32 ? 32 : COUT;
+  static constexpr int B_BYTES = 9 * CIN * NB * 2;  // this CTA's NB output channels
+  static constexpr int TMEM_COLS = NB < 32 ? 32 : NB;
   static constexpr int SMEM = B_BYTES + STAGE_BYTES + 64;
-  static_assert(CIN % 16 == 0 && COUT % 32 == 0 && COUT <= 256, "shape");
+  static_assert(CIN % 16 == 0 && NB % 32 == 0 && NB <= 256, "shape");
   static_assert(B_BYTES % 128 == 0 && STAGE_BYTES % 16 == 0, "alignment");
+  static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
 __device__ __forceinline__ uint32_t bf2(float a, float b) {
@@ -63,9 +64,13 @@ __device__ __forceinline__ uint32_t split12(uint32_t v) {
   return bf2((float)(v >> 4) * (1.0f / 128.0f) - 1.0f, (float)(v & 15u) * (1.0f / 16.0f));
 }
 
-template <int CIN, int COUT, int S, int SRC, bool RELU>
+// SRC: 0 bf16 NHWC input, 1 Bayer frames (hi/lo split), 2 float32 NHWC input
+// rounded to bf16 while staging.  OUTF: 0 bf16 NHWC output, 1 float32 NHWC.
+// Output channels are split over CTAs, NB per CTA (a.cout = total).
+template <int CIN, int NB, int S, int SRC, int OUTF, bool RELU>
 __global__ void __launch_bounds__(kM) conv3x3_tc_kernel(const ConvTcArgs a) {
-  using L = RowConvLayout<CIN, COUT, S>;
+  using L = RowConvLayout<CIN, NB, S>;
+  constexpr int COUT = NB;
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sB = smem;
   uint8_t* sX = smem + L::B_BYTES;
@@ -78,14 +83,17 @@ __global__ void __launch_bounds__(kM) conv3x3_tc_kernel(const ConvTcArgs a) {
     tc::fence_mbar_init();
   }
   if (warp == 0) tc::tmem_alloc(tmem_slot, L::TMEM_COLS);
-  // weights -> B (K-major, k = tap*CIN + ci): element (n, k) at
-  // (n/8)*(9*KC)*128 + (k/8)*128 + (n%8)*16 + (k%8)*2
+  const int nsplit = a.cout / NB;
+  const int split = blockIdx.x % nsplit;
+  const int n0 = split * NB;
+  // weights of channels n0..n0+NB-1 -> B (K-major, k = tap*CIN + ci): element
+  // (n, k) at (n/8)*(9*KC)*128 + (k/8)*128 + (n%8)*16 + (k%8)*2
   for (int i = tid; i < COUT * 9 * CIN; i += kM) {
     const int n = i / (9 * CIN), k = i - n * 9 * CIN;
     const int tap = k / CIN, ci = k - tap * CIN;
     float wv;
-    if (SRC == 0) {
-      wv = __bfloat162float(a.w[(n * CIN + ci) * 9 + tap]);
+    if (SRC != 1) {
+      wv = __bfloat162float(a.w[((n0 + n) * CIN + ci) * 9 + tap]);
     } else {
       wv = __bfloat162float(a.w[(n * 8 + (ci >> 1)) * 9 + tap]);
       if (ci & 1) wv *= (1.0f / 128.0f);
@@ -104,7 +112,8 @@ __global__ void __launch_bounds__(kM) conv3x3_tc_kernel(const ConvTcArgs a) {
   uint32_t phase = 0;
   bool ok = true;
 
-  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  const int cta_stride = gridDim.x / nsplit;
+  for (long long tile = blockIdx.x / nsplit; tile < ntiles; tile += cta_stride) {
     const int seg = (int)(tile % segs);
     const long long row = tile / segs;
     const int b = (int)(row / a.Ho), oy = (int)(row - (long long)b * a.Ho);
@@ -114,7 +123,25 @@ __global__ void __launch_bounds__(kM) conv3x3_tc_kernel(const ConvTcArgs a) {
     // ---- stage rows S*oy - 1 .. S*oy + 1, columns c0 .. c0 + NJ - 1
     constexpr int NITEM = 3 * L::NJ;
     for (int it0 = 0; it0 < NITEM; it0 += 2 * kM) {
-      if (SRC == 0) {
+      if (SRC == 2) {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int it = it0 + u * kM + tid;
+          if (it >= NITEM) continue;
+          const int rho = it / L::NJ, j = it - rho * L::NJ;
+          const int iy = S * oy - 1 + rho, ix = c0 + j;
+          const bool in_ok = iy >= 0 && iy < a.Hi && ix >= 0 && ix < a.Wi;
+          const float4* src = reinterpret_cast<const float4*>(a.in_f32 + (((long long)b * a.Hi + iy) * a.Wi + ix) * CIN);
+          const int q = j % S, pp = j / S;
+#pragma unroll 4
+          for (int kc = 0; kc < L::KC; ++kc) {
+            const float4 f0 = in_ok ? __ldg(src + 2 * kc) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 f1 = in_ok ? __ldg(src + 2 * kc + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+            *reinterpret_cast<uint4*>(sX + (((rho * S + q) * L::KC + kc) * L::NP + pp) * 16) =
+                make_uint4(bf2(f0.x, f0.y), bf2(f0.z, f0.w), bf2(f1.x, f1.y), bf2(f1.z, f1.w));
+          }
+        }
+      } else if (SRC == 0) {
         uint4 v[2][L::KC];
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
@@ -191,26 +218,28 @@ __global__ void __launch_bounds__(kM) conv3x3_tc_kernel(const ConvTcArgs a) {
     tc::fence_after_sync();
     const int ox = ox0 + tid;
     const bool valid = ox < a.Wo;
-    __nv_bfloat16* orow = a.out + (((long long)b * a.Ho + oy) * a.Wo + ox) * COUT;
+    const long long opix = ((long long)b * a.Ho + oy) * a.Wo + ox;
 #pragma unroll
     for (int cc = 0; cc < COUT; cc += 32) {
       float v[32];
       tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cc, v);
       if (valid) {
-        uint32_t o[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          float x0 = v[2 * j] + __bfloat162float(a.bias[cc + 2 * j]);
-          float x1 = v[2 * j + 1] + __bfloat162float(a.bias[cc + 2 * j + 1]);
-          if (RELU) {
-            x0 = fmaxf(x0, 0.f);
-            x1 = fmaxf(x1, 0.f);
-          }
-          o[j] = bf2(x0, x1);
+        for (int j = 0; j < 32; ++j) {
+          v[j] += __bfloat162float(a.bias[n0 + cc + j]);
+          if (RELU) v[j] = fmaxf(v[j], 0.f);
         }
-        uint4* dst = reinterpret_cast<uint4*>(orow + cc);
+        if (OUTF == 0) {
+          uint4* dst = reinterpret_cast<uint4*>(a.out + opix * a.cout + n0 + cc);
 #pragma unroll
-        for (int q4 = 0; q4 < 4; ++q4) dst[q4] = make_uint4(o[4 * q4], o[4 * q4 + 1], o[4 * q4 + 2], o[4 * q4 + 3]);
+          for (int q4 = 0; q4 < 4; ++q4)
+            dst[q4] = make_uint4(bf2(v[8 * q4], v[8 * q4 + 1]), bf2(v[8 * q4 + 2], v[8 * q4 + 3]),
+                                 bf2(v[8 * q4 + 4], v[8 * q4 + 5]), bf2(v[8 * q4 + 6], v[8 * q4 + 7]));
+        } else {
+          float4* dst = reinterpret_cast<float4*>(a.out_f32 + opix * a.cout + n0 + cc);
+#pragma unroll
+          for (int q4 = 0; q4 < 8; ++q4) dst[q4] = make_float4(v[4 * q4], v[4 * q4 + 1], v[4 * q4 + 2], v[4 * q4 + 3]);
+        }
       }
     }
     tc::fence_before_sync();
@@ -221,28 +250,30 @@ __global__ void __launch_bounds__(kM) conv3x3_tc_kernel(const ConvTcArgs a) {
   if (!ok && tid == 0 && a.status) atomicExch(a.status, (int)BAYER_ERR_TIMEOUT);
 }
 
-template <int CIN, int COUT, int S, int SRC, bool RELU>
+template <int CIN, int NB, int S, int SRC, int OUTF, bool RELU>
 cudaError_t launch_t(const ConvTcArgs& a, cudaStream_t st) {
-  using L = RowConvLayout<CIN, COUT, S>;
-  auto kern = conv3x3_tc_kernel<CIN, COUT, S, SRC, RELU>;
+  using L = RowConvLayout<CIN, NB, S>;
+  auto kern = conv3x3_tc_kernel<CIN, NB, S, SRC, OUTF, RELU>;
+  if (a.cout % NB != 0) return cudaErrorInvalidValue;
+  const int nsplit = a.cout / NB;
   int dev = 0, nsm = 148;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int per_sm = tc::ctas_per_sm(kern, kM, L::SMEM, L::TMEM_COLS);
   const long long ntiles = (long long)a.batch * a.Ho * ((a.Wo + kM - 1) / kM);
-  long long grid = (long long)nsm * per_sm;
-  if (grid > ntiles) grid = ntiles;
-  if (grid < 1) return cudaSuccess;
-  kern<<<(unsigned)grid, kM, L::SMEM, st>>>(a);
+  long long per_split = (long long)nsm * per_sm / nsplit;
+  if (per_split > ntiles) per_split = ntiles;
+  if (per_split < 1) per_split = 1;
+  if (ntiles < 1) return cudaSuccess;
+  kern<<<(unsigned)(per_split * nsplit), kM, L::SMEM, st>>>(a);
   return cudaGetLastError();
 }
 
-template <int CIN, int COUT, int S, int SRC, bool RELU>
+template <int CIN, int NB, int S, int SRC, int OUTF, bool RELU>
 cudaError_t configure_t() {
-  using L = RowConvLayout<CIN, COUT, S>;
-  auto kern = conv3x3_tc_kernel<CIN, COUT, S, SRC, RELU>;
+  using L = RowConvLayout<CIN, NB, S>;
+  auto kern = conv3x3_tc_kernel<CIN, NB, S, SRC, OUTF, RELU>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
-  // prefer the largest shared-memory carveout so several CTAs fit per SM (the
-  // occupancy query that sizes the persistent grid follows this preference)
+  // prefer the largest shared-memory carveout so several CTAs fit per SM
   if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   return e;
 }
@@ -251,13 +282,21 @@ cudaError_t configure_t() {
 
 cudaError_t configure_conv_tc() {
   cudaError_t e;
-  if ((e = configure_t<16, 32, 2, 1, true>()) != cudaSuccess) return e;
-  return configure_t<32, 32, 2, 0, true>();
+  if ((e = configure_t<16, 32, 2, 1, 0, true>()) != cudaSuccess) return e;
+  if ((e = configure_t<32, 32, 2, 0, 0, true>()) != cudaSuccess) return e;
+  if ((e = configure_t<128, 32, 1, 2, 0, true>()) != cudaSuccess) return e;
+  if ((e = configure_t<64, 64, 1, 0, 0, true>()) != cudaSuccess) return e;
+  return configure_t<64, 64, 1, 0, 1, false>();
 }
 
-cudaError_t launch_conv_tc(const ConvTcArgs& a, int cin, int cout, int stride, int src, bool relu, cudaStream_t st) {
-  if (cin == 16 && cout == 32 && stride == 2 && src == 1 && relu) return launch_t<16, 32, 2, 1, true>(a, st);
-  if (cin == 32 && cout == 32 && stride == 2 && src == 0 && relu) return launch_t<32, 32, 2, 0, true>(a, st);
+cudaError_t launch_conv_tc(const ConvTcArgs& a, int cin, int stride, int src, int outf, bool relu, cudaStream_t st) {
+  if (cin == 16 && stride == 2 && src == 1 && outf == 0 && relu && a.cout == 32)
+    return launch_t<16, 32, 2, 1, 0, true>(a, st);
+  if (cin == 32 && stride == 2 && src == 0 && outf == 0 && relu && a.cout == 32)
+    return launch_t<32, 32, 2, 0, 0, true>(a, st);
+  if (cin == 128 && stride == 1 && src == 2 && outf == 0 && relu) return launch_t<128, 32, 1, 2, 0, true>(a, st);
+  if (cin == 64 && stride == 1 && src == 0 && outf == 0 && relu) return launch_t<64, 64, 1, 0, 0, true>(a, st);
+  if (cin == 64 && stride == 1 && src == 0 && outf == 1 && !relu) return launch_t<64, 64, 1, 0, 1, false>(a, st);
   return cudaErrorInvalidValue;
 }
 

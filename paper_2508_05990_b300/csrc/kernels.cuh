@@ -75,19 +75,28 @@ cudaError_t cnn_loss_grad(const CnnFrames& fr, int batch, const uint16_t* wbf16,
 // 3x3 convolution on the tensor cores (conv_tc.cu): NHWC bf16 in (or, src 1,
 // the Bayer frames of layer 1), NHWC bf16 out, bias + optional ReLU.
 struct ConvTcArgs {
-  const __nv_bfloat16* in;  // src 0: [batch][Hi][Wi][cin]
+  const __nv_bfloat16* in;  // src 0: [batch][Hi][Wi][cin] bf16
+  const float* in_f32;      // src 2: [batch][Hi][Wi][cin] float32 (rounded to bf16 when staged)
   CnnFrames fr;             // src 1: frames; Hi, Wi are the half-resolution dims
   int Hi, Wi;
   const __nv_bfloat16* w;     // [cout][cin_w][3][3] (cin_w = cin, or 8 for src 1)
   const __nv_bfloat16* bias;  // [cout]
-  __nv_bfloat16* out;         // [batch][Ho][Wo][cout]
-  int Ho, Wo, batch;
+  __nv_bfloat16* out;         // outf 0: [batch][Ho][Wo][cout] bf16
+  float* out_f32;             // outf 1: [batch][Ho][Wo][cout] float32
+  int Ho, Wo, batch, cout;
   int* status;  // device status word: BAYER_ERR_TIMEOUT if a bounded wait expired
 };
 cudaError_t configure_conv_tc();
-cudaError_t launch_conv_tc(const ConvTcArgs& a, int cin, int cout, int stride, int src, bool relu, cudaStream_t st);
+// cin/stride/src/outf/relu select an instantiated form; cout in the args.
+cudaError_t launch_conv_tc(const ConvTcArgs& a, int cin, int stride, int src, int outf, bool relu, cudaStream_t st);
+
+// 3x3 stride-1 convolution in float32 on the SIMT cores (refine_f32.cu):
+// NHWC float32 in and out, bias, optional ReLU.
+cudaError_t launch_conv3x3_f32(const float* in, int batch, int H, int W, int cin, const float* w, const float* bias,
+                               int cout, bool relu, float* out, cudaStream_t st);
 cudaError_t cnn_adamw(float* w, uint16_t* wbf16, const float* g, float* m, float* v, int n, int step, float lr,
                       float b1, float b2, float eps, float wd, cudaStream_t st);
+cudaError_t cnn_to_bf16(const float* w, uint16_t* wbf16, int n, cudaStream_t st);
 
 // Seeded +-4 refine of 16x16 blocks (warp per block) with a compacted list of
 // the low-confidence blocks, and the exhaustive search of a block list.
@@ -112,6 +121,15 @@ cudaError_t launch_full16_list(const uint16_t* ref, const uint16_t* cur, int W, 
                                long long cur_bs, int h, int w, int range, const int* list, const int* count,
                                int max_count, bayer_mv_t* out, cudaStream_t st);
 cudaError_t configure_full16_list();
+
+// Multi-stream persistent search + propagation (multistream.cu).
+struct MultiStream;
+MultiStream* ms_create(int device);
+void ms_destroy(MultiStream* m);
+cudaError_t configure_multistream();
+cudaError_t ms_run(MultiStream* m, const bayer_pair_t* pairs, int n, int range, int interp, long long* end_ns,
+                   cudaStream_t st);
+int ms_config_nw(MultiStream* m, const bayer_pair_t* pairs, int n, int range, int interp);
 
 // Roofline probe of the SAD primitive.
 cudaError_t run_probe_alu(int variant, double* pc_per_clk_per_sm, double* sm_mhz, int* sm_count);

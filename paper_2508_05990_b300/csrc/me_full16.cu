@@ -22,6 +22,7 @@
 //     sad*64 + rank key, rank being the tie-break order within the lane's row
 //     -- then a 5-step shuffle minimum.
 #include "common.cuh"
+#include "full16.cuh"
 #include "kernels.cuh"
 #include "tc_common.cuh"
 
@@ -32,128 +33,12 @@ namespace {
 constexpr int kNW = 8;  // warps (blocks) per CTA
 
 template <int R>
-struct Full16 {
-  static constexpr int NU = 2 * R + 1;         // candidates per row
-  static constexpr int REACH = 2 * R;          // pixels each side
-  static constexpr int WIN_W = 16 * kNW + 2 * REACH;
-  static constexpr int WIN_H = 16 + 2 * REACH;
-  static constexpr int P0 = (WIN_W + 3) / 4 * 4;
-  static constexpr int P = ((P0 / 4) % 2 == 0) ? P0 + 4 : P0;  // 4 * odd words
-  static constexpr int PC = 16 * kNW + 4;      // current-tile pitch (words)
-  static constexpr int SPAN = 16 + 2 * REACH;  // window pixels one block reads per row
-  static constexpr size_t SMEM = (size_t)(WIN_H * P + 16 * PC) * sizeof(uint32_t);
-  static_assert(NU <= 33, "at most 33 candidate rows");
-  static_assert(SPAN % 4 == 0, "span must be a multiple of 4 words");
-};
-
-// SAD of every candidate of one 16x16 block, computed by one warp from a
-// staged window (wbase: the block's window origin, row pitch P words) and
-// current block (cbase, row pitch PC words); returns the lane's best key.
-template <int R, int P, int PC>
-__device__ __forceinline__ uint64_t full16_block(const uint32_t* wbase, const uint32_t* cbase, int lane, int xb, int yb,
-                                                 int W, int H) {
-  constexpr int NU = 2 * R + 1, REACH = 2 * R, SPAN = 16 + 2 * REACH;
-  const int v = lane < NU ? lane : NU - 1;  // lanes past the last row repeat it
-  const int eps = (lane >> 2) & 1;          // row rotation for conflict-free loads
-
-  uint32_t acc[NU];
-#pragma unroll
-  for (int k = 0; k < NU; ++k) acc[k] = 0;
-  uint32_t accx = 0, accc = 0;
-
-#pragma unroll 1
-  for (int i = 0; i < 16; ++i) {
-    const int r = (i + eps) & 15;
-    uint32_t c[16];
-    const uint4* cp = reinterpret_cast<const uint4*>(cbase + r * PC);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const uint4 t = cp[q];
-      c[4 * q + 0] = t.x;
-      c[4 * q + 1] = t.y;
-      c[4 * q + 2] = t.z;
-      c[4 * q + 3] = t.w;
-    }
-    const uint4* wp = reinterpret_cast<const uint4*>(wbase + (2 * v + r) * P);
-#pragma unroll
-    for (int q = 0; q < SPAN / 4; ++q) {
-      const uint4 t = wp[q];
-      const uint32_t rr[4] = {t.x, t.y, t.z, t.w};
-#pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        const int p = 4 * q + s;
-#pragma unroll
-        for (int k = 0; k < NU; ++k) {
-          const int cc = p - 2 * k;
-          if (cc >= 0 && cc < 16) acc[k] = sad_u32(rr[s], c[cc], acc[k]);
-        }
-      }
-    }
-    if constexpr (NU == 33) {
-      // row v = 32: candidate u = lane at window pixel 2*lane
-      const uint2* xp = reinterpret_cast<const uint2*>(wbase + (64 + r) * P + 2 * lane);
-#pragma unroll
-      for (int t2 = 0; t2 < 8; ++t2) {
-        const uint2 e2 = xp[t2];
-        accx = sad_u32(e2.x, c[2 * t2], accx);
-        accx = sad_u32(e2.y, c[2 * t2 + 1], accx);
-      }
-      // corner candidate (u, v) = (32, 32): lane l < 16 takes column l
-      if (lane < 16) accc = sad_u32(wbase[(64 + r) * P + 64 + lane], cbase[r * PC + lane], accc);
-    }
-  }
-
-  // ---- argmin with the (sad, |mv|_1, dy, dx) key
-  const int dy = 2 * v - REACH;
-  uint64_t best = kInvalidKey;
-  const bool interior = xb >= REACH && xb + 16 + REACH <= W && yb >= REACH && yb + 16 + REACH <= H;
-  if (interior) {
-    // Every candidate is valid.  Within a lane dy is fixed, so the tie-break
-    // (|dx|+|dy|, dy, dx) orders the row by rank = 0 for dx = 0, then -2, +2,
-    // -4, +4, ...; sad * 64 + rank is a 32-bit key (sad < 2^25, rank <= 32).
-    uint32_t m = 0xFFFFFFFFu;
-#pragma unroll
-    for (int k = 0; k < NU; ++k) {
-      const uint32_t rank = k == R ? 0u : (k < R ? (uint32_t)(2 * (R - k) - 1) : (uint32_t)(2 * (k - R)));
-      const uint32_t key = acc[k] * 64u + rank;
-      m = key < m ? key : m;
-    }
-    const uint32_t rank = m & 63u;
-    const int k = rank == 0 ? R : ((rank & 1u) ? R - (int)((rank + 1) >> 1) : R + (int)(rank >> 1));
-    if (lane < NU) best = make_key(m >> 6, 2 * k - REACH, dy);
-  } else {
-    const bool row_ok = lane < NU && yb + dy >= 0 && yb + dy + 16 <= H;
-#pragma unroll
-    for (int k = 0; k < NU; ++k) {
-      const int dx = 2 * k - REACH;
-      const bool ok = row_ok && xb + dx >= 0 && xb + dx + 16 <= W;
-      const uint64_t key = ok ? make_key(acc[k], dx, dy) : kInvalidKey;
-      best = key < best ? key : best;
-    }
-  }
-  if constexpr (NU == 33) {
-    {
-      const int dx = 2 * lane - REACH;
-      const bool ok = yb + 48 <= H && xb + dx >= 0 && xb + dx + 16 <= W;
-      const uint64_t key = ok ? make_key(accx, dx, 32) : kInvalidKey;
-      best = key < best ? key : best;
-    }
-    const uint32_t corner = __reduce_add_sync(0xffffffffu, accc);
-    if (lane == 0 && xb + 48 <= W && yb + 48 <= H) {
-      const uint64_t key = make_key(corner, 32, 32);
-      best = key < best ? key : best;
-    }
-  }
-  return best;
-}
-
-template <int R>
 __global__ void __launch_bounds__(kNW * 32) me_full16_even_kernel(const uint16_t* __restrict__ ref_base,
                                                                    const uint16_t* __restrict__ cur_base, int W,
                                                                    int H, int pitch, long long ref_bs,
                                                                    long long cur_bs, int h, int w,
                                                                    bayer_mv_t* __restrict__ out, bool vec_ok) {
-  using C = Full16<R>;
+  using C = Full16Strip<R, kNW>;
   extern __shared__ __align__(16) uint32_t smem[];
   uint32_t* win = smem;                 // WIN_H x P
   uint32_t* curt = smem + C::WIN_H * C::P;  // 16 x PC
@@ -164,68 +49,7 @@ __global__ void __launch_bounds__(kNW * 32) me_full16_even_kernel(const uint16_t
   const uint16_t* cur = cur_base + (long long)pair * cur_bs;
   const int x0 = blockIdx.x * kNW * 16, y0 = blockIdx.y * 16;
 
-  // ---- stage the reference window and the current tile (out-of-frame = 0)
-  if (vec_ok) {
-    // 8 pixels (16 bytes) per load: the window origin x0 - 2R and the tile
-    // origin x0 are multiples of 8 and W is a multiple of 16, so every 8-pixel
-    // chunk lies wholly inside or wholly outside the frame.  All loads of a
-    // thread are issued before any conversion.
-    constexpr int WCH = C::WIN_W / 8, NWCH = WCH * C::WIN_H;
-    constexpr int TCH = 2 * kNW, NTCH = TCH * 16;
-    constexpr int PER = (NWCH + NTCH + kNW * 32 - 1) / (kNW * 32);
-    uint4 raw[PER];
-#pragma unroll
-    for (int i = 0; i < PER; ++i) {
-      const int e = threadIdx.x + i * kNW * 32;
-      raw[i] = make_uint4(0, 0, 0, 0);
-      if (e < NWCH) {
-        const int ry = e / WCH, cx = e - ry * WCH;
-        const int gy = y0 - C::REACH + ry, gx = x0 - C::REACH + 8 * cx;
-        if (gy >= 0 && gy < H && gx >= 0 && gx < W)
-          raw[i] = __ldg(reinterpret_cast<const uint4*>(ref + (long long)gy * pitch + gx));
-      } else if (e < NWCH + NTCH) {
-        const int f = e - NWCH, ry = f / TCH, cx = f - ry * TCH;
-        const int gx = x0 + 8 * cx;
-        if (gx < W) raw[i] = __ldg(reinterpret_cast<const uint4*>(cur + (long long)(y0 + ry) * pitch + gx));
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < PER; ++i) {
-      const int e = threadIdx.x + i * kNW * 32;
-      uint32_t* dst;
-      if (e < NWCH) {
-        const int ry = e / WCH, cx = e - ry * WCH;
-        dst = win + ry * C::P + 8 * cx;
-      } else if (e < NWCH + NTCH) {
-        const int f = e - NWCH, ry = f / TCH, cx = f - ry * TCH;
-        dst = curt + ry * C::PC + 8 * cx;
-      } else {
-        continue;
-      }
-      reinterpret_cast<uint4*>(dst)[0] = make_uint4(pix_lo(raw[i].x), pix_hi(raw[i].x), pix_lo(raw[i].y), pix_hi(raw[i].y));
-      reinterpret_cast<uint4*>(dst)[1] = make_uint4(pix_lo(raw[i].z), pix_hi(raw[i].z), pix_lo(raw[i].w), pix_hi(raw[i].w));
-    }
-  } else {
-    for (int ry = warp; ry < C::WIN_H; ry += kNW) {
-      const int gy = y0 - C::REACH + ry;
-      const bool row_in = gy >= 0 && gy < H;
-      for (int rx = lane; rx < C::WIN_W; rx += 32) {
-        const int gx = x0 - C::REACH + rx;
-        uint32_t v = 0;
-        if (row_in && gx >= 0 && gx < W) v = __ldg(ref + (long long)gy * pitch + gx);
-        win[ry * C::P + rx] = pix_word(v);
-      }
-    }
-    for (int ry = warp; ry < 16; ry += kNW) {
-      const int gy = y0 + ry;
-      for (int rx = lane; rx < 16 * kNW; rx += 32) {
-        const int gx = x0 + rx;
-        uint32_t v = 0;
-        if (gy < H && gx < W) v = __ldg(cur + (long long)gy * pitch + gx);
-        curt[ry * C::PC + rx] = pix_word(v);
-      }
-    }
-  }
+  stage_strip<R, kNW>(ref, cur, W, H, pitch, x0, y0, vec_ok, win, curt);
   __syncthreads();
 
   const int bx = blockIdx.x * kNW + warp;
@@ -239,7 +63,7 @@ __global__ void __launch_bounds__(kNW * 32) me_full16_even_kernel(const uint16_t
 template <int R>
 cudaError_t launch_r(const uint16_t* ref, const uint16_t* cur, int W, int H, int pitch, long long ref_bs,
                      long long cur_bs, int batch, bayer_mv_t* out, cudaStream_t st) {
-  using C = Full16<R>;
+  using C = Full16Strip<R, kNW>;
   const int h = H / 16, w = W / 16;
   dim3 grid((w + kNW - 1) / kNW, h, batch);
   // 16-byte loads need 16-byte aligned rows in every frame of the batch
@@ -371,7 +195,7 @@ cudaError_t configure_list_r() {
 template <int R>
 cudaError_t configure_r() {
   cudaError_t e = cudaFuncSetAttribute(me_full16_even_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)Full16<R>::SMEM);
+                                       (int)Full16Strip<R, kNW>::SMEM);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(me_full16_even_kernel<R>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   return e;

@@ -1,0 +1,464 @@
+// Many camera streams in one persistent launch: the exhaustive 16x16 EVEN
+// search and the MV feature propagation of a set of frame pairs of mixed
+// sizes (one pair per stream per frame time), replayed as a CUDA graph, with
+// the launch schedule chosen by an autotuner and cached per set of sizes.
+//
+// Search: persistent CTAs (NW warps = one strip of NW adjacent blocks) take
+// strips from a device work queue (atomic counter) over all pairs, find the
+// pair by binary search in a prefix table, stage the strip's window
+// (full16.cuh) and search it.  The last strip of a pair stamps %globaltimer.
+// Propagation: persistent CTAs (256 threads) take (pair, 8-channel chunk,
+// 256-cell tile) items from a second queue and warp the pair's NCHW feature
+// map by its MV field (prop_common.cuh); the last item of a pair stamps the
+// pair's completion time relative to the search launch's start.
+// Autotuner: on the first call for a set of sizes it times each schedule
+// (NW in {4, 8} x pair order {as given, largest first}) with CUDA events and
+// keeps the fastest; the graph (counter reset, search, propagation) is then
+// captured once and relaunched with only the descriptor table refreshed.
+#include <algorithm>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "full16.cuh"
+#include "kernels.cuh"
+#include "prop_common.cuh"
+#include "tc_common.cuh"
+
+namespace bme {
+
+namespace {
+
+struct MsPair {
+  const uint16_t* ref;
+  const uint16_t* cur;
+  bayer_mv_t* mv;
+  const float* feat;
+  float* fout;
+  int W, H, pitch;
+  int C, Hf, Wf, stride;
+  int h, w, strips_x;
+  int me_items, pr_items, prop_tiles;
+  int vec;
+};
+
+struct MsCounters {
+  int me_next;
+  int pr_next;
+  unsigned long long t0;
+};
+
+constexpr int kPropThreads = 256;
+constexpr int kPropCh = 8;
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ int find_pair(const int* prefix, int n, int item) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(prefix + mid) <= item) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+template <int R, int NW>
+__global__ void __launch_bounds__(NW * 32) ms_me_kernel(const MsPair* __restrict__ pairs,
+                                                         const int* __restrict__ prefix, int n, int total,
+                                                         MsCounters* ctr, int* __restrict__ done,
+                                                         long long* __restrict__ end_ns) {
+  using C = Full16Strip<R, NW>;
+  extern __shared__ __align__(16) uint32_t smem[];
+  uint32_t* win = smem;
+  uint32_t* curt = smem + C::WIN_H * C::P;
+  __shared__ int s_item;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) atomicMin(&ctr->t0, gtimer());
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(&ctr->me_next, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= total) break;
+    const int p = find_pair(prefix, n, item);
+    const MsPair P = pairs[p];
+    const int local = item - __ldg(prefix + p);
+    const int by = local / P.strips_x, sx = local - by * P.strips_x;
+    const int x0 = sx * NW * 16, y0 = by * 16;
+    stage_strip<R, NW>(P.ref, P.cur, P.W, P.H, P.pitch, x0, y0, P.vec != 0, win, curt);
+    __syncthreads();
+    const int bx = sx * NW + warp;
+    if (bx < P.w) {
+      const uint64_t best =
+          warp_min_u64(full16_block<R, C::P, C::PC>(win + 16 * warp, curt + 16 * warp, lane, bx * 16, y0, P.W, P.H));
+      if (lane == 0) P.mv[(long long)by * P.w + bx] = key_to_mv(best);
+    }
+    __syncthreads();  // window consumed, MV records written
+    if (threadIdx.x == 0) {
+      __threadfence();
+      // pairs without features are complete when their MV field is
+      if (atomicAdd(&done[p], 1) == P.me_items - 1 && P.pr_items == 0) end_ns[p] = (long long)(gtimer() - ctr->t0);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kPropThreads) ms_prop_kernel(const MsPair* __restrict__ pairs,
+                                                                const int* __restrict__ prefix, int n, int total,
+                                                                MsCounters* ctr, int* __restrict__ done,
+                                                                long long* __restrict__ end_ns, int interp) {
+  __shared__ int s_item;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(&ctr->pr_next, 1);
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();
+    if (item >= total) break;
+    const int p = find_pair(prefix, n, item);
+    const MsPair P = pairs[p];
+    const int local = item - __ldg(prefix + p);
+    const int chunk = local / P.prop_tiles, tile = local - chunk * P.prop_tiles;
+    const int cells = P.Hf * P.Wf;
+    const int cell = tile * kPropThreads + threadIdx.x;
+    if (cell < cells) {
+      const int fy = cell / P.Wf, fx = cell - fy * P.Wf;
+      const int cpb = 16 / P.stride;  // feature cells per block side
+      const bayer_mv_t mv = P.mv[(long long)(fy / cpb) * P.w + fx / cpb];
+      const int c0 = chunk * kPropCh;
+      const int nc = min(kPropCh, P.C - c0);
+      const float* in = P.feat + (long long)c0 * cells;
+      float* out = P.fout + (long long)c0 * cells + cell;
+      if (interp == BAYER_INTERP_NEAREST) {
+        const int sy = prop::clampi(fy + prop::rounddiv(mv.dy, P.stride), 0, P.Hf - 1);
+        const int sx = prop::clampi(fx + prop::rounddiv(mv.dx, P.stride), 0, P.Wf - 1);
+        for (int c = 0; c < nc; ++c) __stcs(out + (long long)c * cells, __ldg(in + (long long)c * cells + sy * P.Wf + sx));
+      } else {
+        const prop::Taps tp = prop::bilinear_taps(P.stride, P.Hf, P.Wf, fy, fx, mv);
+        const int oa = tp.y0 * P.Wf + tp.x0, ob = tp.y0 * P.Wf + tp.x1;
+        const int oc = tp.y1 * P.Wf + tp.x0, od = tp.y1 * P.Wf + tp.x1;
+        float va[kPropCh], vb[kPropCh], vc[kPropCh], vd[kPropCh];
+#pragma unroll
+        for (int c = 0; c < kPropCh; ++c) {
+          if (c < nc) {
+            const float* pl = in + (long long)c * cells;
+            va[c] = __ldg(pl + oa);
+            vb[c] = __ldg(pl + ob);
+            vc[c] = __ldg(pl + oc);
+            vd[c] = __ldg(pl + od);
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < kPropCh; ++c)
+          if (c < nc) __stcs(out + (long long)c * cells, prop::blend(tp, va[c], vb[c], vc[c], vd[c]));
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      if (atomicAdd(&done[p], 1) == P.pr_items - 1) end_ns[p] = (long long)(gtimer() - ctr->t0);
+    }
+  }
+}
+
+struct Config {
+  int nw;     // warps (blocks) per search strip: 4 or 8
+  int order;  // 0: pairs as given, 1: largest first
+};
+
+template <int R, int NW>
+cudaError_t ms_me_configure() {
+  cudaError_t e = cudaFuncSetAttribute(ms_me_kernel<R, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)Full16Strip<R, NW>::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(ms_me_kernel<R, NW>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  return e;
+}
+
+template <int R, int NW>
+cudaError_t ms_me_launch(const MsPair* pairs, const int* prefix, int n, int total, MsCounters* ctr, int* done,
+                         long long* end_ns, cudaStream_t st) {
+  using C = Full16Strip<R, NW>;
+  int dev = 0, nsm = 148;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int per_sm = tc::ctas_per_sm(ms_me_kernel<R, NW>, NW * 32, (int)C::SMEM, 0);
+  int grid = nsm * per_sm;
+  if (grid > total) grid = total;
+  if (grid < 1) return cudaSuccess;
+  ms_me_kernel<R, NW><<<grid, NW * 32, C::SMEM, st>>>(pairs, prefix, n, total, ctr, done, end_ns);
+  return cudaGetLastError();
+}
+
+template <int NW>
+cudaError_t ms_me_dispatch(int range, const MsPair* pairs, const int* prefix, int n, int total, MsCounters* ctr,
+                           int* done, long long* end_ns, cudaStream_t st) {
+  switch (range) {
+    case 8: return ms_me_launch<4, NW>(pairs, prefix, n, total, ctr, done, end_ns, st);
+    case 16: return ms_me_launch<8, NW>(pairs, prefix, n, total, ctr, done, end_ns, st);
+    case 24: return ms_me_launch<12, NW>(pairs, prefix, n, total, ctr, done, end_ns, st);
+    case 32: return ms_me_launch<16, NW>(pairs, prefix, n, total, ctr, done, end_ns, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+// Per-handle state: device tables, counters, the autotune table and cached
+// graphs (one per set of frame sizes and schedule).
+struct MultiStream {
+  int device = 0;
+  MsPair* d_pairs = nullptr;
+  int* d_prefix = nullptr;  // [2 * (n + 1)]: search prefix, then propagation prefix
+  int* d_done = nullptr;    // [2 * n]
+  MsCounters* d_ctr = nullptr;
+  long long* d_end = nullptr;  // [n] internal copy of end times
+  int cap = 0;
+  MsPair* h_pairs = nullptr;  // pinned staging of the table
+  int* h_prefix = nullptr;
+  cudaEvent_t copied = nullptr;
+  struct Entry {
+    Config cfg;
+    cudaGraphExec_t exec = nullptr;
+  };
+  std::map<std::string, Entry> cache;  // autotune table + graphs
+  cudaStream_t capture = nullptr;
+};
+
+static void ms_clear_graphs(MultiStream* m) {
+  for (auto& kv : m->cache)
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  m->cache.clear();
+}
+
+MultiStream* ms_create(int device) {
+  MultiStream* m = new MultiStream();
+  m->device = device;
+  cudaError_t e = cudaEventCreateWithFlags(&m->copied, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&m->capture, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMalloc(&m->d_ctr, sizeof(MsCounters));
+  if (e == cudaSuccess) e = configure_multistream();
+  if (e != cudaSuccess) {
+    ms_destroy(m);
+    return nullptr;
+  }
+  return m;
+}
+
+void ms_destroy(MultiStream* m) {
+  if (!m) return;
+  ms_clear_graphs(m);
+  if (m->d_pairs) cudaFree(m->d_pairs);
+  if (m->d_prefix) cudaFree(m->d_prefix);
+  if (m->d_done) cudaFree(m->d_done);
+  if (m->d_ctr) cudaFree(m->d_ctr);
+  if (m->d_end) cudaFree(m->d_end);
+  if (m->h_pairs) cudaFreeHost(m->h_pairs);
+  if (m->h_prefix) cudaFreeHost(m->h_prefix);
+  if (m->copied) cudaEventDestroy(m->copied);
+  if (m->capture) cudaStreamDestroy(m->capture);
+  delete m;
+}
+
+cudaError_t configure_multistream() {
+  cudaError_t e;
+  if ((e = ms_me_configure<4, 4>()) != cudaSuccess) return e;
+  if ((e = ms_me_configure<8, 4>()) != cudaSuccess) return e;
+  if ((e = ms_me_configure<12, 4>()) != cudaSuccess) return e;
+  if ((e = ms_me_configure<16, 4>()) != cudaSuccess) return e;
+  if ((e = ms_me_configure<4, 8>()) != cudaSuccess) return e;
+  if ((e = ms_me_configure<8, 8>()) != cudaSuccess) return e;
+  if ((e = ms_me_configure<12, 8>()) != cudaSuccess) return e;
+  return ms_me_configure<16, 8>();
+}
+
+namespace {
+
+cudaError_t ensure_capacity(MultiStream* m, int n) {
+  if (n <= m->cap) return cudaSuccess;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return e;
+  ms_clear_graphs(m);  // graphs hold the old table addresses
+  if (m->d_pairs) cudaFree(m->d_pairs);
+  if (m->d_prefix) cudaFree(m->d_prefix);
+  if (m->d_done) cudaFree(m->d_done);
+  if (m->d_end) cudaFree(m->d_end);
+  if (m->h_pairs) cudaFreeHost(m->h_pairs);
+  if (m->h_prefix) cudaFreeHost(m->h_prefix);
+  m->d_pairs = nullptr;
+  m->d_prefix = m->d_done = nullptr;
+  m->d_end = nullptr;
+  m->h_pairs = nullptr;
+  m->h_prefix = nullptr;
+  m->cap = 0;
+  const int c = n < 64 ? 64 : n;
+  if ((e = cudaMalloc(&m->d_pairs, sizeof(MsPair) * c)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&m->d_prefix, sizeof(int) * 2 * (c + 1))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&m->d_done, sizeof(int) * 2 * c)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&m->d_end, sizeof(long long) * c)) != cudaSuccess) return e;
+  if ((e = cudaMallocHost(&m->h_pairs, sizeof(MsPair) * c)) != cudaSuccess) return e;
+  if ((e = cudaMallocHost(&m->h_prefix, sizeof(int) * 2 * (c + 1))) != cudaSuccess) return e;
+  m->cap = c;
+  return cudaSuccess;
+}
+
+// Fill the pinned table in schedule order; returns the search and propagation item totals.
+void build_table(MultiStream* m, const bayer_pair_t* pairs, int n, const Config& cfg, int* me_total, int* pr_total,
+                 std::vector<int>* perm) {
+  perm->resize(n);
+  for (int i = 0; i < n; ++i) (*perm)[i] = i;
+  if (cfg.order == 1)
+    std::stable_sort(perm->begin(), perm->end(), [&](int a, int b) {
+      return (long long)pairs[a].W * pairs[a].H > (long long)pairs[b].W * pairs[b].H;
+    });
+  int me = 0, pr = 0;
+  for (int k = 0; k < n; ++k) {
+    const bayer_pair_t& q = pairs[(*perm)[k]];
+    MsPair& P = m->h_pairs[k];
+    P.ref = q.ref;
+    P.cur = q.cur;
+    P.mv = q.mv_out;
+    P.feat = q.feat;
+    P.fout = q.feat_out;
+    P.W = q.W;
+    P.H = q.H;
+    P.pitch = q.pitch;
+    P.C = q.C;
+    P.Hf = q.Hf;
+    P.Wf = q.Wf;
+    P.stride = q.stride;
+    P.h = q.H / 16;
+    P.w = q.W / 16;
+    P.strips_x = (P.w + cfg.nw - 1) / cfg.nw;
+    P.me_items = P.h * P.strips_x;
+    P.prop_tiles = q.feat ? (q.Hf * q.Wf + kPropThreads - 1) / kPropThreads : 0;
+    P.pr_items = q.feat ? ((q.C + kPropCh - 1) / kPropCh) * P.prop_tiles : 0;
+    P.vec = (reinterpret_cast<uintptr_t>(q.ref) % 16 == 0 && reinterpret_cast<uintptr_t>(q.cur) % 16 == 0 &&
+             q.pitch % 8 == 0) ? 1 : 0;
+    m->h_prefix[k] = me;
+    m->h_prefix[(n + 1) + k] = pr;
+    me += P.me_items;
+    pr += P.pr_items;
+  }
+  m->h_prefix[n] = me;
+  m->h_prefix[(n + 1) + n] = pr;
+  *me_total = me;
+  *pr_total = pr;
+}
+
+// Counter reset, search launch, propagation launch (the graph body).
+cudaError_t enqueue(MultiStream* m, int n, int range, int interp, const Config& cfg, int me_total, int pr_total,
+                    cudaStream_t st) {
+  // counters: zero queue positions, start time = max (lowered by atomicMin)
+  cudaError_t e = cudaMemsetAsync(m->d_ctr, 0, offsetof(MsCounters, t0), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(&m->d_ctr->t0, 0xFF, sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->d_done, 0, sizeof(int) * 2 * n, st);
+  const int has_prop = pr_total > 0 ? 1 : 0;
+  if (e == cudaSuccess)
+    e = cfg.nw == 4 ? ms_me_dispatch<4>(range, m->d_pairs, m->d_prefix, n, me_total, m->d_ctr, m->d_done, m->d_end, st)
+                    : ms_me_dispatch<8>(range, m->d_pairs, m->d_prefix, n, me_total, m->d_ctr, m->d_done, m->d_end, st);
+  if (e == cudaSuccess && has_prop) {
+    int dev = 0, nsm = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int grid = nsm * 8;
+    if (grid > pr_total) grid = pr_total;
+    ms_prop_kernel<<<grid, kPropThreads, 0, st>>>(m->d_pairs, m->d_prefix + (n + 1), n, pr_total, m->d_ctr,
+                                                  m->d_done + n, m->d_end, interp);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+std::string signature(const bayer_pair_t* pairs, int n, int range, int interp) {
+  std::string s = std::to_string(n) + ":" + std::to_string(range) + ":" + std::to_string(interp);
+  for (int i = 0; i < n; ++i) {
+    const bayer_pair_t& q = pairs[i];
+    s += ";" + std::to_string(q.W) + "," + std::to_string(q.H) + "," + std::to_string(q.pitch) + "," +
+         std::to_string(q.feat ? q.C : 0) + "," + std::to_string(q.Hf) + "," + std::to_string(q.Wf) + "," +
+         std::to_string(q.stride);
+  }
+  return s;
+}
+
+// Refresh the device table from the pinned staging (after the previous copy has run).
+cudaError_t upload(MultiStream* m, int n, cudaStream_t st) {
+  cudaError_t e = cudaMemcpyAsync(m->d_pairs, m->h_pairs, sizeof(MsPair) * n, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(m->d_prefix, m->h_prefix, sizeof(int) * 2 * (n + 1), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaEventRecord(m->copied, st);
+  return e;
+}
+
+}  // namespace
+
+cudaError_t ms_run(MultiStream* m, const bayer_pair_t* pairs, int n, int range, int interp, long long* end_ns,
+                   cudaStream_t st) {
+  cudaError_t e = ensure_capacity(m, n);
+  if (e != cudaSuccess) return e;
+  const std::string key = signature(pairs, n, range, interp);
+  std::vector<int> perm;
+  int me_total = 0, pr_total = 0;
+  auto it = m->cache.find(key);
+  if (it == m->cache.end()) {
+    // autotune: time every schedule on this set of pairs
+    const Config cands[4] = {{8, 0}, {8, 1}, {4, 0}, {4, 1}};
+    float best_ms = 1e30f;
+    Config best = cands[0];
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (const Config& c : cands) {
+      if ((e = cudaEventSynchronize(m->copied)) != cudaSuccess) break;
+      build_table(m, pairs, n, c, &me_total, &pr_total, &perm);
+      if ((e = upload(m, n, st)) != cudaSuccess) break;
+      if ((e = enqueue(m, n, range, interp, c, me_total, pr_total, st)) != cudaSuccess) break;  // warm
+      cudaEventRecord(e0, st);
+      if ((e = enqueue(m, n, range, interp, c, me_total, pr_total, st)) != cudaSuccess) break;
+      cudaEventRecord(e1, st);
+      if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = c;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return e;
+    // capture the graph of the chosen schedule on the private stream
+    MultiStream::Entry entry;
+    entry.cfg = best;
+    if ((e = cudaEventSynchronize(m->copied)) != cudaSuccess) return e;
+    build_table(m, pairs, n, best, &me_total, &pr_total, &perm);
+    cudaGraph_t g = nullptr;
+    if ((e = cudaStreamBeginCapture(m->capture, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+    cudaError_t ec = enqueue(m, n, range, interp, best, me_total, pr_total, m->capture);
+    e = cudaStreamEndCapture(m->capture, &g);
+    if (ec != cudaSuccess) e = ec;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&entry.exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) return e;
+    it = m->cache.emplace(key, entry).first;
+  } else {
+    if ((e = cudaEventSynchronize(m->copied)) != cudaSuccess) return e;
+    build_table(m, pairs, n, it->second.cfg, &me_total, &pr_total, &perm);
+  }
+  if ((e = upload(m, n, st)) != cudaSuccess) return e;
+  if ((e = cudaGraphLaunch(it->second.exec, st)) != cudaSuccess) return e;
+  if (end_ns) {
+    // end times are in schedule order; scatter them back to the caller's order
+    for (int k = 0; k < n && e == cudaSuccess; ++k)
+      e = cudaMemcpyAsync(end_ns + perm[k], m->d_end + k, sizeof(long long), cudaMemcpyDeviceToDevice, st);
+  }
+  return e;
+}
+
+int ms_config_nw(MultiStream* m, const bayer_pair_t* pairs, int n, int range, int interp) {
+  auto it = m->cache.find(signature(pairs, n, range, interp));
+  return it == m->cache.end() ? 0 : it->second.cfg.nw * 10 + it->second.cfg.order;
+}
+
+}  // namespace bme

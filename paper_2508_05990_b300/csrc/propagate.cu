@@ -17,47 +17,13 @@
 //         contiguous C-vectors), fully coalesced.
 #include "common.cuh"
 #include "kernels.cuh"
+#include "prop_common.cuh"
 
 namespace bme {
 
 namespace {
 
-__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
-
-__device__ __forceinline__ int floordiv(int a, int b) {
-  int q = a / b;
-  if ((a % b != 0) && (a < 0)) --q;
-  return q;
-}
-
-__device__ __forceinline__ int rounddiv(int a, int b) {
-  return a >= 0 ? (2 * a + b) / (2 * b) : -((2 * (-a) + b) / (2 * b));
-}
-
-struct Taps {
-  int y0, y1, x0, x1;
-  float wy, wx, owy, owx;
-};
-
-__device__ __forceinline__ Taps bilinear_taps(const PropArgs& a, int fy, int fx, bayer_mv_t m) {
-  Taps t;
-  const int qy = floordiv(m.dy, a.s), qx = floordiv(m.dx, a.s);
-  t.wy = __fdiv_rn((float)(m.dy - qy * a.s), (float)a.s);
-  t.wx = __fdiv_rn((float)(m.dx - qx * a.s), (float)a.s);
-  t.owy = __fsub_rn(1.0f, t.wy);
-  t.owx = __fsub_rn(1.0f, t.wx);
-  t.y0 = clampi(fy + qy, 0, a.Hf - 1);
-  t.y1 = clampi(fy + qy + 1, 0, a.Hf - 1);
-  t.x0 = clampi(fx + qx, 0, a.Wf - 1);
-  t.x1 = clampi(fx + qx + 1, 0, a.Wf - 1);
-  return t;
-}
-
-__device__ __forceinline__ float blend(const Taps& t, float va, float vb, float vc, float vd) {
-  const float top = __fadd_rn(__fmul_rn(t.owx, va), __fmul_rn(t.wx, vb));
-  const float bot = __fadd_rn(__fmul_rn(t.owx, vc), __fmul_rn(t.wx, vd));
-  return __fadd_rn(__fmul_rn(t.owy, top), __fmul_rn(t.wy, bot));
-}
+using namespace prop;
 
 // NCHW: one thread per output cell (fy, fx) and chunk of kCK channels
 // (grid.y = map x channel chunk).  The MV lookup and tap arithmetic are paid
@@ -91,7 +57,7 @@ __global__ void __launch_bounds__(256) prop_nchw_kernel(const PropArgs a, int nc
       for (int c = 0; c < nc; ++c) __stcs(out + (long long)c * cells, __ldg(src + (long long)c * cells));
     }
   } else {
-    const Taps tp = bilinear_taps(a, fy, fx, mv);
+    const Taps tp = bilinear_taps(a.s, a.Hf, a.Wf, fy, fx, mv);
     const int oa = tp.y0 * a.Wf + tp.x0, ob = tp.y0 * a.Wf + tp.x1;
     const int oc = tp.y1 * a.Wf + tp.x0, od = tp.y1 * a.Wf + tp.x1;
     if (nc == kCK) {
@@ -135,7 +101,7 @@ __global__ void __launch_bounds__(256) prop_nhwc4_kernel(const PropArgs a) {
     const int sx = clampi(fx + rounddiv(mv.dx, a.s), 0, a.Wf - 1);
     __stcs(out, __ldg(in + ((long long)sy * a.Wf + sx) * c4n + c4));
   } else {
-    const Taps tp = bilinear_taps(a, fy, fx, mv);
+    const Taps tp = bilinear_taps(a.s, a.Hf, a.Wf, fy, fx, mv);
     const float4 va = __ldg(in + ((long long)tp.y0 * a.Wf + tp.x0) * c4n + c4);
     const float4 vb = __ldg(in + ((long long)tp.y0 * a.Wf + tp.x1) * c4n + c4);
     const float4 vc = __ldg(in + ((long long)tp.y1 * a.Wf + tp.x0) * c4n + c4);
@@ -167,7 +133,7 @@ __global__ void __launch_bounds__(256) prop_nhwc1_kernel(const PropArgs a) {
     const int sx = clampi(fx + rounddiv(mv.dx, a.s), 0, a.Wf - 1);
     a.out[t] = __ldg(in + ((long long)sy * a.Wf + sx) * a.C + c);
   } else {
-    const Taps tp = bilinear_taps(a, fy, fx, mv);
+    const Taps tp = bilinear_taps(a.s, a.Hf, a.Wf, fy, fx, mv);
     a.out[t] = blend(tp, __ldg(in + ((long long)tp.y0 * a.Wf + tp.x0) * a.C + c),
                      __ldg(in + ((long long)tp.y0 * a.Wf + tp.x1) * a.C + c),
                      __ldg(in + ((long long)tp.y1 * a.Wf + tp.x0) * a.C + c),

@@ -100,3 +100,22 @@ def test_round_bf16_matches_torch():
     x = np.concatenate([rng.normal(size=1000) * 10.0 ** rng.integers(-5, 5, 1000), [0.0, -0.0, 1.0, 3.0, 1 + 2 ** -8]])
     want = torch.from_numpy(x).float().bfloat16().double().numpy()
     np.testing.assert_array_equal(cnn.round_bf16(x), want)
+
+
+def test_refine_conv_matches_torch():
+    """oracle/refine.py: stride-1 3x3 convolution (NHWC) against torch's float64 conv2d."""
+    from oracle import refine
+    rng = np.random.default_rng(12)
+    x = rng.normal(size=(9, 13, 16))
+    w = rng.normal(size=(8, 16, 3, 3))
+    b = rng.normal(size=8)
+    want = F.conv2d(torch.from_numpy(x.transpose(2, 0, 1))[None], torch.from_numpy(w), torch.from_numpy(b),
+                    padding=1)[0].numpy().transpose(1, 2, 0)
+    np.testing.assert_allclose(refine.conv3x3(x, w, b), want, rtol=1e-12, atol=1e-12)
+    w2, w3 = rng.normal(size=(8, 8, 3, 3)), rng.normal(size=(16, 8, 3, 3))
+    t = torch.from_numpy(x.transpose(2, 0, 1))[None]
+    t = F.relu(F.conv2d(t, torch.from_numpy(w), torch.from_numpy(b), padding=1))
+    t = F.relu(F.conv2d(t, torch.from_numpy(w2), torch.zeros(8, dtype=torch.float64), padding=1))
+    t = F.conv2d(t, torch.from_numpy(w3), torch.zeros(16, dtype=torch.float64), padding=1)
+    np.testing.assert_allclose(refine.refine(x, w, b, w2, np.zeros(8), w3, np.zeros(16)),
+                               t[0].numpy().transpose(1, 2, 0), rtol=1e-11, atol=1e-11)
