@@ -13,6 +13,16 @@ flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+Beside the headline, the same JSON line carries (single-GPU runs; ``--no-legs``
+skips them):
+  * learned_seeded: the same clip through the proposal network, the +-4
+    refine and the exhaustive fallback, with fallback rate and SAD regret;
+  * multi_stream: 32 streams of mixed sizes (8x 640x480, 8x 1280x720,
+    12x 1920x1088, 4x 3840x2160), one pair of each per step in one persistent
+    launch pair replayed from a CUDA graph, with p50/p99 per-frame latency;
+  * precision_4k: a 3840x2160 clip, 128-channel stride-4 propagation and the
+    three 3x3 refine convs in BF16 on the tensor cores (FP32 run beside it).
+
 Under torchrun (N > 1) every rank runs an independent replica on its own GPU
 (the path shards into independent clips; no collective on the data path) and
 rank 0 prints the aggregate.  ``--impl reference`` times the CPU oracle on
@@ -55,8 +65,10 @@ def prop_bytes_per_pair() -> int:
     return 2 * C * HF * WF * 4 + (H // BLOCK) * (W // BLOCK) * 8
 
 
-ME_SOURCES = ("paper_2508_05990_b300/csrc/me_full16.cu", "paper_2508_05990_b300/csrc/common.cuh")
-PROP_SOURCES = ("paper_2508_05990_b300/csrc/propagate.cu", "paper_2508_05990_b300/csrc/common.cuh")
+ME_SOURCES = ("paper_2508_05990_b300/csrc/me_full16.cu", "paper_2508_05990_b300/csrc/full16.cuh",
+              "paper_2508_05990_b300/csrc/common.cuh")
+PROP_SOURCES = ("paper_2508_05990_b300/csrc/propagate.cu", "paper_2508_05990_b300/csrc/prop_common.cuh",
+                "paper_2508_05990_b300/csrc/common.cuh")
 
 
 def profiled_traffic(summary: str, sources) -> int | None:
@@ -78,6 +90,48 @@ def profiled_traffic(summary: str, sources) -> int | None:
 
 
 WEIGHTS = os.path.join(ROOT, "paper_2508_05990_b300", "weights", "proposal_1080p_r32.npz")
+
+# batched multi-stream workload: 32 streams of mixed sizes, 16 frames each
+MS_SIZES = [(480, 640)] * 8 + [(720, 1280)] * 8 + [(1088, 1920)] * 12 + [(2160, 3840)] * 4
+MS_FRAMES, MS_C, MS_STRIDE = 16, 256, 8
+MS_SEED = 1004
+# precision form at 4K: 8-frame clip, propagation of 128-channel stride-4 maps, refine convs
+K4_H, K4_W, K4_T = 2160, 3840, 8
+K4_C, K4_HIDDEN, K4_STRIDE = 128, 64, 4
+K4_SEED = 1002
+
+
+def _gen_clip(task):
+    """Pool worker: one synthetic clip (seed, H, W, n_frames)."""
+    from paper_2508_05990_b300 import synth
+    seed, h, w, n = task
+    return synth.pan_clip(seed, h, w, n_frames=n)
+
+
+def gen_clips(tasks, workers=None):
+    """Clips generated in parallel by a spawn-started pool (safe beside an open CUDA context)."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    workers = workers or min(len(tasks), os.cpu_count() or 1)
+    # a worker that dies raises BrokenProcessPool here instead of blocking
+    with ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_gen_clip, tasks))
+
+
+def ms_pc_per_step() -> int:
+    """Pixel-candidates of one multi-stream step (one pair of every stream)."""
+    return sum((hh // BLOCK) * (ww // BLOCK) for hh, ww in MS_SIZES) * BLOCK * BLOCK * (RANGE + 1) ** 2
+
+
+def ms_prop_bytes_per_step() -> int:
+    return sum(2 * MS_C * (hh // MS_STRIDE) * (ww // MS_STRIDE) * 4 + (hh // BLOCK) * (ww // BLOCK) * 8
+               for hh, ww in MS_SIZES)
+
+
+def refine_flops_per_frame() -> int:
+    """Multiply-adds x 2 of the three 3x3 refine convs (C -> hidden -> hidden -> C) on one map."""
+    hf, wf = K4_H // K4_STRIDE, K4_W // K4_STRIDE
+    return 2 * hf * wf * 9 * (K4_C * K4_HIDDEN + K4_HIDDEN * K4_HIDDEN + K4_HIDDEN * K4_C)
 
 
 def dist_env():
@@ -184,6 +238,189 @@ def cpu_baseline_sample(frames, feats):
             "sample": "1 of the 7 pairs of the 1080p clip (full ME + bilinear propagation), all host threads"}
 
 
+def leg_multi_stream(h, clips, steps, warmup, peaks, pc_clk_sm, nsm, sm_mhz):
+    """32 streams of mixed sizes: each step searches one (t, t+1) pair of every
+    stream and propagates its stride-8 256-channel map, all in one persistent
+    search launch + one propagation launch replayed from a CUDA graph.  Per-pair
+    completion times (device global timer, from the step's first CTA) give the
+    latency percentiles.  The same pairs issued as separate per-stream calls
+    (one search + one propagation launch each) are timed beside it."""
+    import torch
+    from paper_2508_05990_b300 import bayer_me as bm
+    stream = torch.cuda.current_stream()
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(MS_SEED)
+    d_clips = [torch.from_numpy(c).cuda() for c in clips]
+    feats, outs, mvs = [], [], []
+    for hh, ww in MS_SIZES:
+        feats.append(torch.randn((MS_C, hh // MS_STRIDE, ww // MS_STRIDE), generator=gen, device="cuda"))
+        outs.append(torch.empty_like(feats[-1]))
+        mvs.append(torch.empty((hh // BLOCK, ww // BLOCK, 2), dtype=torch.int32, device="cuda"))
+    n = len(MS_SIZES)
+
+    def pairs(t):
+        return [{"ref": d_clips[i][t], "cur": d_clips[i][t + 1], "mv": mvs[i], "feat": feats[i],
+                 "feat_out": outs[i], "stride": MS_STRIDE} for i in range(n)]
+
+    tables = [pairs(t) for t in range(MS_FRAMES - 1)]
+    end = torch.zeros((steps, n), dtype=torch.int64, device="cuda")
+    sched = 0
+    for k in range(warmup):
+        sched = h.multi_stream(tables[k % len(tables)], RANGE, end_ns=end[0])
+    torch.cuda.synchronize()
+    if h.sync_status() != bm.OK:
+        raise RuntimeError("device status after multi-stream warm-up")
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for k in range(steps):
+        h.multi_stream(tables[k % len(tables)], RANGE, end_ns=end[k])
+    stop.record(stream)
+    torch.cuda.synchronize()
+    ms = start.elapsed_time(stop)
+    lat_ms = end.cpu().numpy().astype(np.float64).ravel() / 1e6
+
+    # the same work as separate calls per stream
+    sep_steps = max(3, steps // 4)
+
+    def separate(t):
+        for i in range(n):
+            q = tables[t][i]
+            h.estimate(q["ref"], q["cur"], BLOCK, RANGE, out=mvs[i], stream=stream)
+            h.feat_propagate(feats[i], mvs[i], BLOCK, MS_STRIDE, interp=bm.INTERP_BILINEAR, out=outs[i],
+                             stream=stream)
+
+    separate(0)
+    torch.cuda.synchronize()
+    start.record(stream)
+    for k in range(sep_steps):
+        separate(k % len(tables))
+    stop.record(stream)
+    torch.cuda.synchronize()
+    ms_sep = start.elapsed_time(stop) / sep_steps
+    if h.sync_status() != bm.OK:
+        raise RuntimeError("device status after multi-stream leg")
+
+    step_ms = ms / steps
+    t_alu = ms_pc_per_step() / (pc_clk_sm * nsm * sm_mhz * 1e6) * 1e3
+    t_hbm = ms_prop_bytes_per_step() / (peaks.get("hbm_gbs", 6400.0) * 1e9) * 1e3
+    return {
+        "workload": "32 streams (8x 640x480, 8x 1280x720, 12x 1920x1088, 4x 3840x2160), 16 frames each; "
+                    "block 16 +-32 EVEN exhaustive; bilinear propagation of 256-channel stride-8 maps",
+        "value": round(n * steps / (ms / 1e3), 2), "unit": UNIT, "steps": steps, "warmup": warmup,
+        "ms_per_step": round(step_ms, 4), "frames_per_step": n,
+        "latency_ms": {"p50": round(float(np.percentile(lat_ms, 50)), 4),
+                       "p99": round(float(np.percentile(lat_ms, 99)), 4),
+                       "max": round(float(lat_ms.max()), 4),
+                       "definition": "first CTA of the step's search launch -> pair's propagated map written"},
+        "schedule": {"blocks_per_strip": sched // 10, "order": "largest first" if sched % 10 else "stream order",
+                     "picked_by": "autotuner (timed graph replays of each candidate)"},
+        "separate_launches": {"ms_per_step": round(ms_sep, 4), "launches_per_step": 2 * n,
+                              "speedup_of_batched": round(ms_sep / step_ms, 3)},
+        "roofline": {"bound": "alu+hbm", "ideal_ms": round(t_alu + t_hbm, 4), "frac": round((t_alu + t_hbm) / step_ms, 4),
+                     "alu_ms": round(t_alu, 4), "hbm_ms": round(t_hbm, 4),
+                     "algorithmic_per_step": f"{ms_pc_per_step()} pixel-candidates + {ms_prop_bytes_per_step()} "
+                                             "propagation bytes",
+                     "peak_source": "measured sad.u32 rate x SMs x median SM clock; MEASURED_PEAKS.json hbm_gbs "
+                                    "(of measured)"},
+        "gpu_launches": 2 * steps,
+        "l2": "inputs larger than L2 (2.2 GB of feature maps per step); no flush",
+    }
+
+
+def leg_refine_4k(h, clip, steps, warmup, peaks):
+    """Precision form at 4K: exhaustive search of the 7 pairs, bilinear
+    propagation of the 128-channel stride-4 NHWC maps, then the three 3x3 refine
+    convs in BF16 on the tensor cores (FP32 accumulation).  The FP32 SIMT run of
+    the convs is timed beside it; error against FP64 is a test's job."""
+    import torch
+    from paper_2508_05990_b300 import bayer_me as bm
+    from paper_2508_05990_b300 import synth
+    stream = torch.cuda.current_stream()
+    pairs = K4_T - 1
+    hf, wf = K4_H // K4_STRIDE, K4_W // K4_STRIDE
+    d_frames = torch.from_numpy(clip).cuda()
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(K4_SEED)
+    feats = torch.randn((pairs, hf, wf, K4_C), generator=gen, device="cuda")
+    warped = torch.empty_like(feats)
+    refined = torch.empty_like(feats)
+    theta = synth.he_normal_params(K4_SEED, [("w", (K4_HIDDEN, K4_C, 3, 3)), ("b", (K4_HIDDEN,)),
+                                             ("w", (K4_HIDDEN, K4_HIDDEN, 3, 3)), ("b", (K4_HIDDEN,)),
+                                             ("w", (K4_C, K4_HIDDEN, 3, 3)), ("b", (K4_C,))])
+    shapes = [(K4_HIDDEN, K4_C, 3, 3), (K4_HIDDEN,), (K4_HIDDEN, K4_HIDDEN, 3, 3), (K4_HIDDEN,),
+              (K4_C, K4_HIDDEN, 3, 3), (K4_C,)]
+    wts, o = [], 0
+    for shp in shapes:
+        nsz = int(np.prod(shp))
+        wts.append(torch.from_numpy(theta[o:o + nsz].astype(np.float32).reshape(shp)).cuda())
+        o += nsz
+    mv = torch.empty((pairs, K4_H // BLOCK, K4_W // BLOCK, 2), dtype=torch.int32, device="cuda")
+
+    def step(ev=None, prec=bm.PREC_BF16):
+        if ev is not None:
+            ev[0].record(stream)
+        h.estimate_ex(d_frames, d_frames[1:], search_range=RANGE, batch=pairs, ref_batch_stride=K4_H * K4_W,
+                      cur_batch_stride=K4_H * K4_W, out=mv, stream=stream)
+        if ev is not None:
+            ev[1].record(stream)
+        h.feat_propagate(feats, mv, BLOCK, K4_STRIDE, interp=bm.INTERP_BILINEAR, layout=bm.LAYOUT_NHWC,
+                         out=warped, stream=stream)
+        if ev is not None:
+            ev[2].record(stream)
+        h.refine_conv(warped, wts, precision=prec, out=refined, stream=stream)
+        if ev is not None:
+            ev[3].record(stream)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    if h.sync_status() != bm.OK:
+        raise RuntimeError("device status after 4K warm-up")
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    for k in range(steps):
+        step(evs[k])
+    torch.cuda.synchronize()
+    me = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    pr = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+    rf = statistics.mean(e[2].elapsed_time(e[3]) for e in evs)
+    total = statistics.mean(e[0].elapsed_time(e[3]) for e in evs)
+    out_bf16 = refined.clone()
+    # FP32 SIMT run of the convs on the same warped maps
+    fev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    h.refine_conv(warped, wts, precision=bm.PREC_FP32, out=refined, stream=stream)
+    fev[0].record(stream)
+    h.refine_conv(warped, wts, precision=bm.PREC_FP32, out=refined, stream=stream)
+    fev[1].record(stream)
+    torch.cuda.synchronize()
+    rf32 = fev[0].elapsed_time(fev[1])
+    diff = float((out_bf16 - refined).norm() / refined.norm())
+    if h.sync_status() != bm.OK:
+        raise RuntimeError("device status after 4K leg")
+    flops = pairs * refine_flops_per_frame()
+    peak = peaks.get("bf16_tflops_sustained", 1400.0)
+    t_alu_me = pairs * (K4_H // BLOCK) * (K4_W // BLOCK) * BLOCK * BLOCK * (RANGE + 1) ** 2
+    prop_bytes = pairs * (2 * K4_C * hf * wf * 4 + (K4_H // BLOCK) * (K4_W // BLOCK) * 8)
+    return {
+        "workload": "4K clip: 8 frames 3840x2160 RGGB uint16 12-bit; block 16 +-32 EVEN exhaustive; bilinear "
+                    "propagation of 128x540x960 NHWC float32 maps at stride 4; refine convs 128->64->64->128 "
+                    "(3x3, ReLU after the first two, He-normal weights)",
+        "value": round(pairs / (total / 1e3), 2), "unit": UNIT, "steps": steps, "warmup": warmup,
+        "ms_per_step": round(total, 4), "frames_per_step": pairs,
+        "me_ms": round(me, 4), "prop_ms": round(pr, 4), "refine_bf16_ms": round(rf, 4),
+        "refine_fp32_ms": round(rf32, 4),
+        "me_gpc_per_s": round(t_alu_me / (me / 1e3) / 1e9, 1),
+        "prop_gbs": round(prop_bytes / (pr / 1e3) / 1e9, 1),
+        "roofline": {"bound": "tensor", "kernel": "conv3x3_rows_tc_kernel (3 launches, BF16 operands, FP32 accumulate in TMEM)",
+                     "achieved": round(flops / (rf / 1e3) / 1e12, 1), "peak": peak, "unit": "TFLOP/s",
+                     "frac": round(flops / (rf / 1e3) / 1e12 / peak, 4),
+                     "algorithmic_per_launch_set": f"{flops} FLOP ({pairs} maps x {refine_flops_per_frame()})",
+                     "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)",
+                     "fp32_simt_tflops": round(flops / (rf32 / 1e3) / 1e12, 1)},
+        "bf16_vs_fp32_normwise": round(diff, 6),
+        "gpu_launches": 5 * steps,
+    }
+
+
 def run_ours(args):
     import torch
     rank, world, local = init_dist("nccl")
@@ -193,6 +430,14 @@ def run_ours(args):
     build.build()
 
     frames, feats = make_inputs(rank)
+    legs = world == 1 and not args.no_legs
+    leg_clips = None
+    if legs:  # batched multi-stream + 4K clips, generated on the host cores
+        tasks = [(MS_SEED + 10 * i, hh, ww, MS_FRAMES) for i, (hh, ww) in enumerate(MS_SIZES)]
+        tasks.append((K4_SEED, K4_H, K4_W, K4_T))
+        tasks.sort(key=lambda t: -t[1] * t[2])
+        got = dict(zip([t[0] for t in tasks], gen_clips(tasks)))
+        leg_clips = ([got[MS_SEED + 10 * i] for i in range(len(MS_SIZES))], got[K4_SEED])
     h = bm.Handle(local)
     stream = torch.cuda.current_stream()
     d_frames = torch.from_numpy(frames).cuda()
@@ -287,6 +532,24 @@ def run_ours(args):
             "gpu_launches": args.steps * 9,
         }
 
+    # ALU roofline: measured sad.u32 throughput per clock per SM x SMs x SM clock under load
+    pc_clk_sm, probe_mhz, nsm = h.probe_alu(0)
+    clocks = clk.summary(t_host0, t_host1)
+    sm_mhz = clocks["sm_mhz"] or probe_mhz
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+
+    multi_stream = refine_4k = None
+    if legs:
+        multi_stream = leg_multi_stream(h, leg_clips[0], steps=30, warmup=3, peaks=peaks, pc_clk_sm=pc_clk_sm,
+                                        nsm=nsm, sm_mhz=sm_mhz)
+        refine_4k = leg_refine_4k(h, leg_clips[1], steps=10, warmup=3, peaks=peaks)
+        leg_clips = None
+        torch.cuda.empty_cache()
+
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     pin_frames = torch.from_numpy(frames).pin_memory().numpy()
     pin_feats = torch.from_numpy(feats).pin_memory().numpy()
@@ -302,22 +565,13 @@ def run_ours(args):
     h2d = frames.nbytes + feats.nbytes
     d2h = pin_mv.nbytes + pin_out.nbytes
 
-    # ALU roofline: measured sad.u32 throughput per clock per SM x SMs x SM clock under load
-    pc_clk_sm, probe_mhz, nsm = h.probe_alu(0)
     result = None
     if rank == 0:
-        clocks = clk.summary(t_host0, t_host1)
-        sm_mhz = clocks["sm_mhz"] or probe_mhz
         me_avg_s = statistics.mean(me_ms) / 1e3
         achieved = PAIRS * pc_per_pair() / me_avg_s / 1e9
         peak = pc_clk_sm * nsm * sm_mhz * 1e6 / 1e9
         prop_avg_s = statistics.mean(prop_ms) / 1e3
         prop_gbs = PAIRS * prop_bytes_per_pair() / prop_avg_s / 1e9
-        peaks = {}
-        try:
-            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        except (OSError, ValueError):
-            pass
         hbm_peak = peaks.get("hbm_gbs", 6400.0)
         value = world * PAIRS * args.steps / (ms_total / 1e3)
         result = {
@@ -348,6 +602,8 @@ def run_ours(args):
             "gpu_launches": gpu_launches,
             "clocks": clocks,
             "learned_seeded": learned,
+            "multi_stream": multi_stream,
+            "precision_4k": refine_4k,
         }
         if not args.no_cpu_baseline:
             result["cpu_baseline"] = cpu_baseline_sample(frames, feats)
@@ -399,6 +655,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="skip the batched multi-stream and 4K precision legs (single-GPU runs only)")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         ap.error("--warmup must be >= 3")

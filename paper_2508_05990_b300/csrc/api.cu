@@ -202,6 +202,7 @@ bayer_status_t bayer_me_init(bayer_me_t* out, int device) {
   e = bme::configure_full16();
   if (e == cudaSuccess) e = bme::configure_full16_list();
   if (e == cudaSuccess) e = bme::configure_conv_tc();
+  if (e == cudaSuccess) e = bme::configure_conv_rows_tc();
   if (e == cudaSuccess) e = cudaMalloc(&h->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking);
@@ -569,52 +570,45 @@ bayer_status_t bayer_refine_conv(bayer_me_t h, const float* feat, int n, int Hf,
     if (e == cudaSuccess) e = bme::launch_conv3x3_f32(a2, n, Hf, Wf, hidden, w3, b3, C, false, out, st);
     return cuda_status(e);
   }
-  // bf16 copies of the parameters: w1 b1 w2 b2 w3 b3, each 64-byte aligned
-  const size_t nw[6] = {(size_t)hidden * C * 9, (size_t)hidden, (size_t)hidden * hidden * 9, (size_t)hidden,
-                        (size_t)C * hidden * 9, (size_t)C};
-  const float* src[6] = {w1, b1, w2, b2, w3, b3};
-  size_t off[6], total = 0;
-  for (int i = 0; i < 6; ++i) {
+  // weights packed into the row-stream kernel's shared-memory image (bf16), each 256-byte aligned
+  const int cins[3] = {C, hidden, hidden}, couts[3] = {hidden, hidden, C};
+  const float* ws[3] = {w1, w2, w3};
+  size_t off[3], total = 0;
+  for (int i = 0; i < 3; ++i) {
     off[i] = total;
-    total += (nw[i] + 31) / 32 * 32;
+    total += (bme::conv_rows_weight_bytes(cins[i], couts[i]) + 255) / 256 * 256;
   }
-  if ((s = grow(reinterpret_cast<char**>(&h->ref_w), &h->ref_w_bytes, total * 2)) != BAYER_OK) return s;
-  uint16_t* wb = static_cast<uint16_t*>(h->ref_w);
-  for (int i = 0; i < 6; ++i) {
-    e = bme::cnn_to_bf16(src[i], wb + off[i], (int)nw[i], st);
+  if ((s = grow(reinterpret_cast<char**>(&h->ref_w), &h->ref_w_bytes, total)) != BAYER_OK) return s;
+  char* wb = static_cast<char*>(h->ref_w);
+  for (int i = 0; i < 3; ++i) {
+    e = bme::pack_conv_rows_weights(ws[i], couts[i], cins[i], reinterpret_cast<uint16_t*>(wb + off[i]), st);
     if (e != cudaSuccess) return cuda_status(e);
   }
-  const __nv_bfloat16* W[6];
-  for (int i = 0; i < 6; ++i) W[i] = reinterpret_cast<const __nv_bfloat16*>(wb + off[i]);
   __nv_bfloat16* a1 = static_cast<__nv_bfloat16*>(h->ref_act);
   __nv_bfloat16* a2 = a1 + pix * hidden;
-  bme::ConvTcArgs c{};
-  c.Hi = Hf;
-  c.Wi = Wf;
-  c.Ho = Hf;
-  c.Wo = Wf;
+  bme::ConvRowsArgs c{};
+  c.H = Hf;
+  c.W = Wf;
   c.batch = n;
   c.status = h->d_status;
   c.in_f32 = feat;
-  c.w = W[0];
-  c.bias = W[1];
+  c.wimg = reinterpret_cast<const uint4*>(wb + off[0]);
+  c.bias = b1;
   c.out = a1;
-  c.cout = hidden;
-  e = bme::launch_conv_tc(c, C, 1, 2, 0, true, st);
+  e = bme::launch_conv_rows_tc(c, C, hidden, 2, 0, true, st);
   if (e != cudaSuccess) return cuda_status(e);
   c.in = a1;
-  c.w = W[2];
-  c.bias = W[3];
+  c.wimg = reinterpret_cast<const uint4*>(wb + off[1]);
+  c.bias = b2;
   c.out = a2;
-  e = bme::launch_conv_tc(c, hidden, 1, 0, 0, true, st);
+  e = bme::launch_conv_rows_tc(c, hidden, hidden, 0, 0, true, st);
   if (e != cudaSuccess) return cuda_status(e);
   c.in = a2;
-  c.w = W[4];
-  c.bias = W[5];
+  c.wimg = reinterpret_cast<const uint4*>(wb + off[2]);
+  c.bias = b3;
   c.out = nullptr;
   c.out_f32 = out;
-  c.cout = C;
-  e = bme::launch_conv_tc(c, hidden, 1, 0, 1, false, st);
+  e = bme::launch_conv_rows_tc(c, hidden, C, 0, 1, false, st);
   return cuda_status(e);
 }
 

@@ -283,10 +283,7 @@ cudaError_t configure_t() {
 cudaError_t configure_conv_tc() {
   cudaError_t e;
   if ((e = configure_t<16, 32, 2, 1, 0, true>()) != cudaSuccess) return e;
-  if ((e = configure_t<32, 32, 2, 0, 0, true>()) != cudaSuccess) return e;
-  if ((e = configure_t<128, 32, 1, 2, 0, true>()) != cudaSuccess) return e;
-  if ((e = configure_t<64, 64, 1, 0, 0, true>()) != cudaSuccess) return e;
-  return configure_t<64, 64, 1, 0, 1, false>();
+  return configure_t<32, 32, 2, 0, 0, true>();
 }
 
 cudaError_t launch_conv_tc(const ConvTcArgs& a, int cin, int stride, int src, int outf, bool relu, cudaStream_t st) {
@@ -294,9 +291,6 @@ cudaError_t launch_conv_tc(const ConvTcArgs& a, int cin, int stride, int src, in
     return launch_t<16, 32, 2, 1, 0, true>(a, st);
   if (cin == 32 && stride == 2 && src == 0 && outf == 0 && relu && a.cout == 32)
     return launch_t<32, 32, 2, 0, 0, true>(a, st);
-  if (cin == 128 && stride == 1 && src == 2 && outf == 0 && relu) return launch_t<128, 32, 1, 2, 0, true>(a, st);
-  if (cin == 64 && stride == 1 && src == 0 && outf == 0 && relu) return launch_t<64, 64, 1, 0, 0, true>(a, st);
-  if (cin == 64 && stride == 1 && src == 0 && outf == 1 && !relu) return launch_t<64, 64, 1, 0, 1, false>(a, st);
   return cudaErrorInvalidValue;
 }
 

@@ -90,6 +90,26 @@ cudaError_t configure_conv_tc();
 // cin/stride/src/outf/relu select an instantiated form; cout in the args.
 cudaError_t launch_conv_tc(const ConvTcArgs& a, int cin, int stride, int src, int outf, bool relu, cudaStream_t st);
 
+// 3x3 stride-1 convolution streamed row by row on the tensor cores
+// (conv_rows_tc.cu): NHWC input (bf16, or float32 rounded to bf16 when
+// staged), weights pre-packed by pack_conv_rows_weights into the kernel's
+// shared-memory image, float32 bias, bf16 or float32 NHWC output.
+struct ConvRowsArgs {
+  const __nv_bfloat16* in;  // src 0: [batch][H][W][cin] bf16
+  const float* in_f32;      // src 2: [batch][H][W][cin] float32
+  int H, W, batch;
+  const uint4* wimg;  // packed bf16 weights, conv_rows_weight_bytes(cin, cout) bytes, 16-byte aligned
+  const float* bias;  // [cout]
+  __nv_bfloat16* out;  // outf 0: [batch][H][W][cout] bf16
+  float* out_f32;      // outf 1: [batch][H][W][cout] float32
+  int* status;         // device status word: BAYER_ERR_TIMEOUT if a bounded wait expired
+};
+cudaError_t configure_conv_rows_tc();
+size_t conv_rows_weight_bytes(int cin, int cout);
+cudaError_t pack_conv_rows_weights(const float* w, int cout, int cin, uint16_t* img, cudaStream_t st);
+cudaError_t launch_conv_rows_tc(const ConvRowsArgs& a, int cin, int cout, int src, int outf, bool relu,
+                                cudaStream_t st);
+
 // 3x3 stride-1 convolution in float32 on the SIMT cores (refine_f32.cu):
 // NHWC float32 in and out, bias, optional ReLU.
 cudaError_t launch_conv3x3_f32(const float* in, int batch, int H, int W, int cin, const float* w, const float* bias,
