@@ -49,7 +49,8 @@ struct PropArgs {
   const bayer_mv_t* mv;
   int mv_h, mv_w;
   int cells;  // feature cells per block side = block / stride
-  int s;      // stride
+  int s;      // stride (a power of two dividing the block size)
+  int ls, lc;  // log2(s), log2(cells): filled in by launch_propagate
 };
 cudaError_t launch_propagate(const PropArgs& a, int layout, int interp, cudaStream_t st);
 

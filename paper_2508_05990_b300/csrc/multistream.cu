@@ -126,18 +126,18 @@ __global__ void __launch_bounds__(kPropThreads) ms_prop_kernel(const MsPair* __r
     const int cell = tile * kPropThreads + threadIdx.x;
     if (cell < cells) {
       const int fy = cell / P.Wf, fx = cell - fy * P.Wf;
-      const int cpb = 16 / P.stride;  // feature cells per block side
-      const bayer_mv_t mv = P.mv[(long long)(fy / cpb) * P.w + fx / cpb];
+      const int ls = __ffs(P.stride) - 1;  // stride: a power of two dividing 16
+      const bayer_mv_t mv = P.mv[(long long)(fy >> (4 - ls)) * P.w + (fx >> (4 - ls))];
       const int c0 = chunk * kPropCh;
       const int nc = min(kPropCh, P.C - c0);
       const float* in = P.feat + (long long)c0 * cells;
       float* out = P.fout + (long long)c0 * cells + cell;
       if (interp == BAYER_INTERP_NEAREST) {
-        const int sy = prop::clampi(fy + prop::rounddiv(mv.dy, P.stride), 0, P.Hf - 1);
-        const int sx = prop::clampi(fx + prop::rounddiv(mv.dx, P.stride), 0, P.Wf - 1);
+        const int sy = prop::clampi(fy + prop::rounddiv_pow2(mv.dy, ls), 0, P.Hf - 1);
+        const int sx = prop::clampi(fx + prop::rounddiv_pow2(mv.dx, ls), 0, P.Wf - 1);
         for (int c = 0; c < nc; ++c) __stcs(out + (long long)c * cells, __ldg(in + (long long)c * cells + sy * P.Wf + sx));
       } else {
-        const prop::Taps tp = prop::bilinear_taps(P.stride, P.Hf, P.Wf, fy, fx, mv);
+        const prop::Taps tp = prop::bilinear_taps(ls, P.Hf, P.Wf, fy, fx, mv);
         const int oa = tp.y0 * P.Wf + tp.x0, ob = tp.y0 * P.Wf + tp.x1;
         const int oc = tp.y1 * P.Wf + tp.x0, od = tp.y1 * P.Wf + tp.x1;
         float va[kPropCh], vb[kPropCh], vc[kPropCh], vd[kPropCh];

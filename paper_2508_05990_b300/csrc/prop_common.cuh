@@ -11,14 +11,14 @@ namespace prop {
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
-__device__ __forceinline__ int floordiv(int a, int b) {
-  int q = a / b;
-  if ((a % b != 0) && (a < 0)) --q;
-  return q;
-}
+// The feature stride s divides the block size (8, 16, 32 or 64), so s and the
+// cells per block side are powers of two: with ls = log2(s), floor(a / s) is
+// a >> ls, its remainder a & (s - 1), and r / s = r * 2^-ls exactly (the same
+// bits as the rounded quotient).
 
-__device__ __forceinline__ int rounddiv(int a, int b) {
-  return a >= 0 ? (2 * a + b) / (2 * b) : -((2 * (-a) + b) / (2 * b));
+// round(a / s), halves away from zero
+__device__ __forceinline__ int rounddiv_pow2(int a, int ls) {
+  return a >= 0 ? (2 * a + (1 << ls)) >> (ls + 1) : -((-2 * a + (1 << ls)) >> (ls + 1));
 }
 
 struct Taps {
@@ -26,11 +26,12 @@ struct Taps {
   float wy, wx, owy, owx;
 };
 
-__device__ __forceinline__ Taps bilinear_taps(int s, int Hf, int Wf, int fy, int fx, bayer_mv_t m) {
+__device__ __forceinline__ Taps bilinear_taps(int ls, int Hf, int Wf, int fy, int fx, bayer_mv_t m) {
   Taps t;
-  const int qy = floordiv(m.dy, s), qx = floordiv(m.dx, s);
-  t.wy = __fdiv_rn((float)(m.dy - qy * s), (float)s);
-  t.wx = __fdiv_rn((float)(m.dx - qx * s), (float)s);
+  const int qy = (int)m.dy >> ls, qx = (int)m.dx >> ls;
+  const float inv_s = __int_as_float((127 - ls) << 23);  // 2^-ls
+  t.wy = __fmul_rn((float)((int)m.dy & ((1 << ls) - 1)), inv_s);
+  t.wx = __fmul_rn((float)((int)m.dx & ((1 << ls) - 1)), inv_s);
   t.owy = __fsub_rn(1.0f, t.wy);
   t.owx = __fsub_rn(1.0f, t.wx);
   t.y0 = clampi(fy + qy, 0, Hf - 1);

@@ -13,8 +13,10 @@
 //         MV lookup and tap arithmetic are paid once per chunk, all tap loads
 //         of the chunk are in flight together, and every plane's store is a
 //         coalesced 128-byte warp row.
-//   NHWC: one thread per (cell, 4 channels) moves float4 vectors (taps are
-//         contiguous C-vectors), fully coalesced.
+//   NHWC: one thread per (cell, 4 channels) of a feature row moves float4
+//         vectors (taps are contiguous C-vectors), fully coalesced.
+// Stride and cells per block are powers of two: all index divisions by them
+// are shifts.
 #include "common.cuh"
 #include "kernels.cuh"
 #include "prop_common.cuh"
@@ -39,13 +41,13 @@ __global__ void __launch_bounds__(256) prop_nchw_kernel(const PropArgs a, int nc
   const int m = blockIdx.y / nchunks;
   const int c0 = (blockIdx.y - m * nchunks) * kCK;
   const int fy = cell / a.Wf, fx = cell - fy * a.Wf;
-  const bayer_mv_t mv = a.mv[((long long)m * a.mv_h + fy / a.cells) * a.mv_w + fx / a.cells];
+  const bayer_mv_t mv = a.mv[((long long)m * a.mv_h + (fy >> a.lc)) * a.mv_w + (fx >> a.lc)];
   const float* in = a.feat + ((long long)m * a.C + c0) * cells;
   float* out = a.out + ((long long)m * a.C + c0) * cells + cell;
   const int nc = min(kCK, a.C - c0);
   if (INTERP == BAYER_INTERP_NEAREST) {
-    const int sy = clampi(fy + rounddiv(mv.dy, a.s), 0, a.Hf - 1);
-    const int sx = clampi(fx + rounddiv(mv.dx, a.s), 0, a.Wf - 1);
+    const int sy = clampi(fy + rounddiv_pow2(mv.dy, a.ls), 0, a.Hf - 1);
+    const int sx = clampi(fx + rounddiv_pow2(mv.dx, a.ls), 0, a.Wf - 1);
     const float* src = in + sy * a.Wf + sx;
     if (nc == kCK) {
       float v[kCK];
@@ -57,7 +59,7 @@ __global__ void __launch_bounds__(256) prop_nchw_kernel(const PropArgs a, int nc
       for (int c = 0; c < nc; ++c) __stcs(out + (long long)c * cells, __ldg(src + (long long)c * cells));
     }
   } else {
-    const Taps tp = bilinear_taps(a.s, a.Hf, a.Wf, fy, fx, mv);
+    const Taps tp = bilinear_taps(a.ls, a.Hf, a.Wf, fy, fx, mv);
     const int oa = tp.y0 * a.Wf + tp.x0, ob = tp.y0 * a.Wf + tp.x1;
     const int oc = tp.y1 * a.Wf + tp.x0, od = tp.y1 * a.Wf + tp.x1;
     if (nc == kCK) {
@@ -81,31 +83,30 @@ __global__ void __launch_bounds__(256) prop_nchw_kernel(const PropArgs a, int nc
   }
 }
 
-// NHWC with C % 4 == 0: one thread per (map, cell, 4 channels).
+// NHWC with C % 4 == 0: one thread per (cell, 4 channels) of one feature row
+// (grid.x = row's float4 vectors / 256, grid.y = fy, grid.z = map); c4n =
+// C / 4 float4 vectors per cell, lc4 = log2(c4n) when that is a power of two
+// (else -1: divide).
 template <int INTERP>
-__global__ void __launch_bounds__(256) prop_nhwc4_kernel(const PropArgs a) {
-  const int c4n = a.C >> 2;
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long cells = (long long)a.Hf * a.Wf;
-  if (t >= (long long)a.n * cells * c4n) return;
-  const int c4 = (int)(t % c4n);
-  const long long cell = t / c4n;
-  const int m = (int)(cell / cells);
-  const int rem = (int)(cell - (long long)m * cells);
-  const int fy = rem / a.Wf, fx = rem - fy * a.Wf;
-  const bayer_mv_t mv = a.mv[((long long)m * a.mv_h + fy / a.cells) * a.mv_w + fx / a.cells];
-  const float4* in = reinterpret_cast<const float4*>(a.feat + (long long)m * cells * a.C);
-  float4* out = reinterpret_cast<float4*>(a.out) + t;
+__global__ void __launch_bounds__(256) prop_nhwc4_kernel(const PropArgs a, int c4n, int lc4) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= a.Wf * c4n) return;
+  const int fy = blockIdx.y, m = blockIdx.z;
+  const int fx = lc4 >= 0 ? t >> lc4 : t / c4n;
+  const int c4 = t - fx * c4n;
+  const bayer_mv_t mv = a.mv[((long long)m * a.mv_h + (fy >> a.lc)) * a.mv_w + (fx >> a.lc)];
+  const float4* in = reinterpret_cast<const float4*>(a.feat) + (long long)m * a.Hf * a.Wf * c4n + c4;
+  float4* out = reinterpret_cast<float4*>(a.out) + ((long long)m * a.Hf + fy) * a.Wf * c4n + t;
   if (INTERP == BAYER_INTERP_NEAREST) {
-    const int sy = clampi(fy + rounddiv(mv.dy, a.s), 0, a.Hf - 1);
-    const int sx = clampi(fx + rounddiv(mv.dx, a.s), 0, a.Wf - 1);
-    __stcs(out, __ldg(in + ((long long)sy * a.Wf + sx) * c4n + c4));
+    const int sy = clampi(fy + rounddiv_pow2(mv.dy, a.ls), 0, a.Hf - 1);
+    const int sx = clampi(fx + rounddiv_pow2(mv.dx, a.ls), 0, a.Wf - 1);
+    __stcs(out, __ldg(in + (long long)(sy * a.Wf + sx) * c4n));
   } else {
-    const Taps tp = bilinear_taps(a.s, a.Hf, a.Wf, fy, fx, mv);
-    const float4 va = __ldg(in + ((long long)tp.y0 * a.Wf + tp.x0) * c4n + c4);
-    const float4 vb = __ldg(in + ((long long)tp.y0 * a.Wf + tp.x1) * c4n + c4);
-    const float4 vc = __ldg(in + ((long long)tp.y1 * a.Wf + tp.x0) * c4n + c4);
-    const float4 vd = __ldg(in + ((long long)tp.y1 * a.Wf + tp.x1) * c4n + c4);
+    const Taps tp = bilinear_taps(a.ls, a.Hf, a.Wf, fy, fx, mv);
+    const float4 va = __ldg(in + (long long)(tp.y0 * a.Wf + tp.x0) * c4n);
+    const float4 vb = __ldg(in + (long long)(tp.y0 * a.Wf + tp.x1) * c4n);
+    const float4 vc = __ldg(in + (long long)(tp.y1 * a.Wf + tp.x0) * c4n);
+    const float4 vd = __ldg(in + (long long)(tp.y1 * a.Wf + tp.x1) * c4n);
     float4 r;
     r.x = blend(tp, va.x, vb.x, vc.x, vd.x);
     r.y = blend(tp, va.y, vb.y, vc.y, vd.y);
@@ -126,14 +127,14 @@ __global__ void __launch_bounds__(256) prop_nhwc1_kernel(const PropArgs a) {
   const int m = (int)(cell / cells);
   const int rem = (int)(cell - (long long)m * cells);
   const int fy = rem / a.Wf, fx = rem - fy * a.Wf;
-  const bayer_mv_t mv = a.mv[((long long)m * a.mv_h + fy / a.cells) * a.mv_w + fx / a.cells];
+  const bayer_mv_t mv = a.mv[((long long)m * a.mv_h + (fy >> a.lc)) * a.mv_w + (fx >> a.lc)];
   const float* in = a.feat + (long long)m * cells * a.C;
   if (INTERP == BAYER_INTERP_NEAREST) {
-    const int sy = clampi(fy + rounddiv(mv.dy, a.s), 0, a.Hf - 1);
-    const int sx = clampi(fx + rounddiv(mv.dx, a.s), 0, a.Wf - 1);
+    const int sy = clampi(fy + rounddiv_pow2(mv.dy, a.ls), 0, a.Hf - 1);
+    const int sx = clampi(fx + rounddiv_pow2(mv.dx, a.ls), 0, a.Wf - 1);
     a.out[t] = __ldg(in + ((long long)sy * a.Wf + sx) * a.C + c);
   } else {
-    const Taps tp = bilinear_taps(a.s, a.Hf, a.Wf, fy, fx, mv);
+    const Taps tp = bilinear_taps(a.ls, a.Hf, a.Wf, fy, fx, mv);
     a.out[t] = blend(tp, __ldg(in + ((long long)tp.y0 * a.Wf + tp.x0) * a.C + c),
                      __ldg(in + ((long long)tp.y0 * a.Wf + tp.x1) * a.C + c),
                      __ldg(in + ((long long)tp.y1 * a.Wf + tp.x0) * a.C + c),
@@ -141,11 +142,22 @@ __global__ void __launch_bounds__(256) prop_nhwc1_kernel(const PropArgs a) {
   }
 }
 
+inline int log2_exact(int v) {  // log2 of a power of two, else -1
+  if (v <= 0 || (v & (v - 1))) return -1;
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+
 inline unsigned blocks_for(long long threads, int per) { return (unsigned)((threads + per - 1) / per); }
 
 }  // namespace
 
-cudaError_t launch_propagate(const PropArgs& a, int layout, int interp, cudaStream_t st) {
+cudaError_t launch_propagate(const PropArgs& args, int layout, int interp, cudaStream_t st) {
+  PropArgs a = args;
+  a.ls = log2_exact(a.s);
+  a.lc = log2_exact(a.cells);
+  if (a.ls < 0 || a.lc < 0) return cudaErrorInvalidValue;  // stride and block are powers of two
   const long long cells = (long long)a.n * a.Hf * a.Wf;
   if (cells == 0 || a.C == 0) return cudaSuccess;
   if (layout == BAYER_LAYOUT_NCHW) {
@@ -157,12 +169,14 @@ cudaError_t launch_propagate(const PropArgs& a, int layout, int interp, cudaStre
     else
       prop_nchw_kernel<BAYER_INTERP_BILINEAR><<<g, 256, 0, st>>>(a, nchunks);
   } else if ((a.C & 3) == 0 && (reinterpret_cast<uintptr_t>(a.feat) & 15) == 0 &&
-             (reinterpret_cast<uintptr_t>(a.out) & 15) == 0) {
-    const unsigned g = blocks_for(cells * (a.C >> 2), 256);
+             (reinterpret_cast<uintptr_t>(a.out) & 15) == 0 && a.n <= 65535 && a.Hf <= 65535 &&
+             (long long)a.Hf * a.Wf * (a.C >> 2) < (1ll << 31) - 256) {
+    const int c4n = a.C >> 2;
+    dim3 g(blocks_for((long long)a.Wf * c4n, 256), a.Hf, a.n);
     if (interp == BAYER_INTERP_NEAREST)
-      prop_nhwc4_kernel<BAYER_INTERP_NEAREST><<<g, 256, 0, st>>>(a);
+      prop_nhwc4_kernel<BAYER_INTERP_NEAREST><<<g, 256, 0, st>>>(a, c4n, log2_exact(c4n));
     else
-      prop_nhwc4_kernel<BAYER_INTERP_BILINEAR><<<g, 256, 0, st>>>(a);
+      prop_nhwc4_kernel<BAYER_INTERP_BILINEAR><<<g, 256, 0, st>>>(a, c4n, log2_exact(c4n));
   } else {
     const unsigned g = blocks_for(cells * a.C, 256);
     if (interp == BAYER_INTERP_NEAREST)

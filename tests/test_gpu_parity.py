@@ -226,6 +226,20 @@ def test_propagate_batched_1080p(handle):
         np.testing.assert_array_equal(g[t].view(np.uint32), expect.view(np.uint32))
 
 
+@pytest.mark.parametrize("layout", [bm.LAYOUT_NHWC, bm.LAYOUT_NCHW])
+def test_propagate_4k_full(handle, layout):
+    """The 4K precision form's propagation: one 128 x 540 x 960 float32 map at
+    stride 4 (3840 x 2160 frame, 240 x 135 blocks), bilinear, every output bit
+    for bit against the oracle."""
+    B, s, C, Hf, Wf = 16, 4, 128, 540, 960
+    mv = _mv_field(2002, 135, 240, B, 2160, 3840)
+    feat = synth.features(2003, C, Hf, Wf, layout="NCHW" if layout == bm.LAYOUT_NCHW else "NHWC")[0]
+    out = handle.feat_propagate(dev(feat), _records(mv), B, s, interp=bm.INTERP_BILINEAR, layout=layout)
+    g = out[0].cpu().numpy()
+    expect = oracle.propagate(feat, mv, B, s, interp=bm.INTERP_BILINEAR, layout=layout)
+    np.testing.assert_array_equal(g.view(np.uint32), expect.view(np.uint32))
+
+
 # ----------------------------------------------------------------------------
 # end-to-end host path, argument errors, probe
 # ----------------------------------------------------------------------------
