@@ -9,10 +9,10 @@
 // order.  Indices are clamped to the map.
 //
 // HBM-bound: per map C*Hf*Wf*4 bytes read once and written once.
-//   NCHW: one thread per output cell (fy, fx) and chunk of 8 channels; the
-//         MV lookup and tap arithmetic are paid once per chunk, all tap loads
-//         of the chunk are in flight together, and every plane's store is a
-//         coalesced 128-byte warp row.
+//   NCHW: bilinear with two or more cells per block side -- one thread per
+//         2 x 2 quad of cells (they share the MV: 9 tap loads per channel for
+//         4 outputs) and chunk of 4 channels; otherwise one thread per cell and
+//         chunk of 8 channels.
 //   NHWC: one thread per (cell, 4 channels) of a feature row moves float4
 //         vectors (taps are contiguous C-vectors), fully coalesced.
 // Stride and cells per block are powers of two: all index divisions by them
@@ -78,6 +78,63 @@ __global__ void __launch_bounds__(256) prop_nchw_kernel(const PropArgs a, int nc
       for (int c = 0; c < nc; ++c) {
         const float* pl = in + (long long)c * cells;
         __stcs(out + (long long)c * cells, blend(tp, __ldg(pl + oa), __ldg(pl + ob), __ldg(pl + oc), __ldg(pl + od)));
+      }
+    }
+  }
+}
+
+// NCHW bilinear, two or more feature cells per block side: one thread per
+// 2 x 2 quad of cells (fy, fx even) and chunk of kQK channels.  The quad's
+// cells share one MV, so their 16 taps are the 3 x 3 grid rows y0..y0+2 x
+// columns x0..x0+2 (each clamped exactly as for a single cell): 9 loads per
+// channel instead of 16, and each output row pair is a float2 store where
+// the quad is whole and Wf is even.  Warps run along quad rows.
+constexpr int kQK = 4;
+constexpr int kQT = 128;
+
+__global__ void __launch_bounds__(kQT) prop_nchw_quad_kernel(const PropArgs a, int nchunks, int qw, int nquads) {
+  const int q = blockIdx.x * kQT + threadIdx.x;
+  if (q >= nquads) return;
+  const int cells = a.Hf * a.Wf;
+  const int m = blockIdx.y / nchunks;
+  const int c0 = (blockIdx.y - m * nchunks) * kQK;
+  const int qy = q / qw, qx = q - qy * qw;
+  const int fy = 2 * qy, fx = 2 * qx;
+  const bayer_mv_t mv = a.mv[((long long)m * a.mv_h + (fy >> a.lc)) * a.mv_w + (fx >> a.lc)];
+  const Taps tp = bilinear_taps(a.ls, a.Hf, a.Wf, fy, fx, mv);
+  const int oy = (int)mv.dy >> a.ls, ox = (int)mv.dx >> a.ls;
+  int ry[3], rx[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    ry[i] = clampi(fy + oy + i, 0, a.Hf - 1) * a.Wf;
+    rx[i] = clampi(fx + ox + i, 0, a.Wf - 1);
+  }
+  const float* in = a.feat + ((long long)m * a.C + c0) * cells;
+  float* out = a.out + ((long long)m * a.C + c0) * cells + fy * a.Wf + fx;
+  const int nc = min(kQK, a.C - c0);
+  const bool row2 = fy + 1 < a.Hf, col2 = fx + 1 < a.Wf;
+  const bool pair_store = col2 && (a.Wf & 1) == 0;
+#pragma unroll
+  for (int c = 0; c < kQK; ++c) {
+    if (c >= nc) break;
+    const float* pl = in + (long long)c * cells;
+    float v[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) v[3 * i + j] = __ldg(pl + ry[i] + rx[j]);
+    const float r00 = blend(tp, v[0], v[1], v[3], v[4]), r01 = blend(tp, v[1], v[2], v[4], v[5]);
+    const float r10 = blend(tp, v[3], v[4], v[6], v[7]), r11 = blend(tp, v[4], v[5], v[7], v[8]);
+    float* o = out + (long long)c * cells;
+    if (pair_store) {
+      __stcs(reinterpret_cast<float2*>(o), make_float2(r00, r01));
+      if (row2) __stcs(reinterpret_cast<float2*>(o + a.Wf), make_float2(r10, r11));
+    } else {
+      __stcs(o, r00);
+      if (col2) __stcs(o + 1, r01);
+      if (row2) {
+        __stcs(o + a.Wf, r10);
+        if (col2) __stcs(o + a.Wf + 1, r11);
       }
     }
   }
@@ -160,7 +217,13 @@ cudaError_t launch_propagate(const PropArgs& args, int layout, int interp, cudaS
   if (a.ls < 0 || a.lc < 0) return cudaErrorInvalidValue;  // stride and block are powers of two
   const long long cells = (long long)a.n * a.Hf * a.Wf;
   if (cells == 0 || a.C == 0) return cudaSuccess;
-  if (layout == BAYER_LAYOUT_NCHW) {
+  if (layout == BAYER_LAYOUT_NCHW && interp == BAYER_INTERP_BILINEAR && a.lc >= 1 &&
+      (long long)a.n * ((a.C + kQK - 1) / kQK) <= 65535 && (long long)a.Hf * a.Wf <= (1ll << 31) - 256) {
+    const int nchunks = (a.C + kQK - 1) / kQK;
+    const int qw = (a.Wf + 1) / 2, nquads = ((a.Hf + 1) / 2) * qw;
+    dim3 g(blocks_for(nquads, kQT), a.n * nchunks);
+    prop_nchw_quad_kernel<<<g, kQT, 0, st>>>(a, nchunks, qw, nquads);
+  } else if (layout == BAYER_LAYOUT_NCHW) {
     const int nchunks = (a.C + kCK - 1) / kCK;
     if ((long long)a.n * nchunks > 65535 || (long long)a.Hf * a.Wf > (1ll << 31) - 256) return cudaErrorInvalidValue;
     dim3 g(blocks_for((long long)a.Hf * a.Wf, 256), a.n * nchunks);

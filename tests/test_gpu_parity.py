@@ -195,7 +195,8 @@ def _records(mv):
     return dev(np.ascontiguousarray(mv).view(np.int32).reshape(mv.shape + (2,)))
 
 
-@pytest.mark.parametrize("C,Hf,Wf,stride", [(64, 64, 64, 4), (256, 136, 240, 8), (7, 20, 36, 2), (3, 9, 13, 4)])
+@pytest.mark.parametrize("C,Hf,Wf,stride", [(64, 64, 64, 4), (256, 136, 240, 8), (7, 20, 36, 2), (3, 9, 13, 4),
+                                          (6, 11, 7, 8), (5, 8, 12, 16)])
 @pytest.mark.parametrize("interp", [bm.INTERP_NEAREST, bm.INTERP_BILINEAR])
 @pytest.mark.parametrize("layout", [bm.LAYOUT_NCHW, bm.LAYOUT_NHWC])
 def test_propagate(handle, C, Hf, Wf, stride, interp, layout):
