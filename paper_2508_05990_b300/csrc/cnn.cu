@@ -12,7 +12,9 @@
 //   dx = range*tanh(z_0), dy = range*tanh(z_1), conf = sigmoid(z_2)
 // Activations are NHWC bf16 [B][H][W][32].  The four convolutions run on the
 // tensor cores (conv_tc.cu; layer 1 gathers the Bayer frames directly, the
-// packing fused into its operand staging); head, loss and backward are SIMT.  Loss per block:
+// packing fused into its operand staging; in inference the head is evaluated
+// in layer 4's epilogue); the training head, loss and backward are SIMT.
+// Loss per block:
 //   BerHu_4(dx - dx*) + BerHu_4(dy - dy*) - t log(conf) - w_neg (1 - t) log(1 - conf),
 //   t = [round_even(dx) within +-4 of dx* and likewise for dy],
 // averaged over all blocks of the batch.
@@ -53,41 +55,6 @@ __device__ __forceinline__ float l1_input(const uint16_t* ref, const uint16_t* c
 // ---------------------------------------------------------------------------
 // forward
 // ---------------------------------------------------------------------------
-
-// Head: one thread per L4 cell -> 4 blocks' (dx, dy, conf).
-__global__ void __launch_bounds__(128) head_fwd_kernel(const __nv_bfloat16* __restrict__ x4, int H4, int W4,
-                                                       const __nv_bfloat16* __restrict__ w, int range,
-                                                       float* __restrict__ prop, float* __restrict__ conf) {
-  __shared__ float wh[12 * kC + 12];
-  for (int i = threadIdx.x; i < 12 * kC + 12; i += blockDim.x) wh[i] = bf(w[BAYER_CNN_WH + i]);
-  __syncthreads();
-  const int cells = H4 * W4;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int b = blockIdx.y;
-  if (t >= cells) return;
-  const int i = t / W4, k = t - i * W4;
-  float x[kC];
-  const uint4* src = reinterpret_cast<const uint4*>(x4 + ((long long)b * cells + t) * kC);
-#pragma unroll
-  for (int q = 0; q < 4; ++q) unpack8(__ldg(src + q), x + 8 * q);
-  const int h = 2 * H4, wb = 2 * W4;
-#pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    float z[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const int j = 3 * s + q;
-      float a = wh[12 * kC + j];
-#pragma unroll
-      for (int c = 0; c < kC; ++c) a = fmaf(wh[j * kC + c], x[c], a);
-      z[q] = a;
-    }
-    const long long blk = ((long long)b * h + 2 * i + (s >> 1)) * wb + 2 * k + (s & 1);
-    prop[2 * blk] = (float)range * tanhf(z[0]);
-    prop[2 * blk + 1] = (float)range * tanhf(z[1]);
-    conf[blk] = 1.0f / (1.0f + expf(-z[2]));
-  }
-}
 
 // ---------------------------------------------------------------------------
 // training: loss and gradients
@@ -336,22 +303,31 @@ CnnShapes cnn_shapes(int W, int H) {
   return s;
 }
 
-size_t cnn_act_bytes(int W, int H, int batch) {
-  const CnnShapes s = cnn_shapes(W, H);
+namespace {
+
+size_t act_elems(const CnnShapes& s, int batch) {
   size_t n = 0;
   for (int l = 1; l <= 4; ++l) n += (size_t)s.H[l] * s.W[l] * kC;
-  return n * batch * sizeof(__nv_bfloat16);
+  return n * batch;
 }
 
-size_t cnn_grad_bytes(int W, int H, int batch) {
-  const CnnShapes s = cnn_shapes(W, H);
+// Workspace: the bf16 activations of layers 1..4, then the packed weight
+// images of the four convolutions (256-byte aligned).
+size_t wimg_offset(int W, int H, int batch) {
+  return (act_elems(cnn_shapes(W, H), batch) * sizeof(__nv_bfloat16) + 255) / 256 * 256;
+}
+
+size_t wimg_bytes() {
   size_t n = 0;
-  for (int l = 1; l <= 4; ++l) n += (size_t)s.H[l] * s.W[l] * kC;
-  return n * batch * sizeof(float);
+  for (int l = 1; l <= 4; ++l) n += (conv_tc_weight_bytes(l == 1 ? 16 : 32) + 255) / 256 * 256;
+  return n;
 }
 
-cudaError_t cnn_forward_acts(const CnnFrames& fr, int batch, const uint16_t* wbf16, void* acts, int* status,
-                             cudaStream_t st) {
+// Forward through the four convolutions.  head: layer 4's epilogue evaluates
+// the head (activations of layer 4 are then not stored); otherwise all four
+// layers' activations are written.
+cudaError_t cnn_forward_acts(const CnnFrames& fr, int batch, const uint16_t* wbf16, void* acts, int* status, bool head,
+                             int range, float* prop, float* conf, cudaStream_t st) {
   const CnnShapes s = cnn_shapes(fr.W, fr.H);
   const __nv_bfloat16* w = reinterpret_cast<const __nv_bfloat16*>(wbf16);
   __nv_bfloat16* a[5];
@@ -359,44 +335,62 @@ cudaError_t cnn_forward_acts(const CnnFrames& fr, int batch, const uint16_t* wbf
   for (int l = 2; l <= 4; ++l) a[l] = a[l - 1] + (size_t)batch * s.H[l - 1] * s.W[l - 1] * kC;
   const int woff[5] = {0, BAYER_CNN_W1, BAYER_CNN_W2, BAYER_CNN_W3, BAYER_CNN_W4};
   const int boff[5] = {0, BAYER_CNN_B1, BAYER_CNN_B2, BAYER_CNN_B3, BAYER_CNN_B4};
+  char* img = static_cast<char*>(acts) + wimg_offset(fr.W, fr.H, batch);
+  const uint4* wimg[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  size_t img_off[4];
+  size_t off = 0;
+  for (int l = 1; l <= 4; ++l) {
+    img_off[l - 1] = off;
+    wimg[l] = reinterpret_cast<const uint4*>(img + off);
+    off += (conv_tc_weight_bytes(l == 1 ? 16 : 32) + 255) / 256 * 256;
+  }
+  cudaError_t e0 = pack_conv_tc_weights(wbf16, woff + 1, img_off, reinterpret_cast<uint16_t*>(img), st);
+  if (e0 != cudaSuccess) return e0;
+  const bool vec = (reinterpret_cast<uintptr_t>(fr.ref) % 16) == 0 && (reinterpret_cast<uintptr_t>(fr.cur) % 16) == 0 &&
+                   fr.pitch % 8 == 0 && fr.ref_bs % 8 == 0 && fr.cur_bs % 8 == 0 && s.W[0] % 4 == 0;
   for (int l = 1; l <= 4; ++l) {
     ConvTcArgs c{};
     c.in = l == 1 ? nullptr : a[l - 1];
     c.fr = fr;
+    c.vec = vec;
     c.Hi = s.H[l - 1];
     c.Wi = s.W[l - 1];
-    c.w = w + woff[l];
+    c.wimg = wimg[l];
     c.bias = w + boff[l];
     c.out = a[l];
     c.Ho = s.H[l];
     c.Wo = s.W[l];
     c.batch = batch;
-    c.cout = 32;
     c.status = status;
-    cudaError_t e = launch_conv_tc(c, l == 1 ? 16 : 32, 2, l == 1 ? 1 : 0, 0, true, st);
+    const bool fuse = head && l == 4;
+    if (fuse) {
+      c.whead = w + BAYER_CNN_WH;
+      c.prop = prop;
+      c.conf = conf;
+      c.range = range;
+    }
+    cudaError_t e = launch_conv_tc(c, l, fuse, st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
 
+}  // namespace
+
+size_t cnn_act_bytes(int W, int H, int batch) { return wimg_offset(W, H, batch) + wimg_bytes(); }
+
+size_t cnn_grad_bytes(int W, int H, int batch) { return act_elems(cnn_shapes(W, H), batch) * sizeof(float); }
+
 cudaError_t cnn_forward(const CnnFrames& fr, int batch, const uint16_t* wbf16, int range, void* acts, float* prop,
                         float* conf, int* status, cudaStream_t st) {
-  cudaError_t e = cnn_forward_acts(fr, batch, wbf16, acts, status, st);
-  if (e != cudaSuccess) return e;
-  const CnnShapes s = cnn_shapes(fr.W, fr.H);
-  const __nv_bfloat16* a4 = static_cast<const __nv_bfloat16*>(acts);
-  for (int l = 1; l <= 3; ++l) a4 += (size_t)batch * s.H[l] * s.W[l] * kC;
-  dim3 g((s.H[4] * s.W[4] + 127) / 128, batch);
-  head_fwd_kernel<<<g, 128, 0, st>>>(a4, s.H[4], s.W[4], reinterpret_cast<const __nv_bfloat16*>(wbf16), range, prop,
-                                     conf);
-  return cudaGetLastError();
+  return cnn_forward_acts(fr, batch, wbf16, acts, status, true, range, prop, conf, st);
 }
 
 cudaError_t cnn_loss_grad(const CnnFrames& fr, int batch, const uint16_t* wbf16, const bayer_mv_t* labels, int range,
                           float neg_weight, void* acts, void* dpre, float* grad, float* loss, int* status,
                           cudaStream_t st) {
   const CnnShapes s = cnn_shapes(fr.W, fr.H);
-  cudaError_t e = cnn_forward_acts(fr, batch, wbf16, acts, status, st);
+  cudaError_t e = cnn_forward_acts(fr, batch, wbf16, acts, status, false, range, nullptr, nullptr, st);
   if (e != cudaSuccess) return e;
   const __nv_bfloat16* w = reinterpret_cast<const __nv_bfloat16*>(wbf16);
   const __nv_bfloat16* a[5];

@@ -1,25 +1,33 @@
-// 3x3 convolution (zero pad 1, stride 1 or 2) as an implicit GEMM on the 5th-
-// generation tensor cores: BF16 operands in shared memory, FP32 accumulators
-// in tensor memory (TMEM), bias + optional ReLU epilogue, BF16 NHWC output.
+// 3x3 stride-2 convolution (zero pad 1), 32 output channels, as an implicit
+// GEMM on the 5th-generation tensor cores: BF16 operands in shared memory,
+// FP32 accumulators in tensor memory (TMEM) -- the four layers of the
+// learned proposal network.
 //
 //   D[m, n] = sum_k A[m, k] * B[k, n],  m = output pixel, n = output channel,
-//   k = tap * CIN + ci,  A[m, k] = input at (S*oy + ky - 1, S*ox + kx - 1, ci).
+//   k = tap * CIN + ci,  A[m, k] = input at (2*oy + ky - 1, 2*ox + kx - 1, ci).
 //
-// Tile = 128 consecutive output pixels of one output row (MMA M = 128,
-// N = COUT); CTA = 128 threads, persistent over tiles, all nine taps' weights
-// resident in shared memory.  Per tile the CTA stages the three input rows
-// once (coalesced 16-byte loads; no im2col copy), after one barrier thread 0
-// issues 9 * CIN/16 MMAs whose A operands are shifted views of the staged rows
-// and commits them to an mbarrier that gates the epilogue (TMEM -> registers
-// -> bias, ReLU, bf16 -> global).  Several CTAs per SM overlap one tile's
-// staging with another's MMAs and epilogue.  Every mbarrier wait is bounded;
-// on expiry the kernel records BAYER_ERR_TIMEOUT in the status word, frees its
-// TMEM and finishes.
+// Tile = 128 consecutive output pixels of one output row (MMA M = 128, N = 32);
+// CTA = 128 threads, persistent over tiles.
+//   Prologue: the layer's weights, packed once per forward into this kernel's
+//   shared-memory image (one launch of pack_conv_tc_weights for all four
+//   layers), are copied in with 16-byte loads and stay resident.
+//   Staging: per tile the three input rows, once (no im2col copy).  NHWC bf16
+//   input goes through asynchronous 16-byte copies (cp.async, zero-filled
+//   outside the map), so every load of the tile is in flight at once; layer 1
+//   gathers the Bayer frames with 16-byte loads and splits them into operand
+//   channels while storing.
+//   MMA: after one barrier thread 0 issues 9 * CIN/16 MMAs whose A operands
+//   are shifted views of the staged rows and commits them to an mbarrier.
+//   Epilogue: TMEM -> registers -> bias, ReLU -> bf16 NHWC, or, for layer 4
+//   with the head fused, the 1x1 head, tanh and sigmoid straight to the
+//   per-block proposals.
+// Several CTAs per SM overlap one tile's staging with another's MMAs and
+// epilogue.  Every mbarrier wait is bounded; on expiry the kernel records
+// BAYER_ERR_TIMEOUT in the status word, frees its TMEM and finishes.
 //
-// SRC 1 (layer 1 of the proposal network) gathers straight from the Bayer
-// frames: the 8 half-resolution planes x = v/2048 - 1 are split exactly into
-// two bf16 channels, hi = (v >> 4)/128 - 1 and lo = (v & 15)/16, with weights w
-// and w/128, so that hi*w + lo*(w/128) = x*w exactly.
+// Layer 1 reads the Bayer frames directly: the 8 half-resolution planes
+// x = v/2048 - 1 are split exactly into two bf16 channels, hi = (v >> 4)/128 - 1
+// and lo = (v & 15)/16, with weights w and w/128, so that hi*w + lo*(w/128) = x*w.
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -30,26 +38,30 @@ namespace bme {
 
 namespace {
 
-constexpr int kM = 128;  // output pixels per tile (MMA M)
+constexpr int kM = 128;    // output pixels per tile (MMA M)
+constexpr int kN = 32;     // output channels (MMA N)
+constexpr int kS = 2;      // stride
+constexpr int kHeadW = 12 * kN + 12;  // head weights + biases
 constexpr uint32_t kWaitLimit = 1u << 20;
 
 // Shared-memory plan of one CTA.  The three input rows a tile needs are staged
-// once, split into S column-parity planes (S = stride) and into 16-byte
-// channel chunks: element (row rho, plane q, chunk kc, pixel p) at
-// (((rho*S + q)*KC + kc)*NP + p)*16.  Output pixel m of tap (ky, kx) then reads
-// plane q = kx % S at pixel m + kx / S, so every tap's A operand is the staged
+// once, split into 2 column-parity planes and into 16-byte channel chunks:
+// element (row rho, plane q, chunk kc, pixel p) at
+// (((rho*2 + q)*KC + kc)*NP + p)*16.  Output pixel m of tap (ky, kx) then reads
+// plane q = kx % 2 at pixel m + kx / 2, so every tap's A operand is the staged
 // tensor itself at a shifted start address: core matrices of 8 consecutive
 // pixels (SBO = 128 bytes), the next K chunk one plane further (LBO = NP*16).
-template <int CIN, int NB, int S>
+template <int CIN, int EPI>
 struct RowConvLayout {
   static constexpr int KC = CIN / 8;
-  static constexpr int NJ = S * (kM - 1) + 3;       // staged input columns
-  static constexpr int NP = (NJ + S - 1) / S;       // pixels per parity plane
-  static constexpr int STAGE_BYTES = 3 * S * KC * NP * 16;
-  static constexpr int B_BYTES = 9 * CIN * NB * 2;  // this CTA's NB output channels
-  static constexpr int TMEM_COLS = NB < 32 ? 32 : NB;
-  static constexpr int SMEM = B_BYTES + STAGE_BYTES + 64;
-  static_assert(CIN % 16 == 0 && NB % 32 == 0 && NB <= 256, "shape");
+  static constexpr int NJ = kS * (kM - 1) + 3;      // staged input columns
+  static constexpr int NP = (NJ + kS - 1) / kS;     // pixels per parity plane
+  static constexpr int STAGE_BYTES = 3 * kS * KC * NP * 16;
+  static constexpr int B_BYTES = 9 * CIN * kN * 2;  // packed weights
+  static constexpr int HEAD_BYTES = EPI == 1 ? kHeadW * 4 : 0;
+  static constexpr int TMEM_COLS = 32;
+  static constexpr int SMEM = B_BYTES + STAGE_BYTES + HEAD_BYTES + 64;
+  static_assert(CIN % 16 == 0, "shape");
   static_assert(B_BYTES % 128 == 0 && STAGE_BYTES % 16 == 0, "alignment");
   static_assert(SMEM <= 227 * 1024, "shared memory");
 };
@@ -59,22 +71,68 @@ __device__ __forceinline__ uint32_t bf2(float a, float b) {
   return *reinterpret_cast<const uint32_t*>(&v);
 }
 
-// hi/lo bf16 pair of a 12-bit sample (SRC 1): hi = (v >> 4)/128 - 1, lo = (v & 15)/16.
+// hi/lo bf16 pair of a 12-bit sample (layer 1): hi = (v >> 4)/128 - 1, lo = (v & 15)/16.
 __device__ __forceinline__ uint32_t split12(uint32_t v) {
   return bf2((float)(v >> 4) * (1.0f / 128.0f) - 1.0f, (float)(v & 15u) * (1.0f / 16.0f));
 }
 
-// SRC: 0 bf16 NHWC input, 1 Bayer frames (hi/lo split), 2 float32 NHWC input
-// rounded to bf16 while staging.  OUTF: 0 bf16 NHWC output, 1 float32 NHWC.
-// Output channels are split over CTAs, NB per CTA (a.cout = total).
-template <int CIN, int NB, int S, int SRC, int OUTF, bool RELU>
+// 16-byte asynchronous copy global -> shared; src_bytes 0 zero-fills.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Weight images of the four layers (K-major B operand, all 32 output
+// channels): for a layer with cin operand channels, element (n, k), k =
+// tap*cin + ci, at (n/8)*(9*cin/8)*128 + (k/8)*128 + (n%8)*16 + (k%8)*2.
+// Layer 1 (16 operand channels from 8 input planes): channel ci is the hi
+// (even) or lo (odd) half of plane ci/2, the lo weight scaled by 1/128.
+// One thread per element of all four images; image l starts at byte
+// img_off[l] of img and is built from w + w_off[l].
+struct PackArgs {
+  const __nv_bfloat16* w;
+  int w_off[4];
+  unsigned img_off[4];
+};
+
+__global__ void pack_conv_tc_weights_kernel(const PackArgs pa, __nv_bfloat16* __restrict__ img) {
+  constexpr int kL1 = kN * 9 * 16, kL = kN * 9 * 32;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int l = 0;
+  if (i >= kL1) {
+    i -= kL1;
+    l = 1 + i / kL;
+    i -= (l - 1) * kL;
+  }
+  if (l > 3) return;
+  const int cin_op = l == 0 ? 16 : 32;
+  const int K = 9 * cin_op;
+  const int n = i / K, k = i - n * K;
+  const int tap = k / cin_op, ci = k - tap * cin_op;
+  const __nv_bfloat16* w = pa.w + pa.w_off[l];
+  float wv;
+  if (l != 0) {
+    wv = __bfloat162float(w[(n * cin_op + ci) * 9 + tap]);
+  } else {
+    wv = __bfloat162float(w[(n * 8 + (ci >> 1)) * 9 + tap]);
+    if (ci & 1) wv *= (1.0f / 128.0f);
+  }
+  const int kc = cin_op / 8;
+  img[(pa.img_off[l] + (n >> 3) * (9 * kc) * 128 + (k >> 3) * 128 + (n & 7) * 16) / 2 + (k & 7)] =
+      __float2bfloat16_rn(wv);
+}
+
+// SRC: 0 bf16 NHWC input, 1 Bayer frames (hi/lo split).  EPI: 0 bias + ReLU
+// -> bf16 NHWC output; 1 bias + ReLU -> bf16 rounding -> 1x1 head (12
+// outputs) -> (range*tanh, range*tanh, sigmoid) of the 4 blocks of the pixel.
+template <int CIN, int SRC, int EPI>
 __global__ void __launch_bounds__(kM) conv3x3_tc_kernel(const ConvTcArgs a) {
-  using L = RowConvLayout<CIN, NB, S>;
-  constexpr int COUT = NB;
+  using L = RowConvLayout<CIN, EPI>;
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sB = smem;
   uint8_t* sX = smem + L::B_BYTES;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L::B_BYTES + L::STAGE_BYTES);
+  float* sHead = reinterpret_cast<float*>(smem + L::B_BYTES + L::STAGE_BYTES);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L::B_BYTES + L::STAGE_BYTES + L::HEAD_BYTES);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
   const int tid = threadIdx.x, warp = tid >> 5;
 
@@ -83,116 +141,103 @@ __global__ void __launch_bounds__(kM) conv3x3_tc_kernel(const ConvTcArgs a) {
     tc::fence_mbar_init();
   }
   if (warp == 0) tc::tmem_alloc(tmem_slot, L::TMEM_COLS);
-  const int nsplit = a.cout / NB;
-  const int split = blockIdx.x % nsplit;
-  const int n0 = split * NB;
-  // weights of channels n0..n0+NB-1 -> B (K-major, k = tap*CIN + ci): element
-  // (n, k) at (n/8)*(9*KC)*128 + (k/8)*128 + (n%8)*16 + (k%8)*2
-  for (int i = tid; i < COUT * 9 * CIN; i += kM) {
-    const int n = i / (9 * CIN), k = i - n * 9 * CIN;
-    const int tap = k / CIN, ci = k - tap * CIN;
-    float wv;
-    if (SRC != 1) {
-      wv = __bfloat162float(a.w[((n0 + n) * CIN + ci) * 9 + tap]);
-    } else {
-      wv = __bfloat162float(a.w[(n * 8 + (ci >> 1)) * 9 + tap]);
-      if (ci & 1) wv *= (1.0f / 128.0f);
-    }
-    __nv_bfloat16* dst =
-        reinterpret_cast<__nv_bfloat16*>(sB + (n >> 3) * (9 * L::KC) * 128 + (k >> 3) * 128 + (n & 7) * 16) + (k & 7);
-    *dst = __float2bfloat16_rn(wv);
-  }
+  for (int i = tid; i < L::B_BYTES / 16; i += kM) reinterpret_cast<uint4*>(sB)[i] = __ldg(a.wimg + i);
+  if (EPI == 1)
+    for (int i = tid; i < kHeadW; i += kM) sHead[i] = __bfloat162float(a.whead[i]);
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
   const uint32_t sX_addr = tc::smem_addr(sX), sB_addr = tc::smem_addr(sB);
-  constexpr uint32_t idesc = tc::idesc_bf16_f32(kM, COUT);
+  constexpr uint32_t idesc = tc::idesc_bf16_f32(kM, kN);
   const int segs = (a.Wo + kM - 1) / kM;
   const long long ntiles = (long long)a.batch * a.Ho * segs;
   uint32_t phase = 0;
   bool ok = true;
 
-  const int cta_stride = gridDim.x / nsplit;
-  for (long long tile = blockIdx.x / nsplit; tile < ntiles; tile += cta_stride) {
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int seg = (int)(tile % segs);
     const long long row = tile / segs;
     const int b = (int)(row / a.Ho), oy = (int)(row - (long long)b * a.Ho);
     const int ox0 = seg * kM;
-    const int c0 = S * ox0 - 1;  // input column of staged column 0
+    const int c0 = kS * ox0 - 1;  // input column of staged column 0
 
-    // ---- stage rows S*oy - 1 .. S*oy + 1, columns c0 .. c0 + NJ - 1
-    constexpr int NITEM = 3 * L::NJ;
-    for (int it0 = 0; it0 < NITEM; it0 += 2 * kM) {
-      if (SRC == 2) {
+    // ---- stage rows 2*oy - 1 .. 2*oy + 1, columns c0 .. c0 + NJ - 1
+    if (SRC == 0) {
+      // item = (row rho, column j, chunk kc), kc fastest: a warp copies whole pixels
+      constexpr int NITEM = 3 * L::NJ * L::KC;
+      for (int it = tid; it < NITEM; it += kM) {
+        const int rho = it / (L::NJ * L::KC), r = it - rho * (L::NJ * L::KC);
+        const int j = r / L::KC, kc = r - j * L::KC;
+        const int iy = kS * oy - 1 + rho, ix = c0 + j;
+        const bool in_ok = iy >= 0 && iy < a.Hi && ix >= 0 && ix < a.Wi;
+        const __nv_bfloat16* src = in_ok ? a.in + (((long long)b * a.Hi + iy) * a.Wi + ix) * CIN + kc * 8 : a.in;
+        const int q = j & 1, pp = j >> 1;
+        cp_async16(sX_addr + (((rho * kS + q) * L::KC + kc) * L::NP + pp) * 16, src, in_ok ? 16u : 0u);
+      }
+      cp_async_wait_all();
+    } else if (a.vec) {
+      // item = (row rho, frame f, group g of 4 half-resolution columns): two
+      // 16-byte loads (raw rows 2iy, 2iy+1) hold the 4 planes of 4 pixels.
+      // Group g covers columns hb + 4g .. hb + 4g + 3 with hb = c0 - 3 a
+      // multiple of 4, so (Wi a multiple of 4) a group is wholly in or out.
+      constexpr int NG = (L::NJ - 1) / 4 + 1;
+      constexpr int NITEM = 3 * 2 * NG;
+      constexpr int PER = (NITEM + kM - 1) / kM;
+      uint4 r0[PER], r1[PER];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int it = it0 + u * kM + tid;
-          if (it >= NITEM) continue;
-          const int rho = it / L::NJ, j = it - rho * L::NJ;
-          const int iy = S * oy - 1 + rho, ix = c0 + j;
-          const bool in_ok = iy >= 0 && iy < a.Hi && ix >= 0 && ix < a.Wi;
-          const float4* src = reinterpret_cast<const float4*>(a.in_f32 + (((long long)b * a.Hi + iy) * a.Wi + ix) * CIN);
-          const int q = j % S, pp = j / S;
-#pragma unroll 4
-          for (int kc = 0; kc < L::KC; ++kc) {
-            const float4 f0 = in_ok ? __ldg(src + 2 * kc) : make_float4(0.f, 0.f, 0.f, 0.f);
-            const float4 f1 = in_ok ? __ldg(src + 2 * kc + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
-            *reinterpret_cast<uint4*>(sX + (((rho * S + q) * L::KC + kc) * L::NP + pp) * 16) =
-                make_uint4(bf2(f0.x, f0.y), bf2(f0.z, f0.w), bf2(f1.x, f1.y), bf2(f1.z, f1.w));
-          }
+      for (int u = 0; u < PER; ++u) {
+        const int it = tid + u * kM;
+        const int rho = it / (2 * NG), r = it - rho * (2 * NG);
+        const int f = r / NG, g = r - f * NG;
+        const int iy = kS * oy - 1 + rho, hx = c0 - 3 + 4 * g;
+        r0[u] = r1[u] = make_uint4(0, 0, 0, 0);
+        if (it < NITEM && iy >= 0 && iy < a.Hi && hx >= 0 && hx < a.Wi) {
+          const uint16_t* fb = f == 0 ? a.fr.ref + (long long)b * a.fr.ref_bs : a.fr.cur + (long long)b * a.fr.cur_bs;
+          const uint16_t* p = fb + (long long)(2 * iy) * a.fr.pitch + 2 * hx;
+          r0[u] = __ldg(reinterpret_cast<const uint4*>(p));
+          r1[u] = __ldg(reinterpret_cast<const uint4*>(p + a.fr.pitch));
         }
-      } else if (SRC == 0) {
-        uint4 v[2][L::KC];
+      }
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int it = it0 + u * kM + tid;
-          const int rho = it / L::NJ, j = it - rho * L::NJ;
-          const int iy = S * oy - 1 + rho, ix = c0 + j;
-          const bool in_ok = it < NITEM && iy >= 0 && iy < a.Hi && ix >= 0 && ix < a.Wi;
-          const uint4* src = reinterpret_cast<const uint4*>(a.in + (((long long)b * a.Hi + iy) * a.Wi + ix) * CIN);
+      for (int u = 0; u < PER; ++u) {
+        const int it = tid + u * kM;
+        if (it >= NITEM) continue;
+        const int rho = it / (2 * NG), r = it - rho * (2 * NG);
+        const int f = r / NG, g = r - f * NG;
+        const int iy = kS * oy - 1 + rho, hx = c0 - 3 + 4 * g;
+        const bool in_ok = iy >= 0 && iy < a.Hi && hx >= 0 && hx < a.Wi;
+        const uint32_t w0[4] = {r0[u].x, r0[u].y, r0[u].z, r0[u].w};
+        const uint32_t w1[4] = {r1[u].x, r1[u].y, r1[u].z, r1[u].w};
 #pragma unroll
-          for (int kc = 0; kc < L::KC; ++kc) v[u][kc] = in_ok ? __ldg(src + kc) : make_uint4(0, 0, 0, 0);
+        for (int t = 0; t < 4; ++t) {
+          const int j = 4 * g - 3 + t;
+          if (j < 0 || j >= L::NJ) continue;
+          uint4 v = make_uint4(0, 0, 0, 0);
+          if (in_ok)
+            v = make_uint4(split12(w0[t] & 0xFFFFu), split12(w0[t] >> 16), split12(w1[t] & 0xFFFFu),
+                           split12(w1[t] >> 16));
+          *reinterpret_cast<uint4*>(sX + (((rho * kS + (j & 1)) * L::KC + f) * L::NP + (j >> 1)) * 16) = v;
         }
+      }
+    } else {
+      // unaligned frames: one 2-byte load per plane sample
+      constexpr int NITEM = 3 * L::NJ;
+      for (int it = tid; it < NITEM; it += kM) {
+        const int rho = it / L::NJ, j = it - rho * L::NJ;
+        const int iy = kS * oy - 1 + rho, ix = c0 + j;
+        const bool in_ok = iy >= 0 && iy < a.Hi && ix >= 0 && ix < a.Wi;
+        uint32_t wd[8];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int it = it0 + u * kM + tid;
-          if (it >= NITEM) continue;
-          const int rho = it / L::NJ, j = it - rho * L::NJ;
-          const int q = j % S, pp = j / S;
-#pragma unroll
-          for (int kc = 0; kc < L::KC; ++kc)
-            *reinterpret_cast<uint4*>(sX + (((rho * S + q) * L::KC + kc) * L::NP + pp) * 16) = v[u][kc];
+        for (int c = 0; c < 8; ++c) {
+          const uint16_t* f = (c < 4 ? a.fr.ref + (long long)b * a.fr.ref_bs : a.fr.cur + (long long)b * a.fr.cur_bs);
+          const int pl = c & 3;
+          wd[c] = in_ok ? split12(__ldg(f + (long long)(2 * iy + (pl >> 1)) * a.fr.pitch + 2 * ix + (pl & 1))) : 0u;
         }
-      } else {
-        uint32_t raw[2][8];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int it = it0 + u * kM + tid;
-          const int rho = it / L::NJ, j = it - rho * L::NJ;
-          const int iy = S * oy - 1 + rho, ix = c0 + j;
-          const bool in_ok = it < NITEM && iy >= 0 && iy < a.Hi && ix >= 0 && ix < a.Wi;
-#pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            const uint16_t* f = (c < 4 ? a.fr.ref + (long long)b * a.fr.ref_bs : a.fr.cur + (long long)b * a.fr.cur_bs);
-            const int pl = c & 3;
-            raw[u][c] = in_ok ? (uint32_t)__ldg(f + (long long)(2 * iy + (pl >> 1)) * a.fr.pitch + 2 * ix + (pl & 1))
-                              : 0xFFFFFFFFu;
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int it = it0 + u * kM + tid;
-          if (it >= NITEM) continue;
-          const int rho = it / L::NJ, j = it - rho * L::NJ;
-          const int q = j % S, pp = j / S;
-          uint32_t wd[8];
-#pragma unroll
-          for (int c = 0; c < 8; ++c) wd[c] = raw[u][c] == 0xFFFFFFFFu ? 0u : split12(raw[u][c]);
-          *reinterpret_cast<uint4*>(sX + (((rho * S + q) * L::KC + 0) * L::NP + pp) * 16) =
-              make_uint4(wd[0], wd[1], wd[2], wd[3]);
-          *reinterpret_cast<uint4*>(sX + (((rho * S + q) * L::KC + 1) * L::NP + pp) * 16) =
-              make_uint4(wd[4], wd[5], wd[6], wd[7]);
-        }
+        const int q = j & 1, pp = j >> 1;
+        *reinterpret_cast<uint4*>(sX + (((rho * kS + q) * L::KC + 0) * L::NP + pp) * 16) =
+            make_uint4(wd[0], wd[1], wd[2], wd[3]);
+        *reinterpret_cast<uint4*>(sX + (((rho * kS + q) * L::KC + 1) * L::NP + pp) * 16) =
+            make_uint4(wd[4], wd[5], wd[6], wd[7]);
       }
     }
     tc::fence_proxy_async();
@@ -202,10 +247,10 @@ __global__ void __launch_bounds__(kM) conv3x3_tc_kernel(const ConvTcArgs a) {
 #pragma unroll
       for (int tap = 0; tap < 9; ++tap) {
         const int ky = tap / 3, kx = tap % 3;
-        const int q = kx % S, dp = kx / S;
+        const int q = kx % kS, dp = kx / kS;
 #pragma unroll
         for (int s2 = 0; s2 < CIN / 16; ++s2) {
-          const uint32_t a_addr = sX_addr + (((ky * S + q) * L::KC + 2 * s2) * L::NP + dp) * 16;
+          const uint32_t a_addr = sX_addr + (((ky * kS + q) * L::KC + 2 * s2) * L::NP + dp) * 16;
           const uint64_t ad = tc::smem_desc(a_addr, L::NP * 16, 128);
           const uint64_t bd = tc::smem_desc(sB_addr + (tap * L::KC + 2 * s2) * 128, 128, 9 * L::KC * 128);
           tc::mma_bf16(tmem, ad, bd, idesc, (tap > 0 || s2 > 0) ? 1u : 0u);
@@ -218,27 +263,38 @@ __global__ void __launch_bounds__(kM) conv3x3_tc_kernel(const ConvTcArgs a) {
     tc::fence_after_sync();
     const int ox = ox0 + tid;
     const bool valid = ox < a.Wo;
-    const long long opix = ((long long)b * a.Ho + oy) * a.Wo + ox;
+    float v[32];
+    tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
+    if (valid) {
 #pragma unroll
-    for (int cc = 0; cc < COUT; cc += 32) {
-      float v[32];
-      tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cc, v);
-      if (valid) {
+      for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j] + __bfloat162float(a.bias[j]), 0.f);
+      if (EPI == 0) {
+        const long long opix = ((long long)b * a.Ho + oy) * a.Wo + ox;
+        uint4* dst = reinterpret_cast<uint4*>(a.out + opix * kN);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          v[j] += __bfloat162float(a.bias[n0 + cc + j]);
-          if (RELU) v[j] = fmaxf(v[j], 0.f);
-        }
-        if (OUTF == 0) {
-          uint4* dst = reinterpret_cast<uint4*>(a.out + opix * a.cout + n0 + cc);
+        for (int q4 = 0; q4 < 4; ++q4)
+          dst[q4] = make_uint4(bf2(v[8 * q4], v[8 * q4 + 1]), bf2(v[8 * q4 + 2], v[8 * q4 + 3]),
+                               bf2(v[8 * q4 + 4], v[8 * q4 + 5]), bf2(v[8 * q4 + 6], v[8 * q4 + 7]));
+      } else {
+        // the head sees the bf16 activation, as it would read it back from memory
 #pragma unroll
-          for (int q4 = 0; q4 < 4; ++q4)
-            dst[q4] = make_uint4(bf2(v[8 * q4], v[8 * q4 + 1]), bf2(v[8 * q4 + 2], v[8 * q4 + 3]),
-                                 bf2(v[8 * q4 + 4], v[8 * q4 + 5]), bf2(v[8 * q4 + 6], v[8 * q4 + 7]));
-        } else {
-          float4* dst = reinterpret_cast<float4*>(a.out_f32 + opix * a.cout + n0 + cc);
+        for (int j = 0; j < 32; ++j) v[j] = __bfloat162float(__float2bfloat16_rn(v[j]));
+        const int hb = 2 * a.Ho, wb = 2 * a.Wo;
 #pragma unroll
-          for (int q4 = 0; q4 < 8; ++q4) dst[q4] = make_float4(v[4 * q4], v[4 * q4 + 1], v[4 * q4 + 2], v[4 * q4 + 3]);
+        for (int s = 0; s < 4; ++s) {
+          float z[3];
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            const int j = 3 * s + q;
+            float acc = sHead[12 * kN + j];
+#pragma unroll
+            for (int c = 0; c < kN; ++c) acc = fmaf(sHead[j * kN + c], v[c], acc);
+            z[q] = acc;
+          }
+          const long long blk = ((long long)b * hb + 2 * oy + (s >> 1)) * wb + 2 * ox + (s & 1);
+          a.prop[2 * blk] = (float)a.range * tanhf(z[0]);
+          a.prop[2 * blk + 1] = (float)a.range * tanhf(z[1]);
+          a.conf[blk] = 1.0f / (1.0f + expf(-z[2]));
         }
       }
     }
@@ -250,28 +306,25 @@ __global__ void __launch_bounds__(kM) conv3x3_tc_kernel(const ConvTcArgs a) {
   if (!ok && tid == 0 && a.status) atomicExch(a.status, (int)BAYER_ERR_TIMEOUT);
 }
 
-template <int CIN, int NB, int S, int SRC, int OUTF, bool RELU>
+template <int CIN, int SRC, int EPI>
 cudaError_t launch_t(const ConvTcArgs& a, cudaStream_t st) {
-  using L = RowConvLayout<CIN, NB, S>;
-  auto kern = conv3x3_tc_kernel<CIN, NB, S, SRC, OUTF, RELU>;
-  if (a.cout % NB != 0) return cudaErrorInvalidValue;
-  const int nsplit = a.cout / NB;
+  using L = RowConvLayout<CIN, EPI>;
+  auto kern = conv3x3_tc_kernel<CIN, SRC, EPI>;
   int dev = 0, nsm = 148;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int per_sm = tc::ctas_per_sm(kern, kM, L::SMEM, L::TMEM_COLS);
   const long long ntiles = (long long)a.batch * a.Ho * ((a.Wo + kM - 1) / kM);
-  long long per_split = (long long)nsm * per_sm / nsplit;
-  if (per_split > ntiles) per_split = ntiles;
-  if (per_split < 1) per_split = 1;
   if (ntiles < 1) return cudaSuccess;
-  kern<<<(unsigned)(per_split * nsplit), kM, L::SMEM, st>>>(a);
+  long long grid = (long long)nsm * per_sm;
+  if (grid > ntiles) grid = ntiles;
+  kern<<<(unsigned)grid, kM, L::SMEM, st>>>(a);
   return cudaGetLastError();
 }
 
-template <int CIN, int NB, int S, int SRC, int OUTF, bool RELU>
+template <int CIN, int SRC, int EPI>
 cudaError_t configure_t() {
-  using L = RowConvLayout<CIN, NB, S>;
-  auto kern = conv3x3_tc_kernel<CIN, NB, S, SRC, OUTF, RELU>;
+  using L = RowConvLayout<CIN, EPI>;
+  auto kern = conv3x3_tc_kernel<CIN, SRC, EPI>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
   // prefer the largest shared-memory carveout so several CTAs fit per SM
   if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
@@ -280,17 +333,32 @@ cudaError_t configure_t() {
 
 }  // namespace
 
-cudaError_t configure_conv_tc() {
-  cudaError_t e;
-  if ((e = configure_t<16, 32, 2, 1, 0, true>()) != cudaSuccess) return e;
-  return configure_t<32, 32, 2, 0, 0, true>();
+size_t conv_tc_weight_bytes(int cin_op) { return (size_t)9 * cin_op * kN * 2; }
+
+cudaError_t pack_conv_tc_weights(const uint16_t* w, const int* w_off, const size_t* img_off, uint16_t* img,
+                                 cudaStream_t st) {
+  PackArgs pa;
+  pa.w = reinterpret_cast<const __nv_bfloat16*>(w);
+  for (int l = 0; l < 4; ++l) {
+    pa.w_off[l] = w_off[l];
+    pa.img_off[l] = (unsigned)img_off[l];
+  }
+  const int n = kN * 9 * 16 + 3 * kN * 9 * 32;
+  pack_conv_tc_weights_kernel<<<(n + 255) / 256, 256, 0, st>>>(pa, reinterpret_cast<__nv_bfloat16*>(img));
+  return cudaGetLastError();
 }
 
-cudaError_t launch_conv_tc(const ConvTcArgs& a, int cin, int stride, int src, int outf, bool relu, cudaStream_t st) {
-  if (cin == 16 && stride == 2 && src == 1 && outf == 0 && relu && a.cout == 32)
-    return launch_t<16, 32, 2, 1, 0, true>(a, st);
-  if (cin == 32 && stride == 2 && src == 0 && outf == 0 && relu && a.cout == 32)
-    return launch_t<32, 32, 2, 0, 0, true>(a, st);
+cudaError_t configure_conv_tc() {
+  cudaError_t e;
+  if ((e = configure_t<16, 1, 0>()) != cudaSuccess) return e;
+  if ((e = configure_t<32, 0, 0>()) != cudaSuccess) return e;
+  return configure_t<32, 0, 1>();
+}
+
+cudaError_t launch_conv_tc(const ConvTcArgs& a, int layer, bool head, cudaStream_t st) {
+  if (layer == 1 && !head) return launch_t<16, 1, 0>(a, st);
+  if (layer > 1 && !head) return launch_t<32, 0, 0>(a, st);
+  if (layer > 1 && head) return launch_t<32, 0, 1>(a, st);
   return cudaErrorInvalidValue;
 }
 

@@ -65,7 +65,7 @@ struct CnnShapes {
   int H[5], W[5];  // [0] half-resolution input, [1..4] layer outputs
 };
 CnnShapes cnn_shapes(int W, int H);
-size_t cnn_act_bytes(int W, int H, int batch);   // bf16 activations of layers 1..4
+size_t cnn_act_bytes(int W, int H, int batch);   // bf16 activations of layers 1..4 + packed weights
 size_t cnn_grad_bytes(int W, int H, int batch);  // fp32 pre-activation gradients of layers 1..4
 cudaError_t cnn_forward(const CnnFrames& fr, int batch, const uint16_t* wbf16, int range, void* acts, float* prop,
                         float* conf, int* status, cudaStream_t st);
@@ -73,23 +73,34 @@ cudaError_t cnn_loss_grad(const CnnFrames& fr, int batch, const uint16_t* wbf16,
                           float neg_weight, void* acts, void* dpre, float* grad, float* loss, int* status,
                           cudaStream_t st);
 
-// 3x3 convolution on the tensor cores (conv_tc.cu): NHWC bf16 in (or, src 1,
-// the Bayer frames of layer 1), NHWC bf16 out, bias + optional ReLU.
+// 3x3 stride-2 convolution, 32 output channels, on the tensor cores
+// (conv_tc.cu): the proposal network's layers.  NHWC bf16 in (layer 1: the
+// Bayer frames), bias + ReLU, NHWC bf16 out, or (head fused, layer 4) the 1x1
+// head straight to the per-block proposals and confidences.
 struct ConvTcArgs {
-  const __nv_bfloat16* in;  // src 0: [batch][Hi][Wi][cin] bf16
-  const float* in_f32;      // src 2: [batch][Hi][Wi][cin] float32 (rounded to bf16 when staged)
-  CnnFrames fr;             // src 1: frames; Hi, Wi are the half-resolution dims
+  const __nv_bfloat16* in;  // layers 2..4: [batch][Hi][Wi][32] bf16
+  CnnFrames fr;             // layer 1: frames; Hi, Wi are the half-resolution dims
+  bool vec;                 // layer 1: 16-byte frame loads allowed (aligned rows, Wi % 4 == 0)
   int Hi, Wi;
-  const __nv_bfloat16* w;     // [cout][cin_w][3][3] (cin_w = cin, or 8 for src 1)
-  const __nv_bfloat16* bias;  // [cout]
-  __nv_bfloat16* out;         // outf 0: [batch][Ho][Wo][cout] bf16
-  float* out_f32;             // outf 1: [batch][Ho][Wo][cout] float32
-  int Ho, Wo, batch, cout;
+  const uint4* wimg;          // weights packed by pack_conv_tc_weights
+  const __nv_bfloat16* bias;  // [32]
+  __nv_bfloat16* out;         // [batch][Ho][Wo][32] bf16 (no head)
+  const __nv_bfloat16* whead;  // head: [12][32] weights then [12] biases
+  float* prop;                 // head: [batch][2Ho][2Wo][2]
+  float* conf;                 // head: [batch][2Ho][2Wo]
+  int range;                   // head: proposal scale
+  int Ho, Wo, batch;
   int* status;  // device status word: BAYER_ERR_TIMEOUT if a bounded wait expired
 };
 cudaError_t configure_conv_tc();
-// cin/stride/src/outf/relu select an instantiated form; cout in the args.
-cudaError_t launch_conv_tc(const ConvTcArgs& a, int cin, int stride, int src, int outf, bool relu, cudaStream_t st);
+// Packed weight image of one layer: cin_op operand channels (16 for layer 1's
+// split frames, else 32).  pack_conv_tc_weights builds all four layers'
+// images in one launch: layer l from the [32][cin][3][3] bf16 block at
+// w + w_off[l], written at byte img_off[l] (256-byte aligned) of img.
+size_t conv_tc_weight_bytes(int cin_op);
+cudaError_t pack_conv_tc_weights(const uint16_t* w, const int* w_off, const size_t* img_off, uint16_t* img,
+                                 cudaStream_t st);
+cudaError_t launch_conv_tc(const ConvTcArgs& a, int layer, bool head, cudaStream_t st);
 
 // 3x3 stride-1 convolution streamed row by row on the tensor cores
 // (conv_rows_tc.cu): NHWC input (bf16, or float32 rounded to bf16 when
