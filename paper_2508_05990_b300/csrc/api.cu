@@ -201,6 +201,7 @@ bayer_status_t bayer_me_init(bayer_me_t* out, int device) {
   h->device = device;
   e = bme::configure_full16();
   if (e == cudaSuccess) e = bme::configure_full16_list();
+  if (e == cudaSuccess) e = bme::configure_seeded16();
   if (e == cudaSuccess) e = bme::configure_conv_tc();
   if (e == cudaSuccess) e = bme::configure_conv_rows_tc();
   if (e == cudaSuccess) e = cudaMalloc(&h->d_status, sizeof(int));

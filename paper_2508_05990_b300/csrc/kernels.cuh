@@ -148,6 +148,7 @@ struct Seeded16Args {
   int* count;         // number of entries in list (zeroed by the caller)
   bool vec2;          // set by launch_seeded16: 32-bit sample-pair loads allowed
 };
+cudaError_t configure_seeded16();  // once per device: shared-memory opt-in
 cudaError_t launch_seeded16(const Seeded16Args& a, cudaStream_t st);
 cudaError_t launch_full16_list(const uint16_t* ref, const uint16_t* cur, int W, int H, int pitch, long long ref_bs,
                                long long cur_bs, int h, int w, int range, const int* list, const int* count,

@@ -1,15 +1,21 @@
 // Seeded +-4 refine of 16x16 blocks (the learned-seeded search; not in the
-// paper).  One warp per block: a block whose confidence is below the
-// threshold is appended to a device list for the exhaustive search (see
-// me_full16.cu, list mode); otherwise the proposal is limited to +-1024,
-// rounded to the nearest even integer (half away from zero), clamped to
-// [-range, range] and to the block's valid displacements, and the 25
-// candidates centre + (2u, 2v), u, v in [-2, 2], with |dx|, |dy| <= range and
-// the displaced block inside the frame are evaluated from a 24x24 window and
-// the current block staged in the warp's shared memory: lane (v, g) holds the
-// five candidates of row v over column quarter g (each 128-bit window load
-// feeds five accumulators), and two shuffles sum the quarters.
-// Argmin with the (sad, |dx|+|dy|, dy, dx) key as everywhere else.
+// paper).  A block whose confidence is below the threshold goes to a device
+// list for the exhaustive search (me_full16.cu, list mode); otherwise the
+// proposal is limited to +-1024, rounded to the nearest even integer (half
+// away from zero), clamped to [-range, range] and to the block's valid
+// displacements, and the 25 candidates centre + (2u, 2v), u, v in [-2, 2],
+// with |dx|, |dy| <= range and the displaced block inside the frame are
+// evaluated.  Argmin with the (sad, |dx|+|dy|, dy, dx) key as everywhere else.
+//
+// Mapping: one warp per three consecutive blocks, 10 lanes per block.
+// Lanes 0-2 read the blocks' confidences and proposals; low-confidence
+// blocks are appended to the fallback list (one atomic per warp).  For the
+// confident blocks the warp stages the 24 x 24 windows and the current
+// blocks in its shared memory as 32-bit pixel words (every sample-pair load
+// of the three blocks in flight at once), then lane 10 j + 5 half + v owns
+// candidate row v (5 candidates) of block j over one half of its columns:
+// 30 of 32 lanes carry SADs and every 128-bit window load feeds 5
+// candidates.  A block's minimum is gathered from its five row lanes.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -17,135 +23,247 @@ namespace bme {
 
 namespace {
 
-constexpr int kSW = 8;     // warps per CTA
-constexpr int kWin = 24;   // window side (16 + 2 * 4)
-constexpr int kWP = 24;    // window pitch (words)
+constexpr int kSW = 4;            // warps per CTA
+constexpr int kPer = 3;           // blocks per warp
+constexpr int kWin = 24;          // window side (16 + 2 * 4)
+constexpr int kWP = 36;           // window pitch (words); with the lane order below and kSlot = 4 mod 32
+constexpr int kSlot = kWin * kWP + 256 + 4;  // the 128-bit search loads take 7 (window) and 4 (current
+                                             // block) wavefronts instead of 9 and 6 at pitch 24
+// words per block slot: window, then current block (pitch 16), then 4 words of padding
+constexpr int kPairsWin = kWin * kWin / 2;  // sample pairs of a window (288 = 9 * 32)
+constexpr int kPairsCur = 128;              // sample pairs of a current block (4 * 32)
+constexpr size_t kSmem = (size_t)kSW * kPer * kSlot * sizeof(uint32_t);
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
 __global__ void __launch_bounds__(kSW * 32) seeded16_kernel(const Seeded16Args a) {
-  __shared__ __align__(16) uint32_t win_all[kSW][kWin * kWP];
-  __shared__ __align__(16) uint32_t cur_all[kSW][256];
+  extern __shared__ __align__(16) uint32_t smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long nblk = (long long)a.batch * a.h * a.w;
-  const long long gb = (long long)blockIdx.x * kSW + warp;
-  if (gb >= nblk) return;
-  const int pair = (int)(gb / ((long long)a.h * a.w));
-  const int rem = (int)(gb - (long long)pair * a.h * a.w);
-  const int by = rem / a.w, bx = rem - by * a.w;
-  const int x0 = bx * 16, y0 = by * 16;
-  if (!(a.conf[gb] >= a.thresh)) {
-    if (lane == 0) {
-      a.list[atomicAdd(a.count, 1)] = (int)gb;
-      if (a.fallback) a.fallback[gb] = 1;
-    }
-    return;
-  }
-  const float px = fminf(fmaxf(a.prop[2 * gb], -1024.f), 1024.f);
-  const float py = fminf(fmaxf(a.prop[2 * gb + 1], -1024.f), 1024.f);
-  int cx = 2 * (int)roundf(px * 0.5f);
-  int cy = 2 * (int)roundf(py * 0.5f);
-  cx = clampi(clampi(cx, -a.range, a.range), -x0, a.W - 16 - x0);
-  cy = clampi(clampi(cy, -a.range, a.range), -y0, a.H - 16 - y0);
+  const long long gb0 = ((long long)blockIdx.x * kSW + warp) * kPer;
+  if (gb0 >= nblk) return;
 
-  const uint16_t* ref = a.ref + (long long)pair * a.ref_bs;
-  const uint16_t* cur = a.cur + (long long)pair * a.cur_bs;
-  uint32_t* win = win_all[warp];
-  uint32_t* cb = cur_all[warp];
-  const int wx0 = x0 + cx - 4, wy0 = y0 + cy - 4;
-  if (a.vec2) {
-    // pairs of samples: the window starts at an even column (even centre, block
-    // origin a multiple of 16) and W is even, so a pair is wholly in or out
-    uint32_t rw[9], rc[4];
+  // geometry of the warp's three blocks (warp-uniform; consecutive block indices)
+  int bp[kPer], bxy[kPer];
+  {
+    const long long hw = (long long)a.h * a.w;
+    int p = (int)(gb0 / hw);
+    const int rem = (int)(gb0 - (long long)p * hw);
+    int by = rem / a.w, bx = rem - by * a.w;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      const int e = lane + 32 * i, ry = e / 12, px = e - ry * 12;
-      const int gy = wy0 + ry, gx = wx0 + 2 * px;
-      rw[i] = (gy >= 0 && gy < a.H && gx >= 0 && gx < a.W)
-                  ? __ldg(reinterpret_cast<const uint32_t*>(ref + (long long)gy * a.pitch + gx)) : 0u;
+    for (int k = 0; k < kPer; ++k) {
+      bp[k] = p;
+      bxy[k] = (bx * 16) | ((by * 16) << 16);
+      if (++bx == a.w) {
+        bx = 0;
+        if (++by == a.h) {
+          by = 0;
+          ++p;
+        }
+      }
+    }
+  }
+  const bool vec = a.vec2;
+
+  // ---- lanes 0..2 load block gb0 + lane's confidence and proposal while
+  // every lane loads its samples of the three current blocks
+  float cf = 0.f, px = 0.f, py = 0.f;
+  const bool mine = lane < kPer && gb0 + lane < nblk;
+  if (mine) {
+    const long long gb = gb0 + lane;
+    cf = a.conf[gb];
+    px = a.prop[2 * gb];
+    py = a.prop[2 * gb + 1];
+  }
+  uint32_t rc[kPer][kPairsCur / 32];
+  if (vec) {
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int x0 = bxy[k] & 0xFFFF, y0 = bxy[k] >> 16;
+      const uint16_t* cur = a.cur + (long long)bp[k] * a.cur_bs + (long long)y0 * a.pitch + x0;
+#pragma unroll
+      for (int i = 0; i < kPairsCur / 32; ++i) {
+        const int f = lane + 32 * i;
+        rc[k][i] = gb0 + k < nblk ? __ldg(reinterpret_cast<const uint32_t*>(cur + (f >> 3) * a.pitch + 2 * (f & 7)))
+                                  : 0u;
+      }
+    }
+  }
+
+  // ---- confidence test and search centre (lanes 0..2)
+  bool confident = false, fb = false;
+  int cpk = 0;
+  if (mine) {
+    const long long gb = gb0 + lane;
+    fb = !(cf >= a.thresh);
+    if (a.fallback) a.fallback[gb] = fb ? 1 : 0;
+  }
+  {
+    // lane k < 3 handles block k; select its geometry without dynamic indexing
+    const int mxy = lane == 0 ? bxy[0] : (lane == 1 ? bxy[1] : bxy[2]);
+    const int x0 = mxy & 0xFFFF, y0 = mxy >> 16;
+    if (mine && !fb) {
+      const float qx = fminf(fmaxf(px, -1024.f), 1024.f);
+      const float qy = fminf(fmaxf(py, -1024.f), 1024.f);
+      int cx = 2 * (int)roundf(qx * 0.5f);
+      int cy = 2 * (int)roundf(qy * 0.5f);
+      cx = clampi(clampi(cx, -a.range, a.range), -x0, a.W - 16 - x0);
+      cy = clampi(clampi(cy, -a.range, a.range), -y0, a.H - 16 - y0);
+      cpk = (int)(((unsigned)cx & 0xFFFFu) | ((unsigned)cy << 16));
+      confident = true;
+    }
+  }
+  const unsigned m = __ballot_sync(0xffffffffu, fb);
+  if (m) {
+    int base = 0;
+    if (lane == 0) base = atomicAdd(a.count, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (fb) a.list[base + __popc(m & ((1u << lane) - 1u))] = (int)(gb0 + lane);
+  }
+  const unsigned conf_mask = __ballot_sync(0xffffffffu, confident);
+  if (conf_mask == 0) return;
+
+  // ---- stage the confident blocks' windows and current blocks
+  uint32_t* slots = smem + warp * kPer * kSlot;
+  if (vec) {
+    uint32_t raw[kPer][kPairsWin / 32];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int bc = __shfl_sync(0xffffffffu, cpk, k);
+#pragma unroll
+      for (int i = 0; i < kPairsWin / 32; ++i) raw[k][i] = 0;
+      if (conf_mask & (1u << k)) {
+        const int x0 = bxy[k] & 0xFFFF, y0 = bxy[k] >> 16;
+        const int cx = (int)(int16_t)(bc & 0xFFFF), cy = bc >> 16;
+        const uint16_t* ref = a.ref + (long long)bp[k] * a.ref_bs;
+        const int wx0 = x0 + cx - 4, wy0 = y0 + cy - 4;
+#pragma unroll
+        for (int i = 0; i < kPairsWin / 32; ++i) {
+          // the window may reach 4 samples past the frame; a pair is wholly in
+          // or out (even origin, even W)
+          const int e = lane + 32 * i;
+          const int row = e / (kWin / 2), col = 2 * (e - row * (kWin / 2));
+          const int gy = wy0 + row, gx = wx0 + col;
+          if (gy >= 0 && gy < a.H && gx >= 0 && gx < a.W)
+            raw[k][i] = __ldg(reinterpret_cast<const uint32_t*>(ref + (long long)gy * a.pitch + gx));
+        }
+      }
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int e = lane + 32 * i;
-      rc[i] = __ldg(reinterpret_cast<const uint32_t*>(cur + (long long)(y0 + (e >> 3)) * a.pitch + x0 + 2 * (e & 7)));
-    }
+    for (int k = 0; k < kPer; ++k) {
+      if (!(conf_mask & (1u << k))) continue;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      const int e = lane + 32 * i, ry = e / 12, px = e - ry * 12;
-      win[ry * kWP + 2 * px] = pix_lo(rw[i]);
-      win[ry * kWP + 2 * px + 1] = pix_hi(rw[i]);
-    }
+      for (int i = 0; i < kPairsWin / 32; ++i) {
+        const int e = lane + 32 * i;
+        const int row = e / (kWin / 2);
+        const int so = row * kWP + 2 * (e - row * (kWin / 2));
+        *reinterpret_cast<uint2*>(slots + k * kSlot + so) = make_uint2(pix_lo(raw[k][i]), pix_hi(raw[k][i]));
+      }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int e = lane + 32 * i;
-      cb[(e >> 3) * 16 + 2 * (e & 7)] = pix_lo(rc[i]);
-      cb[(e >> 3) * 16 + 2 * (e & 7) + 1] = pix_hi(rc[i]);
+      for (int i = 0; i < kPairsCur / 32; ++i) {
+        const int f = lane + 32 * i;
+        const int so = kWin * kWP + (f >> 3) * 16 + 2 * (f & 7);
+        *reinterpret_cast<uint2*>(slots + k * kSlot + so) = make_uint2(pix_lo(rc[k][i]), pix_hi(rc[k][i]));
+      }
     }
   } else {
-    for (int e = lane; e < kWin * kWin; e += 32) {
-      const int ry = e / kWin, rx = e - ry * kWin;
-      const int gy = wy0 + ry, gx = wx0 + rx;
-      uint32_t v = 0;
-      if (gy >= 0 && gy < a.H && gx >= 0 && gx < a.W) v = __ldg(ref + (long long)gy * a.pitch + gx);
-      win[ry * kWP + rx] = pix_word(v);
+    // unaligned frames: one 16-bit load per sample
+    for (int k = 0; k < kPer; ++k) {
+      const int bc = __shfl_sync(0xffffffffu, cpk, k);
+      if (!(conf_mask & (1u << k))) continue;
+      const int x0 = bxy[k] & 0xFFFF, y0 = bxy[k] >> 16;
+      const int cx = (int)(int16_t)(bc & 0xFFFF), cy = bc >> 16;
+      const uint16_t* ref = a.ref + (long long)bp[k] * a.ref_bs;
+      const uint16_t* cur = a.cur + (long long)bp[k] * a.cur_bs;
+      for (int e = lane; e < kWin * kWin; e += 32) {
+        const int ry = e / kWin, rx = e - ry * kWin;
+        const int gy = y0 + cy - 4 + ry, gx = x0 + cx - 4 + rx;
+        uint32_t smp = 0;
+        if (gy >= 0 && gy < a.H && gx >= 0 && gx < a.W) smp = __ldg(ref + (long long)gy * a.pitch + gx);
+        slots[k * kSlot + ry * kWP + rx] = pix_word(smp);
+      }
+      for (int e = lane; e < 256; e += 32)
+        slots[k * kSlot + kWin * kWP + e] = pix_word(__ldg(cur + (long long)(y0 + (e >> 4)) * a.pitch + x0 + (e & 15)));
     }
-    for (int e = lane; e < 256; e += 32)
-      cb[e] = pix_word(__ldg(cur + (long long)(y0 + (e >> 4)) * a.pitch + x0 + (e & 15)));
   }
   __syncwarp();
 
-  // lane = 4 * v + g (v: candidate row, g: column quarter), 20 lanes: each
-  // 128-bit window load (4 samples) feeds the 5 candidates of the row.
-  uint64_t key = kInvalidKey;
-  const int v = lane >> 2, g = lane & 3;
+  // ---- search: lane 10 j + 5 half + v
+  const int j = lane / 10, r10 = lane - 10 * j, hh = r10 >= 5 ? 1 : 0, v = r10 - 5 * hh;
+  const int jj = j < kPer ? j : 0;
+  const int bc = __shfl_sync(0xffffffffu, cpk, jj);
+  const int mxy = jj == 0 ? bxy[0] : (jj == 1 ? bxy[1] : bxy[2]);
+  const bool live = j < kPer && (conf_mask & (1u << j));
   uint32_t acc[5] = {0, 0, 0, 0, 0};
-  if (lane < 20) {
-    const uint32_t* wr = win + (2 * v) * kWP + 4 * g;
-    const uint32_t* cr = cb + 4 * g;
+  if (live) {
+    const uint32_t* wb = slots + j * kSlot + 2 * v * kWP + 8 * hh;
+    const uint32_t* cb = slots + j * kSlot + kWin * kWP + 8 * hh;
 #pragma unroll 4
     for (int r = 0; r < 16; ++r) {
-      const uint4 w0 = *reinterpret_cast<const uint4*>(wr + r * kWP);
-      const uint4 w1 = *reinterpret_cast<const uint4*>(wr + r * kWP + 4);
-      const uint4 w2 = *reinterpret_cast<const uint4*>(wr + r * kWP + 8);
-      const uint4 c4 = *reinterpret_cast<const uint4*>(cr + r * 16);
-      const uint32_t wv[12] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w, w2.x, w2.y, w2.z, w2.w};
-      const uint32_t cv[4] = {c4.x, c4.y, c4.z, c4.w};
+      uint32_t w[16], c[8];
+#pragma unroll
+      for (int k4 = 0; k4 < 4; ++k4) {
+        const uint4 x = *reinterpret_cast<const uint4*>(wb + r * kWP + 4 * k4);
+        w[4 * k4] = x.x;
+        w[4 * k4 + 1] = x.y;
+        w[4 * k4 + 2] = x.z;
+        w[4 * k4 + 3] = x.w;
+      }
+#pragma unroll
+      for (int k4 = 0; k4 < 2; ++k4) {
+        const uint4 x = *reinterpret_cast<const uint4*>(cb + r * 16 + 4 * k4);
+        c[4 * k4] = x.x;
+        c[4 * k4 + 1] = x.y;
+        c[4 * k4 + 2] = x.z;
+        c[4 * k4 + 3] = x.w;
+      }
 #pragma unroll
       for (int u = 0; u < 5; ++u)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[u] = sad_u32(wv[2 * u + c], cv[c], acc[u]);
+        for (int cc = 0; cc < 8; ++cc) acc[u] = sad_u32(w[2 * u + cc], c[cc], acc[u]);
     }
   }
+  const int partner = lane < 30 ? (hh ? lane - 5 : lane + 5) : lane;
 #pragma unroll
-  for (int u = 0; u < 5; ++u) {
-    acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], 1);
-    acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], 2);
-  }
-  if (lane < 20 && g == 0) {
+  for (int u = 0; u < 5; ++u) acc[u] += __shfl_sync(0xffffffffu, acc[u], partner);
+  uint64_t key = kInvalidKey;
+  if (live) {
+    const int x0 = mxy & 0xFFFF, y0 = mxy >> 16;
+    const int cx = (int)(int16_t)(bc & 0xFFFF), cy = bc >> 16;
+    const int dy = cy + 2 * (v - 2);
 #pragma unroll
     for (int u = 0; u < 5; ++u) {
-      const int dx = cx + 2 * (u - 2), dy = cy + 2 * (v - 2);
+      const int dx = cx + 2 * (u - 2);
       const bool ok = abs(dx) <= a.range && abs(dy) <= a.range && x0 + dx >= 0 && x0 + dx + 16 <= a.W &&
                       y0 + dy >= 0 && y0 + dy + 16 <= a.H;
       const uint64_t k = ok ? make_key(acc[u], dx, dy) : kInvalidKey;
       key = k < key ? k : key;
     }
   }
-  key = warp_min_u64(key);
-  if (lane == 0) {
-    a.out[gb] = key_to_mv(key);
-    if (a.fallback) a.fallback[gb] = 0;
+  // minimum over the block's five candidate rows (lanes 10j + v)
+#pragma unroll
+  for (int vv = 1; vv < 5; ++vv) {
+    const uint64_t o = __shfl_sync(0xffffffffu, key, 10 * jj + vv);
+    key = o < key ? o : key;
   }
+  if (live && r10 == 0) a.out[gb0 + j] = key_to_mv(key);
 }
 
 }  // namespace
+
+cudaError_t configure_seeded16() {
+  cudaError_t e = cudaFuncSetAttribute(seeded16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(seeded16_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  return e;
+}
 
 cudaError_t launch_seeded16(const Seeded16Args& in, cudaStream_t st) {
   Seeded16Args a = in;
   a.vec2 = (reinterpret_cast<uintptr_t>(a.ref) % 4) == 0 && (reinterpret_cast<uintptr_t>(a.cur) % 4) == 0 &&
            a.pitch % 2 == 0 && a.ref_bs % 2 == 0 && a.cur_bs % 2 == 0;
   const long long nblk = (long long)a.batch * a.h * a.w;
-  seeded16_kernel<<<(unsigned)((nblk + kSW - 1) / kSW), kSW * 32, 0, st>>>(a);
+  const long long per_cta = (long long)kSW * kPer;
+  seeded16_kernel<<<(unsigned)((nblk + per_cta - 1) / per_cta), kSW * 32, kSmem, st>>>(a);
   return cudaGetLastError();
 }
 

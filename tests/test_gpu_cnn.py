@@ -152,8 +152,11 @@ def test_learned_equals_seeded_mode_on_network_proposals(handle):
     assert int(nfb.item()) == int(fb.sum().item())
 
 
-@pytest.mark.parametrize("mode", ["all_fallback", "at_optimum", "mixed"])
+@pytest.mark.parametrize("mode", ["all_fallback", "at_optimum", "mixed", "mixed_odd_pitch"])
 def test_seeded_fast_path_vs_oracle(handle, mode):
+    """SEEDED mode (block 16, EVEN, +-32) vs the oracle on a 14 x 20-block frame
+    (the second CTA of 256 blocks is partial); "mixed_odd_pitch" stores the
+    frames with a row pitch of 321 samples, which rules out paired loads."""
     H, W = 224, 320
     frames = synth.pan_clip(94, H, W, n_frames=2, rect_size=(16, 64))
     h, w = H // 16, W // 16
@@ -167,12 +170,19 @@ def test_seeded_fast_path_vs_oracle(handle, mode):
     else:
         pdx, pdy, conf = synth.proposals(95, h, w, 32, true_mv=np.stack([full["dx"], full["dy"]], -1), jitter=4.0)
     prop = np.stack([pdx, pdy], -1)
-    out = handle.estimate_ex(dev(frames[0]), dev(frames[1]), mode=bm.MODE_SEEDED, search_range=32,
-                             prop_dxdy=dev(prop), conf=dev(conf))
+    if mode == "mixed_odd_pitch":
+        padded = np.zeros((2, H, W + 1), np.uint16)
+        padded[:, :, :W] = frames
+        d = dev(padded)
+        out = handle.estimate_ex(d[0], d[1], mode=bm.MODE_SEEDED, search_range=32, prop_dxdy=dev(prop),
+                                 conf=dev(conf), W=W, H=H, pitch=W + 1)
+    else:
+        out = handle.estimate_ex(dev(frames[0]), dev(frames[1]), mode=bm.MODE_SEEDED, search_range=32,
+                                 prop_dxdy=dev(prop), conf=dev(conf))
     want, _, _ = oracle.me_seeded(frames[0], frames[1], 16, 32, pdx, pdy, conf)
     g = bm.records_to_numpy(out[0])
     for k in ("dx", "dy", "sad"):
         np.testing.assert_array_equal(g[k], want[k])
-    if mode != "mixed":
+    if mode in ("all_fallback", "at_optimum"):
         for k in ("dx", "dy", "sad"):
             np.testing.assert_array_equal(g[k], full[k])
