@@ -7,10 +7,12 @@
 // strips from a device work queue (atomic counter) over all pairs, find the
 // pair by binary search in a prefix table, stage the strip's window
 // (full16.cuh) and search it.  The last strip of a pair stamps %globaltimer.
-// Propagation: persistent CTAs (256 threads) take (pair, 8-channel chunk,
-// 256-cell tile) items from a second queue and warp the pair's NCHW feature
-// map by its MV field (prop_common.cuh); the last item of a pair stamps the
-// pair's completion time relative to the search launch's start.
+// Propagation: one CTA (256 threads) per (pair, 4-channel chunk, tile of 256
+// units) item, the pair found by binary search in a second prefix table,
+// warps the pair's NCHW feature map by its MV field (prop_common.cuh); a unit is a 2 x 2 quad of
+// cells sharing one MV (bilinear, two or more cells per block side) or one
+// cell.  The last item of a pair stamps the pair's completion time relative
+// to the search launch's start.
 // Autotuner: on the first call for a set of sizes it times each schedule
 // (NW in {4, 8} x pair order {as given, largest first}) with CUDA events and
 // keeps the fastest; the graph (counter reset, search, propagation) is then
@@ -40,17 +42,17 @@ struct MsPair {
   int C, Hf, Wf, stride;
   int h, w, strips_x;
   int me_items, pr_items, prop_tiles;
+  int quads;  // propagation unit: 2 x 2 quad of cells (1) or one cell (0)
   int vec;
 };
 
 struct MsCounters {
   int me_next;
-  int pr_next;
   unsigned long long t0;
 };
 
 constexpr int kPropThreads = 256;
-constexpr int kPropCh = 8;
+constexpr int kPropCh = 4;
 
 __device__ __forceinline__ unsigned long long gtimer() {
   unsigned long long t;
@@ -108,34 +110,40 @@ __global__ void __launch_bounds__(NW * 32) ms_me_kernel(const MsPair* __restrict
 }
 
 __global__ void __launch_bounds__(kPropThreads) ms_prop_kernel(const MsPair* __restrict__ pairs,
-                                                                const int* __restrict__ prefix, int n, int total,
+                                                                const int* __restrict__ prefix, int n,
                                                                 MsCounters* ctr, int* __restrict__ done,
                                                                 long long* __restrict__ end_ns, int interp) {
-  __shared__ int s_item;
-  for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(&ctr->pr_next, 1);
-    __syncthreads();
-    const int item = s_item;
-    __syncthreads();
-    if (item >= total) break;
+  {
+    const int item = blockIdx.x;
     const int p = find_pair(prefix, n, item);
     const MsPair P = pairs[p];
     const int local = item - __ldg(prefix + p);
     const int chunk = local / P.prop_tiles, tile = local - chunk * P.prop_tiles;
-    const int cells = P.Hf * P.Wf;
-    const int cell = tile * kPropThreads + threadIdx.x;
-    if (cell < cells) {
-      const int fy = cell / P.Wf, fx = cell - fy * P.Wf;
-      const int ls = __ffs(P.stride) - 1;  // stride: a power of two dividing 16
-      const bayer_mv_t mv = P.mv[(long long)(fy >> (4 - ls)) * P.w + (fx >> (4 - ls))];
-      const int c0 = chunk * kPropCh;
-      const int nc = min(kPropCh, P.C - c0);
-      const float* in = P.feat + (long long)c0 * cells;
-      float* out = P.fout + (long long)c0 * cells + cell;
+    const long long cells = (long long)P.Hf * P.Wf;
+    const int ls = __ffs(P.stride) - 1;  // stride: a power of two dividing 16
+    const int lc = 4 - ls;               // log2(cells per block side)
+    const int unit = tile * kPropThreads + threadIdx.x;
+    const int c0 = chunk * kPropCh;
+    const int nc = min(kPropCh, P.C - c0);
+    const float* in = P.feat + (long long)c0 * cells;
+    float* out = P.fout + (long long)c0 * cells;
+    if (P.quads) {
+      // BILINEAR, two or more cells per block side: one thread per 2 x 2 quad
+      const int qw = (P.Wf + 1) >> 1;
+      if (unit < ((P.Hf + 1) >> 1) * qw) {
+        const int qy = unit / qw, qx = unit - qy * qw;
+        const int fy = 2 * qy, fx = 2 * qx;
+        const bayer_mv_t mv = P.mv[(long long)(fy >> lc) * P.w + (fx >> lc)];
+        prop::warp_quad<kPropCh>(in, out, cells, P.Hf, P.Wf, ls, fy, fx, mv, nc);
+      }
+    } else if (unit < cells) {
+      const int fy = unit / P.Wf, fx = unit - fy * P.Wf;
+      const bayer_mv_t mv = P.mv[(long long)(fy >> lc) * P.w + (fx >> lc)];
       if (interp == BAYER_INTERP_NEAREST) {
         const int sy = prop::clampi(fy + prop::rounddiv_pow2(mv.dy, ls), 0, P.Hf - 1);
         const int sx = prop::clampi(fx + prop::rounddiv_pow2(mv.dx, ls), 0, P.Wf - 1);
-        for (int c = 0; c < nc; ++c) __stcs(out + (long long)c * cells, __ldg(in + (long long)c * cells + sy * P.Wf + sx));
+        for (int c = 0; c < nc; ++c)
+          __stcs(out + (long long)c * cells + unit, __ldg(in + (long long)c * cells + sy * P.Wf + sx));
       } else {
         const prop::Taps tp = prop::bilinear_taps(ls, P.Hf, P.Wf, fy, fx, mv);
         const int oa = tp.y0 * P.Wf + tp.x0, ob = tp.y0 * P.Wf + tp.x1;
@@ -153,7 +161,7 @@ __global__ void __launch_bounds__(kPropThreads) ms_prop_kernel(const MsPair* __r
         }
 #pragma unroll
         for (int c = 0; c < kPropCh; ++c)
-          if (c < nc) __stcs(out + (long long)c * cells, prop::blend(tp, va[c], vb[c], vc[c], vd[c]));
+          if (c < nc) __stcs(out + (long long)c * cells + unit, prop::blend(tp, va[c], vb[c], vc[c], vd[c]));
       }
     }
     __syncthreads();
@@ -305,8 +313,8 @@ cudaError_t ensure_capacity(MultiStream* m, int n) {
 }
 
 // Fill the pinned table in schedule order; returns the search and propagation item totals.
-void build_table(MultiStream* m, const bayer_pair_t* pairs, int n, const Config& cfg, int* me_total, int* pr_total,
-                 std::vector<int>* perm) {
+void build_table(MultiStream* m, const bayer_pair_t* pairs, int n, const Config& cfg, int interp, int* me_total,
+                 int* pr_total, std::vector<int>* perm) {
   perm->resize(n);
   for (int i = 0; i < n; ++i) (*perm)[i] = i;
   if (cfg.order == 1)
@@ -333,7 +341,10 @@ void build_table(MultiStream* m, const bayer_pair_t* pairs, int n, const Config&
     P.w = q.W / 16;
     P.strips_x = (P.w + cfg.nw - 1) / cfg.nw;
     P.me_items = P.h * P.strips_x;
-    P.prop_tiles = q.feat ? (q.Hf * q.Wf + kPropThreads - 1) / kPropThreads : 0;
+    // bilinear with two or more cells per block side works on 2 x 2 quads
+    P.quads = (interp == BAYER_INTERP_BILINEAR && q.stride < 16) ? 1 : 0;
+    const int units = P.quads ? ((q.Hf + 1) / 2) * ((q.Wf + 1) / 2) : q.Hf * q.Wf;
+    P.prop_tiles = q.feat ? (units + kPropThreads - 1) / kPropThreads : 0;
     P.pr_items = q.feat ? ((q.C + kPropCh - 1) / kPropCh) * P.prop_tiles : 0;
     P.vec = (reinterpret_cast<uintptr_t>(q.ref) % 16 == 0 && reinterpret_cast<uintptr_t>(q.cur) % 16 == 0 &&
              q.pitch % 8 == 0) ? 1 : 0;
@@ -360,12 +371,8 @@ cudaError_t enqueue(MultiStream* m, int n, int range, int interp, const Config& 
     e = cfg.nw == 4 ? ms_me_dispatch<4>(range, m->d_pairs, m->d_prefix, n, me_total, m->d_ctr, m->d_done, m->d_end, st)
                     : ms_me_dispatch<8>(range, m->d_pairs, m->d_prefix, n, me_total, m->d_ctr, m->d_done, m->d_end, st);
   if (e == cudaSuccess && has_prop) {
-    int dev = 0, nsm = 148;
-    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    int grid = nsm * 8;
-    if (grid > pr_total) grid = pr_total;
-    ms_prop_kernel<<<grid, kPropThreads, 0, st>>>(m->d_pairs, m->d_prefix + (n + 1), n, pr_total, m->d_ctr,
-                                                  m->d_done + n, m->d_end, interp);
+    ms_prop_kernel<<<pr_total, kPropThreads, 0, st>>>(m->d_pairs, m->d_prefix + (n + 1), n, m->d_ctr, m->d_done + n,
+                                                      m->d_end, interp);
     e = cudaGetLastError();
   }
   return e;
@@ -411,7 +418,7 @@ cudaError_t ms_run(MultiStream* m, const bayer_pair_t* pairs, int n, int range, 
     cudaEventCreate(&e1);
     for (const Config& c : cands) {
       if ((e = cudaEventSynchronize(m->copied)) != cudaSuccess) break;
-      build_table(m, pairs, n, c, &me_total, &pr_total, &perm);
+      build_table(m, pairs, n, c, interp, &me_total, &pr_total, &perm);
       if ((e = upload(m, n, st)) != cudaSuccess) break;
       if ((e = enqueue(m, n, range, interp, c, me_total, pr_total, st)) != cudaSuccess) break;  // warm
       cudaEventRecord(e0, st);
@@ -432,7 +439,7 @@ cudaError_t ms_run(MultiStream* m, const bayer_pair_t* pairs, int n, int range, 
     MultiStream::Entry entry;
     entry.cfg = best;
     if ((e = cudaEventSynchronize(m->copied)) != cudaSuccess) return e;
-    build_table(m, pairs, n, best, &me_total, &pr_total, &perm);
+    build_table(m, pairs, n, best, interp, &me_total, &pr_total, &perm);
     cudaGraph_t g = nullptr;
     if ((e = cudaStreamBeginCapture(m->capture, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
     cudaError_t ec = enqueue(m, n, range, interp, best, me_total, pr_total, m->capture);
@@ -444,7 +451,7 @@ cudaError_t ms_run(MultiStream* m, const bayer_pair_t* pairs, int n, int range, 
     it = m->cache.emplace(key, entry).first;
   } else {
     if ((e = cudaEventSynchronize(m->copied)) != cudaSuccess) return e;
-    build_table(m, pairs, n, it->second.cfg, &me_total, &pr_total, &perm);
+    build_table(m, pairs, n, it->second.cfg, interp, &me_total, &pr_total, &perm);
   }
   if ((e = upload(m, n, st)) != cudaSuccess) return e;
   if ((e = cudaGraphLaunch(it->second.exec, st)) != cudaSuccess) return e;

@@ -95,49 +95,14 @@ constexpr int kQT = 128;
 __global__ void __launch_bounds__(kQT) prop_nchw_quad_kernel(const PropArgs a, int nchunks, int qw, int nquads) {
   const int q = blockIdx.x * kQT + threadIdx.x;
   if (q >= nquads) return;
-  const int cells = a.Hf * a.Wf;
+  const long long cells = (long long)a.Hf * a.Wf;
   const int m = blockIdx.y / nchunks;
   const int c0 = (blockIdx.y - m * nchunks) * kQK;
   const int qy = q / qw, qx = q - qy * qw;
   const int fy = 2 * qy, fx = 2 * qx;
   const bayer_mv_t mv = a.mv[((long long)m * a.mv_h + (fy >> a.lc)) * a.mv_w + (fx >> a.lc)];
-  const Taps tp = bilinear_taps(a.ls, a.Hf, a.Wf, fy, fx, mv);
-  const int oy = (int)mv.dy >> a.ls, ox = (int)mv.dx >> a.ls;
-  int ry[3], rx[3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    ry[i] = clampi(fy + oy + i, 0, a.Hf - 1) * a.Wf;
-    rx[i] = clampi(fx + ox + i, 0, a.Wf - 1);
-  }
-  const float* in = a.feat + ((long long)m * a.C + c0) * cells;
-  float* out = a.out + ((long long)m * a.C + c0) * cells + fy * a.Wf + fx;
-  const int nc = min(kQK, a.C - c0);
-  const bool row2 = fy + 1 < a.Hf, col2 = fx + 1 < a.Wf;
-  const bool pair_store = col2 && (a.Wf & 1) == 0;
-#pragma unroll
-  for (int c = 0; c < kQK; ++c) {
-    if (c >= nc) break;
-    const float* pl = in + (long long)c * cells;
-    float v[9];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) v[3 * i + j] = __ldg(pl + ry[i] + rx[j]);
-    const float r00 = blend(tp, v[0], v[1], v[3], v[4]), r01 = blend(tp, v[1], v[2], v[4], v[5]);
-    const float r10 = blend(tp, v[3], v[4], v[6], v[7]), r11 = blend(tp, v[4], v[5], v[7], v[8]);
-    float* o = out + (long long)c * cells;
-    if (pair_store) {
-      __stcs(reinterpret_cast<float2*>(o), make_float2(r00, r01));
-      if (row2) __stcs(reinterpret_cast<float2*>(o + a.Wf), make_float2(r10, r11));
-    } else {
-      __stcs(o, r00);
-      if (col2) __stcs(o + 1, r01);
-      if (row2) {
-        __stcs(o + a.Wf, r10);
-        if (col2) __stcs(o + a.Wf + 1, r11);
-      }
-    }
-  }
+  const long long base = ((long long)m * a.C + c0) * cells;
+  warp_quad<kQK>(a.feat + base, a.out + base, cells, a.Hf, a.Wf, a.ls, fy, fx, mv, min(kQK, a.C - c0));
 }
 
 // NHWC with C % 4 == 0: one thread per (cell, 4 channels) of one feature row
