@@ -57,7 +57,8 @@ struct RowStreamLayout {
   static constexpr int B_BYTES = 9 * CIN * COUT * 2;
   static constexpr int BAR_OFF = B_BYTES + NR * SLOT_BYTES;
   static constexpr int NBAR = 2 * NR + 2 * kAcc + 1;
-  static constexpr int SMEM = BAR_OFF + NBAR * 8 + 16;
+  static constexpr int BIAS_OFF = (BAR_OFF + NBAR * 8 + 16 + 15) / 16 * 16;  // float32 bias, read as broadcasts
+  static constexpr int SMEM = BIAS_OFF + COUT * 4;
   static constexpr int TMEM_COLS = kAcc * COUT;
   static_assert(CIN % 16 == 0 && (COUT == 64 || COUT == 128), "shape");
   static_assert(B_BYTES % 16 == 0 && SLOT_BYTES % 16 == 0, "alignment");
@@ -126,6 +127,8 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_rows_tc_kernel(const Conv
   if (warp == 0) tc::tmem_alloc(tmem_slot, L::TMEM_COLS);
   // weights: the packed image is the shared-memory layout, copied as is
   for (int i = tid; i < L::B_BYTES / 16; i += kThreads) reinterpret_cast<uint4*>(sB)[i] = __ldg(a.wimg + i);
+  float* sBias = reinterpret_cast<float*>(smem + L::BIAS_OFF);
+  for (int i = tid; i < COUT; i += kThreads) sBias[i] = __ldg(a.bias + i);
   tc::fence_proxy_async();
   __syncthreads();
   tc::fence_after_sync();
@@ -291,9 +294,16 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_rows_tc_kernel(const Conv
           }
           if (valid) {
 #pragma unroll
-            for (int q = 0; q < 32; ++q) {
-              v[q] += __ldg(a.bias + cc + q);
-              if (RELU) v[q] = fmaxf(v[q], 0.f);
+            for (int q4 = 0; q4 < 8; ++q4) {
+              const float4 b4 = *reinterpret_cast<const float4*>(sBias + cc + 4 * q4);
+              v[4 * q4] += b4.x;
+              v[4 * q4 + 1] += b4.y;
+              v[4 * q4 + 2] += b4.z;
+              v[4 * q4 + 3] += b4.w;
+            }
+            if (RELU) {
+#pragma unroll
+              for (int q = 0; q < 32; ++q) v[q] = fmaxf(v[q], 0.f);
             }
             if (OUTF == 0) {
               uint4* o4 = reinterpret_cast<uint4*>(a.out + opix * COUT + cc);
