@@ -177,6 +177,24 @@ bayer_status_t bayer_clip_process_host(bayer_me_t h, const uint16_t* frames, int
  * call (e.g. BAYER_ERR_TIMEOUT from a bounded wait). */
 bayer_status_t bayer_me_sync_status(bayer_me_t h, void* stream);
 
+/* Failure-path self-test of the device-side bounded wait (not in the paper).
+ * Every tensor-core kernel of this library waits on mbarriers with an
+ * iteration limit; when the limit runs out the kernel records
+ * BAYER_ERR_TIMEOUT in the handle's status word and finishes instead of
+ * hanging.  This entry point runs that wait in a one-CTA kernel on `stream`:
+ * with arrive != 0 the barrier's phase completes and the wait succeeds; with
+ * arrive == 0 nothing arrives and the wait gives up after `limit` polls
+ * (limit >= 1), leaving BAYER_ERR_TIMEOUT for bayer_me_sync_status to return.
+ * No fault, trap or unbounded loop is involved either way. */
+bayer_status_t bayer_me_selftest_wait(bayer_me_t h, int arrive, unsigned limit, void* stream);
+
+/* Test hook (not in the paper): the next n workspace growths of the handle
+ * (C2F levels, learned search, refine activations, host pipeline buffers)
+ * fail with BAYER_ERR_OOM without allocating; the call that hits one returns
+ * that status and launches nothing, and later calls allocate normally.
+ * n = 0 clears the hook.  Lets tests exercise the out-of-memory path. */
+bayer_status_t bayer_me_debug_fail_allocs(bayer_me_t h, int n);
+
 /* Roofline probe: throughput of the exact SAD primitive on this device.
  * Runs a register-only loop of `variant` (0 = sad.u32 integer, 1 = float
  * subtract + absolute add, 2 = both interleaved) on every SM and returns the

@@ -34,7 +34,8 @@ MAX_LEVELS = MAX_STAGES = 4
 EXPORTS = ("bayer_me_init", "bayer_me_destroy", "bayer_status_string", "bayer_me_estimate",
            "bayer_me_estimate_ex", "bayer_feat_propagate", "bayer_clip_process_host", "bayer_me_sync_status",
            "bayer_probe_alu", "bayer_me_estimate_c2f_noalloc", "bayer_cnn_forward", "bayer_cnn_loss_grad",
-           "bayer_cnn_adamw", "bayer_me_estimate_learned", "bayer_refine_conv", "bayer_me_multi_stream")
+           "bayer_cnn_adamw", "bayer_me_estimate_learned", "bayer_refine_conv", "bayer_me_multi_stream",
+           "bayer_me_selftest_wait", "bayer_me_debug_fail_allocs")
 PREC_BF16, PREC_FP32 = 0, 1
 
 # Flat parameter layout of the proposal network (BAYER_CNN_* in the header).
@@ -97,6 +98,8 @@ def load(path: str = LIB_PATH):
     lib.bayer_me_estimate_learned.argtypes = [P, P, P, I, I, I, I, LL, LL, P, I, F, P, P, P, P]
     lib.bayer_refine_conv.argtypes = [P, P, I, I, I, I, I, P, P, P, P, P, P, I, P, P]
     lib.bayer_me_multi_stream.argtypes = [P, ctypes.POINTER(PairDesc), I, I, I, P, ctypes.POINTER(ctypes.c_int), P]
+    lib.bayer_me_selftest_wait.argtypes = [P, I, ctypes.c_uint, P]
+    lib.bayer_me_debug_fail_allocs.argtypes = [P, I]
     for name in EXPORTS:
         if name != "bayer_status_string":
             getattr(lib, name).restype = I
@@ -339,6 +342,15 @@ class Handle:
         _check(self._lib.bayer_me_multi_stream(self._h, arr, len(pairs), search_range, interp, _ptr(end_ns),
                                                ctypes.byref(sched), _stream(stream)), "bayer_me_multi_stream")
         return sched.value
+
+    def selftest_wait(self, arrive: bool, limit: int = 1000, stream=None):
+        """Run the device's bounded-wait path (see the header); read the outcome with sync_status()."""
+        _check(self._lib.bayer_me_selftest_wait(self._h, int(arrive), int(limit), _stream(stream)),
+               "bayer_me_selftest_wait")
+
+    def debug_fail_allocs(self, n: int):
+        """Test hook: the next n workspace growths report ERR_OOM."""
+        _check(self._lib.bayer_me_debug_fail_allocs(self._h, int(n)), "bayer_me_debug_fail_allocs")
 
     def sync_status(self, stream=None) -> int:
         return int(self._lib.bayer_me_sync_status(self._h, _stream(stream)))

@@ -7,6 +7,8 @@
 #include <cstring>
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -40,6 +42,7 @@ struct bayer_me_s {
   void* ref_act = nullptr;  // two hidden activation maps
   size_t ref_act_bytes = 0;
   bme::MultiStream* ms = nullptr;  // multi-stream tables, autotune table, graphs
+  int fail_allocs = 0;             // test hook: the next n workspace allocations report BAYER_ERR_OOM
 };
 
 namespace {
@@ -54,11 +57,18 @@ bayer_status_t cuda_status(cudaError_t e) {
   return BAYER_ERR_CUDA;
 }
 
-// Grow a device buffer to at least `bytes` (contents not kept).  Synchronises
-// the device first, because work queued earlier may still use the old buffer.
+// Grow a device buffer of the handle to at least `bytes` (contents not kept).
+// Synchronises the device first, because work queued earlier may still use
+// the old buffer.  While the handle's fail_allocs test hook is positive, a
+// growth that would allocate fails with BAYER_ERR_OOM instead (no allocation,
+// the old buffer is kept).
 template <typename T>
-bayer_status_t grow(T** p, size_t* cap, size_t bytes) {
+bayer_status_t grow(bayer_me_s* h, T** p, size_t* cap, size_t bytes) {
   if (*cap >= bytes) return BAYER_OK;
+  if (h->fail_allocs > 0) {
+    --h->fail_allocs;
+    return BAYER_ERR_OOM;
+  }
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_status(e);
   if (*p) cudaFree(*p);
@@ -69,6 +79,13 @@ bayer_status_t grow(T** p, size_t* cap, size_t bytes) {
   *cap = bytes;
   return BAYER_OK;
 }
+
+// NVTX range around each entry point (visible in Nsight timelines; free when
+// no tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 struct DeviceGuard {
   int prev = -1;
@@ -134,7 +151,7 @@ bayer_status_t seeded_fast(bayer_me_s* h, const uint16_t* ref, const uint16_t* c
                            float thresh, bayer_mv_t* out, uint8_t* fallback, int* n_fallback, cudaStream_t st) {
   const int hb = H / 16, wb = W / 16;
   const long long nblk = (long long)batch * hb * wb;
-  bayer_status_t s = grow(&h->list, &h->list_bytes, (size_t)(nblk + 1) * sizeof(int));
+  bayer_status_t s = grow(h, &h->list, &h->list_bytes, (size_t)(nblk + 1) * sizeof(int));
   if (s != BAYER_OK) return s;
   cudaError_t e = cudaMemsetAsync(h->list, 0, sizeof(int), st);
   bme::Seeded16Args a{};
@@ -243,6 +260,7 @@ bayer_status_t bayer_me_destroy(bayer_me_t h) {
 
 bayer_status_t bayer_me_estimate(bayer_me_t h, const uint16_t* ref, const uint16_t* cur, int W, int H, int block,
                                  int range, bayer_mv_t* mv_out, void* stream) {
+  NvtxRange nvtx_range("bayer_me_estimate");
   if (!h || !mv_out) return BAYER_ERR_INVALID_ARG;
   bayer_status_t s = check_frames(ref, cur, W, H, W, block);
   if (s != BAYER_OK) return s;
@@ -255,6 +273,7 @@ bayer_status_t bayer_me_estimate(bayer_me_t h, const uint16_t* ref, const uint16
 bayer_status_t bayer_me_estimate_ex(bayer_me_t h, const uint16_t* ref, const uint16_t* cur, int W, int H,
                                     int pitch, const bayer_me_params_t* p, const float* prop_dxdy,
                                     const float* conf, bayer_mv_t* mv_out, uint8_t* fallback_out, void* stream) {
+  NvtxRange nvtx_range("bayer_me_estimate_ex");
   if (!h || !p || !mv_out) return BAYER_ERR_INVALID_ARG;
   if (p->batch < 1 || p->batch > 65535) return BAYER_ERR_INVALID_ARG;
   if (p->phase != BAYER_PHASE_EVEN && p->phase != BAYER_PHASE_RAW) return BAYER_ERR_INVALID_ARG;
@@ -332,7 +351,7 @@ bayer_status_t bayer_me_estimate_ex(bayer_me_t h, const uint16_t* ref, const uin
       need = n > need ? n : need;
     }
     if (need) {
-      bayer_status_t s = grow(reinterpret_cast<char**>(&h->scratch), &h->scratch_bytes, 2 * need);
+      bayer_status_t s = grow(h, reinterpret_cast<char**>(&h->scratch), &h->scratch_bytes, 2 * need);
       if (s != BAYER_OK) return s;
     }
     bayer_mv_t* buf[2] = {static_cast<bayer_mv_t*>(h->scratch),
@@ -377,6 +396,7 @@ bayer_status_t bayer_me_estimate_ex(bayer_me_t h, const uint16_t* ref, const uin
 bayer_status_t bayer_feat_propagate(bayer_me_t h, const float* feat, int n, int C, int Hf, int Wf, int layout,
                                     int interp, const bayer_mv_t* mv, int mv_h, int mv_w, int block, int stride,
                                     float* out, void* stream) {
+  NvtxRange nvtx_range("bayer_feat_propagate");
   if (!h || !feat || !mv || !out) return BAYER_ERR_INVALID_ARG;
   if (n < 1 || C < 1 || Hf < 1 || Wf < 1) return BAYER_ERR_INVALID_ARG;
   if (layout != BAYER_LAYOUT_NCHW && layout != BAYER_LAYOUT_NHWC) return BAYER_ERR_INVALID_ARG;
@@ -397,6 +417,7 @@ bayer_status_t bayer_feat_propagate(bayer_me_t h, const float* feat, int n, int 
 bayer_status_t bayer_clip_process_host(bayer_me_t h, const uint16_t* frames, int n_frames, int W, int H, int block,
                                        int range, const float* feats, int C, int Hf, int Wf, int stride, int interp,
                                        bayer_mv_t* mv_out, float* feat_out) {
+  NvtxRange nvtx_range("bayer_clip_process_host");
   if (!h || !frames || !feats || !mv_out || !feat_out || n_frames < 2) return BAYER_ERR_INVALID_ARG;
   bayer_status_t s = check_frames(frames, frames, W, H, W, block);
   if (s != BAYER_OK) return s;
@@ -411,10 +432,10 @@ bayer_status_t bayer_clip_process_host(bayer_me_t h, const uint16_t* frames, int
   const size_t frame_elems = (size_t)W * H;
   const size_t map_elems = (size_t)C * Hf * Wf;
   const size_t field = (size_t)h_ * w_;
-  if ((s = grow(&h->d_frames, &h->frames_bytes, frame_elems * n_frames * sizeof(uint16_t))) != BAYER_OK) return s;
-  if ((s = grow(&h->d_feat, &h->feat_bytes, map_elems * npairs * sizeof(float))) != BAYER_OK) return s;
-  if ((s = grow(&h->d_fout, &h->fout_bytes, map_elems * npairs * sizeof(float))) != BAYER_OK) return s;
-  if ((s = grow(&h->d_mv, &h->mv_bytes, field * npairs * sizeof(bayer_mv_t))) != BAYER_OK) return s;
+  if ((s = grow(h, &h->d_frames, &h->frames_bytes, frame_elems * n_frames * sizeof(uint16_t))) != BAYER_OK) return s;
+  if ((s = grow(h, &h->d_feat, &h->feat_bytes, map_elems * npairs * sizeof(float))) != BAYER_OK) return s;
+  if ((s = grow(h, &h->d_fout, &h->fout_bytes, map_elems * npairs * sizeof(float))) != BAYER_OK) return s;
+  if ((s = grow(h, &h->d_mv, &h->mv_bytes, field * npairs * sizeof(bayer_mv_t))) != BAYER_OK) return s;
 
   // Stream plan: s_in copies the frames, then each pair's features; s_comp
   // runs the batched search once the frames are in, then each pair's
@@ -478,11 +499,12 @@ bayer_status_t bayer_clip_process_host(bayer_me_t h, const uint16_t* frames, int
 bayer_status_t bayer_cnn_forward(bayer_me_t h, const uint16_t* ref, const uint16_t* cur, int W, int H, int pitch,
                                  int batch, long long ref_bs, long long cur_bs, const uint16_t* w_bf16, int range,
                                  float* prop_dxdy, float* conf, void* stream) {
+  NvtxRange nvtx_range("bayer_cnn_forward");
   if (!h || !w_bf16 || !prop_dxdy || !conf || range < 1 || range > 510) return BAYER_ERR_INVALID_ARG;
   bayer_status_t s = check_cnn_frames(ref, cur, W, H, pitch, batch, ref_bs, cur_bs);
   if (s != BAYER_OK) return s;
   DeviceGuard g(h->device);
-  if ((s = grow(reinterpret_cast<char**>(&h->cnn_acts), &h->cnn_acts_bytes, bme::cnn_act_bytes(W, H, batch))) !=
+  if ((s = grow(h, reinterpret_cast<char**>(&h->cnn_acts), &h->cnn_acts_bytes, bme::cnn_act_bytes(W, H, batch))) !=
       BAYER_OK)
     return s;
   bme::CnnFrames fr{ref, cur, W, H, pitch, ref_bs, cur_bs};
@@ -494,15 +516,16 @@ bayer_status_t bayer_cnn_loss_grad(bayer_me_t h, const uint16_t* ref, const uint
                                    int batch, long long ref_bs, long long cur_bs, const uint16_t* w_bf16,
                                    const bayer_mv_t* labels, int range, float neg_weight, float* grad, float* loss,
                                    void* stream) {
+  NvtxRange nvtx_range("bayer_cnn_loss_grad");
   if (!h || !w_bf16 || !labels || !grad || !loss || range < 1 || range > 510) return BAYER_ERR_INVALID_ARG;
   if (!(neg_weight > 0.f)) return BAYER_ERR_INVALID_ARG;
   bayer_status_t s = check_cnn_frames(ref, cur, W, H, pitch, batch, ref_bs, cur_bs);
   if (s != BAYER_OK) return s;
   DeviceGuard g(h->device);
-  if ((s = grow(reinterpret_cast<char**>(&h->cnn_acts), &h->cnn_acts_bytes, bme::cnn_act_bytes(W, H, batch))) !=
+  if ((s = grow(h, reinterpret_cast<char**>(&h->cnn_acts), &h->cnn_acts_bytes, bme::cnn_act_bytes(W, H, batch))) !=
       BAYER_OK)
     return s;
-  if ((s = grow(reinterpret_cast<char**>(&h->cnn_dpre), &h->cnn_dpre_bytes, bme::cnn_grad_bytes(W, H, batch))) !=
+  if ((s = grow(h, reinterpret_cast<char**>(&h->cnn_dpre), &h->cnn_dpre_bytes, bme::cnn_grad_bytes(W, H, batch))) !=
       BAYER_OK)
     return s;
   bme::CnnFrames fr{ref, cur, W, H, pitch, ref_bs, cur_bs};
@@ -513,6 +536,7 @@ bayer_status_t bayer_cnn_loss_grad(bayer_me_t h, const uint16_t* ref, const uint
 bayer_status_t bayer_cnn_adamw(bayer_me_t h, float* w, uint16_t* w_bf16, const float* grad, float* m, float* v,
                                int step, float lr, float beta1, float beta2, float eps, float weight_decay,
                                void* stream) {
+  NvtxRange nvtx_range("bayer_cnn_adamw");
   if (!h || !w || !w_bf16 || !grad || !m || !v || step < 1) return BAYER_ERR_INVALID_ARG;
   if (!(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f)) return BAYER_ERR_INVALID_ARG;
   DeviceGuard g(h->device);
@@ -524,6 +548,7 @@ bayer_status_t bayer_me_estimate_learned(bayer_me_t h, const uint16_t* ref, cons
                                          int pitch, int batch, long long ref_bs, long long cur_bs,
                                          const uint16_t* w_bf16, int range, float conf_thresh, bayer_mv_t* mv_out,
                                          uint8_t* fallback_out, int* n_fallback, void* stream) {
+  NvtxRange nvtx_range("bayer_me_estimate_learned");
   if (!h || !w_bf16 || !mv_out) return BAYER_ERR_INVALID_ARG;
   bayer_status_t s = check_cnn_frames(ref, cur, W, H, pitch, batch, ref_bs, cur_bs);
   if (s != BAYER_OK) return s;
@@ -531,10 +556,10 @@ bayer_status_t bayer_me_estimate_learned(bayer_me_t h, const uint16_t* ref, cons
   DeviceGuard g(h->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t nblk = (size_t)batch * (H / 16) * (W / 16);
-  if ((s = grow(reinterpret_cast<char**>(&h->cnn_acts), &h->cnn_acts_bytes, bme::cnn_act_bytes(W, H, batch))) !=
+  if ((s = grow(h, reinterpret_cast<char**>(&h->cnn_acts), &h->cnn_acts_bytes, bme::cnn_act_bytes(W, H, batch))) !=
       BAYER_OK)
     return s;
-  if ((s = grow(reinterpret_cast<char**>(&h->prop), &h->prop_bytes, nblk * 3 * sizeof(float))) != BAYER_OK) return s;
+  if ((s = grow(h, reinterpret_cast<char**>(&h->prop), &h->prop_bytes, nblk * 3 * sizeof(float))) != BAYER_OK) return s;
   float* prop = h->prop;
   float* conf = h->prop + 2 * nblk;
   bme::CnnFrames fr{ref, cur, W, H, pitch, ref_bs, cur_bs};
@@ -547,6 +572,7 @@ bayer_status_t bayer_me_estimate_learned(bayer_me_t h, const uint16_t* ref, cons
 bayer_status_t bayer_refine_conv(bayer_me_t h, const float* feat, int n, int Hf, int Wf, int C, int hidden,
                                  const float* w1, const float* b1, const float* w2, const float* b2, const float* w3,
                                  const float* b3, int precision, float* out, void* stream) {
+  NvtxRange nvtx_range("bayer_refine_conv");
   if (!h || !feat || !out || !w1 || !b1 || !w2 || !b2 || !w3 || !b3) return BAYER_ERR_INVALID_ARG;
   if (n < 1 || Hf < 1 || Wf < 1) return BAYER_ERR_INVALID_ARG;
   if (precision != BAYER_PREC_BF16 && precision != BAYER_PREC_FP32) return BAYER_ERR_INVALID_ARG;
@@ -560,7 +586,7 @@ bayer_status_t bayer_refine_conv(bayer_me_t h, const float* feat, int n, int Hf,
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t pix = (size_t)n * Hf * Wf;
   const size_t esz = precision == BAYER_PREC_BF16 ? 2 : 4;
-  bayer_status_t s = grow(reinterpret_cast<char**>(&h->ref_act), &h->ref_act_bytes, 2 * pix * hidden * esz);
+  bayer_status_t s = grow(h, reinterpret_cast<char**>(&h->ref_act), &h->ref_act_bytes, 2 * pix * hidden * esz);
   if (s != BAYER_OK) return s;
   cudaError_t e;
   if (precision == BAYER_PREC_FP32) {
@@ -579,7 +605,7 @@ bayer_status_t bayer_refine_conv(bayer_me_t h, const float* feat, int n, int Hf,
     off[i] = total;
     total += (bme::conv_rows_weight_bytes(cins[i], couts[i]) + 255) / 256 * 256;
   }
-  if ((s = grow(reinterpret_cast<char**>(&h->ref_w), &h->ref_w_bytes, total)) != BAYER_OK) return s;
+  if ((s = grow(h, reinterpret_cast<char**>(&h->ref_w), &h->ref_w_bytes, total)) != BAYER_OK) return s;
   char* wb = static_cast<char*>(h->ref_w);
   for (int i = 0; i < 3; ++i) {
     e = bme::pack_conv_rows_weights(ws[i], couts[i], cins[i], reinterpret_cast<uint16_t*>(wb + off[i]), st);
@@ -615,6 +641,7 @@ bayer_status_t bayer_refine_conv(bayer_me_t h, const float* feat, int n, int Hf,
 
 bayer_status_t bayer_me_multi_stream(bayer_me_t h, const bayer_pair_t* pairs, int n, int range, int interp,
                                      long long* end_ns, int* schedule, void* stream) {
+  NvtxRange nvtx_range("bayer_me_multi_stream");
   if (!h || !pairs || n < 1) return BAYER_ERR_INVALID_ARG;
   if (!bme::full16_even_supported(range)) return BAYER_ERR_UNSUPPORTED;
   if (interp != BAYER_INTERP_NEAREST && interp != BAYER_INTERP_BILINEAR) return BAYER_ERR_INVALID_ARG;
@@ -644,6 +671,18 @@ bayer_status_t bayer_me_multi_stream(bayer_me_t h, const bayer_pair_t* pairs, in
   return cuda_status(e);
 }
 
+bayer_status_t bayer_me_selftest_wait(bayer_me_t h, int arrive, unsigned limit, void* stream) {
+  if (!h || limit == 0) return BAYER_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  return cuda_status(bme::launch_wait_selftest(h->d_status, arrive != 0, limit, static_cast<cudaStream_t>(stream)));
+}
+
+bayer_status_t bayer_me_debug_fail_allocs(bayer_me_t h, int n) {
+  if (!h || n < 0) return BAYER_ERR_INVALID_ARG;
+  h->fail_allocs = n;
+  return BAYER_OK;
+}
+
 bayer_status_t bayer_me_sync_status(bayer_me_t h, void* stream) {
   if (!h) return BAYER_ERR_INVALID_ARG;
   DeviceGuard g(h->device);
@@ -658,6 +697,7 @@ bayer_status_t bayer_me_sync_status(bayer_me_t h, void* stream) {
 
 bayer_status_t bayer_probe_alu(bayer_me_t h, int variant, double* pc_per_clk_per_sm, double* sm_mhz,
                                int* sm_count) {
+  NvtxRange nvtx_range("bayer_probe_alu");
   if (!h || !pc_per_clk_per_sm || !sm_mhz || !sm_count || variant < 0 || variant > 2)
     return BAYER_ERR_INVALID_ARG;
   DeviceGuard g(h->device);

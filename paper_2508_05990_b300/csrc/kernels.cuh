@@ -164,6 +164,10 @@ cudaError_t ms_run(MultiStream* m, const bayer_pair_t* pairs, int n, int range, 
                    cudaStream_t st);
 int ms_config_nw(MultiStream* m, const bayer_pair_t* pairs, int n, int range, int interp);
 
+// Self-test of the bounded mbarrier wait (tc_common.cuh) every tcgen05 kernel
+// uses: BAYER_ERR_TIMEOUT lands in *status when nothing arrives.
+cudaError_t launch_wait_selftest(int* status, bool arrive, unsigned limit, cudaStream_t st);
+
 // Roofline probe of the SAD primitive.
 cudaError_t run_probe_alu(int variant, double* pc_per_clk_per_sm, double* sm_mhz, int* sm_count);
 
