@@ -369,7 +369,7 @@ cudaError_t cnn_forward_acts(const CnnFrames& fr, int batch, const uint16_t* wbf
       c.conf = conf;
       c.range = range;
     }
-    cudaError_t e = launch_conv_tc(c, l, fuse, st);
+    cudaError_t e = l <= 2 ? launch_conv_s2_rows_tc(c, l, st) : launch_conv_tc(c, l, fuse, st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

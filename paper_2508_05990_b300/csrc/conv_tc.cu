@@ -1,21 +1,20 @@
 // 3x3 stride-2 convolution (zero pad 1), 32 output channels, as an implicit
 // GEMM on the 5th-generation tensor cores: BF16 operands in shared memory,
-// FP32 accumulators in tensor memory (TMEM) -- the four layers of the
-// learned proposal network.
+// FP32 accumulators in tensor memory (TMEM) -- layers 3 and 4 of the learned
+// proposal network (few output rows; layers 1 and 2 stream rows through
+// conv_s2_tc.cu), and the weight packing of all four layers.
 //
 //   D[m, n] = sum_k A[m, k] * B[k, n],  m = output pixel, n = output channel,
 //   k = tap * CIN + ci,  A[m, k] = input at (2*oy + ky - 1, 2*ox + kx - 1, ci).
 //
 // Tile = 128 consecutive output pixels of one output row (MMA M = 128, N = 32);
 // CTA = 128 threads, persistent over tiles.
-//   Prologue: the layer's weights, packed once per forward into this kernel's
+//   Prologue: the layer's weights, packed once per forward into the kernels'
 //   shared-memory image (one launch of pack_conv_tc_weights for all four
 //   layers), are copied in with 16-byte loads and stay resident.
-//   Staging: per tile the three input rows, once (no im2col copy).  NHWC bf16
-//   input goes through asynchronous 16-byte copies (cp.async, zero-filled
-//   outside the map), so every load of the tile is in flight at once; layer 1
-//   gathers the Bayer frames with 16-byte loads and splits them into operand
-//   channels while storing.
+//   Staging: per tile the three NHWC bf16 input rows, once (no im2col copy),
+//   through asynchronous 16-byte copies (cp.async, zero-filled outside the
+//   map), so every load of the tile is in flight at once.
 //   MMA: after one barrier thread 0 issues 9 * CIN/16 MMAs whose A operands
 //   are shifted views of the staged rows and commits them to an mbarrier.
 //   Epilogue: TMEM -> registers -> bias, ReLU -> bf16 NHWC, or, for layer 4
@@ -25,9 +24,9 @@
 // epilogue.  Every mbarrier wait is bounded; on expiry the kernel records
 // BAYER_ERR_TIMEOUT in the status word, frees its TMEM and finishes.
 //
-// Layer 1 reads the Bayer frames directly: the 8 half-resolution planes
-// x = v/2048 - 1 are split exactly into two bf16 channels, hi = (v >> 4)/128 - 1
-// and lo = (v & 15)/16, with weights w and w/128, so that hi*w + lo*(w/128) = x*w.
+// Layer 1's operands split each 12-bit sample exactly into two bf16 channels,
+// hi = (v >> 4)/128 - 1 and lo = (v & 15)/16, with weights w and w/128, so that
+// hi*w + lo*(w/128) = (v/2048 - 1)*w; the packing below builds those weights.
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -69,11 +68,6 @@ struct RowConvLayout {
 __device__ __forceinline__ uint32_t bf2(float a, float b) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
   return *reinterpret_cast<const uint32_t*>(&v);
-}
-
-// hi/lo bf16 pair of a 12-bit sample (layer 1): hi = (v >> 4)/128 - 1, lo = (v & 15)/16.
-__device__ __forceinline__ uint32_t split12(uint32_t v) {
-  return bf2((float)(v >> 4) * (1.0f / 128.0f) - 1.0f, (float)(v & 15u) * (1.0f / 16.0f));
 }
 
 // 16-byte asynchronous copy global -> shared; src_bytes 0 zero-fills.
@@ -122,10 +116,10 @@ __global__ void pack_conv_tc_weights_kernel(const PackArgs pa, __nv_bfloat16* __
       __float2bfloat16_rn(wv);
 }
 
-// SRC: 0 bf16 NHWC input, 1 Bayer frames (hi/lo split).  EPI: 0 bias + ReLU
-// -> bf16 NHWC output; 1 bias + ReLU -> bf16 rounding -> 1x1 head (12
-// outputs) -> (range*tanh, range*tanh, sigmoid) of the 4 blocks of the pixel.
-template <int CIN, int SRC, int EPI>
+// EPI: 0 bias + ReLU -> bf16 NHWC output; 1 bias + ReLU -> bf16 rounding ->
+// 1x1 head (12 outputs) -> (range*tanh, range*tanh, sigmoid) of the 4 blocks
+// of the pixel.
+template <int CIN, int EPI>
 __global__ void __launch_bounds__(kM) conv3x3_tc_kernel(const ConvTcArgs a) {
   using L = RowConvLayout<CIN, EPI>;
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -162,7 +156,7 @@ __global__ void __launch_bounds__(kM) conv3x3_tc_kernel(const ConvTcArgs a) {
     const int c0 = kS * ox0 - 1;  // input column of staged column 0
 
     // ---- stage rows 2*oy - 1 .. 2*oy + 1, columns c0 .. c0 + NJ - 1
-    if (SRC == 0) {
+    {
       // item = (row rho, column j, chunk kc), kc fastest: a warp copies whole pixels
       constexpr int NITEM = 3 * L::NJ * L::KC;
       for (int it = tid; it < NITEM; it += kM) {
@@ -175,70 +169,6 @@ __global__ void __launch_bounds__(kM) conv3x3_tc_kernel(const ConvTcArgs a) {
         cp_async16(sX_addr + (((rho * kS + q) * L::KC + kc) * L::NP + pp) * 16, src, in_ok ? 16u : 0u);
       }
       cp_async_wait_all();
-    } else if (a.vec) {
-      // item = (row rho, frame f, group g of 4 half-resolution columns): two
-      // 16-byte loads (raw rows 2iy, 2iy+1) hold the 4 planes of 4 pixels.
-      // Group g covers columns hb + 4g .. hb + 4g + 3 with hb = c0 - 3 a
-      // multiple of 4, so (Wi a multiple of 4) a group is wholly in or out.
-      constexpr int NG = (L::NJ - 1) / 4 + 1;
-      constexpr int NITEM = 3 * 2 * NG;
-      constexpr int PER = (NITEM + kM - 1) / kM;
-      uint4 r0[PER], r1[PER];
-#pragma unroll
-      for (int u = 0; u < PER; ++u) {
-        const int it = tid + u * kM;
-        const int rho = it / (2 * NG), r = it - rho * (2 * NG);
-        const int f = r / NG, g = r - f * NG;
-        const int iy = kS * oy - 1 + rho, hx = c0 - 3 + 4 * g;
-        r0[u] = r1[u] = make_uint4(0, 0, 0, 0);
-        if (it < NITEM && iy >= 0 && iy < a.Hi && hx >= 0 && hx < a.Wi) {
-          const uint16_t* fb = f == 0 ? a.fr.ref + (long long)b * a.fr.ref_bs : a.fr.cur + (long long)b * a.fr.cur_bs;
-          const uint16_t* p = fb + (long long)(2 * iy) * a.fr.pitch + 2 * hx;
-          r0[u] = __ldg(reinterpret_cast<const uint4*>(p));
-          r1[u] = __ldg(reinterpret_cast<const uint4*>(p + a.fr.pitch));
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < PER; ++u) {
-        const int it = tid + u * kM;
-        if (it >= NITEM) continue;
-        const int rho = it / (2 * NG), r = it - rho * (2 * NG);
-        const int f = r / NG, g = r - f * NG;
-        const int iy = kS * oy - 1 + rho, hx = c0 - 3 + 4 * g;
-        const bool in_ok = iy >= 0 && iy < a.Hi && hx >= 0 && hx < a.Wi;
-        const uint32_t w0[4] = {r0[u].x, r0[u].y, r0[u].z, r0[u].w};
-        const uint32_t w1[4] = {r1[u].x, r1[u].y, r1[u].z, r1[u].w};
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const int j = 4 * g - 3 + t;
-          if (j < 0 || j >= L::NJ) continue;
-          uint4 v = make_uint4(0, 0, 0, 0);
-          if (in_ok)
-            v = make_uint4(split12(w0[t] & 0xFFFFu), split12(w0[t] >> 16), split12(w1[t] & 0xFFFFu),
-                           split12(w1[t] >> 16));
-          *reinterpret_cast<uint4*>(sX + (((rho * kS + (j & 1)) * L::KC + f) * L::NP + (j >> 1)) * 16) = v;
-        }
-      }
-    } else {
-      // unaligned frames: one 2-byte load per plane sample
-      constexpr int NITEM = 3 * L::NJ;
-      for (int it = tid; it < NITEM; it += kM) {
-        const int rho = it / L::NJ, j = it - rho * L::NJ;
-        const int iy = kS * oy - 1 + rho, ix = c0 + j;
-        const bool in_ok = iy >= 0 && iy < a.Hi && ix >= 0 && ix < a.Wi;
-        uint32_t wd[8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const uint16_t* f = (c < 4 ? a.fr.ref + (long long)b * a.fr.ref_bs : a.fr.cur + (long long)b * a.fr.cur_bs);
-          const int pl = c & 3;
-          wd[c] = in_ok ? split12(__ldg(f + (long long)(2 * iy + (pl >> 1)) * a.fr.pitch + 2 * ix + (pl & 1))) : 0u;
-        }
-        const int q = j & 1, pp = j >> 1;
-        *reinterpret_cast<uint4*>(sX + (((rho * kS + q) * L::KC + 0) * L::NP + pp) * 16) =
-            make_uint4(wd[0], wd[1], wd[2], wd[3]);
-        *reinterpret_cast<uint4*>(sX + (((rho * kS + q) * L::KC + 1) * L::NP + pp) * 16) =
-            make_uint4(wd[4], wd[5], wd[6], wd[7]);
-      }
     }
     tc::fence_proxy_async();
     __syncthreads();
@@ -306,10 +236,10 @@ __global__ void __launch_bounds__(kM) conv3x3_tc_kernel(const ConvTcArgs a) {
   if (!ok && tid == 0 && a.status) atomicExch(a.status, (int)BAYER_ERR_TIMEOUT);
 }
 
-template <int CIN, int SRC, int EPI>
+template <int CIN, int EPI>
 cudaError_t launch_t(const ConvTcArgs& a, cudaStream_t st) {
   using L = RowConvLayout<CIN, EPI>;
-  auto kern = conv3x3_tc_kernel<CIN, SRC, EPI>;
+  auto kern = conv3x3_tc_kernel<CIN, EPI>;
   int dev = 0, nsm = 148;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int per_sm = tc::ctas_per_sm(kern, kM, L::SMEM, L::TMEM_COLS);
@@ -321,10 +251,10 @@ cudaError_t launch_t(const ConvTcArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <int CIN, int SRC, int EPI>
+template <int CIN, int EPI>
 cudaError_t configure_t() {
   using L = RowConvLayout<CIN, EPI>;
-  auto kern = conv3x3_tc_kernel<CIN, SRC, EPI>;
+  auto kern = conv3x3_tc_kernel<CIN, EPI>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
   // prefer the largest shared-memory carveout so several CTAs fit per SM
   if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
@@ -350,15 +280,13 @@ cudaError_t pack_conv_tc_weights(const uint16_t* w, const int* w_off, const size
 
 cudaError_t configure_conv_tc() {
   cudaError_t e;
-  if ((e = configure_t<16, 1, 0>()) != cudaSuccess) return e;
-  if ((e = configure_t<32, 0, 0>()) != cudaSuccess) return e;
-  return configure_t<32, 0, 1>();
+  if ((e = configure_t<32, 0>()) != cudaSuccess) return e;
+  return configure_t<32, 1>();
 }
 
 cudaError_t launch_conv_tc(const ConvTcArgs& a, int layer, bool head, cudaStream_t st) {
-  if (layer == 1 && !head) return launch_t<16, 1, 0>(a, st);
-  if (layer > 1 && !head) return launch_t<32, 0, 0>(a, st);
-  if (layer > 1 && head) return launch_t<32, 0, 1>(a, st);
+  if (layer > 1 && !head) return launch_t<32, 0>(a, st);
+  if (layer > 1 && head) return launch_t<32, 1>(a, st);
   return cudaErrorInvalidValue;
 }
 

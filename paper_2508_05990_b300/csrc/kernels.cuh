@@ -73,10 +73,12 @@ cudaError_t cnn_loss_grad(const CnnFrames& fr, int batch, const uint16_t* wbf16,
                           float neg_weight, void* acts, void* dpre, float* grad, float* loss, int* status,
                           cudaStream_t st);
 
-// 3x3 stride-2 convolution, 32 output channels, on the tensor cores
-// (conv_tc.cu): the proposal network's layers.  NHWC bf16 in (layer 1: the
-// Bayer frames), bias + ReLU, NHWC bf16 out, or (head fused, layer 4) the 1x1
-// head straight to the per-block proposals and confidences.
+// 3x3 stride-2 convolutions, 32 output channels, on the tensor cores: the
+// proposal network's layers.  NHWC bf16 in (layer 1: the Bayer frames), bias +
+// ReLU, NHWC bf16 out, or (head fused, layer 4) the 1x1 head straight to the
+// per-block proposals and confidences.  Layers 1 and 2 stream rows
+// (conv_s2_tc.cu: launch_conv_s2_rows_tc); layers 3 and 4 work in tiles
+// (conv_tc.cu: launch_conv_tc, which also packs the weights of all four).
 struct ConvTcArgs {
   const __nv_bfloat16* in;  // layers 2..4: [batch][Hi][Wi][32] bf16
   CnnFrames fr;             // layer 1: frames; Hi, Wi are the half-resolution dims
@@ -100,7 +102,9 @@ cudaError_t configure_conv_tc();
 size_t conv_tc_weight_bytes(int cin_op);
 cudaError_t pack_conv_tc_weights(const uint16_t* w, const int* w_off, const size_t* img_off, uint16_t* img,
                                  cudaStream_t st);
-cudaError_t launch_conv_tc(const ConvTcArgs& a, int layer, bool head, cudaStream_t st);
+cudaError_t launch_conv_tc(const ConvTcArgs& a, int layer, bool head, cudaStream_t st);  // layers 3, 4
+cudaError_t configure_conv_s2_rows_tc();
+cudaError_t launch_conv_s2_rows_tc(const ConvTcArgs& a, int layer, cudaStream_t st);
 
 // 3x3 stride-1 convolution streamed row by row on the tensor cores
 // (conv_rows_tc.cu): NHWC input (bf16, or float32 rounded to bf16 when
