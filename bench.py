@@ -226,6 +226,38 @@ class ClockSampler:
                 "window": "timed region" if inside else "whole run"}
 
 
+def pcie_link(nbytes=256 << 20, reps=5):
+    """Host <-> device copy bandwidth of this machine with pinned buffers: each
+    direction alone and both at once (two streams), GB/s."""
+    import torch
+    h_a = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    h_b = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d_a = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    d_b = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    s_up, s_down = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / reps
+
+    def both():
+        with torch.cuda.stream(s_up):
+            d_a.copy_(h_a, non_blocking=True)
+        with torch.cuda.stream(s_down):
+            h_b.copy_(d_b, non_blocking=True)
+
+    up = timed(lambda: d_a.copy_(h_a, non_blocking=True))
+    down = timed(lambda: h_a.copy_(d_a, non_blocking=True))
+    bi = timed(both)
+    return {"h2d_gbs": round(nbytes / up / 1e9, 1), "d2h_gbs": round(nbytes / down / 1e9, 1),
+            "bidirectional_gbs": round(2 * nbytes / bi / 1e9, 1)}
+
+
 def cpu_baseline_sample(frames, feats):
     """Oracle (as it stands) on one of the 7 pairs: exhaustive search + bilinear warp."""
     import oracle
@@ -564,6 +596,7 @@ def run_ours(args):
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, device="cuda")
     h2d = frames.nbytes + feats.nbytes
     d2h = pin_mv.nbytes + pin_out.nbytes
+    link = pcie_link()
 
     result = None
     if rank == 0:
@@ -598,7 +631,10 @@ def run_ours(args):
             "mblocks_per_s": round(value * hb * wb / 1e6, 3),
             "e2e": {"value": round(world * PAIRS * args.steps / e2e_s, 2), "unit": UNIT,
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                    "api": "bayer_clip_process_host (pinned host buffers, 3 streams)"},
+                    "api": "bayer_clip_process_host (pinned host buffers, 3 streams)",
+                    "link": dict(link, frac_of_bidirectional=round((h2d + d2h) * args.steps / e2e_s / 1e9
+                                                                   / link["bidirectional_gbs"], 4))},
+            "gpu": torch.cuda.get_device_name(local),
             "gpu_launches": gpu_launches,
             "clocks": clocks,
             "learned_seeded": learned,

@@ -26,24 +26,35 @@ struct Full16Strip {
   static_assert(SPAN % 4 == 0, "span must be a multiple of 4 words");
 };
 
-// SAD of every candidate of one 16x16 block, computed by one warp from a
-// staged window (wbase: the block's window origin, row pitch P words) and
-// current block (cbase, row pitch PC words); returns the lane's best key.
-template <int R, int P, int PC>
-__device__ __forceinline__ uint64_t full16_block(const uint32_t* wbase, const uint32_t* cbase, int lane, int xb, int yb,
-                                                 int W, int H) {
-  constexpr int NU = 2 * R + 1, REACH = 2 * R, SPAN = 16 + 2 * REACH;
-  const int v = lane < NU ? lane : NU - 1;  // lanes past the last row repeat it
-  const int eps = (lane >> 2) & 1;          // row rotation for conflict-free loads
-
+// Accumulators of one lane: its candidate row (NU candidates), and for
+// R = 16 the lane's candidate of the 33rd row and its share of the corner.
+template <int R>
+struct Full16Acc {
+  static constexpr int NU = 2 * R + 1;
   uint32_t acc[NU];
+  uint32_t accx, accc;
+};
+
+// SADs of block rows RB .. RB + NRW - 1 of one 16x16 block against every
+// candidate, accumulated by one warp from a staged window (wbase: the block's
+// window origin, row pitch P words) and current block (cbase, row pitch PC
+// words).  Lane v owns candidate row v (lanes past the last row repeat it).
+template <int R, int P, int PC, int RB, int NRW>
+__device__ __forceinline__ void full16_accumulate(const uint32_t* wbase, const uint32_t* cbase, int lane,
+                                                  Full16Acc<R>& A) {
+  constexpr int NU = 2 * R + 1, REACH = 2 * R, SPAN = 16 + 2 * REACH;
+  static_assert(NRW == 4 || NRW == 8 || NRW == 16, "row ranges of 4, 8 or 16");
+  const int v = lane < NU ? lane : NU - 1;
+  const int eps = (lane >> 2) & 1;  // row rotation for conflict-free loads
+
 #pragma unroll
-  for (int k = 0; k < NU; ++k) acc[k] = 0;
-  uint32_t accx = 0, accc = 0;
+  for (int k = 0; k < NU; ++k) A.acc[k] = 0;
+  A.accx = 0;
+  A.accc = 0;
 
 #pragma unroll 1
-  for (int i = 0; i < 16; ++i) {
-    const int r = (i + eps) & 15;
+  for (int i = 0; i < NRW; ++i) {
+    const int r = RB + ((i + eps) & (NRW - 1));
     uint32_t c[16];
     const uint4* cp = reinterpret_cast<const uint4*>(cbase + r * PC);
 #pragma unroll
@@ -65,7 +76,7 @@ __device__ __forceinline__ uint64_t full16_block(const uint32_t* wbase, const ui
 #pragma unroll
         for (int k = 0; k < NU; ++k) {
           const int cc = p - 2 * k;
-          if (cc >= 0 && cc < 16) acc[k] = sad_u32(rr[s], c[cc], acc[k]);
+          if (cc >= 0 && cc < 16) A.acc[k] = sad_u32(rr[s], c[cc], A.acc[k]);
         }
       }
     }
@@ -75,15 +86,22 @@ __device__ __forceinline__ uint64_t full16_block(const uint32_t* wbase, const ui
 #pragma unroll
       for (int t2 = 0; t2 < 8; ++t2) {
         const uint2 e2 = xp[t2];
-        accx = sad_u32(e2.x, c[2 * t2], accx);
-        accx = sad_u32(e2.y, c[2 * t2 + 1], accx);
+        A.accx = sad_u32(e2.x, c[2 * t2], A.accx);
+        A.accx = sad_u32(e2.y, c[2 * t2 + 1], A.accx);
       }
       // corner candidate (u, v) = (32, 32): lane l < 16 takes column l
-      if (lane < 16) accc = sad_u32(wbase[(64 + r) * P + 64 + lane], cbase[r * PC + lane], accc);
+      if (lane < 16) A.accc = sad_u32(wbase[(64 + r) * P + 64 + lane], cbase[r * PC + lane], A.accc);
     }
   }
+}
 
-  // ---- argmin with the (sad, |mv|_1, dy, dx) key
+// The lane's best key (sad, |mv|_1, dy, dx) from its complete accumulators;
+// the warp minimum of the returned keys is the block's MV.  (xb, yb): the
+// block's top-left pixel, for the validity of out-of-frame candidates.
+template <int R>
+__device__ __forceinline__ uint64_t full16_select(const Full16Acc<R>& A, int lane, int xb, int yb, int W, int H) {
+  constexpr int NU = 2 * R + 1, REACH = 2 * R;
+  const int v = lane < NU ? lane : NU - 1;
   const int dy = 2 * v - REACH;
   uint64_t best = kInvalidKey;
   const bool interior = xb >= REACH && xb + 16 + REACH <= W && yb >= REACH && yb + 16 + REACH <= H;
@@ -95,7 +113,7 @@ __device__ __forceinline__ uint64_t full16_block(const uint32_t* wbase, const ui
 #pragma unroll
     for (int k = 0; k < NU; ++k) {
       const uint32_t rank = k == R ? 0u : (k < R ? (uint32_t)(2 * (R - k) - 1) : (uint32_t)(2 * (k - R)));
-      const uint32_t key = acc[k] * 64u + rank;
+      const uint32_t key = A.acc[k] * 64u + rank;
       m = key < m ? key : m;
     }
     const uint32_t rank = m & 63u;
@@ -107,7 +125,7 @@ __device__ __forceinline__ uint64_t full16_block(const uint32_t* wbase, const ui
     for (int k = 0; k < NU; ++k) {
       const int dx = 2 * k - REACH;
       const bool ok = row_ok && xb + dx >= 0 && xb + dx + 16 <= W;
-      const uint64_t key = ok ? make_key(acc[k], dx, dy) : kInvalidKey;
+      const uint64_t key = ok ? make_key(A.acc[k], dx, dy) : kInvalidKey;
       best = key < best ? key : best;
     }
   }
@@ -115,16 +133,27 @@ __device__ __forceinline__ uint64_t full16_block(const uint32_t* wbase, const ui
     {
       const int dx = 2 * lane - REACH;
       const bool ok = yb + 48 <= H && xb + dx >= 0 && xb + dx + 16 <= W;
-      const uint64_t key = ok ? make_key(accx, dx, 32) : kInvalidKey;
+      const uint64_t key = ok ? make_key(A.accx, dx, 32) : kInvalidKey;
       best = key < best ? key : best;
     }
-    const uint32_t corner = __reduce_add_sync(0xffffffffu, accc);
+    const uint32_t corner = __reduce_add_sync(0xffffffffu, A.accc);
     if (lane == 0 && xb + 48 <= W && yb + 48 <= H) {
       const uint64_t key = make_key(corner, 32, 32);
       best = key < best ? key : best;
     }
   }
   return best;
+}
+
+// SAD of every candidate of one 16x16 block, computed by one warp from a
+// staged window (wbase: the block's window origin, row pitch P words) and
+// current block (cbase, row pitch PC words); returns the lane's best key.
+template <int R, int P, int PC>
+__device__ __forceinline__ uint64_t full16_block(const uint32_t* wbase, const uint32_t* cbase, int lane, int xb, int yb,
+                                                 int W, int H) {
+  Full16Acc<R> A;
+  full16_accumulate<R, P, PC, 0, 16>(wbase, cbase, lane, A);
+  return full16_select<R>(A, lane, xb, yb, W, H);
 }
 
 // Stage the window and current tile of the strip whose first block is at
