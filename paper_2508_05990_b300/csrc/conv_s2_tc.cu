@@ -59,13 +59,13 @@ constexpr uint32_t kWaitLimit = 1u << 22;
 // (n / 8) * (9 * KC) * 128 + (k / 8) * 128 + (n % 8) * 16 + (k % 8) * 2.
 // Ring: NR slots filled by G producer groups taking rows j % G (slot j % NR
 // always belongs to group j % G).  Layer 1 (Bayer frames) has small rows and
-// little work per loaded byte, so it keeps more rows in flight: 8 slots, 4
-// groups; layer 2: 4 slots, 2 groups.
+// little work per loaded byte, so it keeps more rows in flight: 8 slots, 8
+// one-warp groups; layer 2: 4 slots, 2 groups.
 template <int CIN, int SRC>
 struct S2Layout {
   static constexpr int KC = CIN / 8;
   static constexpr int NR = SRC == 1 ? 8 : 4;
-  static constexpr int G = SRC == 1 ? 4 : 2;
+  static constexpr int G = SRC == 1 ? 8 : 2;
   static constexpr int GT = kProdThreads / G;
   static constexpr int SLOT_BYTES = 2 * KC * kNP * 16;
   static constexpr int B_BYTES = 9 * CIN * kN * 2;
@@ -85,8 +85,14 @@ __device__ __forceinline__ uint32_t bf2(float a, float b) {
 }
 
 // hi/lo bf16 pair of a 12-bit sample: hi = (v >> 4)/128 - 1, lo = (v & 15)/16.
+// Without integer-to-float conversions: the float with bit pattern
+// 0x4B000000 | k is 2^23 + k, so (2^23 + k)/128 - 65537 = k/128 - 1 and
+// (2^23 + m)/16 - 2^19 = m/16, each one fma whose exact result is
+// representable (so it is returned unrounded).
 __device__ __forceinline__ uint32_t split12(uint32_t v) {
-  return bf2((float)(v >> 4) * (1.0f / 128.0f) - 1.0f, (float)(v & 15u) * (1.0f / 16.0f));
+  const float hi = fmaf(__uint_as_float(0x4B000000u | (v >> 4)), 1.0f / 128.0f, -65537.0f);
+  const float lo = fmaf(__uint_as_float(0x4B000000u | (v & 15u)), 1.0f / 16.0f, -524288.0f);
+  return bf2(hi, lo);
 }
 
 // The CTA's output rows [t, t1) of the (image, segment, y)-ordered list, cut
