@@ -684,6 +684,42 @@ def run_reference(args):
     }
 
 
+def run_refine_only(n_maps: int):
+    """The 4K form's refine convolutions alone on n_maps 540 x 960 x 128 NHWC maps
+    (He-normal weights, N(0,1) input), three untimed and five timed calls: a small
+    case for profiling the tensor-core kernels."""
+    import torch
+    from paper_2508_05990_b300 import bayer_me as bm
+    from paper_2508_05990_b300 import build, synth
+    build.build()
+    shapes = [(K4_HIDDEN, K4_C, 3, 3), (K4_HIDDEN,), (K4_HIDDEN, K4_HIDDEN, 3, 3), (K4_HIDDEN,), (K4_C, K4_HIDDEN, 3, 3),
+              (K4_C,)]
+    theta = synth.he_normal_params(K4_SEED, [("w" if len(sh) == 4 else "b", sh) for sh in shapes])
+    wts, o = [], 0
+    for sh in shapes:
+        nsz = int(np.prod(sh))
+        wts.append(torch.from_numpy(theta[o:o + nsz].astype(np.float32).reshape(sh)).cuda())
+        o += nsz
+    hf, wf = K4_H // K4_STRIDE, K4_W // K4_STRIDE
+    feat = torch.randn((n_maps, hf, wf, K4_C), generator=torch.Generator(device="cuda").manual_seed(K4_SEED),
+                       device="cuda")
+    h = bm.Handle(0)
+    out = torch.empty_like(feat)
+    for _ in range(3):
+        h.refine_conv(feat, wts, out=out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(5):
+        h.refine_conv(feat, wts, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 5
+    flops = n_maps * refine_flops_per_frame()
+    h.close()
+    return {"refine_maps": n_maps, "ms": round(ms, 4), "tflops": round(flops / (ms / 1e3) / 1e12, 1)}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -693,7 +729,12 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
     ap.add_argument("--no-legs", action="store_true",
                     help="skip the batched multi-stream and 4K precision legs (single-GPU runs only)")
+    ap.add_argument("--refine-maps", type=int, default=0,
+                    help="profiling aid: time only the BF16 refine convolutions on this many 4K-form maps and exit")
     args = ap.parse_args(argv)
+    if args.refine_maps > 0:
+        print(json.dumps(run_refine_only(args.refine_maps)), flush=True)
+        return
     if args.warmup < 3 and args.impl == "ours":
         ap.error("--warmup must be >= 3")
     res = run_reference(args) if args.impl == "reference" else run_ours(args)
