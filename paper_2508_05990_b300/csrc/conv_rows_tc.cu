@@ -47,8 +47,22 @@ constexpr uint32_t kWaitLimit = 1u << 22;
 // consecutive pixels (SBO 128 B), next K chunk one plane further (LBO kNP * 16).
 // Weights: element (n, k), k = tap * CIN + ci, at
 // (n / 8) * (9 * KC) * 128 + (k / 8) * 128 + (n % 8) * 16 + (k % 8) * 2.
+//
+// COUT = 64 layers stack the three tap rows along N: B row n = ky * 64 + co,
+// K index k = kx * CIN + ci, element (n, k) at
+// (n / 8) * (3 * KC) * 128 + (k / 8) * 128 + (n % 8) * 16 + (k % 8) * 2.  One
+// MMA with N = 192 then applies an input row's three tap rows at once, to the
+// accumulators of output rows r + 1, r and r - 1, which sit in adjacent
+// 64-column TMEM slots: slot(o) = NS - 1 - o % NS for the CTA's o-th output
+// row.  Where those slots wrap around or a row lies outside the run, the MMA
+// is split into N = 64 / 128 pieces.  Every MMA accumulates: the epilogue
+// zeroes a slot after draining it (and all slots at the start).  A staged row
+// is read by 24 MMAs instead of 72, which cuts the tensor cores' shared-memory
+// operand traffic by 44 %.
 template <int CIN, int COUT, int SRC>
 struct RowStreamLayout {
+  static constexpr bool STACK = COUT == 64;
+  static constexpr int NS = STACK ? 8 : kAcc;  // accumulator slots
   static constexpr int KC = CIN / 8;
   static constexpr int SLOT_BYTES = KC * kNP * 16;
   static constexpr int NR = SRC == 2 ? 2 : 4;  // ring slots (float32 input: the weights leave room for 2)
@@ -56,10 +70,10 @@ struct RowStreamLayout {
   static constexpr int GT = kProdThreads / NG;
   static constexpr int B_BYTES = 9 * CIN * COUT * 2;
   static constexpr int BAR_OFF = B_BYTES + NR * SLOT_BYTES;
-  static constexpr int NBAR = 2 * NR + 2 * kAcc + 1;
+  static constexpr int NBAR = 2 * NR + 2 * NS + 1;
   static constexpr int BIAS_OFF = (BAR_OFF + NBAR * 8 + 16 + 15) / 16 * 16;  // float32 bias, read as broadcasts
   static constexpr int SMEM = BIAS_OFF + COUT * 4;
-  static constexpr int TMEM_COLS = kAcc * COUT;
+  static constexpr int TMEM_COLS = NS * COUT;
   static_assert(CIN % 16 == 0 && (COUT == 64 || COUT == 128), "shape");
   static_assert(B_BYTES % 16 == 0 && SLOT_BYTES % 16 == 0, "alignment");
   static_assert(SMEM <= 227 * 1024, "shared memory");
@@ -105,8 +119,8 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_rows_tc_kernel(const Conv
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::BAR_OFF);
   uint64_t* empty = full + L::NR;
   uint64_t* acc_full = empty + L::NR;
-  uint64_t* acc_empty = acc_full + kAcc;
-  uint64_t* mma_done = acc_empty + kAcc;
+  uint64_t* acc_empty = acc_full + L::NS;
+  uint64_t* mma_done = acc_empty + L::NS;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -116,7 +130,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_rows_tc_kernel(const Conv
       tc::mbar_init(&full[s], L::GT);
       tc::mbar_init(&empty[s], 1);
     }
-    for (int i = 0; i < kAcc; ++i) {
+    for (int i = 0; i < L::NS; ++i) {
       tc::mbar_init(&acc_full[i], 1);
       tc::mbar_init(&acc_empty[i], kEpiWarps);
     }
@@ -215,7 +229,6 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_rows_tc_kernel(const Conv
     // ---- MMA issue: one thread
     if (lane == 0) {
       const uint32_t sX_addr = tc::smem_addr(sX), sB_addr = tc::smem_addr(sB);
-      constexpr uint32_t idesc = tc::idesc_bf16_f32(kM, COUT);
       long long j = 0, o = 0;
       bool stop = false;
       while (!stop && runs.next()) {
@@ -228,33 +241,84 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_rows_tc_kernel(const Conv
           }
           tc::fence_after_sync();
           const uint32_t xs = sX_addr + slot * L::SLOT_BYTES;
-#pragma unroll
-          for (int ky = 0; ky < 3; ++ky) {
-            const int y = r + 1 - ky;
-            if (y < runs.ya || y >= runs.yb) continue;
-            const long long oo = o + (y - runs.ya);
-            const int acc = (int)(oo % kAcc);
-            const long long use = oo / kAcc;
-            if (ky == 0 && use > 0) {  // first contribution: the accumulator's previous row must be drained
-              if (!tc::mbar_wait(&acc_empty[acc], (uint32_t)((use - 1) & 1), kWaitLimit)) {
+          if constexpr (L::STACK) {
+            // tap row ky of input row r goes to output row r + 1 - ky, held in slot s_ky
+            const int y0 = r + 1;
+            const bool v0 = y0 >= runs.ya && y0 < runs.yb, v1 = y0 - 1 >= runs.ya && y0 - 1 < runs.yb,
+                       v2 = y0 - 2 >= runs.ya && y0 - 2 < runs.yb;
+            const int s0 = L::NS - 1 - (int)((o + (y0 - runs.ya)) % L::NS);
+            const int s1 = s0 == L::NS - 1 ? 0 : s0 + 1, s2 = s1 == L::NS - 1 ? 0 : s1 + 1;
+            if (v0) {  // first contribution to row r + 1: its slot must be drained and zeroed
+              const long long use = (o + (y0 - runs.ya)) / L::NS;
+              if (!tc::mbar_wait(&acc_empty[s0], (uint32_t)(use & 1), kWaitLimit)) {
                 raise_abort(abort_flag, a.status);
                 stop = true;
                 break;
               }
               tc::fence_after_sync();
             }
-            const uint32_t d = tmem + (uint32_t)(acc * COUT);
+            // one MMA of N = 64 * cnt for tap rows kys .. kys + cnt - 1 (adjacent slots from sidx)
+            auto issue = [&](int kys, int cnt, int sidx) {
+              const uint32_t d = tmem + (uint32_t)(sidx * COUT);
+              const uint32_t idesc = tc::idesc_bf16_f32(kM, 64 * cnt);
+              const uint32_t bstack = sB_addr + (uint32_t)(kys * 8 * (3 * KC * 128));
+#pragma unroll 1
+              for (int kx = 0; kx < 3; ++kx) {
 #pragma unroll
-            for (int kx = 0; kx < 3; ++kx) {
-#pragma unroll
-              for (int s2 = 0; s2 < CIN / 16; ++s2) {
-                const uint64_t ad = tc::smem_desc(xs + (uint32_t)((2 * s2 * kNP + kx) * 16), kNP * 16, 128);
-                const uint64_t bd =
-                    tc::smem_desc(sB_addr + (uint32_t)(((ky * 3 + kx) * KC + 2 * s2) * 128), 128, 9 * KC * 128);
-                tc::mma_bf16(d, ad, bd, idesc, (ky == 0 && kx == 0 && s2 == 0) ? 0u : 1u);
+                for (int t2 = 0; t2 < CIN / 16; ++t2) {
+                  const uint64_t ad = tc::smem_desc(xs + (uint32_t)((2 * t2 * kNP + kx) * 16), kNP * 16, 128);
+                  const uint64_t bd = tc::smem_desc(bstack + (uint32_t)((kx * KC + 2 * t2) * 128), 128, 3 * KC * 128);
+                  tc::mma_bf16(d, ad, bd, idesc, 1u);
+                }
+              }
+            };
+            const bool a01 = s1 == s0 + 1, a12 = s2 == s1 + 1;  // no wrap-around between the slots
+            if (v0 && v1 && v2 && a01 && a12) {
+              issue(0, 3, s0);
+            } else {
+              if (v0 && v1 && a01) {
+                issue(0, 2, s0);
+                if (v2) issue(2, 1, s2);
+              } else if (v1 && v2 && a12) {
+                if (v0) issue(0, 1, s0);
+                issue(1, 2, s1);
+              } else {
+                if (v0) issue(0, 1, s0);
+                if (v1) issue(1, 1, s1);
+                if (v2) issue(2, 1, s2);
               }
             }
-            if (ky == 2) tc::commit(&acc_full[acc]);  // last contribution to output row y
+            if (v2) tc::commit(&acc_full[s2]);  // output row r - 1 complete
+          } else {
+            constexpr uint32_t idesc = tc::idesc_bf16_f32(kM, COUT);
+#pragma unroll
+            for (int ky = 0; ky < 3; ++ky) {
+              const int y = r + 1 - ky;
+              if (y < runs.ya || y >= runs.yb) continue;
+              const long long oo = o + (y - runs.ya);
+              const int acc = (int)(oo % kAcc);
+              const long long use = oo / kAcc;
+              if (ky == 0 && use > 0) {  // first contribution: the accumulator's previous row must be drained
+                if (!tc::mbar_wait(&acc_empty[acc], (uint32_t)((use - 1) & 1), kWaitLimit)) {
+                  raise_abort(abort_flag, a.status);
+                  stop = true;
+                  break;
+                }
+                tc::fence_after_sync();
+              }
+              const uint32_t d = tmem + (uint32_t)(acc * COUT);
+#pragma unroll
+              for (int kx = 0; kx < 3; ++kx) {
+#pragma unroll
+                for (int s2 = 0; s2 < CIN / 16; ++s2) {
+                  const uint64_t ad = tc::smem_desc(xs + (uint32_t)((2 * s2 * kNP + kx) * 16), kNP * 16, 128);
+                  const uint64_t bd =
+                      tc::smem_desc(sB_addr + (uint32_t)(((ky * 3 + kx) * KC + 2 * s2) * 128), 128, 9 * KC * 128);
+                  tc::mma_bf16(d, ad, bd, idesc, (ky == 0 && kx == 0 && s2 == 0) ? 0u : 1u);
+                }
+              }
+              if (ky == 2) tc::commit(&acc_full[acc]);  // last contribution to output row y
+            }
           }
           if (stop) break;
           tc::commit(&empty[slot]);  // staged row consumed once these MMAs finish
@@ -268,12 +332,23 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_rows_tc_kernel(const Conv
     __syncwarp();
   } else {
     // ---- epilogue: thread = pixel of the segment = TMEM lane
+    if constexpr (L::STACK) {
+      // every slot starts zeroed (first phase of its acc_empty barrier)
+      for (int sidx = 0; sidx < L::NS; ++sidx) {
+#pragma unroll
+        for (int cc = 0; cc < COUT; cc += 32)
+          tc::tmem_zero32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(sidx * COUT + cc));
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&acc_empty[sidx]);
+      }
+    }
     long long o = 0;
     bool stop = false;
     while (!stop && runs.next()) {
       for (int y = runs.ya; y < runs.yb; ++y, ++o) {
-        const int acc = (int)(o % kAcc);
-        const bool got = !*abort_flag && tc::mbar_wait(&acc_full[acc], (uint32_t)((o / kAcc) & 1), kWaitLimit);
+        const int acc = L::STACK ? L::NS - 1 - (int)(o % L::NS) : (int)(o % kAcc);
+        const bool got = !*abort_flag && tc::mbar_wait(&acc_full[acc], (uint32_t)((o / L::NS) & 1), kWaitLimit);
         if (!__all_sync(0xffffffffu, got)) {
           raise_abort(abort_flag, a.status);
           stop = true;
@@ -287,7 +362,8 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_rows_tc_kernel(const Conv
         for (int cc = 0; cc < COUT; cc += 32) {
           float v[32];
           tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * COUT + cc), v);
-          if (cc + 32 == COUT) {  // accumulator drained: hand it back to the MMA thread
+          if (L::STACK) tc::tmem_zero32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * COUT + cc));
+          if (cc + 32 == COUT) {  // accumulator drained (and zeroed): hand it back to the MMA thread
             tc::fence_before_sync();
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&acc_empty[acc]);
@@ -329,15 +405,34 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_rows_tc_kernel(const Conv
   }
 }
 
-// float32 [cout][cin][3][3] -> bf16 image of the shared-memory weight layout.
+// float32 [cout][cin][3][3] -> bf16 image of the shared-memory weight layout:
+// tap-major K (k = tap * cin + ci) for cout != 64, tap rows stacked along N
+// (n = ky * 64 + co, k = kx * cin + ci) for cout == 64.
 __global__ void pack_rows_weights_kernel(const float* __restrict__ w, int cout, int cin, uint16_t* __restrict__ img) {
   const int n_el = cout * 9 * cin;
   const int kc = cin / 8;
+  const bool stack = cout == 64;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_el; i += gridDim.x * blockDim.x) {
-    const int n = i / (9 * cin), k = i - n * 9 * cin;
-    const int tap = k / cin, ci = k - tap * cin;
-    const __nv_bfloat16 v = __float2bfloat16_rn(w[((long long)n * cin + ci) * 9 + tap]);
-    img[(n >> 3) * (9 * kc) * 64 + (k >> 3) * 64 + (n & 7) * 8 + (k & 7)] = *reinterpret_cast<const uint16_t*>(&v);
+    int n, k, co, ci, ky, kx;
+    if (stack) {
+      n = i / (3 * cin);
+      k = i - n * 3 * cin;
+      ky = n / cout;
+      co = n - ky * cout;
+      kx = k / cin;
+      ci = k - kx * cin;
+    } else {
+      n = i / (9 * cin);
+      k = i - n * 9 * cin;
+      const int tap = k / cin;
+      ci = k - tap * cin;
+      co = n;
+      ky = tap / 3;
+      kx = tap - 3 * ky;
+    }
+    const __nv_bfloat16 v = __float2bfloat16_rn(w[(((long long)co * cin + ci) * 3 + ky) * 3 + kx]);
+    const int kchunks = stack ? 3 * kc : 9 * kc;
+    img[(n >> 3) * kchunks * 64 + (k >> 3) * 64 + (n & 7) * 8 + (k & 7)] = *reinterpret_cast<const uint16_t*>(&v);
   }
 }
 
