@@ -186,3 +186,34 @@ def test_seeded_fast_path_vs_oracle(handle, mode):
     if mode in ("all_fallback", "at_optimum"):
         for k in ("dx", "dy", "sad"):
             np.testing.assert_array_equal(g[k], full[k])
+
+
+def test_learned_1080p_clip_as_benchmarked(handle):
+    """The benchmark's learned-seeded step: the 7 pairs of the 1080p clip in
+    one call with the committed trained weights.  Equals SEEDED mode on the
+    network's own proposals bit for bit (fallback flags too), and two pairs
+    equal the oracle's seeded search given those proposals."""
+    import os
+    wl = synth.WORKLOADS["1080p"]
+    H, W = wl["H"], wl["W"]
+    frames = synth.pan_clip(wl["seed"], H, W, n_frames=wl["frames"])
+    d = dev(frames)
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2508_05990_b300",
+                        "weights", "proposal_1080p_r32.npz")
+    wbf = bm.to_bf16_bits(torch.from_numpy(np.load(path)["theta"].astype(np.float32)).cuda()).contiguous()
+    kw = dict(batch=7, ref_batch_stride=H * W, cur_batch_stride=H * W)
+    fb = torch.empty((7, H // 16, W // 16), dtype=torch.uint8, device="cuda")
+    got = handle.estimate_learned(d, d[1:], wbf, 32, 0.5, fallback=fb, **kw)
+    prop, conf = handle.cnn_forward(d, d[1:], wbf, 32, **kw)
+    fb2 = torch.empty_like(fb)
+    want = handle.estimate_ex(d, d[1:], mode=bm.MODE_SEEDED, search_range=32, prop_dxdy=prop, conf=conf,
+                              fallback=fb2, **kw)
+    torch.cuda.synchronize()
+    assert torch.equal(got, want) and torch.equal(fb, fb2)
+    p, c = prop.cpu().numpy(), conf.cpu().numpy()
+    for t in (0, 6):
+        ref_field, ref_fb, _ = oracle.me_seeded(frames[t], frames[t + 1], 16, 32, p[t, ..., 0], p[t, ..., 1], c[t])
+        g = bm.records_to_numpy(got[t])
+        for k in ("dx", "dy", "sad"):
+            np.testing.assert_array_equal(g[k], ref_field[k])
+        np.testing.assert_array_equal(fb[t].cpu().numpy(), ref_fb)

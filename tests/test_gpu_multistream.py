@@ -67,3 +67,43 @@ def test_multi_stream_rejects_bad_sizes(handle):
     mv = torch.empty((2, 4, 2), dtype=torch.int32, device="cuda")
     with pytest.raises(bm.BayerError):
         handle.multi_stream([{"ref": fr, "cur": fr, "mv": mv}], 32)  # H not a multiple of 16
+
+
+def test_multi_stream_bench_configuration(handle):
+    """The benchmark's batched configuration: 32 streams (8x 640x480, 8x
+    1280x720, 12x 1920x1088, 4x 3840x2160), one pair each, +-32, bilinear
+    propagation of 256-channel stride-8 maps, in one call.  Every pair equals
+    the single-pair search and propagation launches bit for bit; one pair of
+    each size is checked against the oracle (whole MV field, whole map)."""
+    sizes = [(480, 640)] * 8 + [(720, 1280)] * 8 + [(1088, 1920)] * 12 + [(2160, 3840)] * 4
+    C, s = 256, 8
+    streams = []
+    for i, (H, W) in enumerate(sizes):
+        fr = synth.pan_clip(5000 + i, H, W, n_frames=2)
+        f = synth.features(6000 + i, C, H // s, W // s)[0]
+        streams.append({"np": fr, "ref": torch.from_numpy(fr[0]).cuda(),
+                        "cur": torch.from_numpy(fr[1]).cuda(),
+                        "mv": torch.empty((H // 16, W // 16, 2), dtype=torch.int32, device="cuda"),
+                        "feat_np": f, "feat": torch.from_numpy(f).cuda(),
+                        "feat_out": torch.empty((C, H // s, W // s), device="cuda"), "stride": s})
+    end = torch.zeros(len(sizes), dtype=torch.int64, device="cuda")
+    handle.multi_stream(streams, 32, end_ns=end)
+    torch.cuda.synchronize()
+    assert handle.sync_status() == bm.OK
+    assert (end.cpu().numpy() > 0).all()
+    checked = set()
+    for q, (H, W) in zip(streams, sizes):
+        single = handle.estimate(q["ref"], q["cur"], 16, 32)
+        prop = handle.feat_propagate(q["feat"], single, 16, s)
+        torch.cuda.synchronize()
+        assert torch.equal(q["mv"], single)
+        assert torch.equal(q["feat_out"].view(torch.int32), prop[0].view(torch.int32))
+        if (H, W) not in checked:
+            checked.add((H, W))
+            want, _ = oracle.me_full(q["np"][0], q["np"][1], 16, 32, even=True)
+            got = bm.records_to_numpy(q["mv"])
+            for k in ("dx", "dy", "sad"):
+                np.testing.assert_array_equal(got[k], want[k])
+            pw = oracle.propagate(q["feat_np"], want, 16, s, interp=oracle.BILINEAR)
+            np.testing.assert_array_equal(q["feat_out"].cpu().numpy().view(np.uint32), pw.view(np.uint32))
+    assert len(checked) == 4
