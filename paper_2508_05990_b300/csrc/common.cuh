@@ -26,6 +26,22 @@ __device__ __forceinline__ uint32_t sad_u32(uint32_t a, uint32_t b, uint32_t c) 
   return d;
 }
 
+// Packed pixel pairs (two 16-bit samples in one 32-bit word, as they lie in
+// the frame).  min.u16x2: the minimum of each half (one instruction, sm_90+).
+__device__ __forceinline__ uint32_t min_u16x2(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+
+// c + a.lo * w.byte0 + a.hi * w.byte1 (PTX dp2a.lo, unsigned): with byte
+// weights (1, 1) the sum of both halves, with (2, 2) twice that.
+__device__ __forceinline__ uint32_t dp2a_lo(uint32_t a, uint32_t w, uint32_t c) {
+  uint32_t d;
+  asm("dp2a.lo.u32.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(w), "r"(c));
+  return d;
+}
+
 // Candidate key: lexicographic (sad, |dx|+|dy|, dy, dx) as one uint64 so that
 // the tie-break is a plain unsigned minimum.  |dx|, |dy| <= 511.
 constexpr uint64_t kInvalidKey = ~0ull;

@@ -1,33 +1,64 @@
 // Exhaustive EVEN-phase search of 16x16 blocks: shared-memory plan, strip
-// staging and the per-warp block search, used by the strip kernel, the
-// list-mode kernel (me_full16.cu) and the multi-stream persistent kernel
-// (multistream.cu).  See me_full16.cu for the mapping.
+// staging, window column sums and the per-warp block search, used by the
+// strip kernel, the list-mode kernel (me_full16.cu) and the multi-stream
+// persistent kernel (multistream.cu).  See me_full16.cu for the mapping.
+//
+// Packed pixel pairs.  Shared memory holds the frames' own layout: one 32-bit
+// word = two horizontally adjacent 12-bit samples, the even column in the low
+// half, so staging is a plain copy.  An EVEN offset moves a candidate by two
+// pixels = one word, so word j of a current-block row always meets word k + j
+// of the window row of candidate column k: whole pairs against whole pairs.
+//
+// SAD through the minimum (Sec. 3.2 "Matching Criterion" defines the SAD;
+// this is an exact rewriting of it): |a - b| = a + b - 2 min(a, b), so
+//   SAD(k) = sum(current block) + sum(window of k) - 2 * sum min(cur, win).
+// min.u16x2 takes both halves' minima in one instruction, dp2a.lo with byte
+// weights (2, 2) adds twice their sum to a 32-bit accumulator in another: one
+// instruction per pixel-candidate at the issue rate, where sad.u32 needs one
+// per pixel-candidate on the half-rate integer pipe.  The window sums come
+// from a table of 16-row column sums at every even row offset, built once per
+// window; a 16-row sum of 12-bit samples (<= 65520) stays inside its half.
 #pragma once
 
 #include "common.cuh"
 
 namespace bme {
 
+constexpr uint32_t kW11 = 0x0101u;  // dp2a byte weights (1, 1): lo + hi
+constexpr uint32_t kW22 = 0x0202u;  // (2, 2): 2 * (lo + hi)
+
+// Row pitch in words for rows of `words` words: a multiple of 4 whose quotient
+// by 4 is odd, so rows 2v + r read by lanes v at one column hit distinct
+// 16-byte bank groups (with the row rotation of half the lanes).
+__host__ __device__ constexpr int pitch4odd(int words) {
+  return ((words + 3) / 4) % 2 == 0 ? (words + 3) / 4 * 4 + 4 : (words + 3) / 4 * 4;
+}
+
 // Shared-memory plan of a strip of NW horizontally adjacent blocks (one warp
-// each): the union of their search windows (WIN_W x WIN_H pixels, row pitch P
-// words = 4 * odd) and their current blocks (16 rows, pitch PC words).
+// each), in 32-bit words: the union of their search windows (WIN_H rows of WW
+// words, pitch P), their current blocks (16 rows of 8 * NW words, pitch PC)
+// and the window's column-sum table (NU rows of WW words, pitch P).
 template <int R, int NW>
 struct Full16Strip {
-  static constexpr int NU = 2 * R + 1;         // candidates per row
+  static constexpr int NU = 2 * R + 1;         // candidates per row, and rows
   static constexpr int REACH = 2 * R;          // pixels each side
-  static constexpr int WIN_W = 16 * NW + 2 * REACH;
+  static constexpr int WIN_W = 16 * NW + 2 * REACH;  // pixels
   static constexpr int WIN_H = 16 + 2 * REACH;
-  static constexpr int P0 = (WIN_W + 3) / 4 * 4;
-  static constexpr int P = ((P0 / 4) % 2 == 0) ? P0 + 4 : P0;  // 4 * odd words
-  static constexpr int PC = 16 * NW + 4;       // current-tile pitch (words)
-  static constexpr int SPAN = 16 + 2 * REACH;  // window pixels one block reads per row
-  static constexpr size_t SMEM = (size_t)(WIN_H * P + 16 * PC) * sizeof(uint32_t);
+  static constexpr int WW = WIN_W / 2;         // words per window row
+  static constexpr int P = pitch4odd(WW);
+  static constexpr int PC = 8 * NW + 4;        // 4 * (2 NW + 1)
+  static constexpr int SPANW = 8 + REACH;      // window words one block reads per row
+  static constexpr int CUR_OFF = WIN_H * P;
+  static constexpr int CS_OFF = CUR_OFF + 16 * PC;
+  static constexpr size_t SMEM = (size_t)(CS_OFF + NU * P) * sizeof(uint32_t);
   static_assert(NU <= 33, "at most 33 candidate rows");
-  static_assert(SPAN % 4 == 0, "span must be a multiple of 4 words");
+  static_assert(SPANW % 4 == 0, "R must be even (128-bit window loads)");
 };
 
 // Accumulators of one lane: its candidate row (NU candidates), and for
 // R = 16 the lane's candidate of the 33rd row and its share of the corner.
+// During the row loop they hold 2 * sum min(cur, win); full16_finish turns
+// them into SADs.
 template <int R>
 struct Full16Acc {
   static constexpr int NU = 2 * R + 1;
@@ -35,15 +66,38 @@ struct Full16Acc {
   uint32_t accx, accc;
 };
 
-// SADs of block rows RB .. RB + NRW - 1 of one 16x16 block against every
-// candidate, accumulated by one warp from a staged window (wbase: the block's
-// window origin, row pitch P words) and current block (cbase, row pitch PC
-// words).  Lane v owns candidate row v (lanes past the last row repeat it).
-template <int R, int P, int PC, int RB, int NRW>
+// cs[v * P + w] = sum of window rows 2v .. 2v + 15 at word column w, both
+// halves at once, for v = 0 .. 2R.  Called by NT threads (index tid) after the
+// window is staged; the caller synchronises before and after.  Two threads
+// per column, each running a 16-row sum down half of the offsets (the 32-bit
+// running sum is exact modulo 2^32, and its final halves each fit 16 bits).
+template <int R, int P, int WW, int NT>
+__device__ __forceinline__ void window_colsums(const uint32_t* win, uint32_t* cs, int tid) {
+  constexpr int NU = 2 * R + 1, HALF = (NU + 1) / 2;
+  for (int e = tid; e < 2 * WW; e += NT) {
+    const int part = e >= WW, w = e - part * WW;
+    const int v0 = part ? HALF : 0, v1 = part ? NU : HALF;
+    const uint32_t* col = win + w;
+    uint32_t s = 0;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) s += col[(2 * v0 + r) * P];
+    cs[v0 * P + w] = s;
+    for (int v = v0 + 1; v < v1; ++v) {
+      s += col[(2 * v + 14) * P] + col[(2 * v + 15) * P];
+      s -= col[(2 * v - 2) * P] + col[(2 * v - 1) * P];
+      cs[v * P + w] = s;
+    }
+  }
+}
+
+// 2 * sum min(cur, win) of one 16x16 block against every candidate,
+// accumulated by one warp from a staged window (wbase: the block's window
+// origin, row pitch P words) and current block (cbase, row pitch PC words).
+// Lane v owns candidate row v (lanes past the last row repeat it).
+template <int R, int P, int PC>
 __device__ __forceinline__ void full16_accumulate(const uint32_t* wbase, const uint32_t* cbase, int lane,
                                                   Full16Acc<R>& A) {
-  constexpr int NU = 2 * R + 1, REACH = 2 * R, SPAN = 16 + 2 * REACH;
-  static_assert(NRW == 4 || NRW == 8 || NRW == 16, "row ranges of 4, 8 or 16");
+  constexpr int NU = 2 * R + 1, SPANW = 8 + 2 * R;
   const int v = lane < NU ? lane : NU - 1;
   const int eps = (lane >> 2) & 1;  // row rotation for conflict-free loads
 
@@ -53,12 +107,12 @@ __device__ __forceinline__ void full16_accumulate(const uint32_t* wbase, const u
   A.accc = 0;
 
 #pragma unroll 1
-  for (int i = 0; i < NRW; ++i) {
-    const int r = RB + ((i + eps) & (NRW - 1));
-    uint32_t c[16];
+  for (int i = 0; i < 16; ++i) {
+    const int r = (i + eps) & 15;
+    uint32_t c[8];
     const uint4* cp = reinterpret_cast<const uint4*>(cbase + r * PC);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < 2; ++q) {
       const uint4 t = cp[q];
       c[4 * q + 0] = t.x;
       c[4 * q + 1] = t.y;
@@ -67,37 +121,76 @@ __device__ __forceinline__ void full16_accumulate(const uint32_t* wbase, const u
     }
     const uint4* wp = reinterpret_cast<const uint4*>(wbase + (2 * v + r) * P);
 #pragma unroll
-    for (int q = 0; q < SPAN / 4; ++q) {
+    for (int q = 0; q < SPANW / 4; ++q) {
       const uint4 t = wp[q];
       const uint32_t rr[4] = {t.x, t.y, t.z, t.w};
 #pragma unroll
       for (int s = 0; s < 4; ++s) {
-        const int p = 4 * q + s;
+        const int w = 4 * q + s;
 #pragma unroll
         for (int k = 0; k < NU; ++k) {
-          const int cc = p - 2 * k;
-          if (cc >= 0 && cc < 16) A.acc[k] = sad_u32(rr[s], c[cc], A.acc[k]);
+          const int j = w - k;
+          if (j >= 0 && j < 8) A.acc[k] = dp2a_lo(min_u16x2(rr[s], c[j]), kW22, A.acc[k]);
         }
       }
     }
     if constexpr (NU == 33) {
-      // row v = 32: candidate u = lane at window pixel 2*lane
-      const uint2* xp = reinterpret_cast<const uint2*>(wbase + (64 + r) * P + 2 * lane);
+      // row v = 32: candidate u = lane, window words lane .. lane + 7
+      const uint32_t* xp = wbase + (64 + r) * P + lane;
 #pragma unroll
-      for (int t2 = 0; t2 < 8; ++t2) {
-        const uint2 e2 = xp[t2];
-        A.accx = sad_u32(e2.x, c[2 * t2], A.accx);
-        A.accx = sad_u32(e2.y, c[2 * t2 + 1], A.accx);
-      }
-      // corner candidate (u, v) = (32, 32): lane l < 16 takes column l
-      if (lane < 16) A.accc = sad_u32(wbase[(64 + r) * P + 64 + lane], cbase[r * PC + lane], A.accc);
+      for (int j = 0; j < 8; ++j) A.accx = dp2a_lo(min_u16x2(xp[j], c[j]), kW22, A.accx);
+      // corner candidate (u, v) = (32, 32): lane l < 8 takes word column l
+      if (lane < 8) A.accc = dp2a_lo(min_u16x2(wbase[(64 + r) * P + 32 + lane], cbase[r * PC + lane]), kW22, A.accc);
     }
   }
 }
 
-// The lane's best key (sad, |mv|_1, dy, dx) from its complete accumulators;
-// the warp minimum of the returned keys is the block's MV.  (xb, yb): the
-// block's top-left pixel, for the validity of out-of-frame candidates.
+// SAD = sum(cur) + sum(win) - 2 sum min: turns the accumulators into SADs.
+// csbase: the column-sum table at the block's window origin (pitch P words);
+// cbase: the block's current words (pitch PC).  The corner's SAD is the warp
+// sum of accc afterwards.
+template <int R, int P, int PC>
+__device__ __forceinline__ void full16_finish(const uint32_t* csbase, const uint32_t* cbase, int lane,
+                                              Full16Acc<R>& A) {
+  constexpr int NU = 2 * R + 1, SPANW = 8 + 2 * R;
+  const int v = lane < NU ? lane : NU - 1;
+  // sum of the current block: lane l adds words 4 (l & 1) .. + 3 of row l / 2
+  const uint4 t = *reinterpret_cast<const uint4*>(cbase + (lane >> 1) * PC + 4 * (lane & 1));
+  uint32_t sc = dp2a_lo(t.x, kW11, dp2a_lo(t.y, kW11, dp2a_lo(t.z, kW11, dp2a_lo(t.w, kW11, 0u))));
+  sc = __reduce_add_sync(0xffffffffu, sc);
+  // window sums of row v: a sliding sum of 8 words along the column sums
+  uint32_t T[SPANW];
+  const uint4* cr = reinterpret_cast<const uint4*>(csbase + v * P);
+#pragma unroll
+  for (int q = 0; q < SPANW / 4; ++q) {
+    const uint4 u = cr[q];
+    T[4 * q + 0] = dp2a_lo(u.x, kW11, 0u);
+    T[4 * q + 1] = dp2a_lo(u.y, kW11, 0u);
+    T[4 * q + 2] = dp2a_lo(u.z, kW11, 0u);
+    T[4 * q + 3] = dp2a_lo(u.w, kW11, 0u);
+  }
+  uint32_t s = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) s += T[j];
+#pragma unroll
+  for (int k = 0; k < NU; ++k) {
+    if (k > 0) s += T[k + 7] - T[k - 1];
+    A.acc[k] = sc + s - A.acc[k];
+  }
+  if constexpr (NU == 33) {
+    const uint32_t* c32 = csbase + 32 * P;
+    uint32_t sx = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) sx = dp2a_lo(c32[lane + j], kW11, sx);
+    A.accx = sc + sx - A.accx;
+    uint32_t part = lane < 8 ? dp2a_lo(c32[32 + lane], kW11, 0u) - A.accc : 0u;
+    A.accc = lane == 0 ? part + sc : part;
+  }
+}
+
+// The lane's best key (sad, |mv|_1, dy, dx) from its SADs; the warp minimum
+// of the returned keys is the block's MV.  (xb, yb): the block's top-left
+// pixel, for the validity of out-of-frame candidates.
 template <int R>
 __device__ __forceinline__ uint64_t full16_select(const Full16Acc<R>& A, int lane, int xb, int yb, int W, int H) {
   constexpr int NU = 2 * R + 1, REACH = 2 * R;
@@ -145,40 +238,49 @@ __device__ __forceinline__ uint64_t full16_select(const Full16Acc<R>& A, int lan
   return best;
 }
 
-// SAD of every candidate of one 16x16 block, computed by one warp from a
-// staged window (wbase: the block's window origin, row pitch P words) and
-// current block (cbase, row pitch PC words); returns the lane's best key.
+// Every candidate of one 16x16 block, by one warp: wbase / csbase are the
+// window and its column-sum table at the block's origin (pitch P words),
+// cbase its current words (pitch PC); returns the lane's best key.
 template <int R, int P, int PC>
-__device__ __forceinline__ uint64_t full16_block(const uint32_t* wbase, const uint32_t* cbase, int lane, int xb, int yb,
-                                                 int W, int H) {
+__device__ __forceinline__ uint64_t full16_block(const uint32_t* wbase, const uint32_t* csbase, const uint32_t* cbase,
+                                                 int lane, int xb, int yb, int W, int H) {
   Full16Acc<R> A;
-  full16_accumulate<R, P, PC, 0, 16>(wbase, cbase, lane, A);
+  full16_accumulate<R, P, PC>(wbase, cbase, lane, A);
+  full16_finish<R, P, PC>(csbase, cbase, lane, A);
   return full16_select<R>(A, lane, xb, yb, W, H);
 }
 
+// A word of two samples (gx, gx + 1) of row gy, out-of-frame samples 0.
+__device__ __forceinline__ uint32_t pair_word(const uint16_t* __restrict__ f, int W, int H, int pitch, int gx, int gy) {
+  if (gy < 0 || gy >= H) return 0u;
+  const uint16_t* row = f + (long long)gy * pitch;
+  const uint32_t lo = (gx >= 0 && gx < W) ? (uint32_t)__ldg(row + gx) : 0u;
+  const uint32_t hi = (gx + 1 >= 0 && gx + 1 < W) ? (uint32_t)__ldg(row + gx + 1) : 0u;
+  return lo | (hi << 16);
+}
+
 // Stage the window and current tile of the strip whose first block is at
-// (x0, y0): 8 pixels per 16-byte load when vec_ok (x0 a multiple of 8, W a
-// multiple of 16, rows 16-byte aligned), all loads of a thread in flight
-// before conversion; out-of-frame samples are 0.  Called by all NW*32 threads.
+// (x0, y0) as packed pairs: 8 pixels per 16-byte load when vec_ok (x0 a
+// multiple of 8, W a multiple of 16, rows 16-byte aligned), all loads of a
+// thread in flight before the first store; out-of-frame samples are 0.
+// Called by all NW*32 threads.
 template <int R, int NW>
 __device__ __forceinline__ void stage_strip(const uint16_t* __restrict__ ref, const uint16_t* __restrict__ cur, int W,
                                             int H, int pitch, int x0, int y0, bool vec_ok, uint32_t* win,
                                             uint32_t* curt) {
   using C = Full16Strip<R, NW>;
-  constexpr int kNW = NW;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int kNT = NW * 32;
   if (vec_ok) {
-    // 8 pixels (16 bytes) per load: the window origin x0 - 2R and the tile
-    // origin x0 are multiples of 8 and W is a multiple of 16, so every 8-pixel
-    // chunk lies wholly inside or wholly outside the frame.  All loads of a
-    // thread are issued before any conversion.
+    // The window origin x0 - 2R and the tile origin x0 are multiples of 8 and
+    // W is a multiple of 16, so every 8-pixel chunk lies wholly inside or
+    // wholly outside the frame.
     constexpr int WCH = C::WIN_W / 8, NWCH = WCH * C::WIN_H;
-    constexpr int TCH = 2 * kNW, NTCH = TCH * 16;
-    constexpr int PER = (NWCH + NTCH + kNW * 32 - 1) / (kNW * 32);
+    constexpr int TCH = 2 * NW, NTCH = TCH * 16;
+    constexpr int PER = (NWCH + NTCH + kNT - 1) / kNT;
     uint4 raw[PER];
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
-      const int e = threadIdx.x + i * kNW * 32;
+      const int e = threadIdx.x + i * kNT;
       raw[i] = make_uint4(0, 0, 0, 0);
       if (e < NWCH) {
         const int ry = e / WCH, cx = e - ry * WCH;
@@ -193,39 +295,23 @@ __device__ __forceinline__ void stage_strip(const uint16_t* __restrict__ ref, co
     }
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
-      const int e = threadIdx.x + i * kNW * 32;
-      uint32_t* dst;
+      const int e = threadIdx.x + i * kNT;
       if (e < NWCH) {
         const int ry = e / WCH, cx = e - ry * WCH;
-        dst = win + ry * C::P + 8 * cx;
+        *reinterpret_cast<uint4*>(win + ry * C::P + 4 * cx) = raw[i];
       } else if (e < NWCH + NTCH) {
         const int f = e - NWCH, ry = f / TCH, cx = f - ry * TCH;
-        dst = curt + ry * C::PC + 8 * cx;
-      } else {
-        continue;
+        *reinterpret_cast<uint4*>(curt + ry * C::PC + 4 * cx) = raw[i];
       }
-      reinterpret_cast<uint4*>(dst)[0] = make_uint4(pix_lo(raw[i].x), pix_hi(raw[i].x), pix_lo(raw[i].y), pix_hi(raw[i].y));
-      reinterpret_cast<uint4*>(dst)[1] = make_uint4(pix_lo(raw[i].z), pix_hi(raw[i].z), pix_lo(raw[i].w), pix_hi(raw[i].w));
     }
   } else {
-    for (int ry = warp; ry < C::WIN_H; ry += kNW) {
-      const int gy = y0 - C::REACH + ry;
-      const bool row_in = gy >= 0 && gy < H;
-      for (int rx = lane; rx < C::WIN_W; rx += 32) {
-        const int gx = x0 - C::REACH + rx;
-        uint32_t v = 0;
-        if (row_in && gx >= 0 && gx < W) v = __ldg(ref + (long long)gy * pitch + gx);
-        win[ry * C::P + rx] = pix_word(v);
-      }
+    for (int e = threadIdx.x; e < C::WIN_H * C::WW; e += kNT) {
+      const int ry = e / C::WW, wx = e - ry * C::WW;
+      win[ry * C::P + wx] = pair_word(ref, W, H, pitch, x0 - C::REACH + 2 * wx, y0 - C::REACH + ry);
     }
-    for (int ry = warp; ry < 16; ry += kNW) {
-      const int gy = y0 + ry;
-      for (int rx = lane; rx < 16 * kNW; rx += 32) {
-        const int gx = x0 + rx;
-        uint32_t v = 0;
-        if (gy < H && gx < W) v = __ldg(cur + (long long)gy * pitch + gx);
-        curt[ry * C::PC + rx] = pix_word(v);
-      }
+    for (int e = threadIdx.x; e < 16 * 8 * NW; e += kNT) {
+      const int ry = e / (8 * NW), wx = e - ry * (8 * NW);
+      curt[ry * C::PC + wx] = pair_word(cur, W, H, pitch, x0 + 2 * wx, y0 + ry);
     }
   }
 }

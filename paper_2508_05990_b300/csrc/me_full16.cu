@@ -1,18 +1,19 @@
 // Exhaustive EVEN-phase block matching for 16 x 16 blocks (Sec. 2.2 "Block
 // Matching-based ME"; Sec. 3.2 "Matching Criterion": SAD, argmin = MV).
 //
-// Mapping (B300: 148 SMs, INT32 sad.u32 at 64 lanes/clk/SM):
+// Mapping (B300: 148 SMs; packed 16-bit min + dp2a at the issue rate):
 //   * one CTA = NW (8) warps = NW horizontally adjacent blocks of one block
 //     row of one frame pair; the CTA stages the union of their search windows
 //     ((16*NW + 4R) x (16 + 4R) pixels) and their current blocks into shared
-//     memory as 32-bit pixel words, 8 pixels per 16-byte load with every load
-//     of a thread in flight before the first conversion;
+//     memory as packed pixel pairs (16-byte loads stored unchanged), then a
+//     table of 16-row column sums of the window at every even row offset;
 //   * one warp = one block; lane v owns candidate row v (dy = 2v - 2R) and all
 //     2R+1 candidates of that row (dx = 2u - 2R).  Adjacent candidates of a
-//     row are one 32-bit word apart (EVEN offsets), so every reference word a
-//     lane loads feeds up to 8 accumulators (register-blocked sliding SAD);
+//     row are one packed word apart (EVEN offsets), so every window word a
+//     lane loads feeds up to 8 accumulators (register-blocked sliding sum of
+//     2 min(cur, win) over pixel pairs); SAD = sum(cur) + sum(win) - that sum;
 //   * for R = 16 the 33rd row (dy = +32) is spread one candidate per lane and
-//     the corner candidate (+32, +32) is split over 16 lanes and summed with a
+//     the corner candidate (+32, +32) is split over 8 lanes and summed with a
 //     warp reduction, so the 1089 candidates divide evenly over 32 lanes;
 //   * half the lanes walk the block rows rotated by one, which together with a
 //     window pitch of 4*(odd) words makes every 128-bit shared load
@@ -40,8 +41,9 @@ __global__ void __launch_bounds__(kNW * 32) me_full16_even_kernel(const uint16_t
                                                                    bayer_mv_t* __restrict__ out, bool vec_ok) {
   using C = Full16Strip<R, kNW>;
   extern __shared__ __align__(16) uint32_t smem[];
-  uint32_t* win = smem;                 // WIN_H x P
-  uint32_t* curt = smem + C::WIN_H * C::P;  // 16 x PC
+  uint32_t* win = smem;                // WIN_H x P
+  uint32_t* curt = smem + C::CUR_OFF;  // 16 x PC
+  uint32_t* cs = smem + C::CS_OFF;     // NU x P
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int pair = blockIdx.z;
@@ -51,12 +53,14 @@ __global__ void __launch_bounds__(kNW * 32) me_full16_even_kernel(const uint16_t
 
   stage_strip<R, kNW>(ref, cur, W, H, pitch, x0, y0, vec_ok, win, curt);
   __syncthreads();
+  window_colsums<R, C::P, C::WW, kNW * 32>(win, cs, threadIdx.x);
+  __syncthreads();
 
   const int bx = blockIdx.x * kNW + warp;
   if (bx >= w) return;
 
   const uint64_t best = warp_min_u64(
-      full16_block<R, C::P, C::PC>(win + 16 * warp, curt + 16 * warp, lane, bx * 16, y0, W, H));
+      full16_block<R, C::P, C::PC>(win + 8 * warp, cs + 8 * warp, curt + 8 * warp, lane, bx * 16, y0, W, H));
   if (lane == 0) out[((long long)pair * h + blockIdx.y) * w + bx] = key_to_mv(best);
 }
 
@@ -82,13 +86,16 @@ constexpr int kLW = 4;  // warps per CTA in list mode
 
 template <int R>
 struct Full16List {
+  static constexpr int NU = 2 * R + 1;
   static constexpr int REACH = 2 * R;
-  static constexpr int WIN_W = 16 + 2 * REACH;
+  static constexpr int WIN_W = 16 + 2 * REACH;  // pixels
   static constexpr int WIN_H = 16 + 2 * REACH;
-  static constexpr int P0 = (WIN_W + 3) / 4 * 4;
-  static constexpr int P = ((P0 / 4) % 2 == 0) ? P0 + 4 : P0;  // 4 * odd words
-  static constexpr int PC = 20;                                // 4 * odd words
-  static constexpr int WARP_WORDS = WIN_H * P + 16 * PC;
+  static constexpr int WW = WIN_W / 2;          // words
+  static constexpr int P = pitch4odd(WW);
+  static constexpr int PC = 12;                 // 4 * odd words
+  static constexpr int CUR_OFF = WIN_H * P;
+  static constexpr int CS_OFF = CUR_OFF + 16 * PC;
+  static constexpr int WARP_WORDS = CS_OFF + NU * P;
   static constexpr size_t SMEM = (size_t)kLW * WARP_WORDS * sizeof(uint32_t);
 };
 
@@ -104,7 +111,8 @@ __global__ void __launch_bounds__(kLW * 32) me_full16_list_kernel(const uint16_t
   extern __shared__ __align__(16) uint32_t smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint32_t* win = smem + warp * C::WARP_WORDS;
-  uint32_t* curt = win + C::WIN_H * C::P;
+  uint32_t* curt = win + C::CUR_OFF;
+  uint32_t* cs = win + C::CS_OFF;
   const int n = *count;
   for (int gi = blockIdx.x * kLW + warp; gi < n; gi += gridDim.x * kLW) {
     const int gb = list[gi];
@@ -135,32 +143,27 @@ __global__ void __launch_bounds__(kLW * 32) me_full16_list_kernel(const uint16_t
 #pragma unroll
         for (int j = 0; j < BATCH; ++j) {
           const int e = e0 + lane + 32 * j;
-          if (e >= NT) continue;
-          uint32_t* dst;
           if (e < NW) {
             const int ry = e / WCH, cx = e - ry * WCH;
-            dst = win + ry * C::P + 8 * cx;
-          } else {
+            *reinterpret_cast<uint4*>(win + ry * C::P + 4 * cx) = raw[j];
+          } else if (e < NT) {
             const int f = e - NW;
-            dst = curt + (f >> 1) * C::PC + 8 * (f & 1);
+            *reinterpret_cast<uint4*>(curt + (f >> 1) * C::PC + 4 * (f & 1)) = raw[j];
           }
-          reinterpret_cast<uint4*>(dst)[0] = make_uint4(pix_lo(raw[j].x), pix_hi(raw[j].x), pix_lo(raw[j].y), pix_hi(raw[j].y));
-          reinterpret_cast<uint4*>(dst)[1] = make_uint4(pix_lo(raw[j].z), pix_hi(raw[j].z), pix_lo(raw[j].w), pix_hi(raw[j].w));
         }
       }
     } else {
-      for (int e = lane; e < C::WIN_H * C::WIN_W; e += 32) {
-        const int ry = e / C::WIN_W, rx = e - ry * C::WIN_W;
-        const int gy = y0 - C::REACH + ry, gx = x0 - C::REACH + rx;
-        uint32_t v = 0;
-        if (gy >= 0 && gy < H && gx >= 0 && gx < W) v = __ldg(ref + (long long)gy * pitch + gx);
-        win[ry * C::P + rx] = pix_word(v);
+      for (int e = lane; e < C::WIN_H * C::WW; e += 32) {
+        const int ry = e / C::WW, wx = e - ry * C::WW;
+        win[ry * C::P + wx] = pair_word(ref, W, H, pitch, x0 - C::REACH + 2 * wx, y0 - C::REACH + ry);
       }
-      for (int e = lane; e < 256; e += 32)
-        curt[(e >> 4) * C::PC + (e & 15)] = pix_word(__ldg(cur + (long long)(y0 + (e >> 4)) * pitch + x0 + (e & 15)));
+      for (int e = lane; e < 128; e += 32)
+        curt[(e >> 3) * C::PC + (e & 7)] = pair_word(cur, W, H, pitch, x0 + 2 * (e & 7), y0 + (e >> 3));
     }
     __syncwarp();
-    const uint64_t best = warp_min_u64(full16_block<R, C::P, C::PC>(win, curt, lane, x0, y0, W, H));
+    window_colsums<R, C::P, C::WW, 32>(win, cs, lane);
+    __syncwarp();
+    const uint64_t best = warp_min_u64(full16_block<R, C::P, C::PC>(win, cs, curt, lane, x0, y0, W, H));
     if (lane == 0) out[gb] = key_to_mv(best);
   }
 }

@@ -78,7 +78,8 @@ __global__ void __launch_bounds__(NW * 32) ms_me_kernel(const MsPair* __restrict
   using C = Full16Strip<R, NW>;
   extern __shared__ __align__(16) uint32_t smem[];
   uint32_t* win = smem;
-  uint32_t* curt = smem + C::WIN_H * C::P;
+  uint32_t* curt = smem + C::CUR_OFF;
+  uint32_t* cs = smem + C::CS_OFF;
   __shared__ int s_item;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) atomicMin(&ctr->t0, gtimer());
@@ -94,10 +95,12 @@ __global__ void __launch_bounds__(NW * 32) ms_me_kernel(const MsPair* __restrict
     const int x0 = sx * NW * 16, y0 = by * 16;
     stage_strip<R, NW>(P.ref, P.cur, P.W, P.H, P.pitch, x0, y0, P.vec != 0, win, curt);
     __syncthreads();
+    window_colsums<R, C::P, C::WW, NW * 32>(win, cs, threadIdx.x);
+    __syncthreads();
     const int bx = sx * NW + warp;
     if (bx < P.w) {
-      const uint64_t best =
-          warp_min_u64(full16_block<R, C::P, C::PC>(win + 16 * warp, curt + 16 * warp, lane, bx * 16, y0, P.W, P.H));
+      const uint64_t best = warp_min_u64(
+          full16_block<R, C::P, C::PC>(win + 8 * warp, cs + 8 * warp, curt + 8 * warp, lane, bx * 16, y0, P.W, P.H));
       if (lane == 0) P.mv[(long long)by * P.w + bx] = key_to_mv(best);
     }
     __syncthreads();  // window consumed, MV records written

@@ -94,8 +94,13 @@ def test_full16_adversarial(handle, kind):
 @pytest.mark.parametrize("block", [8, 16, 32])
 def test_full_ragged_and_blocks(handle, shape, block):
     """Partial edge blocks and non-16 blocks take the generic kernel; a frame
-    smaller than one block is a single clipped block."""
+    smaller than one block is rejected (W, H >= block is the contract)."""
     H, W = shape
+    if W < block or H < block:
+        f = dev(np.zeros((H, W), np.uint16))
+        with pytest.raises(bm.BayerError):
+            handle.estimate(f, f, block, 12)
+        return
     f0, f1 = synth.pan_clip(5, H, W, n_frames=2, rect_size=(8, 24))
     out = handle.estimate(dev(f0), dev(f1), block, 12)
     ref_field, _ = oracle.me_full(f0, f1, block, 12, even=True)
