@@ -18,8 +18,9 @@ skips them):
   * learned_seeded: the same clip through the proposal network, the +-4
     refine and the exhaustive fallback, with fallback rate and SAD regret;
   * multi_stream: 32 streams of mixed sizes (8x 640x480, 8x 1280x720,
-    12x 1920x1088, 4x 3840x2160), one pair of each per step in one persistent
-    launch pair replayed from a CUDA graph, with p50/p99 per-frame latency;
+    12x 1920x1088, 4x 3840x2160), one pair of each per step in one search
+    launch and one propagation launch replayed from a CUDA graph, with p50/p99
+    per-frame latency;
   * precision_4k: a 3840x2160 clip, 128-channel stride-4 propagation and the
     three 3x3 refine convs in BF16 on the tensor cores (FP32 run beside it).
 
@@ -272,8 +273,8 @@ def cpu_baseline_sample(frames, feats):
 
 def leg_multi_stream(h, clips, steps, warmup, peaks, pc_clk_sm, nsm, sm_mhz):
     """32 streams of mixed sizes: each step searches one (t, t+1) pair of every
-    stream and propagates its stride-8 256-channel map, all in one persistent
-    search launch + one propagation launch replayed from a CUDA graph.  Per-pair
+    stream and propagates its stride-8 256-channel map, all in one search
+    launch + one propagation launch replayed from a CUDA graph.  Per-pair
     completion times (device global timer, from the step's first CTA) give the
     latency percentiles.  The same pairs issued as separate per-stream calls
     (one search + one propagation launch each) are timed beside it."""
@@ -352,8 +353,8 @@ def leg_multi_stream(h, clips, steps, warmup, peaks, pc_clk_sm, nsm, sm_mhz):
                      "alu_ms": round(t_alu, 4), "hbm_ms": round(t_hbm, 4),
                      "algorithmic_per_step": f"{ms_pc_per_step()} pixel-candidates + {ms_prop_bytes_per_step()} "
                                              "propagation bytes",
-                     "peak_source": "measured sad.u32 rate x SMs x median SM clock; MEASURED_PEAKS.json hbm_gbs "
-                                    "(of measured)"},
+                     "peak_source": "measured packed min.u16x2 + dp2a rate x SMs x median SM clock; "
+                                    "MEASURED_PEAKS.json hbm_gbs (of measured)"},
         "gpu_launches": 2 * steps,
         "l2": "inputs larger than L2 (2.2 GB of feature maps per step); no flush",
     }
@@ -564,8 +565,10 @@ def run_ours(args):
             "gpu_launches": args.steps * 9,
         }
 
-    # ALU roofline: measured sad.u32 throughput per clock per SM x SMs x SM clock under load
-    pc_clk_sm, probe_mhz, nsm = h.probe_alu(0)
+    # ALU roofline: measured throughput of the search's primitive (packed min.u16x2 + dp2a, two
+    # pixel-candidates per pair) per clock per SM x SMs x SM clock under load; sad.u32 beside it
+    pc_clk_sm, probe_mhz, nsm = h.probe_alu(3)
+    sad_clk_sm = h.probe_alu(0)[0]
     clocks = clk.summary(t_host0, t_host1)
     sm_mhz = clocks["sm_mhz"] or probe_mhz
     peaks = {}
@@ -610,15 +613,16 @@ def run_ours(args):
         result = {
             "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_total / args.steps, 4), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u16 frames, u32 SAD, f32 features",
+            "scaling": "weak", "vs_baseline": None, "dtype": "u16 frames (packed 16x2 min), u32 SAD, f32 features",
             "data": "synthetic (seeded pan+rectangles Bayer clip, N(0,1) features)",
             "config": {"workload": WORKLOAD, "pairs_per_step": PAIRS, "search": "plain exhaustive",
                        "l2": "inputs larger than L2 (267 MB read + 234 MB written per step); no flush",
                        "parallelism": f"replicas x{world} (independent clips, no collective)"},
             "roofline": {"bound": "alu", "kernel": "me_full16_even_kernel<16>", "achieved": round(achieved, 1),
                          "peak": round(peak, 1), "unit": "G pixel-candidates/s", "frac": round(achieved / peak, 4),
-                         "peak_source": f"measured sad.u32 loop: {pc_clk_sm:.1f} pc/clk/SM x {nsm} SMs x "
-                                        f"{sm_mhz:.0f} MHz (median SM clock under load)",
+                         "peak_source": f"measured packed min.u16x2 + dp2a loop: {pc_clk_sm:.1f} pc/clk/SM x {nsm} "
+                                        f"SMs x {sm_mhz:.0f} MHz (median SM clock under load); sad.u32 loop "
+                                        f"{sad_clk_sm:.1f} pc/clk/SM",
                          "traffic": profiled_traffic("me_full16_even_1080p_clip.md", ME_SOURCES),
                          "traffic_unit": "DRAM bytes per launch (ncu)",
                          "algorithmic_per_launch": f"{PAIRS * pc_per_pair()} pixel-candidates",

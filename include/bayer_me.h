@@ -197,7 +197,8 @@ bayer_status_t bayer_me_debug_fail_allocs(bayer_me_t h, int n);
 
 /* Roofline probe: throughput of the exact SAD primitive on this device.
  * Runs a register-only loop of `variant` (0 = sad.u32 integer, 1 = float
- * subtract + absolute add, 2 = both interleaved) on every SM and returns the
+ * subtract + absolute add, 2 = both interleaved, 3 = packed pixel pairs:
+ * min.u16x2 + dp2a, two pixel-candidates per pair) on every SM and returns the
  * pixel-candidates per clock per SM and the SM clock (MHz) seen during the
  * run.  Synchronous. */
 bayer_status_t bayer_probe_alu(bayer_me_t h, int variant, double* pc_per_clk_per_sm, double* sm_mhz,
@@ -301,8 +302,8 @@ bayer_status_t bayer_refine_conv(bayer_me_t h, const float* feat, int n, int Hf,
  * {8, 16, 24, 32}; W and H multiples of 16), then, where feat is not NULL,
  * propagation of that pair's NCHW feature map as in bayer_feat_propagate
  * (stride divides 16; Hf*stride/16 == H/16 and Wf*stride/16 == W/16).
- * All searches run in one persistent launch over a work queue of strips of
- * all pairs, all propagations in a second one; the two are captured as a CUDA
+ * All searches run in one launch (one CTA per strip of blocks of any pair),
+ * all propagations in a second one; the two are captured as a CUDA
  * graph and replayed on later calls with the same set of sizes.  The first
  * call for a set of sizes also runs an autotuner: it times each launch
  * schedule (blocks per strip 4 or 8; pairs as given or largest first) and

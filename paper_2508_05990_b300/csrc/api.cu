@@ -699,7 +699,7 @@ bayer_status_t bayer_me_sync_status(bayer_me_t h, void* stream) {
 bayer_status_t bayer_probe_alu(bayer_me_t h, int variant, double* pc_per_clk_per_sm, double* sm_mhz,
                                int* sm_count) {
   NvtxRange nvtx_range("bayer_probe_alu");
-  if (!h || !pc_per_clk_per_sm || !sm_mhz || !sm_count || variant < 0 || variant > 2)
+  if (!h || !pc_per_clk_per_sm || !sm_mhz || !sm_count || variant < 0 || variant > 3)
     return BAYER_ERR_INVALID_ARG;
   DeviceGuard g(h->device);
   return cuda_status(bme::run_probe_alu(variant, pc_per_clk_per_sm, sm_mhz, sm_count));

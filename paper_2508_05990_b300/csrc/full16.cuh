@@ -1,7 +1,7 @@
 // Exhaustive EVEN-phase search of 16x16 blocks: shared-memory plan, strip
 // staging, window column sums and the per-warp block search, used by the
 // strip kernel, the list-mode kernel (me_full16.cu) and the multi-stream
-// persistent kernel (multistream.cu).  See me_full16.cu for the mapping.
+// search kernel (multistream.cu).  See me_full16.cu for the mapping.
 //
 // Packed pixel pairs.  Shared memory holds the frames' own layout: one 32-bit
 // word = two horizontally adjacent 12-bit samples, the even column in the low

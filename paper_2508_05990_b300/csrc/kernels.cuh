@@ -159,7 +159,7 @@ cudaError_t launch_full16_list(const uint16_t* ref, const uint16_t* cur, int W, 
                                int max_count, bayer_mv_t* out, cudaStream_t st);
 cudaError_t configure_full16_list();
 
-// Multi-stream persistent search + propagation (multistream.cu).
+// Multi-stream search + propagation (multistream.cu).
 struct MultiStream;
 MultiStream* ms_create(int device);
 void ms_destroy(MultiStream* m);

@@ -1,12 +1,14 @@
-// Many camera streams in one persistent launch: the exhaustive 16x16 EVEN
-// search and the MV feature propagation of a set of frame pairs of mixed
-// sizes (one pair per stream per frame time), replayed as a CUDA graph, with
-// the launch schedule chosen by an autotuner and cached per set of sizes.
+// Many camera streams in two launches: the exhaustive 16x16 EVEN search and
+// the MV feature propagation of a set of frame pairs of mixed sizes (one pair
+// per stream per frame time), replayed as a CUDA graph, with the launch
+// schedule chosen by an autotuner and cached per set of sizes.
 //
-// Search: persistent CTAs (NW warps = one strip of NW adjacent blocks) take
-// strips from a device work queue (atomic counter) over all pairs, find the
-// pair by binary search in a prefix table, stage the strip's window
-// (full16.cuh) and search it.  The last strip of a pair stamps %globaltimer.
+// Search: one CTA (NW warps) per strip of NW adjacent blocks of any pair; the
+// CTA finds its pair by binary search in a prefix table over the strips of
+// all pairs, stages the strip's window (full16.cuh) and searches it.  The
+// hardware block scheduler balances the strips (a persistent variant with an
+// atomic work queue measured slower once the search itself got cheaper).
+// The last strip of a pair stamps %globaltimer.
 // Propagation: one CTA (256 threads) per (pair, 4-channel chunk, tile of 256
 // units) item, the pair found by binary search in a second prefix table,
 // warps the pair's NCHW feature map by its MV field (prop_common.cuh); a unit is a 2 x 2 quad of
@@ -47,8 +49,7 @@ struct MsPair {
 };
 
 struct MsCounters {
-  int me_next;
-  unsigned long long t0;
+  unsigned long long t0;  // earliest CTA start of the search launch (%globaltimer)
 };
 
 constexpr int kPropThreads = 256;
@@ -71,44 +72,38 @@ __device__ __forceinline__ int find_pair(const int* prefix, int n, int item) {
 }
 
 template <int R, int NW>
-__global__ void __launch_bounds__(NW * 32) ms_me_kernel(const MsPair* __restrict__ pairs,
-                                                         const int* __restrict__ prefix, int n, int total,
-                                                         MsCounters* ctr, int* __restrict__ done,
-                                                         long long* __restrict__ end_ns) {
+__global__ void __launch_bounds__(NW * 32, NW == 8 ? 4 : 6) ms_me_kernel(const MsPair* __restrict__ pairs,
+                                                                          const int* __restrict__ prefix, int n,
+                                                                          MsCounters* ctr, int* __restrict__ done,
+                                                                          long long* __restrict__ end_ns) {
   using C = Full16Strip<R, NW>;
   extern __shared__ __align__(16) uint32_t smem[];
   uint32_t* win = smem;
   uint32_t* curt = smem + C::CUR_OFF;
   uint32_t* cs = smem + C::CS_OFF;
-  __shared__ int s_item;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) atomicMin(&ctr->t0, gtimer());
-  for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(&ctr->me_next, 1);
-    __syncthreads();
-    const int item = s_item;
-    if (item >= total) break;
-    const int p = find_pair(prefix, n, item);
-    const MsPair P = pairs[p];
-    const int local = item - __ldg(prefix + p);
-    const int by = local / P.strips_x, sx = local - by * P.strips_x;
-    const int x0 = sx * NW * 16, y0 = by * 16;
-    stage_strip<R, NW>(P.ref, P.cur, P.W, P.H, P.pitch, x0, y0, P.vec != 0, win, curt);
-    __syncthreads();
-    window_colsums<R, C::P, C::WW, NW * 32>(win, cs, threadIdx.x);
-    __syncthreads();
-    const int bx = sx * NW + warp;
-    if (bx < P.w) {
-      const uint64_t best = warp_min_u64(
-          full16_block<R, C::P, C::PC>(win + 8 * warp, cs + 8 * warp, curt + 8 * warp, lane, bx * 16, y0, P.W, P.H));
-      if (lane == 0) P.mv[(long long)by * P.w + bx] = key_to_mv(best);
-    }
-    __syncthreads();  // window consumed, MV records written
-    if (threadIdx.x == 0) {
-      __threadfence();
-      // pairs without features are complete when their MV field is
-      if (atomicAdd(&done[p], 1) == P.me_items - 1 && P.pr_items == 0) end_ns[p] = (long long)(gtimer() - ctr->t0);
-    }
+  const int item = blockIdx.x;
+  const int p = find_pair(prefix, n, item);
+  const MsPair P = pairs[p];
+  const int local = item - __ldg(prefix + p);
+  const int by = local / P.strips_x, sx = local - by * P.strips_x;
+  const int x0 = sx * NW * 16, y0 = by * 16;
+  stage_strip<R, NW>(P.ref, P.cur, P.W, P.H, P.pitch, x0, y0, P.vec != 0, win, curt);
+  __syncthreads();
+  window_colsums<R, C::P, C::WW, NW * 32>(win, cs, threadIdx.x);
+  __syncthreads();
+  const int bx = sx * NW + warp;
+  if (bx < P.w) {
+    const uint64_t best = warp_min_u64(
+        full16_block<R, C::P, C::PC>(win + 8 * warp, cs + 8 * warp, curt + 8 * warp, lane, bx * 16, y0, P.W, P.H));
+    if (lane == 0) P.mv[(long long)by * P.w + bx] = key_to_mv(best);
+  }
+  __syncthreads();  // MV records written
+  if (threadIdx.x == 0) {
+    __threadfence();
+    // pairs without features are complete when their MV field is
+    if (atomicAdd(&done[p], 1) == P.me_items - 1 && P.pr_items == 0) end_ns[p] = (long long)(gtimer() - ctr->t0);
   }
 }
 
@@ -193,13 +188,8 @@ template <int R, int NW>
 cudaError_t ms_me_launch(const MsPair* pairs, const int* prefix, int n, int total, MsCounters* ctr, int* done,
                          long long* end_ns, cudaStream_t st) {
   using C = Full16Strip<R, NW>;
-  int dev = 0, nsm = 148;
-  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int per_sm = tc::ctas_per_sm(ms_me_kernel<R, NW>, NW * 32, (int)C::SMEM, 0);
-  int grid = nsm * per_sm;
-  if (grid > total) grid = total;
-  if (grid < 1) return cudaSuccess;
-  ms_me_kernel<R, NW><<<grid, NW * 32, C::SMEM, st>>>(pairs, prefix, n, total, ctr, done, end_ns);
+  if (total < 1) return cudaSuccess;
+  ms_me_kernel<R, NW><<<total, NW * 32, C::SMEM, st>>>(pairs, prefix, n, ctr, done, end_ns);
   return cudaGetLastError();
 }
 
@@ -365,9 +355,8 @@ void build_table(MultiStream* m, const bayer_pair_t* pairs, int n, const Config&
 // Counter reset, search launch, propagation launch (the graph body).
 cudaError_t enqueue(MultiStream* m, int n, int range, int interp, const Config& cfg, int me_total, int pr_total,
                     cudaStream_t st) {
-  // counters: zero queue positions, start time = max (lowered by atomicMin)
-  cudaError_t e = cudaMemsetAsync(m->d_ctr, 0, offsetof(MsCounters, t0), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(&m->d_ctr->t0, 0xFF, sizeof(unsigned long long), st);
+  // start time = max, lowered by atomicMin
+  cudaError_t e = cudaMemsetAsync(&m->d_ctr->t0, 0xFF, sizeof(unsigned long long), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(m->d_done, 0, sizeof(int) * 2 * n, st);
   const int has_prop = pr_total > 0 ? 1 : 0;
   if (e == cudaSuccess)

@@ -5,6 +5,9 @@
 //   0  sad.u32 on 32-bit pixel words (integer pipe)
 //   1  float subtract + absolute-value add (two float ops per pixel-candidate)
 //   2  both interleaved (the two pipes side by side)
+//   3  packed pixel pairs: min.u16x2 then dp2a.lo into a 32-bit accumulator
+//      (two pixel-candidates per instruction pair; the exhaustive search's
+//      primitive)
 // The SM clock during the run is measured from %clock64 against %globaltimer
 // in one thread, so the peak can be stated per clock and at the clock seen.
 #include "common.cuh"
@@ -33,6 +36,10 @@ __global__ void __launch_bounds__(256) probe_kernel(const uint32_t* __restrict__
   }
   uint32_t yi = pix_word(seed[(t + 77) & 255] & 4095u);
   float yf = __uint_as_float(yi);
+  uint32_t xp[kNCH];
+#pragma unroll
+  for (int k = 0; k < kNCH; ++k) xp[k] = (seed[(t + k) & 255] & 0x0FFF0FFFu);
+  uint32_t yp = seed[(t + 77) & 255] & 0x0FFF0FFFu;
   unsigned long long c0, g0, c1, g1;
   asm volatile("mov.u64 %0, %%clock64;" : "=l"(c0));
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(g0));
@@ -43,9 +50,11 @@ __global__ void __launch_bounds__(256) probe_kernel(const uint32_t* __restrict__
       for (int k = 0; k < kNCH; ++k) {
         if (VARIANT == 0 || VARIANT == 2) ai[k] = sad_u32(xi[k], yi, ai[k]);
         if (VARIANT == 1 || VARIANT == 2) af[k] += fabsf(xf[k] - yf);
+        if (VARIANT == 3) ai[k] = dp2a_lo(min_u16x2(xp[k], yp), 0x0202u, ai[k]);
       }
       yi += 1u;
       yf = __uint_as_float(yi);
+      yp += 0x00010001u;
     }
   }
   asm volatile("mov.u64 %0, %%clock64;" : "=l"(c1));
@@ -106,7 +115,8 @@ cudaError_t run_probe_alu(int variant, double* pc_per_clk_per_sm, double* sm_mhz
   if (e == cudaSuccess) {
     if (variant == 0) e = run_variant<0>(grid, seed, sink, clk, &ms);
     else if (variant == 1) e = run_variant<1>(grid, seed, sink, clk, &ms);
-    else e = run_variant<2>(grid, seed, sink, clk, &ms);
+    else if (variant == 2) e = run_variant<2>(grid, seed, sink, clk, &ms);
+    else e = run_variant<3>(grid, seed, sink, clk, &ms);
   }
   unsigned long long hc[2] = {0, 1};
   if (e == cudaSuccess) e = cudaMemcpy(hc, clk, sizeof(hc), cudaMemcpyDeviceToHost);
@@ -115,7 +125,7 @@ cudaError_t run_probe_alu(int variant, double* pc_per_clk_per_sm, double* sm_mhz
   cudaFree(clk);
   if (e != cudaSuccess) return e;
   const double mhz = (double)hc[0] / (double)(hc[1] ? hc[1] : 1) * 1000.0;
-  const double pcs = (double)grid * 256 * kIters * kUnroll * kNCH * (variant == 2 ? 2 : 1);
+  const double pcs = (double)grid * 256 * kIters * kUnroll * kNCH * (variant >= 2 ? 2 : 1);
   const double cycles = (double)ms * 1e-3 * mhz * 1e6;
   *pc_per_clk_per_sm = pcs / (cycles * nsm);
   *sm_mhz = mhz;

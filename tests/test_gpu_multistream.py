@@ -1,4 +1,4 @@
-"""Many streams of mixed sizes in one persistent launch (bayer_me_multi_stream):
+"""Many streams of mixed sizes in one search launch (bayer_me_multi_stream):
 every pair's MV field equals the single-pair search and the oracle bit for
 bit, propagated features equal the float oracle bit for bit, and a second
 call (cached CUDA graph, refreshed descriptor table) is exact too."""
