@@ -175,8 +175,8 @@ bayer_status_t seeded_fast(bayer_me_s* h, const uint16_t* ref, const uint16_t* c
   a.list = h->list + 1;
   if (e == cudaSuccess) e = bme::launch_seeded16(a, st);
   if (e == cudaSuccess)
-    e = bme::launch_full16_list(ref, cur, W, H, pitch, rbs, cbs, hb, wb, range, h->list + 1, h->list, (int)nblk, out,
-                                st);
+    e = bme::launch_full16_list(ref, cur, W, H, pitch, rbs, cbs, batch, hb, wb, range, h->list + 1, h->list, (int)nblk,
+                                out, h->d_status, st);
   if (e == cudaSuccess && n_fallback) e = cudaMemcpyAsync(n_fallback, h->list, sizeof(int), cudaMemcpyDeviceToDevice, st);
   return cuda_status(e);
 }

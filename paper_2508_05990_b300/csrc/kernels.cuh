@@ -155,8 +155,8 @@ struct Seeded16Args {
 cudaError_t configure_seeded16();  // once per device: shared-memory opt-in
 cudaError_t launch_seeded16(const Seeded16Args& a, cudaStream_t st);
 cudaError_t launch_full16_list(const uint16_t* ref, const uint16_t* cur, int W, int H, int pitch, long long ref_bs,
-                               long long cur_bs, int h, int w, int range, const int* list, const int* count,
-                               int max_count, bayer_mv_t* out, cudaStream_t st);
+                               long long cur_bs, int batch, int h, int w, int range, const int* list, const int* count,
+                               int max_count, bayer_mv_t* out, int* status, cudaStream_t st);
 cudaError_t configure_full16_list();
 
 // Multi-stream search + propagation (multistream.cu).

@@ -26,6 +26,7 @@
 #include "full16.cuh"
 #include "kernels.cuh"
 #include "tc_common.cuh"
+#include "tma.cuh"
 
 namespace bme {
 
@@ -40,7 +41,7 @@ __global__ void __launch_bounds__(kNW * 32) me_full16_even_kernel(const uint16_t
                                                                    long long cur_bs, int h, int w,
                                                                    bayer_mv_t* __restrict__ out, bool vec_ok) {
   using C = Full16Strip<R, kNW>;
-  extern __shared__ __align__(16) uint32_t smem[];
+  extern __shared__ __align__(128) uint32_t smem[];
   uint32_t* win = smem;                // WIN_H x P
   uint32_t* curt = smem + C::CUR_OFF;  // 16 x PC
   uint32_t* cs = smem + C::CS_OFF;     // NU x P
@@ -79,10 +80,21 @@ cudaError_t launch_r(const uint16_t* ref, const uint16_t* cur, int W, int H, int
 
 // ---------------------------------------------------------------------------
 // List mode: the exhaustive search of the blocks named in a device list (the
-// low-confidence blocks of the learned-seeded search).  Each warp stages its
-// own block's window, so the blocks need not be adjacent; warps loop over the
-// list (grid-stride) up to the count found in device memory.
-constexpr int kLW = 4;  // warps per CTA in list mode
+// low-confidence blocks of the learned-seeded search).  Each warp searches
+// its own block from its own window, so the blocks need not be adjacent;
+// warps loop over the list (grid-stride) up to the count found in device
+// memory.  One CTA of 11 warps per SM (the 11 windows fill shared memory).
+//
+// Staging: with 16-byte aligned frames, two TMA tile loads per block (the
+// window as a box 2P pixels wide, which lands at the 4*odd-word pitch the
+// sliding loads want, and the 16 x 16 current block), completing on one
+// mbarrier per warp.  The next block's window is requested as soon as the
+// row loop is done with the current one and its current block after the SAD
+// finish, so the copies overlap the finish and the argmin.  Every wait is
+// bounded: on expiry the kernel records BAYER_ERR_TIMEOUT and the warp stops.
+// Other layouts stage with plain loads.
+constexpr int kLW = 11;  // warps per CTA in list mode
+constexpr uint32_t kWaitLimit = 1u << 22;
 
 template <int R>
 struct Full16List {
@@ -92,106 +104,189 @@ struct Full16List {
   static constexpr int WIN_H = 16 + 2 * REACH;
   static constexpr int WW = WIN_W / 2;          // words
   static constexpr int P = pitch4odd(WW);
-  static constexpr int PC = 12;                 // 4 * odd words
+  static constexpr int BOX_W = 2 * P;           // TMA window box width (pixels)
+  static constexpr int PC = 8;                  // current block: dense rows (read as broadcasts)
   static constexpr int CUR_OFF = WIN_H * P;
   static constexpr int CS_OFF = CUR_OFF + 16 * PC;
-  static constexpr int WARP_WORDS = CS_OFF + NU * P;
-  static constexpr size_t SMEM = (size_t)kLW * WARP_WORDS * sizeof(uint32_t);
+  static constexpr int WARP_WORDS = (CS_OFF + NU * P + 31) / 32 * 32;  // 128-byte aligned windows
+  static constexpr uint32_t TX_BYTES = (uint32_t)(WIN_H * P + 16 * PC) * 4u;
+  static constexpr int MBAR_OFF = kLW * WARP_WORDS;  // one mbarrier per warp after the windows
+  static constexpr size_t SMEM = (size_t)MBAR_OFF * sizeof(uint32_t) + kLW * sizeof(uint64_t);
+  static_assert((CUR_OFF * 4) % 128 == 0, "current block 128-byte aligned");
 };
 
+// Plain-load staging of one block's window and current block (any layout).
 template <int R>
-__global__ void __launch_bounds__(kLW * 32) me_full16_list_kernel(const uint16_t* __restrict__ ref_base,
+__device__ __forceinline__ void list_stage(const uint16_t* __restrict__ ref, const uint16_t* __restrict__ cur, int W,
+                                           int H, int pitch, int x0, int y0, bool vec_ok, int lane, uint32_t* win,
+                                           uint32_t* curt) {
+  using C = Full16List<R>;
+  if (vec_ok) {
+    constexpr int WCH = C::WIN_W / 8, NW = WCH * C::WIN_H, NT = NW + 32, BATCH = 8;
+    for (int e0 = 0; e0 < NT; e0 += 32 * BATCH) {
+      uint4 raw[BATCH];
+#pragma unroll
+      for (int j = 0; j < BATCH; ++j) {
+        const int e = e0 + lane + 32 * j;
+        raw[j] = make_uint4(0, 0, 0, 0);
+        if (e < NW) {
+          const int ry = e / WCH, cx = e - ry * WCH;
+          const int gy = y0 - C::REACH + ry, gx = x0 - C::REACH + 8 * cx;
+          if (gy >= 0 && gy < H && gx >= 0 && gx < W)
+            raw[j] = __ldg(reinterpret_cast<const uint4*>(ref + (long long)gy * pitch + gx));
+        } else if (e < NT) {
+          const int f = e - NW, ry = f >> 1, cx = f & 1;
+          raw[j] = __ldg(reinterpret_cast<const uint4*>(cur + (long long)(y0 + ry) * pitch + x0 + 8 * cx));
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < BATCH; ++j) {
+        const int e = e0 + lane + 32 * j;
+        if (e < NW) {
+          const int ry = e / WCH, cx = e - ry * WCH;
+          *reinterpret_cast<uint4*>(win + ry * C::P + 4 * cx) = raw[j];
+        } else if (e < NT) {
+          const int f = e - NW;
+          *reinterpret_cast<uint4*>(curt + (f >> 1) * C::PC + 4 * (f & 1)) = raw[j];
+        }
+      }
+    }
+  } else {
+    for (int e = lane; e < C::WIN_H * C::WW; e += 32) {
+      const int ry = e / C::WW, wx = e - ry * C::WW;
+      win[ry * C::P + wx] = pair_word(ref, W, H, pitch, x0 - C::REACH + 2 * wx, y0 - C::REACH + ry);
+    }
+    for (int e = lane; e < 128; e += 32)
+      curt[(e >> 3) * C::PC + (e & 7)] = pair_word(cur, W, H, pitch, x0 + 2 * (e & 7), y0 + (e >> 3));
+  }
+}
+
+// Block gb of the list: its pair and tile origin (x0, y0).
+__device__ __forceinline__ void list_where(int gb, int h, int w, int& pair, int& x0, int& y0) {
+  pair = gb / (h * w);
+  const int rem = gb - pair * h * w;
+  const int by = rem / w;
+  y0 = by * 16;
+  x0 = (rem - by * w) * 16;
+}
+
+template <int R, bool TMA>
+__global__ void __launch_bounds__(kLW * 32) me_full16_list_kernel(const __grid_constant__ CUtensorMap tm_ref,
+                                                                   const __grid_constant__ CUtensorMap tm_cur,
+                                                                   const uint16_t* __restrict__ ref_base,
                                                                    const uint16_t* __restrict__ cur_base, int W,
                                                                    int H, int pitch, long long ref_bs,
                                                                    long long cur_bs, int h, int w,
                                                                    const int* __restrict__ list,
                                                                    const int* __restrict__ count,
-                                                                   bayer_mv_t* __restrict__ out, bool vec_ok) {
+                                                                   bayer_mv_t* __restrict__ out, bool vec_ok,
+                                                                   int* __restrict__ status) {
   using C = Full16List<R>;
-  extern __shared__ __align__(16) uint32_t smem[];
+  extern __shared__ __align__(128) uint32_t smem[];
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + C::MBAR_OFF);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint32_t* win = smem + warp * C::WARP_WORDS;
   uint32_t* curt = win + C::CUR_OFF;
   uint32_t* cs = win + C::CS_OFF;
   const int n = *count;
-  for (int gi = blockIdx.x * kLW + warp; gi < n; gi += gridDim.x * kLW) {
-    const int gb = list[gi];
-    const int pair = gb / (h * w), rem = gb - pair * h * w;
-    const int by = rem / w, bx = rem - by * w;
-    const uint16_t* ref = ref_base + (long long)pair * ref_bs;
-    const uint16_t* cur = cur_base + (long long)pair * cur_bs;
-    const int x0 = bx * 16, y0 = by * 16;
-    __syncwarp();  // the previous block's reads are done
-    if (vec_ok) {
-      constexpr int WCH = C::WIN_W / 8, NW = WCH * C::WIN_H, NT = NW + 32, BATCH = 8;
-      for (int e0 = 0; e0 < NT; e0 += 32 * BATCH) {
-        uint4 raw[BATCH];
-#pragma unroll
-        for (int j = 0; j < BATCH; ++j) {
-          const int e = e0 + lane + 32 * j;
-          raw[j] = make_uint4(0, 0, 0, 0);
-          if (e < NW) {
-            const int ry = e / WCH, cx = e - ry * WCH;
-            const int gy = y0 - C::REACH + ry, gx = x0 - C::REACH + 8 * cx;
-            if (gy >= 0 && gy < H && gx >= 0 && gx < W)
-              raw[j] = __ldg(reinterpret_cast<const uint4*>(ref + (long long)gy * pitch + gx));
-          } else if (e < NT) {
-            const int f = e - NW, ry = f >> 1, cx = f & 1;
-            raw[j] = __ldg(reinterpret_cast<const uint4*>(cur + (long long)(y0 + ry) * pitch + x0 + 8 * cx));
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < BATCH; ++j) {
-          const int e = e0 + lane + 32 * j;
-          if (e < NW) {
-            const int ry = e / WCH, cx = e - ry * WCH;
-            *reinterpret_cast<uint4*>(win + ry * C::P + 4 * cx) = raw[j];
-          } else if (e < NT) {
-            const int f = e - NW;
-            *reinterpret_cast<uint4*>(curt + (f >> 1) * C::PC + 4 * (f & 1)) = raw[j];
-          }
-        }
-      }
-    } else {
-      for (int e = lane; e < C::WIN_H * C::WW; e += 32) {
-        const int ry = e / C::WW, wx = e - ry * C::WW;
-        win[ry * C::P + wx] = pair_word(ref, W, H, pitch, x0 - C::REACH + 2 * wx, y0 - C::REACH + ry);
-      }
-      for (int e = lane; e < 128; e += 32)
-        curt[(e >> 3) * C::PC + (e & 7)] = pair_word(cur, W, H, pitch, x0 + 2 * (e & 7), y0 + (e >> 3));
+  const int step = gridDim.x * kLW;
+  int gi = blockIdx.x * kLW + warp;
+
+  if constexpr (TMA) {
+    if (lane == 0) {
+      tc::mbar_init(&mbar[warp], 1);
+      tc::fence_mbar_init();
     }
     __syncwarp();
+    if (lane == 0 && gi < n) {
+      int pr, x0, y0;
+      list_where(list[gi], h, w, pr, x0, y0);
+      tma::mbar_arrive_expect_tx(&mbar[warp], C::TX_BYTES);
+      tma::load_3d(win, &tm_ref, x0 - C::REACH, y0 - C::REACH, pr, &mbar[warp]);
+      tma::load_3d(curt, &tm_cur, x0, y0, pr, &mbar[warp]);
+    }
+  }
+  uint32_t phase = 0;
+  for (; gi < n; gi += step) {
+    const int gb = list[gi];
+    int pair, x0, y0;
+    list_where(gb, h, w, pair, x0, y0);
+    if constexpr (TMA) {
+      const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(&mbar[warp], phase, kWaitLimit));
+      phase ^= 1u;
+      if (!ok) {
+        if (lane == 0 && status) atomicExch(status, (int)BAYER_ERR_TIMEOUT);
+        return;
+      }
+    } else {
+      __syncwarp();  // the previous block's reads are done
+      list_stage<R>(ref_base + (long long)pair * ref_bs, cur_base + (long long)pair * cur_bs, W, H, pitch, x0, y0,
+                    vec_ok, lane, win, curt);
+      __syncwarp();
+    }
     window_colsums<R, C::P, C::WW, 32>(win, cs, lane);
     __syncwarp();
-    const uint64_t best = warp_min_u64(full16_block<R, C::P, C::PC>(win, cs, curt, lane, x0, y0, W, H));
+    Full16Acc<R> A;
+    full16_accumulate<R, C::P, C::PC>(win, curt, lane, A);
+    const int gn = gi + step;
+    int pn = 0, xn = 0, yn = 0;
+    if constexpr (TMA) {
+      __syncwarp();  // every lane is done reading the window
+      if (lane == 0 && gn < n) {
+        list_where(list[gn], h, w, pn, xn, yn);
+        tc::fence_proxy_async();
+        tma::mbar_arrive_expect_tx(&mbar[warp], C::TX_BYTES);
+        tma::load_3d(win, &tm_ref, xn - C::REACH, yn - C::REACH, pn, &mbar[warp]);
+      }
+    }
+    full16_finish<R, C::P, C::PC>(cs, curt, lane, A);
+    if constexpr (TMA) {
+      __syncwarp();  // every lane is done reading the current block
+      if (lane == 0 && gn < n) {
+        tc::fence_proxy_async();
+        tma::load_3d(curt, &tm_cur, xn, yn, pn, &mbar[warp]);
+      }
+    }
+    const uint64_t best = warp_min_u64(full16_select<R>(A, lane, x0, y0, W, H));
     if (lane == 0) out[gb] = key_to_mv(best);
   }
 }
 
 template <int R>
 cudaError_t launch_list_r(const uint16_t* ref, const uint16_t* cur, int W, int H, int pitch, long long ref_bs,
-                          long long cur_bs, int h, int w, const int* list, const int* count, int max_count,
-                          bayer_mv_t* out, cudaStream_t st) {
+                          long long cur_bs, int batch, int h, int w, const int* list, const int* count, int max_count,
+                          bayer_mv_t* out, int* status, cudaStream_t st) {
   using C = Full16List<R>;
   int dev = 0, nsm = 148;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int per_sm = tc::ctas_per_sm(me_full16_list_kernel<R>, kLW * 32, (int)C::SMEM, 0);
+  const bool vec_ok = (reinterpret_cast<uintptr_t>(ref) % 16) == 0 && (reinterpret_cast<uintptr_t>(cur) % 16) == 0 &&
+                      pitch % 8 == 0 && ref_bs % 8 == 0 && cur_bs % 8 == 0;
+  CUtensorMap tref{}, tcur{};
+  const bool use_tma = vec_ok &&
+                       tma::encode_u16_frames(&tref, ref, W, H, batch, pitch, ref_bs, C::BOX_W, C::WIN_H) &&
+                       tma::encode_u16_frames(&tcur, cur, W, H, batch, pitch, cur_bs, 16, 16);
+  const int per_sm = use_tma ? tc::ctas_per_sm(me_full16_list_kernel<R, true>, kLW * 32, (int)C::SMEM, 0)
+                             : tc::ctas_per_sm(me_full16_list_kernel<R, false>, kLW * 32, (int)C::SMEM, 0);
   int grid = (max_count + kLW - 1) / kLW;
   if (grid > per_sm * nsm) grid = per_sm * nsm;
   if (grid < 1) grid = 1;
-  const bool vec_ok = (reinterpret_cast<uintptr_t>(ref) % 16) == 0 && (reinterpret_cast<uintptr_t>(cur) % 16) == 0 &&
-                      pitch % 8 == 0 && ref_bs % 8 == 0 && cur_bs % 8 == 0;
-  me_full16_list_kernel<R><<<grid, kLW * 32, C::SMEM, st>>>(ref, cur, W, H, pitch, ref_bs, cur_bs, h, w, list, count,
-                                                             out, vec_ok);
+  if (use_tma)
+    me_full16_list_kernel<R, true><<<grid, kLW * 32, C::SMEM, st>>>(tref, tcur, ref, cur, W, H, pitch, ref_bs, cur_bs,
+                                                                     h, w, list, count, out, vec_ok, status);
+  else
+    me_full16_list_kernel<R, false><<<grid, kLW * 32, C::SMEM, st>>>(tref, tcur, ref, cur, W, H, pitch, ref_bs,
+                                                                      cur_bs, h, w, list, count, out, vec_ok, status);
   return cudaGetLastError();
 }
 
 template <int R>
 cudaError_t configure_list_r() {
-  cudaError_t e = cudaFuncSetAttribute(me_full16_list_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)Full16List<R>::SMEM);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(me_full16_list_kernel<R>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  cudaError_t e = cudaSuccess;
+  for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+    const void* fn = v ? (const void*)me_full16_list_kernel<R, true> : (const void*)me_full16_list_kernel<R, false>;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Full16List<R>::SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  }
   return e;
 }
 
@@ -223,13 +318,21 @@ cudaError_t configure_full16_list() {
 }
 
 cudaError_t launch_full16_list(const uint16_t* ref, const uint16_t* cur, int W, int H, int pitch, long long ref_bs,
-                               long long cur_bs, int h, int w, int range, const int* list, const int* count,
-                               int max_count, bayer_mv_t* out, cudaStream_t st) {
+                               long long cur_bs, int batch, int h, int w, int range, const int* list, const int* count,
+                               int max_count, bayer_mv_t* out, int* status, cudaStream_t st) {
   switch (range) {
-    case 8: return launch_list_r<4>(ref, cur, W, H, pitch, ref_bs, cur_bs, h, w, list, count, max_count, out, st);
-    case 16: return launch_list_r<8>(ref, cur, W, H, pitch, ref_bs, cur_bs, h, w, list, count, max_count, out, st);
-    case 24: return launch_list_r<12>(ref, cur, W, H, pitch, ref_bs, cur_bs, h, w, list, count, max_count, out, st);
-    case 32: return launch_list_r<16>(ref, cur, W, H, pitch, ref_bs, cur_bs, h, w, list, count, max_count, out, st);
+    case 8:
+      return launch_list_r<4>(ref, cur, W, H, pitch, ref_bs, cur_bs, batch, h, w, list, count, max_count, out, status,
+                              st);
+    case 16:
+      return launch_list_r<8>(ref, cur, W, H, pitch, ref_bs, cur_bs, batch, h, w, list, count, max_count, out, status,
+                              st);
+    case 24:
+      return launch_list_r<12>(ref, cur, W, H, pitch, ref_bs, cur_bs, batch, h, w, list, count, max_count, out, status,
+                               st);
+    case 32:
+      return launch_list_r<16>(ref, cur, W, H, pitch, ref_bs, cur_bs, batch, h, w, list, count, max_count, out, status,
+                               st);
     default: return cudaErrorInvalidValue;
   }
 }
