@@ -11,11 +11,15 @@
 // Lanes 0-2 read the blocks' confidences and proposals; low-confidence
 // blocks are appended to the fallback list (one atomic per warp).  For the
 // confident blocks the warp stages the 24 x 24 windows and the current
-// blocks in its shared memory as 32-bit pixel words (every sample-pair load
-// of the three blocks in flight at once), then lane 10 j + 5 half + v owns
-// candidate row v (5 candidates) of block j over one half of its columns:
-// 30 of 32 lanes carry SADs and every 128-bit window load feeds 5
-// candidates.  A block's minimum is gathered from its five row lanes.
+// blocks in its shared memory as packed pixel pairs (the centre is even, so
+// the window starts on a pair; every pair load of the three blocks in flight
+// at once), then lane 10 j + 5 half + v owns candidate row v (5 candidates)
+// of block j over one half of its columns: 30 of 32 lanes carry SADs.  As in
+// the exhaustive search (full16.cuh), SAD = sum(cur) + sum(win) -
+// 2 sum min(cur, win) with min.u16x2 + dp2a per pixel pair; each lane keeps
+// the column sums of the 8 window words and 4 current words it loads per row,
+// so the two halves' partial SADs add up exactly.  A block's minimum is
+// gathered from its five row lanes.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -26,10 +30,11 @@ namespace {
 constexpr int kSW = 4;            // warps per CTA
 constexpr int kPer = 3;           // blocks per warp
 constexpr int kWin = 24;          // window side (16 + 2 * 4)
-constexpr int kWP = 36;           // window pitch (words); with the lane order below and kSlot = 4 mod 32
-constexpr int kSlot = kWin * kWP + 256 + 4;  // the 128-bit search loads take 7 (window) and 4 (current
-                                             // block) wavefronts instead of 9 and 6 at pitch 24
-// words per block slot: window, then current block (pitch 16), then 4 words of padding
+constexpr int kWP = 12;           // window pitch (words): dense pixel pairs
+constexpr int kCurOff = kWin * kWP;          // current block: 16 rows of 8 words
+constexpr int kSlot = kCurOff + 128 + 8;     // words per block slot; with this lane order the search's
+                                             // 128-bit loads take 14 (window) + 4 (current) wavefronts
+                                             // per row (36 with 32-bit pixel words)
 constexpr int kPairsWin = kWin * kWin / 2;  // sample pairs of a window (288 = 9 * 32)
 constexpr int kPairsCur = 128;              // sample pairs of a current block (4 * 32)
 constexpr size_t kSmem = (size_t)kSW * kPer * kSlot * sizeof(uint32_t);
@@ -153,18 +158,9 @@ __global__ void __launch_bounds__(kSW * 32) seeded16_kernel(const Seeded16Args a
     for (int k = 0; k < kPer; ++k) {
       if (!(conf_mask & (1u << k))) continue;
 #pragma unroll
-      for (int i = 0; i < kPairsWin / 32; ++i) {
-        const int e = lane + 32 * i;
-        const int row = e / (kWin / 2);
-        const int so = row * kWP + 2 * (e - row * (kWin / 2));
-        *reinterpret_cast<uint2*>(slots + k * kSlot + so) = make_uint2(pix_lo(raw[k][i]), pix_hi(raw[k][i]));
-      }
+      for (int i = 0; i < kPairsWin / 32; ++i) slots[k * kSlot + lane + 32 * i] = raw[k][i];  // pitch 12 = dense
 #pragma unroll
-      for (int i = 0; i < kPairsCur / 32; ++i) {
-        const int f = lane + 32 * i;
-        const int so = kWin * kWP + (f >> 3) * 16 + 2 * (f & 7);
-        *reinterpret_cast<uint2*>(slots + k * kSlot + so) = make_uint2(pix_lo(rc[k][i]), pix_hi(rc[k][i]));
-      }
+      for (int i = 0; i < kPairsCur / 32; ++i) slots[k * kSlot + kCurOff + lane + 32 * i] = rc[k][i];
     }
   } else {
     // unaligned frames: one 16-bit load per sample
@@ -175,15 +171,20 @@ __global__ void __launch_bounds__(kSW * 32) seeded16_kernel(const Seeded16Args a
       const int cx = (int)(int16_t)(bc & 0xFFFF), cy = bc >> 16;
       const uint16_t* ref = a.ref + (long long)bp[k] * a.ref_bs;
       const uint16_t* cur = a.cur + (long long)bp[k] * a.cur_bs;
-      for (int e = lane; e < kWin * kWin; e += 32) {
-        const int ry = e / kWin, rx = e - ry * kWin;
-        const int gy = y0 + cy - 4 + ry, gx = x0 + cx - 4 + rx;
-        uint32_t smp = 0;
-        if (gy >= 0 && gy < a.H && gx >= 0 && gx < a.W) smp = __ldg(ref + (long long)gy * a.pitch + gx);
-        slots[k * kSlot + ry * kWP + rx] = pix_word(smp);
+      for (int e = lane; e < kPairsWin; e += 32) {
+        const int ry = e / kWP, wx = e - ry * kWP;
+        const int gy = y0 + cy - 4 + ry, gx = x0 + cx - 4 + 2 * wx;
+        uint32_t lo = 0, hi = 0;
+        if (gy >= 0 && gy < a.H) {
+          if (gx >= 0 && gx < a.W) lo = __ldg(ref + (long long)gy * a.pitch + gx);
+          if (gx + 1 >= 0 && gx + 1 < a.W) hi = __ldg(ref + (long long)gy * a.pitch + gx + 1);
+        }
+        slots[k * kSlot + e] = lo | (hi << 16);
       }
-      for (int e = lane; e < 256; e += 32)
-        slots[k * kSlot + kWin * kWP + e] = pix_word(__ldg(cur + (long long)(y0 + (e >> 4)) * a.pitch + x0 + (e & 15)));
+      for (int e = lane; e < kPairsCur; e += 32) {
+        const uint16_t* cp = cur + (long long)(y0 + (e >> 3)) * a.pitch + x0 + 2 * (e & 7);
+        slots[k * kSlot + kCurOff + e] = (uint32_t)__ldg(cp) | ((uint32_t)__ldg(cp + 1) << 16);
+      }
     }
   }
   __syncwarp();
@@ -196,31 +197,47 @@ __global__ void __launch_bounds__(kSW * 32) seeded16_kernel(const Seeded16Args a
   const bool live = j < kPer && (conf_mask & (1u << j));
   uint32_t acc[5] = {0, 0, 0, 0, 0};
   if (live) {
-    const uint32_t* wb = slots + j * kSlot + 2 * v * kWP + 8 * hh;
-    const uint32_t* cb = slots + j * kSlot + kWin * kWP + 8 * hh;
+    // half hh: current words 4 hh .. 4 hh + 3, window words 4 hh .. 4 hh + 7 of rows 2 v + r
+    const uint32_t* wb = slots + j * kSlot + 2 * v * kWP + 4 * hh;
+    const uint32_t* cb = slots + j * kSlot + kCurOff + 4 * hh;
+    uint32_t tw[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // window column sums (lo + hi), 16 rows
+    uint32_t pc[4] = {0, 0, 0, 0};              // current column sums, packed (each half <= 65520)
 #pragma unroll 4
     for (int r = 0; r < 16; ++r) {
-      uint32_t w[16], c[8];
+      uint32_t w[8], c[4];
 #pragma unroll
-      for (int k4 = 0; k4 < 4; ++k4) {
+      for (int k4 = 0; k4 < 2; ++k4) {
         const uint4 x = *reinterpret_cast<const uint4*>(wb + r * kWP + 4 * k4);
         w[4 * k4] = x.x;
         w[4 * k4 + 1] = x.y;
         w[4 * k4 + 2] = x.z;
         w[4 * k4 + 3] = x.w;
       }
-#pragma unroll
-      for (int k4 = 0; k4 < 2; ++k4) {
-        const uint4 x = *reinterpret_cast<const uint4*>(cb + r * 16 + 4 * k4);
-        c[4 * k4] = x.x;
-        c[4 * k4 + 1] = x.y;
-        c[4 * k4 + 2] = x.z;
-        c[4 * k4 + 3] = x.w;
+      {
+        const uint4 x = *reinterpret_cast<const uint4*>(cb + r * 8);
+        c[0] = x.x;
+        c[1] = x.y;
+        c[2] = x.z;
+        c[3] = x.w;
       }
 #pragma unroll
       for (int u = 0; u < 5; ++u)
 #pragma unroll
-        for (int cc = 0; cc < 8; ++cc) acc[u] = sad_u32(w[2 * u + cc], c[cc], acc[u]);
+        for (int cc = 0; cc < 4; ++cc) acc[u] = dp2a_lo(min_u16x2(w[u + cc], c[cc]), 0x0202u, acc[u]);
+#pragma unroll
+      for (int t = 0; t < 8; ++t) tw[t] = dp2a_lo(w[t], 0x0101u, tw[t]);
+#pragma unroll
+      for (int t = 0; t < 4; ++t) pc[t] += c[t];
+    }
+    // this half's SAD of candidate u: sum(cur) + sum(win of u) - 2 sum min
+    uint32_t sc = 0;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) sc = dp2a_lo(pc[t], 0x0101u, sc);
+    uint32_t sw = tw[0] + tw[1] + tw[2] + tw[3];
+#pragma unroll
+    for (int u = 0; u < 5; ++u) {
+      if (u > 0) sw += tw[u + 3] - tw[u - 1];
+      acc[u] = sc + sw - acc[u];
     }
   }
   const int partner = lane < 30 ? (hh ? lane - 5 : lane + 5) : lane;
