@@ -90,13 +90,27 @@ __device__ __forceinline__ void window_colsums(const uint32_t* win, uint32_t* cs
   }
 }
 
+// A lane's window sums gathered during the row loop (the variant without a
+// column-sum table): per window word of its candidate row, the 16-row column
+// sum -- the first half of the words packed (each half <= 65520, plain
+// adds on the integer pipe), the rest as lo + hi (dp2a on the FMA pipe), so
+// the extra work splits over both pipes -- and for R = 16 the window sum of
+// its 33rd-row candidate and its share of the corner's.
+template <int R>
+struct Full16WinSums {
+  static constexpr int SPANW = 8 + 2 * R;
+  uint32_t cw[SPANW];
+  uint32_t sx, scn;
+};
+
 // 2 * sum min(cur, win) of one 16x16 block against every candidate,
 // accumulated by one warp from a staged window (wbase: the block's window
 // origin, row pitch P words) and current block (cbase, row pitch PC words).
-// Lane v owns candidate row v (lanes past the last row repeat it).
-template <int R, int P, int PC>
+// Lane v owns candidate row v (lanes past the last row repeat it).  With
+// SUMS the lane also gathers its window sums into S.
+template <int R, int P, int PC, bool SUMS = false>
 __device__ __forceinline__ void full16_accumulate(const uint32_t* wbase, const uint32_t* cbase, int lane,
-                                                  Full16Acc<R>& A) {
+                                                  Full16Acc<R>& A, Full16WinSums<R>& S) {
   constexpr int NU = 2 * R + 1, SPANW = 8 + 2 * R;
   const int v = lane < NU ? lane : NU - 1;
   const int eps = (lane >> 2) & 1;  // row rotation for conflict-free loads
@@ -105,6 +119,12 @@ __device__ __forceinline__ void full16_accumulate(const uint32_t* wbase, const u
   for (int k = 0; k < NU; ++k) A.acc[k] = 0;
   A.accx = 0;
   A.accc = 0;
+  if constexpr (SUMS) {
+#pragma unroll
+    for (int w = 0; w < SPANW; ++w) S.cw[w] = 0;
+    S.sx = 0;
+    S.scn = 0;
+  }
 
 #pragma unroll 1
   for (int i = 0; i < 16; ++i) {
@@ -132,16 +152,61 @@ __device__ __forceinline__ void full16_accumulate(const uint32_t* wbase, const u
           const int j = w - k;
           if (j >= 0 && j < 8) A.acc[k] = dp2a_lo(min_u16x2(rr[s], c[j]), kW22, A.acc[k]);
         }
+        if constexpr (SUMS) {
+          if (w < SPANW / 2) S.cw[w] += rr[s];
+          else S.cw[w] = dp2a_lo(rr[s], kW11, S.cw[w]);
+        }
       }
     }
     if constexpr (NU == 33) {
       // row v = 32: candidate u = lane, window words lane .. lane + 7
       const uint32_t* xp = wbase + (64 + r) * P + lane;
 #pragma unroll
-      for (int j = 0; j < 8; ++j) A.accx = dp2a_lo(min_u16x2(xp[j], c[j]), kW22, A.accx);
+      for (int j = 0; j < 8; ++j) {
+        const uint32_t x = xp[j];
+        A.accx = dp2a_lo(min_u16x2(x, c[j]), kW22, A.accx);
+        if constexpr (SUMS) S.sx = dp2a_lo(x, kW11, S.sx);
+      }
       // corner candidate (u, v) = (32, 32): lane l < 8 takes word column l
-      if (lane < 8) A.accc = dp2a_lo(min_u16x2(wbase[(64 + r) * P + 32 + lane], cbase[r * PC + lane]), kW22, A.accc);
+      if (lane < 8) {
+        const uint32_t x = wbase[(64 + r) * P + 32 + lane];
+        A.accc = dp2a_lo(min_u16x2(x, cbase[r * PC + lane]), kW22, A.accc);
+        if constexpr (SUMS) S.scn = dp2a_lo(x, kW11, S.scn);
+      }
     }
+  }
+}
+
+// The current block's sum (all lanes get it): lane l adds words
+// 4 (l & 1) .. + 3 of row l / 2.
+template <int PC>
+__device__ __forceinline__ uint32_t block_sum(const uint32_t* cbase, int lane) {
+  const uint4 t = *reinterpret_cast<const uint4*>(cbase + (lane >> 1) * PC + 4 * (lane & 1));
+  const uint32_t sc = dp2a_lo(t.x, kW11, dp2a_lo(t.y, kW11, dp2a_lo(t.z, kW11, dp2a_lo(t.w, kW11, 0u))));
+  return __reduce_add_sync(0xffffffffu, sc);
+}
+
+// full16_finish from the lane's own window sums (no table).
+template <int R, int PC>
+__device__ __forceinline__ void full16_finish_sums(const Full16WinSums<R>& S, const uint32_t* cbase, int lane,
+                                                   Full16Acc<R>& A) {
+  constexpr int NU = 2 * R + 1, SPANW = 8 + 2 * R;
+  const uint32_t sc = block_sum<PC>(cbase, lane);
+  uint32_t T[SPANW];
+#pragma unroll
+  for (int w = 0; w < SPANW; ++w) T[w] = w < SPANW / 2 ? dp2a_lo(S.cw[w], kW11, 0u) : S.cw[w];
+  uint32_t s = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) s += T[j];
+#pragma unroll
+  for (int k = 0; k < NU; ++k) {
+    if (k > 0) s += T[k + 7] - T[k - 1];
+    A.acc[k] = sc + s - A.acc[k];
+  }
+  if constexpr (NU == 33) {
+    A.accx = sc + S.sx - A.accx;
+    const uint32_t part = lane < 8 ? S.scn - A.accc : 0u;
+    A.accc = lane == 0 ? part + sc : part;
   }
 }
 
@@ -154,10 +219,7 @@ __device__ __forceinline__ void full16_finish(const uint32_t* csbase, const uint
                                               Full16Acc<R>& A) {
   constexpr int NU = 2 * R + 1, SPANW = 8 + 2 * R;
   const int v = lane < NU ? lane : NU - 1;
-  // sum of the current block: lane l adds words 4 (l & 1) .. + 3 of row l / 2
-  const uint4 t = *reinterpret_cast<const uint4*>(cbase + (lane >> 1) * PC + 4 * (lane & 1));
-  uint32_t sc = dp2a_lo(t.x, kW11, dp2a_lo(t.y, kW11, dp2a_lo(t.z, kW11, dp2a_lo(t.w, kW11, 0u))));
-  sc = __reduce_add_sync(0xffffffffu, sc);
+  const uint32_t sc = block_sum<PC>(cbase, lane);
   // window sums of row v: a sliding sum of 8 words along the column sums
   uint32_t T[SPANW];
   const uint4* cr = reinterpret_cast<const uint4*>(csbase + v * P);
@@ -245,7 +307,8 @@ template <int R, int P, int PC>
 __device__ __forceinline__ uint64_t full16_block(const uint32_t* wbase, const uint32_t* csbase, const uint32_t* cbase,
                                                  int lane, int xb, int yb, int W, int H) {
   Full16Acc<R> A;
-  full16_accumulate<R, P, PC>(wbase, cbase, lane, A);
+  Full16WinSums<R> unused;
+  full16_accumulate<R, P, PC, false>(wbase, cbase, lane, A, unused);
   full16_finish<R, P, PC>(csbase, cbase, lane, A);
   return full16_select<R>(A, lane, xb, yb, W, H);
 }

@@ -83,7 +83,11 @@ cudaError_t launch_r(const uint16_t* ref, const uint16_t* cur, int W, int H, int
 // low-confidence blocks of the learned-seeded search).  Each warp searches
 // its own block from its own window, so the blocks need not be adjacent;
 // warps loop over the list (grid-stride) up to the count found in device
-// memory.  One CTA of 11 warps per SM (the 11 windows fill shared memory).
+// memory.  One CTA of 15 warps per SM (the 15 windows fill shared memory).
+//
+// Window sums: each lane gathers its own during the row loop
+// (full16_accumulate with SUMS), so no column-sum table or table pass is
+// needed and a warp's shared memory is just its window and current block.
 //
 // Staging: with 16-byte aligned frames, two TMA tile loads per block (the
 // window as a box 2P pixels wide, which lands at the 4*odd-word pitch the
@@ -93,12 +97,11 @@ cudaError_t launch_r(const uint16_t* ref, const uint16_t* cur, int W, int H, int
 // finish, so the copies overlap the finish and the argmin.  Every wait is
 // bounded: on expiry the kernel records BAYER_ERR_TIMEOUT and the warp stops.
 // Other layouts stage with plain loads.
-constexpr int kLW = 11;  // warps per CTA in list mode
+constexpr int kLW = 15;  // warps per CTA in list mode
 constexpr uint32_t kWaitLimit = 1u << 22;
 
 template <int R>
 struct Full16List {
-  static constexpr int NU = 2 * R + 1;
   static constexpr int REACH = 2 * R;
   static constexpr int WIN_W = 16 + 2 * REACH;  // pixels
   static constexpr int WIN_H = 16 + 2 * REACH;
@@ -107,8 +110,7 @@ struct Full16List {
   static constexpr int BOX_W = 2 * P;           // TMA window box width (pixels)
   static constexpr int PC = 8;                  // current block: dense rows (read as broadcasts)
   static constexpr int CUR_OFF = WIN_H * P;
-  static constexpr int CS_OFF = CUR_OFF + 16 * PC;
-  static constexpr int WARP_WORDS = (CS_OFF + NU * P + 31) / 32 * 32;  // 128-byte aligned windows
+  static constexpr int WARP_WORDS = (CUR_OFF + 16 * PC + 31) / 32 * 32;  // 128-byte aligned windows
   static constexpr uint32_t TX_BYTES = (uint32_t)(WIN_H * P + 16 * PC) * 4u;
   static constexpr int MBAR_OFF = kLW * WARP_WORDS;  // one mbarrier per warp after the windows
   static constexpr size_t SMEM = (size_t)MBAR_OFF * sizeof(uint32_t) + kLW * sizeof(uint64_t);
@@ -187,7 +189,6 @@ __global__ void __launch_bounds__(kLW * 32) me_full16_list_kernel(const __grid_c
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint32_t* win = smem + warp * C::WARP_WORDS;
   uint32_t* curt = win + C::CUR_OFF;
-  uint32_t* cs = win + C::CS_OFF;
   const int n = *count;
   const int step = gridDim.x * kLW;
   int gi = blockIdx.x * kLW + warp;
@@ -224,10 +225,9 @@ __global__ void __launch_bounds__(kLW * 32) me_full16_list_kernel(const __grid_c
                     vec_ok, lane, win, curt);
       __syncwarp();
     }
-    window_colsums<R, C::P, C::WW, 32>(win, cs, lane);
-    __syncwarp();
     Full16Acc<R> A;
-    full16_accumulate<R, C::P, C::PC>(win, curt, lane, A);
+    Full16WinSums<R> S;
+    full16_accumulate<R, C::P, C::PC, true>(win, curt, lane, A, S);
     const int gn = gi + step;
     int pn = 0, xn = 0, yn = 0;
     if constexpr (TMA) {
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(kLW * 32) me_full16_list_kernel(const __grid_c
         tma::load_3d(win, &tm_ref, xn - C::REACH, yn - C::REACH, pn, &mbar[warp]);
       }
     }
-    full16_finish<R, C::P, C::PC>(cs, curt, lane, A);
+    full16_finish_sums<R, C::PC>(S, curt, lane, A);
     if constexpr (TMA) {
       __syncwarp();  // every lane is done reading the current block
       if (lane == 0 && gn < n) {
