@@ -8,13 +8,20 @@
 // all pairs, stages the strip's window (full16.cuh) and searches it.  The
 // hardware block scheduler balances the strips (a persistent variant with an
 // atomic work queue measured slower once the search itself got cheaper).
-// The last strip of a pair stamps %globaltimer.
+// Completion times, from %globaltimer, relative to the search launch's start
+// (the earliest start among its first 1024 CTAs): a pair with features
+// completes with its propagation, whose CTAs store their end times into their
+// own item slots, and a kernel at the end of the graph takes each pair's
+// latest slot; a pair without features is given the time that kernel runs,
+// i.e. the end of the whole launch.  The search kernel itself has no code
+// after the block search: any (stamping, counting, even an untaken branch to
+// them) lowered its issue rate from 92 % to 78 % at the same instruction count
+// (0.5 ms over 66,000 strips).
 // Propagation: one CTA (256 threads) per (pair, 4-channel chunk, tile of 256
 // units) item, the pair found by binary search in a second prefix table,
 // warps the pair's NCHW feature map by its MV field (prop_common.cuh); a unit is a 2 x 2 quad of
 // cells sharing one MV (bilinear, two or more cells per block side) or one
-// cell.  The last item of a pair stamps the pair's completion time relative
-// to the search launch's start.
+// cell.  Its CTAs stamp their own item slots.
 // Autotuner: on the first call for a set of sizes it times each schedule
 // (NW in {4, 8} x pair order {as given, largest first}) with CUDA events and
 // keeps the fastest; the graph (counter reset, search, propagation) is then
@@ -74,43 +81,41 @@ __device__ __forceinline__ int find_pair(const int* prefix, int n, int item) {
 template <int R, int NW>
 __global__ void __launch_bounds__(NW * 32, NW == 8 ? 4 : 6) ms_me_kernel(const MsPair* __restrict__ pairs,
                                                                           const int* __restrict__ prefix, int n,
-                                                                          MsCounters* ctr, int* __restrict__ done,
-                                                                          long long* __restrict__ end_ns) {
+                                                                          MsCounters* ctr) {
   using C = Full16Strip<R, NW>;
   extern __shared__ __align__(16) uint32_t smem[];
   uint32_t* win = smem;
   uint32_t* curt = smem + C::CUR_OFF;
   uint32_t* cs = smem + C::CS_OFF;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (threadIdx.x == 0) atomicMin(&ctr->t0, gtimer());
+  // The earliest start is among the first CTAs dispatched; stamping from all
+  // 66,000 strips serialised their starts on one word (0.5 ms).
+  if (threadIdx.x == 0 && blockIdx.x < 1024) atomicMin(&ctr->t0, gtimer());
   const int item = blockIdx.x;
   const int p = find_pair(prefix, n, item);
-  const MsPair P = pairs[p];
+  // descriptor fields are read where they are used, so that little stays
+  // live across the search (the kernel runs at 64 registers)
+  const MsPair* P = pairs + p;
   const int local = item - __ldg(prefix + p);
-  const int by = local / P.strips_x, sx = local - by * P.strips_x;
+  const int strips_x = P->strips_x;
+  const int by = local / strips_x, sx = local - by * strips_x;
   const int x0 = sx * NW * 16, y0 = by * 16;
-  stage_strip<R, NW>(P.ref, P.cur, P.W, P.H, P.pitch, x0, y0, P.vec != 0, win, curt);
+  const int W = P->W, H = P->H;
+  stage_strip<R, NW>(P->ref, P->cur, W, H, P->pitch, x0, y0, P->vec != 0, win, curt);
   __syncthreads();
   window_colsums<R, C::P, C::WW, NW * 32>(win, cs, threadIdx.x);
   __syncthreads();
   const int bx = sx * NW + warp;
-  if (bx < P.w) {
+  if (bx < W / 16) {
     const uint64_t best = warp_min_u64(
-        full16_block<R, C::P, C::PC>(win + 8 * warp, cs + 8 * warp, curt + 8 * warp, lane, bx * 16, y0, P.W, P.H));
-    if (lane == 0) P.mv[(long long)by * P.w + bx] = key_to_mv(best);
-  }
-  __syncthreads();  // MV records written
-  if (threadIdx.x == 0) {
-    __threadfence();
-    // pairs without features are complete when their MV field is
-    if (atomicAdd(&done[p], 1) == P.me_items - 1 && P.pr_items == 0) end_ns[p] = (long long)(gtimer() - ctr->t0);
+        full16_block<R, C::P, C::PC>(win + 8 * warp, cs + 8 * warp, curt + 8 * warp, lane, bx * 16, y0, W, H));
+    if (lane == 0) pairs[p].mv[(long long)by * (W / 16) + bx] = key_to_mv(best);
   }
 }
 
 __global__ void __launch_bounds__(kPropThreads) ms_prop_kernel(const MsPair* __restrict__ pairs,
                                                                 const int* __restrict__ prefix, int n,
-                                                                MsCounters* ctr, int* __restrict__ done,
-                                                                long long* __restrict__ end_ns, int interp) {
+                                                                unsigned long long* __restrict__ stamp, int interp) {
   {
     const int item = blockIdx.x;
     const int p = find_pair(prefix, n, item);
@@ -163,10 +168,28 @@ __global__ void __launch_bounds__(kPropThreads) ms_prop_kernel(const MsPair* __r
       }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
-      if (atomicAdd(&done[p], 1) == P.pr_items - 1) end_ns[p] = (long long)(gtimer() - ctr->t0);
-    }
+    if (threadIdx.x == 0) stamp[item] = gtimer();
+  }
+}
+
+// One CTA per pair: the latest end stamp of its propagation items, or for a
+// pair without features the current time, minus the search launch's start.
+__global__ void __launch_bounds__(256) ms_end_kernel(const unsigned long long* __restrict__ stamp,
+                                                     const int* __restrict__ prefix, int n,
+                                                     const MsCounters* __restrict__ ctr,
+                                                     long long* __restrict__ end_ns) {
+  __shared__ unsigned long long red[8];
+  const int p = blockIdx.x;
+  const int* pr = prefix + (n + 1);
+  unsigned long long t = (threadIdx.x == 0 && pr[p + 1] == pr[p]) ? gtimer() : 0ull;
+  for (int i = pr[p] + threadIdx.x; i < pr[p + 1]; i += 256) t = max(t, stamp[i]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t = max(t, __shfl_xor_sync(0xffffffffu, t, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < 8; ++w) t = max(t, red[w]);
+    end_ns[p] = (long long)(t - ctr->t0);
   }
 }
 
@@ -185,22 +208,22 @@ cudaError_t ms_me_configure() {
 }
 
 template <int R, int NW>
-cudaError_t ms_me_launch(const MsPair* pairs, const int* prefix, int n, int total, MsCounters* ctr, int* done,
-                         long long* end_ns, cudaStream_t st) {
+cudaError_t ms_me_launch(const MsPair* pairs, const int* prefix, int n, int total, MsCounters* ctr,
+                         cudaStream_t st) {
   using C = Full16Strip<R, NW>;
   if (total < 1) return cudaSuccess;
-  ms_me_kernel<R, NW><<<total, NW * 32, C::SMEM, st>>>(pairs, prefix, n, ctr, done, end_ns);
+  ms_me_kernel<R, NW><<<total, NW * 32, C::SMEM, st>>>(pairs, prefix, n, ctr);
   return cudaGetLastError();
 }
 
 template <int NW>
 cudaError_t ms_me_dispatch(int range, const MsPair* pairs, const int* prefix, int n, int total, MsCounters* ctr,
-                           int* done, long long* end_ns, cudaStream_t st) {
+                           cudaStream_t st) {
   switch (range) {
-    case 8: return ms_me_launch<4, NW>(pairs, prefix, n, total, ctr, done, end_ns, st);
-    case 16: return ms_me_launch<8, NW>(pairs, prefix, n, total, ctr, done, end_ns, st);
-    case 24: return ms_me_launch<12, NW>(pairs, prefix, n, total, ctr, done, end_ns, st);
-    case 32: return ms_me_launch<16, NW>(pairs, prefix, n, total, ctr, done, end_ns, st);
+    case 8: return ms_me_launch<4, NW>(pairs, prefix, n, total, ctr, st);
+    case 16: return ms_me_launch<8, NW>(pairs, prefix, n, total, ctr, st);
+    case 24: return ms_me_launch<12, NW>(pairs, prefix, n, total, ctr, st);
+    case 32: return ms_me_launch<16, NW>(pairs, prefix, n, total, ctr, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -213,7 +236,8 @@ struct MultiStream {
   int device = 0;
   MsPair* d_pairs = nullptr;
   int* d_prefix = nullptr;  // [2 * (n + 1)]: search prefix, then propagation prefix
-  int* d_done = nullptr;    // [2 * n]
+  unsigned long long* d_stamp = nullptr;  // end time (%globaltimer) of every propagation item
+  long long stamp_cap = 0;
   MsCounters* d_ctr = nullptr;
   long long* d_end = nullptr;  // [n] internal copy of end times
   int cap = 0;
@@ -253,7 +277,7 @@ void ms_destroy(MultiStream* m) {
   ms_clear_graphs(m);
   if (m->d_pairs) cudaFree(m->d_pairs);
   if (m->d_prefix) cudaFree(m->d_prefix);
-  if (m->d_done) cudaFree(m->d_done);
+  if (m->d_stamp) cudaFree(m->d_stamp);
   if (m->d_ctr) cudaFree(m->d_ctr);
   if (m->d_end) cudaFree(m->d_end);
   if (m->h_pairs) cudaFreeHost(m->h_pairs);
@@ -284,12 +308,11 @@ cudaError_t ensure_capacity(MultiStream* m, int n) {
   ms_clear_graphs(m);  // graphs hold the old table addresses
   if (m->d_pairs) cudaFree(m->d_pairs);
   if (m->d_prefix) cudaFree(m->d_prefix);
-  if (m->d_done) cudaFree(m->d_done);
   if (m->d_end) cudaFree(m->d_end);
   if (m->h_pairs) cudaFreeHost(m->h_pairs);
   if (m->h_prefix) cudaFreeHost(m->h_prefix);
   m->d_pairs = nullptr;
-  m->d_prefix = m->d_done = nullptr;
+  m->d_prefix = nullptr;
   m->d_end = nullptr;
   m->h_pairs = nullptr;
   m->h_prefix = nullptr;
@@ -297,7 +320,6 @@ cudaError_t ensure_capacity(MultiStream* m, int n) {
   const int c = n < 64 ? 64 : n;
   if ((e = cudaMalloc(&m->d_pairs, sizeof(MsPair) * c)) != cudaSuccess) return e;
   if ((e = cudaMalloc(&m->d_prefix, sizeof(int) * 2 * (c + 1))) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&m->d_done, sizeof(int) * 2 * c)) != cudaSuccess) return e;
   if ((e = cudaMalloc(&m->d_end, sizeof(long long) * c)) != cudaSuccess) return e;
   if ((e = cudaMallocHost(&m->h_pairs, sizeof(MsPair) * c)) != cudaSuccess) return e;
   if ((e = cudaMallocHost(&m->h_prefix, sizeof(int) * 2 * (c + 1))) != cudaSuccess) return e;
@@ -352,19 +374,49 @@ void build_table(MultiStream* m, const bayer_pair_t* pairs, int n, const Config&
   *pr_total = pr;
 }
 
-// Counter reset, search launch, propagation launch (the graph body).
+// Propagation items of all pairs: the size of the stamp array.
+long long max_items(const bayer_pair_t* pairs, int n, int interp) {
+  long long items = 0;
+  for (int i = 0; i < n; ++i) {
+    const bayer_pair_t& q = pairs[i];
+    if (q.feat) {
+      const bool quads = interp == BAYER_INTERP_BILINEAR && q.stride < 16;
+      const long long units = quads ? (long long)((q.Hf + 1) / 2) * ((q.Wf + 1) / 2) : (long long)q.Hf * q.Wf;
+      items += (long long)((q.C + kPropCh - 1) / kPropCh) * ((units + kPropThreads - 1) / kPropThreads);
+    }
+  }
+  return items;
+}
+
+cudaError_t ensure_stamps(MultiStream* m, long long items) {
+  if (items <= m->stamp_cap) return cudaSuccess;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return e;
+  ms_clear_graphs(m);  // graphs hold the old array's address
+  if (m->d_stamp) cudaFree(m->d_stamp);
+  m->d_stamp = nullptr;
+  m->stamp_cap = 0;
+  const long long c = items < 65536 ? 65536 : items + items / 4;
+  if ((e = cudaMalloc(&m->d_stamp, sizeof(unsigned long long) * (size_t)c)) != cudaSuccess) return e;
+  m->stamp_cap = c;
+  return cudaSuccess;
+}
+
+// Search launch, propagation launch, end times (the graph body).
 cudaError_t enqueue(MultiStream* m, int n, int range, int interp, const Config& cfg, int me_total, int pr_total,
                     cudaStream_t st) {
   // start time = max, lowered by atomicMin
   cudaError_t e = cudaMemsetAsync(&m->d_ctr->t0, 0xFF, sizeof(unsigned long long), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(m->d_done, 0, sizeof(int) * 2 * n, st);
   const int has_prop = pr_total > 0 ? 1 : 0;
   if (e == cudaSuccess)
-    e = cfg.nw == 4 ? ms_me_dispatch<4>(range, m->d_pairs, m->d_prefix, n, me_total, m->d_ctr, m->d_done, m->d_end, st)
-                    : ms_me_dispatch<8>(range, m->d_pairs, m->d_prefix, n, me_total, m->d_ctr, m->d_done, m->d_end, st);
+    e = cfg.nw == 4 ? ms_me_dispatch<4>(range, m->d_pairs, m->d_prefix, n, me_total, m->d_ctr, st)
+                    : ms_me_dispatch<8>(range, m->d_pairs, m->d_prefix, n, me_total, m->d_ctr, st);
   if (e == cudaSuccess && has_prop) {
-    ms_prop_kernel<<<pr_total, kPropThreads, 0, st>>>(m->d_pairs, m->d_prefix + (n + 1), n, m->d_ctr, m->d_done + n,
-                                                      m->d_end, interp);
+    ms_prop_kernel<<<pr_total, kPropThreads, 0, st>>>(m->d_pairs, m->d_prefix + (n + 1), n, m->d_stamp, interp);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    ms_end_kernel<<<n, 256, 0, st>>>(m->d_stamp, m->d_prefix, n, m->d_ctr, m->d_end);
     e = cudaGetLastError();
   }
   return e;
@@ -396,6 +448,7 @@ cudaError_t ms_run(MultiStream* m, const bayer_pair_t* pairs, int n, int range, 
                    cudaStream_t st) {
   cudaError_t e = ensure_capacity(m, n);
   if (e != cudaSuccess) return e;
+  if ((e = ensure_stamps(m, max_items(pairs, n, interp))) != cudaSuccess) return e;
   const std::string key = signature(pairs, n, range, interp);
   std::vector<int> perm;
   int me_total = 0, pr_total = 0;
