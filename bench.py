@@ -22,7 +22,9 @@ skips them):
     launch and one propagation launch replayed from a CUDA graph, with p50/p99
     per-frame latency;
   * precision_4k: a 3840x2160 clip, 128-channel stride-4 propagation and the
-    three 3x3 refine convs in BF16 on the tensor cores (FP32 run beside it).
+    three 3x3 refine convs in BF16 on the tensor cores (FP32 run beside it);
+  * c2f: the paper's coarse-to-fine pyramid presets (standard, modes 1-4) on
+    the same clip, EVEN phase, search alone and search + propagation.
 
 Under torchrun (N > 1) every rank runs an independent replica on its own GPU
 (the path shards into independent clips; no collective on the data path) and
@@ -360,6 +362,59 @@ def leg_multi_stream(h, clips, steps, warmup, peaks, pc_clk_sm, nsm, sm_mhz):
     }
 
 
+def leg_c2f(h, d_frames, d_feats, d_out, stream, steps, warmup, pc_clk_sm, nsm, sm_mhz, full_me_ms, full_step_ms):
+    """The paper's FME presets (coarse-to-fine pyramid) on the 1080p clip, EVEN
+    phase, 7 pairs per launch: the search alone and the search plus bilinear
+    propagation of the same feature maps at the last level's block size, beside
+    the exhaustive +-32 search of the plain step."""
+    import torch
+    from paper_2508_05990_b300 import bayer_me as bm
+    peak = pc_clk_sm * nsm * sm_mhz * 1e6
+    kw = dict(batch=PAIRS, ref_batch_stride=H * W, cur_batch_stride=H * W)
+    rows = {}
+    for name, setting in bm.C2F_PRESETS.items():
+        B = setting.levels[-1]
+        mv = torch.empty((PAIRS, -(-H // B), -(-W // B), 2), dtype=torch.int32, device="cuda")
+
+        def me():
+            h.estimate_ex(d_frames, d_frames[1:], mode=bm.MODE_C2F, phase=bm.PHASE_EVEN, c2f=setting, out=mv,
+                          stream=stream, **kw)
+
+        def step():
+            me()
+            h.feat_propagate(d_feats, mv, B, STRIDE, interp=bm.INTERP_BILINEAR, out=d_out, stream=stream)
+
+        res = {}
+        for label, fn in (("me", me), ("step", step)):
+            for _ in range(warmup):
+                fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            res[label] = e0.elapsed_time(e1) / steps
+        if h.sync_status() != bm.OK:
+            raise RuntimeError("device status after the C2F leg")
+        pc = PAIRS * bm.c2f_pixel_candidates(setting, H, W, even=True)
+        rows[name] = {"levels": list(setting.levels), "stages": [list(x) for x in setting.stages],
+                      "me_ms": round(res["me"], 4), "ms_per_step": round(res["step"], 4),
+                      "value": round(PAIRS / (res["step"] / 1e3), 2), "unit": UNIT,
+                      "pixel_candidates_per_launch": pc,
+                      "achieved_gpc_per_s": round(pc / (res["me"] / 1e3) / 1e9, 1),
+                      "frac_of_alu_peak": round(pc / (res["me"] / 1e3) / peak, 4),
+                      "me_vs_full_search": round(full_me_ms / res["me"], 3),
+                      "step_vs_plain_step": round(full_step_ms / res["step"], 3)}
+    return {"workload": "1080p clip (7 pairs per launch), EVEN phase; levels are block sizes, stages "
+                        "(radius in steps, step); propagation of the plain step's feature maps at the last "
+                        "level's block size",
+            "presets": rows, "steps": steps, "warmup": warmup,
+            "peak_source": "measured packed min.u16x2 + dp2a rate x SMs x median SM clock",
+            "gpu_launches": steps * 2 * len(rows)}
+
+
 def leg_refine_4k(h, clip, steps, warmup, peaks):
     """Precision form at 4K: exhaustive search of the 7 pairs, bilinear
     propagation of the 128-channel stride-4 NHWC maps, then the three 3x3 refine
@@ -577,8 +632,10 @@ def run_ours(args):
     except (OSError, ValueError):
         pass
 
-    multi_stream = refine_4k = None
+    multi_stream = refine_4k = c2f = None
     if legs:
+        c2f = leg_c2f(h, d_frames, d_feats, d_out, stream, steps=10, warmup=3, pc_clk_sm=pc_clk_sm, nsm=nsm,
+                      sm_mhz=sm_mhz, full_me_ms=statistics.mean(me_ms), full_step_ms=ms_total / args.steps)
         multi_stream = leg_multi_stream(h, leg_clips[0], steps=30, warmup=3, peaks=peaks, pc_clk_sm=pc_clk_sm,
                                         nsm=nsm, sm_mhz=sm_mhz)
         refine_4k = leg_refine_4k(h, leg_clips[1], steps=10, warmup=3, peaks=peaks)
@@ -644,6 +701,7 @@ def run_ours(args):
             "learned_seeded": learned,
             "multi_stream": multi_stream,
             "precision_4k": refine_4k,
+            "c2f": c2f,
         }
         if not args.no_cpu_baseline:
             result["cpu_baseline"] = cpu_baseline_sample(frames, feats)

@@ -142,6 +142,31 @@ class C2FSetting:
     stages: tuple = ((8, 8), (4, 4), (2, 1))
 
 
+# The paper's FME settings (Sec. 4.2, FME-settings table; Sec. 3.2 for the
+# standard pyramid): block sizes per level, (radius in steps, step) per stage.
+C2F_PRESETS = {
+    "standard": C2FSetting((64, 32), ((8, 8), (4, 4), (2, 1))),
+    "mode1": C2FSetting((64, 32), ((4, 8), (2, 4), (2, 1))),
+    "mode2": C2FSetting((64, 32), ((10, 8), (6, 4), (4, 1))),
+    "mode3": C2FSetting((32,), ((8, 8), (4, 4), (2, 1))),
+    "mode4": C2FSetting((64, 32, 16, 8), ((8, 8), (4, 4), (2, 1))),
+}
+
+
+def c2f_pixel_candidates(setting: C2FSetting, H: int, W: int, even: bool = True) -> int:
+    """Pixel-candidates one pair's C2F search schedules (candidates leaving the
+    frame included): sum over levels and stages of blocks x block pixels x
+    (2R+1)^2, with EVEN mapping an odd step s to s+1 and R*s/(s+1) steps."""
+    total = 0
+    for B in setting.levels:
+        blocks = -(-H // B) * -(-W // B)
+        for R, st in setting.stages:
+            if even and st % 2:
+                R, st = R * st // (st + 1), st + 1
+            total += blocks * B * B * (2 * R + 1) ** 2
+    return total
+
+
 class Handle:
     """A library handle bound to one CUDA device (``bayer_me_init``)."""
 

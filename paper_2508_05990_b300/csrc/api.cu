@@ -384,7 +384,8 @@ bayer_status_t bayer_me_estimate_ex(bayer_me_t h, const uint16_t* ref, const uin
       a.parent_h = parent ? (H + parent_B - 1) / parent_B : 0;
       a.parent_w = parent ? (W + parent_B - 1) / parent_B : 0;
       a.out = (l == p->n_levels - 1) ? mv_out : buf[l & 1];
-      cudaError_t e = bme::launch_generic(a, p->batch, st);
+      cudaError_t e = bme::launch_c2f_level(a, p->batch, st);
+      if (e == cudaErrorNotSupported) e = bme::launch_generic(a, p->batch, st);
       if (e != cudaSuccess) return cuda_status(e);
       parent = a.out;
       parent_B = B;

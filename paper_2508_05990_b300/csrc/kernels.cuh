@@ -40,6 +40,10 @@ struct GenericArgs {
   bayer_mv_t* out;
 };
 cudaError_t launch_generic(const GenericArgs& a, int batch, cudaStream_t st);
+// One C2F level on packed pixel pairs (me_c2f.cu): EVEN steps 2/4/8, whole
+// 32- or 64-pixel blocks, 16-byte aligned frames; cudaErrorNotSupported when
+// the level falls outside that (the caller runs launch_generic).
+cudaError_t launch_c2f_level(const GenericArgs& a, int batch, cudaStream_t st);
 
 // Propagation z_pred = Warp(z_R, MV).
 struct PropArgs {

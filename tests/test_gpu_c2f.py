@@ -1,0 +1,84 @@
+"""The paper's coarse-to-fine presets in the EVEN phase on the GPU vs the
+oracle, bit for bit: levels of whole 32- and 64-pixel blocks run the packed
+C2F kernel (me_c2f.cu), finer levels and unaligned frames the generic one."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2508_05990_b300 import bayer_me as bm
+from paper_2508_05990_b300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def handle():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2508_05990_b300 import build
+    build.build()
+    h = bm.Handle(0)
+    yield h
+    h.close()
+
+
+def check(got, want):
+    g = bm.records_to_numpy(got)
+    for k in ("dx", "dy", "sad"):
+        np.testing.assert_array_equal(g[k], want[k])
+
+
+@pytest.mark.parametrize("mode", ["standard", "mode1", "mode2", "mode3", "mode4"])
+def test_presets_even_batched(handle, mode):
+    H, W = 512, 768
+    frames = synth.pan_clip(60, H, W, n_frames=3, rect_size=(16, 96))
+    d = torch.from_numpy(frames).cuda()
+    setting = bm.C2F_PRESETS[mode]
+    out = handle.estimate_ex(d, d[1:], mode=bm.MODE_C2F, phase=bm.PHASE_EVEN, c2f=setting, batch=2,
+                             ref_batch_stride=H * W, cur_batch_stride=H * W)
+    torch.cuda.synchronize()
+    for t in range(2):
+        want, _ = oracle.me_c2f(frames[t], frames[t + 1], levels=list(setting.levels),
+                                stages=[tuple(s) for s in setting.stages], even=True)
+        check(out[t], want)
+
+
+def test_standard_1080p_clip(handle):
+    """Two pairs of the benchmark's 1080p clip with the standard pyramid."""
+    wl = synth.WORKLOADS["1080p"]
+    H, W = wl["H"], wl["W"]
+    frames = synth.pan_clip(wl["seed"], H, W, n_frames=3)
+    d = torch.from_numpy(frames).cuda()
+    out = handle.estimate_ex(d, d[1:], mode=bm.MODE_C2F, phase=bm.PHASE_EVEN, batch=2, ref_batch_stride=H * W,
+                             cur_batch_stride=H * W)
+    torch.cuda.synchronize()
+    for t in range(2):
+        want, _ = oracle.me_c2f(frames[t], frames[t + 1], even=True)
+        check(out[t], want)
+
+
+def test_large_motion_near_borders(handle):
+    """Fast global motion: the pyramid's windows reach past every frame edge."""
+    H, W = 256, 384
+    rng = np.random.default_rng(61)
+    base = synth.round_clip(synth.blob_texture_scene(rng, H + 128, W + 128))
+    f0 = np.ascontiguousarray(base[64:64 + H, 64:64 + W])
+    f1 = np.ascontiguousarray(base[64 - 38:64 - 38 + H, 64 + 52:64 + 52 + W])
+    out = handle.estimate_ex(torch.from_numpy(f0).cuda(), torch.from_numpy(f1).cuda(), mode=bm.MODE_C2F,
+                             phase=bm.PHASE_EVEN)
+    torch.cuda.synchronize()
+    want, _ = oracle.me_c2f(f0, f1, even=True)
+    check(out[0], want)
+
+
+def test_odd_pitch_takes_the_generic_kernel(handle):
+    H, W, pitch = 256, 320, 321
+    f0, f1 = synth.pan_clip(62, H, W, n_frames=2)
+    buf = np.zeros((2, H, pitch), np.uint16)
+    buf[0, :, :W], buf[1, :, :W] = f0, f1
+    d = torch.from_numpy(buf).cuda()
+    out = handle.estimate_ex(d[0], d[1], mode=bm.MODE_C2F, phase=bm.PHASE_EVEN, W=W, H=H, pitch=pitch)
+    torch.cuda.synchronize()
+    want, _ = oracle.me_c2f(f0, f1, even=True)
+    check(out[0], want)
