@@ -782,6 +782,39 @@ def run_refine_only(n_maps: int):
     return {"refine_maps": n_maps, "ms": round(ms, 4), "tflops": round(flops / (ms / 1e3) / 1e12, 1)}
 
 
+def run_c2f_only(steps: int):
+    """The C2F leg alone on the 1080p clip (its presets, search and search +
+    propagation, beside the exhaustive search): a small case for profiling the
+    pyramid kernels (frames 33 MB, features 2 x 234 MB on the device)."""
+    import torch
+    from paper_2508_05990_b300 import bayer_me as bm
+    from paper_2508_05990_b300 import build
+    build.build()
+    frames, feats = make_inputs(0)
+    h = bm.Handle(0)
+    stream = torch.cuda.current_stream()
+    d_frames = torch.from_numpy(frames).cuda()
+    d_feats = torch.from_numpy(feats).cuda()
+    d_out = torch.empty_like(d_feats)
+    full = torch.empty((PAIRS, H // BLOCK, W // BLOCK, 2), dtype=torch.int32, device="cuda")
+    kw = dict(batch=PAIRS, ref_batch_stride=H * W, cur_batch_stride=H * W)
+    for _ in range(3):
+        h.estimate_ex(d_frames, d_frames[1:], search_range=RANGE, out=full, **kw)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        h.estimate_ex(d_frames, d_frames[1:], search_range=RANGE, out=full, **kw)
+    e1.record()
+    torch.cuda.synchronize()
+    full_ms = e0.elapsed_time(e1) / steps
+    pc_clk_sm, mhz, nsm = h.probe_alu(3)
+    res = leg_c2f(h, d_frames, d_feats, d_out, stream, steps=steps, warmup=3, pc_clk_sm=pc_clk_sm, nsm=nsm,
+                  sm_mhz=mhz, full_me_ms=full_ms, full_step_ms=full_ms)
+    h.close()
+    return res
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -791,9 +824,14 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
     ap.add_argument("--no-legs", action="store_true",
                     help="skip the batched multi-stream and 4K precision legs (single-GPU runs only)")
+    ap.add_argument("--c2f-only", action="store_true",
+                    help="run only the coarse-to-fine leg (small case for profiling the pyramid kernels)")
     ap.add_argument("--refine-maps", type=int, default=0,
                     help="profiling aid: time only the BF16 refine convolutions on this many 4K-form maps and exit")
     args = ap.parse_args(argv)
+    if args.c2f_only:
+        print(json.dumps(run_c2f_only(10)), flush=True)
+        return
     if args.refine_maps > 0:
         print(json.dumps(run_refine_only(args.refine_maps)), flush=True)
         return
