@@ -43,6 +43,7 @@ struct C2FLevel {
   int TP;       // table pitch (words)
   int tab_off;  // first table (words)
   int tab_sz;   // words per block's table
+  int ms_off;   // per-candidate 2 sum min (words)
   int smem;     // bytes
 };
 
@@ -180,19 +181,26 @@ __global__ void __launch_bounds__(NW * 32) me_c2f_kernel(const GenericArgs a, co
   for (int k = 0; k < a.nst; ++k) {
     const int R = a.R[k], s = a.S[k], n = 2 * R + 1, hs = s >> 1;
     const int WT = BW + R * s;  // stage window words per row
-    // ---- column-sum tables: tab_b[v * TP + t] = sum of the B rows from the
-    // block's stage-window row v s, at the block's stage-window word t
-    for (int e = threadIdx.x; e < NB * WT; e += NT) {
-      const int b = e / WT, t = e - b * WT;
+    // ---- (1) column-sum tables: tab_b[v * TP + t] = sum of the B rows from
+    // the block's stage-window row v s, at the block's stage-window word t;
+    // each column in up to three runs of row offsets, so that every thread
+    // has some.  No barrier follows: the work items do not read the tables.
+    constexpr int kParts = 3;
+    const int vp = (n + kParts - 1) / kParts;
+    for (int e = threadIdx.x; e < NB * kParts * WT; e += NT) {
+      const int b = e / (kParts * WT), rem = e - b * kParts * WT;
+      const int part = rem / WT, t = rem - part * WT;
+      const int va = part * vp, vb = min(n, va + vp);
+      if (va >= vb) continue;
       const int r0 = L.reach - R * s + (scy[b] - cy0) + (b / T) * B;
       const int w0 = ((L.reach - R * s + (scx[b] - cx0)) >> 1) + (b % T) * BW;
       uint32_t* tab = smem + L.tab_off + b * L.tab_sz;
       const uint32_t* col = win + w0 + t;
       uint32_t acc = 0;
 #pragma unroll 16
-      for (int r = 0; r < B; ++r) acc = dp2a_lo(col[(r0 + r) * L.P], 0x0101u, acc);
-      tab[t] = acc;
-      for (int v = 1; v < n; ++v) {
+      for (int r = 0; r < B; ++r) acc = dp2a_lo(col[(r0 + va * s + r) * L.P], 0x0101u, acc);
+      tab[va * L.TP + t] = acc;
+      for (int v = va + 1; v < vb; ++v) {
         const int ra = r0 + (v - 1) * s;
 #pragma unroll 8
         for (int q = 0; q < s; ++q) {
@@ -203,16 +211,16 @@ __global__ void __launch_bounds__(NW * 32) me_c2f_kernel(const GenericArgs a, co
       }
     }
     if (threadIdx.x < NB) sbest[threadIdx.x] = kInvalidKey;
-    __syncthreads();
-    // ---- work items: (block b, candidate row v, columns u0 .. u0 + 8)
+    // ---- (2) work items: (block b, candidate row v, columns u0 .. u0 + 8) ->
+    // 2 sum min of each candidate into msum
+    uint32_t* msum = smem + L.ms_off;
     const int nchunk = (n + kUC - 1) / kUC;
     for (int it = warp; it < NB * n * nchunk; it += NW) {
       const int b = it / (n * nchunk), rem = it - b * n * nchunk;
       if (!valid[b]) continue;  // warp-uniform
       const int v = rem / nchunk, u0 = (rem - v * nchunk) * kUC;
-      const int cx = scx[b], cy = scy[b];
-      const int r0 = L.reach - R * s + (cy - cy0) + (b / T) * B;
-      const int w0 = ((L.reach - R * s + (cx - cx0)) >> 1) + (b % T) * BW;
+      const int r0 = L.reach - R * s + (scy[b] - cy0) + (b / T) * B;
+      const int w0 = ((L.reach - R * s + (scx[b] - cx0)) >> 1) + (b % T) * BW;
       uint32_t acc[kUC];
       // b is warp-uniform; the register arrays are indexed statically
 #pragma unroll
@@ -223,7 +231,6 @@ __global__ void __launch_bounds__(NW * 32) me_c2f_kernel(const GenericArgs a, co
           else c2f_item<B, 1>(win, L.P, r0 + v * s, w0 + u0 * hs, cr[bb], lane, acc);
         }
       }
-      // lane u < ucn finishes candidate u0 + u
       const int ucn = min(kUC, n - u0);
       uint32_t mine = 0;
 #pragma unroll
@@ -231,21 +238,35 @@ __global__ void __launch_bounds__(NW * 32) me_c2f_kernel(const GenericArgs a, co
         const uint32_t tot = __reduce_add_sync(0xffffffffu, acc[u]);
         if (lane == u) mine = tot;
       }
+      if (lane < ucn) msum[(b * n + v) * n + u0 + lane] = mine;
+    }
+    __syncthreads();
+    // ---- (3) keys, one thread per candidate; each block's minimum by warp
+    // reductions and one shared atomicMin per warp and block
+    for (int e0 = 0; e0 < NB * n * n; e0 += NT) {
+      const int e = e0 + threadIdx.x;
       uint64_t key = kInvalidKey;
-      if (lane < ucn) {
-        const int u = u0 + lane;
+      int b = NB;
+      if (e < NB * n * n) {
+        b = e / (n * n);
+        const int c = e - b * n * n, v = c / n, u = c - v * n;
         const int x0 = tx0 + (b % T) * B, y0 = ty0 + (b / T) * B;
-        const int dx = cx + (u - R) * s, dy = cy + (v - R) * s;
-        if (abs(dx) <= a.lim && abs(dy) <= a.lim && x0 + dx >= 0 && x0 + dx + B <= a.W && y0 + dy >= 0 &&
-            y0 + dy + B <= a.H) {
+        const int dx = scx[b] + (u - R) * s, dy = scy[b] + (v - R) * s;
+        const int bx = blockIdx.x * T + (b % T), by = blockIdx.y * T + (b / T);
+        if (bx < a.w && by < a.h && abs(dx) <= a.lim && abs(dy) <= a.lim && x0 + dx >= 0 && x0 + dx + B <= a.W &&
+            y0 + dy >= 0 && y0 + dy + B <= a.H) {
           const uint32_t* trow = smem + L.tab_off + b * L.tab_sz + v * L.TP + u * hs;
           uint32_t sw = 0;
+#pragma unroll 8
           for (int j = 0; j < BW; ++j) sw += trow[j];
-          key = make_key(ssc[b] + sw - mine, dx, dy);
+          key = make_key(ssc[b] + sw - msum[(b * n + v) * n + u], dx, dy);
         }
       }
-      key = warp_min_u64(key);
-      if (lane == 0 && key != kInvalidKey) atomicMin(&sbest[b], (unsigned long long)key);
+#pragma unroll
+      for (int bb = 0; bb < NB; ++bb) {
+        const uint64_t m = warp_min_u64(b == bb ? key : kInvalidKey);
+        if (lane == 0 && m != kInvalidKey) atomicMin(&sbest[bb], (unsigned long long)m);
+      }
     }
     __syncthreads();
     if (threadIdx.x < NB && sbest[threadIdx.x] != kInvalidKey) {
@@ -296,7 +317,8 @@ bool plan(const GenericArgs& a, int T, C2FLevel* L) {
   // the window, 64 words of padding (an item's unused columns read up to 32
   // words past the window), then the tables
   L->tab_off = (L->rows * L->P + 64 + 3) / 4 * 4;
-  const long long bytes = ((long long)L->tab_off + (long long)T * T * L->tab_sz) * 4;
+  L->ms_off = L->tab_off + T * T * L->tab_sz;
+  const long long bytes = ((long long)L->ms_off + (long long)T * T * vmax * vmax) * 4;
   if (bytes > 220 * 1024) return false;
   L->smem = (int)bytes;
   return true;
