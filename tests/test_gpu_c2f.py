@@ -82,3 +82,18 @@ def test_odd_pitch_takes_the_generic_kernel(handle):
     torch.cuda.synchronize()
     want, _ = oracle.me_c2f(f0, f1, even=True)
     check(out[0], want)
+
+
+@pytest.mark.parametrize("mode", ["standard", "mode3"])
+def test_partial_tiles_and_mixed_levels(handle, mode):
+    """480 x 800: 15 x 25 blocks of 32 (partial 2 x 2 tiles at the right and
+    bottom); 480 is no multiple of 64, so the standard pyramid's first level
+    takes the generic kernel and its second the packed one."""
+    H, W = 480, 800
+    f0, f1 = synth.pan_clip(63, H, W, n_frames=2, rect_size=(16, 96))
+    setting = bm.C2F_PRESETS[mode]
+    out = handle.estimate_ex(torch.from_numpy(f0).cuda(), torch.from_numpy(f1).cuda(), mode=bm.MODE_C2F,
+                             phase=bm.PHASE_EVEN, c2f=setting)
+    torch.cuda.synchronize()
+    want, _ = oracle.me_c2f(f0, f1, levels=list(setting.levels), stages=[tuple(s) for s in setting.stages], even=True)
+    check(out[0], want)
