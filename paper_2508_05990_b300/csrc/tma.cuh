@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 
 #include "tc_common.cuh"
 
@@ -30,15 +31,14 @@ inline bool encode_u16_frames(CUtensorMap* map, const void* base, int W, int H, 
                           const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
                           CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
   static Fn fn = nullptr;
-  static bool looked = false;
-  if (!looked) {
+  static std::once_flag once;
+  std::call_once(once, [] {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
       fn = reinterpret_cast<Fn>(p);
-    looked = true;
-  }
+  });
   if (!fn) return false;
   if ((reinterpret_cast<uintptr_t>(base) & 15) || ((pitch * 2) & 15) || ((box_w * 2) & 15)) return false;
   if (n > 1 && (frame_stride <= 0 || ((frame_stride * 2) & 15))) return false;
