@@ -13,7 +13,10 @@
 //
 // Warp roles (416 threads):
 //   warps 0-3   epilogue: TMEM -> registers -> bias, ReLU -> bf16 / float32 NHWC
-//               (warp w reads TMEM lanes 32w..32w+31 = pixels of the segment);
+//               (warp w reads TMEM lanes 32w..32w+31 = pixels of the segment),
+//               each 32-channel chunk turned around in a per-warp shared-memory
+//               tile so that a store instruction writes 64 / 128 contiguous bytes
+//               per pixel instead of 16 bytes at a stride of one pixel;
 //   warp 4      one thread issues the MMAs (9 * CIN/16 per input row and
 //               output row it touches) and commits them to mbarriers;
 //   warps 5-12  producers: global loads of the next input row (float32 input
@@ -59,20 +62,26 @@ constexpr uint32_t kWaitLimit = 1u << 22;
 // zeroes a slot after draining it (and all slots at the start).  A staged row
 // is read by 24 MMAs instead of 72, which cuts the tensor cores' shared-memory
 // operand traffic by 44 %.
-template <int CIN, int COUT, int SRC>
+template <int CIN, int COUT, int SRC, int OUTF>
 struct RowStreamLayout {
   static constexpr bool STACK = COUT == 64;
   static constexpr int NS = STACK ? 8 : kAcc;  // accumulator slots
   static constexpr int KC = CIN / 8;
   static constexpr int SLOT_BYTES = KC * kNP * 16;
-  static constexpr int NR = SRC == 2 ? 2 : 4;  // ring slots (float32 input: the weights leave room for 2)
+  // ring slots: float32 input leaves room for 2; float32 output gives one up to the store transpose
+  static constexpr int NR = SRC == 2 ? 2 : (OUTF == 1 ? 3 : 4);
   static constexpr int NG = SRC == 2 ? 1 : 2;  // producer groups taking alternate rows
   static constexpr int GT = kProdThreads / NG;
   static constexpr int B_BYTES = 9 * CIN * COUT * 2;
   static constexpr int BAR_OFF = B_BYTES + NR * SLOT_BYTES;
   static constexpr int NBAR = 2 * NR + 2 * NS + 1;
   static constexpr int BIAS_OFF = (BAR_OFF + NBAR * 8 + 16 + 15) / 16 * 16;  // float32 bias, read as broadcasts
-  static constexpr int SMEM = BIAS_OFF + COUT * 4;
+  // store transpose: per epilogue warp a tile of 32 pixels x 32 channels (float32: 4 KB,
+  // bf16: 2 KB) that turns the pixel-per-lane TMEM rows into contiguous runs of 128 / 64
+  // bytes per pixel for the global stores
+  static constexpr int XB_OFF = (BIAS_OFF + COUT * 4 + 127) / 128 * 128;
+  static constexpr int XB_BYTES = kEpiWarps * 32 * (OUTF == 1 ? 128 : 64);
+  static constexpr int SMEM = XB_OFF + XB_BYTES;
   static constexpr int TMEM_COLS = NS * COUT;
   static_assert(CIN % 16 == 0 && (COUT == 64 || COUT == 128), "shape");
   static_assert(B_BYTES % 16 == 0 && SLOT_BYTES % 16 == 0, "alignment");
@@ -111,7 +120,7 @@ __device__ __forceinline__ void raise_abort(volatile int* abort_flag, int* statu
 
 template <int CIN, int COUT, int SRC, int OUTF, bool RELU>
 __global__ void __launch_bounds__(kThreads, 1) conv3x3_rows_tc_kernel(const ConvRowsArgs a) {
-  using L = RowStreamLayout<CIN, COUT, SRC>;
+  using L = RowStreamLayout<CIN, COUT, SRC, OUTF>;
   constexpr int KC = L::KC;
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sB = smem;
@@ -355,9 +364,6 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_rows_tc_kernel(const Conv
           break;
         }
         tc::fence_after_sync();
-        const int ox = runs.seg * kM + tid;
-        const bool valid = ox < a.W;
-        const long long opix = ((long long)runs.b * a.H + y) * a.W + ox;
 #pragma unroll
         for (int cc = 0; cc < COUT; cc += 32) {
           float v[32];
@@ -368,31 +374,58 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_rows_tc_kernel(const Conv
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&acc_empty[acc]);
           }
-          if (valid) {
 #pragma unroll
-            for (int q4 = 0; q4 < 8; ++q4) {
-              const float4 b4 = *reinterpret_cast<const float4*>(sBias + cc + 4 * q4);
-              v[4 * q4] += b4.x;
-              v[4 * q4 + 1] += b4.y;
-              v[4 * q4 + 2] += b4.z;
-              v[4 * q4 + 3] += b4.w;
+          for (int q4 = 0; q4 < 8; ++q4) {
+            const float4 b4 = *reinterpret_cast<const float4*>(sBias + cc + 4 * q4);
+            v[4 * q4] += b4.x;
+            v[4 * q4 + 1] += b4.y;
+            v[4 * q4 + 2] += b4.z;
+            v[4 * q4 + 3] += b4.w;
+          }
+          if (RELU) {
+#pragma unroll
+            for (int q = 0; q < 32; ++q) v[q] = fmaxf(v[q], 0.f);
+          }
+          const int ox0 = runs.seg * kM + warp * 32;  // pixel of the warp's lane 0
+          const long long opix0 = ((long long)runs.b * a.H + y) * a.W + ox0;
+          if (OUTF == 0) {
+            // lane = pixel row of 64 bytes (four 16-byte slots), slot q stored at q ^ ((row >> 1) & 3):
+            // conflict-free both when a lane writes its row and when 4 lanes read one row
+            uint4* xb = reinterpret_cast<uint4*>(smem + L::XB_OFF) + warp * 128;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              xb[lane * 4 + (q ^ ((lane >> 1) & 3))] =
+                  make_uint4(bf2(v[8 * q], v[8 * q + 1]), bf2(v[8 * q + 2], v[8 * q + 3]),
+                             bf2(v[8 * q + 4], v[8 * q + 5]), bf2(v[8 * q + 6], v[8 * q + 7]));
+            __syncwarp();
+            // each store instruction: 8 pixels x 64 contiguous bytes (lanes 4i..4i+3 one pixel)
+            const int q = lane & 3;
+            __nv_bfloat16* obase = a.out + opix0 * COUT + cc + 8 * q;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const int p = 8 * i + (lane >> 2);
+              const uint4 t = xb[p * 4 + (q ^ ((p >> 1) & 3))];
+              if (ox0 + p < a.W) *reinterpret_cast<uint4*>(obase + (long long)p * COUT) = t;
             }
-            if (RELU) {
+            __syncwarp();
+          } else {
+            // lane = pixel row of the warp's tile, 16-byte slot q stored at q ^ (row & 7):
+            // conflict-free both when a lane writes its row and when 8 lanes read one row
+            float4* xb = reinterpret_cast<float4*>(smem + L::XB_OFF) + warp * 256;
 #pragma unroll
-              for (int q = 0; q < 32; ++q) v[q] = fmaxf(v[q], 0.f);
+            for (int q = 0; q < 8; ++q)
+              xb[lane * 8 + (q ^ (lane & 7))] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            __syncwarp();
+            // each store instruction: 4 pixels x 128 contiguous bytes (lanes 8i..8i+7 one pixel)
+            const int q = lane & 7;
+            float* obase = a.out_f32 + opix0 * COUT + cc + 4 * q;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const int p = 4 * i + (lane >> 3);
+              const float4 t = xb[p * 8 + (q ^ (p & 7))];
+              if (ox0 + p < a.W) *reinterpret_cast<float4*>(obase + (long long)p * COUT) = t;
             }
-            if (OUTF == 0) {
-              uint4* o4 = reinterpret_cast<uint4*>(a.out + opix * COUT + cc);
-#pragma unroll
-              for (int q4 = 0; q4 < 4; ++q4)
-                o4[q4] = make_uint4(bf2(v[8 * q4], v[8 * q4 + 1]), bf2(v[8 * q4 + 2], v[8 * q4 + 3]),
-                                    bf2(v[8 * q4 + 4], v[8 * q4 + 5]), bf2(v[8 * q4 + 6], v[8 * q4 + 7]));
-            } else {
-              float4* o4 = reinterpret_cast<float4*>(a.out_f32 + opix * COUT + cc);
-#pragma unroll
-              for (int q4 = 0; q4 < 8; ++q4)
-                o4[q4] = make_float4(v[4 * q4], v[4 * q4 + 1], v[4 * q4 + 2], v[4 * q4 + 3]);
-            }
+            __syncwarp();
           }
         }
       }
@@ -438,7 +471,7 @@ __global__ void pack_rows_weights_kernel(const float* __restrict__ w, int cout, 
 
 template <int CIN, int COUT, int SRC, int OUTF, bool RELU>
 cudaError_t launch_rows(const ConvRowsArgs& a, cudaStream_t st) {
-  using L = RowStreamLayout<CIN, COUT, SRC>;
+  using L = RowStreamLayout<CIN, COUT, SRC, OUTF>;
   const long long T = (long long)a.batch * ((a.W + kM - 1) / kM) * a.H;
   if (T < 1) return cudaSuccess;
   int dev = 0, nsm = 148;
@@ -450,7 +483,7 @@ cudaError_t launch_rows(const ConvRowsArgs& a, cudaStream_t st) {
 
 template <int CIN, int COUT, int SRC, int OUTF, bool RELU>
 cudaError_t configure_rows() {
-  using L = RowStreamLayout<CIN, COUT, SRC>;
+  using L = RowStreamLayout<CIN, COUT, SRC, OUTF>;
   return cudaFuncSetAttribute(conv3x3_rows_tc_kernel<CIN, COUT, SRC, OUTF, RELU>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
 }
