@@ -2,8 +2,8 @@
 // Coarse-to-fine Block Matching": large blocks first, each stage a (2R+1)^2
 // grid of step s around the previous stage's best; "Matching Criterion":
 // SAD, argmin = MV) on packed pixel pairs, for the EVEN phase (every step
-// even) and whole blocks of 32 or 64 pixels.  Other levels take the generic
-// kernel (me_generic.cu); both give the same MV field bit for bit.
+// even) and whole blocks of 8, 16, 32 or 64 pixels.  Other levels take the
+// generic kernel (me_generic.cu); both give the same MV field bit for bit.
 //
 // Mapping: one CTA per tile of T x T blocks that start from the same centre
 // (every block of level 0; at a finer level the blocks of one parent block).
@@ -24,6 +24,15 @@
 //     accumulating 2 min(cur, win) with min.u16x2 + dp2a.  Then one warp
 //     reduction per candidate, and SAD = sum(cur) + sum(win) - 2 sum min (the
 //     window sum from the table).
+//   * Blocks of 8 or 16 pixels (2 x 2 tiles, the four children of one parent
+//     block): a work item is one pair of candidate rows and up to 9 columns
+//     of all four blocks; lane (b, vv, r) = 8 b + 4 vv + r holds rows r,
+//     r + 4, ... of block b and reads them at candidate row 2 p + vv, so
+//     every lane works.  Per pixel cur + win - 2 min(cur, win) = |cur - win|,
+//     so a lane's partial Sum cur + Sum win - 2 Sum min is its pixels' exact
+//     partial SAD: the window sums come from a running prefix sum along the
+//     lane's row (two operations per column), two shuffles give each SAD,
+//     and the lanes keep running minimum keys.  No tables, no key phase.
 //   * A candidate whose displaced block leaves the frame is skipped; each
 //     block's minimum key (sad, |mv|_1, dy, dx) is its next stage's centre.
 #include "common.cuh"
@@ -77,11 +86,57 @@ __device__ __forceinline__ void c2f_item(const uint32_t* win, int P, int wr0, in
   }
 }
 
+// Small-block work item: the partial SADs of the lane's B / 4 block rows
+// (window row row0 + 4 k for block row r + 4 k) at candidate columns
+// u0 .. u0 + 8 (wb as in c2f_item), csum = the lane's sum of current samples.
+// Column u covers words [u H, u H + BW) of the row: its window sum is the
+// difference of the row's running sum S at those two words.
+template <int B, int H>
+__device__ __forceinline__ void c2f_item_small(const uint32_t* win, int P, int row0, int wb,
+                                               const uint32_t (&cr)[B / 4][B / 2], uint32_t csum, uint32_t* sad) {
+  constexpr int BW = B / 2;
+  constexpr int NWW = (kUC - 1) * H + BW;
+  uint32_t m2[kUC];  // 2 sum min per column
+#pragma unroll
+  for (int u = 0; u < kUC; ++u) {
+    sad[u] = csum;
+    m2[u] = 0;
+  }
+#pragma unroll
+  for (int k = 0; k < B / 4; ++k) {
+    const uint32_t* c = cr[k];
+    const uint32_t* wrow = win + (row0 + 4 * k) * P + wb;
+    uint32_t S = 0;
+#pragma unroll
+    for (int w = 0; w < NWW; ++w) {
+#pragma unroll
+      for (int u = 0; u < kUC; ++u) {
+        if (w == u * H) sad[u] -= S;
+        if (w == u * H + BW) sad[u] += S;
+      }
+      const uint32_t x = wrow[w];
+      S = dp2a_lo(x, 0x0101u, S);
+#pragma unroll
+      for (int u = 0; u < kUC; ++u) {
+        const int j = w - u * H;
+        if (j >= 0 && j < BW) m2[u] = dp2a_lo(min_u16x2(x, c[j]), 0x0202u, m2[u]);
+      }
+    }
+    sad[kUC - 1] += S;  // the last column ends at the row's last word
+  }
+#pragma unroll
+  for (int u = 0; u < kUC; ++u) sad[u] -= m2[u];  // modulo 2^32 throughout; the result is exact
+}
+
 template <int B, int T, int NW>
 __global__ void __launch_bounds__(NW * 32) me_c2f_kernel(const GenericArgs a, const C2FLevel L) {
   constexpr int NB = T * T;  // blocks per tile
   constexpr int BW = B / 2;
   constexpr int NT = NW * 32;
+  constexpr bool SMALL = B < 32;
+  static_assert(!SMALL || T == 2, "8- and 16-pixel blocks: 2 x 2 tiles, 8 lanes per block");
+  constexpr int KR = SMALL ? B / 4 : B / 32;  // block rows per lane
+  constexpr int CRB = SMALL ? 1 : NB;         // blocks whose rows a lane holds
   extern __shared__ __align__(16) uint32_t smem[];
   uint32_t* win = smem;  // rows x P
   __shared__ unsigned long long sbest[NB];
@@ -149,31 +204,57 @@ __global__ void __launch_bounds__(NW * 32) me_c2f_kernel(const GenericArgs a, co
   }
   // ---- the tile's blocks: validity, the lane's current rows in registers, block sums
   bool valid[NB];
-  uint32_t cr[NB][B / 32][BW];
 #pragma unroll
-  for (int b = 0; b < NB; ++b) {
-    const int bx = blockIdx.x * T + (b % T), by = blockIdx.y * T + (b / T);
-    valid[b] = bx < a.w && by < a.h;
+  for (int b = 0; b < NB; ++b) valid[b] = blockIdx.x * T + (b % T) < a.w && blockIdx.y * T + (b / T) < a.h;
+  uint32_t cr[CRB][KR][BW];
+  const int sb = lane >> 3, svv = (lane >> 2) & 1, sr = lane & 3;  // small blocks: the lane's (b, vv, r)
+  uint32_t csum = 0;                                                 // small blocks: the lane's sum of cur
+  if (threadIdx.x < NB) sbest[threadIdx.x] = kInvalidKey;
+  if constexpr (SMALL) {
+    const int bx = blockIdx.x * T + (sb % T), by = blockIdx.y * T + (sb / T);
     const uint16_t* curb = cur + (long long)(by * B) * a.pitch + bx * B;
-    uint32_t part = 0;
 #pragma unroll
-    for (int half = 0; half < B / 32; ++half) {
+    for (int k = 0; k < KR; ++k) {
 #pragma unroll
       for (int q = 0; q < BW / 4; ++q) {
         uint4 t = make_uint4(0, 0, 0, 0);
-        if (valid[b]) t = __ldg(reinterpret_cast<const uint4*>(curb + (long long)(lane + 32 * half) * a.pitch) + q);
-        cr[b][half][4 * q + 0] = t.x;
-        cr[b][half][4 * q + 1] = t.y;
-        cr[b][half][4 * q + 2] = t.z;
-        cr[b][half][4 * q + 3] = t.w;
-        part = dp2a_lo(t.x, 0x0101u, dp2a_lo(t.y, 0x0101u, dp2a_lo(t.z, 0x0101u, dp2a_lo(t.w, 0x0101u, part))));
+        if (valid[sb]) t = __ldg(reinterpret_cast<const uint4*>(curb + (long long)(sr + 4 * k) * a.pitch) + q);
+        cr[0][k][4 * q + 0] = t.x;
+        cr[0][k][4 * q + 1] = t.y;
+        cr[0][k][4 * q + 2] = t.z;
+        cr[0][k][4 * q + 3] = t.w;
+        csum = dp2a_lo(t.x, 0x0101u, dp2a_lo(t.y, 0x0101u, dp2a_lo(t.z, 0x0101u, dp2a_lo(t.w, 0x0101u, csum))));
       }
     }
-    part = __reduce_add_sync(0xffffffffu, part);  // every warp holds the same rows
-    if (threadIdx.x == 0) {
-      ssc[b] = part;
-      scx[b] = cx0;
-      scy[b] = cy0;
+    if (warp == 0 && (lane & 7) == 0) {
+      scx[sb] = cx0;
+      scy[sb] = cy0;
+    }
+  } else {
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const int bx = blockIdx.x * T + (b % T), by = blockIdx.y * T + (b / T);
+      const uint16_t* curb = cur + (long long)(by * B) * a.pitch + bx * B;
+      uint32_t part = 0;
+#pragma unroll
+      for (int half = 0; half < KR; ++half) {
+#pragma unroll
+        for (int q = 0; q < BW / 4; ++q) {
+          uint4 t = make_uint4(0, 0, 0, 0);
+          if (valid[b]) t = __ldg(reinterpret_cast<const uint4*>(curb + (long long)(lane + 32 * half) * a.pitch) + q);
+          cr[b][half][4 * q + 0] = t.x;
+          cr[b][half][4 * q + 1] = t.y;
+          cr[b][half][4 * q + 2] = t.z;
+          cr[b][half][4 * q + 3] = t.w;
+          part = dp2a_lo(t.x, 0x0101u, dp2a_lo(t.y, 0x0101u, dp2a_lo(t.z, 0x0101u, dp2a_lo(t.w, 0x0101u, part))));
+        }
+      }
+      part = __reduce_add_sync(0xffffffffu, part);  // every warp holds the same rows
+      if (threadIdx.x == 0) {
+        ssc[b] = part;
+        scx[b] = cx0;
+        scy[b] = cy0;
+      }
     }
   }
   __syncthreads();
@@ -187,7 +268,7 @@ __global__ void __launch_bounds__(NW * 32) me_c2f_kernel(const GenericArgs a, co
     // has some.  No barrier follows: the work items do not read the tables.
     constexpr int kParts = 3;
     const int vp = (n + kParts - 1) / kParts;
-    for (int e = threadIdx.x; e < NB * kParts * WT; e += NT) {
+    for (int e = threadIdx.x; e < (SMALL ? 0 : NB * kParts * WT); e += NT) {
       const int b = e / (kParts * WT), rem = e - b * kParts * WT;
       const int part = rem / WT, t = rem - part * WT;
       const int va = part * vp, vb = min(n, va + vp);
@@ -210,40 +291,81 @@ __global__ void __launch_bounds__(NW * 32) me_c2f_kernel(const GenericArgs a, co
         tab[v * L.TP + t] = acc;
       }
     }
-    if (threadIdx.x < NB) sbest[threadIdx.x] = kInvalidKey;
+    if (!SMALL && threadIdx.x < NB) sbest[threadIdx.x] = kInvalidKey;
     // ---- (2) work items: (block b, candidate row v, columns u0 .. u0 + 8) ->
     // 2 sum min of each candidate into msum
     uint32_t* msum = smem + L.ms_off;
     const int nchunk = (n + kUC - 1) / kUC;
-    for (int it = warp; it < NB * n * nchunk; it += NW) {
-      const int b = it / (n * nchunk), rem = it - b * n * nchunk;
-      if (!valid[b]) continue;  // warp-uniform
-      const int v = rem / nchunk, u0 = (rem - v * nchunk) * kUC;
-      const int r0 = L.reach - R * s + (scy[b] - cy0) + (b / T) * B;
-      const int w0 = ((L.reach - R * s + (scx[b] - cx0)) >> 1) + (b % T) * BW;
-      uint32_t acc[kUC];
-      // b is warp-uniform; the register arrays are indexed statically
+    if constexpr (SMALL) {
+      // items (candidate-row pair p, columns u0 .. u0 + 8) of all four blocks: SADs and the
+      // lanes' running minimum keys; a lane past the last candidate row recomputes the last
+      // one and keeps nothing
+      const int r0 = L.reach - R * s + (scy[sb] - cy0) + (sb / T) * B;
+      const int w0 = ((L.reach - R * s + (scx[sb] - cx0)) >> 1) + (sb % T) * BW;
+      const int x0 = tx0 + (sb % T) * B, y0 = ty0 + (sb / T) * B;
+      const int npair = (n + 1) >> 1;
+      uint64_t best = kInvalidKey;
+      for (int it = warp; it < npair * nchunk; it += NW) {
+        const int vp = it / nchunk, u0 = (it - vp * nchunk) * kUC;
+        const int v = 2 * vp + svv, ve = min(v, n - 1);
+        uint32_t sad[kUC];
+        if (hs == 4) c2f_item_small<B, 4>(win, L.P, r0 + ve * s + sr, w0 + u0 * hs, cr[0], csum, sad);
+        else if (hs == 2) c2f_item_small<B, 2>(win, L.P, r0 + ve * s + sr, w0 + u0 * hs, cr[0], csum, sad);
+        else c2f_item_small<B, 1>(win, L.P, r0 + ve * s + sr, w0 + u0 * hs, cr[0], csum, sad);
 #pragma unroll
-      for (int bb = 0; bb < NB; ++bb) {
-        if (bb == b) {
-          if (hs == 4) c2f_item<B, 4>(win, L.P, r0 + v * s, w0 + u0 * hs, cr[bb], lane, acc);
-          else if (hs == 2) c2f_item<B, 2>(win, L.P, r0 + v * s, w0 + u0 * hs, cr[bb], lane, acc);
-          else c2f_item<B, 1>(win, L.P, r0 + v * s, w0 + u0 * hs, cr[bb], lane, acc);
+        for (int u = 0; u < kUC; ++u) {
+          sad[u] += __shfl_xor_sync(0xffffffffu, sad[u], 2);
+          sad[u] += __shfl_xor_sync(0xffffffffu, sad[u], 1);
+        }
+        const int dy = scy[sb] + (v - R) * s;
+        const bool row_ok = v < n && valid[sb] && abs(dy) <= a.lim && y0 + dy >= 0 && y0 + dy + B <= a.H;
+#pragma unroll
+        for (int u = 0; u < kUC; ++u) {
+          const int dx = scx[sb] + (u0 + u - R) * s;
+          if ((u & 3) == sr && row_ok && u0 + u < n && abs(dx) <= a.lim && x0 + dx >= 0 && x0 + dx + B <= a.W) {
+            const uint64_t key = make_key(sad[u], dx, dy);
+            best = key < best ? key : best;
+          }
         }
       }
-      const int ucn = min(kUC, n - u0);
-      uint32_t mine = 0;
+      // the block's eight lanes, then one shared atomic per warp and block
 #pragma unroll
-      for (int u = 0; u < kUC; ++u) {
-        const uint32_t tot = __reduce_add_sync(0xffffffffu, acc[u]);
-        if (lane == u) mine = tot;
+      for (int o = 4; o >= 1; o >>= 1) {
+        const uint64_t other = __shfl_xor_sync(0xffffffffu, best, o);
+        best = other < best ? other : best;
       }
-      if (lane < ucn) msum[(b * n + v) * n + u0 + lane] = mine;
+      if ((lane & 7) == 0 && best != kInvalidKey) atomicMin(&sbest[sb], (unsigned long long)best);
+    } else {
+      for (int it = warp; it < NB * n * nchunk; it += NW) {
+        const int b = it / (n * nchunk), rem = it - b * n * nchunk;
+        if (!valid[b]) continue;  // warp-uniform
+        const int v = rem / nchunk, u0 = (rem - v * nchunk) * kUC;
+        const int r0 = L.reach - R * s + (scy[b] - cy0) + (b / T) * B;
+        const int w0 = ((L.reach - R * s + (scx[b] - cx0)) >> 1) + (b % T) * BW;
+        uint32_t acc[kUC];
+        // b is warp-uniform; the register arrays are indexed statically
+#pragma unroll
+        for (int bb = 0; bb < NB; ++bb) {
+          if (bb == b) {
+            if (hs == 4) c2f_item<B, 4>(win, L.P, r0 + v * s, w0 + u0 * hs, cr[bb], lane, acc);
+            else if (hs == 2) c2f_item<B, 2>(win, L.P, r0 + v * s, w0 + u0 * hs, cr[bb], lane, acc);
+            else c2f_item<B, 1>(win, L.P, r0 + v * s, w0 + u0 * hs, cr[bb], lane, acc);
+          }
+        }
+        const int ucn = min(kUC, n - u0);
+        uint32_t mine = 0;
+#pragma unroll
+        for (int u = 0; u < kUC; ++u) {
+          const uint32_t tot = __reduce_add_sync(0xffffffffu, acc[u]);
+          if (lane == u) mine = tot;
+        }
+        if (lane < ucn) msum[(b * n + v) * n + u0 + lane] = mine;
+      }
     }
     __syncthreads();
     // ---- (3) keys, one thread per candidate; each block's minimum by warp
     // reductions and one shared atomicMin per warp and block
-    for (int e0 = 0; e0 < NB * n * n; e0 += NT) {
+    for (int e0 = 0; e0 < (SMALL ? 0 : NB * n * n); e0 += NT) {
       const int e = e0 + threadIdx.x;
       uint64_t key = kInvalidKey;
       int b = NB;
@@ -273,6 +395,9 @@ __global__ void __launch_bounds__(NW * 32) me_c2f_kernel(const GenericArgs a, co
       const bayer_mv_t m = key_to_mv(sbest[threadIdx.x]);
       scx[threadIdx.x] = m.dx;
       scy[threadIdx.x] = m.dy;
+      // small blocks take their atomics in the items phase: reset for the next stage here
+      // (behind this stage's barriers); the last stage's minimum stays for the output
+      if (SMALL && k + 1 < a.nst) sbest[threadIdx.x] = kInvalidKey;
     }
     __syncthreads();  // centres, tables and bests are reused by the next stage
   }
@@ -301,7 +426,7 @@ cudaError_t c2f_launch(const GenericArgs& a, int batch, const C2FLevel& L, cudaS
   return cudaGetLastError();
 }
 
-bool plan(const GenericArgs& a, int T, C2FLevel* L) {
+bool plan(const GenericArgs& a, int T, C2FLevel* L, bool tables = true) {
   *L = C2FLevel{};
   int vmax = 0, wtmax = 0;
   for (int k = 0; k < a.nst; ++k) {
@@ -317,8 +442,8 @@ bool plan(const GenericArgs& a, int T, C2FLevel* L) {
   // the window, 64 words of padding (an item's unused columns read up to 32
   // words past the window), then the tables
   L->tab_off = (L->rows * L->P + 64 + 3) / 4 * 4;
-  L->ms_off = L->tab_off + T * T * L->tab_sz;
-  const long long bytes = ((long long)L->ms_off + (long long)T * T * vmax * vmax) * 4;
+  L->ms_off = L->tab_off + (tables ? T * T * L->tab_sz : 0);
+  const long long bytes = ((long long)L->ms_off + (tables ? (long long)T * T * vmax * vmax : 0)) * 4;
   if (bytes > 220 * 1024) return false;
   L->smem = (int)bytes;
   return true;
@@ -326,14 +451,15 @@ bool plan(const GenericArgs& a, int T, C2FLevel* L) {
 
 }  // namespace
 
-// The packed C2F level kernel serves EVEN-phase levels of whole 32- or
-// 64-pixel blocks with steps 2, 4 or 8, 16-byte aligned frames, and a union
+// The packed C2F level kernel serves EVEN-phase levels of whole 8-, 16-, 32-
+// or 64-pixel blocks with steps 2, 4 or 8, 16-byte aligned frames, and a union
 // window that fits shared memory; returns cudaErrorNotSupported otherwise
-// (the caller then runs the generic kernel).  32-pixel levels with large
-// windows take 2 x 2 tiles where the tile's blocks share a start centre
-// (level 0, or a parent block that is a multiple of twice their size).
+// (the caller then runs the generic kernel).  8- and 16-pixel levels, and
+// 32-pixel levels with large windows, take 2 x 2 tiles where the tile's blocks
+// share a start centre (level 0, or a parent block that is a multiple of
+// twice their size); 8- and 16-pixel levels without one take the generic kernel.
 cudaError_t launch_c2f_level(const GenericArgs& a, int batch, cudaStream_t st) {
-  if (a.B != 32 && a.B != 64) return cudaErrorNotSupported;
+  if (a.B != 8 && a.B != 16 && a.B != 32 && a.B != 64) return cudaErrorNotSupported;
   if (a.center_mode == 2 || a.W % a.B || a.H % a.B) return cudaErrorNotSupported;
   if ((reinterpret_cast<uintptr_t>(a.ref) % 16) || (reinterpret_cast<uintptr_t>(a.cur) % 16) || a.pitch % 8 ||
       a.ref_bs % 8 || a.cur_bs % 8)
@@ -341,6 +467,10 @@ cudaError_t launch_c2f_level(const GenericArgs& a, int batch, cudaStream_t st) {
   for (int k = 0; k < a.nst; ++k)
     if (a.S[k] != 2 && a.S[k] != 4 && a.S[k] != 8) return cudaErrorNotSupported;
   C2FLevel L{};
+  if (a.B <= 16) {
+    if (!(a.center_mode == 0 || a.parent_B % (2 * a.B) == 0) || !plan(a, 2, &L, false)) return cudaErrorNotSupported;
+    return a.B == 16 ? c2f_launch<16, 2, 8>(a, batch, L, st) : c2f_launch<8, 2, 8>(a, batch, L, st);
+  }
   if (a.B == 64) {
     if (!plan(a, 1, &L)) return cudaErrorNotSupported;
     return c2f_launch<64, 1, 8>(a, batch, L, st);

@@ -1,6 +1,7 @@
 """The paper's coarse-to-fine presets in the EVEN phase on the GPU vs the
-oracle, bit for bit: levels of whole 32- and 64-pixel blocks run the packed
-C2F kernel (me_c2f.cu), finer levels and unaligned frames the generic one."""
+oracle, bit for bit: levels of whole 8- to 64-pixel blocks run the packed
+C2F kernel (me_c2f.cu); levels without a whole-block grid or a shared start
+centre, and unaligned frames, the generic one."""
 import numpy as np
 import pytest
 
@@ -92,6 +93,50 @@ def test_partial_tiles_and_mixed_levels(handle, mode):
     H, W = 480, 800
     f0, f1 = synth.pan_clip(63, H, W, n_frames=2, rect_size=(16, 96))
     setting = bm.C2F_PRESETS[mode]
+    out = handle.estimate_ex(torch.from_numpy(f0).cuda(), torch.from_numpy(f1).cuda(), mode=bm.MODE_C2F,
+                             phase=bm.PHASE_EVEN, c2f=setting)
+    torch.cuda.synchronize()
+    want, _ = oracle.me_c2f(f0, f1, levels=list(setting.levels), stages=[tuple(s) for s in setting.stages], even=True)
+    check(out[0], want)
+
+
+def test_mode4_partial_small_tiles(handle):
+    """496 x 816: 31 x 51 blocks of 16 (partial 2 x 2 tiles of the small-block
+    path) and 62 x 102 of 8; no whole 32- or 64-pixel grid, so the two coarse
+    levels run the generic kernel and hand it their MVs as start centres."""
+    H, W = 496, 816
+    f0, f1 = synth.pan_clip(64, H, W, n_frames=2, rect_size=(8, 48))
+    setting = bm.C2F_PRESETS["mode4"]
+    out = handle.estimate_ex(torch.from_numpy(f0).cuda(), torch.from_numpy(f1).cuda(), mode=bm.MODE_C2F,
+                             phase=bm.PHASE_EVEN, c2f=setting)
+    torch.cuda.synchronize()
+    want, _ = oracle.me_c2f(f0, f1, levels=list(setting.levels), stages=[tuple(s) for s in setting.stages], even=True)
+    check(out[0], want)
+
+
+@pytest.mark.parametrize("levels,stages", [((16, 8), ((4, 4), (2, 1))), ((8,), ((8, 8), (4, 4), (2, 1))),
+                                           ((16,), ((2, 8), (2, 4), (2, 2)))])
+def test_small_block_levels(handle, levels, stages):
+    """Pyramids that start at a 16- or 8-pixel level (common start centre 0)."""
+    H, W = 256, 384
+    frames = synth.pan_clip(65, H, W, n_frames=3, rect_size=(8, 48))
+    d = torch.from_numpy(frames).cuda()
+    setting = bm.C2FSetting(levels, stages)
+    out = handle.estimate_ex(d, d[1:], mode=bm.MODE_C2F, phase=bm.PHASE_EVEN, c2f=setting, batch=2,
+                             ref_batch_stride=H * W, cur_batch_stride=H * W)
+    torch.cuda.synchronize()
+    for t in range(2):
+        want, _ = oracle.me_c2f(frames[t], frames[t + 1], levels=list(levels), stages=[tuple(s) for s in stages],
+                                even=True)
+        check(out[t], want)
+
+
+def test_mode4_1080p_pair(handle):
+    """One pair of the benchmark's 1080p clip through all four mode-4 levels."""
+    wl = synth.WORKLOADS["1080p"]
+    H, W = wl["H"], wl["W"]
+    f0, f1 = synth.pan_clip(wl["seed"], H, W, n_frames=2)
+    setting = bm.C2F_PRESETS["mode4"]
     out = handle.estimate_ex(torch.from_numpy(f0).cuda(), torch.from_numpy(f1).cuda(), mode=bm.MODE_C2F,
                              phase=bm.PHASE_EVEN, c2f=setting)
     torch.cuda.synchronize()
