@@ -326,10 +326,10 @@ bool plan(const GenericArgs& a, int T, C2FLevel* L) {
 // The packed C2F level kernel serves EVEN-phase levels of whole 8-, 16-, 32-
 // or 64-pixel blocks with steps 2, 4 or 8, 16-byte aligned frames, and a union
 // window that fits shared memory; returns cudaErrorNotSupported otherwise
-// (the caller then runs the generic kernel).  8- and 16-pixel levels, and
-// 32-pixel levels with large windows, take 2 x 2 tiles where the tile's blocks
-// share a start centre (level 0, or a parent block that is a multiple of
-// twice their size); 8- and 16-pixel levels without one take the generic kernel.
+// (the caller then runs the generic kernel).  8-, 16- and 32-pixel levels
+// take 2 x 2 tiles where the tile's blocks share a start centre (level 0, or
+// a parent block that is a multiple of twice their size); without one, 32-pixel
+// levels take one block per CTA and 8- and 16-pixel levels the generic kernel.
 cudaError_t launch_c2f_level(const GenericArgs& a, int batch, cudaStream_t st) {
   if (a.B != 8 && a.B != 16 && a.B != 32 && a.B != 64) return cudaErrorNotSupported;
   if (a.center_mode == 2 || a.W % a.B || a.H % a.B) return cudaErrorNotSupported;
@@ -346,15 +346,16 @@ cudaError_t launch_c2f_level(const GenericArgs& a, int batch, cudaStream_t st) {
   }
   if (a.B == 64) {
     if (!plan(a, 1, &L)) return cudaErrorNotSupported;
-    return c2f_launch<64, 1, 8>(a, batch, L, st);
+    // a stage of n candidate rows is n (n <= 9) or 2n items of the block: with
+    // n <= 9 everywhere four warps split them more evenly than eight
+    int nmax = 0;
+    for (int k = 0; k < a.nst; ++k) nmax = 2 * a.R[k] + 1 > nmax ? 2 * a.R[k] + 1 : nmax;
+    return nmax <= kUC ? c2f_launch<64, 1, 4>(a, batch, L, st) : c2f_launch<64, 1, 8>(a, batch, L, st);
   }
-  // a 2 x 2 tile when one block's window alone would leave at most two CTAs
-  // per SM (its window is then mostly shared); else one block per CTA
-  const bool one = plan(a, 1, &L);
-  if (one && L.smem <= 76 * 1024) return c2f_launch<32, 1, 8>(a, batch, L, st);
-  C2FLevel L2{};
-  if (shared_centre && plan(a, 2, &L2)) return c2f_launch<32, 2, 8>(a, batch, L2, st);
-  if (!one) return cudaErrorNotSupported;
+  // 32-pixel blocks: a 2 x 2 tile (two warps per block, one shared window)
+  // where the blocks share a start centre, else one block per CTA
+  if (shared_centre && plan(a, 2, &L)) return c2f_launch<32, 2, 8>(a, batch, L, st);
+  if (!plan(a, 1, &L)) return cudaErrorNotSupported;
   return c2f_launch<32, 1, 8>(a, batch, L, st);
 }
 

@@ -142,3 +142,18 @@ def test_mode4_1080p_pair(handle):
     torch.cuda.synchronize()
     want, _ = oracle.me_c2f(f0, f1, levels=list(setting.levels), stages=[tuple(s) for s in setting.stages], even=True)
     check(out[0], want)
+
+
+@pytest.mark.parametrize("levels", [(64, 32, 32), (16, 16)])
+def test_children_without_a_shared_centre(handle, levels):
+    """A repeated level: each block's parent is the same-sized block, so a 2 x 2
+    tile would mix start centres; the second 32-pixel level takes one block per
+    CTA and the second 16-pixel level the generic kernel."""
+    H, W = 288, 384
+    f0, f1 = synth.pan_clip(66, H, W, n_frames=2, rect_size=(8, 48))
+    stages = ((4, 8), (2, 4), (2, 1))
+    out = handle.estimate_ex(torch.from_numpy(f0).cuda(), torch.from_numpy(f1).cuda(), mode=bm.MODE_C2F,
+                             phase=bm.PHASE_EVEN, c2f=bm.C2FSetting(levels, stages))
+    torch.cuda.synchronize()
+    want, _ = oracle.me_c2f(f0, f1, levels=list(levels), stages=list(stages), even=True)
+    check(out[0], want)
