@@ -22,9 +22,14 @@
 //     |cur - win|, so Sum cur + Sum win - 2 Sum min over the lane's pixels is
 //     its exact partial SAD, a candidate column's window sum being the
 //     difference of the running sum at the column's two ends.
-//       - 32- and 64-pixel blocks: each warp serves one block of the tile;
-//         lane r holds block row r (and r + 32); one warp reduction per
-//         candidate column gives its SAD.
+//       - 32-pixel blocks: each warp serves one block of the tile; lane r
+//         holds block row r; one warp reduction per candidate column gives
+//         its SAD.
+//       - 64-pixel blocks: lane r holds rows r and r + 32.  Where every stage
+//         has at most 9 candidate rows (at most 9 items), warps pair up on an
+//         item instead, one per 32-row half; the second warp hands its column
+//         sums to the first through shared memory, behind a named barrier of
+//         the pair, so the short stages split into more, shorter items.
 //       - 8- and 16-pixel blocks (2 x 2 tiles): an item covers a pair of
 //         candidate rows of all four blocks; lane (b, vv, r) = 8 b + 4 vv + r
 //         holds rows r, r + 4, ... of block b at candidate row 2 p + vv, and
@@ -102,7 +107,7 @@ __device__ __forceinline__ void c2f_item_hs(int hs, const uint32_t* win, int P, 
   else c2f_item<KR, RS, BW, 1>(win, P, row0, wb, cr, csum, sad);
 }
 
-template <int B, int T, int NW>
+template <int B, int T, int NW, bool PAIRED = false>
 __global__ void __launch_bounds__(NW * 32) me_c2f_kernel(const GenericArgs a, const C2FLevel L) {
   constexpr int NB = T * T;  // blocks per tile
   constexpr int BW = B / 2;
@@ -110,13 +115,17 @@ __global__ void __launch_bounds__(NW * 32) me_c2f_kernel(const GenericArgs a, co
   constexpr bool SMALL = B < 32;
   static_assert(!SMALL || T == 2, "8- and 16-pixel blocks: 2 x 2 tiles, 8 lanes per block");
   static_assert(SMALL || NW % NB == 0, "32- and 64-pixel blocks: the same number of warps per block");
-  constexpr int KR = SMALL ? B / 4 : B / 32;  // block rows per lane
-  constexpr int RS = SMALL ? 4 : 32;          // row stride between a lane's rows
-  constexpr int WPB = SMALL ? NW : NW / NB;   // warps per block (large blocks)
+  static_assert(!PAIRED || B == 64, "warp pairs: 64-pixel blocks");
+  constexpr int KR = SMALL ? B / 4 : (PAIRED ? 1 : B / 32);  // block rows per lane
+  constexpr int RS = SMALL ? 4 : 32;                         // row stride between a lane's rows
+  constexpr int WPB = SMALL ? NW : NW / NB;                  // warps per block (large blocks)
+  constexpr int NPAIR = PAIRED ? WPB / 2 : 1;
+  static_assert(!PAIRED || (T == 1 && WPB % 2 == 0 && NPAIR <= 8), "64-pixel blocks: warp pairs");
   extern __shared__ __align__(16) uint32_t smem[];
   uint32_t* win = smem;  // rows x P
   __shared__ unsigned long long sbest[NB];
   __shared__ int scx[NB], scy[NB];
+  __shared__ uint32_t xsum[NPAIR][2][16];  // 64-pixel blocks: second half's column sums, by item parity
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int pair = blockIdx.z;
@@ -180,7 +189,8 @@ __global__ void __launch_bounds__(NW * 32) me_c2f_kernel(const GenericArgs a, co
   // ---- the lane's block (small blocks: lane group; large: the warp's) and its rows
   const int mb = SMALL ? lane >> 3 : warp / WPB;
   const int svv = (lane >> 2) & 1;                 // small blocks: candidate-row offset
-  const int rl = SMALL ? (lane & 3) : lane;        // the lane's first block row
+  const int hb = PAIRED ? (warp - mb * WPB) / NPAIR : 0;  // 64-pixel blocks: the warp's 32-row half
+  const int rl = SMALL ? (lane & 3) : lane + 32 * hb;     // the lane's first block row
   const int bx = blockIdx.x * T + (mb % T), by = blockIdx.y * T + (mb / T);
   const bool valid = bx < a.w && by < a.h;
   const int x0 = tx0 + (mb % T) * B, y0 = ty0 + (mb / T) * B;  // block origin (pixels)
@@ -251,7 +261,9 @@ __global__ void __launch_bounds__(NW * 32) me_c2f_kernel(const GenericArgs a, co
     } else {
       // items (candidate row v, columns u0 .. u0 + 8) of the warp's block, over its WPB warps
       if (valid) {
-        for (int it = warp - mb * WPB; it < n * nchunk; it += WPB) {
+        const int wi = warp - mb * WPB, pi = PAIRED ? wi % NPAIR : wi;
+        int parity = 0;
+        for (int it = pi; it < n * nchunk; it += (PAIRED ? NPAIR : WPB), parity ^= 1) {
           const int v = it / nchunk, u0 = (it - v * nchunk) * kUC;
           uint32_t sad[kUC];
           c2f_item_hs<KR, RS, BW>(hs, win, L.P, r0 + v * s + rl, w0 + u0 * hs, cr, csum, sad);
@@ -260,6 +272,14 @@ __global__ void __launch_bounds__(NW * 32) me_c2f_kernel(const GenericArgs a, co
           for (int u = 0; u < kUC; ++u) {
             const uint32_t tot = __reduce_add_sync(0xffffffffu, sad[u]);
             if (lane == u) mine = tot;
+          }
+          if constexpr (PAIRED) {
+            // both warps of the pair run the same items; the parity buffers let the second
+            // warp write the next item's sums while the first still reads these
+            if (hb == 1 && lane < kUC) xsum[pi][parity][lane] = mine;
+            asm volatile("bar.sync %0, 64;" ::"r"(1 + pi) : "memory");
+            if (hb == 1) continue;
+            mine += xsum[pi][parity][lane & 15];
           }
           // lane u: candidate column u0 + u
           const int dx = scx[mb] + (u0 + lane - R) * s, dy = scy[mb] + (v - R) * s;
@@ -299,11 +319,12 @@ __global__ void __launch_bounds__(NW * 32) me_c2f_kernel(const GenericArgs a, co
   }
 }
 
-template <int B, int T, int NW>
+template <int B, int T, int NW, bool PAIRED = false>
 cudaError_t c2f_launch(const GenericArgs& a, int batch, const C2FLevel& L, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(me_c2f_kernel<B, T, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem);
+  cudaError_t e =
+      cudaFuncSetAttribute(me_c2f_kernel<B, T, NW, PAIRED>, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem);
   if (e != cudaSuccess) return e;
-  me_c2f_kernel<B, T, NW><<<dim3((a.w + T - 1) / T, (a.h + T - 1) / T, batch), NW * 32, L.smem, st>>>(a, L);
+  me_c2f_kernel<B, T, NW, PAIRED><<<dim3((a.w + T - 1) / T, (a.h + T - 1) / T, batch), NW * 32, L.smem, st>>>(a, L);
   return cudaGetLastError();
 }
 
@@ -346,11 +367,12 @@ cudaError_t launch_c2f_level(const GenericArgs& a, int batch, cudaStream_t st) {
   }
   if (a.B == 64) {
     if (!plan(a, 1, &L)) return cudaErrorNotSupported;
-    // a stage of n candidate rows is n (n <= 9) or 2n items of the block: with
-    // n <= 9 everywhere four warps split them more evenly than eight
+    // a stage of n candidate rows is n (n <= 9) or more items of the block:
+    // with n <= 9 everywhere, two warp pairs on half-block items split them
+    // more evenly than eight warps on whole-block ones
     int nmax = 0;
     for (int k = 0; k < a.nst; ++k) nmax = 2 * a.R[k] + 1 > nmax ? 2 * a.R[k] + 1 : nmax;
-    return nmax <= kUC ? c2f_launch<64, 1, 4>(a, batch, L, st) : c2f_launch<64, 1, 8>(a, batch, L, st);
+    return nmax <= kUC ? c2f_launch<64, 1, 4, true>(a, batch, L, st) : c2f_launch<64, 1, 8>(a, batch, L, st);
   }
   // 32-pixel blocks: a 2 x 2 tile (two warps per block, one shared window)
   // where the blocks share a start centre, else one block per CTA
