@@ -57,19 +57,19 @@ struct C2FLevel {
 
 // One work item's partial SADs over the lane's KR block rows (window row
 // row0 + RS k for the lane's k-th row, current words cr[k]) at candidate
-// columns u0 .. u0 + 8: wb is the first window word of column u0, column u
-// starts H words further per step; csum = the lane's sum of current samples.
-// All nine columns are always computed -- straight-line code, no per-pair
+// columns u0 .. u0 + NC - 1: wb is the first window word of column u0, column
+// u starts H words further per step; csum = the lane's sum of current samples.
+// All NC columns are always computed -- straight-line code, no per-pair
 // guards; columns past the stage's last (at most 8 H = 32 words past its
 // window: inside the row pitch, or past the last row inside the padding that
 // follows the window) are discarded by the caller.
-template <int KR, int RS, int BW, int H>
+template <int KR, int RS, int BW, int H, int NC>
 __device__ __forceinline__ void c2f_item(const uint32_t* win, int P, int row0, int wb, const uint32_t (&cr)[KR][BW],
                                          uint32_t csum, uint32_t* sad) {
-  constexpr int NWW = (kUC - 1) * H + BW;  // window words of a row the item touches
-  uint32_t m2[kUC];                        // 2 sum min per column
+  constexpr int NWW = (NC - 1) * H + BW;  // window words of a row the item touches
+  uint32_t m2[NC];                        // 2 sum min per column
 #pragma unroll
-  for (int u = 0; u < kUC; ++u) {
+  for (int u = 0; u < NC; ++u) {
     sad[u] = csum;
     m2[u] = 0;
   }
@@ -81,30 +81,30 @@ __device__ __forceinline__ void c2f_item(const uint32_t* win, int P, int row0, i
 #pragma unroll
     for (int w = 0; w < NWW; ++w) {
 #pragma unroll
-      for (int u = 0; u < kUC; ++u) {
+      for (int u = 0; u < NC; ++u) {
         if (w == u * H) sad[u] -= S;
         if (w == u * H + BW) sad[u] += S;
       }
       const uint32_t x = wrow[w];
       S = dp2a_lo(x, 0x0101u, S);
 #pragma unroll
-      for (int u = 0; u < kUC; ++u) {
+      for (int u = 0; u < NC; ++u) {
         const int j = w - u * H;
         if (j >= 0 && j < BW) m2[u] = dp2a_lo(min_u16x2(x, c[j]), 0x0202u, m2[u]);
       }
     }
-    sad[kUC - 1] += S;  // the last column ends at the row's last word
+    sad[NC - 1] += S;  // the last column ends at the row's last word
   }
 #pragma unroll
-  for (int u = 0; u < kUC; ++u) sad[u] -= m2[u];  // modulo 2^32 throughout; the result is exact
+  for (int u = 0; u < NC; ++u) sad[u] -= m2[u];  // modulo 2^32 throughout; the result is exact
 }
 
-template <int KR, int RS, int BW>
+template <int KR, int RS, int BW, int NC = kUC>
 __device__ __forceinline__ void c2f_item_hs(int hs, const uint32_t* win, int P, int row0, int wb,
                                             const uint32_t (&cr)[KR][BW], uint32_t csum, uint32_t* sad) {
-  if (hs == 4) c2f_item<KR, RS, BW, 4>(win, P, row0, wb, cr, csum, sad);
-  else if (hs == 2) c2f_item<KR, RS, BW, 2>(win, P, row0, wb, cr, csum, sad);
-  else c2f_item<KR, RS, BW, 1>(win, P, row0, wb, cr, csum, sad);
+  if (hs == 4) c2f_item<KR, RS, BW, 4, NC>(win, P, row0, wb, cr, csum, sad);
+  else if (hs == 2) c2f_item<KR, RS, BW, 2, NC>(win, P, row0, wb, cr, csum, sad);
+  else c2f_item<KR, RS, BW, 1, NC>(win, P, row0, wb, cr, csum, sad);
 }
 
 template <int B, int T, int NW, bool PAIRED = false>
@@ -121,6 +121,7 @@ __global__ void __launch_bounds__(NW * 32) me_c2f_kernel(const GenericArgs a, co
   constexpr int WPB = SMALL ? NW : NW / NB;                  // warps per block (large blocks)
   constexpr int NPAIR = PAIRED ? WPB / 2 : 1;
   static_assert(!PAIRED || (T == 1 && WPB % 2 == 0 && NPAIR <= 8), "64-pixel blocks: warp pairs");
+  constexpr bool SLICE = B == 64 && !PAIRED;  // a stage's partial last round as 3-column slices
   extern __shared__ __align__(16) uint32_t smem[];
   uint32_t* win = smem;  // rows x P
   __shared__ unsigned long long sbest[NB];
@@ -259,19 +260,38 @@ __global__ void __launch_bounds__(NW * 32) me_c2f_kernel(const GenericArgs a, co
       }
       if ((lane & 7) == 0 && best != kInvalidKey) atomicMin(&sbest[mb], (unsigned long long)best);
     } else {
-      // items (candidate row v, columns u0 .. u0 + 8) of the warp's block, over its WPB warps
+      // items (candidate row v, columns u0 .. u0 + 8) of the warp's block, over its WPB warps.
+      // 64-pixel blocks: where the stage's last round would hold only a few whole items
+      // (3 x their number <= WPB), those items run as three 3-column slices each instead,
+      // all in one round (a slice costs about 37 % of a whole item)
       if (valid) {
         const int wi = warp - mb * WPB, pi = PAIRED ? wi % NPAIR : wi;
+        const int nitems = n * nchunk;
+        const int full = SLICE ? nitems / WPB * WPB : nitems;
+        const bool sliced = SLICE && nitems > full && 3 * (nitems - full) <= WPB;
+        const int nwork = sliced ? full + 3 * (nitems - full) : nitems;
         int parity = 0;
-        for (int it = pi; it < n * nchunk; it += (PAIRED ? NPAIR : WPB), parity ^= 1) {
-          const int v = it / nchunk, u0 = (it - v * nchunk) * kUC;
+        for (int it = pi; it < nwork; it += (PAIRED ? NPAIR : WPB), parity ^= 1) {
+          const bool sl = sliced && it >= full;
+          const int ti = sl ? full + (it - full) / 3 : it;  // the whole item
+          const int v = ti / nchunk, u0 = (ti - v * nchunk) * kUC + (sl ? 3 * ((it - full) % 3) : 0);
+          const int nc = sl ? 3 : kUC;
           uint32_t sad[kUC];
-          c2f_item_hs<KR, RS, BW>(hs, win, L.P, r0 + v * s + rl, w0 + u0 * hs, cr, csum, sad);
           uint32_t mine = 0;
+          if (sl) {
+            c2f_item_hs<KR, RS, BW, 3>(hs, win, L.P, r0 + v * s + rl, w0 + u0 * hs, cr, csum, sad);
 #pragma unroll
-          for (int u = 0; u < kUC; ++u) {
-            const uint32_t tot = __reduce_add_sync(0xffffffffu, sad[u]);
-            if (lane == u) mine = tot;
+            for (int u = 0; u < 3; ++u) {
+              const uint32_t tot = __reduce_add_sync(0xffffffffu, sad[u]);
+              if (lane == u) mine = tot;
+            }
+          } else {
+            c2f_item_hs<KR, RS, BW>(hs, win, L.P, r0 + v * s + rl, w0 + u0 * hs, cr, csum, sad);
+#pragma unroll
+            for (int u = 0; u < kUC; ++u) {
+              const uint32_t tot = __reduce_add_sync(0xffffffffu, sad[u]);
+              if (lane == u) mine = tot;
+            }
           }
           if constexpr (PAIRED) {
             // both warps of the pair run the same items; the parity buffers let the second
@@ -283,7 +303,7 @@ __global__ void __launch_bounds__(NW * 32) me_c2f_kernel(const GenericArgs a, co
           }
           // lane u: candidate column u0 + u
           const int dx = scx[mb] + (u0 + lane - R) * s, dy = scy[mb] + (v - R) * s;
-          if (lane < kUC && u0 + lane < n && abs(dx) <= a.lim && abs(dy) <= a.lim && x0 + dx >= 0 &&
+          if (lane < nc && u0 + lane < n && abs(dx) <= a.lim && abs(dy) <= a.lim && x0 + dx >= 0 &&
               x0 + dx + B <= a.W && y0 + dy >= 0 && y0 + dy + B <= a.H) {
             const uint64_t key = make_key(mine, dx, dy);
             best = key < best ? key : best;
