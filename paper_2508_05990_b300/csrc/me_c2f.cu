@@ -30,6 +30,8 @@
 //         item instead, one per 32-row half; the second warp hands its column
 //         sums to the first through shared memory, behind a named barrier of
 //         the pair, so the short stages split into more, shorter items.
+//         Otherwise a stage whose last round holds only a few whole items
+//         runs those as 3-column slices, all in that one round.
 //       - 8- and 16-pixel blocks (2 x 2 tiles): an item covers a pair of
 //         candidate rows of all four blocks; lane (b, vv, r) = 8 b + 4 vv + r
 //         holds rows r, r + 4, ... of block b at candidate row 2 p + vv, and
