@@ -364,20 +364,24 @@ def leg_multi_stream(h, clips, steps, warmup, peaks, pc_clk_sm, nsm, sm_mhz):
 
 def leg_c2f(h, d_frames, d_feats, d_out, stream, steps, warmup, pc_clk_sm, nsm, sm_mhz, full_me_ms, full_step_ms):
     """The paper's FME presets (coarse-to-fine pyramid) on the 1080p clip, EVEN
-    phase, 7 pairs per launch: the search alone and the search plus bilinear
-    propagation of the same feature maps at the last level's block size, beside
-    the exhaustive +-32 search of the plain step."""
+    phase, 7 pairs per launch, and the standard pyramid in the RAW phase (the
+    paper's step-1 fine stage taken literally): the search alone and the search
+    plus bilinear propagation of the same feature maps at the last level's block
+    size, beside the exhaustive +-32 search of the plain step."""
     import torch
     from paper_2508_05990_b300 import bayer_me as bm
     peak = pc_clk_sm * nsm * sm_mhz * 1e6
     kw = dict(batch=PAIRS, ref_batch_stride=H * W, cur_batch_stride=H * W)
     rows = {}
-    for name, setting in bm.C2F_PRESETS.items():
+    launches = 0
+    runs = [(name, setting, bm.PHASE_EVEN) for name, setting in bm.C2F_PRESETS.items()]
+    runs.append(("raw_standard", bm.C2F_PRESETS["standard"], bm.PHASE_RAW))
+    for name, setting, phase in runs:
         B = setting.levels[-1]
         mv = torch.empty((PAIRS, -(-H // B), -(-W // B), 2), dtype=torch.int32, device="cuda")
 
         def me():
-            h.estimate_ex(d_frames, d_frames[1:], mode=bm.MODE_C2F, phase=bm.PHASE_EVEN, c2f=setting, out=mv,
+            h.estimate_ex(d_frames, d_frames[1:], mode=bm.MODE_C2F, phase=phase, c2f=setting, out=mv,
                           stream=stream, **kw)
 
         def step():
@@ -398,8 +402,10 @@ def leg_c2f(h, d_frames, d_feats, d_out, stream, steps, warmup, pc_clk_sm, nsm, 
             res[label] = e0.elapsed_time(e1) / steps
         if h.sync_status() != bm.OK:
             raise RuntimeError("device status after the C2F leg")
-        pc = PAIRS * bm.c2f_pixel_candidates(setting, H, W, even=True)
-        rows[name] = {"levels": list(setting.levels), "stages": [list(x) for x in setting.stages],
+        pc = PAIRS * bm.c2f_pixel_candidates(setting, H, W, even=phase == bm.PHASE_EVEN)
+        launches += steps * (2 * len(setting.levels) + 1)  # the search's levels, then levels + propagation
+        rows[name] = {"phase": "EVEN" if phase == bm.PHASE_EVEN else "RAW",
+                      "levels": list(setting.levels), "stages": [list(x) for x in setting.stages],
                       "me_ms": round(res["me"], 4), "ms_per_step": round(res["step"], 4),
                       "value": round(PAIRS / (res["step"] / 1e3), 2), "unit": UNIT,
                       "pixel_candidates_per_launch": pc,
@@ -407,12 +413,12 @@ def leg_c2f(h, d_frames, d_feats, d_out, stream, steps, warmup, pc_clk_sm, nsm, 
                       "frac_of_alu_peak": round(pc / (res["me"] / 1e3) / peak, 4),
                       "me_vs_full_search": round(full_me_ms / res["me"], 3),
                       "step_vs_plain_step": round(full_step_ms / res["step"], 3)}
-    return {"workload": "1080p clip (7 pairs per launch), EVEN phase; levels are block sizes, stages "
-                        "(radius in steps, step); propagation of the plain step's feature maps at the last "
-                        "level's block size",
+    return {"workload": "1080p clip (7 pairs per launch), EVEN phase, and the standard pyramid in the RAW phase; "
+                        "levels are block sizes, stages (radius in steps, step); propagation of the plain step's "
+                        "feature maps at the last level's block size",
             "presets": rows, "steps": steps, "warmup": warmup,
             "peak_source": "measured packed min.u16x2 + dp2a rate x SMs x median SM clock",
-            "gpu_launches": steps * 2 * len(rows)}
+            "gpu_launches": launches}
 
 
 def leg_refine_4k(h, clip, steps, warmup, peaks):

@@ -1,9 +1,11 @@
 // One level of the paper's coarse-to-fine block matching (Sec. 3.2 "Parallel
 // Coarse-to-fine Block Matching": large blocks first, each stage a (2R+1)^2
 // grid of step s around the previous stage's best; "Matching Criterion":
-// SAD, argmin = MV) on packed pixel pairs, for the EVEN phase (every step
-// even) and whole blocks of 8, 16, 32 or 64 pixels.  Other levels take the
-// generic kernel (me_generic.cu); both give the same MV field bit for bit.
+// SAD, argmin = MV) on packed pixel pairs, for whole blocks of 8, 16, 32 or 64
+// pixels: the EVEN phase (every step even) and the RAW phase's pyramids, whose
+// steps are even but the last (step 1) and whose start centres may be odd.
+// Other levels take the generic kernel (me_generic.cu); both give the same MV
+// field bit for bit.
 //
 // Mapping: one CTA per tile of T x T blocks that start from the same centre
 // (every block of level 0; at a finer level the blocks of one parent block).
@@ -12,7 +14,13 @@
 //     packed pixel pairs (16-byte global loads, 32-bit stores; out-of-frame
 //     samples 0) at an odd row pitch, so that lanes reading one column of
 //     different rows hit different banks.  Sharing it between T x T blocks
-//     cuts the staged pixels per block.
+//     cuts the staged pixels per block.  The pairs start at the centre's
+//     column parity (an odd start joins the halves of adjacent aligned words
+//     with a funnel shift), so every candidate of an even-step stage begins
+//     on a word.
+//   * A step-1 last stage (RAW): its candidates of each column parity form a
+//     step-2 grid; each block stages one small window per parity in the
+//     union window's space, and the same work items run on those.
 //   * Work items: one candidate row (or pair of rows) and up to 9 consecutive
 //     candidate columns.  A lane holds block rows of the current frame in
 //     registers, reads each window word of its row once and feeds it to every
@@ -50,12 +58,81 @@ namespace {
 constexpr int kUC = 9;  // candidate columns per work item
 
 struct C2FLevel {
-  int reach;  // sum over stages of R * s (pixels)
+  int reach;  // sum over the even-step stages of R * s (pixels)
   int rows;   // union window rows = T B + 2 reach
   int P;      // union window pitch (words, odd)
   int WWu;    // union window words per row
+  // an odd-step (s = 1) last stage: per block and column parity a half window
+  int SR;     // its rows (B + 2R)
+  int SWW;    // its words per row (B/2 + R)
+  int SP;     // its pitch (words, odd)
+  int SSZ;    // words per half window, padding included
   int smem;   // bytes
 };
+
+// Stage rows x WW words of packed pixel pairs into dst (row pitch P words):
+// word w of row r holds the pixels gx0 + 2w and gx0 + 2w + 1 of frame row
+// gy0 + r, samples outside the frame 0.  16-byte loads of 8-pixel chunks from
+// the aligned column at or left of gx0; for an odd gx0 each word joins the
+// high half of one aligned word and the low half of the next (one funnel
+// shift), a chunk's last word taking the next chunk's first (one 4-byte
+// load).  Every thread takes chunks tid, tid + NT, ...; (row, chunk) of
+// consecutive ones advance by the constant divmod(NT, chunks per row), so
+// only the first needs a division; the BATCH loads of a batch are in flight
+// before its stores.  Every thread of the CTA calls it; no barrier.
+template <int NT, int BATCH, bool ODD>
+__device__ __forceinline__ void stage_window(uint32_t* dst, int P, int WW, int rows, int gx0, int gy0,
+                                             const uint16_t* ref, int W, int H, int pitch) {
+  const int par = ODD ? gx0 & 1 : 0;  // without ODD, gx0 is even
+  const int e0 = gx0 - par;                   // even pixel of word 0's aligned pair
+  const int xa = e0 - (((e0 % 8) + 8) % 8);   // its 16-byte aligned chunk
+  const int offw = (e0 - xa) >> 1;            // 0..3
+  constexpr int kBatch = BATCH;
+  const int nch = (WW + offw + 3) / 4;  // chunks per row
+  const int dry = NT / nch, dch = NT - dry * nch;
+  int ry = threadIdx.x / nch, ch = threadIdx.x - ry * nch;
+  while (ry < rows) {
+    uint4 v[kBatch];
+    uint32_t nx[kBatch];
+    int rys[kBatch], chs[kBatch];
+#pragma unroll
+    for (int i = 0; i < kBatch; ++i) {
+      rys[i] = ry;
+      chs[i] = ch;
+      const int gy = gy0 + ry, gx = xa + 8 * ch;
+      v[i] = make_uint4(0, 0, 0, 0);
+      nx[i] = 0;
+      if (ry < rows && gy >= 0 && gy < H) {
+        const uint16_t* rowp = ref + (long long)gy * pitch;
+        if (gx >= 0 && gx < W) v[i] = __ldg(reinterpret_cast<const uint4*>(rowp + gx));
+        if (par && gx + 8 >= 0 && gx + 8 < W) nx[i] = __ldg(reinterpret_cast<const uint32_t*>(rowp + gx + 8));
+      }
+      ry += dry;
+      ch += dch;
+      if (ch >= nch) {
+        ch -= nch;
+        ++ry;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < kBatch; ++i) {
+      if (rys[i] < rows) {
+        uint32_t t[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
+        if (par) {
+          t[0] = __funnelshift_r(v[i].x, v[i].y, 16);
+          t[1] = __funnelshift_r(v[i].y, v[i].z, 16);
+          t[2] = __funnelshift_r(v[i].z, v[i].w, 16);
+          t[3] = __funnelshift_r(v[i].w, nx[i], 16);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int wcol = 4 * chs[i] + k - offw;
+          if (wcol >= 0 && wcol < WW) dst[rys[i] * P + wcol] = t[k];
+        }
+      }
+    }
+  }
+}
 
 // One work item's partial SADs over the lane's KR block rows (window row
 // row0 + RS k for the lane's k-th row, current words cr[k]) at candidate
@@ -109,7 +186,9 @@ __device__ __forceinline__ void c2f_item_hs(int hs, const uint32_t* win, int P, 
   else c2f_item<KR, RS, BW, 1, NC>(win, P, row0, wb, cr, csum, sad);
 }
 
-template <int B, int T, int NW, bool PAIRED = false>
+// ODD: the level's last stage may step by 1 and its start centres may be odd
+// (the RAW phase); without it every step and centre is even.
+template <int B, int T, int NW, bool PAIRED = false, bool ODD = false>
 __global__ void __launch_bounds__(NW * 32) me_c2f_kernel(const GenericArgs a, const C2FLevel L) {
   constexpr int NB = T * T;  // blocks per tile
   constexpr int BW = B / 2;
@@ -144,51 +223,10 @@ __global__ void __launch_bounds__(NW * 32) me_c2f_kernel(const GenericArgs a, co
     cy0 = p.dy;
   }
 
-  // ---- stage the union window: origin (ox, oy); 8-pixel chunks from the
-  // 16-byte aligned column xa <= ox, word w of the window = pixel pair ox + 2w
-  const int ox = tx0 + cx0 - L.reach, oy = ty0 + cy0 - L.reach;
-  const int xa = ox - (((ox % 8) + 8) % 8);
-  const int offw = (ox - xa) >> 1;  // 0..3
-  {
-    // every thread takes chunks e = tid, tid + NT, ...; (row, chunk) of
-    // consecutive ones advance by the constant divmod(NT, nch), so only the
-    // first needs a division; all loads of a batch are in flight before the
-    // stores
-    constexpr int kBatch = 9;
-    const int nch = (L.WWu + offw + 3) / 4;  // chunks per row
-    const int dry = NT / nch, dch = NT - dry * nch;
-    int ry = threadIdx.x / nch, ch = threadIdx.x - ry * nch;
-    while (ry < L.rows) {
-      uint4 v[kBatch];
-      int rys[kBatch], chs[kBatch];
-#pragma unroll
-      for (int i = 0; i < kBatch; ++i) {
-        rys[i] = ry;
-        chs[i] = ch;
-        const int gy = oy + ry, gx = xa + 8 * ch;
-        v[i] = make_uint4(0, 0, 0, 0);
-        if (ry < L.rows && gy >= 0 && gy < a.H && gx >= 0 && gx < a.W)
-          v[i] = __ldg(reinterpret_cast<const uint4*>(ref + (long long)gy * a.pitch + gx));
-        ry += dry;
-        ch += dch;
-        if (ch >= nch) {
-          ch -= nch;
-          ++ry;
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < kBatch; ++i) {
-        if (rys[i] < L.rows) {
-          const uint32_t t[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const int wcol = 4 * chs[i] + k - offw;
-            if (wcol >= 0 && wcol < L.WWu) win[rys[i] * L.P + wcol] = t[k];
-          }
-        }
-      }
-    }
-  }
+  // ---- stage the union window of the even-step stages: origin (ox, oy), of
+  // the start centre's column parity
+  stage_window<NT, 9, ODD>(win, L.P, L.WWu, L.rows, tx0 + cx0 - L.reach, ty0 + cy0 - L.reach, ref, a.W, a.H,
+                           a.pitch);
   // ---- the lane's block (small blocks: lane group; large: the warp's) and its rows
   const int mb = SMALL ? lane >> 3 : warp / WPB;
   const int svv = (lane >> 2) & 1;                 // small blocks: candidate-row offset
@@ -223,32 +261,51 @@ __global__ void __launch_bounds__(NW * 32) me_c2f_kernel(const GenericArgs a, co
   __syncthreads();
 
   for (int k = 0; k < a.nst; ++k) {
-    const int R = a.R[k], s = a.S[k], n = 2 * R + 1, hs = s >> 1;
-    const int nchunk = (n + kUC - 1) / kUC;
+    const int R = a.R[k], s = a.S[k], n = 2 * R + 1;
+    // An odd step (s = 1, the last stage only): the candidates of each column
+    // parity form a step-2 grid; each block stages one half window per parity
+    // (set sg: columns u = 2j + sg, dx = centre + u - R) into the space of the
+    // union window, which no later stage reads.
+    const bool odd = ODD && (s & 1);
+    if (odd) {
+      for (int b = 0; b < NB; ++b)
+        for (int sg = 0; sg < 2; ++sg)
+          // a short batch: the lanes' current rows are live here
+          stage_window<NT, 2, true>(win + (b * 2 + sg) * L.SSZ, L.SP, L.SWW, L.SR, tx0 + (b % T) * B + scx[b] - R + sg,
+                           ty0 + (b / T) * B + scy[b] - R, ref, a.W, a.H, a.pitch);
+      __syncthreads();
+    }
+    const int hs = odd ? 1 : s >> 1;          // words between an item's columns
+    const int nset = odd ? 2 : 1;
+    const int ncol = odd ? R + 1 : n;         // columns of set 0 (set 1: R)
+    const int nchunk = (ncol + kUC - 1) / kUC;
     // the block's stage window: window row of block row 0 and word of candidate column 0
     const int r0 = L.reach - R * s + (scy[mb] - cy0) + (mb / T) * B;
     const int w0 = ((L.reach - R * s + (scx[mb] - cx0)) >> 1) + (mb % T) * BW;
     uint64_t best = kInvalidKey;
     if constexpr (SMALL) {
-      // items (candidate-row pair p, columns u0 .. u0 + 8) of all four blocks; a lane past
-      // the last candidate row recomputes the last one and keeps nothing
+      // items (set sg, candidate-row pair p, columns u0 .. u0 + 8) of all four blocks; a lane
+      // past the last candidate row recomputes the last one and keeps nothing
       const int npair = (n + 1) >> 1;
-      for (int it = warp; it < npair * nchunk; it += NW) {
-        const int vp = it / nchunk, u0 = (it - vp * nchunk) * kUC;
+      for (int it = warp; it < nset * npair * nchunk; it += NW) {
+        const int sg = ODD ? it / (npair * nchunk) : 0, rem = it - sg * npair * nchunk;
+        const int vp = rem / nchunk, u0 = (rem - vp * nchunk) * kUC;
         const int v = 2 * vp + svv, ve = min(v, n - 1);
+        const uint32_t* wsrc = odd ? win + (mb * 2 + sg) * L.SSZ : win;
         uint32_t sad[kUC];
-        c2f_item_hs<KR, RS, BW>(hs, win, L.P, r0 + ve * s + rl, w0 + u0 * hs, cr, csum, sad);
+        c2f_item_hs<KR, RS, BW>(hs, wsrc, odd ? L.SP : L.P, (odd ? 0 : r0) + ve * s + rl, (odd ? 0 : w0) + u0 * hs,
+                                cr, csum, sad);
 #pragma unroll
         for (int u = 0; u < kUC; ++u) {
           sad[u] += __shfl_xor_sync(0xffffffffu, sad[u], 2);
           sad[u] += __shfl_xor_sync(0xffffffffu, sad[u], 1);
         }
-        const int dy = scy[mb] + (v - R) * s;
+        const int dy = scy[mb] + (v - R) * s, cnt = odd ? ncol - sg : n;
         const bool row_ok = v < n && valid && abs(dy) <= a.lim && y0 + dy >= 0 && y0 + dy + B <= a.H;
 #pragma unroll
         for (int u = 0; u < kUC; ++u) {
-          const int dx = scx[mb] + (u0 + u - R) * s;
-          if ((u & 3) == rl && row_ok && u0 + u < n && abs(dx) <= a.lim && x0 + dx >= 0 && x0 + dx + B <= a.W) {
+          const int dx = scx[mb] + (odd ? 2 * (u0 + u) + sg - R : (u0 + u - R) * s);
+          if ((u & 3) == rl && row_ok && u0 + u < cnt && abs(dx) <= a.lim && x0 + dx >= 0 && x0 + dx + B <= a.W) {
             const uint64_t key = make_key(sad[u], dx, dy);
             best = key < best ? key : best;
           }
@@ -262,33 +319,37 @@ __global__ void __launch_bounds__(NW * 32) me_c2f_kernel(const GenericArgs a, co
       }
       if ((lane & 7) == 0 && best != kInvalidKey) atomicMin(&sbest[mb], (unsigned long long)best);
     } else {
-      // items (candidate row v, columns u0 .. u0 + 8) of the warp's block, over its WPB warps.
-      // 64-pixel blocks: where the stage's last round would hold only a few whole items
-      // (3 x their number <= WPB), those items run as three 3-column slices each instead,
-      // all in one round (a slice costs about 37 % of a whole item)
+      // items (set sg, candidate row v, columns u0 .. u0 + 8) of the warp's block, over its WPB
+      // warps.  64-pixel blocks: where an even-step stage's last round would hold only a few
+      // whole items (3 x their number <= WPB), those items run as three 3-column slices each
+      // instead, all in one round (a slice costs about 37 % of a whole item)
       if (valid) {
         const int wi = warp - mb * WPB, pi = PAIRED ? wi % NPAIR : wi;
-        const int nitems = n * nchunk;
+        const int nitems = nset * n * nchunk;
         const int full = SLICE ? nitems / WPB * WPB : nitems;
-        const bool sliced = SLICE && nitems > full && 3 * (nitems - full) <= WPB;
+        const bool sliced = SLICE && !odd && nitems > full && 3 * (nitems - full) <= WPB;
         const int nwork = sliced ? full + 3 * (nitems - full) : nitems;
         int parity = 0;
         for (int it = pi; it < nwork; it += (PAIRED ? NPAIR : WPB), parity ^= 1) {
           const bool sl = sliced && it >= full;
           const int ti = sl ? full + (it - full) / 3 : it;  // the whole item
-          const int v = ti / nchunk, u0 = (ti - v * nchunk) * kUC + (sl ? 3 * ((it - full) % 3) : 0);
+          const int sg = ODD ? ti / (n * nchunk) : 0, rem = ti - sg * n * nchunk;
+          const int v = rem / nchunk, u0 = (rem - v * nchunk) * kUC + (sl ? 3 * ((it - full) % 3) : 0);
           const int nc = sl ? 3 : kUC;
+          const uint32_t* wsrc = odd ? win + (mb * 2 + sg) * L.SSZ : win;
+          const int wp = odd ? L.SP : L.P;
+          const int row = (odd ? 0 : r0) + v * s + rl, wb = (odd ? 0 : w0) + u0 * hs;
           uint32_t sad[kUC];
           uint32_t mine = 0;
           if (sl) {
-            c2f_item_hs<KR, RS, BW, 3>(hs, win, L.P, r0 + v * s + rl, w0 + u0 * hs, cr, csum, sad);
+            c2f_item_hs<KR, RS, BW, 3>(hs, wsrc, wp, row, wb, cr, csum, sad);
 #pragma unroll
             for (int u = 0; u < 3; ++u) {
               const uint32_t tot = __reduce_add_sync(0xffffffffu, sad[u]);
               if (lane == u) mine = tot;
             }
           } else {
-            c2f_item_hs<KR, RS, BW>(hs, win, L.P, r0 + v * s + rl, w0 + u0 * hs, cr, csum, sad);
+            c2f_item_hs<KR, RS, BW>(hs, wsrc, wp, row, wb, cr, csum, sad);
 #pragma unroll
             for (int u = 0; u < kUC; ++u) {
               const uint32_t tot = __reduce_add_sync(0xffffffffu, sad[u]);
@@ -303,9 +364,10 @@ __global__ void __launch_bounds__(NW * 32) me_c2f_kernel(const GenericArgs a, co
             if (hb == 1) continue;
             mine += xsum[pi][parity][lane & 15];
           }
-          // lane u: candidate column u0 + u
-          const int dx = scx[mb] + (u0 + lane - R) * s, dy = scy[mb] + (v - R) * s;
-          if (lane < nc && u0 + lane < n && abs(dx) <= a.lim && abs(dy) <= a.lim && x0 + dx >= 0 &&
+          // lane u: candidate column u0 + u of the set
+          const int dx = scx[mb] + (odd ? 2 * (u0 + lane) + sg - R : (u0 + lane - R) * s);
+          const int dy = scy[mb] + (v - R) * s, cnt = odd ? ncol - sg : n;
+          if (lane < nc && u0 + lane < cnt && abs(dx) <= a.lim && abs(dy) <= a.lim && x0 + dx >= 0 &&
               x0 + dx + B <= a.W && y0 + dy >= 0 && y0 + dy + B <= a.H) {
             const uint64_t key = make_key(mine, dx, dy);
             best = key < best ? key : best;
@@ -341,24 +403,47 @@ __global__ void __launch_bounds__(NW * 32) me_c2f_kernel(const GenericArgs a, co
   }
 }
 
+template <int B, int T, int NW, bool PAIRED, bool ODD>
+cudaError_t c2f_launch_k(const GenericArgs& a, int batch, const C2FLevel& L, cudaStream_t st) {
+  cudaError_t e =
+      cudaFuncSetAttribute(me_c2f_kernel<B, T, NW, PAIRED, ODD>, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem);
+  if (e != cudaSuccess) return e;
+  me_c2f_kernel<B, T, NW, PAIRED, ODD>
+      <<<dim3((a.w + T - 1) / T, (a.h + T - 1) / T, batch), NW * 32, L.smem, st>>>(a, L);
+  return cudaGetLastError();
+}
+
+// Every level runs the same stages, so only a step-1 last stage yields odd
+// centres: such pyramids take the ODD kernels.
 template <int B, int T, int NW, bool PAIRED = false>
 cudaError_t c2f_launch(const GenericArgs& a, int batch, const C2FLevel& L, cudaStream_t st) {
-  cudaError_t e =
-      cudaFuncSetAttribute(me_c2f_kernel<B, T, NW, PAIRED>, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem);
-  if (e != cudaSuccess) return e;
-  me_c2f_kernel<B, T, NW, PAIRED><<<dim3((a.w + T - 1) / T, (a.h + T - 1) / T, batch), NW * 32, L.smem, st>>>(a, L);
-  return cudaGetLastError();
+  return (a.S[a.nst - 1] & 1) ? c2f_launch_k<B, T, NW, PAIRED, true>(a, batch, L, st)
+                              : c2f_launch_k<B, T, NW, PAIRED, false>(a, batch, L, st);
 }
 
 bool plan(const GenericArgs& a, int T, C2FLevel* L) {
   *L = C2FLevel{};
-  for (int k = 0; k < a.nst; ++k) L->reach += a.R[k] * a.S[k];
+  const int last = a.nst - 1;
+  for (int k = 0; k < a.nst; ++k)
+    if (!(a.S[k] & 1)) L->reach += a.R[k] * a.S[k];
   L->rows = T * a.B + 2 * L->reach;
   L->WWu = (T * a.B + 2 * L->reach) / 2;
   L->P = L->WWu | 1;  // odd pitch
   // the window, then 64 words of padding (an item's unused columns read up to
   // 32 words past the window)
-  const long long bytes = ((long long)L->rows * L->P + 64) * 4;
+  long long words = (long long)L->rows * L->P + 64;
+  if (a.S[last] & 1) {
+    // an odd-step last stage: two half windows per block, each padded like the window,
+    // in the same space
+    const int R = a.R[last];
+    L->SR = a.B + 2 * R;
+    L->SWW = a.B / 2 + R;
+    L->SP = L->SWW | 1;
+    L->SSZ = L->SR * L->SP + 64;
+    const long long halves = (long long)T * T * 2 * L->SSZ;
+    words = halves > words ? halves : words;
+  }
+  const long long bytes = words * 4;
   if (bytes > 220 * 1024) return false;
   L->smem = (int)bytes;
   return true;
@@ -366,9 +451,10 @@ bool plan(const GenericArgs& a, int T, C2FLevel* L) {
 
 }  // namespace
 
-// The packed C2F level kernel serves EVEN-phase levels of whole 8-, 16-, 32-
-// or 64-pixel blocks with steps 2, 4 or 8, 16-byte aligned frames, and a union
-// window that fits shared memory; returns cudaErrorNotSupported otherwise
+// The packed C2F level kernel serves levels of whole 8-, 16-, 32- or 64-pixel
+// blocks with steps 2, 4 or 8 (and step 1 in the last stage: the RAW phase's
+// fine stage), any start centre, 16-byte aligned frames, and a union window
+// that fits shared memory; returns cudaErrorNotSupported otherwise
 // (the caller then runs the generic kernel).  8-, 16- and 32-pixel levels
 // take 2 x 2 tiles where the tile's blocks share a start centre (level 0, or
 // a parent block that is a multiple of twice their size); without one, 32-pixel
@@ -380,7 +466,7 @@ cudaError_t launch_c2f_level(const GenericArgs& a, int batch, cudaStream_t st) {
       a.ref_bs % 8 || a.cur_bs % 8)
     return cudaErrorNotSupported;
   for (int k = 0; k < a.nst; ++k)
-    if (a.S[k] != 2 && a.S[k] != 4 && a.S[k] != 8) return cudaErrorNotSupported;
+    if (a.S[k] != 2 && a.S[k] != 4 && a.S[k] != 8 && !(a.S[k] == 1 && k == a.nst - 1)) return cudaErrorNotSupported;
   const bool shared_centre = a.center_mode == 0 || (a.parent_B % (2 * a.B) == 0);
   C2FLevel L{};
   if (a.B <= 16) {

@@ -1,5 +1,5 @@
-"""The paper's coarse-to-fine presets in the EVEN phase on the GPU vs the
-oracle, bit for bit: levels of whole 8- to 64-pixel blocks run the packed
+"""The paper's coarse-to-fine presets in the EVEN and RAW phases on the GPU vs
+the oracle, bit for bit: levels of whole 8- to 64-pixel blocks run the packed
 C2F kernel (me_c2f.cu); levels without a whole-block grid or a shared start
 centre, and unaligned frames, the generic one."""
 import numpy as np
@@ -156,4 +156,46 @@ def test_children_without_a_shared_centre(handle, levels):
                              phase=bm.PHASE_EVEN, c2f=bm.C2FSetting(levels, stages))
     torch.cuda.synchronize()
     want, _ = oracle.me_c2f(f0, f1, levels=list(levels), stages=list(stages), even=True)
+    check(out[0], want)
+
+
+@pytest.mark.parametrize("mode", ["standard", "mode1", "mode2", "mode3", "mode4"])
+def test_presets_raw_batched(handle, mode):
+    """RAW phase: steps 8 and 4, then step 1 (both column parities), and start
+    centres of either parity below the first level."""
+    H, W = 512, 768
+    frames = synth.pan_clip(67, H, W, n_frames=3, rect_size=(16, 96))
+    d = torch.from_numpy(frames).cuda()
+    setting = bm.C2F_PRESETS[mode]
+    out = handle.estimate_ex(d, d[1:], mode=bm.MODE_C2F, phase=bm.PHASE_RAW, c2f=setting, batch=2,
+                             ref_batch_stride=H * W, cur_batch_stride=H * W)
+    torch.cuda.synchronize()
+    for t in range(2):
+        want, _ = oracle.me_c2f(frames[t], frames[t + 1], levels=list(setting.levels),
+                                stages=[tuple(s) for s in setting.stages], even=False)
+        check(out[t], want)
+
+
+def test_raw_large_motion_near_borders(handle):
+    """Odd global motion in RAW: the odd-parity windows reach past every frame edge."""
+    H, W = 256, 384
+    rng = np.random.default_rng(68)
+    base = synth.round_clip(synth.blob_texture_scene(rng, H + 128, W + 128))
+    f0 = np.ascontiguousarray(base[64:64 + H, 64:64 + W])
+    f1 = np.ascontiguousarray(base[64 - 37:64 - 37 + H, 64 + 51:64 + 51 + W])
+    out = handle.estimate_ex(torch.from_numpy(f0).cuda(), torch.from_numpy(f1).cuda(), mode=bm.MODE_C2F,
+                             phase=bm.PHASE_RAW)
+    torch.cuda.synchronize()
+    want, _ = oracle.me_c2f(f0, f1, even=False)
+    check(out[0], want)
+
+
+def test_raw_standard_1080p_pair(handle):
+    wl = synth.WORKLOADS["1080p"]
+    H, W = wl["H"], wl["W"]
+    f0, f1 = synth.pan_clip(wl["seed"], H, W, n_frames=2)
+    out = handle.estimate_ex(torch.from_numpy(f0).cuda(), torch.from_numpy(f1).cuda(), mode=bm.MODE_C2F,
+                             phase=bm.PHASE_RAW)
+    torch.cuda.synchronize()
+    want, _ = oracle.me_c2f(f0, f1, even=False)
     check(out[0], want)
