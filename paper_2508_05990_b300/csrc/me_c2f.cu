@@ -279,6 +279,7 @@ __global__ void __launch_bounds__(NW * 32) me_c2f_kernel(const GenericArgs a, co
     const int nset = odd ? 2 : 1;
     const int ncol = odd ? R + 1 : n;         // columns of set 0 (set 1: R)
     const int nchunk = (ncol + kUC - 1) / kUC;
+    const bool narrow = ncol <= 3;            // 3-column items (e.g. the fine stage, R = 1 or 2)
     // the block's stage window: window row of block row 0 and word of candidate column 0
     const int r0 = L.reach - R * s + (scy[mb] - cy0) + (mb / T) * B;
     const int w0 = ((L.reach - R * s + (scx[mb] - cx0)) >> 1) + (mb % T) * BW;
@@ -293,19 +294,29 @@ __global__ void __launch_bounds__(NW * 32) me_c2f_kernel(const GenericArgs a, co
         const int v = 2 * vp + svv, ve = min(v, n - 1);
         const uint32_t* wsrc = odd ? win + (mb * 2 + sg) * L.SSZ : win;
         uint32_t sad[kUC];
-        c2f_item_hs<KR, RS, BW>(hs, wsrc, odd ? L.SP : L.P, (odd ? 0 : r0) + ve * s + rl, (odd ? 0 : w0) + u0 * hs,
-                                cr, csum, sad);
+        const int row = (odd ? 0 : r0) + ve * s + rl, wb = (odd ? 0 : w0) + u0 * hs;
+        if (narrow) {
+          c2f_item_hs<KR, RS, BW, 3>(hs, wsrc, odd ? L.SP : L.P, row, wb, cr, csum, sad);
 #pragma unroll
-        for (int u = 0; u < kUC; ++u) {
-          sad[u] += __shfl_xor_sync(0xffffffffu, sad[u], 2);
-          sad[u] += __shfl_xor_sync(0xffffffffu, sad[u], 1);
+          for (int u = 0; u < 3; ++u) {
+            sad[u] += __shfl_xor_sync(0xffffffffu, sad[u], 2);
+            sad[u] += __shfl_xor_sync(0xffffffffu, sad[u], 1);
+          }
+        } else {
+          c2f_item_hs<KR, RS, BW>(hs, wsrc, odd ? L.SP : L.P, row, wb, cr, csum, sad);
+#pragma unroll
+          for (int u = 0; u < kUC; ++u) {
+            sad[u] += __shfl_xor_sync(0xffffffffu, sad[u], 2);
+            sad[u] += __shfl_xor_sync(0xffffffffu, sad[u], 1);
+          }
         }
         const int dy = scy[mb] + (v - R) * s, cnt = odd ? ncol - sg : n;
         const bool row_ok = v < n && valid && abs(dy) <= a.lim && y0 + dy >= 0 && y0 + dy + B <= a.H;
 #pragma unroll
         for (int u = 0; u < kUC; ++u) {
           const int dx = scx[mb] + (odd ? 2 * (u0 + u) + sg - R : (u0 + u - R) * s);
-          if ((u & 3) == rl && row_ok && u0 + u < cnt && abs(dx) <= a.lim && x0 + dx >= 0 && x0 + dx + B <= a.W) {
+          if ((u & 3) == rl && row_ok && u0 + u < cnt && (u < 3 || !narrow) && abs(dx) <= a.lim && x0 + dx >= 0 &&
+              x0 + dx + B <= a.W) {
             const uint64_t key = make_key(sad[u], dx, dy);
             best = key < best ? key : best;
           }
@@ -327,7 +338,7 @@ __global__ void __launch_bounds__(NW * 32) me_c2f_kernel(const GenericArgs a, co
         const int wi = warp - mb * WPB, pi = PAIRED ? wi % NPAIR : wi;
         const int nitems = nset * n * nchunk;
         const int full = SLICE ? nitems / WPB * WPB : nitems;
-        const bool sliced = SLICE && !odd && nitems > full && 3 * (nitems - full) <= WPB;
+        const bool sliced = SLICE && !odd && !narrow && nitems > full && 3 * (nitems - full) <= WPB;
         const int nwork = sliced ? full + 3 * (nitems - full) : nitems;
         int parity = 0;
         for (int it = pi; it < nwork; it += (PAIRED ? NPAIR : WPB), parity ^= 1) {
@@ -335,13 +346,14 @@ __global__ void __launch_bounds__(NW * 32) me_c2f_kernel(const GenericArgs a, co
           const int ti = sl ? full + (it - full) / 3 : it;  // the whole item
           const int sg = ODD ? ti / (n * nchunk) : 0, rem = ti - sg * n * nchunk;
           const int v = rem / nchunk, u0 = (rem - v * nchunk) * kUC + (sl ? 3 * ((it - full) % 3) : 0);
-          const int nc = sl ? 3 : kUC;
+          const bool n3 = sl || narrow;  // a 3-column item
+          const int nc = n3 ? 3 : kUC;
           const uint32_t* wsrc = odd ? win + (mb * 2 + sg) * L.SSZ : win;
           const int wp = odd ? L.SP : L.P;
           const int row = (odd ? 0 : r0) + v * s + rl, wb = (odd ? 0 : w0) + u0 * hs;
           uint32_t sad[kUC];
           uint32_t mine = 0;
-          if (sl) {
+          if (n3) {
             c2f_item_hs<KR, RS, BW, 3>(hs, wsrc, wp, row, wb, cr, csum, sad);
 #pragma unroll
             for (int u = 0; u < 3; ++u) {
