@@ -109,8 +109,10 @@ bayer_status_t check_frames(const void* ref, const void* cur, int W, int H, int 
   return BAYER_OK;
 }
 
-// Full search dispatch: the specialised 16x16 EVEN kernel where it applies,
-// the generic stage kernel otherwise.
+// Full search dispatch: the specialised 16x16 EVEN kernel where it applies;
+// else the packed C2F level kernel running the search as one stage (step 2
+// for EVEN, 1 for RAW, centre 0: the same candidates, limit and key); the
+// generic stage kernel where neither applies.
 bayer_status_t full_search(const uint16_t* ref, const uint16_t* cur, int W, int H, int pitch, long long rbs,
                            long long cbs, int batch, int block, int range, int phase, bayer_mv_t* out,
                            cudaStream_t st) {
@@ -136,7 +138,9 @@ bayer_status_t full_search(const uint16_t* ref, const uint16_t* cur, int W, int 
   a.lim = range;
   a.center_mode = 0;
   a.out = out;
-  return cuda_status(bme::launch_generic(a, batch, st));
+  cudaError_t e = bme::launch_c2f_level(a, batch, st);
+  if (e == cudaErrorNotSupported) e = bme::launch_generic(a, batch, st);
+  return cuda_status(e);
 }
 
 bool seeded16_fast(int block, int phase, int W, int H, int range) {

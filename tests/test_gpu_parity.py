@@ -283,3 +283,19 @@ def test_invalid_arguments_return_status(handle):
 def test_probe_alu(handle):
     pc, mhz, nsm = handle.probe_alu(0)
     assert 20 < pc < 140 and 500 < mhz < 2500 and nsm > 0
+
+
+@pytest.mark.parametrize("block,rng_px,phase", [(8, 32, bm.PHASE_EVEN), (32, 32, bm.PHASE_EVEN),
+                                                (64, 32, bm.PHASE_EVEN), (16, 32, bm.PHASE_RAW),
+                                                (64, 12, bm.PHASE_RAW)])
+def test_full_search_as_one_level(handle, block, rng_px, phase):
+    """Exhaustive searches the 16-pixel strip kernel does not take run as a
+    one-stage pyramid level on the packed C2F kernel (RAW: both column parities)."""
+    H, W = 256, 384
+    frames = synth.pan_clip(45, H, W, n_frames=3)
+    d = dev(frames)
+    out = handle.estimate_ex(d, d[1:], mode=bm.MODE_FULL, phase=phase, block=block, search_range=rng_px, batch=2,
+                             ref_batch_stride=H * W, cur_batch_stride=H * W)
+    for t in range(2):
+        ref_field, _ = oracle.me_full(frames[t], frames[t + 1], block, rng_px, even=phase == bm.PHASE_EVEN)
+        assert_fields_equal(out[t], ref_field)
