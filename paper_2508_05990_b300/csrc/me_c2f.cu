@@ -268,11 +268,12 @@ __global__ void __launch_bounds__(NW * 32) me_c2f_kernel(const GenericArgs a, co
     // union window, which no later stage reads.
     const bool odd = ODD && (s & 1);
     if (odd) {
+      // a short load batch: the lanes' current rows are live here
       for (int b = 0; b < NB; ++b)
         for (int sg = 0; sg < 2; ++sg)
-          // a short batch: the lanes' current rows are live here
-          stage_window<NT, 2, true>(win + (b * 2 + sg) * L.SSZ, L.SP, L.SWW, L.SR, tx0 + (b % T) * B + scx[b] - R + sg,
-                           ty0 + (b / T) * B + scy[b] - R, ref, a.W, a.H, a.pitch);
+          stage_window<NT, 2, true>(win + (b * 2 + sg) * L.SSZ, L.SP, L.SWW, L.SR,
+                                    tx0 + (b % T) * B + scx[b] - R + sg, ty0 + (b / T) * B + scy[b] - R, ref, a.W,
+                                    a.H, a.pitch);
       __syncthreads();
     }
     const int hs = odd ? 1 : s >> 1;          // words between an item's columns
