@@ -199,3 +199,30 @@ def test_raw_standard_1080p_pair(handle):
     torch.cuda.synchronize()
     want, _ = oracle.me_c2f(f0, f1, even=False)
     check(out[0], want)
+
+
+def test_raw_mode4_partial_small_tiles(handle):
+    """RAW mode 4 at 496 x 816: partial 2 x 2 tiles at the 16-pixel level, odd
+    start centres from every RAW parent level, step-1 windows at both parities."""
+    H, W = 496, 816
+    f0, f1 = synth.pan_clip(69, H, W, n_frames=2, rect_size=(8, 48))
+    setting = bm.C2F_PRESETS["mode4"]
+    out = handle.estimate_ex(torch.from_numpy(f0).cuda(), torch.from_numpy(f1).cuda(), mode=bm.MODE_C2F,
+                             phase=bm.PHASE_RAW, c2f=setting)
+    torch.cuda.synchronize()
+    want, _ = oracle.me_c2f(f0, f1, levels=list(setting.levels), stages=[tuple(s) for s in setting.stages],
+                            even=False)
+    check(out[0], want)
+
+
+@pytest.mark.parametrize("block,rng_px,even", [(8, 13, False), (32, 14, True), (64, 7, False), (16, 10, True)])
+def test_full_search_other_ranges(handle, block, rng_px, even):
+    """Exhaustive searches through the one-stage level path: odd RAW ranges, and
+    EVEN ranges the 16-pixel strip kernel does not take (R = range / 2 steps)."""
+    H, W = 192, 320
+    f0, f1 = synth.pan_clip(70, H, W, n_frames=2)
+    out = handle.estimate_ex(torch.from_numpy(f0).cuda(), torch.from_numpy(f1).cuda(), mode=bm.MODE_FULL,
+                             phase=bm.PHASE_EVEN if even else bm.PHASE_RAW, block=block, search_range=rng_px)
+    torch.cuda.synchronize()
+    want, _ = oracle.me_full(f0, f1, block, rng_px, even=even)
+    check(out[0], want)
