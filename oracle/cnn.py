@@ -169,6 +169,12 @@ def berhu_grad(e, c=BERHU_C):
 
 def loss_and_grad(theta, ref, cur, label_dx, label_dy, search_range: int, act_round=None, neg_weight=1.0):
     """Mean loss over blocks and its gradient w.r.t. theta (float64)."""
+    loss, cache, dz = loss_and_dz(theta, ref, cur, label_dx, label_dy, search_range, act_round, neg_weight)
+    return loss, backward(cache, dz)
+
+
+def loss_and_dz(theta, ref, cur, label_dx, label_dy, search_range: int, act_round=None, neg_weight=1.0):
+    """Mean loss over blocks, the forward cache and dL/dz for ``backward``."""
     dx, dy, conf, cache = forward(theta, ref, cur, search_range, act_round)
     n = dx.size
     ex, ey = dx - label_dx, dy - label_dy
@@ -182,7 +188,7 @@ def loss_and_grad(theta, ref, cur, label_dx, label_dy, search_range: int, act_ro
     dz[0] = berhu_grad(ex) * R * (1 - np.tanh(z[0]) ** 2) / n
     dz[1] = berhu_grad(ey) * R * (1 - np.tanh(z[1]) ** 2) / n
     dz[2] = (conf * (t + neg_weight * (1 - t)) - t) / n
-    return loss, backward(cache, dz)
+    return loss, cache, dz
 
 
 def backward(cache, dz):

@@ -5,19 +5,27 @@ The oracle (oracle/cnn.py) evaluates the same bf16 weights in float64, either
 keeping activations exact (act_round=None) or rounding them to bfloat16 at the
 points the network's definition stores them (act_round="bf16").
 
-Tolerances (normwise relative):
-* forward outputs vs the exact float64 oracle: 2e-2 (the BF16 tolerance);
-* gradient vs the bf16-activation oracle: 1e-4 (only float32 accumulation
-  order differs; measured 1.3e-7);
-* gradient vs the exact float64 oracle: 5e-2 -- rounding the activations to
-  bfloat16 (relative 2^-9 each) moves the loss surface itself, and the
-  gradient of four stacked layers moves with it (measured 3.2 %, identical for
-  the GPU and for the bf16-activation oracle).
+Forward, per block (tests/fp_bounds.py states the measure): with z the exact
+head logits and m_z = |b_h| + sum |w_h| |x4| the absolute sum of their terms,
+every output (dx, dy, conf) must come from logits within 2e-2 m_z of the exact
+oracle's and within 2^-8 m_z of the bfloat16-rounded oracle's (tanh and the
+sigmoid are monotone, so this is an interval test on the outputs).
+
+Gradient, per parameter: within 2^-8 M (+ a floor of 2^-8 * 1e-3 * max M) of
+the bf16-activation oracle, M being the sum of the absolute values of every
+term of the parameter's chain-rule expansion; the two differ only in the
+order of the float32 sums (and where that flips the bfloat16 rounding or the
+ReLU mask of a value at a boundary).  Against the exact float64 oracle the
+gradient is compared normwise (5e-2): rounding the activations to bfloat16
+moves the loss surface itself, ReLU masks included, so no per-parameter bound
+against the exact gradient exists (measured: 3.2 %, identical for the GPU and
+for the bf16-activation oracle).
 Integer outputs (MV fields) are compared bit for bit.
 """
 import numpy as np
 import pytest
 
+import fp_bounds as fb
 import oracle
 from oracle import cnn
 from paper_2508_05990_b300 import bayer_me as bm
@@ -25,8 +33,6 @@ from paper_2508_05990_b300 import synth
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
-
-TOL = 2e-2
 
 
 @pytest.fixture(scope="module")
@@ -56,16 +62,23 @@ def rel(a, b):
     return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-30))
 
 
+def check_forward(prop, conf, theta, ref, cur, R=32):
+    """Every block's outputs against both oracles (see the module docstring)."""
+    z, mz, _ = fb.cnn_logits(theta, ref, cur, R)
+    zb, _, _ = fb.cnn_logits(theta, ref, cur, R, act_round="bf16")
+    ok = fb.outputs_within(prop, conf, z, fb.TOL_BF16 * mz, R)
+    assert ok.all(), ("vs exact", np.argwhere(~ok)[:5])
+    ok = fb.outputs_within(prop, conf, zb, fb.TOL_BF16_SAME_ROUNDING * mz, R)
+    assert ok.all(), ("vs bf16-rounded", np.argwhere(~ok)[:5])
+
+
 @pytest.mark.parametrize("shape", [(128, 192), (1088, 1920)])
 def test_cnn_forward_matches_oracle(handle, shape):
     H, W = shape
     ref, cur = synth.pan_clip(90, H, W, n_frames=2, rect_size=(16, 64))
     _, wbf, theta = weights(3)
     prop, conf = handle.cnn_forward(dev(ref), dev(cur), wbf, 32)
-    dx, dy, cf, _ = cnn.forward(theta, ref, cur, 32)
-    p = prop[0].cpu().numpy()
-    assert rel(p[..., 0], dx) < TOL and rel(p[..., 1], dy) < TOL
-    assert rel(conf[0].cpu().numpy(), cf) < TOL
+    check_forward(prop[0].cpu().numpy(), conf[0].cpu().numpy(), theta, ref, cur)
 
 
 def test_cnn_forward_batched_strides(handle):
@@ -75,9 +88,7 @@ def test_cnn_forward_batched_strides(handle):
     d = dev(frames)
     prop, conf = handle.cnn_forward(d, d[1:], wbf, 16, batch=3, ref_batch_stride=H * W, cur_batch_stride=H * W)
     for t in range(3):
-        dx, dy, cf, _ = cnn.forward(theta, frames[t], frames[t + 1], 16)
-        assert rel(prop[t, ..., 0].cpu().numpy(), dx) < TOL
-        assert rel(conf[t].cpu().numpy(), cf) < TOL
+        check_forward(prop[t].cpu().numpy(), conf[t].cpu().numpy(), theta, frames[t], frames[t + 1], 16)
 
 
 @pytest.mark.parametrize("neg_weight", [1.0, 8.0])
@@ -102,19 +113,17 @@ def test_cnn_loss_and_gradient_match_oracle(handle, neg_weight):
         losses.append(l)
         grads.append(gr)
     want_loss, want_grad = np.mean(losses), np.mean(grads, axis=0)
-    assert abs(float(loss.item()) - want_loss) <= TOL * abs(want_loss)
+    assert abs(float(loss.item()) - want_loss) <= fb.TOL_BF16 * abs(want_loss)
     assert rel(g, want_grad) < 5e-2
-    # the same network with its bfloat16 activation rounding modelled in the oracle
-    gb = np.mean([cnn.loss_and_grad(theta, frames[t], frames[t + 1], labels["dx"][t].astype(np.float64),
-                                    labels["dy"][t].astype(np.float64), 32, act_round="bf16",
-                                    neg_weight=neg_weight)[1] for t in range(2)],
-                 axis=0)
-    assert rel(g, gb) < 1e-4
-    for name, (kind, shape) in zip(["w1", "b1", "w2", "b2", "w3", "b3", "w4", "b4", "wh", "bh"], bm.CNN_SHAPES):
-        o = bm.CNN_OFFSETS[name]
-        n = int(np.prod(shape))
-        if np.linalg.norm(gb[o:o + n]) > 1e-6:
-            assert rel(g[o:o + n], gb[o:o + n]) < 1e-3, name
+    # per parameter against the same network with its bfloat16 activation rounding modelled
+    gb, Mb = zip(*[fb.cnn_grad_magnitudes(theta, frames[t], frames[t + 1], labels["dx"][t].astype(np.float64),
+                                          labels["dy"][t].astype(np.float64), 32, neg_weight=neg_weight,
+                                          act_round="bf16") for t in range(2)])
+    gb, Mb = np.mean(gb, axis=0), np.mean(Mb, axis=0)
+    t = fb.TOL_BF16_SAME_ROUNDING
+    bound = t * Mb + t * 1e-3 * Mb.max()
+    worst = int(np.argmax(np.abs(g - gb) - bound))
+    assert np.all(np.abs(g - gb) <= bound), (worst, g[worst], gb[worst], Mb[worst])
 
 
 def test_adamw_matches_formula(handle):
