@@ -333,8 +333,10 @@ bayer_status_t bayer_me_multi_stream(bayer_me_t h, const bayer_pair_t* pairs, in
  * real-time frame loop, where an allocation can synchronise the device and
  * stall every stream, or a host that commits all device memory to a fixed
  * budget at start-up and forbids later allocations.  It takes no handle (a
- * handle allocates its workspace) and runs the same search as
- * bayer_me_estimate_ex with mode BAYER_MODE_C2F, on the current device.
+ * handle allocates its workspace) and runs the same search, on the same
+ * kernels, as bayer_me_estimate_ex with mode BAYER_MODE_C2F.
+ *   Device: it launches on the CURRENT device; the caller makes the device
+ *     that holds ref, cur and mv_out current (cudaSetDevice) before the call.
  *   Scratch: the intermediate pyramid fields live in one static device array
  *     of BAYER_NOALLOC_SCRATCH_BYTES (1 MiB), which every GPU that loads the
  *     library holds until the process exits.  2 x the largest intermediate
@@ -342,7 +344,9 @@ bayer_status_t bayer_me_multi_stream(bayer_me_t h, const bayer_pair_t* pairs, in
  *     it; larger requests return BAYER_ERR_UNSUPPORTED and launch nothing.
  *   Set-up: the first call on a device looks the array's device address up
  *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *     before any stream capture.  With CUDA's lazy module loading, that first
+ *     call is also when the driver loads the kernels it launches, so make it
+ *     at start-up, where the driver may still take device memory.
  *   Sharing: all calls share the array, which keeps the last call's contents.
  *     Every intermediate field is written before it is read, so nothing needs
  *     clearing; calls whose work overlaps on the GPU (several streams or host

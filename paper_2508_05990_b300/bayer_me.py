@@ -131,6 +131,16 @@ def _ptr(t) -> ctypes.c_void_p:
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _check_out(out, numel: int, dtype, device, what: str) -> None:
+    """A caller-supplied output must be a contiguous tensor of the record (or
+    value) dtype on the inputs' device, with room for every element the kernel
+    writes: the kernels write numel elements from its first address."""
+    if out.dtype != dtype or not out.is_contiguous() or out.device != device or out.numel() < numel:
+        raise ValueError(f"{what}: out must be a contiguous {dtype} tensor on {device} with at least {numel} "
+                         f"elements (got {out.dtype}, {tuple(out.shape)}, contiguous={out.is_contiguous()}, "
+                         f"{out.device})")
+
+
 def grid_shape(H: int, W: int, block: int):
     return (H + block - 1) // block, (W + block - 1) // block
 
@@ -203,6 +213,7 @@ class Handle:
         h, w = grid_shape(H, W, block)
         if out is None:
             out = torch.empty((h, w, 2), dtype=torch.int32, device=ref.device)
+        _check_out(out, h * w * 2, torch.int32, ref.device, "estimate")
         _check(self._lib.bayer_me_estimate(self._h, _ptr(ref), _ptr(cur), W, H, block, search_range, _ptr(out),
                                            _stream(stream)), "bayer_me_estimate")
         return out
@@ -237,6 +248,7 @@ class Handle:
         h, w = grid_shape(H, W, out_block)
         if out is None:
             out = torch.empty((batch, h, w, 2), dtype=torch.int32, device=ref.device)
+        _check_out(out, batch * h * w * 2, torch.int32, ref.device, "estimate_ex")
         _check(self._lib.bayer_me_estimate_ex(self._h, _ptr(ref), _ptr(cur), W, H, pitch, ctypes.byref(p),
                                               _ptr(prop_dxdy), _ptr(conf), _ptr(out), _ptr(fallback),
                                               _stream(stream)), "bayer_me_estimate_ex")
@@ -329,6 +341,7 @@ class Handle:
         H, W = ref.shape[-2:]
         if out is None:
             out = torch.empty((batch, H // 16, W // 16, 2), dtype=torch.int32, device=ref.device)
+        _check_out(out, batch * (H // 16) * (W // 16) * 2, torch.int32, ref.device, "estimate_learned")
         _check(self._lib.bayer_me_estimate_learned(self._h, _ptr(ref), _ptr(cur), W, H, W, batch, ref_batch_stride,
                                                    cur_batch_stride, _ptr(w_bf16), search_range, float(conf_thresh),
                                                    _ptr(out), _ptr(fallback), _ptr(n_fallback), _stream(stream)),
@@ -395,9 +408,13 @@ def estimate_c2f_noalloc(ref, cur, c2f=None, phase=PHASE_EVEN, batch=1, ref_batc
     For callers that must not allocate after start-up.  ``out`` must be given
     by such callers (allocating it here would defeat the purpose); it is only
     created when omitted, for convenience in tests.  Calls that overlap on the
-    GPU share the scratch and must be serialised."""
+    GPU share the scratch and must be serialised.  The C entry point launches
+    on the current device, so this wrapper makes ``ref``'s device current for
+    the call; ``cur`` and ``out`` must be on that device too."""
     import torch
     lib = load()
+    if cur.device != ref.device:
+        raise ValueError("estimate_c2f_noalloc: ref and cur must be on the same device")
     if H is None or W is None:
         H, W = ref.shape[-2:]
     if pitch is None:
@@ -416,8 +433,10 @@ def estimate_c2f_noalloc(ref, cur, c2f=None, phase=PHASE_EVEN, batch=1, ref_batc
     h, w = grid_shape(H, W, c2f.levels[-1])
     if out is None:
         out = torch.empty((batch, h, w, 2), dtype=torch.int32, device=ref.device)
-    _check(lib.bayer_me_estimate_c2f_noalloc(_ptr(ref), _ptr(cur), W, H, pitch, ctypes.byref(p), _ptr(out),
-                                             _stream(stream)), "bayer_me_estimate_c2f_noalloc")
+    _check_out(out, batch * h * w * 2, torch.int32, ref.device, "estimate_c2f_noalloc")
+    with torch.cuda.device(ref.device):
+        _check(lib.bayer_me_estimate_c2f_noalloc(_ptr(ref), _ptr(cur), W, H, pitch, ctypes.byref(p), _ptr(out),
+                                                 _stream(stream)), "bayer_me_estimate_c2f_noalloc")
     return out
 
 

@@ -117,7 +117,11 @@ extern "C" bayer_status_t bayer_me_estimate_c2f_noalloc(const uint16_t* ref, con
     a.parent_h = parent ? (H + parent_B - 1) / parent_B : 0;
     a.parent_w = parent ? (W + parent_B - 1) / parent_B : 0;
     a.out = (l == p->n_levels - 1) ? mv_out : buf[l & 1];
-    e = bme::launch_generic(a, p->batch, st);
+    // the packed level kernel where it applies (it only sets a kernel
+    // attribute, no allocation), else the generic one: the same kernels, in
+    // the same order, as the handle path
+    e = bme::launch_c2f_level(a, p->batch, st);
+    if (e == cudaErrorNotSupported) e = bme::launch_generic(a, p->batch, st);
     if (e != cudaSuccess) return BAYER_ERR_CUDA;
     parent = a.out;
     parent_B = B;
