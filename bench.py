@@ -229,6 +229,66 @@ class ClockSampler:
                 "window": "timed region" if inside else "whole run"}
 
 
+class NvmlClockSampler:
+    """SM clock and clock-event (throttle) reasons read through NVML every
+    ~0.5 ms from a host thread, so that even a timed region of ~10 ms gets tens
+    of samples (nvidia-smi's loop samples every 20 ms at best).  Each sample is
+    (host time, SM MHz, max SM MHz, set of active reasons)."""
+    REASONS = (("hw_slowdown", "nvmlClocksEventReasonHwSlowdown"),
+               ("hw_thermal_slowdown", "nvmlClocksEventReasonHwThermalSlowdown"),
+               ("sw_thermal_slowdown", "nvmlClocksEventReasonSwThermalSlowdown"),
+               ("sw_power_cap", "nvmlClocksEventReasonSwPowerCap"))
+
+    def __init__(self, index: int, period_s: float = 5e-4):
+        self.index, self.period = index, period_s
+        self.samples, self.ok = [], False
+
+    def __enter__(self):
+        import threading
+        try:
+            import pynvml as nv
+            nv.nvmlInit()
+            self._nv = nv
+            self._h = nv.nvmlDeviceGetHandleByIndex(self.index)
+            self._max = float(nv.nvmlDeviceGetMaxClockInfo(self._h, nv.NVML_CLOCK_SM))
+            self._bits = [(n, getattr(nv, c)) for n, c in self.REASONS]
+            self.ok = True
+        except Exception:  # no NVML: the nvidia-smi sampler stands alone
+            return self
+        self._stop = threading.Event()
+        self._thr = threading.Thread(target=self._run, daemon=True)
+        self._thr.start()
+        return self
+
+    def _run(self):
+        nv, h = self._nv, self._h
+        while not self._stop.is_set():
+            try:
+                sm = float(nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM))
+                r = nv.nvmlDeviceGetCurrentClocksEventReasons(h)
+            except Exception:
+                break
+            self.samples.append((time.time(), sm, self._max, {n for n, b in self._bits if r & b}))
+            time.sleep(self.period)
+
+    def __exit__(self, *exc):
+        if self.ok:
+            self._stop.set()
+            self._thr.join(timeout=2)
+            try:
+                self._nv.nvmlShutdown()
+            except Exception:
+                pass
+
+    def summary(self, t0, t1):
+        use = [p for p in self.samples if t0 <= p[0] <= t1]
+        if not use:
+            return None
+        return {"sm_mhz": statistics.median(p[1] for p in use), "sm_max_mhz": max(p[2] for p in use),
+                "reasons": sorted(set().union(*(p[3] for p in use))), "samples": len(use),
+                "window": "timed region", "source": "NVML, ~0.5 ms apart"}
+
+
 def pcie_link(nbytes=256 << 20, reps=5):
     """Host <-> device copy bandwidth of this machine with pinned buffers: each
     direction alone and both at once (two streams), GB/s."""
@@ -261,16 +321,41 @@ def pcie_link(nbytes=256 << 20, reps=5):
             "bidirectional_gbs": round(2 * nbytes / bi / 1e9, 1)}
 
 
-def cpu_baseline_sample(frames, feats):
-    """Oracle (as it stands) on one of the 7 pairs: exhaustive search + bilinear warp."""
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def cpu_baseline_sample(frames, feats, repeats=3):
+    """The oracle as it stands on this host's cores: exhaustive search + bilinear
+    warp of one pair per step, a warm-up pair then ``repeats`` timed pairs, once
+    with every host thread and once with one thread."""
     import oracle
     oracle.build()
-    t0 = time.perf_counter()
-    field, _ = oracle.me_full(frames[0], frames[1], BLOCK, RANGE, even=True)
-    oracle.propagate(feats[0], field, BLOCK, STRIDE, interp=oracle.BILINEAR)
-    dt = time.perf_counter() - t0
-    return {"value": 1.0 / dt, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
-            "sample": "1 of the 7 pairs of the 1080p clip (full ME + bilinear propagation), all host threads"}
+    all_threads = oracle.get_threads()
+
+    def rate(threads):
+        oracle.set_threads(threads)
+        for k in range(repeats + 1):
+            if k == 1:
+                t0 = time.perf_counter()
+            field, _ = oracle.me_full(frames[k % PAIRS], frames[k % PAIRS + 1], BLOCK, RANGE, even=True)
+            oracle.propagate(feats[k % PAIRS], field, BLOCK, STRIDE, interp=oracle.BILINEAR)
+        return repeats / (time.perf_counter() - t0)
+
+    v_all = rate(all_threads)
+    v_one = rate(1)
+    oracle.set_threads(all_threads)
+    return {"value": round(v_all, 4), "unit": UNIT, "cores": all_threads, "kind": "oracle",
+            "value_1_thread": round(v_one, 4), "nproc": os.cpu_count(), "cpu_model": cpu_model(),
+            "sample": f"1080p clip, one pair (full +-32 ME + bilinear propagation) per step: a warm-up pair, then "
+                      f"{repeats} timed pairs, at all {all_threads} oracle threads (value) and at 1 thread"}
 
 
 def leg_multi_stream(h, clips, steps, warmup, peaks, pc_clk_sm, nsm, sm_mhz):
@@ -562,8 +647,8 @@ def run_ours(args):
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier(world)
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        time.sleep(0.5)  # let the sampler start
+    with ClockSampler(local) as clk, NvmlClockSampler(local) as nclk:
+        time.sleep(0.5)  # let the samplers start
         t_host0 = time.time()
         start.record(stream)
         for k in range(args.steps):
@@ -630,7 +715,13 @@ def run_ours(args):
     # pixel-candidates per pair) per clock per SM x SMs x SM clock under load; sad.u32 beside it
     pc_clk_sm, probe_mhz, nsm = h.probe_alu(3)
     sad_clk_sm = h.probe_alu(0)[0]
-    clocks = clk.summary(t_host0, t_host1)
+    clocks = nclk.summary(t_host0, t_host1)
+    smi = clk.summary(t_host0, t_host1)
+    if clocks is None:
+        clocks = smi
+    else:  # nvidia-smi's reasons too, for the timed region's few 20 ms samples
+        clocks["reasons"] = sorted(set(clocks["reasons"]) | set(r for r in smi["reasons"] if r != "unsampled"))
+        clocks["nvidia_smi_samples"] = smi["samples"]
     sm_mhz = clocks["sm_mhz"] or probe_mhz
     peaks = {}
     try:
@@ -683,6 +774,7 @@ def run_ours(args):
                        "parallelism": f"replicas x{world} (independent clips, no collective)"},
             "roofline": {"bound": "alu", "kernel": "me_full16_even_kernel<16>", "achieved": round(achieved, 1),
                          "peak": round(peak, 1), "unit": "G pixel-candidates/s", "frac": round(achieved / peak, 4),
+                         "clock_samples": clocks.get("samples"),
                          "peak_source": f"measured packed min.u16x2 + dp2a loop: {pc_clk_sm:.1f} pc/clk/SM x {nsm} "
                                         f"SMs x {sm_mhz:.0f} MHz (median SM clock under load); sad.u32 loop "
                                         f"{sad_clk_sm:.1f} pc/clk/SM",
@@ -704,13 +796,14 @@ def run_ours(args):
             "gpu": torch.cuda.get_device_name(local),
             "gpu_launches": gpu_launches,
             "clocks": clocks,
-            "learned_seeded": learned,
             "multi_stream": multi_stream,
             "precision_4k": refine_4k,
             "c2f": c2f,
         }
         if not args.no_cpu_baseline:
             result["cpu_baseline"] = cpu_baseline_sample(frames, feats)
+        # the metric's second half last, so that a reader keeping only the end of the line keeps it
+        result["learned_seeded"] = learned
     h.close()
     if world > 1:
         import torch.distributed as dist
