@@ -138,7 +138,7 @@ def test_cnn_tolerances_hold_for_the_bf16_oracle():
     assert (np.abs(zb - z) / mz).max() < fb.TOL_BF16 / 2
     prop = np.stack([gx, gy], -1)
     assert fb.outputs_within(prop, gc, z, fb.TOL_BF16 * mz, 32).all()
-    assert fb.outputs_within(prop, gc, zb, fb.TOL_BF16_SAME_ROUNDING * mz, 32).all()
+    assert fb.outputs_within(prop, gc, zb, fb.TOL_CNN_SAME_ROUNDING * mz, 32).all()
     # a proposal moved by 1 px where the network is confident fails
     i = np.unravel_index(np.argmin(mz[0]), mz[0].shape)
     bad = prop.copy()
@@ -147,4 +147,4 @@ def test_cnn_tolerances_hold_for_the_bf16_oracle():
     # a confidence moved by 0.02 fails the same-rounding check
     bad = gc.copy()
     bad[np.unravel_index(np.argmax(gc * (1 - gc)), gc.shape)] += 0.02
-    assert not fb.outputs_within(prop, bad, zb, fb.TOL_BF16_SAME_ROUNDING * mz, 32).all()
+    assert not fb.outputs_within(prop, bad, zb, fb.TOL_CNN_SAME_ROUNDING * mz, 32).all()
