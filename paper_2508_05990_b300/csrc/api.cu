@@ -109,16 +109,16 @@ bayer_status_t check_frames(const void* ref, const void* cur, int W, int H, int 
   return BAYER_OK;
 }
 
-// Full search dispatch: the specialised 16x16 EVEN kernel where it applies;
-// else the packed C2F level kernel running the search as one stage (step 2
-// for EVEN, 1 for RAW, centre 0: the same candidates, limit and key); the
-// generic stage kernel where neither applies.
+// Full search dispatch: the specialised 16x16 EVEN kernel where it applies
+// (W a multiple of 16; a last block row clipped by the frame height is served
+// by the same kernel); else the packed C2F level kernel running the search as
+// one stage (step 2 for EVEN, 1 for RAW, centre 0: the same candidates, limit
+// and key); the generic stage kernel where neither applies.
 bayer_status_t full_search(const uint16_t* ref, const uint16_t* cur, int W, int H, int pitch, long long rbs,
                            long long cbs, int batch, int block, int range, int phase, bayer_mv_t* out,
                            cudaStream_t st) {
   const int h = (H + block - 1) / block, w = (W + block - 1) / block;
-  if (phase == BAYER_PHASE_EVEN && block == 16 && (W % 16) == 0 && (H % 16) == 0 &&
-      bme::full16_even_supported(range)) {
+  if (phase == BAYER_PHASE_EVEN && block == 16 && (W % 16) == 0 && bme::full16_even_supported(range)) {
     return cuda_status(bme::launch_full16_even(ref, cur, W, H, pitch, rbs, cbs, batch, range, out, st));
   }
   GenericArgs a{};

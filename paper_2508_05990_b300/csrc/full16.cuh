@@ -66,24 +66,29 @@ struct Full16Acc {
   uint32_t accx, accc;
 };
 
-// cs[v * P + w] = sum of window rows 2v .. 2v + 15 at word column w, both
-// halves at once, for v = 0 .. 2R.  Called by NT threads (index tid) after the
-// window is staged; the caller synchronises before and after.  Two threads
-// per column, each running a 16-row sum down half of the offsets (the 32-bit
-// running sum is exact modulo 2^32, and its final halves each fit 16 bits).
+// cs[v * P + w] = sum of window rows 2v .. 2v + bh - 1 at word column w, both
+// halves at once, for v = 0 .. 2R; bh (even, 2..16) is the block height: 16,
+// or the rows left in a frame whose height is not a multiple of 16 (the last
+// block row is clipped to the frame, and its SAD covers only those rows).
+// Called by NT threads (index tid) after the window is staged; the caller
+// synchronises before and after.  Two threads per column, each running a
+// bh-row sum down half of the offsets (the 32-bit running sum is exact modulo
+// 2^32, and its final halves each fit 16 bits).
 template <int R, int P, int WW, int NT>
-__device__ __forceinline__ void window_colsums(const uint32_t* win, uint32_t* cs, int tid) {
+__device__ __forceinline__ void window_colsums(const uint32_t* win, uint32_t* cs, int tid, int bh = 16) {
   constexpr int NU = 2 * R + 1, HALF = (NU + 1) / 2;
+  const int tail = (bh - 2) * P;  // the rows entering a sum that moves down by two
   for (int e = tid; e < 2 * WW; e += NT) {
     const int part = e >= WW, w = e - part * WW;
     const int v0 = part ? HALF : 0, v1 = part ? NU : HALF;
     const uint32_t* col = win + w;
     uint32_t s = 0;
 #pragma unroll
-    for (int r = 0; r < 16; ++r) s += col[(2 * v0 + r) * P];
+    for (int r = 0; r < 16; ++r)
+      if (r < bh) s += col[(2 * v0 + r) * P];
     cs[v0 * P + w] = s;
     for (int v = v0 + 1; v < v1; ++v) {
-      s += col[(2 * v + 14) * P] + col[(2 * v + 15) * P];
+      s += col[2 * v * P + tail] + col[2 * v * P + tail + P];
       s -= col[(2 * v - 2) * P] + col[(2 * v - 1) * P];
       cs[v * P + w] = s;
     }
@@ -252,14 +257,16 @@ __device__ __forceinline__ void full16_finish(const uint32_t* csbase, const uint
 
 // The lane's best key (sad, |mv|_1, dy, dx) from its SADs; the warp minimum
 // of the returned keys is the block's MV.  (xb, yb): the block's top-left
-// pixel, for the validity of out-of-frame candidates.
+// pixel, bh its height (clipped to the frame), for the validity of
+// out-of-frame candidates.
 template <int R>
-__device__ __forceinline__ uint64_t full16_select(const Full16Acc<R>& A, int lane, int xb, int yb, int W, int H) {
+__device__ __forceinline__ uint64_t full16_select(const Full16Acc<R>& A, int lane, int xb, int yb, int W, int H,
+                                                  int bh = 16) {
   constexpr int NU = 2 * R + 1, REACH = 2 * R;
   const int v = lane < NU ? lane : NU - 1;
   const int dy = 2 * v - REACH;
   uint64_t best = kInvalidKey;
-  const bool interior = xb >= REACH && xb + 16 + REACH <= W && yb >= REACH && yb + 16 + REACH <= H;
+  const bool interior = xb >= REACH && xb + 16 + REACH <= W && yb >= REACH && yb + bh + REACH <= H;
   if (interior) {
     // Every candidate is valid.  Within a lane dy is fixed, so the tie-break
     // (|dx|+|dy|, dy, dx) orders the row by rank = 0 for dx = 0, then -2, +2,
@@ -275,7 +282,7 @@ __device__ __forceinline__ uint64_t full16_select(const Full16Acc<R>& A, int lan
     const int k = rank == 0 ? R : ((rank & 1u) ? R - (int)((rank + 1) >> 1) : R + (int)(rank >> 1));
     if (lane < NU) best = make_key(m >> 6, 2 * k - REACH, dy);
   } else {
-    const bool row_ok = lane < NU && yb + dy >= 0 && yb + dy + 16 <= H;
+    const bool row_ok = lane < NU && yb + dy >= 0 && yb + dy + bh <= H;
 #pragma unroll
     for (int k = 0; k < NU; ++k) {
       const int dx = 2 * k - REACH;
@@ -287,12 +294,12 @@ __device__ __forceinline__ uint64_t full16_select(const Full16Acc<R>& A, int lan
   if constexpr (NU == 33) {
     {
       const int dx = 2 * lane - REACH;
-      const bool ok = yb + 48 <= H && xb + dx >= 0 && xb + dx + 16 <= W;
+      const bool ok = yb + 32 + bh <= H && xb + dx >= 0 && xb + dx + 16 <= W;
       const uint64_t key = ok ? make_key(A.accx, dx, 32) : kInvalidKey;
       best = key < best ? key : best;
     }
     const uint32_t corner = __reduce_add_sync(0xffffffffu, A.accc);
-    if (lane == 0 && xb + 48 <= W && yb + 48 <= H) {
+    if (lane == 0 && xb + 48 <= W && yb + 32 + bh <= H) {
       const uint64_t key = make_key(corner, 32, 32);
       best = key < best ? key : best;
     }
@@ -302,15 +309,17 @@ __device__ __forceinline__ uint64_t full16_select(const Full16Acc<R>& A, int lan
 
 // Every candidate of one 16x16 block, by one warp: wbase / csbase are the
 // window and its column-sum table at the block's origin (pitch P words),
-// cbase its current words (pitch PC); returns the lane's best key.
+// cbase its current words (pitch PC); returns the lane's best key.  A block
+// clipped to bh < 16 rows has zero current rows below bh (min(win, 0) = 0
+// adds nothing) and a table of bh-row sums.
 template <int R, int P, int PC>
 __device__ __forceinline__ uint64_t full16_block(const uint32_t* wbase, const uint32_t* csbase, const uint32_t* cbase,
-                                                 int lane, int xb, int yb, int W, int H) {
+                                                 int lane, int xb, int yb, int W, int H, int bh = 16) {
   Full16Acc<R> A;
   Full16WinSums<R> unused;
   full16_accumulate<R, P, PC, false>(wbase, cbase, lane, A, unused);
   full16_finish<R, P, PC>(csbase, cbase, lane, A);
-  return full16_select<R>(A, lane, xb, yb, W, H);
+  return full16_select<R>(A, lane, xb, yb, W, H, bh);
 }
 
 // A word of two samples (gx, gx + 1) of row gy, out-of-frame samples 0.
@@ -325,7 +334,8 @@ __device__ __forceinline__ uint32_t pair_word(const uint16_t* __restrict__ f, in
 // Stage the window and current tile of the strip whose first block is at
 // (x0, y0) as packed pairs: 8 pixels per 16-byte load when vec_ok (x0 a
 // multiple of 8, W a multiple of 16, rows 16-byte aligned), all loads of a
-// thread in flight before the first store; out-of-frame samples are 0.
+// thread in flight before the first store; out-of-frame samples are 0 (also
+// the current rows below the frame of a clipped last block row).
 // Called by all NW*32 threads.
 template <int R, int NW>
 __device__ __forceinline__ void stage_strip(const uint16_t* __restrict__ ref, const uint16_t* __restrict__ cur, int W,
@@ -353,7 +363,8 @@ __device__ __forceinline__ void stage_strip(const uint16_t* __restrict__ ref, co
       } else if (e < NWCH + NTCH) {
         const int f = e - NWCH, ry = f / TCH, cx = f - ry * TCH;
         const int gx = x0 + 8 * cx;
-        if (gx < W) raw[i] = __ldg(reinterpret_cast<const uint4*>(cur + (long long)(y0 + ry) * pitch + gx));
+        if (gx < W && y0 + ry < H)
+          raw[i] = __ldg(reinterpret_cast<const uint4*>(cur + (long long)(y0 + ry) * pitch + gx));
       }
     }
 #pragma unroll

@@ -10,8 +10,10 @@
 namespace bme {
 
 // Exhaustive EVEN search, block 16, radius R = range/2 steps of 2, zero
-// centre, W and H multiples of 16.  Specialised for range 8, 16, 24, 32; the
-// caller checks full16_even_supported and otherwise uses the generic kernel.
+// centre, W a multiple of 16 (any even H >= 16: a last block row that the
+// frame clips is searched over its rows inside the frame).  Specialised for
+// range 8, 16, 24, 32; the caller checks full16_even_supported and otherwise
+// uses another kernel.
 bool full16_even_supported(int range);
 cudaError_t configure_full16();  // once per device: shared-memory opt-in
 cudaError_t launch_full16_even(const uint16_t* ref, const uint16_t* cur, int W, int H, int pitch, long long ref_bs,

@@ -4,6 +4,8 @@
 // SAD, argmin = MV) on packed pixel pairs, for whole blocks of 8, 16, 32 or 64
 // pixels: the EVEN phase (every step even) and the RAW phase's pyramids, whose
 // steps are even but the last (step 1) and whose start centres may be odd.
+// The frame width must be a multiple of the block size; a height that is not
+// clips the last block row, whose SAD covers the rows inside the frame.
 // Other levels take the generic kernel (me_generic.cu); both give the same MV
 // field bit for bit.
 //
@@ -138,13 +140,16 @@ __device__ __forceinline__ void stage_window(uint32_t* dst, int P, int WW, int r
 // row0 + RS k for the lane's k-th row, current words cr[k]) at candidate
 // columns u0 .. u0 + NC - 1: wb is the first window word of column u0, column
 // u starts H words further per step; csum = the lane's sum of current samples.
+// ws[k] weighs row k's window samples in the running sums: 0x0101 (lo + hi),
+// or 0 for a row below the frame in a block the frame clips, whose current
+// words are 0 too, so that the row adds nothing to the SAD.
 // All NC columns are always computed -- straight-line code, no per-pair
 // guards; columns past the stage's last (at most 8 H = 32 words past its
 // window: inside the row pitch, or past the last row inside the padding that
 // follows the window) are discarded by the caller.
 template <int KR, int RS, int BW, int H, int NC>
 __device__ __forceinline__ void c2f_item(const uint32_t* win, int P, int row0, int wb, const uint32_t (&cr)[KR][BW],
-                                         uint32_t csum, uint32_t* sad) {
+                                         const uint32_t (&ws)[KR], uint32_t csum, uint32_t* sad) {
   constexpr int NWW = (NC - 1) * H + BW;  // window words of a row the item touches
   uint32_t m2[NC];                        // 2 sum min per column
 #pragma unroll
@@ -165,7 +170,7 @@ __device__ __forceinline__ void c2f_item(const uint32_t* win, int P, int row0, i
         if (w == u * H + BW) sad[u] += S;
       }
       const uint32_t x = wrow[w];
-      S = dp2a_lo(x, 0x0101u, S);
+      S = dp2a_lo(x, ws[k], S);
 #pragma unroll
       for (int u = 0; u < NC; ++u) {
         const int j = w - u * H;
@@ -180,16 +185,23 @@ __device__ __forceinline__ void c2f_item(const uint32_t* win, int P, int row0, i
 
 template <int KR, int RS, int BW, int NC = kUC>
 __device__ __forceinline__ void c2f_item_hs(int hs, const uint32_t* win, int P, int row0, int wb,
-                                            const uint32_t (&cr)[KR][BW], uint32_t csum, uint32_t* sad) {
-  if (hs == 4) c2f_item<KR, RS, BW, 4, NC>(win, P, row0, wb, cr, csum, sad);
-  else if (hs == 2) c2f_item<KR, RS, BW, 2, NC>(win, P, row0, wb, cr, csum, sad);
-  else c2f_item<KR, RS, BW, 1, NC>(win, P, row0, wb, cr, csum, sad);
+                                            const uint32_t (&cr)[KR][BW], const uint32_t (&ws)[KR], uint32_t csum,
+                                            uint32_t* sad) {
+  if (hs == 4) c2f_item<KR, RS, BW, 4, NC>(win, P, row0, wb, cr, ws, csum, sad);
+  else if (hs == 2) c2f_item<KR, RS, BW, 2, NC>(win, P, row0, wb, cr, ws, csum, sad);
+  else c2f_item<KR, RS, BW, 1, NC>(win, P, row0, wb, cr, ws, csum, sad);
 }
 
 // ODD: the level's last stage may step by 1 and its start centres may be odd
-// (the RAW phase); without it every step and centre is even.
-template <int B, int T, int NW, bool PAIRED = false, bool ODD = false>
-__global__ void __launch_bounds__(NW * 32) me_c2f_kernel(const GenericArgs a, const C2FLevel L) {
+// (the RAW phase); without it every step and centre is even.  CLIP: the frame
+// height is not a multiple of B, so the last block row is clipped (frames
+// whose height is a multiple of B take the kernel without that logic).  The
+// clipping logic pushes the 8-warp 64-pixel level past 128 registers, which
+// would leave one CTA per SM (the shared memory allows two); its bound keeps
+// two (a few bytes spilled).  Every other form has no minimum (0).
+template <int B, int T, int NW, bool PAIRED = false, bool ODD = false, bool CLIP = false>
+__global__ void __launch_bounds__(NW * 32, (CLIP && B == 64 && !PAIRED) ? 2 : 0)
+    me_c2f_kernel(const GenericArgs a, const C2FLevel L) {
   constexpr int NB = T * T;  // blocks per tile
   constexpr int BW = B / 2;
   constexpr int NT = NW * 32;
@@ -235,16 +247,23 @@ __global__ void __launch_bounds__(NW * 32) me_c2f_kernel(const GenericArgs a, co
   const int bx = blockIdx.x * T + (mb % T), by = blockIdx.y * T + (mb / T);
   const bool valid = bx < a.w && by < a.h;
   const int x0 = tx0 + (mb % T) * B, y0 = ty0 + (mb / T) * B;  // block origin (pixels)
+  // a frame height that is not a multiple of B clips the last block row to bh
+  // rows; the lane's rows below the frame keep zero current words and weigh
+  // their window samples by 0, so they add nothing
+  const int bh = CLIP ? min(B, a.H - y0) : B;
   uint32_t cr[KR][BW];
+  uint32_t ws[KR];
   uint32_t csum = 0;  // the lane's sum of current samples
   {
     const uint16_t* curb = cur + (long long)y0 * a.pitch + x0;
 #pragma unroll
     for (int k = 0; k < KR; ++k) {
+      const bool in_frame = !CLIP || rl + RS * k < bh;
+      ws[k] = in_frame ? 0x0101u : 0u;
 #pragma unroll
       for (int q = 0; q < BW / 4; ++q) {
         uint4 t = make_uint4(0, 0, 0, 0);
-        if (valid) t = __ldg(reinterpret_cast<const uint4*>(curb + (long long)(rl + RS * k) * a.pitch) + q);
+        if (valid && in_frame) t = __ldg(reinterpret_cast<const uint4*>(curb + (long long)(rl + RS * k) * a.pitch) + q);
         cr[k][4 * q + 0] = t.x;
         cr[k][4 * q + 1] = t.y;
         cr[k][4 * q + 2] = t.z;
@@ -297,14 +316,14 @@ __global__ void __launch_bounds__(NW * 32) me_c2f_kernel(const GenericArgs a, co
         uint32_t sad[kUC];
         const int row = (odd ? 0 : r0) + ve * s + rl, wb = (odd ? 0 : w0) + u0 * hs;
         if (narrow) {
-          c2f_item_hs<KR, RS, BW, 3>(hs, wsrc, odd ? L.SP : L.P, row, wb, cr, csum, sad);
+          c2f_item_hs<KR, RS, BW, 3>(hs, wsrc, odd ? L.SP : L.P, row, wb, cr, ws, csum, sad);
 #pragma unroll
           for (int u = 0; u < 3; ++u) {
             sad[u] += __shfl_xor_sync(0xffffffffu, sad[u], 2);
             sad[u] += __shfl_xor_sync(0xffffffffu, sad[u], 1);
           }
         } else {
-          c2f_item_hs<KR, RS, BW>(hs, wsrc, odd ? L.SP : L.P, row, wb, cr, csum, sad);
+          c2f_item_hs<KR, RS, BW>(hs, wsrc, odd ? L.SP : L.P, row, wb, cr, ws, csum, sad);
 #pragma unroll
           for (int u = 0; u < kUC; ++u) {
             sad[u] += __shfl_xor_sync(0xffffffffu, sad[u], 2);
@@ -312,7 +331,7 @@ __global__ void __launch_bounds__(NW * 32) me_c2f_kernel(const GenericArgs a, co
           }
         }
         const int dy = scy[mb] + (v - R) * s, cnt = odd ? ncol - sg : n;
-        const bool row_ok = v < n && valid && abs(dy) <= a.lim && y0 + dy >= 0 && y0 + dy + B <= a.H;
+        const bool row_ok = v < n && valid && abs(dy) <= a.lim && y0 + dy >= 0 && y0 + dy + bh <= a.H;
 #pragma unroll
         for (int u = 0; u < kUC; ++u) {
           const int dx = scx[mb] + (odd ? 2 * (u0 + u) + sg - R : (u0 + u - R) * s);
@@ -355,14 +374,14 @@ __global__ void __launch_bounds__(NW * 32) me_c2f_kernel(const GenericArgs a, co
           uint32_t sad[kUC];
           uint32_t mine = 0;
           if (n3) {
-            c2f_item_hs<KR, RS, BW, 3>(hs, wsrc, wp, row, wb, cr, csum, sad);
+            c2f_item_hs<KR, RS, BW, 3>(hs, wsrc, wp, row, wb, cr, ws, csum, sad);
 #pragma unroll
             for (int u = 0; u < 3; ++u) {
               const uint32_t tot = __reduce_add_sync(0xffffffffu, sad[u]);
               if (lane == u) mine = tot;
             }
           } else {
-            c2f_item_hs<KR, RS, BW>(hs, wsrc, wp, row, wb, cr, csum, sad);
+            c2f_item_hs<KR, RS, BW>(hs, wsrc, wp, row, wb, cr, ws, csum, sad);
 #pragma unroll
             for (int u = 0; u < kUC; ++u) {
               const uint32_t tot = __reduce_add_sync(0xffffffffu, sad[u]);
@@ -381,7 +400,7 @@ __global__ void __launch_bounds__(NW * 32) me_c2f_kernel(const GenericArgs a, co
           const int dx = scx[mb] + (odd ? 2 * (u0 + lane) + sg - R : (u0 + lane - R) * s);
           const int dy = scy[mb] + (v - R) * s, cnt = odd ? ncol - sg : n;
           if (lane < nc && u0 + lane < cnt && abs(dx) <= a.lim && abs(dy) <= a.lim && x0 + dx >= 0 &&
-              x0 + dx + B <= a.W && y0 + dy >= 0 && y0 + dy + B <= a.H) {
+              x0 + dx + B <= a.W && y0 + dy >= 0 && y0 + dy + bh <= a.H) {
             const uint64_t key = make_key(mine, dx, dy);
             best = key < best ? key : best;
           }
@@ -416,14 +435,19 @@ __global__ void __launch_bounds__(NW * 32) me_c2f_kernel(const GenericArgs a, co
   }
 }
 
+template <int B, int T, int NW, bool PAIRED, bool ODD, bool CLIP>
+cudaError_t c2f_launch_kc(const GenericArgs& a, int batch, const C2FLevel& L, cudaStream_t st) {
+  auto kern = me_c2f_kernel<B, T, NW, PAIRED, ODD, CLIP>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem);
+  if (e != cudaSuccess) return e;
+  kern<<<dim3((a.w + T - 1) / T, (a.h + T - 1) / T, batch), NW * 32, L.smem, st>>>(a, L);
+  return cudaGetLastError();
+}
+
 template <int B, int T, int NW, bool PAIRED, bool ODD>
 cudaError_t c2f_launch_k(const GenericArgs& a, int batch, const C2FLevel& L, cudaStream_t st) {
-  cudaError_t e =
-      cudaFuncSetAttribute(me_c2f_kernel<B, T, NW, PAIRED, ODD>, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem);
-  if (e != cudaSuccess) return e;
-  me_c2f_kernel<B, T, NW, PAIRED, ODD>
-      <<<dim3((a.w + T - 1) / T, (a.h + T - 1) / T, batch), NW * 32, L.smem, st>>>(a, L);
-  return cudaGetLastError();
+  return (a.H % B) ? c2f_launch_kc<B, T, NW, PAIRED, ODD, true>(a, batch, L, st)
+                   : c2f_launch_kc<B, T, NW, PAIRED, ODD, false>(a, batch, L, st);
 }
 
 // Every level runs the same stages, so only a step-1 last stage yields odd
@@ -464,17 +488,19 @@ bool plan(const GenericArgs& a, int T, C2FLevel* L) {
 
 }  // namespace
 
-// The packed C2F level kernel serves levels of whole 8-, 16-, 32- or 64-pixel
-// blocks with steps 2, 4 or 8 (and step 1 in the last stage: the RAW phase's
-// fine stage), any start centre, 16-byte aligned frames, and a union window
-// that fits shared memory; returns cudaErrorNotSupported otherwise
+// The packed C2F level kernel serves levels of 8-, 16-, 32- or 64-pixel
+// blocks on frames whose width is a multiple of the block (the last block row
+// may be clipped by the frame height), with steps 2, 4 or 8 (and step 1 in the
+// last stage: the RAW phase's fine stage), any start centre, 16-byte aligned
+// frames, and a union window that fits shared memory; returns
+// cudaErrorNotSupported otherwise
 // (the caller then runs the generic kernel).  8-, 16- and 32-pixel levels
 // take 2 x 2 tiles where the tile's blocks share a start centre (level 0, or
 // a parent block that is a multiple of twice their size); without one, 32-pixel
 // levels take one block per CTA and 8- and 16-pixel levels the generic kernel.
 cudaError_t launch_c2f_level(const GenericArgs& a, int batch, cudaStream_t st) {
   if (a.B != 8 && a.B != 16 && a.B != 32 && a.B != 64) return cudaErrorNotSupported;
-  if (a.center_mode == 2 || a.W % a.B || a.H % a.B) return cudaErrorNotSupported;
+  if (a.center_mode == 2 || a.W % a.B) return cudaErrorNotSupported;
   if ((reinterpret_cast<uintptr_t>(a.ref) % 16) || (reinterpret_cast<uintptr_t>(a.cur) % 16) || a.pitch % 8 ||
       a.ref_bs % 8 || a.cur_bs % 8)
     return cudaErrorNotSupported;

@@ -18,6 +18,11 @@
 //   * half the lanes walk the block rows rotated by one, which together with a
 //     window pitch of 4*(odd) words makes every 128-bit shared load
 //     conflict-free;
+//   * a frame height that is not a multiple of 16 clips the last block row
+//     to bh rows: its current rows below the frame are staged as zeros (their
+//     min(cur, win) adds nothing) and its column-sum table sums bh rows, so
+//     its SAD covers exactly the rows inside the frame, as the definition of
+//     a clipped edge block asks;
 //   * argmin: each lane folds its candidates into a uint64 key
 //     (sad, |dx|+|dy|, dy, dx) -- on interior blocks through a 32-bit
 //     sad*64 + rank key, rank being the tie-break order within the lane's row
@@ -55,16 +60,19 @@ __global__ void __launch_bounds__(kNW * 32, 6) me_full16_even_kernel(const uint1
   const uint16_t* cur = cur_base + (long long)pair * cur_bs;
   const int x0 = blockIdx.x * kNW * 16, y0 = blockIdx.y * 16;
 
+  // the last block row of a frame whose height is not a multiple of 16 is
+  // clipped to bh rows (its SAD covers the rows inside the frame)
+  const int bh = min(16, H - y0);
   stage_strip<R, kNW>(ref, cur, W, H, pitch, x0, y0, vec_ok, win, curt);
   __syncthreads();
-  window_colsums<R, C::P, C::WW, kNW * 32>(win, cs, threadIdx.x);
+  window_colsums<R, C::P, C::WW, kNW * 32>(win, cs, threadIdx.x, bh);
   __syncthreads();
 
   const int bx = blockIdx.x * kNW + warp;
   if (bx >= w) return;
 
   const uint64_t best = warp_min_u64(
-      full16_block<R, C::P, C::PC>(win + 8 * warp, cs + 8 * warp, curt + 8 * warp, lane, bx * 16, y0, W, H));
+      full16_block<R, C::P, C::PC>(win + 8 * warp, cs + 8 * warp, curt + 8 * warp, lane, bx * 16, y0, W, H, bh));
   if (lane == 0) out[((long long)pair * h + blockIdx.y) * w + bx] = key_to_mv(best);
 }
 
@@ -72,7 +80,7 @@ template <int R>
 cudaError_t launch_r(const uint16_t* ref, const uint16_t* cur, int W, int H, int pitch, long long ref_bs,
                      long long cur_bs, int batch, bayer_mv_t* out, cudaStream_t st) {
   using C = Full16Strip<R, kNW>;
-  const int h = H / 16, w = W / 16;
+  const int h = (H + 15) / 16, w = W / 16;
   dim3 grid((w + kNW - 1) / kNW, h, batch);
   // 16-byte loads need 16-byte aligned rows in every frame of the batch
   const bool vec_ok = (reinterpret_cast<uintptr_t>(ref) % 16) == 0 && (reinterpret_cast<uintptr_t>(cur) % 16) == 0 &&
