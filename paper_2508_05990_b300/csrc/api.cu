@@ -115,11 +115,11 @@ bayer_status_t check_frames(const void* ref, const void* cur, int W, int H, int 
 // one stage (step 2 for EVEN, 1 for RAW, centre 0: the same candidates, limit
 // and key); the generic stage kernel where neither applies.
 bayer_status_t full_search(const uint16_t* ref, const uint16_t* cur, int W, int H, int pitch, long long rbs,
-                           long long cbs, int batch, int block, int range, int phase, bayer_mv_t* out,
+                           long long cbs, int batch, int block, int range, int phase, bayer_mv_t* out, int* status,
                            cudaStream_t st) {
   const int h = (H + block - 1) / block, w = (W + block - 1) / block;
   if (phase == BAYER_PHASE_EVEN && block == 16 && (W % 16) == 0 && bme::full16_even_supported(range)) {
-    return cuda_status(bme::launch_full16_even(ref, cur, W, H, pitch, rbs, cbs, batch, range, out, st));
+    return cuda_status(bme::launch_full16_even(ref, cur, W, H, pitch, rbs, cbs, batch, range, out, status, st));
   }
   GenericArgs a{};
   a.ref = ref;
@@ -271,7 +271,7 @@ bayer_status_t bayer_me_estimate(bayer_me_t h, const uint16_t* ref, const uint16
   if (s != BAYER_OK) return s;
   if (range < 0 || (range & 1) || range > 510) return BAYER_ERR_INVALID_ARG;
   DeviceGuard g(h->device);
-  return full_search(ref, cur, W, H, W, 0, 0, 1, block, range, BAYER_PHASE_EVEN, mv_out,
+  return full_search(ref, cur, W, H, W, 0, 0, 1, block, range, BAYER_PHASE_EVEN, mv_out, h->d_status,
                      static_cast<cudaStream_t>(stream));
 }
 
@@ -292,7 +292,7 @@ bayer_status_t bayer_me_estimate_ex(bayer_me_t h, const uint16_t* ref, const uin
     if (p->range < 0 || p->range > 510) return BAYER_ERR_INVALID_ARG;
     if (p->phase == BAYER_PHASE_EVEN && (p->range & 1)) return BAYER_ERR_INVALID_ARG;
     return full_search(ref, cur, W, H, pitch, p->ref_batch_stride, p->cur_batch_stride, p->batch, p->block,
-                       p->range, p->phase, mv_out, st);
+                       p->range, p->phase, mv_out, h->d_status, st);
   }
 
   if (p->mode == BAYER_MODE_SEEDED) {
@@ -467,7 +467,7 @@ bayer_status_t bayer_clip_process_host(bayer_me_t h, const uint16_t* frames, int
   if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_comp, ev_frames, 0);
   if (e == cudaSuccess) {
     s = full_search(h->d_frames, h->d_frames + frame_elems, W, H, W, (long long)frame_elems,
-                    (long long)frame_elems, npairs, block, range, BAYER_PHASE_EVEN, h->d_mv, h->s_comp);
+                    (long long)frame_elems, npairs, block, range, BAYER_PHASE_EVEN, h->d_mv, h->d_status, h->s_comp);
     if (s != BAYER_OK) e = cudaErrorLaunchFailure;
   }
   if (e == cudaSuccess) e = cudaEventRecord(ev_me, h->s_comp);

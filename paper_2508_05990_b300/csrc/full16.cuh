@@ -50,9 +50,17 @@ struct Full16Strip {
   static constexpr int SPANW = 8 + REACH;      // window words one block reads per row
   static constexpr int CUR_OFF = WIN_H * P;
   static constexpr int CS_OFF = CUR_OFF + 16 * PC;
-  static constexpr size_t SMEM = (size_t)(CS_OFF + NU * P) * sizeof(uint32_t);
+  // TMA staging: the window as one box 2P pixels wide (its rows land at pitch
+  // P), the current tile as one box 2PC pixels wide; both complete on one
+  // mbarrier after the column-sum table
+  static constexpr int BOX_W = 2 * P, CUR_BOX_W = 2 * PC;
+  static constexpr uint32_t TX_BYTES = (uint32_t)(WIN_H * P + 16 * PC) * 4u;
+  static constexpr int MBAR_OFF = (CS_OFF + NU * P + 1) / 2 * 2;  // 8-byte aligned
+  static constexpr size_t SMEM = (size_t)MBAR_OFF * sizeof(uint32_t) + sizeof(uint64_t);
   static_assert(NU <= 33, "at most 33 candidate rows");
   static_assert(SPANW % 4 == 0, "R must be even (128-bit window loads)");
+  static_assert((CUR_OFF * 4) % 128 == 0, "current tile 128-byte aligned (TMA destination)");
+  static_assert(BOX_W <= 256 && CUR_BOX_W <= 256, "TMA box at most 256 elements wide");
 };
 
 // Accumulators of one lane: its candidate row (NU candidates), and for

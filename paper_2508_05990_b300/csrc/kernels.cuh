@@ -16,8 +16,10 @@ namespace bme {
 // uses another kernel.
 bool full16_even_supported(int range);
 cudaError_t configure_full16();  // once per device: shared-memory opt-in
+// status: device word that receives BAYER_ERR_TIMEOUT if the TMA staging's
+// bounded wait expires.
 cudaError_t launch_full16_even(const uint16_t* ref, const uint16_t* cur, int W, int H, int pitch, long long ref_bs,
-                               long long cur_bs, int batch, int range, bayer_mv_t* out, cudaStream_t st);
+                               long long cur_bs, int batch, int range, bayer_mv_t* out, int* status, cudaStream_t st);
 
 // Generic matching kernel: one CTA per block, up to BAYER_MAX_STAGES stages
 // run in order, each centred on the previous stage's best.

@@ -5,8 +5,10 @@
 //   * one CTA = NW (4) warps = NW horizontally adjacent blocks of one block
 //     row of one frame pair; the CTA stages the union of their search windows
 //     ((16*NW + 4R) x (16 + 4R) pixels) and their current blocks into shared
-//     memory as packed pixel pairs (16-byte loads stored unchanged), then a
-//     table of 16-row column sums of the window at every even row offset;
+//     memory as packed pixel pairs -- two TMA tensor tiles whose rows land at
+//     the pitches below (16-byte register-staged loads for unaligned frames)
+//     -- then a table of 16-row column sums of the window at every even row
+//     offset;
 //   * one warp = one block; lane v owns candidate row v (dy = 2v - 2R) and all
 //     2R+1 candidates of that row (dx = 2u - 2R).  Adjacent candidates of a
 //     row are one packed word apart (EVEN offsets), so every window word a
@@ -41,13 +43,21 @@ namespace {
 // faster than 8-block strips at 4 (0.531 vs 0.559 ms for the 1080p clip),
 // although each block stages a third more window.
 constexpr int kNW = 4;
+constexpr uint32_t kStripWaitLimit = 1u << 22;
 
-template <int R>
-__global__ void __launch_bounds__(kNW * 32, 6) me_full16_even_kernel(const uint16_t* __restrict__ ref_base,
+// TMA: the window and the current tile arrive as two tensor tiles (16-byte
+// aligned frames); the rows land at the pitches the sliding loads want, and
+// samples outside the frame read 0 -- the current rows below the frame of a
+// clipped last block row too.  Without TMA, 16-byte register-staged loads.
+template <int R, bool TMA>
+__global__ void __launch_bounds__(kNW * 32, 6) me_full16_even_kernel(const __grid_constant__ CUtensorMap tm_ref,
+                                                                   const __grid_constant__ CUtensorMap tm_cur,
+                                                                   const uint16_t* __restrict__ ref_base,
                                                                    const uint16_t* __restrict__ cur_base, int W,
                                                                    int H, int pitch, long long ref_bs,
                                                                    long long cur_bs, int h, int w,
-                                                                   bayer_mv_t* __restrict__ out, bool vec_ok) {
+                                                                   bayer_mv_t* __restrict__ out, bool vec_ok,
+                                                                   int* __restrict__ status) {
   using C = Full16Strip<R, kNW>;
   extern __shared__ __align__(128) uint32_t smem[];
   uint32_t* win = smem;                // WIN_H x P
@@ -56,15 +66,36 @@ __global__ void __launch_bounds__(kNW * 32, 6) me_full16_even_kernel(const uint1
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int pair = blockIdx.z;
-  const uint16_t* ref = ref_base + (long long)pair * ref_bs;
-  const uint16_t* cur = cur_base + (long long)pair * cur_bs;
   const int x0 = blockIdx.x * kNW * 16, y0 = blockIdx.y * 16;
 
   // the last block row of a frame whose height is not a multiple of 16 is
   // clipped to bh rows (its SAD covers the rows inside the frame)
   const int bh = min(16, H - y0);
-  stage_strip<R, kNW>(ref, cur, W, H, pitch, x0, y0, vec_ok, win, curt);
-  __syncthreads();
+  if constexpr (TMA) {
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + C::MBAR_OFF);
+    if (threadIdx.x == 0) {
+      tc::mbar_init(mbar, 1);
+      tc::fence_mbar_init();
+      tma::mbar_arrive_expect_tx(mbar, C::TX_BYTES);
+      tma::load_3d(win, &tm_ref, x0 - C::REACH, y0 - C::REACH, pair, mbar);
+      tma::load_3d(curt, &tm_cur, x0, y0, pair, mbar);
+    }
+    __syncthreads();  // the barrier is initialised before anyone waits on it
+    const bool ok = tc::mbar_wait(mbar, 0, kStripWaitLimit);
+    if (!__syncthreads_and(ok)) {
+      // record the expiry, give the copies a last bounded wait, and stop
+      if (threadIdx.x == 0) {
+        if (status) atomicExch(status, (int)BAYER_ERR_TIMEOUT);
+        tc::mbar_wait(mbar, 0, kStripWaitLimit);
+      }
+      __syncthreads();
+      return;
+    }
+  } else {
+    stage_strip<R, kNW>(ref_base + (long long)pair * ref_bs, cur_base + (long long)pair * cur_bs, W, H, pitch, x0,
+                        y0, vec_ok, win, curt);
+    __syncthreads();
+  }
   window_colsums<R, C::P, C::WW, kNW * 32>(win, cs, threadIdx.x, bh);
   __syncthreads();
 
@@ -78,14 +109,22 @@ __global__ void __launch_bounds__(kNW * 32, 6) me_full16_even_kernel(const uint1
 
 template <int R>
 cudaError_t launch_r(const uint16_t* ref, const uint16_t* cur, int W, int H, int pitch, long long ref_bs,
-                     long long cur_bs, int batch, bayer_mv_t* out, cudaStream_t st) {
+                     long long cur_bs, int batch, bayer_mv_t* out, int* status, cudaStream_t st) {
   using C = Full16Strip<R, kNW>;
   const int h = (H + 15) / 16, w = W / 16;
   dim3 grid((w + kNW - 1) / kNW, h, batch);
-  // 16-byte loads need 16-byte aligned rows in every frame of the batch
+  // 16-byte loads and TMA tiles need 16-byte aligned rows in every frame of the batch
   const bool vec_ok = (reinterpret_cast<uintptr_t>(ref) % 16) == 0 && (reinterpret_cast<uintptr_t>(cur) % 16) == 0 &&
                       pitch % 8 == 0 && ref_bs % 8 == 0 && cur_bs % 8 == 0;
-  me_full16_even_kernel<R><<<grid, kNW * 32, C::SMEM, st>>>(ref, cur, W, H, pitch, ref_bs, cur_bs, h, w, out, vec_ok);
+  CUtensorMap tref{}, tcur{};
+  const bool use_tma = vec_ok && tma::encode_u16_frames(&tref, ref, W, H, batch, pitch, ref_bs, C::BOX_W, C::WIN_H) &&
+                       tma::encode_u16_frames(&tcur, cur, W, H, batch, pitch, cur_bs, C::CUR_BOX_W, 16);
+  if (use_tma)
+    me_full16_even_kernel<R, true><<<grid, kNW * 32, C::SMEM, st>>>(tref, tcur, ref, cur, W, H, pitch, ref_bs, cur_bs,
+                                                                     h, w, out, vec_ok, status);
+  else
+    me_full16_even_kernel<R, false><<<grid, kNW * 32, C::SMEM, st>>>(tref, tcur, ref, cur, W, H, pitch, ref_bs,
+                                                                      cur_bs, h, w, out, vec_ok, status);
   return cudaGetLastError();
 }
 
@@ -303,10 +342,12 @@ cudaError_t configure_list_r() {
 
 template <int R>
 cudaError_t configure_r() {
-  cudaError_t e = cudaFuncSetAttribute(me_full16_even_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)Full16Strip<R, kNW>::SMEM);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(me_full16_even_kernel<R>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  cudaError_t e = cudaSuccess;
+  for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+    const void* fn = v ? (const void*)me_full16_even_kernel<R, true> : (const void*)me_full16_even_kernel<R, false>;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Full16Strip<R, kNW>::SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  }
   return e;
 }
 
@@ -351,12 +392,12 @@ cudaError_t launch_full16_list(const uint16_t* ref, const uint16_t* cur, int W, 
 bool full16_even_supported(int range) { return range == 8 || range == 16 || range == 24 || range == 32; }
 
 cudaError_t launch_full16_even(const uint16_t* ref, const uint16_t* cur, int W, int H, int pitch, long long ref_bs,
-                               long long cur_bs, int batch, int range, bayer_mv_t* out, cudaStream_t st) {
+                               long long cur_bs, int batch, int range, bayer_mv_t* out, int* status, cudaStream_t st) {
   switch (range) {
-    case 8: return launch_r<4>(ref, cur, W, H, pitch, ref_bs, cur_bs, batch, out, st);
-    case 16: return launch_r<8>(ref, cur, W, H, pitch, ref_bs, cur_bs, batch, out, st);
-    case 24: return launch_r<12>(ref, cur, W, H, pitch, ref_bs, cur_bs, batch, out, st);
-    case 32: return launch_r<16>(ref, cur, W, H, pitch, ref_bs, cur_bs, batch, out, st);
+    case 8: return launch_r<4>(ref, cur, W, H, pitch, ref_bs, cur_bs, batch, out, status, st);
+    case 16: return launch_r<8>(ref, cur, W, H, pitch, ref_bs, cur_bs, batch, out, status, st);
+    case 24: return launch_r<12>(ref, cur, W, H, pitch, ref_bs, cur_bs, batch, out, status, st);
+    case 32: return launch_r<16>(ref, cur, W, H, pitch, ref_bs, cur_bs, batch, out, status, st);
     default: return cudaErrorInvalidValue;
   }
 }
