@@ -232,28 +232,38 @@ class ClockSampler:
 class NvmlClockSampler:
     """SM clock and clock-event (throttle) reasons read through NVML every
     ~0.5 ms from a host thread, so that even a timed region of ~10 ms gets tens
-    of samples (nvidia-smi's loop samples every 20 ms at best).  Each sample is
-    (host time, SM MHz, max SM MHz, set of active reasons)."""
-    REASONS = (("hw_slowdown", "nvmlClocksEventReasonHwSlowdown"),
-               ("hw_thermal_slowdown", "nvmlClocksEventReasonHwThermalSlowdown"),
-               ("sw_thermal_slowdown", "nvmlClocksEventReasonSwThermalSlowdown"),
-               ("sw_power_cap", "nvmlClocksEventReasonSwPowerCap"))
+    of samples (nvidia-smi's loop samples every 20 ms at best).  NVML is the
+    driver's libnvidia-ml.so.1, called through ctypes.  Each sample is (host
+    time, SM MHz, max SM MHz, set of active reasons)."""
+    # nvmlClocksEventReason* bits (nvml.h)
+    REASONS = (("sw_power_cap", 0x4), ("hw_slowdown", 0x8), ("sw_thermal_slowdown", 0x20),
+               ("hw_thermal_slowdown", 0x40))
+    NVML_CLOCK_SM = 1
 
     def __init__(self, index: int, period_s: float = 5e-4):
         self.index, self.period = index, period_s
-        self.samples, self.ok = [], False
+        self.samples, self.ok, self.error = [], False, None
 
     def __enter__(self):
+        import ctypes
         import threading
         try:
-            import pynvml as nv
-            nv.nvmlInit()
-            self._nv = nv
-            self._h = nv.nvmlDeviceGetHandleByIndex(self.index)
-            self._max = float(nv.nvmlDeviceGetMaxClockInfo(self._h, nv.NVML_CLOCK_SM))
-            self._bits = [(n, getattr(nv, c)) for n, c in self.REASONS]
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                raise OSError("nvmlInit_v2 failed")
+            self._lib = lib
+            self._h = ctypes.c_void_p()
+            if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.index), ctypes.byref(self._h)) != 0:
+                raise OSError("nvmlDeviceGetHandleByIndex_v2 failed")
+            mx = ctypes.c_uint()
+            if lib.nvmlDeviceGetMaxClockInfo(self._h, self.NVML_CLOCK_SM, ctypes.byref(mx)) != 0:
+                raise OSError("nvmlDeviceGetMaxClockInfo failed")
+            self._max = float(mx.value)
+            self._reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                lib.nvmlDeviceGetCurrentClocksThrottleReasons
             self.ok = True
-        except Exception:  # no NVML: the nvidia-smi sampler stands alone
+        except (OSError, AttributeError) as e:  # no NVML: the nvidia-smi sampler stands alone
+            self.error = str(e)
             return self
         self._stop = threading.Event()
         self._thr = threading.Thread(target=self._run, daemon=True)
@@ -261,24 +271,22 @@ class NvmlClockSampler:
         return self
 
     def _run(self):
-        nv, h = self._nv, self._h
+        import ctypes
+        clk, r = ctypes.c_uint(), ctypes.c_ulonglong()
         while not self._stop.is_set():
-            try:
-                sm = float(nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM))
-                r = nv.nvmlDeviceGetCurrentClocksEventReasons(h)
-            except Exception:
+            if (self._lib.nvmlDeviceGetClockInfo(self._h, self.NVML_CLOCK_SM, ctypes.byref(clk)) != 0
+                    or self._reasons(self._h, ctypes.byref(r)) != 0):
+                self.error = "NVML query failed"
                 break
-            self.samples.append((time.time(), sm, self._max, {n for n, b in self._bits if r & b}))
+            self.samples.append((time.time(), float(clk.value), self._max,
+                                 {n for n, b in self.REASONS if r.value & b}))
             time.sleep(self.period)
 
     def __exit__(self, *exc):
         if self.ok:
             self._stop.set()
             self._thr.join(timeout=2)
-            try:
-                self._nv.nvmlShutdown()
-            except Exception:
-                pass
+            self._lib.nvmlShutdown()
 
     def summary(self, t0, t1):
         use = [p for p in self.samples if t0 <= p[0] <= t1]
@@ -440,8 +448,9 @@ def leg_multi_stream(h, clips, steps, warmup, peaks, pc_clk_sm, nsm, sm_mhz):
                      "alu_ms": round(t_alu, 4), "hbm_ms": round(t_hbm, 4),
                      "algorithmic_per_step": f"{ms_pc_per_step()} pixel-candidates + {ms_prop_bytes_per_step()} "
                                              "propagation bytes",
-                     "peak_source": "measured packed min.u16x2 + dp2a rate x SMs x median SM clock; "
-                                    "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+                     "peak_source": "measured packed min.u16x2 + dp2a rate x SMs x median SM clock; " + (
+                         "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks
+                         else "fallback 6400 GB/s (MEASURED_PEAKS.json absent)")},
         "gpu_launches": 2 * steps,
         "l2": "inputs larger than L2 (2.2 GB of feature maps per step); no flush",
     }
@@ -504,6 +513,64 @@ def leg_c2f(h, d_frames, d_feats, d_out, stream, steps, warmup, pc_clk_sm, nsm, 
             "presets": rows, "steps": steps, "warmup": warmup,
             "peak_source": "measured packed min.u16x2 + dp2a rate x SMs x median SM clock",
             "gpu_launches": launches}
+
+
+RAGGED_SEED = 1005
+
+
+def c2f_pc_in_frame(setting, Hh: int, Ww: int) -> int:
+    """Pixel-candidates of one pair's EVEN pyramid counting only pixels inside
+    the frame (a clipped block row has fewer): every pixel lies in one block
+    per level, so each level costs H * W * sum over stages of (2R+1)^2."""
+    per = 0
+    for R, st in setting.stages:
+        if st % 2:
+            R, st = R * st // (st + 1), st + 1
+        per += (2 * R + 1) ** 2
+    return len(setting.levels) * Hh * Ww * per
+
+
+def leg_ragged(h, steps, warmup, peak_gpcs):
+    """Frames whose height is not a multiple of the block: the real 1920x1080
+    frame (exhaustive block 16 +-32, its last block row 8 rows high) beside the
+    1920x1088 workload, and the paper's 720x960 runtime resolution (standard
+    pyramid, EVEN; 720 is no multiple of 64 or 32) beside 768x960.  Seven pairs
+    per launch, search alone; G pixel-candidates/s count in-frame pixels."""
+    import torch
+    from paper_2508_05990_b300 import bayer_me as bm
+    from paper_2508_05990_b300 import synth
+    std = bm.C2F_PRESETS["standard"]
+    out = {}
+    for name, Hh, Ww, mode in (("full_1920x1080", 1080, 1920, bm.MODE_FULL), ("full_1920x1088", 1088, 1920, bm.MODE_FULL),
+                               ("c2f_standard_720x960", 720, 960, bm.MODE_C2F),
+                               ("c2f_standard_768x960", 768, 960, bm.MODE_C2F)):
+        frames = torch.from_numpy(synth.pan_clip(RAGGED_SEED, Hh, Ww, n_frames=T)).cuda()
+        B = std.levels[-1] if mode == bm.MODE_C2F else BLOCK
+        mv = torch.empty((PAIRS, -(-Hh // B), -(-Ww // B), 2), dtype=torch.int32, device="cuda")
+        kw = dict(batch=PAIRS, ref_batch_stride=Hh * Ww, cur_batch_stride=Hh * Ww, out=mv)
+        run = (lambda: h.estimate_ex(frames, frames[1:], search_range=RANGE, **kw)) if mode == bm.MODE_FULL else \
+            (lambda: h.estimate_ex(frames, frames[1:], mode=bm.MODE_C2F, c2f=std, **kw))
+        for _ in range(warmup):
+            run()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(steps):
+            run()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        pc = PAIRS * (Hh * Ww * (2 * (RANGE // 2) + 1) ** 2 if mode == bm.MODE_FULL else c2f_pc_in_frame(std, Hh, Ww))
+        out[name] = {"me_ms": round(ms, 4), "frames_per_s": round(PAIRS / (ms / 1e3), 1),
+                     "gpc_per_s": round(pc / (ms / 1e3) / 1e9, 1), "frac_of_alu_peak": round(pc / (ms / 1e3) / peak_gpcs, 4)}
+    if h.sync_status() != bm.OK:
+        raise RuntimeError("device status after the ragged-frame leg")
+    out["ratio_1080_vs_1088"] = round(out["full_1920x1080"]["gpc_per_s"] / out["full_1920x1088"]["gpc_per_s"], 4)
+    out["ratio_720_vs_768"] = round(out["c2f_standard_720x960"]["gpc_per_s"] / out["c2f_standard_768x960"]["gpc_per_s"],
+                                    4)
+    out["note"] = ("7 pairs per launch; the paper's standard FME takes 3.36 ms per 720x960 frame on an A100 "
+                   "(context, another machine)")
+    return out
 
 
 def leg_refine_4k(h, clip, steps, warmup, peaks):
@@ -593,7 +660,9 @@ def leg_refine_4k(h, clip, steps, warmup, peaks):
                      "achieved": round(flops / (rf / 1e3) / 1e12, 1), "peak": peak, "unit": "TFLOP/s",
                      "frac": round(flops / (rf / 1e3) / 1e12 / peak, 4),
                      "algorithmic_per_launch_set": f"{flops} FLOP ({pairs} maps x {refine_flops_per_frame()})",
-                     "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)",
+                     "peak_source": ("MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"
+                                     if "bf16_tflops_sustained" in peaks
+                                     else "fallback 1400 TFLOP/s sustained (MEASURED_PEAKS.json absent)"),
                      "fp32_simt_tflops": round(flops / (rf32 / 1e3) / 1e12, 1)},
         "bf16_vs_fp32_normwise": round(diff, 6),
         "gpu_launches": 5 * steps,
@@ -718,7 +787,7 @@ def run_ours(args):
     clocks = nclk.summary(t_host0, t_host1)
     smi = clk.summary(t_host0, t_host1)
     if clocks is None:
-        clocks = smi
+        clocks = dict(smi, nvml=nclk.error or "no samples in the timed region")
     else:  # nvidia-smi's reasons too, for the timed region's few 20 ms samples
         clocks["reasons"] = sorted(set(clocks["reasons"]) | set(r for r in smi["reasons"] if r != "unsampled"))
         clocks["nvidia_smi_samples"] = smi["samples"]
@@ -729,13 +798,14 @@ def run_ours(args):
     except (OSError, ValueError):
         pass
 
-    multi_stream = refine_4k = c2f = None
+    multi_stream = refine_4k = c2f = ragged = None
     if legs:
         c2f = leg_c2f(h, d_frames, d_feats, d_out, stream, steps=10, warmup=3, pc_clk_sm=pc_clk_sm, nsm=nsm,
                       sm_mhz=sm_mhz, full_me_ms=statistics.mean(me_ms), full_step_ms=ms_total / args.steps)
         multi_stream = leg_multi_stream(h, leg_clips[0], steps=30, warmup=3, peaks=peaks, pc_clk_sm=pc_clk_sm,
                                         nsm=nsm, sm_mhz=sm_mhz)
         refine_4k = leg_refine_4k(h, leg_clips[1], steps=10, warmup=3, peaks=peaks)
+        ragged = leg_ragged(h, steps=20, warmup=3, peak_gpcs=pc_clk_sm * nsm * sm_mhz * 1e6)
         leg_clips = None
         torch.cuda.empty_cache()
 
@@ -763,6 +833,8 @@ def run_ours(args):
         prop_avg_s = statistics.mean(prop_ms) / 1e3
         prop_gbs = PAIRS * prop_bytes_per_pair() / prop_avg_s / 1e9
         hbm_peak = peaks.get("hbm_gbs", 6400.0)
+        hbm_src = ("MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks
+                   else "fallback 6400 GB/s (MEASURED_PEAKS.json absent)")
         value = world * PAIRS * args.steps / (ms_total / 1e3)
         result = {
             "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -786,7 +858,7 @@ def run_ours(args):
                             "frac": round(prop_gbs / hbm_peak, 4), "avg_launch_ms": round(prop_avg_s * 1e3, 4),
                             "traffic": profiled_traffic("prop_nchw_bilinear_1080p_clip.md", PROP_SOURCES),
                             "algorithmic_bytes_per_launch": PAIRS * prop_bytes_per_pair(),
-                            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+                            "peak_source": hbm_src},
             "mblocks_per_s": round(value * hb * wb / 1e6, 3),
             "e2e": {"value": round(world * PAIRS * args.steps / e2e_s, 2), "unit": UNIT,
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
@@ -799,6 +871,7 @@ def run_ours(args):
             "multi_stream": multi_stream,
             "precision_4k": refine_4k,
             "c2f": c2f,
+            "ragged": ragged,
         }
         if not args.no_cpu_baseline:
             result["cpu_baseline"] = cpu_baseline_sample(frames, feats)
