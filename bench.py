@@ -69,7 +69,8 @@ def prop_bytes_per_pair() -> int:
 
 
 ME_SOURCES = ("paper_2508_05990_b300/csrc/me_full16.cu", "paper_2508_05990_b300/csrc/full16.cuh",
-              "paper_2508_05990_b300/csrc/common.cuh")
+              "paper_2508_05990_b300/csrc/common.cuh", "paper_2508_05990_b300/csrc/tma.cuh",
+              "paper_2508_05990_b300/csrc/tc_common.cuh")
 PROP_SOURCES = ("paper_2508_05990_b300/csrc/propagate.cu", "paper_2508_05990_b300/csrc/prop_common.cuh",
                 "paper_2508_05990_b300/csrc/common.cuh")
 
@@ -93,6 +94,8 @@ def profiled_traffic(summary: str, sources) -> int | None:
 
 
 WEIGHTS = os.path.join(ROOT, "paper_2508_05990_b300", "weights", "proposal_1080p_r32.npz")
+# the same network trained on exactly the 2,000 pairs of the learned-proposal workload
+WEIGHTS_2000 = os.path.join(ROOT, "paper_2508_05990_b300", "weights", "proposal_1080p_r32_2000pairs.npz")
 
 # batched multi-stream workload: 32 streams of mixed sizes, 16 frames each
 MS_SIZES = [(480, 640)] * 8 + [(720, 1280)] * 8 + [(1088, 1920)] * 12 + [(2160, 3840)] * 4
@@ -776,9 +779,27 @@ def run_ours(args):
             "sad_regret": round(float((sad_l.sum() - sad_plain.sum()) / sad_plain.sum()), 5),
             "mean_block_rel_regret": round(float(((sad_l - sad_plain) / np.maximum(sad_plain, 1)).mean()), 5),
             "search": "proposal CNN (BF16, tcgen05) + +-4 refine; exhaustive +-32 where conf < 0.5",
-            "weights": os.path.relpath(WEIGHTS, ROOT),
+            "weights": os.path.relpath(WEIGHTS, ROOT) + " (4,000 training pairs)",
             "gpu_launches": args.steps * 9,
         }
+        if os.path.exists(WEIGHTS_2000):
+            # the configured training scale: same clip, same timing
+            wbf = bm.to_bf16_bits(torch.from_numpy(np.load(WEIGHTS_2000)["theta"].astype(np.float32)).cuda()).contiguous()
+            for _ in range(args.warmup):
+                lstep()
+            torch.cuda.synchronize()
+            start.record(stream)
+            for k in range(args.steps):
+                lstep()
+            end.record(stream)
+            torch.cuda.synchronize()
+            ms_c = start.elapsed_time(end)
+            sad_c = bm.records_to_numpy(d_mv_l)["sad"].astype(np.int64)
+            learned["configured_scale"] = {
+                "weights": os.path.relpath(WEIGHTS_2000, ROOT) + " (2,000 training pairs)",
+                "value": round(PAIRS * args.steps / (ms_c / 1e3), 2), "ms_per_step": round(ms_c / args.steps, 4),
+                "fallback_rate": round(float(d_fb.float().mean().item()), 4),
+                "sad_regret": round(float((sad_c.sum() - sad_plain.sum()) / sad_plain.sum()), 5)}
 
     # ALU roofline: measured throughput of the search's primitive (packed min.u16x2 + dp2a, two
     # pixel-candidates per pair) per clock per SM x SMs x SM clock under load; sad.u32 beside it

@@ -97,3 +97,23 @@ def test_trained_network_gain(handle, heldout):
     assert regret_t <= 0.1 * regret_zero
     # untrained weights either fall back far more often or lose far more SAD
     assert cand_u >= 2 * cand_t or regret_u >= 5 * max(regret_t, 1e-3)
+
+
+def test_configured_scale_weights_on_the_configured_heldout_pairs(handle):
+    """The network trained on exactly 2,000 pairs, evaluated on exactly the 200
+    held-out pairs of the learned-proposal workload (seeds 2e6 + k, first 200
+    pairs of 29 clips): SAD regret at most 1 % against the exhaustive search,
+    with at most a quarter of the blocks falling back."""
+    import os
+    from paper_2508_05990_b300 import train_proposal as tp
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2508_05990_b300",
+                        "weights", "proposal_1080p_r32_2000pairs.npz")
+    theta = torch.from_numpy(np.load(path)["theta"].astype(np.float32)).cuda()
+    clips = tp.make_clips(tp.EVAL_SEED, 29, max(1, (os.cpu_count() or 2) - 1))
+    clips_d = torch.from_numpy(clips.view(np.int16)).cuda()
+    labels = tp.label_clips(handle, clips_d)
+    res = tp.evaluate(handle, clips_d, labels, bm.to_bf16_bits(theta).contiguous(), reps=2, n_pairs=200)
+    print(f"\nconfigured scale: {res}")
+    assert res["pairs"] == 200
+    assert 0.0 <= res["sad_regret"] <= 0.01
+    assert res["fallback_rate"] <= 0.25
