@@ -302,17 +302,25 @@ bayer_status_t bayer_refine_conv(bayer_me_t h, const float* feat, int n, int Hf,
  * {8, 16, 24, 32}; W and H multiples of 16), then, where feat is not NULL,
  * propagation of that pair's NCHW feature map as in bayer_feat_propagate
  * (stride divides 16; Hf*stride/16 == H/16 and Wf*stride/16 == W/16).
- * All searches run in one launch (one CTA per strip of blocks of any pair),
- * all propagations in a second one; the two are captured as a CUDA
- * graph and replayed on later calls with the same set of sizes.  The first
- * call for a set of sizes also runs an autotuner: it times each launch
- * schedule (blocks per strip 4 or 8; pairs as given or largest first) and
- * keeps the fastest for that set (the handle's autotune table).
+ * The searches run in one launch (one CTA per strip of blocks of any pair)
+ * and the propagations in a second one, or, smallest frames first, per class
+ * of frame size a search launch followed by that class's propagation launch;
+ * the launches are captured as a CUDA graph and replayed on later calls with
+ * the same set of sizes.  The first call for a
+ * set of sizes also runs an autotuner: it times each launch schedule (blocks
+ * per strip 4 or 8; pairs as given or largest first; the per-size launches
+ * smallest first) and keeps, among those within 3 % of the fastest step,
+ * the one with the lowest median per-pair completion time (the handle's
+ * autotune table).
  *   pairs: HOST array of n descriptors of device buffers (caller-owned).
  *   end_ns: optional device int64 [n]: per pair, nanoseconds from the start
  *     of the search launch until that pair's output (propagated features, or
  *     the MV field without features) was complete.
- *   schedule: optional host int, receives 10 * blocks per strip + order.
+ *   schedule: optional host int.  In: 0 to let the autotuner choose, or a
+ *     schedule code to run that schedule instead (40, 41, 80, 81, 142, 182;
+ *     any other value returns BAYER_ERR_INVALID_ARG).  Out: the schedule
+ *     run, 100 * (per-size launches) + 10 * blocks per strip + order (0 as
+ *     given, 1 largest first, 2 smallest first).
  * The first call synchronises the device (autotuning); later calls are
  * asynchronous on `stream`. */
 typedef struct {

@@ -362,10 +362,11 @@ class Handle:
                                            int(precision), _ptr(out), _stream(stream)), "bayer_refine_conv")
         return out
 
-    def multi_stream(self, pairs, search_range=32, interp=INTERP_BILINEAR, end_ns=None, stream=None):
+    def multi_stream(self, pairs, search_range=32, interp=INTERP_BILINEAR, end_ns=None, stream=None, schedule=0):
         """pairs: list of dicts with ref, cur (uint16/int16 [H, W] tensors), mv (int32 [H/16, W/16, 2]) and
         optionally feat, feat_out (float32 [C, Hf, Wf]) and stride.  Returns the schedule the autotuner chose
-        (10 * blocks per strip + order)."""
+        (100 * per-size launches + 10 * blocks per strip + order; order 0 as given, 1 largest first,
+        2 smallest first).  ``schedule``: 0 lets the autotuner choose; a code runs that schedule."""
         arr = (PairDesc * len(pairs))()
         for i, q in enumerate(pairs):
             H, W = q["ref"].shape[-2:]
@@ -376,7 +377,7 @@ class Handle:
                 C, Hf, Wf = q["feat"].shape[-3:]
                 d.feat, d.feat_out = q["feat"].data_ptr(), q["feat_out"].data_ptr()
                 d.C, d.Hf, d.Wf, d.stride = C, Hf, Wf, q.get("stride", 8)
-        sched = ctypes.c_int(0)
+        sched = ctypes.c_int(int(schedule))
         _check(self._lib.bayer_me_multi_stream(self._h, arr, len(pairs), search_range, interp, _ptr(end_ns),
                                                ctypes.byref(sched), _stream(stream)), "bayer_me_multi_stream")
         return sched.value

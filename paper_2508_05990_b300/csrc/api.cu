@@ -667,13 +667,15 @@ bayer_status_t bayer_me_multi_stream(bayer_me_t h, const bayer_pair_t* pairs, in
       if (ob < fb + bytes && fb < ob + bytes) return BAYER_ERR_INVALID_ARG;
     }
   }
+  const int force = schedule ? *schedule : 0;
+  if (force != 0 && !bme::ms_schedule_valid(force)) return BAYER_ERR_INVALID_ARG;
   DeviceGuard g(h->device);
   if (!h->ms) {
     h->ms = bme::ms_create(h->device);
     if (!h->ms) return BAYER_ERR_CUDA;
   }
-  cudaError_t e = bme::ms_run(h->ms, pairs, n, range, interp, end_ns, static_cast<cudaStream_t>(stream));
-  if (e == cudaSuccess && schedule) *schedule = bme::ms_config_nw(h->ms, pairs, n, range, interp);
+  cudaError_t e = bme::ms_run(h->ms, pairs, n, range, interp, end_ns, force, static_cast<cudaStream_t>(stream));
+  if (e == cudaSuccess && schedule) *schedule = bme::ms_config_nw(h->ms, pairs, n, range, interp, force);
   return cuda_status(e);
 }
 

@@ -172,9 +172,11 @@ struct MultiStream;
 MultiStream* ms_create(int device);
 void ms_destroy(MultiStream* m);
 cudaError_t configure_multistream();
+// force: a schedule code to run instead of the autotuned one (0: autotune).
+bool ms_schedule_valid(int code);
 cudaError_t ms_run(MultiStream* m, const bayer_pair_t* pairs, int n, int range, int interp, long long* end_ns,
-                   cudaStream_t st);
-int ms_config_nw(MultiStream* m, const bayer_pair_t* pairs, int n, int range, int interp);
+                   int force, cudaStream_t st);
+int ms_config_nw(MultiStream* m, const bayer_pair_t* pairs, int n, int range, int interp, int force);
 
 // Self-test of the bounded mbarrier wait (tc_common.cuh) every tcgen05 kernel
 // uses: BAYER_ERR_TIMEOUT lands in *status when nothing arrives.

@@ -22,10 +22,19 @@
 // warps the pair's NCHW feature map by its MV field (prop_common.cuh); a unit is a 2 x 2 quad of
 // cells sharing one MV (bilinear, two or more cells per block side) or one
 // cell.  Its CTAs stamp their own item slots.
+// Classes mode: the pairs sorted smallest first and cut into classes of equal
+// frame size (merged up to an eighth of the search each); each class gets its
+// own search launch and then its own
+// propagation launch, so the small frames' pairs complete early in the step
+// instead of all at its end (a launch boundary per class costs about 1-2 %
+// of the step).
 // Autotuner: on the first call for a set of sizes it times each schedule
-// (NW in {4, 8} x pair order {as given, largest first}) with CUDA events and
-// keeps the fastest; the graph (counter reset, search, propagation) is then
-// captured once and relaunched with only the descriptor table refreshed.
+// (NW in {4, 8} x pair order {as given, largest first}, and the classes mode
+// with NW in {4, 8}) with CUDA events and reads each one's per-pair
+// completion times; it keeps the schedule with the lowest median completion
+// time among those whose step takes at most 3 % longer than the fastest.  The
+// graph (counter reset, launches, end times) is then captured once and
+// relaunched with only the descriptor table refreshed.
 #include <algorithm>
 #include <map>
 #include <string>
@@ -81,7 +90,7 @@ __device__ __forceinline__ int find_pair(const int* prefix, int n, int item) {
 template <int R, int NW>
 __global__ void __launch_bounds__(NW * 32, NW == 8 ? 4 : 6) ms_me_kernel(const MsPair* __restrict__ pairs,
                                                                           const int* __restrict__ prefix, int n,
-                                                                          MsCounters* ctr) {
+                                                                          MsCounters* ctr, int item0) {
   using C = Full16Strip<R, NW>;
   extern __shared__ __align__(16) uint32_t smem[];
   uint32_t* win = smem;
@@ -90,8 +99,8 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 4 : 6) ms_me_kernel(const M
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // The earliest start is among the first CTAs dispatched; stamping from all
   // 66,000 strips serialised their starts on one word (0.5 ms).
-  if (threadIdx.x == 0 && blockIdx.x < 1024) atomicMin(&ctr->t0, gtimer());
-  const int item = blockIdx.x;
+  if (threadIdx.x == 0 && blockIdx.x < 1024 && item0 == 0) atomicMin(&ctr->t0, gtimer());
+  const int item = item0 + blockIdx.x;
   const int p = find_pair(prefix, n, item);
   // descriptor fields are read where they are used, so that little stays
   // live across the search (the kernel runs at 64 registers)
@@ -115,9 +124,10 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 4 : 6) ms_me_kernel(const M
 
 __global__ void __launch_bounds__(kPropThreads) ms_prop_kernel(const MsPair* __restrict__ pairs,
                                                                 const int* __restrict__ prefix, int n,
-                                                                unsigned long long* __restrict__ stamp, int interp) {
+                                                                unsigned long long* __restrict__ stamp, int interp,
+                                                                int item0) {
   {
-    const int item = blockIdx.x;
+    const int item = item0 + blockIdx.x;
     const int p = find_pair(prefix, n, item);
     const MsPair P = pairs[p];
     const int local = item - __ldg(prefix + p);
@@ -194,8 +204,18 @@ __global__ void __launch_bounds__(256) ms_end_kernel(const unsigned long long* _
 }
 
 struct Config {
-  int nw;     // warps (blocks) per search strip: 4 or 8
-  int order;  // 0: pairs as given, 1: largest first
+  int nw;       // warps (blocks) per search strip: 4 or 8
+  int order;    // 0: pairs as given, 1: largest first, 2: smallest first
+  int classes;  // 1: a search and a propagation launch per class of frame size, smallest first
+};
+
+constexpr int kMaxClasses = 8;
+
+// Runs of pairs in schedule order whose search items [me0, me1) and
+// propagation items [pr0, pr1) form one launch each (classes mode).
+struct Classes {
+  int n = 0;
+  int me0[kMaxClasses], me1[kMaxClasses], pr0[kMaxClasses], pr1[kMaxClasses];
 };
 
 template <int R, int NW>
@@ -208,22 +228,22 @@ cudaError_t ms_me_configure() {
 }
 
 template <int R, int NW>
-cudaError_t ms_me_launch(const MsPair* pairs, const int* prefix, int n, int total, MsCounters* ctr,
+cudaError_t ms_me_launch(const MsPair* pairs, const int* prefix, int n, int item0, int item1, MsCounters* ctr,
                          cudaStream_t st) {
   using C = Full16Strip<R, NW>;
-  if (total < 1) return cudaSuccess;
-  ms_me_kernel<R, NW><<<total, NW * 32, C::SMEM, st>>>(pairs, prefix, n, ctr);
+  if (item1 <= item0) return cudaSuccess;
+  ms_me_kernel<R, NW><<<item1 - item0, NW * 32, C::SMEM, st>>>(pairs, prefix, n, ctr, item0);
   return cudaGetLastError();
 }
 
 template <int NW>
-cudaError_t ms_me_dispatch(int range, const MsPair* pairs, const int* prefix, int n, int total, MsCounters* ctr,
-                           cudaStream_t st) {
+cudaError_t ms_me_dispatch(int range, const MsPair* pairs, const int* prefix, int n, int item0, int item1,
+                           MsCounters* ctr, cudaStream_t st) {
   switch (range) {
-    case 8: return ms_me_launch<4, NW>(pairs, prefix, n, total, ctr, st);
-    case 16: return ms_me_launch<8, NW>(pairs, prefix, n, total, ctr, st);
-    case 24: return ms_me_launch<12, NW>(pairs, prefix, n, total, ctr, st);
-    case 32: return ms_me_launch<16, NW>(pairs, prefix, n, total, ctr, st);
+    case 8: return ms_me_launch<4, NW>(pairs, prefix, n, item0, item1, ctr, st);
+    case 16: return ms_me_launch<8, NW>(pairs, prefix, n, item0, item1, ctr, st);
+    case 24: return ms_me_launch<12, NW>(pairs, prefix, n, item0, item1, ctr, st);
+    case 32: return ms_me_launch<16, NW>(pairs, prefix, n, item0, item1, ctr, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -250,6 +270,7 @@ struct MultiStream {
   };
   std::map<std::string, Entry> cache;  // autotune table + graphs
   cudaStream_t capture = nullptr;
+  Classes classes;  // of the last table built
 };
 
 static void ms_clear_graphs(MultiStream* m) {
@@ -336,6 +357,10 @@ void build_table(MultiStream* m, const bayer_pair_t* pairs, int n, const Config&
     std::stable_sort(perm->begin(), perm->end(), [&](int a, int b) {
       return (long long)pairs[a].W * pairs[a].H > (long long)pairs[b].W * pairs[b].H;
     });
+  if (cfg.order == 2)
+    std::stable_sort(perm->begin(), perm->end(), [&](int a, int b) {
+      return (long long)pairs[a].W * pairs[a].H < (long long)pairs[b].W * pairs[b].H;
+    });
   int me = 0, pr = 0;
   for (int k = 0; k < n; ++k) {
     const bayer_pair_t& q = pairs[(*perm)[k]];
@@ -372,6 +397,30 @@ void build_table(MultiStream* m, const bayer_pair_t* pairs, int n, const Config&
   m->h_prefix[(n + 1) + n] = pr;
   *me_total = me;
   *pr_total = pr;
+  // classes: runs of equal frame size in schedule order, consecutive runs
+  // merged until a class holds at least an eighth of the search items (each
+  // class ends in a launch boundary whose last wave runs part-full, so small
+  // classes cost more than they gain); at most kMaxClasses
+  Classes& c = m->classes;
+  c.n = 0;
+  if (!cfg.classes) return;
+  std::vector<int> run_end;
+  for (int k = 1; k <= n; ++k)
+    if (k == n || pairs[(*perm)[k]].W != pairs[(*perm)[k - 1]].W || pairs[(*perm)[k]].H != pairs[(*perm)[k - 1]].H)
+      run_end.push_back(k);
+  const int min_items = (me + kMaxClasses - 1) / kMaxClasses;
+  int k0 = 0;
+  for (size_t r = 0; r < run_end.size(); ++r) {
+    const int k1 = run_end[r];
+    const bool last = r + 1 == run_end.size();
+    if (!last && (m->h_prefix[k1] - m->h_prefix[k0] < min_items || c.n == kMaxClasses - 1)) continue;
+    c.me0[c.n] = m->h_prefix[k0];
+    c.me1[c.n] = m->h_prefix[k1];
+    c.pr0[c.n] = m->h_prefix[(n + 1) + k0];
+    c.pr1[c.n] = m->h_prefix[(n + 1) + k1];
+    ++c.n;
+    k0 = k1;
+  }
 }
 
 // Propagation items of all pairs: the size of the stamp array.
@@ -402,18 +451,35 @@ cudaError_t ensure_stamps(MultiStream* m, long long items) {
   return cudaSuccess;
 }
 
-// Search launch, propagation launch, end times (the graph body).
+cudaError_t search_items(MultiStream* m, int n, int range, const Config& cfg, int i0, int i1, cudaStream_t st) {
+  return cfg.nw == 4 ? ms_me_dispatch<4>(range, m->d_pairs, m->d_prefix, n, i0, i1, m->d_ctr, st)
+                     : ms_me_dispatch<8>(range, m->d_pairs, m->d_prefix, n, i0, i1, m->d_ctr, st);
+}
+
+cudaError_t prop_items(MultiStream* m, int n, int interp, int i0, int i1, cudaStream_t st) {
+  if (i1 <= i0) return cudaSuccess;
+  ms_prop_kernel<<<i1 - i0, kPropThreads, 0, st>>>(m->d_pairs, m->d_prefix + (n + 1), n, m->d_stamp, interp, i0);
+  return cudaGetLastError();
+}
+
+// The graph body.  One search launch and one propagation launch over all
+// pairs; or (classes) per class of frame sizes, smallest first, a search
+// launch and that class's propagation launch, so that the smaller frames'
+// pairs complete early in the step.  Then the end times.
 cudaError_t enqueue(MultiStream* m, int n, int range, int interp, const Config& cfg, int me_total, int pr_total,
                     cudaStream_t st) {
   // start time = max, lowered by atomicMin
   cudaError_t e = cudaMemsetAsync(&m->d_ctr->t0, 0xFF, sizeof(unsigned long long), st);
-  const int has_prop = pr_total > 0 ? 1 : 0;
-  if (e == cudaSuccess)
-    e = cfg.nw == 4 ? ms_me_dispatch<4>(range, m->d_pairs, m->d_prefix, n, me_total, m->d_ctr, st)
-                    : ms_me_dispatch<8>(range, m->d_pairs, m->d_prefix, n, me_total, m->d_ctr, st);
-  if (e == cudaSuccess && has_prop) {
-    ms_prop_kernel<<<pr_total, kPropThreads, 0, st>>>(m->d_pairs, m->d_prefix + (n + 1), n, m->d_stamp, interp);
-    e = cudaGetLastError();
+  if (cfg.classes) {
+    // each class's propagation right after its search
+    const Classes& c = m->classes;
+    for (int k = 0; k < c.n && e == cudaSuccess; ++k) {
+      e = search_items(m, n, range, cfg, c.me0[k], c.me1[k], st);
+      if (e == cudaSuccess) e = prop_items(m, n, interp, c.pr0[k], c.pr1[k], st);
+    }
+  } else {
+    if (e == cudaSuccess) e = search_items(m, n, range, cfg, 0, me_total, st);
+    if (e == cudaSuccess) e = prop_items(m, n, interp, 0, pr_total, st);
   }
   if (e == cudaSuccess) {
     ms_end_kernel<<<n, 256, 0, st>>>(m->d_stamp, m->d_prefix, n, m->d_ctr, m->d_end);
@@ -444,24 +510,48 @@ cudaError_t upload(MultiStream* m, int n, cudaStream_t st) {
 
 }  // namespace
 
+bool ms_schedule_valid(int code) {
+  return code == 40 || code == 41 || code == 80 || code == 81 || code == 142 || code == 182;
+}
+
 cudaError_t ms_run(MultiStream* m, const bayer_pair_t* pairs, int n, int range, int interp, long long* end_ns,
-                   cudaStream_t st) {
+                   int force, cudaStream_t st) {
   cudaError_t e = ensure_capacity(m, n);
   if (e != cudaSuccess) return e;
   if ((e = ensure_stamps(m, max_items(pairs, n, interp))) != cudaSuccess) return e;
-  const std::string key = signature(pairs, n, range, interp);
+  // a requested schedule has a graph of its own beside the autotuned one
+  const std::string key = signature(pairs, n, range, interp) + (force ? ":" + std::to_string(force) : "");
   std::vector<int> perm;
   int me_total = 0, pr_total = 0;
   auto it = m->cache.find(key);
-  if (it == m->cache.end()) {
-    // autotune: time every schedule on this set of pairs
-    const Config cands[4] = {{8, 0}, {8, 1}, {4, 0}, {4, 1}};
-    float best_ms = 1e30f;
-    Config best = cands[0];
+  if (it == m->cache.end() && force) {
+    const Config cfg = {force % 100 / 10, force % 10, force / 100};
+    MultiStream::Entry entry;
+    entry.cfg = cfg;
+    if ((e = cudaEventSynchronize(m->copied)) != cudaSuccess) return e;
+    build_table(m, pairs, n, cfg, interp, &me_total, &pr_total, &perm);
+    cudaGraph_t g = nullptr;
+    if ((e = cudaStreamBeginCapture(m->capture, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+    cudaError_t ec = enqueue(m, n, range, interp, cfg, me_total, pr_total, m->capture);
+    e = cudaStreamEndCapture(m->capture, &g);
+    if (ec != cudaSuccess) e = ec;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&entry.exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) return e;
+    it = m->cache.emplace(key, entry).first;
+  } else if (it == m->cache.end()) {
+    // autotune: time every schedule on this set of pairs; keep the one with the
+    // lowest median per-pair completion time among those whose step time is
+    // within 3 % of the fastest
+    constexpr int NC = 6;
+    const Config cands[NC] = {{8, 0, 0}, {8, 1, 0}, {4, 0, 0}, {4, 1, 0}, {8, 2, 1}, {4, 2, 1}};
+    float ms_of[NC], p50_of[NC];
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    for (const Config& c : cands) {
+    std::vector<long long> ends(n);
+    for (int ci = 0; ci < NC; ++ci) {
+      const Config& c = cands[ci];
       if ((e = cudaEventSynchronize(m->copied)) != cudaSuccess) break;
       build_table(m, pairs, n, c, interp, &me_total, &pr_total, &perm);
       if ((e = upload(m, n, st)) != cudaSuccess) break;
@@ -469,17 +559,24 @@ cudaError_t ms_run(MultiStream* m, const bayer_pair_t* pairs, int n, int range, 
       cudaEventRecord(e0, st);
       if ((e = enqueue(m, n, range, interp, c, me_total, pr_total, st)) != cudaSuccess) break;
       cudaEventRecord(e1, st);
-      if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < best_ms) {
-        best_ms = ms;
-        best = c;
-      }
+      if ((e = cudaMemcpyAsync(ends.data(), m->d_end, sizeof(long long) * n, cudaMemcpyDeviceToHost, st)) !=
+          cudaSuccess)
+        break;
+      if ((e = cudaStreamSynchronize(st)) != cudaSuccess) break;
+      cudaEventElapsedTime(&ms_of[ci], e0, e1);
+      std::vector<long long> sorted = ends;
+      std::nth_element(sorted.begin(), sorted.begin() + n / 2, sorted.end());
+      p50_of[ci] = (float)sorted[n / 2];
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (e != cudaSuccess) return e;
+    float fastest = 1e30f;
+    for (int ci = 0; ci < NC; ++ci) fastest = ms_of[ci] < fastest ? ms_of[ci] : fastest;
+    int pick = -1;
+    for (int ci = 0; ci < NC; ++ci)
+      if (ms_of[ci] <= 1.03f * fastest && (pick < 0 || p50_of[ci] < p50_of[pick])) pick = ci;
+    const Config best = cands[pick];
     // capture the graph of the chosen schedule on the private stream
     MultiStream::Entry entry;
     entry.cfg = best;
@@ -508,9 +605,9 @@ cudaError_t ms_run(MultiStream* m, const bayer_pair_t* pairs, int n, int range, 
   return e;
 }
 
-int ms_config_nw(MultiStream* m, const bayer_pair_t* pairs, int n, int range, int interp) {
-  auto it = m->cache.find(signature(pairs, n, range, interp));
-  return it == m->cache.end() ? 0 : it->second.cfg.nw * 10 + it->second.cfg.order;
+int ms_config_nw(MultiStream* m, const bayer_pair_t* pairs, int n, int range, int interp, int force) {
+  auto it = m->cache.find(signature(pairs, n, range, interp) + (force ? ":" + std::to_string(force) : ""));
+  return it == m->cache.end() ? 0 : it->second.cfg.classes * 100 + it->second.cfg.nw * 10 + it->second.cfg.order;
 }
 
 }  // namespace bme

@@ -46,7 +46,7 @@ def test_multi_stream_exact(handle, search_range):
         streams = make(seed + search_range)
         sched = handle.multi_stream(streams, search_range, end_ns=end)
         torch.cuda.synchronize()
-        assert sched in (40, 41, 80, 81)
+        assert sched in (40, 41, 80, 81, 142, 182)
         assert handle.sync_status() == bm.OK
         assert (end.cpu().numpy() > 0).all()
         for q in streams:
@@ -67,14 +67,21 @@ def test_multi_stream_rejects_bad_sizes(handle):
     mv = torch.empty((2, 4, 2), dtype=torch.int32, device="cuda")
     with pytest.raises(bm.BayerError):
         handle.multi_stream([{"ref": fr, "cur": fr, "mv": mv}], 32)  # H not a multiple of 16
+    gr = torch.zeros((32, 64), dtype=torch.int16, device="cuda")
+    with pytest.raises(bm.BayerError) as err:
+        handle.multi_stream([{"ref": gr, "cur": gr, "mv": mv}], 32, schedule=43)  # no such schedule
+    assert err.value.status == bm.ERR_INVALID_ARG
 
 
-def test_multi_stream_bench_configuration(handle):
+@pytest.mark.parametrize("schedule", [0, 40, 142])
+def test_multi_stream_bench_configuration(handle, schedule):
     """The benchmark's batched configuration: 32 streams (8x 640x480, 8x
     1280x720, 12x 1920x1088, 4x 3840x2160), one pair each, +-32, bilinear
-    propagation of 256-channel stride-8 maps, in one call.  Every pair equals
+    propagation of 256-channel stride-8 maps, in one call -- autotuned, and
+    pinned to the two-launch and to the per-size schedule.  Every pair equals
     the single-pair search and propagation launches bit for bit; one pair of
-    each size is checked against the oracle (whole MV field, whole map)."""
+    each size is checked against the oracle (whole MV field, whole map).  The
+    per-size schedule completes every 640x480 pair before any 3840x2160 one."""
     sizes = [(480, 640)] * 8 + [(720, 1280)] * 8 + [(1088, 1920)] * 12 + [(2160, 3840)] * 4
     C, s = 256, 8
     streams = []
@@ -87,10 +94,14 @@ def test_multi_stream_bench_configuration(handle):
                         "feat_np": f, "feat": torch.from_numpy(f).cuda(),
                         "feat_out": torch.empty((C, H // s, W // s), device="cuda"), "stride": s})
     end = torch.zeros(len(sizes), dtype=torch.int64, device="cuda")
-    handle.multi_stream(streams, 32, end_ns=end)
+    got_sched = handle.multi_stream(streams, 32, end_ns=end, schedule=schedule)
     torch.cuda.synchronize()
     assert handle.sync_status() == bm.OK
-    assert (end.cpu().numpy() > 0).all()
+    assert got_sched in (40, 41, 80, 81, 142, 182) and (schedule == 0 or got_sched == schedule)
+    e = end.cpu().numpy()
+    assert (e > 0).all()
+    if got_sched >= 100:
+        assert e[:8].max() < e[-4:].min()
     checked = set()
     for q, (H, W) in zip(streams, sizes):
         single = handle.estimate(q["ref"], q["cur"], 16, 32)
