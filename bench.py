@@ -72,7 +72,8 @@ ME_SOURCES = ("paper_2508_05990_b300/csrc/me_full16.cu", "paper_2508_05990_b300/
               "paper_2508_05990_b300/csrc/common.cuh", "paper_2508_05990_b300/csrc/tma.cuh",
               "paper_2508_05990_b300/csrc/tc_common.cuh")
 PROP_SOURCES = ("paper_2508_05990_b300/csrc/propagate.cu", "paper_2508_05990_b300/csrc/prop_common.cuh",
-                "paper_2508_05990_b300/csrc/common.cuh")
+                "paper_2508_05990_b300/csrc/common.cuh", "paper_2508_05990_b300/csrc/tma.cuh",
+                "paper_2508_05990_b300/csrc/tc_common.cuh")
 
 
 def profiled_traffic(summary: str, sources) -> int | None:

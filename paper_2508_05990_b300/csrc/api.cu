@@ -417,6 +417,7 @@ bayer_status_t bayer_feat_propagate(bayer_me_t h, const float* feat, int n, int 
   if (ob < fb + bytes && fb < ob + bytes) return BAYER_ERR_INVALID_ARG;  // out overlaps feat
   DeviceGuard g(h->device);
   bme::PropArgs a{feat, out, n, C, Hf, Wf, mv, mv_h, mv_w, block / stride, stride};
+  a.status = h->d_status;
   return cuda_status(bme::launch_propagate(a, layout, interp, static_cast<cudaStream_t>(stream)));
 }
 
@@ -475,6 +476,7 @@ bayer_status_t bayer_clip_process_host(bayer_me_t h, const uint16_t* frames, int
     e = cudaStreamWaitEvent(h->s_comp, ev_in[t], 0);
     bme::PropArgs a{h->d_feat + map_elems * t, h->d_fout + map_elems * t, 1, C, Hf, Wf, h->d_mv + field * t,
                     h_, w_, block / stride, stride};
+    a.status = h->d_status;
     if (e == cudaSuccess) e = bme::launch_propagate(a, BAYER_LAYOUT_NCHW, interp, h->s_comp);
     if (e == cudaSuccess) e = cudaEventRecord(ev_done[t], h->s_comp);
   }

@@ -59,6 +59,7 @@ struct PropArgs {
   int cells;  // feature cells per block side = block / stride
   int s;      // stride (a power of two dividing the block size)
   int ls, lc;  // log2(s), log2(cells): filled in by launch_propagate
+  int* status = nullptr;  // device status word: BAYER_ERR_TIMEOUT if a bounded wait expired
 };
 cudaError_t launch_propagate(const PropArgs& a, int layout, int interp, cudaStream_t st);
 

@@ -1,4 +1,5 @@
-// Tensor-memory-accelerator (TMA) tile loads of uint16 frame stacks: the
+// Tensor-memory-accelerator (TMA) tile loads of uint16 frame stacks and of
+// float32 feature planes: the
 // host-side tensor map (cuTensorMapEncodeTiled, fetched from the driver
 // through the runtime so nothing links libcuda) and the device-side bulk
 // tensor copy that completes on an mbarrier.
@@ -6,8 +7,8 @@
 // Rules kept by every caller: the global base is 16-byte aligned, the row
 // pitch and the frame stride are multiples of 16 bytes, the box's inner extent
 // is a multiple of 16 bytes, and the innermost start coordinate x is a
-// multiple of 8 elements (16 bytes).  Other coordinates may lie outside the
-// frame (loads there read zeros); only loads are issued.
+// multiple of 16 bytes (8 uint16 or 4 float32 elements).  Other coordinates
+// may lie outside the frame (loads there read zeros); only loads are issued.
 #pragma once
 
 #include <cuda.h>
@@ -21,24 +22,31 @@
 namespace bme {
 namespace tma {
 
-// A rank-3 map over n frames of H x W uint16 samples (row pitch and frame
-// stride in elements), box box_w x box_h x 1, out-of-range samples read as 0.
-// Returns false (map unusable) when the driver entry point is missing or the
-// layout breaks an alignment rule.
-inline bool encode_u16_frames(CUtensorMap* map, const void* base, int W, int H, int n, long long pitch,
-                              long long frame_stride, int box_w, int box_h) {
-  using Fn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*, const cuuint64_t*,
-                          const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
-                          CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-  static Fn fn = nullptr;
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled, looked up once through the runtime (null if missing).
+inline EncodeFn encode_fn() {
+  static EncodeFn fn = nullptr;
   static std::once_flag once;
   std::call_once(once, [] {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<Fn>(p);
+      fn = reinterpret_cast<EncodeFn>(p);
   });
+  return fn;
+}
+
+// A rank-3 map over n frames of H x W uint16 samples (row pitch and frame
+// stride in elements), box box_w x box_h x 1, out-of-range samples read as 0.
+// Returns false (map unusable) when the driver entry point is missing or the
+// layout breaks an alignment rule.
+inline bool encode_u16_frames(CUtensorMap* map, const void* base, int W, int H, int n, long long pitch,
+                              long long frame_stride, int box_w, int box_h) {
+  const EncodeFn fn = encode_fn();
   if (!fn) return false;
   if ((reinterpret_cast<uintptr_t>(base) & 15) || ((pitch * 2) & 15) || ((box_w * 2) & 15)) return false;
   if (n > 1 && (frame_stride <= 0 || ((frame_stride * 2) & 15))) return false;
@@ -49,6 +57,26 @@ inline bool encode_u16_frames(CUtensorMap* map, const void* base, int W, int H, 
   const cuuint32_t box[3] = {(cuuint32_t)box_w, (cuuint32_t)box_h, 1};
   const cuuint32_t estride[3] = {1, 1, 1};
   return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, const_cast<void*>(base), dims, strides, box, estride,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// A rank-3 map over `planes` contiguous H x W float32 planes (row pitch W,
+// plane stride H * W elements), box box_w x box_h x 1, out-of-range elements
+// read as 0.  Returns false when the driver entry point is missing or the
+// layout breaks an alignment rule (16-byte base, row pitch and plane stride
+// multiples of 16 bytes, box_w a multiple of 4).
+inline bool encode_f32_planes(CUtensorMap* map, const void* base, int W, int H, long long planes, int box_w,
+                              int box_h) {
+  const EncodeFn fn = encode_fn();
+  if (!fn) return false;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || ((4ll * W) & 15) || ((4ll * W * H) & 15) || (box_w & 3)) return false;
+  if (box_w > 256 || box_h > 256 || box_w < 1 || box_h < 1 || planes < 1) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)planes};
+  const cuuint64_t strides[2] = {(cuuint64_t)(4ll * W), (cuuint64_t)(4ll * W * H)};
+  const cuuint32_t box[3] = {(cuuint32_t)box_w, (cuuint32_t)box_h, 1};
+  const cuuint32_t estride[3] = {1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, estride,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
