@@ -29,7 +29,9 @@ Activations: the network's definition stores each post-ReLU activation in
 bfloat16 (weights are bfloat16 too).  ``act_round="bf16"`` applies that
 rounding (round to nearest, ties to even, of the float32 value) at the same
 points; ``act_round=None`` keeps every activation in float64, the exact
-reference.
+reference.  Training stores each layer's pre-activation gradient in bfloat16
+too (the operand of that layer's weight- and input-gradient products);
+``grad_round="bf16"`` rounds it there.
 
 Parameters are one flat vector (``param_layout``); the CUDA path uses the same
 order.  Every function below is plain numpy; the convolution uses einsum over
@@ -167,10 +169,11 @@ def berhu_grad(e, c=BERHU_C):
     return np.where(np.abs(e) <= c, np.sign(e), e / c)
 
 
-def loss_and_grad(theta, ref, cur, label_dx, label_dy, search_range: int, act_round=None, neg_weight=1.0):
+def loss_and_grad(theta, ref, cur, label_dx, label_dy, search_range: int, act_round=None, neg_weight=1.0,
+                  grad_round=None):
     """Mean loss over blocks and its gradient w.r.t. theta (float64)."""
     loss, cache, dz = loss_and_dz(theta, ref, cur, label_dx, label_dy, search_range, act_round, neg_weight)
-    return loss, backward(cache, dz)
+    return loss, backward(cache, dz, grad_round)
 
 
 def loss_and_dz(theta, ref, cur, label_dx, label_dy, search_range: int, act_round=None, neg_weight=1.0):
@@ -191,8 +194,13 @@ def loss_and_dz(theta, ref, cur, label_dx, label_dy, search_range: int, act_roun
     return loss, cache, dz
 
 
-def backward(cache, dz):
+def backward(cache, dz, grad_round=None):
+    """Gradient w.r.t. theta.  ``grad_round="bf16"``: each layer's
+    pre-activation gradient is rounded to bfloat16 (as the network's training
+    definition stores it) before it enters that layer's weight and input
+    gradients; otherwise it stays float64."""
     p, acts, pre = cache["p"], cache["acts"], cache["pre"]
+    rnd = round_bf16 if grad_round == "bf16" else (lambda v: v)
     x4 = acts[-1]
     h4, w4 = x4.shape[1:]
     dzh = np.zeros((12, h4, w4))
@@ -203,7 +211,7 @@ def backward(cache, dz):
     g = {"wh": np.einsum("jhw,chw->jc", dzh, x4), "bh": dzh.sum(axis=(1, 2))}
     da = np.einsum("jc,jhw->chw", p["wh"], dzh)
     for l in reversed(range(N_LAYERS)):
-        dpre = da * (pre[l] > 0)
+        dpre = rnd(da * (pre[l] > 0))
         dxin, g[f"w{l + 1}"], g[f"b{l + 1}"] = conv3x3s2_backward(acts[l], p[f"w{l + 1}"], dpre)
         da = dxin
     return flatten(g)

@@ -86,16 +86,17 @@ def cnn_logits(theta, ref, cur, search_range, act_round=None):
     return c["z"], _to_blocks(mh), (dx, dy, conf)
 
 
-def cnn_grad_magnitudes(theta, ref, cur, label_dx, label_dy, search_range, neg_weight=1.0, act_round=None):
+def cnn_grad_magnitudes(theta, ref, cur, label_dx, label_dy, search_range, neg_weight=1.0, act_round=None,
+                        grad_round=None):
     """(gradient, M): the oracle's gradient and, per parameter, the sum of the
     absolute values of every term of its expansion -- the oracle's own
     backward pass run on |dL/dz|, |weights| and |activations| (the ReLU masks
     unchanged), so that every product and sum of the chain rule adds
     magnitudes."""
     _, cache, dz = cnn.loss_and_dz(theta, ref, cur, label_dx, label_dy, search_range, act_round, neg_weight)
-    g = cnn.backward(cache, dz)
+    g = cnn.backward(cache, dz, grad_round)
     cache_abs = dict(cache, p={k: np.abs(v) for k, v in cache["p"].items()}, acts=[np.abs(a) for a in cache["acts"]])
-    return g, cnn.backward(cache_abs, np.abs(dz))
+    return g, cnn.backward(cache_abs, np.abs(dz), grad_round)
 
 
 # The GPU evaluates tanhf and expf in float32: a few units in the last place.

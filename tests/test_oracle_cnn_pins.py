@@ -119,3 +119,46 @@ def test_refine_conv_matches_torch():
     t = F.conv2d(t, torch.from_numpy(w3), torch.zeros(16, dtype=torch.float64), padding=1)
     np.testing.assert_allclose(refine.refine(x, w, b, w2, np.zeros(8), w3, np.zeros(16)),
                                t[0].numpy().transpose(1, 2, 0), rtol=1e-11, atol=1e-11)
+
+
+def test_gradient_rounding_matches_torch_hooks():
+    """grad_round="bf16" rounds each layer's pre-activation gradient: the same
+    network in torch float64 with a backward hook on every pre-activation that
+    rounds its gradient to bfloat16 (float32 first) gives the same gradient."""
+    ref, cur = synth.pan_clip(7, 64, 96, n_frames=2, rect_size=(8, 24))
+    theta = synth.he_normal_params(13, shapes()).astype(np.float64)
+    R = 32
+    rng = np.random.default_rng(9)
+    ldx = 2.0 * rng.integers(-16, 17, (4, 6))
+    ldy = 2.0 * rng.integers(-16, 17, (4, 6))
+    _, g = cnn.loss_and_grad(theta, ref, cur, ldx, ldy, R, grad_round="bf16")
+    _, g_exact = cnn.loss_and_grad(theta, ref, cur, ldx, ldy, R)
+    assert not np.allclose(g, g_exact, rtol=1e-6, atol=0)  # the rounding is there
+
+    def rnd(t):
+        return torch.from_numpy(cnn.round_bf16(t.detach().numpy()))
+
+    p = {k: torch.from_numpy(v).requires_grad_(True) for k, v in cnn.unflatten(theta).items()}
+    x = torch.from_numpy(cnn.pack(ref, cur))[None]
+    for l in range(4):
+        z = F.conv2d(x, p[f"w{l + 1}"], p[f"b{l + 1}"], stride=2, padding=1)
+        z.register_hook(rnd)
+        x = F.relu(z)
+    zh = torch.einsum("jc,bchw->bjhw", p["wh"], x) + p["bh"][None, :, None, None]
+    h4, w4 = zh.shape[2:]
+    z = zh[0].reshape(2, 2, 3, h4, w4).permute(2, 3, 0, 4, 1).reshape(3, 2 * h4, 2 * w4)
+    tdx, tdy, tconf = R * torch.tanh(z[0]), R * torch.tanh(z[1]), torch.sigmoid(z[2])
+    dx = tdx.detach().numpy()
+    dy = tdy.detach().numpy()
+    t = ((np.abs(cnn.round_even(dx) - ldx) <= 4) & (np.abs(cnn.round_even(dy) - ldy) <= 4)).astype(np.float64)
+    c = cnn.BERHU_C
+
+    def bh(e):
+        a = e.abs()
+        return torch.where(a <= c, a, (e * e + c * c) / (2 * c))
+    tt = torch.from_numpy(t)
+    tl = (bh(tdx - torch.from_numpy(ldx)) + bh(tdy - torch.from_numpy(ldy))
+          - (tt * torch.log(tconf + 1e-12) + (1 - tt) * torch.log(1 - tconf + 1e-12))).mean()
+    tl.backward()
+    tg = np.concatenate([p[n].grad.numpy().ravel() for n, _ in cnn.param_layout()])
+    np.testing.assert_allclose(g, tg, rtol=1e-9, atol=1e-13)
