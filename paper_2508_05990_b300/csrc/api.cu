@@ -226,6 +226,7 @@ bayer_status_t bayer_me_init(bayer_me_t* out, int device) {
   if (e == cudaSuccess) e = bme::configure_conv_tc();
   if (e == cudaSuccess) e = bme::configure_conv_s2_rows_tc();
   if (e == cudaSuccess) e = bme::configure_conv_rows_tc();
+  if (e == cudaSuccess) e = bme::configure_conv_bwd_tc();
   if (e == cudaSuccess) e = cudaMalloc(&h->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking);

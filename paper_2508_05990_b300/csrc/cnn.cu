@@ -11,9 +11,11 @@
 //       is quantity q of block (2i + sy, 2k + sx)
 //   dx = range*tanh(z_0), dy = range*tanh(z_1), conf = sigmoid(z_2)
 // Activations are NHWC bf16 [B][H][W][32].  The four convolutions run on the
-// tensor cores (conv_tc.cu; layer 1 gathers the Bayer frames directly, the
-// packing fused into its operand staging; in inference the head is evaluated
-// in layer 4's epilogue); the training head, loss and backward are SIMT.
+// tensor cores (conv_s2_tc.cu, conv_tc.cu; layer 1 gathers the Bayer frames
+// directly, the packing fused into its operand staging; in inference the head
+// is evaluated in layer 4's epilogue), and so do the convolutions' input and
+// weight gradients (conv_bwd_tc.cu), on bf16 pre-activation gradients; the
+// training head and loss are SIMT (one thread per layer-4 cell).
 // Loss per block:
 //   BerHu_4(dx - dx*) + BerHu_4(dy - dy*) - t log(conf) - w_neg (1 - t) log(1 - conf),
 //   t = [round_even(dx) within +-4 of dx* and likewise for dy],
@@ -22,6 +24,7 @@
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "tc_common.cuh"
 
 namespace bme {
 
@@ -41,21 +44,6 @@ __device__ __forceinline__ void unpack8(const uint4 u, float* f) {
   }
 }
 
-// Layer-1 input sample: channel ci (0..7) at half-resolution (hy, hx), zero
-// outside the half-resolution map.
-__device__ __forceinline__ float l1_input(const uint16_t* ref, const uint16_t* cur, int pitch, int Hh, int Wh, int ci,
-                                          int hy, int hx) {
-  if (hy < 0 || hy >= Hh || hx < 0 || hx >= Wh) return 0.f;
-  const uint16_t* f = ci < 4 ? ref : cur;
-  const int p = ci & 3;
-  const int y = 2 * hy + (p >> 1), x = 2 * hx + (p & 1);
-  return (float)__ldg(f + (long long)y * pitch + x) * (1.0f / 2048.0f) - 1.0f;
-}
-
-// ---------------------------------------------------------------------------
-// forward
-// ---------------------------------------------------------------------------
-
 // ---------------------------------------------------------------------------
 // training: loss and gradients
 // ---------------------------------------------------------------------------
@@ -70,12 +58,13 @@ __device__ __forceinline__ float berhu_grad(float e) {
 }
 
 // Head forward + loss + head backward.  One thread per L4 cell.  Writes
-// dpre4 = dL/d(L4 pre-activation) (fp32 NHWC), accumulates dL/d(head w, b)
-// into grad and the loss sum into *loss (both already scaled by 1/n).
+// dpre4 = dL/d(L4 pre-activation) (bf16 NHWC, rounded to nearest even),
+// accumulates dL/d(head w, b) into grad and the loss sum into *loss (both
+// already scaled by 1/n).
 __global__ void __launch_bounds__(128) head_loss_bwd_kernel(const __nv_bfloat16* __restrict__ x4, int H4, int W4,
                                                             const __nv_bfloat16* __restrict__ w, int range,
                                                             const bayer_mv_t* __restrict__ labels, float inv_n,
-                                                            float neg_w, float* __restrict__ dpre4,
+                                                            float neg_w, __nv_bfloat16* __restrict__ dpre4,
                                                             float* __restrict__ grad,
                                                             float* __restrict__ loss) {
   __shared__ float wh[12 * kC + 12];
@@ -124,14 +113,19 @@ __global__ void __launch_bounds__(128) head_loss_bwd_kernel(const __nv_bfloat16*
       dz[3 * s + 2] = (cf * (tgt + neg_w * (1.f - tgt)) - tgt) * inv_n;
     }
     // d x4, masked by ReLU (x4 > 0 iff its pre-activation > 0)
-    float* dst = dpre4 + ((long long)b * cells + t) * kC;
+    float d[kC];
 #pragma unroll
     for (int c = 0; c < kC; ++c) {
       float a = 0.f;
 #pragma unroll
       for (int j = 0; j < 12; ++j) a = fmaf(wh[j * kC + c], dz[j], a);
-      dst[c] = x[c] > 0.f ? a : 0.f;
+      d[c] = x[c] > 0.f ? a : 0.f;
     }
+    uint4* dst = reinterpret_cast<uint4*>(dpre4 + ((long long)b * cells + t) * kC);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      dst[q] = make_uint4(tc::bf2(d[8 * q], d[8 * q + 1]), tc::bf2(d[8 * q + 2], d[8 * q + 3]),
+                          tc::bf2(d[8 * q + 4], d[8 * q + 5]), tc::bf2(d[8 * q + 6], d[8 * q + 7]));
 #pragma unroll
     for (int j = 0; j < 12; ++j) {
 #pragma unroll
@@ -143,128 +137,6 @@ __global__ void __launch_bounds__(128) head_loss_bwd_kernel(const __nv_bfloat16*
   __syncthreads();
   for (int i = threadIdx.x; i < 12 * kC + 12; i += blockDim.x) atomicAdd(&grad[BAYER_CNN_WH + i], gsum[i]);
   if (threadIdx.x == 0) atomicAdd(loss, lsum);
-}
-
-// dX of a stride-2 3x3 conv (32 -> 32), masked by ReLU of the layer below:
-// dpre_in[b, iy, ix, ci] = [x_in > 0] * sum_{taps, co} dpre_out[b, oy, ox, co] * w[co, ci, tap]
-// with iy = 2 oy + ky - 1.  One thread per input pixel.
-__global__ void __launch_bounds__(128) conv_bwd_data_kernel(const float* __restrict__ dout, int Ho, int Wo,
-                                                            const __nv_bfloat16* __restrict__ w,
-                                                            const __nv_bfloat16* __restrict__ xin, int Hi, int Wi,
-                                                            float* __restrict__ din) {
-  __shared__ __align__(16) float wt[9 * kC * kC];  // [tap][co][ci]
-  for (int i = threadIdx.x; i < 9 * kC * kC; i += blockDim.x) {
-    const int tap = i / (kC * kC), r = i - tap * kC * kC, co = r / kC, ci = r - co * kC;
-    wt[i] = bf(w[co * 288 + ci * 9 + tap]);
-  }
-  __syncthreads();
-  const int b = blockIdx.z, iy = blockIdx.y;
-  const int ix = blockIdx.x * blockDim.x + threadIdx.x;
-  if (ix >= Wi) return;
-  float acc[kC];
-#pragma unroll
-  for (int c = 0; c < kC; ++c) acc[c] = 0.f;
-  for (int ky = 0; ky < 3; ++ky) {
-    const int ny = iy + 1 - ky;
-    if (ny < 0 || (ny & 1)) continue;
-    const int oy = ny >> 1;
-    if (oy >= Ho) continue;
-    for (int kx = 0; kx < 3; ++kx) {
-      const int nx = ix + 1 - kx;
-      if (nx < 0 || (nx & 1)) continue;
-      const int ox = nx >> 1;
-      if (ox >= Wo) continue;
-      const float4* dr = reinterpret_cast<const float4*>(dout + (((long long)b * Ho + oy) * Wo + ox) * kC);
-      const int tap = ky * 3 + kx;
-#pragma unroll 2
-      for (int q = 0; q < 8; ++q) {
-        const float4 d4 = __ldg(dr + q);
-        const float dv[4] = {d4.x, d4.y, d4.z, d4.w};
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const float4* wr = reinterpret_cast<const float4*>(wt + (tap * kC + 4 * q + e) * kC);
-#pragma unroll
-          for (int m = 0; m < 8; ++m) {
-            const float4 wv = wr[m];
-            acc[4 * m + 0] = fmaf(dv[e], wv.x, acc[4 * m + 0]);
-            acc[4 * m + 1] = fmaf(dv[e], wv.y, acc[4 * m + 1]);
-            acc[4 * m + 2] = fmaf(dv[e], wv.z, acc[4 * m + 2]);
-            acc[4 * m + 3] = fmaf(dv[e], wv.w, acc[4 * m + 3]);
-          }
-        }
-      }
-    }
-  }
-  float xv[kC];
-  const uint4* xs = reinterpret_cast<const uint4*>(xin + (((long long)b * Hi + iy) * Wi + ix) * kC);
-#pragma unroll
-  for (int q = 0; q < 4; ++q) unpack8(__ldg(xs + q), xv + 8 * q);
-  float4* dst = reinterpret_cast<float4*>(din + (((long long)b * Hi + iy) * Wi + ix) * kC);
-#pragma unroll
-  for (int q = 0; q < 8; ++q)
-    dst[q] = make_float4(xv[4 * q] > 0.f ? acc[4 * q] : 0.f, xv[4 * q + 1] > 0.f ? acc[4 * q + 1] : 0.f,
-                         xv[4 * q + 2] > 0.f ? acc[4 * q + 2] : 0.f, xv[4 * q + 3] > 0.f ? acc[4 * q + 3] : 0.f);
-}
-
-// dW, db of a stride-2 3x3 conv: dW[co, k] = sum_pixels dout[p, co] * patch[p, k],
-// k = ci*9 + tap (the flat weight order), db[co] = sum_p dout[p, co].  Each CTA
-// walks output pixels in chunks of 32 (grid-stride), stages the chunk's dout rows
-// and input patches in shared memory, keeps its partial sums in registers (thread
-// = one co and KPT consecutive k) and adds them to grad once at the end.
-template <int CIN, bool FRAMES>
-__global__ void __launch_bounds__(256) conv_bwd_w_kernel(const float* __restrict__ dout, int Ho, int Wo, int B,
-                                                         const __nv_bfloat16* __restrict__ xin, int Hi, int Wi,
-                                                         CnnFrames fr, float* __restrict__ gw, float* __restrict__ gb) {
-  constexpr int K = CIN * 9;
-  constexpr int KPT = K / 8;  // k per thread (8 threads per co)
-  constexpr int PCH = 32;     // pixels per chunk
-  __shared__ __align__(16) float ds[PCH][kC];
-  __shared__ __align__(16) float xs[PCH][K];
-  const int co = threadIdx.x >> 3, kg = threadIdx.x & 7;
-  float acc[KPT];
-#pragma unroll
-  for (int j = 0; j < KPT; ++j) acc[j] = 0.f;
-  float accb = 0.f;
-  const long long npix = (long long)B * Ho * Wo;
-  const int Hh = fr.H / 2, Wh = fr.W / 2;
-  for (long long base = (long long)blockIdx.x * PCH; base < npix; base += (long long)gridDim.x * PCH) {
-    __syncthreads();
-    for (int i = threadIdx.x; i < PCH * kC; i += blockDim.x) {
-      const int p = i / kC, c = i - p * kC;
-      const long long gp = base + p;
-      ds[p][c] = gp < npix ? dout[gp * kC + c] : 0.f;
-    }
-    for (int i = threadIdx.x; i < PCH * K; i += blockDim.x) {
-      const int p = i / K, k = i - p * K;
-      const long long gp = base + p;
-      float v = 0.f;
-      if (gp < npix) {
-        const int b = (int)(gp / ((long long)Ho * Wo));
-        const int r = (int)(gp - (long long)b * Ho * Wo);
-        const int oy = r / Wo, ox = r - oy * Wo;
-        const int ci = k / 9, tap = k - 9 * ci;
-        const int iy = 2 * oy + tap / 3 - 1, ix = 2 * ox + tap % 3 - 1;
-        if (FRAMES) {
-          v = l1_input(fr.ref + (long long)b * fr.ref_bs, fr.cur + (long long)b * fr.cur_bs, fr.pitch, Hh, Wh, ci, iy,
-                       ix);
-        } else if (iy >= 0 && iy < Hi && ix >= 0 && ix < Wi) {
-          v = bf(xin[(((long long)b * Hi + iy) * Wi + ix) * kC + ci]);
-        }
-      }
-      xs[p][k] = v;
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (int p = 0; p < PCH; ++p) {
-      const float d = ds[p][co];
-      accb += d;
-#pragma unroll
-      for (int j = 0; j < KPT; ++j) acc[j] = fmaf(d, xs[p][kg * KPT + j], acc[j]);
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < KPT; ++j) atomicAdd(&gw[co * K + kg * KPT + j], acc[j]);
-  if (kg == 0) atomicAdd(&gb[co], accb);
 }
 
 __global__ void adamw_kernel(float* __restrict__ w, __nv_bfloat16* __restrict__ wb, const float* __restrict__ g,
@@ -312,7 +184,8 @@ size_t act_elems(const CnnShapes& s, int batch) {
 }
 
 // Workspace: the bf16 activations of layers 1..4, then the packed weight
-// images of the four convolutions (256-byte aligned).
+// images of the four convolutions and the transposed images of layers 2..4
+// for the input gradient (256-byte aligned).
 size_t wimg_offset(int W, int H, int batch) {
   return (act_elems(cnn_shapes(W, H), batch) * sizeof(__nv_bfloat16) + 255) / 256 * 256;
 }
@@ -322,6 +195,10 @@ size_t wimg_bytes() {
   for (int l = 1; l <= 4; ++l) n += (conv_tc_weight_bytes(l == 1 ? 16 : 32) + 255) / 256 * 256;
   return n;
 }
+
+size_t wimg_t_offset() { return wimg_bytes(); }
+
+size_t wimg_all_bytes() { return wimg_bytes() + (conv_dx_weight_bytes() + 255) / 256 * 256; }
 
 // Forward through the four convolutions.  head: layer 4's epilogue evaluates
 // the head (activations of layer 4 are then not stored); otherwise all four
@@ -377,9 +254,11 @@ cudaError_t cnn_forward_acts(const CnnFrames& fr, int batch, const uint16_t* wbf
 
 }  // namespace
 
-size_t cnn_act_bytes(int W, int H, int batch) { return wimg_offset(W, H, batch) + wimg_bytes(); }
+size_t cnn_act_bytes(int W, int H, int batch) { return wimg_offset(W, H, batch) + wimg_all_bytes(); }
 
-size_t cnn_grad_bytes(int W, int H, int batch) { return act_elems(cnn_shapes(W, H), batch) * sizeof(float); }
+size_t cnn_grad_bytes(int W, int H, int batch) {
+  return act_elems(cnn_shapes(W, H), batch) * sizeof(__nv_bfloat16);
+}
 
 cudaError_t cnn_forward(const CnnFrames& fr, int batch, const uint16_t* wbf16, int range, void* acts, float* prop,
                         float* conf, int* status, cudaStream_t st) {
@@ -396,8 +275,8 @@ cudaError_t cnn_loss_grad(const CnnFrames& fr, int batch, const uint16_t* wbf16,
   const __nv_bfloat16* a[5];
   a[1] = static_cast<const __nv_bfloat16*>(acts);
   for (int l = 2; l <= 4; ++l) a[l] = a[l - 1] + (size_t)batch * s.H[l - 1] * s.W[l - 1] * kC;
-  float* d[5];
-  d[1] = static_cast<float*>(dpre);
+  __nv_bfloat16* d[5];
+  d[1] = static_cast<__nv_bfloat16*>(dpre);
   for (int l = 2; l <= 4; ++l) d[l] = d[l - 1] + (size_t)batch * s.H[l - 1] * s.W[l - 1] * kC;
   if ((e = cudaMemsetAsync(grad, 0, BAYER_CNN_NPARAMS * sizeof(float), st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(loss, 0, sizeof(float), st)) != cudaSuccess) return e;
@@ -409,18 +288,33 @@ cudaError_t cnn_loss_grad(const CnnFrames& fr, int batch, const uint16_t* wbf16,
   }
   const int woff[5] = {0, BAYER_CNN_W1, BAYER_CNN_W2, BAYER_CNN_W3, BAYER_CNN_W4};
   const int boff[5] = {0, BAYER_CNN_B1, BAYER_CNN_B2, BAYER_CNN_B3, BAYER_CNN_B4};
-  int nsm = 148;
-  int dev = 0;
-  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  for (int l = 4; l >= 2; --l) {
-    conv_bwd_w_kernel<32, false><<<nsm * 2, 256, 0, st>>>(d[l], s.H[l], s.W[l], batch, a[l - 1], s.H[l - 1],
-                                                           s.W[l - 1], fr, grad + woff[l], grad + boff[l]);
-    dim3 g((s.W[l - 1] + 127) / 128, s.H[l - 1], batch);
-    conv_bwd_data_kernel<<<g, 128, 0, st>>>(d[l], s.H[l], s.W[l], w + woff[l], a[l - 1], s.H[l - 1], s.W[l - 1],
-                                            d[l - 1]);
+  char* img_t = static_cast<char*>(acts) + wimg_offset(fr.W, fr.H, batch) + wimg_t_offset();
+  if ((e = pack_conv_dx_weights(wbf16, woff + 2, reinterpret_cast<uint16_t*>(img_t), st)) != cudaSuccess) return e;
+  const bool vec_atomics = (reinterpret_cast<uintptr_t>(grad) & 15) == 0;
+  const bool vec = (reinterpret_cast<uintptr_t>(fr.ref) % 4) == 0 && (reinterpret_cast<uintptr_t>(fr.cur) % 4) == 0 &&
+                   fr.pitch % 2 == 0 && fr.ref_bs % 2 == 0 && fr.cur_bs % 2 == 0;
+  for (int l = 4; l >= 1; --l) {
+    ConvBwdArgs c{};
+    c.dout = d[l];
+    c.Ho = s.H[l];
+    c.Wo = s.W[l];
+    c.xin = l > 1 ? a[l - 1] : nullptr;
+    c.fr = fr;
+    c.vec = vec;
+    c.Hi = s.H[l - 1];
+    c.Wi = s.W[l - 1];
+    c.batch = batch;
+    c.gw = grad + woff[l];
+    c.gb = grad + boff[l];
+    c.vec_atomics = vec_atomics;
+    c.status = status;
+    if ((e = launch_conv_dw_tc(c, l == 1, st)) != cudaSuccess) return e;
+    if (l > 1) {
+      c.wimg_t = reinterpret_cast<const uint4*>(img_t + (size_t)(l - 2) * (conv_dx_weight_bytes() / 3));
+      c.din = d[l - 1];
+      if ((e = launch_conv_dx_tc(c, st)) != cudaSuccess) return e;
+    }
   }
-  conv_bwd_w_kernel<8, true><<<nsm * 2, 256, 0, st>>>(d[1], s.H[1], s.W[1], batch, nullptr, 0, 0, fr,
-                                                      grad + BAYER_CNN_W1, grad + BAYER_CNN_B1);
   return cudaGetLastError();
 }
 

@@ -89,10 +89,7 @@ struct RowStreamLayout {
   static_assert(TMEM_COLS <= 512, "tensor memory");
 };
 
-__device__ __forceinline__ uint32_t bf2(float a, float b) {
-  const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
-  return *reinterpret_cast<const uint32_t*>(&v);
-}
+using tc::bf2;
 
 // The CTA's output rows [t0, t1) of the (b, segment, y)-ordered list, cut into
 // runs that stay inside one column strip.

@@ -79,21 +79,8 @@ struct S2Layout {
   static_assert(NR % G == 0, "a slot belongs to one group");
 };
 
-__device__ __forceinline__ uint32_t bf2(float a, float b) {
-  const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
-  return *reinterpret_cast<const uint32_t*>(&v);
-}
-
-// hi/lo bf16 pair of a 12-bit sample: hi = (v >> 4)/128 - 1, lo = (v & 15)/16.
-// Without integer-to-float conversions: the float with bit pattern
-// 0x4B000000 | k is 2^23 + k, so (2^23 + k)/128 - 65537 = k/128 - 1 and
-// (2^23 + m)/16 - 2^19 = m/16, each one fma whose exact result is
-// representable (so it is returned unrounded).
-__device__ __forceinline__ uint32_t split12(uint32_t v) {
-  const float hi = fmaf(__uint_as_float(0x4B000000u | (v >> 4)), 1.0f / 128.0f, -65537.0f);
-  const float lo = fmaf(__uint_as_float(0x4B000000u | (v & 15u)), 1.0f / 16.0f, -524288.0f);
-  return bf2(hi, lo);
-}
+using tc::bf2;
+using tc::split12;
 
 // The CTA's output rows [t, t1) of the (image, segment, y)-ordered list, cut
 // into runs that stay inside one column strip.

@@ -65,16 +65,10 @@ struct RowConvLayout {
   static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
-__device__ __forceinline__ uint32_t bf2(float a, float b) {
-  const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
-  return *reinterpret_cast<const uint32_t*>(&v);
-}
+using tc::bf2;
 
-// 16-byte asynchronous copy global -> shared; src_bytes 0 zero-fills.
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+using tc::cp_async16;
+using tc::cp_async_wait_all;
 
 // Weight images of the four layers (K-major B operand, all 32 output
 // channels): for a layer with cin operand channels, element (n, k), k =

@@ -75,7 +75,7 @@ struct CnnShapes {
 };
 CnnShapes cnn_shapes(int W, int H);
 size_t cnn_act_bytes(int W, int H, int batch);   // bf16 activations of layers 1..4 + packed weights
-size_t cnn_grad_bytes(int W, int H, int batch);  // fp32 pre-activation gradients of layers 1..4
+size_t cnn_grad_bytes(int W, int H, int batch);  // bf16 pre-activation gradients of layers 1..4
 cudaError_t cnn_forward(const CnnFrames& fr, int batch, const uint16_t* wbf16, int range, void* acts, float* prop,
                         float* conf, int* status, cudaStream_t st);
 cudaError_t cnn_loss_grad(const CnnFrames& fr, int batch, const uint16_t* wbf16, const bayer_mv_t* labels, int range,
@@ -114,6 +114,31 @@ cudaError_t pack_conv_tc_weights(const uint16_t* w, const int* w_off, const size
 cudaError_t launch_conv_tc(const ConvTcArgs& a, int layer, bool head, cudaStream_t st);  // layers 3, 4
 cudaError_t configure_conv_s2_rows_tc();
 cudaError_t launch_conv_s2_rows_tc(const ConvTcArgs& a, int layer, cudaStream_t st);
+
+// Backward of those convolutions on the tensor cores (conv_bwd_tc.cu): the
+// input gradient of layers 2..4 masked by the layer below's ReLU (bf16 out),
+// and the weight and bias gradients of all four layers (added to gw, gb).
+struct ConvBwdArgs {
+  const __nv_bfloat16* dout;  // [batch][Ho][Wo][32] bf16 pre-activation gradient of this layer
+  int Ho, Wo;
+  const __nv_bfloat16* xin;   // layers 2..4: [batch][Hi][Wi][32] bf16 input activation
+  CnnFrames fr;               // layer 1 (weight gradient): frames; Hi, Wi the half-resolution dims
+  bool vec;                   // layer 1: 4-byte frame loads allowed (even pitch, 4-byte aligned rows)
+  int Hi, Wi, batch;
+  const uint4* wimg_t;        // input gradient: this layer's transposed weight image
+  __nv_bfloat16* din;         // input gradient: [batch][Hi][Wi][32] bf16 out
+  float* gw;                  // weight gradient: [32][cin][3][3], accumulated
+  float* gb;                  // bias gradient: [32], accumulated
+  bool vec_atomics;           // gw 16-byte aligned: float4 atomics
+  int* status;                // device status word: BAYER_ERR_TIMEOUT if a bounded wait expired
+};
+cudaError_t configure_conv_bwd_tc();
+// Transposed weight images of layers 2..4 (the [32][32][3][3] bf16 blocks at
+// w + w_off[0..2]) for the input gradient, written to img (16-byte aligned).
+size_t conv_dx_weight_bytes();
+cudaError_t pack_conv_dx_weights(const uint16_t* w, const int* w_off, uint16_t* img, cudaStream_t st);
+cudaError_t launch_conv_dx_tc(const ConvBwdArgs& a, cudaStream_t st);
+cudaError_t launch_conv_dw_tc(const ConvBwdArgs& a, bool frames, cudaStream_t st);
 
 // 3x3 stride-1 convolution streamed row by row on the tensor cores
 // (conv_rows_tc.cu): NHWC input (bf16, or float32 rounded to bf16 when

@@ -5,14 +5,46 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 namespace bme {
 namespace tc {
 
+// Two floats as a packed bf16 pair (round to nearest even), a in the low half.
+__device__ __forceinline__ uint32_t bf2(float a, float b) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// The proposal network's layer-1 operands: a 12-bit sample v as two exact
+// bf16 values hi = (v >> 4)/128 - 1 and lo = (v & 15)/16, packed (hi low),
+// so that hi * w + lo * (w/128) = (v/2048 - 1) * w.  Without integer-to-float
+// conversions: the float with bit pattern 0x4B000000 | k is 2^23 + k, so
+// (2^23 + k)/128 - 65537 = k/128 - 1 and (2^23 + m)/16 - 2^19 = m/16, each one
+// fma whose exact result is representable (so it is returned unrounded).
+__device__ __forceinline__ uint32_t split12(uint32_t v) {
+  const float hi = fmaf(__uint_as_float(0x4B000000u | (v >> 4)), 1.0f / 128.0f, -65537.0f);
+  const float lo = fmaf(__uint_as_float(0x4B000000u | (v & 15u)), 1.0f / 16.0f, -524288.0f);
+  return bf2(hi, lo);
+}
+
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
+
+// 16-byte asynchronous copy global -> shared (dst a shared-space address);
+// src_bytes 0 zero-fills.  Copies issued since the last commit form a group.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// Wait until at most N committed groups of this thread are still in flight.
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Shared-memory matrix descriptor, no swizzle (canonical K-major layout of
 // 8-row x 16-byte core matrices): start address, leading-dimension byte offset

@@ -12,10 +12,12 @@ oracle's and within 2^-7 m_z of the bfloat16-rounded oracle's (tanh and the
 sigmoid are monotone, so this is an interval test on the outputs).
 
 Gradient, per parameter: within 2^-8 M (+ a floor of 2^-8 * 1e-3 * max M) of
-the bf16-activation oracle, M being the sum of the absolute values of every
-term of the parameter's chain-rule expansion; the two differ only in the
-order of the float32 sums (and where that flips the bfloat16 rounding or the
-ReLU mask of a value at a boundary).  Against the exact float64 oracle the
+the oracle with the network's training roundings modelled (bf16 activations
+and bf16 pre-activation gradients, the operands of the tensor-core backward),
+M being the sum of the absolute values of every term of the parameter's
+chain-rule expansion; the two differ only in the order of the float32 sums
+(and where that flips the bfloat16 rounding or the ReLU mask of a value at a
+boundary).  Against the exact float64 oracle the
 gradient is compared normwise (5e-2): rounding the activations to bfloat16
 moves the loss surface itself, ReLU masks included, so no per-parameter bound
 against the exact gradient exists (measured: 3.2 %, identical for the GPU and
@@ -91,9 +93,17 @@ def test_cnn_forward_batched_strides(handle):
         check_forward(prop[t].cpu().numpy(), conf[t].cpu().numpy(), theta, frames[t], frames[t + 1], 16)
 
 
-@pytest.mark.parametrize("neg_weight", [1.0, 8.0])
-def test_cnn_loss_and_gradient_match_oracle(handle, neg_weight):
-    H, W = 128, 192
+@pytest.mark.parametrize("shape,neg_weight", [((128, 192), 1.0), ((128, 192), 8.0), ((64, 1088), 5.0),
+                                              ((1088, 1920), 5.0)])
+def test_cnn_loss_and_gradient_match_oracle(handle, shape, neg_weight):
+    """Loss and gradient of a batch of 2 pairs.  128x192: every backward
+    launch covers a ragged tail (layer-4 weight gradient: 48 pixels, under one
+    64-pixel stage; input gradients: one partial 128-column tile) and the
+    layer-1 weight gradient runs 4 pipelined stages per CTA.  64x1088: the
+    input gradient of layer 2 spans two column tiles (136 = 128 + 8).
+    1088x1920, the training resolution: every CTA loops over several tiles
+    and stages."""
+    H, W = shape
     frames = synth.pan_clip(92, H, W, n_frames=3, rect_size=(16, 48))
     _, wbf, theta = weights(5)
     rng = np.random.default_rng(8)
@@ -105,6 +115,7 @@ def test_cnn_loss_and_gradient_match_oracle(handle, neg_weight):
     lab = dev(labels.view(np.int32).reshape(2, h, w, 2))
     grad, loss = handle.cnn_loss_grad(d, d[1:], wbf, lab, 32, batch=2, ref_batch_stride=H * W, cur_batch_stride=H * W,
                                       neg_weight=neg_weight)
+    assert handle.sync_status() == bm.OK
     g = grad.cpu().numpy()
     losses, grads = [], []
     for t in range(2):
@@ -115,10 +126,11 @@ def test_cnn_loss_and_gradient_match_oracle(handle, neg_weight):
     want_loss, want_grad = np.mean(losses), np.mean(grads, axis=0)
     assert abs(float(loss.item()) - want_loss) <= fb.TOL_BF16 * abs(want_loss)
     assert rel(g, want_grad) < 5e-2
-    # per parameter against the same network with its bfloat16 activation rounding modelled
+    # per parameter against the same network with its bfloat16 activation and
+    # pre-activation-gradient roundings modelled
     gb, Mb = zip(*[fb.cnn_grad_magnitudes(theta, frames[t], frames[t + 1], labels["dx"][t].astype(np.float64),
                                           labels["dy"][t].astype(np.float64), 32, neg_weight=neg_weight,
-                                          act_round="bf16") for t in range(2)])
+                                          act_round="bf16", grad_round="bf16") for t in range(2)])
     gb, Mb = np.mean(gb, axis=0), np.mean(Mb, axis=0)
     t = fb.TOL_BF16_SAME_ROUNDING
     bound = t * Mb + t * 1e-3 * Mb.max()
