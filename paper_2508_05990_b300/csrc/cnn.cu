@@ -57,38 +57,44 @@ __device__ __forceinline__ float berhu_grad(float e) {
   return fabsf(e) <= 4.0f ? (e > 0.f ? 1.f : (e < 0.f ? -1.f : 0.f)) : e * 0.25f;
 }
 
-// Head forward + loss + head backward.  One thread per L4 cell.  Writes
-// dpre4 = dL/d(L4 pre-activation) (bf16 NHWC, rounded to nearest even),
-// accumulates dL/d(head w, b) into grad and the loss sum into *loss (both
-// already scaled by 1/n).
-__global__ void __launch_bounds__(128) head_loss_bwd_kernel(const __nv_bfloat16* __restrict__ x4, int H4, int W4,
-                                                            const __nv_bfloat16* __restrict__ w, int range,
-                                                            const bayer_mv_t* __restrict__ labels, float inv_n,
-                                                            float neg_w, __nv_bfloat16* __restrict__ dpre4,
-                                                            float* __restrict__ grad,
-                                                            float* __restrict__ loss) {
+// Head forward + loss + head backward.  One thread per L4 cell, 128 cells per
+// CTA.  Writes dpre4 = dL/d(L4 pre-activation) (bf16 NHWC, rounded to nearest
+// even); the CTA's cells stage their dL/dz and activations in shared memory,
+// then thread t sums the head-weight gradients t, t + 128, t + 256 (and t <
+// 12 a head-bias gradient) over the 128 cells and adds them to grad once, so
+// that grad receives one atomic per parameter per CTA.  The loss sum goes to
+// *loss.  Both already scaled by 1/n.
+constexpr int kHeadCells = 128;
+
+__global__ void __launch_bounds__(kHeadCells) head_loss_bwd_kernel(const __nv_bfloat16* __restrict__ x4, int H4,
+                                                                   int W4, const __nv_bfloat16* __restrict__ w,
+                                                                   int range, const bayer_mv_t* __restrict__ labels,
+                                                                   float inv_n, float neg_w,
+                                                                   __nv_bfloat16* __restrict__ dpre4,
+                                                                   float* __restrict__ grad,
+                                                                   float* __restrict__ loss) {
   __shared__ float wh[12 * kC + 12];
-  __shared__ float gsum[12 * kC + 12];
-  __shared__ float lsum;
-  for (int i = threadIdx.x; i < 12 * kC + 12; i += blockDim.x) {
-    wh[i] = bf(w[BAYER_CNN_WH + i]);
-    gsum[i] = 0.f;
-  }
-  if (threadIdx.x == 0) lsum = 0.f;
+  __shared__ float sdz[kHeadCells][13];
+  __shared__ float sx[kHeadCells][kC + 1];
+  __shared__ float lsum[kHeadCells / 32];
+  for (int i = threadIdx.x; i < 12 * kC + 12; i += blockDim.x) wh[i] = bf(w[BAYER_CNN_WH + i]);
   __syncthreads();
   const int cells = H4 * W4;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int b = blockIdx.y;
+  float x[kC], dz[12];
+  float l = 0.f;
+#pragma unroll
+  for (int c = 0; c < kC; ++c) x[c] = 0.f;
+#pragma unroll
+  for (int j = 0; j < 12; ++j) dz[j] = 0.f;
   if (t < cells) {
     const int i = t / W4, k = t - i * W4;
-    float x[kC];
     const uint4* src = reinterpret_cast<const uint4*>(x4 + ((long long)b * cells + t) * kC);
 #pragma unroll
     for (int q = 0; q < 4; ++q) unpack8(__ldg(src + q), x + 8 * q);
     const int h = 2 * H4, wb = 2 * W4;
-    float dz[12];
-    float l = 0.f;
-#pragma unroll
+#pragma unroll 1  // unrolled, the four blocks' live ranges spill
     for (int s = 0; s < 4; ++s) {
       float z[3];
 #pragma unroll
@@ -126,17 +132,31 @@ __global__ void __launch_bounds__(128) head_loss_bwd_kernel(const __nv_bfloat16*
     for (int q = 0; q < 4; ++q)
       dst[q] = make_uint4(tc::bf2(d[8 * q], d[8 * q + 1]), tc::bf2(d[8 * q + 2], d[8 * q + 3]),
                           tc::bf2(d[8 * q + 4], d[8 * q + 5]), tc::bf2(d[8 * q + 6], d[8 * q + 7]));
-#pragma unroll
-    for (int j = 0; j < 12; ++j) {
-#pragma unroll
-      for (int c = 0; c < kC; ++c) atomicAdd(&gsum[j * kC + c], dz[j] * x[c]);
-      atomicAdd(&gsum[12 * kC + j], dz[j]);
-    }
-    atomicAdd(&lsum, l * inv_n);
   }
+  const int tl = threadIdx.x;
+#pragma unroll
+  for (int j = 0; j < 12; ++j) sdz[tl][j] = dz[j];
+#pragma unroll
+  for (int c = 0; c < kC; ++c) sx[tl][c] = x[c];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+  if ((tl & 31) == 0) lsum[tl >> 5] = l;
   __syncthreads();
-  for (int i = threadIdx.x; i < 12 * kC + 12; i += blockDim.x) atomicAdd(&grad[BAYER_CNN_WH + i], gsum[i]);
-  if (threadIdx.x == 0) atomicAdd(loss, lsum);
+  // head weight gradients (j, c) = (g / 32, g % 32): a warp shares j (dL/dz
+  // broadcast) and reads 32 consecutive activations
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const int g = tl + r * kHeadCells, j = g >> 5, c = g & 31;
+    float a = 0.f;
+    for (int m = 0; m < kHeadCells; ++m) a = fmaf(sdz[m][j], sx[m][c], a);
+    atomicAdd(&grad[BAYER_CNN_WH + g], a);
+  }
+  if (tl < 12) {
+    float a = 0.f;
+    for (int m = 0; m < kHeadCells; ++m) a += sdz[m][tl];
+    atomicAdd(&grad[BAYER_CNN_BH + tl], a);
+  }
+  if (tl == 0) atomicAdd(loss, (lsum[0] + lsum[1] + lsum[2] + lsum[3]) * inv_n);
 }
 
 __global__ void adamw_kernel(float* __restrict__ w, __nv_bfloat16* __restrict__ wb, const float* __restrict__ g,
@@ -282,8 +302,8 @@ cudaError_t cnn_loss_grad(const CnnFrames& fr, int batch, const uint16_t* wbf16,
   if ((e = cudaMemsetAsync(loss, 0, sizeof(float), st)) != cudaSuccess) return e;
   const float inv_n = 1.0f / ((float)batch * (2 * s.H[4]) * (2 * s.W[4]));
   {
-    dim3 g((s.H[4] * s.W[4] + 127) / 128, batch);
-    head_loss_bwd_kernel<<<g, 128, 0, st>>>(a[4], s.H[4], s.W[4], w, range, labels, inv_n, neg_weight, d[4], grad,
+    dim3 g((s.H[4] * s.W[4] + kHeadCells - 1) / kHeadCells, batch);
+    head_loss_bwd_kernel<<<g, kHeadCells, 0, st>>>(a[4], s.H[4], s.W[4], w, range, labels, inv_n, neg_weight, d[4], grad,
                                             loss);
   }
   const int woff[5] = {0, BAYER_CNN_W1, BAYER_CNN_W2, BAYER_CNN_W3, BAYER_CNN_W4};

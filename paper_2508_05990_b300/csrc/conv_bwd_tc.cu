@@ -23,18 +23,21 @@
 //   db[co] = sum dpre_out[b, oy, ox, co],
 // a GEMM with the output pixels as the reduction: D[k, co] = sum_p A[k, p] B[co, p]
 // with k = tap * CIN + ci (M, 3 tiles of 128 rows for CIN = 32, 2 for layer
-// 1's 16 operand channels) and the pixels as K.  Per stage of 64 pixels the
-// patches (im2col, one 16-byte copy per pixel, tap and 8 channels) and the
-// output gradients are staged MN-major -- the natural order of NHWC memory --
-// and the MMAs read them with the transpose bits of the instruction
-// descriptor.  Row k = 9 * CIN of A holds 1.0 for every pixel, so row 9 * CIN
-// of D is the bias gradient.  Two stages alternate: the copies of the next
-// stage are in flight while the MMAs of the current one run.  Each CTA
-// accumulates a contiguous range of pixels in TMEM and adds its partial
+// 1's 16 operand channels) and the pixels as K.  Per chunk of 64 output
+// pixels (one row segment) the patches (im2col: one 16-byte cell per pixel,
+// tap and 8 channels) and the output gradients are staged MN-major -- the
+// natural order of NHWC memory -- and the MMAs read them with the transpose
+// bits of the instruction descriptor.  Row k = 9 * CIN of A holds 1.0 for
+// every pixel, so row 9 * CIN of D is the bias gradient.  The copies of the
+// next chunks are in flight while the MMAs of the current one run.  Each CTA
+// accumulates a contiguous range of chunks in TMEM and adds its partial
 // gradients to the output once.
 // Layer 1's patches are the Bayer frames, split exactly as in the forward:
 // channel 2c + h of a tap is the hi (h = 0) or lo (h = 1) part of input plane
-// c, so dW1[co, c, tap] = D[hi] + D[lo] / 128.
+// c, so dW1[co, c, tap] = D[hi] + D[lo] / 128.  With 16-byte aligned frame
+// rows the six raw rows of a chunk are copied whole (cp.async, two chunks
+// ahead) and converted in shared memory; otherwise each thread loads the
+// samples of its patches.
 //
 // Every mbarrier wait is bounded; on expiry the kernel records
 // BAYER_ERR_TIMEOUT in the status word, frees its TMEM and finishes.
@@ -217,10 +220,17 @@ __global__ void __launch_bounds__(kDxM) conv_dx_tc_kernel(const ConvBwdArgs a) {
 // ---------------------------------------------------------------------------
 
 constexpr int kDwThreads = 256;
-constexpr int kDwP = 64;  // pixels per stage (4 MMA K-steps of 16)
+constexpr int kDwP = 64;         // output pixels per chunk: one row segment (4 MMA K-steps of 16)
+constexpr int kRawPieces = 33;   // 16-byte pieces of a staged raw row: samples 4*ox0 - 8 .. 4*ox0 + 255
 
-template <bool FRAMES>
+// MODE 0: hidden maps (patches gathered by cp.async in 16-byte channel chunks);
+// MODE 1: Bayer frames, any alignment (per-thread sample loads);
+// MODE 2: Bayer frames with 16-byte aligned rows: the six raw rows a chunk
+// needs are copied by cp.async two chunks ahead into a ring and converted to
+// the hi/lo operand in shared memory.
+template <int MODE>
 struct DwLayout {
+  static constexpr bool FRAMES = MODE != 0;
   static constexpr int KOP = FRAMES ? 16 : kC;  // operand channels per tap
   static constexpr int KCH = 9 * KOP / 8;       // 16-byte patch chunks per pixel (18 or 36)
   static constexpr int MT = FRAMES ? 2 : 3;     // M tiles of 128 rows (patch rows + ones row + padding)
@@ -230,188 +240,182 @@ struct DwLayout {
   static constexpr int A_BYTES = NCH * kDwP * 16;
   // B: cell (co chunk, pixel p) at (chunk * P + p) * 16.
   static constexpr int B_BYTES = 4 * kDwP * 16;
-  static constexpr int STAGE = A_BYTES + B_BYTES;
+  // MODE 2 raw ring: cell (frame f, raw row r, piece q) at ((f*6 + r)*kRawPieces + q) * 16
+  static constexpr int R_BYTES = 2 * 6 * kRawPieces * 16;
+  static constexpr int NB = MODE == 2 ? 4 : 2;  // B buffers (MODE 2: copies run two chunks ahead)
+  static constexpr int NR = MODE == 2 ? 3 : 0;  // raw buffers
+  static constexpr int B_OFF = 2 * A_BYTES;
+  static constexpr int R_OFF = B_OFF + NB * B_BYTES;
+  static constexpr int MBAR_OFF = R_OFF + NR * R_BYTES;
+  static constexpr int SMEM = MBAR_OFF + 64;
   static constexpr int GS = KCH * 8 + 1;  // epilogue row stride: the patch rows and the ones row
-  static constexpr int SMEM = 2 * STAGE + 64;
   static constexpr int TMEM_COLS = MT == 2 ? 64 : 128;
-  static_assert(kC * GS * 4 <= 2 * STAGE, "epilogue scratch fits in the stages");
+  static_assert(kC * GS * 4 <= 2 * A_BYTES, "epilogue scratch fits in the A buffers");
   static_assert(KCH < NCH, "room for the ones row");
+  static_assert(B_OFF % 16 == 0 && R_OFF % 16 == 0 && MBAR_OFF % 8 == 0, "alignment");
   static_assert(SMEM <= 113 * 1024, "two CTAs per SM");
 };
 
-// Output pixel gp of the flattened (b, oy, ox) order.
-struct Pix {
-  int b, oy, ox;
+// Chunk c of the (b, oy, segment) order: output pixels ox0 .. ox0 + 63 of row
+// oy of image b (those at ox >= Wo are padding: zero output gradient).
+struct Seg {
+  int b, oy, ox0;
 };
-__device__ __forceinline__ Pix pix_of(long long gp, int Ho, int Wo) {
-  Pix q;
-  const long long hw = (long long)Ho * Wo;
-  q.b = (int)(gp / hw);
-  const int r = (int)(gp - (long long)q.b * hw);
-  q.oy = r / Wo;
-  q.ox = r - q.oy * Wo;
-  return q;
+__device__ __forceinline__ Seg seg_of(int c, int Ho, int segs) {
+  Seg s;
+  const int row = c / segs;
+  s.ox0 = (c - row * segs) * kDwP;
+  s.b = row / Ho;
+  s.oy = row - s.b * Ho;
+  return s;
 }
 
-// Stage the patches and output gradients of pixels [base, base + 64) into one
-// stage (A at sA, B at sB; shared-space addresses and generic pointer of A).
-template <bool FRAMES>
-__device__ __forceinline__ void dw_stage(const ConvBwdArgs& a, long long base, long long npix, uint32_t sA,
-                                         uint8_t* sA_ptr, uint32_t sB, int tid) {
-  using L = DwLayout<FRAMES>;
-  // output gradients: 4 lanes per pixel (64 contiguous bytes), 8 pixels per warp
-  {
-    const int kc = tid & 3, p = tid >> 2;  // kDwThreads == 4 * kDwP
-    const long long gp = base + p;
-    const bool in = gp < npix;
-    tc::cp_async16(sB + (kc * kDwP + p) * 16, in ? a.dout + gp * kC + kc * 8 : a.dout, in ? 16u : 0u);
-  }
-  if (!FRAMES) {
-    // patches: lanes = 8 pixels x 4 channel chunks of one tap (64 contiguous
-    // bytes per pixel); items (tap, pixel octet) across warps and iterations
-    const int p_lo = tid & 7, kc = (tid >> 3) & 3;
+// Output gradients of a chunk into a B buffer: 4 lanes per pixel (64
+// contiguous bytes), 8 pixels per warp.
+__device__ __forceinline__ void dw_stage_dout(const ConvBwdArgs& a, const Seg& s, uint32_t sB, int tid) {
+  const int kc = tid & 3, p = tid >> 2;  // kDwThreads == 4 * kDwP
+  const int ox = s.ox0 + p;
+  const bool in = ox < a.Wo;
+  const __nv_bfloat16* src = in ? a.dout + (((long long)s.b * a.Ho + s.oy) * a.Wo + ox) * kC + kc * 8 : a.dout;
+  tc::cp_async16(sB + (kc * kDwP + p) * 16, src, in ? 16u : 0u);
+}
+
+// MODE 0 patches: lanes = 8 pixels x 4 channel chunks of one tap (64
+// contiguous bytes per pixel); items (tap, pixel octet) across warps.
+__device__ __forceinline__ void dw_stage_hidden(const ConvBwdArgs& a, const Seg& s, uint32_t sA, int tid) {
+  const int p_lo = tid & 7, kc = (tid >> 3) & 3;
+  const long long img = (long long)s.b * a.Hi;
 #pragma unroll 3
-    for (int rest = tid >> 5; rest < 9 * (kDwP / 8); rest += kDwThreads / 32) {
-      const int tap = rest % 9, p = (rest / 9) * 8 + p_lo;
-      const long long gp = base + p;
-      bool in = gp < npix;
-      const __nv_bfloat16* src = a.xin;
-      if (in) {
-        const Pix q = pix_of(gp, a.Ho, a.Wo);
-        const int iy = 2 * q.oy + tap / 3 - 1, ix = 2 * q.ox + tap % 3 - 1;
-        in = iy >= 0 && iy < a.Hi && ix >= 0 && ix < a.Wi;
-        if (in) src = a.xin + (((long long)q.b * a.Hi + iy) * a.Wi + ix) * kC + kc * 8;
-      }
-      tc::cp_async16(sA + ((tap * 4 + kc) * kDwP + p) * 16, src, in ? 16u : 0u);
-    }
-  } else {
-    // Bayer patches: item (pixel, tap, frame) -> the 4 samples of the RGGB
-    // quad at half-resolution (hy, hx), split into hi/lo bf16 pairs
-    constexpr int NIT = kDwP * 9 * 2;
-    constexpr int PER = (NIT + kDwThreads - 1) / kDwThreads;
-    const int Hh = a.fr.H / 2, Wh = a.fr.W / 2;
-    uint32_t r0[PER], r1[PER];
-    bool in[PER];
-#pragma unroll
-    for (int u = 0; u < PER; ++u) {
-      const int it = tid + u * kDwThreads;
-      const int p = it & (kDwP - 1), tf = it / kDwP;
-      const int tap = tf >> 1, f = tf & 1;
-      const long long gp = base + p;
-      in[u] = it < NIT && gp < npix;
-      r0[u] = r1[u] = 0;
-      if (in[u]) {
-        const Pix q = pix_of(gp, a.Ho, a.Wo);
-        const int hy = 2 * q.oy + tap / 3 - 1, hx = 2 * q.ox + tap % 3 - 1;
-        in[u] = hy >= 0 && hy < Hh && hx >= 0 && hx < Wh;
-        if (in[u]) {
-          const uint16_t* fp = f ? a.fr.cur + (long long)q.b * a.fr.cur_bs : a.fr.ref + (long long)q.b * a.fr.ref_bs;
-          const uint16_t* s0 = fp + (long long)(2 * hy) * a.fr.pitch + 2 * hx;
-          const uint16_t* s1 = s0 + a.fr.pitch;
-          if (a.vec) {
-            r0[u] = __ldg(reinterpret_cast<const uint32_t*>(s0));
-            r1[u] = __ldg(reinterpret_cast<const uint32_t*>(s1));
-          } else {
-            r0[u] = (uint32_t)__ldg(s0) | ((uint32_t)__ldg(s0 + 1) << 16);
-            r1[u] = (uint32_t)__ldg(s1) | ((uint32_t)__ldg(s1 + 1) << 16);
-          }
-        }
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < PER; ++u) {
-      const int it = tid + u * kDwThreads;
-      if (it < NIT) {
-        const int p = it & (kDwP - 1), tf = it / kDwP;
-        uint4 cell = make_uint4(0, 0, 0, 0);
-        if (in[u])
-          cell = make_uint4(tc::split12(r0[u] & 0xFFFFu), tc::split12(r0[u] >> 16), tc::split12(r1[u] & 0xFFFFu),
-                            tc::split12(r1[u] >> 16));
-        *reinterpret_cast<uint4*>(sA_ptr + (tf * kDwP + p) * 16) = cell;
-      }
-    }
-    (void)L::KCH;
+  for (int rest = tid >> 5; rest < 9 * (kDwP / 8); rest += kDwThreads / 32) {
+    const int tap = rest % 9, p = (rest / 9) * 8 + p_lo;
+    const int ox = s.ox0 + p;
+    const int iy = 2 * s.oy + tap / 3 - 1, ix = 2 * ox + tap % 3 - 1;
+    const bool in = ox < a.Wo && iy >= 0 && iy < a.Hi && ix >= 0 && ix < a.Wi;
+    const __nv_bfloat16* src = in ? a.xin + ((img + iy) * a.Wi + ix) * kC + kc * 8 : a.xin;
+    tc::cp_async16(sA + ((tap * 4 + kc) * kDwP + p) * 16, src, in ? 16u : 0u);
   }
 }
 
-template <bool FRAMES>
-__global__ void __launch_bounds__(kDwThreads, 2) conv_dw_tc_kernel(const ConvBwdArgs a, int chunks_per_cta) {
-  using L = DwLayout<FRAMES>;
-  extern __shared__ __align__(1024) uint8_t smem[];
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * L::STAGE);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 2);
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const long long npix = (long long)a.batch * a.Ho * a.Wo;
-  const long long nchunks = (npix + kDwP - 1) / kDwP;
-  const long long c_begin = (long long)blockIdx.x * chunks_per_cta;
-  long long c_end = c_begin + chunks_per_cta;
-  if (c_end > nchunks) c_end = nchunks;
-  const int n = c_begin < c_end ? (int)(c_end - c_begin) : 0;
+// The A cell of Bayer patch (pixel, tap, frame): the RGGB quad's samples
+// (row 0: w0, row 1: w1; two samples each, left one low) split into hi/lo
+// pairs, or zeros outside the half-resolution map.
+__device__ __forceinline__ uint4 bayer_cell(bool in, uint32_t w0, uint32_t w1) {
+  if (!in) return make_uint4(0, 0, 0, 0);
+  return make_uint4(tc::split12(w0 & 0xFFFFu), tc::split12(w0 >> 16), tc::split12(w1 & 0xFFFFu),
+                    tc::split12(w1 >> 16));
+}
 
-  if (tid == 0) {
-    tc::mbar_init(&mbar[0], 1);
-    tc::mbar_init(&mbar[1], 1);
-    tc::fence_mbar_init();
+// MODE 1 patches: item (pixel, tap, frame), loads first, then conversion.
+__device__ __forceinline__ void dw_stage_bayer_direct(const ConvBwdArgs& a, const Seg& s, uint8_t* sA, int tid) {
+  constexpr int NIT = kDwP * 9 * 2;
+  constexpr int PER = (NIT + kDwThreads - 1) / kDwThreads;
+  const int Hh = a.fr.H / 2, Wh = a.fr.W / 2;
+  uint32_t r0[PER], r1[PER];
+  bool in[PER];
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int it = tid + u * kDwThreads;
+    const int p = it & (kDwP - 1), tf = it / kDwP;
+    const int tap = tf >> 1, f = tf & 1;
+    const int ox = s.ox0 + p;
+    const int hy = 2 * s.oy + tap / 3 - 1, hx = 2 * ox + tap % 3 - 1;
+    in[u] = it < NIT && ox < a.Wo && hy >= 0 && hy < Hh && hx >= 0 && hx < Wh;
+    r0[u] = r1[u] = 0;
+    if (in[u]) {
+      const uint16_t* fp = f ? a.fr.cur + (long long)s.b * a.fr.cur_bs : a.fr.ref + (long long)s.b * a.fr.ref_bs;
+      const uint16_t* s0 = fp + (long long)(2 * hy) * a.fr.pitch + 2 * hx;
+      const uint16_t* s1 = s0 + a.fr.pitch;
+      if (a.vec) {
+        r0[u] = __ldg(reinterpret_cast<const uint32_t*>(s0));
+        r1[u] = __ldg(reinterpret_cast<const uint32_t*>(s1));
+      } else {
+        r0[u] = (uint32_t)__ldg(s0) | ((uint32_t)__ldg(s0 + 1) << 16);
+        r1[u] = (uint32_t)__ldg(s1) | ((uint32_t)__ldg(s1 + 1) << 16);
+      }
+    }
   }
-  if (warp == 0) tc::tmem_alloc(tmem_slot, L::TMEM_COLS);
-  // ones row (row KCH*8 of A: element 0 of chunk KCH) and zero padding rows,
-  // both stages; the patch copies never touch them
-  for (int i = tid; i < 2 * (L::NCH - L::KCH) * kDwP; i += kDwThreads) {
-    const int s = i / ((L::NCH - L::KCH) * kDwP), r = i - s * ((L::NCH - L::KCH) * kDwP);
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int it = tid + u * kDwThreads;
+    if (it < NIT) *reinterpret_cast<uint4*>(sA + ((it / kDwP) * kDwP + (it & (kDwP - 1))) * 16) =
+        bayer_cell(in[u], r0[u], r1[u]);
+  }
+}
+
+// MODE 2: raw rows 4oy - 2 .. 4oy + 3 of both frames, samples 4ox0 - 8 ..
+// 4ox0 + 255 (zero-filled outside the frame) into a raw buffer.
+__device__ __forceinline__ void dw_stage_raw(const ConvBwdArgs& a, const Seg& s, uint32_t sR, int tid) {
+  const uint16_t* ref = a.fr.ref + (long long)s.b * a.fr.ref_bs;
+  const uint16_t* cur = a.fr.cur + (long long)s.b * a.fr.cur_bs;
+  for (int it = tid; it < 2 * 6 * kRawPieces; it += kDwThreads) {
+    const int q = it % kRawPieces, fr = it / kRawPieces;
+    const int f = fr / 6, r = fr - 6 * f;
+    const int y = 4 * s.oy - 2 + r, x = 4 * s.ox0 - 8 + 8 * q;
+    const bool in = y >= 0 && y < a.fr.H && x >= 0 && x < a.fr.W;  // W % 8 == 0: whole pieces
+    const uint16_t* src = in ? (f ? cur : ref) + (long long)y * a.fr.pitch + x : a.fr.ref;
+    tc::cp_async16(sR + it * 16, src, in ? 16u : 0u);
+  }
+}
+
+// MODE 2: a staged raw buffer -> the chunk's A cells.  Patch (p, tap, f)
+// reads raw rows 2ky, 2ky + 1 at sample 4p + 2kx + 6 (= 2hx - (4ox0 - 8)).
+__device__ __forceinline__ void dw_convert_raw(const ConvBwdArgs& a, const Seg& s, const uint8_t* R, uint8_t* A,
+                                               int tid) {
+  const int Hh = a.fr.H / 2, Wh = a.fr.W / 2;
+#pragma unroll
+  for (int u = 0; u < (kDwP * 18 + kDwThreads - 1) / kDwThreads; ++u) {
+    const int it = tid + u * kDwThreads;
+    if (it < kDwP * 18) {
+      const int p = it & (kDwP - 1), tf = it / kDwP;
+      const int tap = tf >> 1, f = tf & 1, ky = tap / 3, kx = tap - 3 * ky;
+      const int ox = s.ox0 + p, hy = 2 * s.oy + ky - 1, hx = 2 * ox + kx - 1;
+      const bool in = ox < a.Wo && hy >= 0 && hy < Hh && hx >= 0 && hx < Wh;
+      const uint8_t* row = R + (f * 6 + 2 * ky) * (kRawPieces * 16) + 2 * (4 * p + 2 * kx + 6);
+      const uint32_t w0 = *reinterpret_cast<const uint32_t*>(row);
+      const uint32_t w1 = *reinterpret_cast<const uint32_t*>(row + kRawPieces * 16);
+      *reinterpret_cast<uint4*>(A + (tf * kDwP + p) * 16) = bayer_cell(in, w0, w1);
+    }
+  }
+}
+
+// The ones row (row KCH*8 of A: element 0 of chunk KCH) and the zero padding
+// rows of both A buffers; the patch staging never touches them.
+template <int MODE>
+__device__ __forceinline__ void dw_init_pad(uint8_t* smem, int tid) {
+  using L = DwLayout<MODE>;
+  constexpr int PAD = (L::NCH - L::KCH) * kDwP;
+  for (int i = tid; i < 2 * PAD; i += kDwThreads) {
+    const int s = i / PAD, r = i - s * PAD;
     const int j = L::KCH + r / kDwP, p = r % kDwP;
-    *reinterpret_cast<uint4*>(smem + s * L::STAGE + (j * kDwP + p) * 16) =
+    *reinterpret_cast<uint4*>(smem + s * L::A_BYTES + (j * kDwP + p) * 16) =
         make_uint4(j == L::KCH ? 0x3F80u : 0u, 0u, 0u, 0u);
   }
-  const uint32_t s0 = tc::smem_addr(smem);
+}
+
+// MMAs of one chunk (thread 0): K step = 16 pixels; core matrices are 8
+// pixels (K, 128 bytes apart) x 8 rows (M or N, kDwP * 16 bytes apart).
+template <int MT>
+__device__ __forceinline__ void dw_mma(uint32_t tmem, uint32_t sa, uint32_t sb, bool first) {
   constexpr uint32_t idesc = tc::idesc_bf16_f32(128, kC) | (1u << 15) | (1u << 16);  // A, B MN-major
-  bool ok = true;
-
-  if (n > 0) dw_stage<FRAMES>(a, c_begin * kDwP, npix, s0, smem, s0 + L::A_BYTES, tid);
-  tc::cp_async_commit();
-  __syncthreads();
-  tc::fence_after_sync();
-  const uint32_t tmem = *tmem_slot;
-
-  for (int i = 0; i < n; ++i) {
-    const int buf = i & 1;
-    if (i + 1 < n) {
-      // the other stage was read by the MMAs of chunk i - 1
-      if (i >= 1) ok &= tc::mbar_wait(&mbar[buf ^ 1], ((i - 1) >> 1) & 1, kWaitLimit);
-      const uint32_t so = s0 + (buf ^ 1) * L::STAGE;
-      dw_stage<FRAMES>(a, (c_begin + i + 1) * kDwP, npix, so, smem + (buf ^ 1) * L::STAGE, so + L::A_BYTES, tid);
-      tc::cp_async_commit();
-      tc::cp_async_wait<1>();
-    } else {
-      tc::cp_async_wait<0>();
-    }
-    tc::fence_proxy_async();
-    if (__syncthreads_or(!ok)) {  // a timed-out wait anywhere in the CTA: stop issuing
-      tc::cp_async_wait_all();
-      break;
-    }
-    if (tid == 0) {
-      tc::fence_after_sync();
-      const uint32_t sa = s0 + buf * L::STAGE, sb = sa + L::A_BYTES;
 #pragma unroll
-      for (int s = 0; s < kDwP / 16; ++s) {
-        // K step = 16 pixels: core matrices 8 pixels (K, 128 bytes apart) x
-        // 8 rows (M or N, kDwP * 16 bytes apart)
-        const uint64_t bd = tc::smem_desc(sb + s * 256, 128, kDwP * 16);
+  for (int s = 0; s < kDwP / 16; ++s) {
+    const uint64_t bd = tc::smem_desc(sb + s * 256, 128, kDwP * 16);
 #pragma unroll
-        for (int mt = 0; mt < L::MT; ++mt) {
-          const uint64_t ad = tc::smem_desc(sa + mt * 16 * kDwP * 16 + s * 256, 128, kDwP * 16);
-          tc::mma_bf16(tmem + 32 * mt, ad, bd, idesc, (i > 0 || s > 0) ? 1u : 0u);
-        }
-      }
-      tc::commit(&mbar[buf]);
+    for (int mt = 0; mt < MT; ++mt) {
+      const uint64_t ad = tc::smem_desc(sa + mt * 16 * kDwP * 16 + s * 256, 128, kDwP * 16);
+      tc::mma_bf16(tmem + 32 * mt, ad, bd, idesc, (!first || s > 0) ? 1u : 0u);
     }
   }
-  if (n > 0 && ok) ok &= tc::mbar_wait(&mbar[(n - 1) & 1], ((n - 1) >> 1) & 1, kWaitLimit);
-  ok = __syncthreads_and(ok);  // every stage consumed: reuse them as the epilogue scratch
-  tc::fence_after_sync();
+}
 
-  float* G = reinterpret_cast<float*>(smem);  // G[co * GS + k]
-  if (n > 0 && ok) {
+// TMEM partial sums -> shared scratch G[co][k] (over the A buffers) -> the
+// gradient, once per CTA.  ok is CTA-uniform; every MMA has completed.
+template <int MODE>
+__device__ __forceinline__ void dw_epilogue(const ConvBwdArgs& a, uint8_t* smem, uint32_t tmem, bool live, int tid) {
+  using L = DwLayout<MODE>;
+  const int warp = tid >> 5;
+  float* G = reinterpret_cast<float*>(smem);
+  if (live) {
     const int quarter = warp & 3;
     for (int mt = warp >> 2; mt < L::MT; mt += 2) {
       float v[32];
@@ -425,9 +429,9 @@ __global__ void __launch_bounds__(kDwThreads, 2) conv_dw_tc_kernel(const ConvBwd
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (n > 0 && ok) {
+  if (live) {
     // dW in the flat order [co][ci][tap], 4 consecutive entries per thread
-    constexpr int CIN = FRAMES ? 8 : kC, PER_CO = CIN * 9;
+    constexpr int CIN = L::FRAMES ? 8 : kC, PER_CO = CIN * 9;
     for (int i = tid; i < kC * PER_CO / 4; i += kDwThreads) {
       const int co = (4 * i) / PER_CO, j0 = 4 * i - co * PER_CO;
       float g[4];
@@ -435,7 +439,7 @@ __global__ void __launch_bounds__(kDwThreads, 2) conv_dw_tc_kernel(const ConvBwd
       for (int e = 0; e < 4; ++e) {
         const int j = j0 + e, ci = j / 9, tap = j - 9 * ci;
         const float* gr = G + co * L::GS;
-        g[e] = FRAMES ? gr[tap * 16 + 2 * ci] + gr[tap * 16 + 2 * ci + 1] * (1.0f / 128.0f) : gr[tap * kC + ci];
+        g[e] = L::FRAMES ? gr[tap * 16 + 2 * ci] + gr[tap * 16 + 2 * ci + 1] * (1.0f / 128.0f) : gr[tap * kC + ci];
       }
       float* dst = a.gw + co * PER_CO + j0;
       if (a.vec_atomics) {
@@ -447,6 +451,143 @@ __global__ void __launch_bounds__(kDwThreads, 2) conv_dw_tc_kernel(const ConvBwd
     }
     if (tid < kC) atomicAdd(a.gb + tid, G[tid * L::GS + L::KCH * 8]);
   }
+}
+
+// MODE 0 and 1: two stages, the copies of chunk i + 1 in flight while the MMAs
+// of chunk i run.
+template <int MODE>
+__global__ void __launch_bounds__(kDwThreads, 2) conv_dw_tc_kernel(const ConvBwdArgs a, int chunks_per_cta) {
+  using L = DwLayout<MODE>;
+  static_assert(MODE != 2, "MODE 2 has its own pipeline");
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L::MBAR_OFF);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 2);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int segs = (a.Wo + kDwP - 1) / kDwP;
+  const int nchunks = a.batch * a.Ho * segs;
+  const int c_begin = blockIdx.x * chunks_per_cta;
+  const int c_end = min(c_begin + chunks_per_cta, nchunks);
+  const int n = c_begin < c_end ? c_end - c_begin : 0;
+
+  if (tid == 0) {
+    tc::mbar_init(&mbar[0], 1);
+    tc::mbar_init(&mbar[1], 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) tc::tmem_alloc(tmem_slot, L::TMEM_COLS);
+  dw_init_pad<MODE>(smem, tid);
+  const uint32_t s0 = tc::smem_addr(smem);
+  bool ok = true;
+
+  auto stage = [&](int i, int buf) {
+    const Seg s = seg_of(c_begin + i, a.Ho, segs);
+    dw_stage_dout(a, s, s0 + L::B_OFF + buf * L::B_BYTES, tid);
+    if (MODE == 0)
+      dw_stage_hidden(a, s, s0 + buf * L::A_BYTES, tid);
+    else
+      dw_stage_bayer_direct(a, s, smem + buf * L::A_BYTES, tid);
+  };
+  if (n > 0) stage(0, 0);
+  tc::cp_async_commit();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+
+  for (int i = 0; i < n; ++i) {
+    const int buf = i & 1;
+    if (i + 1 < n) {
+      // the other stage was read by the MMAs of chunk i - 1
+      if (i >= 1) ok &= tc::mbar_wait(&mbar[buf ^ 1], ((i - 1) >> 1) & 1, kWaitLimit);
+      stage(i + 1, buf ^ 1);
+      tc::cp_async_commit();
+      tc::cp_async_wait<1>();
+    } else {
+      tc::cp_async_wait<0>();
+    }
+    tc::fence_proxy_async();
+    if (__syncthreads_or(!ok)) {  // a timed-out wait anywhere in the CTA: stop issuing
+      tc::cp_async_wait_all();
+      break;
+    }
+    if (tid == 0) {
+      tc::fence_after_sync();
+      dw_mma<L::MT>(tmem, s0 + buf * L::A_BYTES, s0 + L::B_OFF + buf * L::B_BYTES, i == 0);
+      tc::commit(&mbar[buf]);
+    }
+  }
+  if (n > 0 && ok) ok &= tc::mbar_wait(&mbar[(n - 1) & 1], ((n - 1) >> 1) & 1, kWaitLimit);
+  ok = __syncthreads_and(ok);  // every buffer consumed: the A buffers become the epilogue scratch
+  tc::fence_after_sync();
+  dw_epilogue<MODE>(a, smem, tmem, n > 0 && ok, tid);
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, L::TMEM_COLS);
+  if (!ok && tid == 0 && a.status) atomicExch(a.status, (int)BAYER_ERR_TIMEOUT);
+}
+
+// MODE 2: raw rows and output gradients are copied two chunks ahead (raw ring
+// of 3, B ring of 4); per chunk the threads convert the staged raw rows into
+// the A buffer the MMAs of chunk i - 2 have released.
+__global__ void __launch_bounds__(kDwThreads, 2) conv_dw1_ring_tc_kernel(const ConvBwdArgs a, int chunks_per_cta) {
+  using L = DwLayout<2>;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L::MBAR_OFF);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 2);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int segs = (a.Wo + kDwP - 1) / kDwP;
+  const int nchunks = a.batch * a.Ho * segs;
+  const int c_begin = blockIdx.x * chunks_per_cta;
+  const int c_end = min(c_begin + chunks_per_cta, nchunks);
+  const int n = c_begin < c_end ? c_end - c_begin : 0;
+
+  if (tid == 0) {
+    tc::mbar_init(&mbar[0], 1);
+    tc::mbar_init(&mbar[1], 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) tc::tmem_alloc(tmem_slot, L::TMEM_COLS);
+  dw_init_pad<2>(smem, tid);
+  const uint32_t s0 = tc::smem_addr(smem);
+  bool ok = true;
+
+  auto issue = [&](int i) {  // copies of chunk i, one cp.async group (empty past the end)
+    if (i < n) {
+      const Seg s = seg_of(c_begin + i, a.Ho, segs);
+      dw_stage_raw(a, s, s0 + L::R_OFF + (i % 3) * L::R_BYTES, tid);
+      dw_stage_dout(a, s, s0 + L::B_OFF + (i & 3) * L::B_BYTES, tid);
+    }
+    tc::cp_async_commit();
+  };
+  issue(0);
+  issue(1);
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+
+  for (int i = 0; i < n; ++i) {
+    const int buf = i & 1;
+    // A[buf] and B[(i + 2) % 4] were read by the MMAs of chunk i - 2
+    if (i >= 2) ok &= tc::mbar_wait(&mbar[buf], ((i - 2) >> 1) & 1, kWaitLimit);
+    issue(i + 2);
+    tc::cp_async_wait<2>();  // chunk i's copies (this thread's) have landed
+    if (__syncthreads_or(!ok)) {
+      tc::cp_async_wait_all();
+      break;
+    }
+    dw_convert_raw(a, seg_of(c_begin + i, a.Ho, segs), smem + L::R_OFF + (i % 3) * L::R_BYTES,
+                   smem + buf * L::A_BYTES, tid);
+    tc::fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      dw_mma<L::MT>(tmem, s0 + buf * L::A_BYTES, s0 + L::B_OFF + (i & 3) * L::B_BYTES, i == 0);
+      tc::commit(&mbar[buf]);
+    }
+  }
+  if (n > 0 && ok) ok &= tc::mbar_wait(&mbar[(n - 1) & 1], ((n - 1) >> 1) & 1, kWaitLimit);
+  tc::cp_async_wait_all();
+  ok = __syncthreads_and(ok);
+  tc::fence_after_sync();
+  dw_epilogue<2>(a, smem, tmem, n > 0 && ok, tid);
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, L::TMEM_COLS);
   if (!ok && tid == 0 && a.status) atomicExch(a.status, (int)BAYER_ERR_TIMEOUT);
@@ -458,21 +599,27 @@ int sm_count() {
   return nsm;
 }
 
-template <bool FRAMES>
-cudaError_t launch_dw(const ConvBwdArgs& a, cudaStream_t st) {
-  using L = DwLayout<FRAMES>;
-  auto kern = conv_dw_tc_kernel<FRAMES>;
-  const long long npix = (long long)a.batch * a.Ho * a.Wo;
-  const long long nchunks = (npix + kDwP - 1) / kDwP;
+template <int MODE, typename K>
+cudaError_t launch_dw(K kern, const ConvBwdArgs& a, cudaStream_t st) {
+  using L = DwLayout<MODE>;
+  const long long nchunks = (long long)a.batch * a.Ho * ((a.Wo + kDwP - 1) / kDwP);
   if (nchunks < 1) return cudaSuccess;
+  if (nchunks > 0x7FFFFFFFll) return cudaErrorInvalidValue;
   const int per_sm = tc::ctas_per_sm(kern, kDwThreads, L::SMEM, L::TMEM_COLS);
   const long long slots = (long long)sm_count() * per_sm;
-  // at least 4 stages per CTA: the partial sums are added once per CTA
+  // at least 4 chunks per CTA: the partial sums are added once per CTA
   long long per = (nchunks + slots - 1) / slots;
   if (per < 4) per = 4;
   const long long grid = (nchunks + per - 1) / per;
   kern<<<(unsigned)grid, kDwThreads, L::SMEM, st>>>(a, (int)per);
   return cudaGetLastError();
+}
+
+template <int MODE, typename K>
+cudaError_t configure_dw(K kern) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, DwLayout<MODE>::SMEM);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  return e;
 }
 
 }  // namespace
@@ -491,16 +638,9 @@ cudaError_t pack_conv_dx_weights(const uint16_t* w, const int* w_off, uint16_t* 
 cudaError_t configure_conv_bwd_tc() {
   cudaError_t e = cudaFuncSetAttribute(conv_dx_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDxSmem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(conv_dx_tc_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(conv_dw_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             DwLayout<false>::SMEM);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(conv_dw_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             DwLayout<true>::SMEM);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(conv_dw_tc_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(conv_dw_tc_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (e == cudaSuccess) e = configure_dw<0>(conv_dw_tc_kernel<0>);
+  if (e == cudaSuccess) e = configure_dw<1>(conv_dw_tc_kernel<1>);
+  if (e == cudaSuccess) e = configure_dw<2>(conv_dw1_ring_tc_kernel);
   return e;
 }
 
@@ -515,7 +655,14 @@ cudaError_t launch_conv_dx_tc(const ConvBwdArgs& a, cudaStream_t st) {
 }
 
 cudaError_t launch_conv_dw_tc(const ConvBwdArgs& a, bool frames, cudaStream_t st) {
-  return frames ? launch_dw<true>(a, st) : launch_dw<false>(a, st);
+  if (!frames) return launch_dw<0>(conv_dw_tc_kernel<0>, a, st);
+  // the raw-row ring copies 16-byte pieces: 16-byte aligned frames, pitch and
+  // batch strides multiples of 8 samples (W is a multiple of 32)
+  const bool ring = (reinterpret_cast<uintptr_t>(a.fr.ref) & 15) == 0 &&
+                    (reinterpret_cast<uintptr_t>(a.fr.cur) & 15) == 0 && a.fr.pitch % 8 == 0 &&
+                    a.fr.ref_bs % 8 == 0 && a.fr.cur_bs % 8 == 0 && a.fr.W % 8 == 0;
+  if (ring) return launch_dw<2>(conv_dw1_ring_tc_kernel, a, st);
+  return launch_dw<1>(conv_dw_tc_kernel<1>, a, st);
 }
 
 }  // namespace bme

@@ -93,16 +93,20 @@ def test_cnn_forward_batched_strides(handle):
         check_forward(prop[t].cpu().numpy(), conf[t].cpu().numpy(), theta, frames[t], frames[t + 1], 16)
 
 
-@pytest.mark.parametrize("shape,neg_weight", [((128, 192), 1.0), ((128, 192), 8.0), ((64, 1088), 5.0),
-                                              ((1088, 1920), 5.0)])
-def test_cnn_loss_and_gradient_match_oracle(handle, shape, neg_weight):
+@pytest.mark.parametrize("shape,neg_weight,offset", [((128, 192), 1.0, 0), ((128, 192), 8.0, 0),
+                                                     ((64, 1088), 5.0, 0), ((1088, 1920), 5.0, 0),
+                                                     ((128, 192), 1.0, 2), ((128, 192), 1.0, 1)])
+def test_cnn_loss_and_gradient_match_oracle(handle, shape, neg_weight, offset):
     """Loss and gradient of a batch of 2 pairs.  128x192: every backward
-    launch covers a ragged tail (layer-4 weight gradient: 48 pixels, under one
-    64-pixel stage; input gradients: one partial 128-column tile) and the
-    layer-1 weight gradient runs 4 pipelined stages per CTA.  64x1088: the
+    launch covers a ragged tail (a layer's last row segment of 64 pixels
+    partly past the row; input gradients: one partial 128-column tile) and the
+    layer-1 weight gradient runs 4 pipelined chunks per CTA.  64x1088: the
     input gradient of layer 2 spans two column tiles (136 = 128 + 8).
     1088x1920, the training resolution: every CTA loops over several tiles
-    and stages."""
+    and chunks.  offset: the frames start `offset` samples into their buffer,
+    so that the layer-1 weight gradient loads the samples itself (4-byte loads
+    at offset 2, 2-byte loads at offset 1) instead of copying 16-byte pieces
+    of raw rows."""
     H, W = shape
     frames = synth.pan_clip(92, H, W, n_frames=3, rect_size=(16, 48))
     _, wbf, theta = weights(5)
@@ -112,6 +116,10 @@ def test_cnn_loss_and_gradient_match_oracle(handle, shape, neg_weight):
     labels["dx"] = 2 * rng.integers(-16, 17, (2, h, w))
     labels["dy"] = 2 * rng.integers(-16, 17, (2, h, w))
     d = dev(frames)
+    if offset:
+        flat = torch.zeros(d.numel() + 8, dtype=d.dtype, device="cuda")
+        flat[offset:offset + d.numel()].copy_(d.reshape(-1))
+        d = flat[offset:offset + d.numel()].view(d.shape)
     lab = dev(labels.view(np.int32).reshape(2, h, w, 2))
     grad, loss = handle.cnn_loss_grad(d, d[1:], wbf, lab, 32, batch=2, ref_batch_stride=H * W, cur_batch_stride=H * W,
                                       neg_weight=neg_weight)
