@@ -24,9 +24,9 @@
 // epilogue.  Every mbarrier wait is bounded; on expiry the kernel records
 // BAYER_ERR_TIMEOUT in the status word, frees its TMEM and finishes.
 //
-// Layer 1's operands split each 12-bit sample exactly into two bf16 channels,
-// hi = (v >> 4)/128 - 1 and lo = (v & 15)/16, with weights w and w/128, so that
-// hi*w + lo*(w/128) = (v/2048 - 1)*w; the packing below builds those weights.
+// Layer 1 (conv_s2_tc.cu) takes its operands as TF32: each 12-bit sample v as
+// v/2048 - 1 (exact in TF32), the bf16 weights widened exactly; the packing
+// below builds that layer's TF32 weight image too.
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -71,10 +71,11 @@ using tc::cp_async16;
 using tc::cp_async_wait_all;
 
 // Weight images of the four layers (K-major B operand, all 32 output
-// channels): for a layer with cin operand channels, element (n, k), k =
-// tap*cin + ci, at (n/8)*(9*cin/8)*128 + (k/8)*128 + (n%8)*16 + (k%8)*2.
-// Layer 1 (16 operand channels from 8 input planes): channel ci is the hi
-// (even) or lo (odd) half of plane ci/2, the lo weight scaled by 1/128.
+// channels): for layers 2..4 (32 input channels), element (n, k), k =
+// tap*32 + ci, bf16 at (n/8)*(9*4)*128 + (k/8)*128 + (n%8)*16 + (k%8)*2.
+// Layer 1 (8 input planes, TF32 operands): element (n, k), k = tap*8 + ci, the
+// float32 value of the bf16 weight at (n/8)*(9*2)*128 + (k/4)*128 + (n%8)*16 +
+// (k%4)*4 (core matrices of 8 rows x 4 TF32 values); the same 9216 bytes.
 // One thread per element of all four images; image l starts at byte
 // img_off[l] of img and is built from w + w_off[l].
 struct PackArgs {
@@ -84,30 +85,28 @@ struct PackArgs {
 };
 
 __global__ void pack_conv_tc_weights_kernel(const PackArgs pa, __nv_bfloat16* __restrict__ img) {
-  constexpr int kL1 = kN * 9 * 16, kL = kN * 9 * 32;
+  constexpr int kL1 = kN * 9 * 8, kL = kN * 9 * 32;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  int l = 0;
-  if (i >= kL1) {
-    i -= kL1;
-    l = 1 + i / kL;
-    i -= (l - 1) * kL;
+  if (i < kL1) {
+    const int n = i / 72, k = i - n * 72;
+    const int tap = k / 8, ci = k - tap * 8;
+    const float wv = __bfloat162float(pa.w[pa.w_off[0] + (n * 8 + ci) * 9 + tap]);
+    reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(img) + pa.img_off[0] + (n >> 3) * (18 * 128) +
+                             (k >> 2) * 128 + (n & 7) * 16)[k & 3] = wv;
+    return;
   }
+  i -= kL1;
+  const int l = 1 + i / kL;
+  i -= (l - 1) * kL;
   if (l > 3) return;
-  const int cin_op = l == 0 ? 16 : 32;
-  const int K = 9 * cin_op;
+  constexpr int cin_op = 32, K = 9 * cin_op;
   const int n = i / K, k = i - n * K;
   const int tap = k / cin_op, ci = k - tap * cin_op;
-  const __nv_bfloat16* w = pa.w + pa.w_off[l];
-  float wv;
-  if (l != 0) {
-    wv = __bfloat162float(w[(n * cin_op + ci) * 9 + tap]);
-  } else {
-    wv = __bfloat162float(w[(n * 8 + (ci >> 1)) * 9 + tap]);
-    if (ci & 1) wv *= (1.0f / 128.0f);
-  }
-  const int kc = cin_op / 8;
-  img[(pa.img_off[l] + (n >> 3) * (9 * kc) * 128 + (k >> 3) * 128 + (n & 7) * 16) / 2 + (k & 7)] =
-      __float2bfloat16_rn(wv);
+  const __nv_bfloat16* w = pa.w + (l == 1 ? pa.w_off[1] : (l == 2 ? pa.w_off[2] : pa.w_off[3]));
+  const float wv = __bfloat162float(w[(n * cin_op + ci) * 9 + tap]);
+  const unsigned off = l == 1 ? pa.img_off[1] : (l == 2 ? pa.img_off[2] : pa.img_off[3]);
+  constexpr int kc = cin_op / 8;
+  img[(off + (n >> 3) * (9 * kc) * 128 + (k >> 3) * 128 + (n & 7) * 16) / 2 + (k & 7)] = __float2bfloat16_rn(wv);
 }
 
 // EPI: 0 bias + ReLU -> bf16 NHWC output; 1 bias + ReLU -> bf16 rounding ->
@@ -132,6 +131,10 @@ __global__ void __launch_bounds__(kM) conv3x3_tc_kernel(const ConvTcArgs a) {
   for (int i = tid; i < L::B_BYTES / 16; i += kM) reinterpret_cast<uint4*>(sB)[i] = __ldg(a.wimg + i);
   if (EPI == 1)
     for (int i = tid; i < kHeadW; i += kM) sHead[i] = __bfloat162float(a.whead[i]);
+  // launched as a dependent of the previous layer (whose own wait covered the
+  // weight packing): its output is read only after this wait
+  tc::grid_dep_wait();
+  tc::grid_dep_launch();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
@@ -241,8 +244,7 @@ cudaError_t launch_t(const ConvTcArgs& a, cudaStream_t st) {
   if (ntiles < 1) return cudaSuccess;
   long long grid = (long long)nsm * per_sm;
   if (grid > ntiles) grid = ntiles;
-  kern<<<(unsigned)grid, kM, L::SMEM, st>>>(a);
-  return cudaGetLastError();
+  return tc::launch_dependent(kern, dim3((unsigned)grid), dim3(kM), L::SMEM, st, a);
 }
 
 template <int CIN, int EPI>
@@ -267,7 +269,7 @@ cudaError_t pack_conv_tc_weights(const uint16_t* w, const int* w_off, const size
     pa.w_off[l] = w_off[l];
     pa.img_off[l] = (unsigned)img_off[l];
   }
-  const int n = kN * 9 * 16 + 3 * kN * 9 * 32;
+  const int n = kN * 9 * 8 + 3 * kN * 9 * 32;
   pack_conv_tc_weights_kernel<<<(n + 255) / 256, 256, 0, st>>>(pa, reinterpret_cast<__nv_bfloat16*>(img));
   return cudaGetLastError();
 }

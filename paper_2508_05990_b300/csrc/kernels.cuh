@@ -104,8 +104,8 @@ struct ConvTcArgs {
   int* status;  // device status word: BAYER_ERR_TIMEOUT if a bounded wait expired
 };
 cudaError_t configure_conv_tc();
-// Packed weight image of one layer: cin_op operand channels (16 for layer 1's
-// split frames, else 32).  pack_conv_tc_weights builds all four layers'
+// Packed weight image of one layer in bytes: cin_op = 32 for layers 2..4, 16
+// for layer 1 (whose TF32 image of 8 planes has the same 9216 bytes).  pack_conv_tc_weights builds all four layers'
 // images in one launch: layer l from the [32][cin][3][3] bf16 block at
 // w + w_off[l], written at byte img_off[l] (256-byte aligned) of img.
 size_t conv_tc_weight_bytes(int cin_op);

@@ -8,6 +8,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <utility>
+
 namespace bme {
 namespace tc {
 
@@ -15,6 +17,15 @@ namespace tc {
 __device__ __forceinline__ uint32_t bf2(float a, float b) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
   return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// max(a, 0), max(b, 0) as a packed bf16 pair (round to nearest even), a in the
+// low half: one cvt.rn.relu.bf16x2 (which stores its first source in the
+// upper half).
+__device__ __forceinline__ uint32_t bf2_relu(float a, float b) {
+  uint32_t d;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(b), "f"(a));
+  return d;
 }
 
 // The proposal network's layer-1 operands: a 12-bit sample v as two exact
@@ -27,6 +38,14 @@ __device__ __forceinline__ uint32_t split12(uint32_t v) {
   const float hi = fmaf(__uint_as_float(0x4B000000u | (v >> 4)), 1.0f / 128.0f, -65537.0f);
   const float lo = fmaf(__uint_as_float(0x4B000000u | (v & 15u)), 1.0f / 16.0f, -524288.0f);
   return bf2(hi, lo);
+}
+
+// A 12-bit sample v as the float32 (and exact TF32) value v/2048 - 1: the
+// float with bit pattern 0x4B000000 | v is 2^23 + v, and (2^23 + v)/2048 - 4097
+// = v/2048 - 1 is one fma whose exact result has at most 11 significant bits
+// (|v - 2048| <= 2048), so TF32 operands hold it exactly.
+__device__ __forceinline__ uint32_t tf32_sample12(uint32_t v) {
+  return __float_as_uint(fmaf(__uint_as_float(0x4B000000u | v), 1.0f / 2048.0f, -4097.0f));
 }
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -65,6 +84,12 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// Instruction descriptor of tcgen05.mma kind::tf32: D float32, A and B TF32
+// (float32 storage), both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_tf32_f32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(dst_smem)),
                "r"(ncols));
@@ -83,6 +108,15 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
+// D (+)= A * B with TF32 operands (K = 8 per instruction).
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
 __device__ __forceinline__ void commit(uint64_t* mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(mbar))
                : "memory");
@@ -91,6 +125,34 @@ __device__ __forceinline__ void commit(uint64_t* mbar) {
 __device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Programmatic dependent launch: wait until the grid this one depends on
+// (the previous kernel in the stream, when launched with programmatic stream
+// serialization) has completed and its memory is visible; a no-op otherwise.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Let the dependent grid start launching (its CTAs take SM resources as this
+// grid's CTAs leave; it must wait with grid_dep_wait before using our results).
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Launch `kern` with programmatic stream serialization: it may start while the
+// previous kernel of the stream finishes, and must call grid_dep_wait before
+// reading what that kernel wrote (or what any earlier kernel wrote, unless the
+// previous kernel itself waited before triggering).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_dependent(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                    Args&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 
 __device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(mbar)), "r"(count));
