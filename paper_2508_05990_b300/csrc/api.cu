@@ -150,14 +150,28 @@ bool seeded16_fast(int block, int phase, int W, int H, int range) {
 
 // Seeded refine on the fast kernels: warp-per-block +-4 refine, compacted list
 // of low-confidence blocks, list-mode exhaustive search of that list.
-bayer_status_t seeded_fast(bayer_me_s* h, const uint16_t* ref, const uint16_t* cur, int W, int H, int pitch,
-                           long long rbs, long long cbs, int batch, int range, const float* prop, const float* conf,
-                           float thresh, bayer_mv_t* out, uint8_t* fallback, int* n_fallback, cudaStream_t st) {
-  const int hb = H / 16, wb = W / 16;
-  const long long nblk = (long long)batch * hb * wb;
+// The fallback list (counter, then block indices) for nblk blocks, its counter
+// zeroed on st.
+bayer_status_t fallback_list(bayer_me_s* h, long long nblk, cudaStream_t st) {
   bayer_status_t s = grow(h, &h->list, &h->list_bytes, (size_t)(nblk + 1) * sizeof(int));
   if (s != BAYER_OK) return s;
-  cudaError_t e = cudaMemsetAsync(h->list, 0, sizeof(int), st);
+  return cuda_status(cudaMemsetAsync(h->list, 0, sizeof(int), st));
+}
+
+// The +-4 refine and the fallback searches; list_ready: fallback_list already
+// ran on st (so that the refine kernel follows the network's last layer
+// directly, as its dependent launch).
+bayer_status_t seeded_fast(bayer_me_s* h, const uint16_t* ref, const uint16_t* cur, int W, int H, int pitch,
+                           long long rbs, long long cbs, int batch, int range, const float* prop, const float* conf,
+                           float thresh, bayer_mv_t* out, uint8_t* fallback, int* n_fallback, cudaStream_t st,
+                           bool list_ready = false) {
+  const int hb = H / 16, wb = W / 16;
+  const long long nblk = (long long)batch * hb * wb;
+  if (!list_ready) {
+    bayer_status_t s = fallback_list(h, nblk, st);
+    if (s != BAYER_OK) return s;
+  }
+  cudaError_t e = cudaSuccess;
   bme::Seeded16Args a{};
   a.ref = ref;
   a.cur = cur;
@@ -571,11 +585,12 @@ bayer_status_t bayer_me_estimate_learned(bayer_me_t h, const uint16_t* ref, cons
   if ((s = grow(h, reinterpret_cast<char**>(&h->prop), &h->prop_bytes, nblk * 3 * sizeof(float))) != BAYER_OK) return s;
   float* prop = h->prop;
   float* conf = h->prop + 2 * nblk;
+  if ((s = fallback_list(h, (long long)nblk, st)) != BAYER_OK) return s;
   bme::CnnFrames fr{ref, cur, W, H, pitch, ref_bs, cur_bs};
   cudaError_t e = bme::cnn_forward(fr, batch, w_bf16, range, h->cnn_acts, prop, conf, h->d_status, st);
   if (e != cudaSuccess) return cuda_status(e);
   return seeded_fast(h, ref, cur, W, H, pitch, ref_bs, cur_bs, batch, range, prop, conf, conf_thresh, mv_out,
-                     fallback_out, n_fallback, st);
+                     fallback_out, n_fallback, st, true);
 }
 
 bayer_status_t bayer_refine_conv(bayer_me_t h, const float* feat, int n, int Hf, int Wf, int C, int hidden,

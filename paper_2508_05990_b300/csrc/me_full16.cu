@@ -239,6 +239,10 @@ __global__ void __launch_bounds__(kLW * 32) me_full16_list_kernel(const __grid_c
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint32_t* win = smem + warp * C::WARP_WORDS;
   uint32_t* curt = win + C::CUR_OFF;
+  // launched as a dependent of the kernel that built the list: read it (and
+  // write the fallback blocks' fields) only after this wait
+  tc::grid_dep_wait();
+  tc::grid_dep_launch();
   const int n = *count;
   const int step = gridDim.x * kLW;
   int gi = blockIdx.x * kLW + warp;
@@ -321,12 +325,10 @@ cudaError_t launch_list_r(const uint16_t* ref, const uint16_t* cur, int W, int H
   if (grid > per_sm * nsm) grid = per_sm * nsm;
   if (grid < 1) grid = 1;
   if (use_tma)
-    me_full16_list_kernel<R, true><<<grid, kLW * 32, C::SMEM, st>>>(tref, tcur, ref, cur, W, H, pitch, ref_bs, cur_bs,
-                                                                     h, w, list, count, out, vec_ok, status);
-  else
-    me_full16_list_kernel<R, false><<<grid, kLW * 32, C::SMEM, st>>>(tref, tcur, ref, cur, W, H, pitch, ref_bs,
-                                                                      cur_bs, h, w, list, count, out, vec_ok, status);
-  return cudaGetLastError();
+    return tc::launch_dependent(me_full16_list_kernel<R, true>, dim3(grid), dim3(kLW * 32), C::SMEM, st, tref, tcur,
+                                ref, cur, W, H, pitch, ref_bs, cur_bs, h, w, list, count, out, vec_ok, status);
+  return tc::launch_dependent(me_full16_list_kernel<R, false>, dim3(grid), dim3(kLW * 32), C::SMEM, st, tref, tcur,
+                              ref, cur, W, H, pitch, ref_bs, cur_bs, h, w, list, count, out, vec_ok, status);
 }
 
 template <int R>

@@ -22,6 +22,7 @@
 // gathered from its five row lanes.
 #include "common.cuh"
 #include "kernels.cuh"
+#include "tc_common.cuh"
 
 namespace bme {
 
@@ -69,6 +70,11 @@ __global__ void __launch_bounds__(kSW * 32) seeded16_kernel(const Seeded16Args a
     }
   }
   const bool vec = a.vec2;
+  // launched as a dependent of the network's last layer: its proposals are
+  // read only after this wait (the fallback list's counter was zeroed before
+  // the network ran)
+  tc::grid_dep_wait();
+  tc::grid_dep_launch();
 
   // ---- lanes 0..2 load block gb0 + lane's confidence and proposal while
   // every lane loads its samples of the three current blocks
@@ -280,8 +286,8 @@ cudaError_t launch_seeded16(const Seeded16Args& in, cudaStream_t st) {
            a.pitch % 2 == 0 && a.ref_bs % 2 == 0 && a.cur_bs % 2 == 0;
   const long long nblk = (long long)a.batch * a.h * a.w;
   const long long per_cta = (long long)kSW * kPer;
-  seeded16_kernel<<<(unsigned)((nblk + per_cta - 1) / per_cta), kSW * 32, kSmem, st>>>(a);
-  return cudaGetLastError();
+  return tc::launch_dependent(seeded16_kernel, dim3((unsigned)((nblk + per_cta - 1) / per_cta)), dim3(kSW * 32),
+                              kSmem, st, a);
 }
 
 }  // namespace bme
