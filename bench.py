@@ -784,7 +784,7 @@ def run_ours(args):
             "mean_block_rel_regret": round(float(((sad_l - sad_plain) / np.maximum(sad_plain, 1)).mean()), 5),
             "search": "proposal CNN (BF16, tcgen05) + +-4 refine; exhaustive +-32 where conf < 0.5",
             "weights": os.path.relpath(WEIGHTS, ROOT) + " (4,000 training pairs)",
-            "gpu_launches": args.steps * 9,
+            "gpu_launches": args.steps * 8,
         }
         if os.path.exists(WEIGHTS_2000):
             # the configured training scale: same clip, same timing
@@ -804,6 +804,9 @@ def run_ours(args):
                 "value": round(PAIRS * args.steps / (ms_c / 1e3), 2), "ms_per_step": round(ms_c / args.steps, 4),
                 "fallback_rate": round(float(d_fb.float().mean().item()), 4),
                 "sad_regret": round(float((sad_c.sum() - sad_plain.sum()) / sad_plain.sum()), 5)}
+        if legs:
+            # the network's training step (recipe: batch 16), kernels only
+            learned["train_step"] = train_step_timing(h, d_frames, d_mv, steps=10)
 
     # ALU roofline: measured throughput of the search's primitive (packed min.u16x2 + dp2a, two
     # pixel-candidates per pair) per clock per SM x SMs x SM clock under load; sad.u32 beside it
@@ -900,7 +903,12 @@ def run_ours(args):
         }
         if not args.no_cpu_baseline:
             result["cpu_baseline"] = cpu_baseline_sample(frames, feats)
-        # the metric's second half last, so that a reader keeping only the end of the line keeps it
+        # the metric's second half last, so that a reader keeping only the end of the line keeps it;
+        # within it the headline keys last too
+        if learned is not None:
+            tail = ("speedup_vs_plain", "fallback_rate", "sad_regret", "value")
+            learned = {**{k: v for k, v in learned.items() if k not in tail},
+                       **{k: learned[k] for k in tail if k in learned}}
         result["learned_seeded"] = learned
     h.close()
     if world > 1:
@@ -979,6 +987,67 @@ def run_refine_only(n_maps: int):
     return {"refine_maps": n_maps, "ms": round(ms, 4), "tflops": round(flops / (ms / 1e3) / 1e12, 1)}
 
 
+def train_step_timing(h, d_frames, d_mv, steps: int, batch: int = 16):
+    """The proposal network's training step on a batch of `batch` 1080p pairs
+    (the clip's 7 pairs repeated, labelled by the exhaustive field): loss +
+    gradient (network forward and tensor-core backward) and the AdamW update,
+    `steps` timed calls each after three untimed ones."""
+    import torch
+    from paper_2508_05990_b300 import bayer_me as bm
+    from paper_2508_05990_b300 import synth
+    idx = torch.arange(batch, device=d_frames.device) % PAIRS
+    fr = d_frames.view(torch.int16)  # (CUDA indexing has no uint16 kernels)
+    ref, cur = fr[idx].contiguous().view(d_frames.dtype), fr[idx + 1].contiguous().view(d_frames.dtype)
+    lab = d_mv[idx].contiguous()
+    theta = (np.load(WEIGHTS)["theta"].astype(np.float32) if os.path.exists(WEIGHTS)
+             else synth.he_normal_params(5, bm.CNN_SHAPES))
+    w = torch.from_numpy(theta).cuda()
+    wbf = bm.to_bf16_bits(w).contiguous()
+    grad = torch.empty_like(w)
+    loss = torch.empty(1, device="cuda")
+    m, v = torch.zeros_like(w), torch.zeros_like(w)
+
+    def lg():
+        h.cnn_loss_grad(ref, cur, wbf, lab, RANGE, batch=batch, ref_batch_stride=H * W, cur_batch_stride=H * W,
+                        grad=grad, loss=loss, neg_weight=5.0)
+
+    def opt():
+        h.cnn_adamw(w.clone(), wbf.clone(), grad, m, v, 1, 1e-3)
+
+    out = {"batch": batch, "resolution": f"{W}x{H}"}
+    for name, fn in (("loss_grad_ms", lg), ("adamw_ms", opt)):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = round(e0.elapsed_time(e1) / steps, 4)
+    if h.sync_status() != bm.OK:
+        raise RuntimeError("device status after the training step")
+    out["pairs_per_s"] = round(batch / (out["loss_grad_ms"] / 1e3), 1)
+    return out
+
+
+def run_train_only(steps: int):
+    """The proposal network's training step alone (loss + gradient and AdamW
+    on 16 1080p pairs): a small case for profiling the backward kernels."""
+    import torch
+    from paper_2508_05990_b300 import bayer_me as bm
+    from paper_2508_05990_b300 import build, synth
+    build.build()
+    h = bm.Handle(0)
+    d_frames = torch.from_numpy(synth.pan_clip(SEED, H, W, n_frames=T)).cuda()
+    d_mv = h.estimate_ex(d_frames, d_frames[1:], block=BLOCK, search_range=RANGE, batch=PAIRS,
+                         ref_batch_stride=H * W, cur_batch_stride=H * W)
+    res = train_step_timing(h, d_frames, d_mv, steps)
+    h.close()
+    return res
+
+
 def run_c2f_only(steps: int):
     """The C2F leg alone on the 1080p clip (its presets, search and search +
     propagation, beside the exhaustive search): a small case for profiling the
@@ -1025,7 +1094,13 @@ def main(argv=None):
                     help="run only the coarse-to-fine leg (small case for profiling the pyramid kernels)")
     ap.add_argument("--refine-maps", type=int, default=0,
                     help="profiling aid: time only the BF16 refine convolutions on this many 4K-form maps and exit")
+    ap.add_argument("--train-steps", type=int, default=0,
+                    help="profiling aid: time only the proposal network's training step (16 1080p pairs) this many "
+                         "times and exit")
     args = ap.parse_args(argv)
+    if args.train_steps > 0:
+        print(json.dumps(run_train_only(args.train_steps)), flush=True)
+        return
     if args.c2f_only:
         print(json.dumps(run_c2f_only(10)), flush=True)
         return
