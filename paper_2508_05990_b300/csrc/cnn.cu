@@ -12,8 +12,9 @@
 //   dx = range*tanh(z_0), dy = range*tanh(z_1), conf = sigmoid(z_2)
 // Activations are NHWC bf16 [B][H][W][32].  The four convolutions run on the
 // tensor cores (conv_s2_tc.cu, conv_tc.cu; layer 1 gathers the Bayer frames
-// directly, the packing fused into its operand staging; in inference the head
-// is evaluated in layer 4's epilogue), and so do the convolutions' input and
+// directly, the packing fused into its operand staging; in inference layers
+// 3, 4 and the head run as one kernel, the layer-3 map kept in shared memory,
+// where its rows fit one tile), and so do the convolutions' input and
 // weight gradients (conv_bwd_tc.cu), on bf16 pre-activation gradients; the
 // training head and loss are SIMT (one thread per layer-4 cell).
 // Loss per block:
@@ -260,12 +261,16 @@ cudaError_t cnn_forward_acts(const CnnFrames& fr, int batch, const uint16_t* wbf
     c.batch = batch;
     c.status = status;
     const bool fuse = head && l == 4;
-    if (fuse) {
+    if (head && l >= 3) {
       c.whead = w + BAYER_CNN_WH;
       c.prop = prop;
       c.conf = conf;
       c.range = range;
     }
+    // inference: layers 3, 4 and the head in one kernel where layer-3 rows fit
+    // one tile (the layer-3 map then stays on chip)
+    if (head && l == 3 && conv34_head_supported(s.W[3]))
+      return launch_conv34_head_tc(c, wimg[4], w + boff[4], s.H[4], s.W[4], st);
     cudaError_t e = l <= 2 ? launch_conv_s2_rows_tc(c, l, st) : launch_conv_tc(c, l, fuse, st);
     if (e != cudaSuccess) return e;
   }

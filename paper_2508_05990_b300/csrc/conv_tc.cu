@@ -233,6 +233,212 @@ __global__ void __launch_bounds__(kM) conv3x3_tc_kernel(const ConvTcArgs a) {
   if (!ok && tid == 0 && a.status) atomicExch(a.status, (int)BAYER_ERR_TIMEOUT);
 }
 
+// ---------------------------------------------------------------------------
+// Layers 3 and 4 and the head in one kernel (inference; layer-3 rows of at most
+// 128 pixels).  CTA = (image, pair of layer-4 rows u0, u0 + 1): the 11 layer-2
+// rows 4u0 - 3 .. 4u0 + 7 they depend on are staged at once (slot r = row 4u0
+// - 3 + r, the tile kernel's layout, zero outside the map); layer-3 row t (=
+// 2u0 - 1 + t, t = 0..4) reads slots 2t .. 2t + 2, so once its MMAs are done
+// (and those of row t - 1) slot 2t is free and its epilogue writes the row
+// there, bias + ReLU + bf16, in the same layout as layer 4's input; layer-4 row
+// u0 + v then reads slots 2(2v + ky) and its epilogue evaluates the head.
+// Layer-3 rows alternate between two TMEM accumulators, so the MMAs of row t + 1
+// run while row t drains.  The layer-3 map never goes to memory.
+// ---------------------------------------------------------------------------
+
+constexpr int k34Rows = 11;                       // staged layer-2 rows
+constexpr int k34Slot = 2 * 4 * 129 * 16;         // one staged row (NP = 129 pixels per parity)
+constexpr int k34B = 9 * 32 * kN * 2;             // one layer's weight image
+constexpr int k34Smem = 2 * k34B + kHeadW * 4 + k34Rows * k34Slot + 64 + 2 * kN * 4;
+static_assert(k34Smem <= 227 * 1024, "shared memory");
+
+struct Conv34Args {
+  ConvTcArgs l3;              // layer 3: in = layer-2 map, wimg, bias, Ho/Wo = layer-3 dims; head fields
+  const uint4* wimg4;         // layer 4 weights
+  const __nv_bfloat16* bias4;
+  int H4, W4;
+};
+
+constexpr int k34Threads = 256;  // two warps per TMEM lane quarter: channel halves, or the two layer-4 rows
+
+__global__ void __launch_bounds__(k34Threads) conv34_head_tc_kernel(const Conv34Args c) {
+  const ConvTcArgs& a = c.l3;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* sB3 = smem;
+  uint8_t* sB4 = smem + k34B;
+  float* sHead = reinterpret_cast<float*>(smem + 2 * k34B);
+  uint8_t* sX = smem + 2 * k34B + kHeadW * 4;  // kHeadW * 4 = 1584, a multiple of 16
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sX + k34Rows * k34Slot);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 3);
+  float* sBias = reinterpret_cast<float*>(sX + k34Rows * k34Slot + 64);  // layer 3, then layer 4
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int bands = (c.H4 + 1) / 2;
+  const int b = blockIdx.x / bands, u0 = 2 * (blockIdx.x - b * bands);
+  const int H3 = a.Ho, W3 = a.Wo, H2 = a.Hi, W2 = a.Wi;
+
+  if (tid == 0) {
+    for (int i = 0; i < 3; ++i) tc::mbar_init(&mbar[i], 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) tc::tmem_alloc(tmem_slot, 128);  // acc 0, 1: layer 3; 2, 3: layer 4
+  for (int i = tid; i < k34B / 16; i += k34Threads) {
+    reinterpret_cast<uint4*>(sB3)[i] = __ldg(a.wimg + i);
+    reinterpret_cast<uint4*>(sB4)[i] = __ldg(c.wimg4 + i);
+  }
+  for (int i = tid; i < kHeadW; i += k34Threads) sHead[i] = __bfloat162float(a.whead[i]);
+  if (tid < 2 * kN) sBias[tid] = __bfloat162float(tid < kN ? a.bias[tid] : c.bias4[tid - kN]);
+  // launched as a dependent of layer 2: read its output only after this wait
+  tc::grid_dep_wait();
+  tc::grid_dep_launch();
+  const uint32_t sX_addr = tc::smem_addr(sX);
+  // ---- stage layer-2 rows 4u0 - 3 .. 4u0 + 7, columns -1 .. 255, as five
+  // cp.async groups: rows 0-2 (what layer-3 row 0 reads), then 2 rows each
+  // (what row t adds), so that row t's MMAs wait only for groups 0..t
+  {
+    constexpr int NJ = 2 * kM + 1;
+#pragma unroll 1
+    for (int g = 0; g < 5; ++g) {
+      const int r0 = g == 0 ? 0 : 2 * g + 1, nr = g == 0 ? 3 : 2;
+      for (int it = tid; it < nr * NJ * 4; it += k34Threads) {
+        const int rr = it / (NJ * 4), rem = it - rr * (NJ * 4);
+        const int r = r0 + rr, j = rem >> 2, kc = rem & 3;
+        const int iy = 4 * u0 - 3 + r, ix = j - 1;
+        const bool in = iy >= 0 && iy < H2 && ix >= 0 && ix < W2;
+        const __nv_bfloat16* src = in ? a.in + (((long long)b * H2 + iy) * W2 + ix) * 32 + kc * 8 : a.in;
+        tc::cp_async16(sX_addr + r * k34Slot + (((j & 1) * 4 + kc) * 129 + (j >> 1)) * 16, src, in ? 16u : 0u);
+      }
+      tc::cp_async_commit();
+    }
+  }
+  // groups 0..t landed for every thread, visible to the tensor cores
+  auto rows_ready = [&](int t) {
+    switch (t) {
+      case 0: tc::cp_async_wait<4>(); break;
+      case 1: tc::cp_async_wait<3>(); break;
+      case 2: tc::cp_async_wait<2>(); break;
+      case 3: tc::cp_async_wait<1>(); break;
+      default: tc::cp_async_wait<0>(); break;
+    }
+    tc::fence_proxy_async();
+  };
+  rows_ready(0);
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t sB3_addr = tc::smem_addr(sB3), sB4_addr = tc::smem_addr(sB4);
+  constexpr uint32_t idesc = tc::idesc_bf16_f32(kM, kN);
+  const uint64_t a_base = tc::smem_desc(sX_addr, 129 * 16, 128);
+  // a 3x3 conv row: 9 taps x 2 K steps, tap row ky from slot slot_of(ky)
+  auto conv_row = [&](uint32_t bimg, int slot0, int slot_step, uint32_t d) {
+    const uint64_t b_base = tc::smem_desc(bimg, 128, 9 * 4 * 128);
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      const int ky = tap / 3, kx = tap % 3;
+      const uint64_t a_row = a_base + (uint64_t)((slot0 + slot_step * ky) * (k34Slot / 16));
+#pragma unroll
+      for (int s2 = 0; s2 < 2; ++s2) {
+        const uint64_t ad = a_row + (uint64_t)(((kx & 1) * 4 + 2 * s2) * 129 + (kx >> 1));
+        const uint64_t bd = b_base + (uint64_t)((tap * 4 + 2 * s2) * 8);
+        tc::mma_bf16(d, ad, bd, idesc, (tap > 0 || s2 > 0) ? 1u : 0u);
+      }
+    }
+  };
+  bool ok = true;
+  if (tid == 0) {
+    tc::fence_after_sync();
+    conv_row(sB3_addr, 0, 1, tmem);
+    tc::commit(&mbar[0]);
+  }
+  rows_ready(1);
+  __syncthreads();
+  if (tid == 0) {
+    tc::fence_after_sync();
+    conv_row(sB3_addr, 2, 1, tmem + 32);
+    tc::commit(&mbar[1]);
+  }
+  // warp w reads TMEM lanes 32 (w % 4) .. (pixel x); layer 3: channel half w / 4
+  const int quarter = warp & 3, half = warp >> 2;
+  const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+  const int x = quarter * 32 + lane;
+  for (int t = 0; t < 5; ++t) {
+    ok &= tc::mbar_wait(&mbar[t & 1], (uint32_t)((t >> 1) & 1), kWaitLimit);
+    tc::fence_after_sync();
+    float v[16];
+    tc::tmem_ld16(tmem + lane_base + (uint32_t)(32 * (t & 1) + 16 * half), v);
+    // layer-3 row y3 -> slot 2t as layer 4's input: pixel x at staged column x + 1
+    const int y3 = 2 * u0 - 1 + t;
+    const bool valid = y3 >= 0 && y3 < H3 && x < W3;
+    uint8_t* dst = sX + 2 * t * k34Slot;
+    const int j = x + 1;
+#pragma unroll
+    for (int k2 = 0; k2 < 2; ++k2) {
+      const int kc = 2 * half + k2;
+      uint4 o = make_uint4(0, 0, 0, 0);
+      if (valid) {
+        float u[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) u[e] = v[8 * k2 + e] + sBias[8 * kc + e];
+        o = make_uint4(tc::bf2_relu(u[0], u[1]), tc::bf2_relu(u[2], u[3]), tc::bf2_relu(u[4], u[5]),
+                       tc::bf2_relu(u[6], u[7]));
+      }
+      *reinterpret_cast<uint4*>(dst + (((j & 1) * 4 + kc) * 129 + (j >> 1)) * 16) = o;
+      if (x == 0) *reinterpret_cast<uint4*>(dst + (kc * 129) * 16) = make_uint4(0, 0, 0, 0);  // column -1
+    }
+    tc::fence_before_sync();
+    if (t + 2 <= 4) rows_ready(t + 2);
+    tc::fence_proxy_async();  // the row is layer 4's operand (async proxy)
+    __syncthreads();          // accumulator t & 1 drained, slot 2t written, row t + 2's inputs landed
+    if (tid == 0 && t + 2 <= 4) {
+      tc::fence_after_sync();
+      conv_row(sB3_addr, 2 * (t + 2), 1, tmem + (uint32_t)(32 * (t & 1)));
+      tc::commit(&mbar[t & 1]);
+    }
+  }
+  // ---- layer 4: rows u0 + v, v = 0, 1, tap row ky from layer-3 row 2v + ky in slot 2(2v + ky)
+  if (tid == 0) {
+    tc::fence_after_sync();
+    conv_row(sB4_addr, 0, 2, tmem + 64);
+    conv_row(sB4_addr, 4, 2, tmem + 96);
+    tc::commit(&mbar[2]);
+  }
+  ok &= tc::mbar_wait(&mbar[2], 0, kWaitLimit);
+  tc::fence_after_sync();
+  const int hb = 2 * c.H4, wb = 2 * c.W4;
+  {
+    // warps 0-3: layer-4 row u0, warps 4-7: row u0 + 1
+    const int v2 = half;
+    float v[32];
+    tc::tmem_ld32(tmem + lane_base + (uint32_t)(64 + 32 * v2), v);
+    const int y4 = u0 + v2;
+    if (y4 < c.H4 && x < c.W4) {
+      // the head sees the bf16 activation, as it would read it back from memory
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj)
+        v[jj] = __bfloat162float(__float2bfloat16_rn(fmaxf(v[jj] + sBias[kN + jj], 0.f)));
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        float z[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const int jh = 3 * s + q;
+          float acc = sHead[12 * kN + jh];
+#pragma unroll
+          for (int cc = 0; cc < kN; ++cc) acc = fmaf(sHead[jh * kN + cc], v[cc], acc);
+          z[q] = acc;
+        }
+        const long long blk = ((long long)b * hb + 2 * y4 + (s >> 1)) * wb + 2 * x + (s & 1);
+        a.prop[2 * blk] = (float)a.range * tanhf(z[0]);
+        a.prop[2 * blk + 1] = (float)a.range * tanhf(z[1]);
+        a.conf[blk] = 1.0f / (1.0f + expf(-z[2]));
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 128);
+  if (!ok && tid == 0 && a.status) atomicExch(a.status, (int)BAYER_ERR_TIMEOUT);
+}
+
 template <int CIN, int EPI>
 cudaError_t launch_t(const ConvTcArgs& a, cudaStream_t st) {
   using L = RowConvLayout<CIN, EPI>;
@@ -277,7 +483,24 @@ cudaError_t pack_conv_tc_weights(const uint16_t* w, const int* w_off, const size
 cudaError_t configure_conv_tc() {
   cudaError_t e;
   if ((e = configure_t<32, 0>()) != cudaSuccess) return e;
-  return configure_t<32, 1>();
+  if ((e = configure_t<32, 1>()) != cudaSuccess) return e;
+  return cudaFuncSetAttribute(conv34_head_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, k34Smem);
+}
+
+bool conv34_head_supported(int W3) { return W3 >= 1 && W3 <= kM; }
+
+cudaError_t launch_conv34_head_tc(const ConvTcArgs& l3, const uint4* wimg4, const __nv_bfloat16* bias4, int H4, int W4,
+                                  cudaStream_t st) {
+  if (!conv34_head_supported(l3.Wo)) return cudaErrorInvalidValue;
+  Conv34Args c;
+  c.l3 = l3;
+  c.wimg4 = wimg4;
+  c.bias4 = bias4;
+  c.H4 = H4;
+  c.W4 = W4;
+  const long long grid = (long long)l3.batch * ((H4 + 1) / 2);
+  if (grid < 1) return cudaSuccess;
+  return tc::launch_dependent(conv34_head_tc_kernel, dim3((unsigned)grid), dim3(k34Threads), k34Smem, st, c);
 }
 
 cudaError_t launch_conv_tc(const ConvTcArgs& a, int layer, bool head, cudaStream_t st) {

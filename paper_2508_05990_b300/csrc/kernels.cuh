@@ -112,6 +112,12 @@ size_t conv_tc_weight_bytes(int cin_op);
 cudaError_t pack_conv_tc_weights(const uint16_t* w, const int* w_off, const size_t* img_off, uint16_t* img,
                                  cudaStream_t st);
 cudaError_t launch_conv_tc(const ConvTcArgs& a, int layer, bool head, cudaStream_t st);  // layers 3, 4
+// Inference: layers 3 and 4 and the head in one kernel (the layer-3 map stays
+// in shared memory); l3 describes layer 3 (and carries the head's fields),
+// wimg4 / bias4 layer 4.  Layer-3 rows of at most 128 pixels.
+bool conv34_head_supported(int W3);
+cudaError_t launch_conv34_head_tc(const ConvTcArgs& l3, const uint4* wimg4, const __nv_bfloat16* bias4, int H4, int W4,
+                                  cudaStream_t st);
 cudaError_t configure_conv_s2_rows_tc();
 cudaError_t launch_conv_s2_rows_tc(const ConvTcArgs& a, int layer, cudaStream_t st);
 
