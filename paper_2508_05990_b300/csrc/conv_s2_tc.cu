@@ -27,7 +27,8 @@
 //               kind::tf32 on the bf16 weights widened exactly to float32;
 //   warp 13     (layer 1 with 16-byte aligned frame rows) one thread copies
 //               the two raw rows of each staged half-resolution row of both
-//               frames by TMA into a ring that the producers convert from,
+//               frames by TMA (one box per frame) into a ring that the
+//               producers convert from,
 //               so that they do no global address arithmetic or loads.
 //               Otherwise the producers load the frames themselves.
 // Ring of staged rows: full mbarriers, and a slot is free again once the
@@ -67,11 +68,11 @@ template <int SRC>
 __host__ __device__ constexpr int threads_of() {
   return Roles<SRC>::THREADS;
 }
-// SRC 2 raw ring: per staged row, for each frame, 3 TMA boxes of 176 samples x
-// 2 raw rows (samples 512 * seg - 8 .. + 527 of raw rows 2r, 2r + 1), each box
-// at a 768-byte (128-byte aligned) step.
-constexpr int kRawBoxW = 176, kRawBoxBytes = kRawBoxW * 2 * 2, kRawBoxStep = 768;
-constexpr int kRawSlot = 6 * kRawBoxStep;
+// SRC 2 raw ring: per staged row, for each frame, one TMA box of 66 16-byte
+// chunks x 2 raw rows (samples 512 * seg - 8 .. + 527 of raw rows 2r, 2r + 1,
+// 1056 bytes per row), the frames 2176 bytes (128-byte aligned) apart.
+constexpr int kRawChunks = 66, kRawRowBytes = kRawChunks * 16, kRawBoxBytes = 2 * kRawRowBytes, kRawBoxStep = 2176;
+constexpr int kRawSlot = 2 * kRawBoxStep;
 constexpr int kTmemCols = kAcc * kN;
 constexpr uint32_t kWaitLimit = 1u << 22;
 
@@ -141,7 +142,7 @@ __device__ __forceinline__ void raise_abort(volatile int* abort_flag, int* statu
 // SRC 0: bf16 NHWC input [batch][Hi][Wi][CIN]; SRC 1: the Bayer frames (CIN =
 // 16: the bytes of 8 TF32 half-resolution planes), loaded by the producers;
 // SRC 2: the same, raw rows staged by TMA (tm_ref, tm_cur: boxes of
-// kRawBoxW x 2 samples over [batch][H][pitch]).
+// 66 chunks of 8 samples x 2 rows over [batch][H][W/8][8]).
 template <int CIN, int SRC>
 __global__ void __launch_bounds__(threads_of<SRC>(), 2)
     conv3x3s2_rows_tc_kernel(const ConvTcArgs a, const __grid_constant__ CUtensorMap tm_ref,
@@ -223,11 +224,10 @@ __global__ void __launch_bounds__(threads_of<SRC>(), 2)
             break;
           }
           if (r >= 0 && r < a.Hi) {
-            tma::mbar_arrive_expect_tx(&raw_full[s], 6 * kRawBoxBytes);
-#pragma unroll
-            for (int q = 0; q < 6; ++q)
-              tma::load_3d(sRaw + s * kRawSlot + q * kRawBoxStep, q < 3 ? &tm_ref : &tm_cur,
-                           4 * runs.seg * kM - 8 + kRawBoxW * (q % 3), 2 * r, runs.b, &raw_full[s]);
+            tma::mbar_arrive_expect_tx(&raw_full[s], 2 * kRawBoxBytes);
+            tma::load_4d(sRaw + s * kRawSlot, &tm_ref, 0, (4 * runs.seg * kM - 8) / 8, 2 * r, runs.b, &raw_full[s]);
+            tma::load_4d(sRaw + s * kRawSlot + kRawBoxStep, &tm_cur, 0, (4 * runs.seg * kM - 8) / 8, 2 * r, runs.b,
+                         &raw_full[s]);
           } else {
             tc::mbar_arrive(&raw_full[s]);
           }
@@ -242,16 +242,13 @@ __global__ void __launch_bounds__(threads_of<SRC>(), 2)
     // ---- producers: input rows 2ya-1 .. 2yb-1 of each run; group g takes rows j % G == g
     const int ptid = tid - R::PROD0 * 32;
     const int group = ptid / kGT, gtid = ptid - group * kGT;
-    // SRC 2: byte offset in a raw slot of the sample pair 2jj + 6 of column
-    // jj = gtid + kGT * i (box (2jj + 6) / kRawBoxW; the pair never straddles)
+    // SRC 2: byte offset in a raw row of the sample pair 2jj + 6 of column
+    // jj = gtid + kGT * i
     constexpr int kConvPer = (kNJ + kGT - 1) / kGT;
     int raw_off[SRC == 2 ? kConvPer : 1];
     if (SRC == 2) {
 #pragma unroll
-      for (int i = 0; i < kConvPer; ++i) {
-        const int o = 2 * (gtid + kGT * i) + 6, k = o / kRawBoxW;
-        raw_off[i] = k * kRawBoxStep + (o - k * kRawBoxW) * 2;
-      }
+      for (int i = 0; i < kConvPer; ++i) raw_off[i] = (2 * (gtid + kGT * i) + 6) * 2;
     }
     // A staged row is released by the commit of output row o_base + max(0,
     // (t - 1) / 2) (t: its index in the run; the MMA issues an odd row's ky = 0
@@ -317,7 +314,7 @@ __global__ void __launch_bounds__(threads_of<SRC>(), 2)
         } else if (SRC == 2) {
           // convert the TMA-staged raw rows: staged column jj (half-resolution
           // column c0 + jj) of frame fr reads raw samples 2jj + 6, 2jj + 7 of
-          // the slot's rows (box (2jj + 6) / kRawBoxW; the pair never straddles)
+          // the frame's two rows in the slot
           const int s = (int)(j % kRRm);
           if (!tc::mbar_wait(&raw_full[s], (uint32_t)((j / kRRm) & 1), kWaitLimit) ||
               !slot_free()) {
@@ -339,9 +336,9 @@ __global__ void __launch_bounds__(threads_of<SRC>(), 2)
               for (int fr = 0; fr < 2; ++fr) {
                 uint4 val = make_uint4(0, 0, 0, 0);
                 if (in) {
-                  const uint8_t* p0 = raw + raw_off[i] + fr * 3 * kRawBoxStep;
+                  const uint8_t* p0 = raw + raw_off[i] + fr * kRawBoxStep;
                   const uint32_t w0 = *reinterpret_cast<const uint32_t*>(p0);
-                  const uint32_t w1 = *reinterpret_cast<const uint32_t*>(p0 + kRawBoxW * 2);
+                  const uint32_t w1 = *reinterpret_cast<const uint32_t*>(p0 + kRawRowBytes);
                   val = make_uint4(tf32_sample12(w0 & 0xFFFFu), tf32_sample12(w0 >> 16),
                                    tf32_sample12(w1 & 0xFFFFu), tf32_sample12(w1 >> 16));
                 }
@@ -598,8 +595,10 @@ cudaError_t launch_conv_s2_rows_tc(const ConvTcArgs& a, int layer, cudaStream_t 
     // TMA raw rows where the frames' layout allows it (16-byte aligned rows
     // and batch strides), else the producers' own loads
     if (a.vec &&
-        tma::encode_u16_frames(&tm_ref, a.fr.ref, a.fr.W, a.fr.H, a.batch, a.fr.pitch, a.fr.ref_bs, kRawBoxW, 2) &&
-        tma::encode_u16_frames(&tm_cur, a.fr.cur, a.fr.W, a.fr.H, a.batch, a.fr.pitch, a.fr.cur_bs, kRawBoxW, 2))
+        tma::encode_u16_frame_chunks(&tm_ref, a.fr.ref, a.fr.W, a.fr.H, a.batch, a.fr.pitch, a.fr.ref_bs, kRawChunks,
+                                     2) &&
+        tma::encode_u16_frame_chunks(&tm_cur, a.fr.cur, a.fr.W, a.fr.H, a.batch, a.fr.pitch, a.fr.cur_bs, kRawChunks,
+                                     2))
       return launch_s2<16, 2>(a, tm_ref, tm_cur, st);
     return launch_s2<16, 1>(a, tm_ref, tm_cur, st);
   }

@@ -61,6 +61,29 @@ inline bool encode_u16_frames(CUtensorMap* map, const void* base, int W, int H, 
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// A rank-4 map over n frames of H x W uint16 samples seen as 16-byte chunks:
+// dims (8 samples, W/8 chunks, H rows, n frames), box 8 x box_chunks x box_h x
+// 1, so that one copy brings box_h rows of box_chunks * 8 consecutive samples
+// (more than the 256 of a box dimension) starting at a 16-byte chunk; chunks
+// and rows outside the frame read as 0.  Returns false when the driver entry
+// point is missing or the layout breaks an alignment rule (W % 8 == 0 too).
+inline bool encode_u16_frame_chunks(CUtensorMap* map, const void* base, int W, int H, int n, long long pitch,
+                                    long long frame_stride, int box_chunks, int box_h) {
+  const EncodeFn fn = encode_fn();
+  if (!fn) return false;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || ((pitch * 2) & 15) || (W & 7)) return false;
+  if (n > 1 && (frame_stride <= 0 || ((frame_stride * 2) & 15))) return false;
+  if (box_chunks > 256 || box_h > 256 || box_chunks < 1 || box_h < 1) return false;
+  const long long fstride = n > 1 ? frame_stride : pitch * H;  // unused when n == 1; any valid value
+  const cuuint64_t dims[4] = {8, (cuuint64_t)(W / 8), (cuuint64_t)H, (cuuint64_t)n};
+  const cuuint64_t strides[3] = {16, (cuuint64_t)(pitch * 2), (cuuint64_t)(((fstride * 2) + 15) / 16 * 16)};
+  const cuuint32_t box[4] = {8, (cuuint32_t)box_chunks, (cuuint32_t)box_h, 1};
+  const cuuint32_t estride[4] = {1, 1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, const_cast<void*>(base), dims, strides, box, estride,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // A rank-3 map over `planes` contiguous H x W float32 planes (row pitch W,
 // plane stride H * W elements), box box_w x box_h x 1, out-of-range elements
 // read as 0.  Returns false when the driver entry point is missing or the
@@ -97,6 +120,16 @@ __device__ __forceinline__ void load_3d(void* dst, const CUtensorMap* map, int x
       "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
       "[%5];" ::"r"(tc::smem_addr(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(tc::smem_addr(mbar))
+      : "memory");
+}
+
+// One box of a rank-4 `map` at (x, y, z, w) into shared memory at `dst`
+// (128-byte aligned); completes its bytes on `mbar`.
+__device__ __forceinline__ void load_4d(void* dst, const CUtensorMap* map, int x, int y, int z, int w, uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(tc::smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(tc::smem_addr(mbar))
       : "memory");
 }
 
