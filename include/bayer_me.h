@@ -252,7 +252,11 @@ bayer_status_t bayer_cnn_forward(bayer_me_t h, const uint16_t* ref, const uint16
 
 /* Loss (neg_weight = w_neg > 0) and its gradient w.r.t. all parameters on
  * `batch` pairs labelled by `labels` [batch][H/16][W/16] (the exhaustive-search fields): grad
- * [BAYER_CNN_NPARAMS] and loss [1], device float32, overwritten. */
+ * [BAYER_CNN_NPARAMS] and loss [1], device float32, overwritten.  The backward
+ * runs on the tensor cores with bfloat16 operands (the forward's activations
+ * and weights, each layer's pre-activation gradient rounded to bfloat16) and
+ * float32 accumulation; gradients are summed with atomics, so their last bits
+ * vary from call to call. */
 bayer_status_t bayer_cnn_loss_grad(bayer_me_t h, const uint16_t* ref, const uint16_t* cur, int W, int H, int pitch,
                                    int batch, long long ref_batch_stride, long long cur_batch_stride,
                                    const uint16_t* w_bf16, const bayer_mv_t* labels, int range, float neg_weight,

@@ -57,7 +57,6 @@ constexpr int kAcc = 4;     // TMEM accumulators (output rows in flight)
 template <int SRC>
 struct Roles {
   static constexpr int EPI = 4;
-  static constexpr int TEAMS = EPI / 4;
   static constexpr int MMA = EPI;
   static constexpr int PROD0 = MMA + 1;
   static constexpr int PROD = 8;
@@ -173,7 +172,7 @@ __global__ void __launch_bounds__(threads_of<SRC>(), 2)
     }
     for (int i = 0; i < kAcc; ++i) {
       tc::mbar_init(&acc_full[i], 1);
-      tc::mbar_init(&acc_empty[i], 4);  // the 4 warps of the team draining it
+      tc::mbar_init(&acc_empty[i], R::EPI);
     }
     tc::mbar_init(mma_done, 1);
     for (int s = 0; s < kRR; ++s) {
@@ -505,14 +504,13 @@ __global__ void __launch_bounds__(threads_of<SRC>(), 2)
     }
     __syncwarp();
   } else {
-    // ---- epilogue: thread = pixel of the segment = TMEM lane; team t drains
-    // the output rows o with o % TEAMS == t (warp w reads lanes 32 (w % 4) ..)
-    const int team = warp >> 2, quarter = warp & 3;
+    // ---- epilogue: thread = pixel of the segment = TMEM lane (warp w reads
+    // lanes 32w .. 32w + 31)
+    const int quarter = warp;
     long long o = 0;
     bool stop = false;
     while (!stop && runs.next()) {
       for (int y = runs.ya; y < runs.yb; ++y, ++o) {
-        if ((int)(o % R::TEAMS) != team) continue;
         const int acc = (int)(o % kAcc);
         const bool got = !*abort_flag && tc::mbar_wait(&acc_full[acc], (uint32_t)((o / kAcc) & 1), kWaitLimit);
         if (!__all_sync(0xffffffffu, got)) {
