@@ -34,10 +34,13 @@
 // gradients to the output once.
 // Layer 1's patches are the Bayer frames, split exactly as in the forward:
 // channel 2c + h of a tap is the hi (h = 0) or lo (h = 1) part of input plane
-// c, so dW1[co, c, tap] = D[hi] + D[lo] / 128.  With 16-byte aligned frame
-// rows the six raw rows of a chunk are copied whole (cp.async, two chunks
-// ahead) and converted in shared memory; otherwise each thread loads the
-// samples of its patches.
+// c, so dW1[co, c, tap] = D[hi] + D[lo] / 128, where each thread loads the
+// samples of its patches (any alignment).  With 16-byte aligned frame rows the
+// six raw rows and the output gradients of a chunk are copied whole (cp.async,
+// two chunks ahead) and converted in shared memory to K-major TF32 operands
+// instead: v/2048 - 1 has at most 11 significant bits, so TF32 holds it
+// exactly, and the bf16 gradients widen exactly (kind::tf32 MMAs, products
+// exact as well), at a quarter of the split's conversion work per sample.
 //
 // Every mbarrier wait is bounded; on expiry the kernel records
 // BAYER_ERR_TIMEOUT in the status word, frees its TMEM and finishes.
@@ -224,10 +227,9 @@ constexpr int kDwP = 64;         // output pixels per chunk: one row segment (4 
 constexpr int kRawPieces = 33;   // 16-byte pieces of a staged raw row: samples 4*ox0 - 8 .. 4*ox0 + 255
 
 // MODE 0: hidden maps (patches gathered by cp.async in 16-byte channel chunks);
-// MODE 1: Bayer frames, any alignment (per-thread sample loads);
-// MODE 2: Bayer frames with 16-byte aligned rows: the six raw rows a chunk
-// needs are copied by cp.async two chunks ahead into a ring and converted to
-// the hi/lo operand in shared memory.
+// MODE 1: Bayer frames, any alignment (per-thread sample loads, the exact
+// bf16 hi/lo split).  Layer 1 with 16-byte aligned frame rows has a kernel of
+// its own (conv_dw1_ring_tc_kernel, TF32 operands).
 template <int MODE>
 struct DwLayout {
   static constexpr bool FRAMES = MODE != 0;
@@ -240,19 +242,14 @@ struct DwLayout {
   static constexpr int A_BYTES = NCH * kDwP * 16;
   // B: cell (co chunk, pixel p) at (chunk * P + p) * 16.
   static constexpr int B_BYTES = 4 * kDwP * 16;
-  // MODE 2 raw ring: cell (frame f, raw row r, piece q) at ((f*6 + r)*kRawPieces + q) * 16
-  static constexpr int R_BYTES = 2 * 6 * kRawPieces * 16;
-  static constexpr int NB = MODE == 2 ? 4 : 2;  // B buffers (MODE 2: copies run two chunks ahead)
-  static constexpr int NR = MODE == 2 ? 3 : 0;  // raw buffers
   static constexpr int B_OFF = 2 * A_BYTES;
-  static constexpr int R_OFF = B_OFF + NB * B_BYTES;
-  static constexpr int MBAR_OFF = R_OFF + NR * R_BYTES;
+  static constexpr int MBAR_OFF = B_OFF + 2 * B_BYTES;
   static constexpr int SMEM = MBAR_OFF + 64;
   static constexpr int GS = KCH * 8 + 1;  // epilogue row stride: the patch rows and the ones row
   static constexpr int TMEM_COLS = MT == 2 ? 64 : 128;
   static_assert(kC * GS * 4 <= 2 * A_BYTES, "epilogue scratch fits in the A buffers");
   static_assert(KCH < NCH, "room for the ones row");
-  static_assert(B_OFF % 16 == 0 && R_OFF % 16 == 0 && MBAR_OFF % 8 == 0, "alignment");
+  static_assert(B_OFF % 16 == 0 && MBAR_OFF % 8 == 0, "alignment");
   static_assert(SMEM <= 113 * 1024, "two CTAs per SM");
 };
 
@@ -342,7 +339,7 @@ __device__ __forceinline__ void dw_stage_bayer_direct(const ConvBwdArgs& a, cons
   }
 }
 
-// MODE 2: raw rows 4oy - 2 .. 4oy + 3 of both frames, samples 4ox0 - 8 ..
+// Layer 1 (aligned frames): raw rows 4oy - 2 .. 4oy + 3 of both frames, samples 4ox0 - 8 ..
 // 4ox0 + 255 (zero-filled outside the frame) into a raw buffer.
 __device__ __forceinline__ void dw_stage_raw(const ConvBwdArgs& a, const Seg& s, uint32_t sR, int tid) {
   const uint16_t* ref = a.fr.ref + (long long)s.b * a.fr.ref_bs;
@@ -354,27 +351,6 @@ __device__ __forceinline__ void dw_stage_raw(const ConvBwdArgs& a, const Seg& s,
     const bool in = y >= 0 && y < a.fr.H && x >= 0 && x < a.fr.W;  // W % 8 == 0: whole pieces
     const uint16_t* src = in ? (f ? cur : ref) + (long long)y * a.fr.pitch + x : a.fr.ref;
     tc::cp_async16(sR + it * 16, src, in ? 16u : 0u);
-  }
-}
-
-// MODE 2: a staged raw buffer -> the chunk's A cells.  Patch (p, tap, f)
-// reads raw rows 2ky, 2ky + 1 at sample 4p + 2kx + 6 (= 2hx - (4ox0 - 8)).
-__device__ __forceinline__ void dw_convert_raw(const ConvBwdArgs& a, const Seg& s, const uint8_t* R, uint8_t* A,
-                                               int tid) {
-  const int Hh = a.fr.H / 2, Wh = a.fr.W / 2;
-#pragma unroll
-  for (int u = 0; u < (kDwP * 18 + kDwThreads - 1) / kDwThreads; ++u) {
-    const int it = tid + u * kDwThreads;
-    if (it < kDwP * 18) {
-      const int p = it & (kDwP - 1), tf = it / kDwP;
-      const int tap = tf >> 1, f = tf & 1, ky = tap / 3, kx = tap - 3 * ky;
-      const int ox = s.ox0 + p, hy = 2 * s.oy + ky - 1, hx = 2 * ox + kx - 1;
-      const bool in = ox < a.Wo && hy >= 0 && hy < Hh && hx >= 0 && hx < Wh;
-      const uint8_t* row = R + (f * 6 + 2 * ky) * (kRawPieces * 16) + 2 * (4 * p + 2 * kx + 6);
-      const uint32_t w0 = *reinterpret_cast<const uint32_t*>(row);
-      const uint32_t w1 = *reinterpret_cast<const uint32_t*>(row + kRawPieces * 16);
-      *reinterpret_cast<uint4*>(A + (tf * kDwP + p) * 16) = bayer_cell(in, w0, w1);
-    }
   }
 }
 
@@ -458,7 +434,6 @@ __device__ __forceinline__ void dw_epilogue(const ConvBwdArgs& a, uint8_t* smem,
 template <int MODE>
 __global__ void __launch_bounds__(kDwThreads, 2) conv_dw_tc_kernel(const ConvBwdArgs a, int chunks_per_cta) {
   using L = DwLayout<MODE>;
-  static_assert(MODE != 2, "MODE 2 has its own pipeline");
   extern __shared__ __align__(1024) uint8_t smem[];
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L::MBAR_OFF);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 2);
@@ -524,13 +499,79 @@ __global__ void __launch_bounds__(kDwThreads, 2) conv_dw_tc_kernel(const ConvBwd
   if (!ok && tid == 0 && a.status) atomicExch(a.status, (int)BAYER_ERR_TIMEOUT);
 }
 
-// MODE 2: raw rows and output gradients are copied two chunks ahead (raw ring
-// of 3, B ring of 4); per chunk the threads convert the staged raw rows into
-// the A buffer the MMAs of chunk i - 2 have released.
+// Layer 1 with 16-byte aligned frame rows (launch MODE 2): TF32 operands,
+// K-major.  The raw rows and the output gradients of a chunk are copied two
+// chunks ahead (rings of 3); per chunk the threads convert them into the A and
+// B buffers the MMAs of chunk i - 2 have released:
+//   A (M = 128 rows: patch row m = tap * 8 + frame * 4 + plane, 72 of them,
+//     row 72 = 1.0 for the bias, K = the chunk's 64 pixels): element (m, p) at
+//     (m/8) * kT1SBO + (p/4) * kT1LBO + (m%8) * 16 + (p%4) * 4, the float32
+//     value v/2048 - 1 (exact in TF32) of the patch's sample;
+//   B (N = 32 channels): element (co, p) at the same offsets, the bf16
+//     gradient widened exactly.
+// kT1LBO = 144 bytes (9 words) spreads the 4-pixel groups over distinct banks,
+// so a warp's 32 pixel stores of one row are conflict-free.  Only the first 10
+// of A's 16 row groups hold data (the MMA reads the others from whatever lies
+// after them: rows 80..127 of D are not used).
+constexpr int kT1LBO = 144, kT1SBO = (kDwP / 4) * kT1LBO;  // 2304
+constexpr int kT1ABytes = 10 * kT1SBO;                       // written part of A
+constexpr int kT1BBytes = 4 * kT1SBO;
+constexpr int kT1R = 2 * 6 * kRawPieces * 16;                // raw rows of a chunk (both frames)
+constexpr int kT1D = kDwP * kC * 2;                          // raw gradients of a chunk
+constexpr int kT1B_OFF = 2 * kT1ABytes;
+constexpr int kT1R_OFF = kT1B_OFF + 2 * kT1BBytes;
+constexpr int kT1D_OFF = kT1R_OFF + 3 * kT1R;
+constexpr int kT1MBAR_OFF = kT1D_OFF + 3 * kT1D;
+constexpr int kT1Smem = kT1MBAR_OFF + 64;
+constexpr int kT1GS = 73;  // epilogue row stride: 72 patch rows and the ones row
+static_assert(kT1MBAR_OFF - kT1ABytes >= 16 * kT1SBO, "the second A buffer's unused row groups stay in bounds");
+static_assert(kT1R_OFF % 16 == 0 && kT1D_OFF % 16 == 0 && kT1MBAR_OFF % 8 == 0, "alignment");
+static_assert(kT1Smem <= 113 * 1024, "two CTAs per SM");
+static_assert(kC * kT1GS * 4 <= 2 * kT1ABytes, "epilogue scratch fits in the A buffers");
+
+// The chunk's converted operands from its raw buffers.  Items (pixel p, tap,
+// frame) -> 4 plane values of patch rows tap*8 + frame*4 + plane; items (p,
+// channel group g of 8) -> 8 widened gradients.
+__device__ __forceinline__ void dw1_convert_tf32(const ConvBwdArgs& a, const Seg& s, const uint8_t* R,
+                                                 const uint8_t* Dr, uint8_t* A, uint8_t* B, int tid) {
+  const int Hh = a.fr.H / 2, Wh = a.fr.W / 2;
+  const int p = tid & (kDwP - 1), q = tid / kDwP;  // q = 0..3
+  const int ox = s.ox0 + p;
+  const int pix = (p >> 2) * kT1LBO + (p & 3) * 4;
+#pragma unroll
+  for (int u = 0; u < 5; ++u) {
+    const int tf = q + 4 * u;
+    if (tf < 18) {
+      const int tap = tf >> 1, f = tf & 1, ky = tap / 3, kx = tap - 3 * ky;
+      const int hy = 2 * s.oy + ky - 1, hx = 2 * ox + kx - 1;
+      const bool in = ox < a.Wo && hy >= 0 && hy < Hh && hx >= 0 && hx < Wh;
+      uint32_t w0 = 0, w1 = 0;
+      if (in) {
+        const uint8_t* row = R + (f * 6 + 2 * ky) * (kRawPieces * 16) + 2 * (4 * p + 2 * kx + 6);
+        w0 = *reinterpret_cast<const uint32_t*>(row);
+        w1 = *reinterpret_cast<const uint32_t*>(row + kRawPieces * 16);
+      }
+      uint8_t* dst = A + tap * kT1SBO + f * 4 * 16 + pix;
+      *reinterpret_cast<uint32_t*>(dst) = in ? tc::tf32_sample12(w0 & 0xFFFFu) : 0u;
+      *reinterpret_cast<uint32_t*>(dst + 16) = in ? tc::tf32_sample12(w0 >> 16) : 0u;
+      *reinterpret_cast<uint32_t*>(dst + 32) = in ? tc::tf32_sample12(w1 & 0xFFFFu) : 0u;
+      *reinterpret_cast<uint32_t*>(dst + 48) = in ? tc::tf32_sample12(w1 >> 16) : 0u;
+    }
+  }
+  // B: pixel p, channels 8q .. 8q + 7 (n-group q, rows n % 8)
+  const uint4 v = *reinterpret_cast<const uint4*>(Dr + p * 64 + q * 16);
+  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+  uint8_t* dst = B + q * kT1SBO + pix;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    *reinterpret_cast<uint32_t*>(dst + (2 * e) * 16) = w[e] << 16;
+    *reinterpret_cast<uint32_t*>(dst + (2 * e + 1) * 16) = w[e] & 0xFFFF0000u;
+  }
+}
+
 __global__ void __launch_bounds__(kDwThreads, 2) conv_dw1_ring_tc_kernel(const ConvBwdArgs a, int chunks_per_cta) {
-  using L = DwLayout<2>;
   extern __shared__ __align__(1024) uint8_t smem[];
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L::MBAR_OFF);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + kT1MBAR_OFF);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 2);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int segs = (a.Wo + kDwP - 1) / kDwP;
@@ -544,16 +585,27 @@ __global__ void __launch_bounds__(kDwThreads, 2) conv_dw1_ring_tc_kernel(const C
     tc::mbar_init(&mbar[1], 1);
     tc::fence_mbar_init();
   }
-  if (warp == 0) tc::tmem_alloc(tmem_slot, L::TMEM_COLS);
-  dw_init_pad<2>(smem, tid);
+  if (warp == 0) tc::tmem_alloc(tmem_slot, 32);
+  // row group 9 of both A buffers: row 72 = 1.0, rows 73..79 = 0 (never rewritten)
+  for (int i = tid; i < 2 * 8 * kDwP; i += kDwThreads) {
+    const int sb = i / (8 * kDwP), r = i - sb * (8 * kDwP);
+    const int row = r / kDwP, p = r - row * kDwP;
+    *reinterpret_cast<uint32_t*>(smem + sb * kT1ABytes + 9 * kT1SBO + (p >> 2) * kT1LBO + row * 16 + (p & 3) * 4) =
+        row == 0 ? 0x3F800000u : 0u;
+  }
   const uint32_t s0 = tc::smem_addr(smem);
   bool ok = true;
 
   auto issue = [&](int i) {  // copies of chunk i, one cp.async group (empty past the end)
     if (i < n) {
       const Seg s = seg_of(c_begin + i, a.Ho, segs);
-      dw_stage_raw(a, s, s0 + L::R_OFF + (i % 3) * L::R_BYTES, tid);
-      dw_stage_dout(a, s, s0 + L::B_OFF + (i & 3) * L::B_BYTES, tid);
+      dw_stage_raw(a, s, s0 + kT1R_OFF + (i % 3) * kT1R, tid);
+      const int kc = tid & 3, p = tid >> 2;  // raw gradients: pixel p at p * 64
+      const int ox = s.ox0 + p;
+      const bool in = ox < a.Wo;
+      const __nv_bfloat16* src =
+          in ? a.dout + (((long long)s.b * a.Ho + s.oy) * a.Wo + ox) * kC + kc * 8 : a.dout;
+      tc::cp_async16(s0 + kT1D_OFF + (i % 3) * kT1D + (p * 4 + kc) * 16, src, in ? 16u : 0u);
     }
     tc::cp_async_commit();
   };
@@ -562,10 +614,11 @@ __global__ void __launch_bounds__(kDwThreads, 2) conv_dw1_ring_tc_kernel(const C
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
+  constexpr uint32_t idesc = tc::idesc_tf32_f32(128, kC);  // K-major A and B
 
   for (int i = 0; i < n; ++i) {
     const int buf = i & 1;
-    // A[buf] and B[(i + 2) % 4] were read by the MMAs of chunk i - 2
+    // A[buf] and B[buf] were read by the MMAs of chunk i - 2
     if (i >= 2) ok &= tc::mbar_wait(&mbar[buf], ((i - 2) >> 1) & 1, kWaitLimit);
     issue(i + 2);
     tc::cp_async_wait<2>();  // chunk i's copies (this thread's) have landed
@@ -573,13 +626,20 @@ __global__ void __launch_bounds__(kDwThreads, 2) conv_dw1_ring_tc_kernel(const C
       tc::cp_async_wait_all();
       break;
     }
-    dw_convert_raw(a, seg_of(c_begin + i, a.Ho, segs), smem + L::R_OFF + (i % 3) * L::R_BYTES,
-                   smem + buf * L::A_BYTES, tid);
+    dw1_convert_tf32(a, seg_of(c_begin + i, a.Ho, segs), smem + kT1R_OFF + (i % 3) * kT1R,
+                     smem + kT1D_OFF + (i % 3) * kT1D, smem + buf * kT1ABytes, smem + kT1B_OFF + buf * kT1BBytes,
+                     tid);
     tc::fence_proxy_async();
     __syncthreads();
     if (tid == 0) {
       tc::fence_after_sync();
-      dw_mma<L::MT>(tmem, s0 + buf * L::A_BYTES, s0 + L::B_OFF + (i & 3) * L::B_BYTES, i == 0);
+      const uint32_t sa = s0 + buf * kT1ABytes, sb = s0 + kT1B_OFF + buf * kT1BBytes;
+#pragma unroll
+      for (int k = 0; k < kDwP / 8; ++k) {  // K step = 8 pixels = 2 groups of 4
+        const uint64_t ad = tc::smem_desc(sa + k * 2 * kT1LBO, kT1LBO, kT1SBO);
+        const uint64_t bd = tc::smem_desc(sb + k * 2 * kT1LBO, kT1LBO, kT1SBO);
+        tc::mma_tf32(tmem, ad, bd, idesc, (i > 0 || k > 0) ? 1u : 0u);
+      }
       tc::commit(&mbar[buf]);
     }
   }
@@ -587,9 +647,41 @@ __global__ void __launch_bounds__(kDwThreads, 2) conv_dw1_ring_tc_kernel(const C
   tc::cp_async_wait_all();
   ok = __syncthreads_and(ok);
   tc::fence_after_sync();
-  dw_epilogue<2>(a, smem, tmem, n > 0 && ok, tid);
+  // TMEM -> G[co][m] (over the A buffers) -> dW1[co][ci][tap] = G[co][tap*8 + ci], db = G[co][72]
+  float* G = reinterpret_cast<float*>(smem);
+  const bool live = n > 0 && ok;
+  if (live && warp < 4) {
+    float v[32];
+    tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
+    const int m = warp * 32 + (tid & 31);
+    if (m < kT1GS) {
+#pragma unroll
+      for (int co = 0; co < kC; ++co) G[co * kT1GS + m] = v[co];
+    }
+  }
+  tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, L::TMEM_COLS);
+  if (live) {
+    for (int i = tid; i < kC * 72 / 4; i += kDwThreads) {
+      const int co = (4 * i) / 72, j0 = 4 * i - co * 72;
+      float g[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int j = j0 + e, ci = j / 9, tap = j - 9 * ci;
+        g[e] = G[co * kT1GS + tap * 8 + ci];
+      }
+      float* dst = a.gw + co * 72 + j0;
+      if (a.vec_atomics) {
+        atomicAdd(reinterpret_cast<float4*>(dst), make_float4(g[0], g[1], g[2], g[3]));
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) atomicAdd(dst + e, g[e]);
+      }
+    }
+    if (tid < kC) atomicAdd(a.gb + tid, G[tid * kT1GS + 72]);
+  }
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 32);
   if (!ok && tid == 0 && a.status) atomicExch(a.status, (int)BAYER_ERR_TIMEOUT);
 }
 
@@ -599,25 +691,24 @@ int sm_count() {
   return nsm;
 }
 
-template <int MODE, typename K>
-cudaError_t launch_dw(K kern, const ConvBwdArgs& a, cudaStream_t st) {
-  using L = DwLayout<MODE>;
+template <typename K>
+cudaError_t launch_dw(K kern, const ConvBwdArgs& a, int smem, int tmem_cols, cudaStream_t st) {
   const long long nchunks = (long long)a.batch * a.Ho * ((a.Wo + kDwP - 1) / kDwP);
   if (nchunks < 1) return cudaSuccess;
   if (nchunks > 0x7FFFFFFFll) return cudaErrorInvalidValue;
-  const int per_sm = tc::ctas_per_sm(kern, kDwThreads, L::SMEM, L::TMEM_COLS);
+  const int per_sm = tc::ctas_per_sm(kern, kDwThreads, smem, tmem_cols);
   const long long slots = (long long)sm_count() * per_sm;
   // at least 4 chunks per CTA: the partial sums are added once per CTA
   long long per = (nchunks + slots - 1) / slots;
   if (per < 4) per = 4;
   const long long grid = (nchunks + per - 1) / per;
-  kern<<<(unsigned)grid, kDwThreads, L::SMEM, st>>>(a, (int)per);
+  kern<<<(unsigned)grid, kDwThreads, smem, st>>>(a, (int)per);
   return cudaGetLastError();
 }
 
-template <int MODE, typename K>
-cudaError_t configure_dw(K kern) {
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, DwLayout<MODE>::SMEM);
+template <typename K>
+cudaError_t configure_dw(K kern, int smem) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   return e;
 }
@@ -638,9 +729,9 @@ cudaError_t pack_conv_dx_weights(const uint16_t* w, const int* w_off, uint16_t* 
 cudaError_t configure_conv_bwd_tc() {
   cudaError_t e = cudaFuncSetAttribute(conv_dx_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDxSmem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(conv_dx_tc_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-  if (e == cudaSuccess) e = configure_dw<0>(conv_dw_tc_kernel<0>);
-  if (e == cudaSuccess) e = configure_dw<1>(conv_dw_tc_kernel<1>);
-  if (e == cudaSuccess) e = configure_dw<2>(conv_dw1_ring_tc_kernel);
+  if (e == cudaSuccess) e = configure_dw(conv_dw_tc_kernel<0>, DwLayout<0>::SMEM);
+  if (e == cudaSuccess) e = configure_dw(conv_dw_tc_kernel<1>, DwLayout<1>::SMEM);
+  if (e == cudaSuccess) e = configure_dw(conv_dw1_ring_tc_kernel, kT1Smem);
   return e;
 }
 
@@ -655,14 +746,14 @@ cudaError_t launch_conv_dx_tc(const ConvBwdArgs& a, cudaStream_t st) {
 }
 
 cudaError_t launch_conv_dw_tc(const ConvBwdArgs& a, bool frames, cudaStream_t st) {
-  if (!frames) return launch_dw<0>(conv_dw_tc_kernel<0>, a, st);
+  if (!frames) return launch_dw(conv_dw_tc_kernel<0>, a, DwLayout<0>::SMEM, DwLayout<0>::TMEM_COLS, st);
   // the raw-row ring copies 16-byte pieces: 16-byte aligned frames, pitch and
   // batch strides multiples of 8 samples (W is a multiple of 32)
   const bool ring = (reinterpret_cast<uintptr_t>(a.fr.ref) & 15) == 0 &&
                     (reinterpret_cast<uintptr_t>(a.fr.cur) & 15) == 0 && a.fr.pitch % 8 == 0 &&
                     a.fr.ref_bs % 8 == 0 && a.fr.cur_bs % 8 == 0 && a.fr.W % 8 == 0;
-  if (ring) return launch_dw<2>(conv_dw1_ring_tc_kernel, a, st);
-  return launch_dw<1>(conv_dw_tc_kernel<1>, a, st);
+  if (ring) return launch_dw(conv_dw1_ring_tc_kernel, a, kT1Smem, 32, st);
+  return launch_dw(conv_dw_tc_kernel<1>, a, DwLayout<1>::SMEM, DwLayout<1>::TMEM_COLS, st);
 }
 
 }  // namespace bme
