@@ -74,8 +74,12 @@ def check_forward(prop, conf, theta, ref, cur, R=32):
     assert ok.all(), ("vs bf16-rounded", np.argwhere(~ok)[:5])
 
 
-@pytest.mark.parametrize("shape", [(128, 192), (1088, 1920)])
+@pytest.mark.parametrize("shape", [(128, 192), (1088, 1920), (64, 2048), (96, 2080)])
 def test_cnn_forward_matches_oracle(handle, shape):
+    """128x192 and 1088x1920: layers 3, 4 and the head in one kernel; 64x2048:
+    its widest case (layer-3 rows of 128 pixels); 96x2080: layer-3 rows of 130
+    pixels, so the per-tile layer-3 and layer-4 kernels run instead (and H4 = 3
+    leaves the last layer-4 row pair half outside the map)."""
     H, W = shape
     ref, cur = synth.pan_clip(90, H, W, n_frames=2, rect_size=(16, 64))
     _, wbf, theta = weights(3)
