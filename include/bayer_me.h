@@ -315,7 +315,12 @@ bayer_status_t bayer_refine_conv(bayer_me_t h, const float* feat, int n, int Hf,
  * per strip 4 or 8; pairs as given or largest first; the per-size launches
  * smallest first) and keeps, among those within 3 % of the fastest step,
  * the one with the lowest median per-pair completion time (the handle's
- * autotune table).
+ * autotune table).  A bilinear propagation with stride < 16 whose feat is
+ * 16-byte aligned and Wf a multiple of 4 is staged through shared memory by
+ * TMA tile loads (a tensor map per pair, encoded on every call); other maps
+ * are read straight from global memory.  Either way the result is the same
+ * bit for bit.  A TMA wait that expires records BAYER_ERR_TIMEOUT in the
+ * handle's status word (bayer_me_sync_status).
  *   pairs: HOST array of n descriptors of device buffers (caller-owned).
  *   end_ns: optional device int64 [n]: per pair, nanoseconds from the start
  *     of the search launch until that pair's output (propagated features, or

@@ -689,7 +689,7 @@ bayer_status_t bayer_me_multi_stream(bayer_me_t h, const bayer_pair_t* pairs, in
   if (force != 0 && !bme::ms_schedule_valid(force)) return BAYER_ERR_INVALID_ARG;
   DeviceGuard g(h->device);
   if (!h->ms) {
-    h->ms = bme::ms_create(h->device);
+    h->ms = bme::ms_create(h->device, h->d_status);
     if (!h->ms) return BAYER_ERR_CUDA;
   }
   cudaError_t e = bme::ms_run(h->ms, pairs, n, range, interp, end_ns, force, static_cast<cudaStream_t>(stream));

@@ -199,9 +199,11 @@ cudaError_t launch_full16_list(const uint16_t* ref, const uint16_t* cur, int W, 
                                int max_count, bayer_mv_t* out, int* status, cudaStream_t st);
 cudaError_t configure_full16_list();
 
-// Multi-stream search + propagation (multistream.cu).
+// Multi-stream search + propagation (multistream.cu); status: the handle's
+// device status word, where a propagation wait that expires records
+// BAYER_ERR_TIMEOUT.
 struct MultiStream;
-MultiStream* ms_create(int device);
+MultiStream* ms_create(int device, int* status);
 void ms_destroy(MultiStream* m);
 cudaError_t configure_multistream();
 // force: a schedule code to run instead of the autotuned one (0: autotune).

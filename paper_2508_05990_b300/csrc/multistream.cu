@@ -17,11 +17,17 @@
 // after the block search: any (stamping, counting, even an untaken branch to
 // them) lowered its issue rate from 92 % to 78 % at the same instruction count
 // (0.5 ms over 66,000 strips).
-// Propagation: one CTA (256 threads) per (pair, 4-channel chunk, tile of 256
-// units) item, the pair found by binary search in a second prefix table,
-// warps the pair's NCHW feature map by its MV field (prop_common.cuh); a unit is a 2 x 2 quad of
-// cells sharing one MV (bilinear, two or more cells per block side) or one
-// cell.  Its CTAs stamp their own item slots.
+// Propagation: one CTA (288 threads) per item, the pair found by binary
+// search in a second prefix table; the CTA warps part of the pair's NCHW
+// feature map by its MV field.  Bilinear with two or more cells per block
+// side, on a map whose rows and base allow TMA loads: an item is a tile of
+// 16 x 64 cells and 16 channels staged through shared memory by TMA loads
+// (prop_tma.cuh), from a tensor map per pair that the host encodes into the
+// descriptor table on every call.  Otherwise an item is a chunk of 4
+// channels and a tile of 256 units on the first 256 threads, straight from
+// global memory (prop_common.cuh); a unit is a 2 x 2 quad of cells sharing
+// one MV (bilinear, two or more cells per block side) or one cell.  Its CTAs
+// stamp their own item slots.
 // Classes mode: the pairs sorted smallest first and cut into classes of equal
 // frame size (merged up to an eighth of the search each); each class gets its
 // own search launch and then its own
@@ -44,7 +50,9 @@
 #include "full16.cuh"
 #include "kernels.cuh"
 #include "prop_common.cuh"
+#include "prop_tma.cuh"
 #include "tc_common.cuh"
+#include "tma.cuh"
 
 namespace bme {
 
@@ -60,7 +68,9 @@ struct MsPair {
   int C, Hf, Wf, stride;
   int h, w, strips_x;
   int me_items, pr_items, prop_tiles;
-  int quads;  // propagation unit: 2 x 2 quad of cells (1) or one cell (0)
+  int quads;    // propagation unit: 2 x 2 quad of cells (1) or one cell (0)
+  int tma;      // propagation items are TMA-staged tiles (tensor map in the map table)
+  int tiles_x;  // TMA tiles per row of the map
   int vec;
 };
 
@@ -68,8 +78,10 @@ struct MsCounters {
   unsigned long long t0;  // earliest CTA start of the search launch (%globaltimer)
 };
 
-constexpr int kPropThreads = 256;
+constexpr int kPropThreads = 256;  // threads of a global-memory item
 constexpr int kPropCh = 4;
+constexpr int kMsPropThreads = prop::kTileThreads;  // 288: a TMA tile's consumers and producer warp
+constexpr int kTmaSmem = (int)sizeof(prop::TileStage) + 128;  // + alignment slack
 
 __device__ __forceinline__ unsigned long long gtimer() {
   unsigned long long t;
@@ -122,19 +134,44 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 4 : 6) ms_me_kernel(const M
   }
 }
 
-__global__ void __launch_bounds__(kPropThreads) ms_prop_kernel(const MsPair* __restrict__ pairs,
-                                                                const int* __restrict__ prefix, int n,
-                                                                unsigned long long* __restrict__ stamp, int interp,
-                                                                int item0) {
-  {
-    const int item = item0 + blockIdx.x;
-    const int p = find_pair(prefix, n, item);
-    const MsPair P = pairs[p];
-    const int local = item - __ldg(prefix + p);
-    const int chunk = local / P.prop_tiles, tile = local - chunk * P.prop_tiles;
+// Launched with kTmaSmem bytes of dynamic shared memory when its item range
+// holds a TMA item, else none.
+__global__ void __launch_bounds__(kMsPropThreads) ms_prop_kernel(const MsPair* __restrict__ pairs,
+                                                                  const CUtensorMap* __restrict__ maps,
+                                                                  const int* __restrict__ prefix, int n,
+                                                                  unsigned long long* __restrict__ stamp, int interp,
+                                                                  int item0, int* status) {
+  extern __shared__ unsigned char ms_dyn[];
+  const int item = item0 + blockIdx.x;
+  const int p = find_pair(prefix, n, item);
+  const MsPair P = pairs[p];
+  const int local = item - __ldg(prefix + p);
+  const int chunk = local / P.prop_tiles, tile = local - chunk * P.prop_tiles;
+  const int ls = __ffs(P.stride) - 1;  // stride: a power of two dividing 16
+  const int lc = 4 - ls;               // log2(cells per block side)
+  if (P.tma) {
+    prop::TileStage& s =
+        *reinterpret_cast<prop::TileStage*>((reinterpret_cast<uintptr_t>(ms_dyn) + 127) & ~(uintptr_t)127);
+    const int ty = tile / P.tiles_x, tx = tile - ty * P.tiles_x;
+    prop::TileJob j;
+    j.tm = maps + p;
+    j.feat = P.feat;
+    j.out = P.fout;
+    j.mv = P.mv;
+    j.mv_w = P.w;
+    j.Hf = P.Hf;
+    j.Wf = P.Wf;
+    j.ls = ls;
+    j.lc = lc;
+    j.plane0 = chunk * prop::kTC;
+    j.nc = min(prop::kTC, P.C - j.plane0);
+    j.y0 = ty * prop::kTileH;
+    j.x0 = tx * prop::kTileW;
+    j.status = status;
+    j.map_in_global = true;
+    prop::tma_tile(s, j);
+  } else if (threadIdx.x < kPropThreads) {
     const long long cells = (long long)P.Hf * P.Wf;
-    const int ls = __ffs(P.stride) - 1;  // stride: a power of two dividing 16
-    const int lc = 4 - ls;               // log2(cells per block side)
     const int unit = tile * kPropThreads + threadIdx.x;
     const int c0 = chunk * kPropCh;
     const int nc = min(kPropCh, P.C - c0);
@@ -177,9 +214,9 @@ __global__ void __launch_bounds__(kPropThreads) ms_prop_kernel(const MsPair* __r
           if (c < nc) __stcs(out + (long long)c * cells + unit, prop::blend(tp, va[c], vb[c], vc[c], vd[c]));
       }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) stamp[item] = gtimer();
   }
+  __syncthreads();
+  if (threadIdx.x == 0) stamp[item] = gtimer();
 }
 
 // One CTA per pair: the latest end stamp of its propagation items, or for a
@@ -254,7 +291,9 @@ cudaError_t ms_me_dispatch(int range, const MsPair* pairs, const int* prefix, in
 // graphs (one per set of frame sizes and schedule).
 struct MultiStream {
   int device = 0;
+  int* status = nullptr;  // the handle's device status word (bounded waits record BAYER_ERR_TIMEOUT)
   MsPair* d_pairs = nullptr;
+  CUtensorMap* d_maps = nullptr;  // [n] tensor maps of the TMA-staged pairs' feature maps
   int* d_prefix = nullptr;  // [2 * (n + 1)]: search prefix, then propagation prefix
   unsigned long long* d_stamp = nullptr;  // end time (%globaltimer) of every propagation item
   long long stamp_cap = 0;
@@ -262,6 +301,7 @@ struct MultiStream {
   long long* d_end = nullptr;  // [n] internal copy of end times
   int cap = 0;
   MsPair* h_pairs = nullptr;  // pinned staging of the table
+  CUtensorMap* h_maps = nullptr;
   int* h_prefix = nullptr;
   cudaEvent_t copied = nullptr;
   struct Entry {
@@ -279,9 +319,10 @@ static void ms_clear_graphs(MultiStream* m) {
   m->cache.clear();
 }
 
-MultiStream* ms_create(int device) {
+MultiStream* ms_create(int device, int* status) {
   MultiStream* m = new MultiStream();
   m->device = device;
+  m->status = status;
   cudaError_t e = cudaEventCreateWithFlags(&m->copied, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&m->capture, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMalloc(&m->d_ctr, sizeof(MsCounters));
@@ -297,11 +338,13 @@ void ms_destroy(MultiStream* m) {
   if (!m) return;
   ms_clear_graphs(m);
   if (m->d_pairs) cudaFree(m->d_pairs);
+  if (m->d_maps) cudaFree(m->d_maps);
   if (m->d_prefix) cudaFree(m->d_prefix);
   if (m->d_stamp) cudaFree(m->d_stamp);
   if (m->d_ctr) cudaFree(m->d_ctr);
   if (m->d_end) cudaFree(m->d_end);
   if (m->h_pairs) cudaFreeHost(m->h_pairs);
+  if (m->h_maps) cudaFreeHost(m->h_maps);
   if (m->h_prefix) cudaFreeHost(m->h_prefix);
   if (m->copied) cudaEventDestroy(m->copied);
   if (m->capture) cudaStreamDestroy(m->capture);
@@ -328,28 +371,63 @@ cudaError_t ensure_capacity(MultiStream* m, int n) {
   if (e != cudaSuccess) return e;
   ms_clear_graphs(m);  // graphs hold the old table addresses
   if (m->d_pairs) cudaFree(m->d_pairs);
+  if (m->d_maps) cudaFree(m->d_maps);
   if (m->d_prefix) cudaFree(m->d_prefix);
   if (m->d_end) cudaFree(m->d_end);
   if (m->h_pairs) cudaFreeHost(m->h_pairs);
+  if (m->h_maps) cudaFreeHost(m->h_maps);
   if (m->h_prefix) cudaFreeHost(m->h_prefix);
   m->d_pairs = nullptr;
+  m->d_maps = nullptr;
   m->d_prefix = nullptr;
   m->d_end = nullptr;
   m->h_pairs = nullptr;
+  m->h_maps = nullptr;
   m->h_prefix = nullptr;
   m->cap = 0;
   const int c = n < 64 ? 64 : n;
   if ((e = cudaMalloc(&m->d_pairs, sizeof(MsPair) * c)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&m->d_maps, sizeof(CUtensorMap) * c)) != cudaSuccess) return e;
   if ((e = cudaMalloc(&m->d_prefix, sizeof(int) * 2 * (c + 1))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&m->d_end, sizeof(long long) * c)) != cudaSuccess) return e;
   if ((e = cudaMallocHost(&m->h_pairs, sizeof(MsPair) * c)) != cudaSuccess) return e;
+  if ((e = cudaMallocHost(&m->h_maps, sizeof(CUtensorMap) * c)) != cudaSuccess) return e;
   if ((e = cudaMallocHost(&m->h_prefix, sizeof(int) * 2 * (c + 1))) != cudaSuccess) return e;
   m->cap = c;
   return cudaSuccess;
 }
 
-// Fill the pinned table in schedule order; returns the search and propagation item totals.
-void build_table(MultiStream* m, const bayer_pair_t* pairs, int n, const Config& cfg, int interp, int* me_total,
+// A pair's propagation items.  TMA tiles where the map allows them: bilinear
+// with two or more cells per block side, the map's rows and base 16-byte
+// aligned (the tensor map's rules), the tensor-map encoder present; the
+// choice depends only on the pair's sizes and the alignment of its feature
+// base, both part of a graph's signature.
+struct PropGeom {
+  int quads, tma, tiles_x, tiles, items;
+};
+
+PropGeom prop_geom(const bayer_pair_t& q, int interp) {
+  PropGeom g{};
+  if (!q.feat) return g;
+  g.quads = (interp == BAYER_INTERP_BILINEAR && q.stride < 16) ? 1 : 0;
+  g.tma = g.quads && (q.Wf % 4) == 0 && (reinterpret_cast<uintptr_t>(q.feat) % 16) == 0 &&
+          (long long)q.Hf * q.Wf <= (1ll << 31) - 256 && tma::encode_fn() != nullptr;
+  if (g.tma) {
+    g.tiles_x = (q.Wf + prop::kTileW - 1) / prop::kTileW;
+    g.tiles = g.tiles_x * ((q.Hf + prop::kTileH - 1) / prop::kTileH);
+    g.items = ((q.C + prop::kTC - 1) / prop::kTC) * g.tiles;
+  } else {
+    const long long units = g.quads ? (long long)((q.Hf + 1) / 2) * ((q.Wf + 1) / 2) : (long long)q.Hf * q.Wf;
+    g.tiles = (int)((units + kPropThreads - 1) / kPropThreads);
+    g.items = ((q.C + kPropCh - 1) / kPropCh) * g.tiles;
+  }
+  return g;
+}
+
+// Fill the pinned table and the tensor maps in schedule order; returns the
+// search and propagation item totals, or false if a tensor map could not be
+// encoded.
+bool build_table(MultiStream* m, const bayer_pair_t* pairs, int n, const Config& cfg, int interp, int* me_total,
                  int* pr_total, std::vector<int>* perm) {
   perm->resize(n);
   for (int i = 0; i < n; ++i) (*perm)[i] = i;
@@ -381,11 +459,14 @@ void build_table(MultiStream* m, const bayer_pair_t* pairs, int n, const Config&
     P.w = q.W / 16;
     P.strips_x = (P.w + cfg.nw - 1) / cfg.nw;
     P.me_items = P.h * P.strips_x;
-    // bilinear with two or more cells per block side works on 2 x 2 quads
-    P.quads = (interp == BAYER_INTERP_BILINEAR && q.stride < 16) ? 1 : 0;
-    const int units = P.quads ? ((q.Hf + 1) / 2) * ((q.Wf + 1) / 2) : q.Hf * q.Wf;
-    P.prop_tiles = q.feat ? (units + kPropThreads - 1) / kPropThreads : 0;
-    P.pr_items = q.feat ? ((q.C + kPropCh - 1) / kPropCh) * P.prop_tiles : 0;
+    const PropGeom g = prop_geom(q, interp);
+    P.quads = g.quads;
+    P.tma = g.tma;
+    P.tiles_x = g.tiles_x;
+    P.prop_tiles = g.tiles;
+    P.pr_items = g.items;
+    m->h_maps[k] = CUtensorMap{};
+    if (g.tma && !tma::encode_f32_planes(&m->h_maps[k], q.feat, q.Wf, q.Hf, q.C, prop::kBW, prop::kRH)) return false;
     P.vec = (reinterpret_cast<uintptr_t>(q.ref) % 16 == 0 && reinterpret_cast<uintptr_t>(q.cur) % 16 == 0 &&
              q.pitch % 8 == 0) ? 1 : 0;
     m->h_prefix[k] = me;
@@ -403,7 +484,7 @@ void build_table(MultiStream* m, const bayer_pair_t* pairs, int n, const Config&
   // classes cost more than they gain); at most kMaxClasses
   Classes& c = m->classes;
   c.n = 0;
-  if (!cfg.classes) return;
+  if (!cfg.classes) return true;
   std::vector<int> run_end;
   for (int k = 1; k <= n; ++k)
     if (k == n || pairs[(*perm)[k]].W != pairs[(*perm)[k - 1]].W || pairs[(*perm)[k]].H != pairs[(*perm)[k - 1]].H)
@@ -421,19 +502,13 @@ void build_table(MultiStream* m, const bayer_pair_t* pairs, int n, const Config&
     ++c.n;
     k0 = k1;
   }
+  return true;
 }
 
 // Propagation items of all pairs: the size of the stamp array.
 long long max_items(const bayer_pair_t* pairs, int n, int interp) {
   long long items = 0;
-  for (int i = 0; i < n; ++i) {
-    const bayer_pair_t& q = pairs[i];
-    if (q.feat) {
-      const bool quads = interp == BAYER_INTERP_BILINEAR && q.stride < 16;
-      const long long units = quads ? (long long)((q.Hf + 1) / 2) * ((q.Wf + 1) / 2) : (long long)q.Hf * q.Wf;
-      items += (long long)((q.C + kPropCh - 1) / kPropCh) * ((units + kPropThreads - 1) / kPropThreads);
-    }
-  }
+  for (int i = 0; i < n; ++i) items += prop_geom(pairs[i], interp).items;
   return items;
 }
 
@@ -456,9 +531,17 @@ cudaError_t search_items(MultiStream* m, int n, int range, const Config& cfg, in
                      : ms_me_dispatch<8>(range, m->d_pairs, m->d_prefix, n, i0, i1, m->d_ctr, st);
 }
 
+// Items [i0, i1) of the table last built: shared memory for TMA tiles only
+// where the range holds one.
 cudaError_t prop_items(MultiStream* m, int n, int interp, int i0, int i1, cudaStream_t st) {
   if (i1 <= i0) return cudaSuccess;
-  ms_prop_kernel<<<i1 - i0, kPropThreads, 0, st>>>(m->d_pairs, m->d_prefix + (n + 1), n, m->d_stamp, interp, i0);
+  bool tma = false;
+  for (int k = 0; k < n && !tma; ++k) {
+    const int b0 = m->h_prefix[(n + 1) + k], b1 = m->h_prefix[(n + 1) + k + 1];
+    tma = m->h_pairs[k].tma && b0 < i1 && b1 > i0;
+  }
+  ms_prop_kernel<<<i1 - i0, kMsPropThreads, tma ? kTmaSmem : 0, st>>>(m->d_pairs, m->d_maps, m->d_prefix + (n + 1), n,
+                                                                      m->d_stamp, interp, i0, m->status);
   return cudaGetLastError();
 }
 
@@ -488,13 +571,16 @@ cudaError_t enqueue(MultiStream* m, int n, int range, int interp, const Config& 
   return e;
 }
 
+// Everything a graph's launch shapes depend on: sizes, and whether each
+// pair's propagation runs as TMA tiles (which depends on its feature base's
+// alignment too).
 std::string signature(const bayer_pair_t* pairs, int n, int range, int interp) {
   std::string s = std::to_string(n) + ":" + std::to_string(range) + ":" + std::to_string(interp);
   for (int i = 0; i < n; ++i) {
     const bayer_pair_t& q = pairs[i];
     s += ";" + std::to_string(q.W) + "," + std::to_string(q.H) + "," + std::to_string(q.pitch) + "," +
          std::to_string(q.feat ? q.C : 0) + "," + std::to_string(q.Hf) + "," + std::to_string(q.Wf) + "," +
-         std::to_string(q.stride);
+         std::to_string(q.stride) + (prop_geom(q, interp).tma ? "t" : "");
   }
   return s;
 }
@@ -502,6 +588,8 @@ std::string signature(const bayer_pair_t* pairs, int n, int range, int interp) {
 // Refresh the device table from the pinned staging (after the previous copy has run).
 cudaError_t upload(MultiStream* m, int n, cudaStream_t st) {
   cudaError_t e = cudaMemcpyAsync(m->d_pairs, m->h_pairs, sizeof(MsPair) * n, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(m->d_maps, m->h_maps, sizeof(CUtensorMap) * n, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(m->d_prefix, m->h_prefix, sizeof(int) * 2 * (n + 1), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaEventRecord(m->copied, st);
@@ -529,7 +617,7 @@ cudaError_t ms_run(MultiStream* m, const bayer_pair_t* pairs, int n, int range, 
     MultiStream::Entry entry;
     entry.cfg = cfg;
     if ((e = cudaEventSynchronize(m->copied)) != cudaSuccess) return e;
-    build_table(m, pairs, n, cfg, interp, &me_total, &pr_total, &perm);
+    if (!build_table(m, pairs, n, cfg, interp, &me_total, &pr_total, &perm)) return cudaErrorInvalidValue;
     cudaGraph_t g = nullptr;
     if ((e = cudaStreamBeginCapture(m->capture, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
     cudaError_t ec = enqueue(m, n, range, interp, cfg, me_total, pr_total, m->capture);
@@ -553,7 +641,10 @@ cudaError_t ms_run(MultiStream* m, const bayer_pair_t* pairs, int n, int range, 
     for (int ci = 0; ci < NC; ++ci) {
       const Config& c = cands[ci];
       if ((e = cudaEventSynchronize(m->copied)) != cudaSuccess) break;
-      build_table(m, pairs, n, c, interp, &me_total, &pr_total, &perm);
+      if (!build_table(m, pairs, n, c, interp, &me_total, &pr_total, &perm)) {
+        e = cudaErrorInvalidValue;
+        break;
+      }
       if ((e = upload(m, n, st)) != cudaSuccess) break;
       if ((e = enqueue(m, n, range, interp, c, me_total, pr_total, st)) != cudaSuccess) break;  // warm
       cudaEventRecord(e0, st);
@@ -581,7 +672,7 @@ cudaError_t ms_run(MultiStream* m, const bayer_pair_t* pairs, int n, int range, 
     MultiStream::Entry entry;
     entry.cfg = best;
     if ((e = cudaEventSynchronize(m->copied)) != cudaSuccess) return e;
-    build_table(m, pairs, n, best, interp, &me_total, &pr_total, &perm);
+    if (!build_table(m, pairs, n, best, interp, &me_total, &pr_total, &perm)) return cudaErrorInvalidValue;
     cudaGraph_t g = nullptr;
     if ((e = cudaStreamBeginCapture(m->capture, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
     cudaError_t ec = enqueue(m, n, range, interp, best, me_total, pr_total, m->capture);
@@ -593,7 +684,7 @@ cudaError_t ms_run(MultiStream* m, const bayer_pair_t* pairs, int n, int range, 
     it = m->cache.emplace(key, entry).first;
   } else {
     if ((e = cudaEventSynchronize(m->copied)) != cudaSuccess) return e;
-    build_table(m, pairs, n, it->second.cfg, interp, &me_total, &pr_total, &perm);
+    if (!build_table(m, pairs, n, it->second.cfg, interp, &me_total, &pr_total, &perm)) return cudaErrorInvalidValue;
   }
   if ((e = upload(m, n, st)) != cudaSuccess) return e;
   if ((e = cudaGraphLaunch(it->second.exec, st)) != cudaSuccess) return e;

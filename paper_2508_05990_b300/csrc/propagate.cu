@@ -20,6 +20,7 @@
 #include "common.cuh"
 #include "kernels.cuh"
 #include "prop_common.cuh"
+#include "prop_tma.cuh"
 #include "tc_common.cuh"
 #include "tma.cuh"
 
@@ -108,135 +109,30 @@ __global__ void __launch_bounds__(kQT) prop_nchw_quad_kernel(const PropArgs a, i
 }
 
 // NCHW bilinear, two or more cells per block side, through shared memory:
-// a CTA owns a tile of kTQY x kTQX quads (16 x 64 cells) and kTC channels of
-// one map.  Per channel a TMA tile load stages the tile's source region --
-// the tile grown by kHalo cells on every side plus one more row and column
-// for the second bilinear tap (25 x 76 floats) -- into a ring of kNS buffers,
-// so kNS channels' loads are in flight at once.  At the map's borders the
-// load reads zeros outside; a tap row or column outside the map reads the
-// staged edge row or column instead (its index clamped to the staged rows and
-// columns inside the map, once per quad), which is the clamped element of the
-// map.  Every quad whose integer MV offsets lie within +-kHalo cells takes its
-// nine taps from the buffer: the same clamped elements as warp_quad reads from
-// global memory, blended in the same order, so the output is the same bit for
-// bit; a quad
-// with a larger offset reads its taps from global memory (warp_quad).  Each
-// warp covers one quad row of the tile: a channel's stores are 256-byte rows.
-// A ninth warp's lane 0 is the producer: it issues the loads and refills a
-// buffer once all 256 quads have read their taps from it (an "empty" mbarrier
-// of 256 arrivals per buffer; a "full" one completes with the load's bytes).
-// Every mbarrier wait is bounded (on expiry: BAYER_ERR_TIMEOUT and the thread
-// stops; a consumer that stops leaves its buffer unreleased, so the producer's
-// wait for it expires too).
-constexpr int kTQY = 8, kTQX = 32;             // quads per tile (rows, columns)
-constexpr int kHalo = 4;                       // cells: +-32 pixels at stride 8
-constexpr int kRH = 2 * kTQY + 2 * kHalo + 1;  // 25 staged rows
-constexpr int kRW = 2 * kTQX + 2 * kHalo + 1;  // 73 staged columns
-constexpr int kBW = (kRW + 3) / 4 * 4;         // 76: the box width (16-byte rows)
-constexpr int kTT = kTQY * kTQX;               // 256 threads
-constexpr int kTC = 16;                        // channels per CTA
-constexpr int kNS = 6;                         // staging buffers
-constexpr uint32_t kBoxBytes = kRH * kBW * 4;
-constexpr int kBufF = (kBoxBytes + 127) / 128 * 32;  // floats per buffer: 128-byte aligned buffers
-constexpr uint32_t kPropWait = 1u << 22;
-
-__global__ void __launch_bounds__(kTT + 32) prop_nchw_tma_kernel(const __grid_constant__ CUtensorMap tm,
-                                                                  const PropArgs a, int nchunks) {
-  __shared__ __align__(128) float buf[kNS][kBufF];
-  __shared__ __align__(8) uint64_t full[kNS], empty[kNS];
-  const int tid = threadIdx.x;
+// one CTA per tile of 16 x 64 cells and kTC channels of one map (grid.z =
+// map x channel chunk), the tile staged by TMA loads (prop_tma.cuh).
+__global__ void __launch_bounds__(kTileThreads) prop_nchw_tma_kernel(const __grid_constant__ CUtensorMap tm,
+                                                                      const PropArgs a, int nchunks) {
+  __shared__ __align__(128) TileStage stage;
   const int m = blockIdx.z / nchunks;
   const int c0 = (blockIdx.z - m * nchunks) * kTC;
-  const int nc = min(kTC, a.C - c0);
-  const int y0 = blockIdx.y * 2 * kTQY, x0 = blockIdx.x * 2 * kTQX;  // tile origin (cells)
-  const long long cells = (long long)a.Hf * a.Wf;
-  const int plane0 = m * a.C + c0;
-
-  if (tid == 0) {
-    for (int i = 0; i < kNS; ++i) {
-      tc::mbar_init(&full[i], 1);
-      tc::mbar_init(&empty[i], kTT);
-    }
-    tc::fence_mbar_init();
-  }
-  __syncthreads();
-
-  if (tid >= kTT) {
-    // producer warp: one lane refills each buffer once its kTT readers are done
-    if (tid == kTT) {
-      for (int c = 0; c < nc; ++c) {
-        const int sl = c % kNS;
-        if (c >= kNS && !tc::mbar_wait(&empty[sl], (uint32_t)(((c - kNS) / kNS) & 1), kPropWait)) {
-          if (a.status) atomicExch(a.status, (int)BAYER_ERR_TIMEOUT);
-          break;
-        }
-        tma::mbar_arrive_expect_tx(&full[sl], kBoxBytes);
-        tma::load_3d(buf[sl], &tm, x0 - kHalo, y0 - kHalo, plane0 + c, &full[sl]);
-      }
-    }
-    return;
-  }
-
-  // this thread's quad
-  const int qy = tid / kTQX, qx = tid - qy * kTQX;
-  const int fy = y0 + 2 * qy, fx = x0 + 2 * qx;
-  const bool live = fy < a.Hf && fx < a.Wf;
-  bayer_mv_t mv{};
-  if (live) mv = a.mv[((long long)m * a.mv_h + (fy >> a.lc)) * a.mv_w + (fx >> a.lc)];
-  const Taps tp = bilinear_taps(a.ls, a.Hf, a.Wf, fy, fx, mv);
-  const int oy = (int)mv.dy >> a.ls, ox = (int)mv.dx >> a.ls;
-  const bool near = oy >= -kHalo && oy <= kHalo && ox >= -kHalo && ox <= kHalo;
-  const bool row2 = fy + 1 < a.Hf, col2 = fx + 1 < a.Wf;
-  const bool pair_store = col2 && (a.Wf & 1) == 0;
-  // the staged rows [top, bot) and columns [lft, rgt) lie inside the map; a tap
-  // outside them reads the nearest one inside, which is the clamped element
-  const int top = max(0, kHalo - y0), bot = min(kRH, a.Hf - (y0 - kHalo));
-  const int lft = max(0, kHalo - x0), rgt = min(kRW, a.Wf - (x0 - kHalo));
-  int tr[3], tcol[3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    tr[i] = clampi(2 * qy + oy + kHalo + i, top, bot - 1) * kBW;
-    tcol[i] = clampi(2 * qx + ox + kHalo + i, lft, rgt - 1);
-  }
-
-  for (int c = 0; c < nc; ++c) {
-    const int sl = c % kNS;
-    const float* bf = buf[sl];
-    if (!tc::mbar_wait(&full[sl], (uint32_t)((c / kNS) & 1), kPropWait)) {
-      if (a.status) atomicExch(a.status, (int)BAYER_ERR_TIMEOUT);
-      return;
-    }
-    if (live) {
-      float* o = a.out + (long long)(plane0 + c) * cells + (long long)fy * a.Wf + fx;
-      if (near) {
-        float v[9];
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-          for (int j = 0; j < 3; ++j) v[3 * i + j] = bf[tr[i] + tcol[j]];
-        tc::mbar_arrive(&empty[sl]);  // the taps are in registers: the buffer may refill
-        const float r00 = blend(tp, v[0], v[1], v[3], v[4]), r01 = blend(tp, v[1], v[2], v[4], v[5]);
-        const float r10 = blend(tp, v[3], v[4], v[6], v[7]), r11 = blend(tp, v[4], v[5], v[7], v[8]);
-        if (pair_store) {
-          __stcs(reinterpret_cast<float2*>(o), make_float2(r00, r01));
-          if (row2) __stcs(reinterpret_cast<float2*>(o + a.Wf), make_float2(r10, r11));
-        } else {
-          __stcs(o, r00);
-          if (col2) __stcs(o + 1, r01);
-          if (row2) {
-            __stcs(o + a.Wf, r10);
-            if (col2) __stcs(o + a.Wf + 1, r11);
-          }
-        }
-        continue;
-      }
-      tc::mbar_arrive(&empty[sl]);
-      warp_quad<1>(a.feat + (long long)(plane0 + c) * cells, a.out + (long long)(plane0 + c) * cells, cells, a.Hf,
-                   a.Wf, a.ls, fy, fx, mv, 1);
-    } else {
-      tc::mbar_arrive(&empty[sl]);
-    }
-  }
+  TileJob j;
+  j.tm = &tm;
+  j.feat = a.feat;
+  j.out = a.out;
+  j.mv = a.mv + (long long)m * a.mv_h * a.mv_w;
+  j.mv_w = a.mv_w;
+  j.Hf = a.Hf;
+  j.Wf = a.Wf;
+  j.ls = a.ls;
+  j.lc = a.lc;
+  j.plane0 = m * a.C + c0;
+  j.nc = min(kTC, a.C - c0);
+  j.y0 = blockIdx.y * kTileH;
+  j.x0 = blockIdx.x * kTileW;
+  j.status = a.status;
+  j.map_in_global = false;
+  tma_tile(stage, j);
 }
 
 // NHWC with C % 4 == 0: one thread per (cell, 4 channels) of one feature row
@@ -322,8 +218,8 @@ cudaError_t launch_propagate(const PropArgs& args, int layout, int interp, cudaS
       (long long)a.Hf * a.Wf <= (1ll << 31) - 256 &&
       tma::encode_f32_planes(&tm, a.feat, a.Wf, a.Hf, (long long)a.n * a.C, kBW, kRH)) {
     const int nchunks = (a.C + kTC - 1) / kTC;
-    dim3 g((a.Wf + 2 * kTQX - 1) / (2 * kTQX), (a.Hf + 2 * kTQY - 1) / (2 * kTQY), a.n * nchunks);
-    prop_nchw_tma_kernel<<<g, kTT + 32, 0, st>>>(tm, a, nchunks);
+    dim3 g((a.Wf + kTileW - 1) / kTileW, (a.Hf + kTileH - 1) / kTileH, a.n * nchunks);
+    prop_nchw_tma_kernel<<<g, kTileThreads, 0, st>>>(tm, a, nchunks);
   } else if (layout == BAYER_LAYOUT_NCHW && interp == BAYER_INTERP_BILINEAR && a.lc >= 1 &&
              (long long)a.n * ((a.C + kQK - 1) / kQK) <= 65535 && (long long)a.Hf * a.Wf <= (1ll << 31) - 256) {
     const int nchunks = (a.C + kQK - 1) / kQK;

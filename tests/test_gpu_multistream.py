@@ -12,7 +12,12 @@ from paper_2508_05990_b300 import synth
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-SIZES = [(128, 160, 32, 8), (128, 160, 16, 4), (272, 480, 32, 8), (96, 64, 8, 16), (64, 96, 0, 8)]
+# (H, W, C, stride): TMA-staged tiles where Wf % 4 == 0 (one with a ragged
+# 16-channel chunk, one at stride 4 where pan offsets pass the staged halo),
+# global-memory items at stride 16 and where Wf % 4 != 0, and a pair without
+# features
+SIZES = [(128, 160, 32, 8), (128, 160, 16, 4), (272, 480, 32, 8), (96, 64, 8, 16), (64, 96, 0, 8),
+         (64, 48, 20, 8), (160, 128, 20, 4)]
 
 
 @pytest.fixture(scope="module")
@@ -118,3 +123,35 @@ def test_multi_stream_bench_configuration(handle, schedule):
             pw = oracle.propagate(q["feat_np"], want, 16, s, interp=oracle.BILINEAR)
             np.testing.assert_array_equal(q["feat_out"].cpu().numpy().view(np.uint32), pw.view(np.uint32))
     assert len(checked) == 4
+
+
+def test_multi_stream_feature_alignment(handle):
+    """The same sizes with the feature maps 16-byte aligned (TMA-staged
+    propagation tiles) and one float off (global-memory items): each call
+    keeps a graph of its own, and both are bit-exact with the oracle, in
+    either order and again on a repeated call."""
+    sizes = [(128, 160, 24, 8), (96, 128, 16, 4)]
+    frames, feats = [], []
+    for i, (H, W, C, s) in enumerate(sizes):
+        frames.append(synth.pan_clip(700 + i, H, W, n_frames=2, rect_size=(8, 48)))
+        feats.append(synth.features(750 + i, C, H // s, W // s)[0])
+    want = [oracle.me_full(fr[0], fr[1], 16, 32, even=True)[0] for fr in frames]
+    prop = [oracle.propagate(f, w, 16, s, interp=oracle.BILINEAR) for f, w, (_, _, _, s) in zip(feats, want, sizes)]
+    for shift in (0, 1, 0, 1):
+        streams = []
+        for fr, f, (H, W, C, s) in zip(frames, feats, sizes):
+            base = torch.zeros(f.size + 4, device="cuda")
+            base[shift:shift + f.size] = torch.from_numpy(f.ravel()).cuda()
+            fin = base[shift:shift + f.size].view(C, H // s, W // s)
+            assert (fin.data_ptr() % 16 == 0) == (shift == 0)
+            streams.append({"ref": torch.from_numpy(fr[0]).cuda(), "cur": torch.from_numpy(fr[1]).cuda(),
+                            "mv": torch.empty((H // 16, W // 16, 2), dtype=torch.int32, device="cuda"),
+                            "feat": fin, "feat_out": torch.empty((C, H // s, W // s), device="cuda"), "stride": s})
+        handle.multi_stream(streams, 32)
+        torch.cuda.synchronize()
+        assert handle.sync_status() == bm.OK
+        for q, w, pw in zip(streams, want, prop):
+            got = bm.records_to_numpy(q["mv"])
+            for k in ("dx", "dy", "sad"):
+                np.testing.assert_array_equal(got[k], w[k])
+            np.testing.assert_array_equal(q["feat_out"].cpu().numpy().view(np.uint32), pw.view(np.uint32))
