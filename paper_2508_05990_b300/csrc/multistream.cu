@@ -5,7 +5,11 @@
 //
 // Search: one CTA (NW warps) per strip of NW adjacent blocks of any pair; the
 // CTA finds its pair by binary search in a prefix table over the strips of
-// all pairs, stages the strip's window (full16.cuh) and searches it.  The
+// all pairs, stages the strip's window (full16.cuh) and searches it.  Frames
+// with 16-byte aligned rows are staged by two TMA tile loads (window and
+// current tile, as in the single-pair search) from tensor maps per pair that
+// the host encodes for the schedule's strip width into the map table on
+// every call; other frames by 16-byte or pair-word loads.  The
 // hardware block scheduler balances the strips (a persistent variant with an
 // atomic work queue measured slower once the search itself got cheaper).
 // Completion times, from %globaltimer, relative to the search launch's start
@@ -71,7 +75,14 @@ struct MsPair {
   int quads;    // propagation unit: 2 x 2 quad of cells (1) or one cell (0)
   int tma;      // propagation items are TMA-staged tiles (tensor map in the map table)
   int tiles_x;  // TMA tiles per row of the map
-  int vec;
+  int vec;      // 16-byte aligned frame rows
+  int win_tma;  // search window and current tile staged by TMA (maps ref, cur)
+};
+
+// Tensor maps of one pair: its frames (boxes of the schedule's strip) and its
+// feature map.
+struct MsMaps {
+  CUtensorMap ref, cur, feat;
 };
 
 struct MsCounters {
@@ -99,10 +110,13 @@ __device__ __forceinline__ int find_pair(const int* prefix, int n, int item) {
   return lo;
 }
 
+constexpr uint32_t kStripWait = 1u << 22;
+
 template <int R, int NW>
 __global__ void __launch_bounds__(NW * 32, NW == 8 ? 4 : 6) ms_me_kernel(const MsPair* __restrict__ pairs,
+                                                                          const MsMaps* __restrict__ maps,
                                                                           const int* __restrict__ prefix, int n,
-                                                                          MsCounters* ctr, int item0) {
+                                                                          MsCounters* ctr, int item0, int* status) {
   using C = Full16Strip<R, NW>;
   extern __shared__ __align__(16) uint32_t smem[];
   uint32_t* win = smem;
@@ -122,8 +136,33 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 4 : 6) ms_me_kernel(const M
   const int by = local / strips_x, sx = local - by * strips_x;
   const int x0 = sx * NW * 16, y0 = by * 16;
   const int W = P->W, H = P->H;
-  stage_strip<R, NW>(P->ref, P->cur, W, H, P->pitch, x0, y0, P->vec != 0, win, curt);
-  __syncthreads();
+  if (P->win_tma) {
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + C::MBAR_OFF);
+    if (threadIdx.x == 0) {
+      const MsMaps* mp = maps + p;
+      tma::fence_map_acquire(&mp->ref);
+      tma::fence_map_acquire(&mp->cur);
+      tc::mbar_init(mbar, 1);
+      tc::fence_mbar_init();
+      tma::mbar_arrive_expect_tx(mbar, C::TX_BYTES);
+      tma::load_3d(win, &mp->ref, x0 - C::REACH, y0 - C::REACH, 0, mbar);
+      tma::load_3d(curt, &mp->cur, x0, y0, 0, mbar);
+    }
+    __syncthreads();  // the barrier is initialised before anyone waits on it
+    const bool ok = tc::mbar_wait(mbar, 0, kStripWait);
+    if (!__syncthreads_and(ok)) {
+      // record the expiry, give the copies a last bounded wait, and stop
+      if (threadIdx.x == 0) {
+        if (status) atomicExch(status, (int)BAYER_ERR_TIMEOUT);
+        tc::mbar_wait(mbar, 0, kStripWait);
+      }
+      __syncthreads();
+      return;
+    }
+  } else {
+    stage_strip<R, NW>(P->ref, P->cur, W, H, P->pitch, x0, y0, P->vec != 0, win, curt);
+    __syncthreads();
+  }
   window_colsums<R, C::P, C::WW, NW * 32>(win, cs, threadIdx.x);
   __syncthreads();
   const int bx = sx * NW + warp;
@@ -137,7 +176,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 4 : 6) ms_me_kernel(const M
 // Launched with kTmaSmem bytes of dynamic shared memory when its item range
 // holds a TMA item, else none.
 __global__ void __launch_bounds__(kMsPropThreads) ms_prop_kernel(const MsPair* __restrict__ pairs,
-                                                                  const CUtensorMap* __restrict__ maps,
+                                                                  const MsMaps* __restrict__ maps,
                                                                   const int* __restrict__ prefix, int n,
                                                                   unsigned long long* __restrict__ stamp, int interp,
                                                                   int item0, int* status) {
@@ -154,7 +193,7 @@ __global__ void __launch_bounds__(kMsPropThreads) ms_prop_kernel(const MsPair* _
         *reinterpret_cast<prop::TileStage*>((reinterpret_cast<uintptr_t>(ms_dyn) + 127) & ~(uintptr_t)127);
     const int ty = tile / P.tiles_x, tx = tile - ty * P.tiles_x;
     prop::TileJob j;
-    j.tm = maps + p;
+    j.tm = &maps[p].feat;
     j.feat = P.feat;
     j.out = P.fout;
     j.mv = P.mv;
@@ -265,23 +304,43 @@ cudaError_t ms_me_configure() {
 }
 
 template <int R, int NW>
-cudaError_t ms_me_launch(const MsPair* pairs, const int* prefix, int n, int item0, int item1, MsCounters* ctr,
-                         cudaStream_t st) {
+cudaError_t ms_me_launch(const MsPair* pairs, const MsMaps* maps, const int* prefix, int n, int item0, int item1,
+                         MsCounters* ctr, int* status, cudaStream_t st) {
   using C = Full16Strip<R, NW>;
   if (item1 <= item0) return cudaSuccess;
-  ms_me_kernel<R, NW><<<item1 - item0, NW * 32, C::SMEM, st>>>(pairs, prefix, n, ctr, item0);
+  ms_me_kernel<R, NW><<<item1 - item0, NW * 32, C::SMEM, st>>>(pairs, maps, prefix, n, ctr, item0, status);
   return cudaGetLastError();
 }
 
 template <int NW>
-cudaError_t ms_me_dispatch(int range, const MsPair* pairs, const int* prefix, int n, int item0, int item1,
-                           MsCounters* ctr, cudaStream_t st) {
+cudaError_t ms_me_dispatch(int range, const MsPair* pairs, const MsMaps* maps, const int* prefix, int n, int item0,
+                           int item1, MsCounters* ctr, int* status, cudaStream_t st) {
   switch (range) {
-    case 8: return ms_me_launch<4, NW>(pairs, prefix, n, item0, item1, ctr, st);
-    case 16: return ms_me_launch<8, NW>(pairs, prefix, n, item0, item1, ctr, st);
-    case 24: return ms_me_launch<12, NW>(pairs, prefix, n, item0, item1, ctr, st);
-    case 32: return ms_me_launch<16, NW>(pairs, prefix, n, item0, item1, ctr, st);
+    case 8: return ms_me_launch<4, NW>(pairs, maps, prefix, n, item0, item1, ctr, status, st);
+    case 16: return ms_me_launch<8, NW>(pairs, maps, prefix, n, item0, item1, ctr, status, st);
+    case 24: return ms_me_launch<12, NW>(pairs, maps, prefix, n, item0, item1, ctr, status, st);
+    case 32: return ms_me_launch<16, NW>(pairs, maps, prefix, n, item0, item1, ctr, status, st);
     default: return cudaErrorInvalidValue;
+  }
+}
+
+// The search frames' tensor maps of one pair for strips of NW blocks and
+// reach 2R (window box BOX_W x WIN_H, current box CUR_BOX_W x 16).
+template <int R, int NW>
+bool encode_strip_maps(MsMaps* mp, const bayer_pair_t& q) {
+  using C = Full16Strip<R, NW>;
+  return tma::encode_u16_frames(&mp->ref, q.ref, q.W, q.H, 1, q.pitch, 0, C::BOX_W, C::WIN_H) &&
+         tma::encode_u16_frames(&mp->cur, q.cur, q.W, q.H, 1, q.pitch, 0, C::CUR_BOX_W, 16);
+}
+
+template <int NW>
+bool encode_strip_maps_nw(int range, MsMaps* mp, const bayer_pair_t& q) {
+  switch (range) {
+    case 8: return encode_strip_maps<4, NW>(mp, q);
+    case 16: return encode_strip_maps<8, NW>(mp, q);
+    case 24: return encode_strip_maps<12, NW>(mp, q);
+    case 32: return encode_strip_maps<16, NW>(mp, q);
+    default: return false;
   }
 }
 
@@ -293,7 +352,7 @@ struct MultiStream {
   int device = 0;
   int* status = nullptr;  // the handle's device status word (bounded waits record BAYER_ERR_TIMEOUT)
   MsPair* d_pairs = nullptr;
-  CUtensorMap* d_maps = nullptr;  // [n] tensor maps of the TMA-staged pairs' feature maps
+  MsMaps* d_maps = nullptr;  // [n] tensor maps of the TMA-staged pairs' frames and feature maps
   int* d_prefix = nullptr;  // [2 * (n + 1)]: search prefix, then propagation prefix
   unsigned long long* d_stamp = nullptr;  // end time (%globaltimer) of every propagation item
   long long stamp_cap = 0;
@@ -301,7 +360,7 @@ struct MultiStream {
   long long* d_end = nullptr;  // [n] internal copy of end times
   int cap = 0;
   MsPair* h_pairs = nullptr;  // pinned staging of the table
-  CUtensorMap* h_maps = nullptr;
+  MsMaps* h_maps = nullptr;
   int* h_prefix = nullptr;
   cudaEvent_t copied = nullptr;
   struct Entry {
@@ -387,11 +446,11 @@ cudaError_t ensure_capacity(MultiStream* m, int n) {
   m->cap = 0;
   const int c = n < 64 ? 64 : n;
   if ((e = cudaMalloc(&m->d_pairs, sizeof(MsPair) * c)) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&m->d_maps, sizeof(CUtensorMap) * c)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&m->d_maps, sizeof(MsMaps) * c)) != cudaSuccess) return e;
   if ((e = cudaMalloc(&m->d_prefix, sizeof(int) * 2 * (c + 1))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&m->d_end, sizeof(long long) * c)) != cudaSuccess) return e;
   if ((e = cudaMallocHost(&m->h_pairs, sizeof(MsPair) * c)) != cudaSuccess) return e;
-  if ((e = cudaMallocHost(&m->h_maps, sizeof(CUtensorMap) * c)) != cudaSuccess) return e;
+  if ((e = cudaMallocHost(&m->h_maps, sizeof(MsMaps) * c)) != cudaSuccess) return e;
   if ((e = cudaMallocHost(&m->h_prefix, sizeof(int) * 2 * (c + 1))) != cudaSuccess) return e;
   m->cap = c;
   return cudaSuccess;
@@ -427,8 +486,8 @@ PropGeom prop_geom(const bayer_pair_t& q, int interp) {
 // Fill the pinned table and the tensor maps in schedule order; returns the
 // search and propagation item totals, or false if a tensor map could not be
 // encoded.
-bool build_table(MultiStream* m, const bayer_pair_t* pairs, int n, const Config& cfg, int interp, int* me_total,
-                 int* pr_total, std::vector<int>* perm) {
+bool build_table(MultiStream* m, const bayer_pair_t* pairs, int n, const Config& cfg, int interp, int range,
+                 int* me_total, int* pr_total, std::vector<int>* perm) {
   perm->resize(n);
   for (int i = 0; i < n; ++i) (*perm)[i] = i;
   if (cfg.order == 1)
@@ -465,10 +524,14 @@ bool build_table(MultiStream* m, const bayer_pair_t* pairs, int n, const Config&
     P.tiles_x = g.tiles_x;
     P.prop_tiles = g.tiles;
     P.pr_items = g.items;
-    m->h_maps[k] = CUtensorMap{};
-    if (g.tma && !tma::encode_f32_planes(&m->h_maps[k], q.feat, q.Wf, q.Hf, q.C, prop::kBW, prop::kRH)) return false;
+    m->h_maps[k] = MsMaps{};
+    if (g.tma && !tma::encode_f32_planes(&m->h_maps[k].feat, q.feat, q.Wf, q.Hf, q.C, prop::kBW, prop::kRH))
+      return false;
     P.vec = (reinterpret_cast<uintptr_t>(q.ref) % 16 == 0 && reinterpret_cast<uintptr_t>(q.cur) % 16 == 0 &&
              q.pitch % 8 == 0) ? 1 : 0;
+    // a map that cannot be encoded leaves the pair on plain-load staging (same launch shape)
+    P.win_tma = P.vec && (cfg.nw == 4 ? encode_strip_maps_nw<4>(range, &m->h_maps[k], q)
+                                      : encode_strip_maps_nw<8>(range, &m->h_maps[k], q)) ? 1 : 0;
     m->h_prefix[k] = me;
     m->h_prefix[(n + 1) + k] = pr;
     me += P.me_items;
@@ -527,8 +590,9 @@ cudaError_t ensure_stamps(MultiStream* m, long long items) {
 }
 
 cudaError_t search_items(MultiStream* m, int n, int range, const Config& cfg, int i0, int i1, cudaStream_t st) {
-  return cfg.nw == 4 ? ms_me_dispatch<4>(range, m->d_pairs, m->d_prefix, n, i0, i1, m->d_ctr, st)
-                     : ms_me_dispatch<8>(range, m->d_pairs, m->d_prefix, n, i0, i1, m->d_ctr, st);
+  return cfg.nw == 4
+             ? ms_me_dispatch<4>(range, m->d_pairs, m->d_maps, m->d_prefix, n, i0, i1, m->d_ctr, m->status, st)
+             : ms_me_dispatch<8>(range, m->d_pairs, m->d_maps, m->d_prefix, n, i0, i1, m->d_ctr, m->status, st);
 }
 
 // Items [i0, i1) of the table last built: shared memory for TMA tiles only
@@ -589,7 +653,7 @@ std::string signature(const bayer_pair_t* pairs, int n, int range, int interp) {
 cudaError_t upload(MultiStream* m, int n, cudaStream_t st) {
   cudaError_t e = cudaMemcpyAsync(m->d_pairs, m->h_pairs, sizeof(MsPair) * n, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(m->d_maps, m->h_maps, sizeof(CUtensorMap) * n, cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyAsync(m->d_maps, m->h_maps, sizeof(MsMaps) * n, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(m->d_prefix, m->h_prefix, sizeof(int) * 2 * (n + 1), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaEventRecord(m->copied, st);
@@ -617,7 +681,7 @@ cudaError_t ms_run(MultiStream* m, const bayer_pair_t* pairs, int n, int range, 
     MultiStream::Entry entry;
     entry.cfg = cfg;
     if ((e = cudaEventSynchronize(m->copied)) != cudaSuccess) return e;
-    if (!build_table(m, pairs, n, cfg, interp, &me_total, &pr_total, &perm)) return cudaErrorInvalidValue;
+    if (!build_table(m, pairs, n, cfg, interp, range, &me_total, &pr_total, &perm)) return cudaErrorInvalidValue;
     cudaGraph_t g = nullptr;
     if ((e = cudaStreamBeginCapture(m->capture, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
     cudaError_t ec = enqueue(m, n, range, interp, cfg, me_total, pr_total, m->capture);
@@ -641,7 +705,7 @@ cudaError_t ms_run(MultiStream* m, const bayer_pair_t* pairs, int n, int range, 
     for (int ci = 0; ci < NC; ++ci) {
       const Config& c = cands[ci];
       if ((e = cudaEventSynchronize(m->copied)) != cudaSuccess) break;
-      if (!build_table(m, pairs, n, c, interp, &me_total, &pr_total, &perm)) {
+      if (!build_table(m, pairs, n, c, interp, range, &me_total, &pr_total, &perm)) {
         e = cudaErrorInvalidValue;
         break;
       }
@@ -672,7 +736,7 @@ cudaError_t ms_run(MultiStream* m, const bayer_pair_t* pairs, int n, int range, 
     MultiStream::Entry entry;
     entry.cfg = best;
     if ((e = cudaEventSynchronize(m->copied)) != cudaSuccess) return e;
-    if (!build_table(m, pairs, n, best, interp, &me_total, &pr_total, &perm)) return cudaErrorInvalidValue;
+    if (!build_table(m, pairs, n, best, interp, range, &me_total, &pr_total, &perm)) return cudaErrorInvalidValue;
     cudaGraph_t g = nullptr;
     if ((e = cudaStreamBeginCapture(m->capture, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
     cudaError_t ec = enqueue(m, n, range, interp, best, me_total, pr_total, m->capture);
@@ -684,7 +748,8 @@ cudaError_t ms_run(MultiStream* m, const bayer_pair_t* pairs, int n, int range, 
     it = m->cache.emplace(key, entry).first;
   } else {
     if ((e = cudaEventSynchronize(m->copied)) != cudaSuccess) return e;
-    if (!build_table(m, pairs, n, it->second.cfg, interp, &me_total, &pr_total, &perm)) return cudaErrorInvalidValue;
+    if (!build_table(m, pairs, n, it->second.cfg, interp, range, &me_total, &pr_total, &perm))
+      return cudaErrorInvalidValue;
   }
   if ((e = upload(m, n, st)) != cudaSuccess) return e;
   if ((e = cudaGraphLaunch(it->second.exec, st)) != cudaSuccess) return e;

@@ -73,11 +73,6 @@ struct TileJob {
   bool map_in_global;
 };
 
-__device__ __forceinline__ void fence_tensormap_acquire(const CUtensorMap* tm) {
-  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(tm))
-               : "memory");
-}
-
 // Run by all kTileThreads threads of the CTA (it holds a __syncthreads after
 // the barrier set-up); returns in every thread, also after a timeout.
 __device__ __forceinline__ void tma_tile(TileStage& s, const TileJob& j) {
@@ -96,7 +91,7 @@ __device__ __forceinline__ void tma_tile(TileStage& s, const TileJob& j) {
   if (tid >= kTT) {
     // producer warp: one lane refills each buffer once its kTT readers are done
     if (tid == kTT) {
-      if (j.map_in_global) fence_tensormap_acquire(j.tm);
+      if (j.map_in_global) tma::fence_map_acquire(j.tm);
       for (int c = 0; c < j.nc; ++c) {
         const int sl = c % kNS;
         if (c >= kNS && !tc::mbar_wait(&s.empty[sl], (uint32_t)(((c - kNS) / kNS) & 1), kPropWait)) {

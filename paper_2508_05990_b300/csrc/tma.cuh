@@ -113,6 +113,14 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* mbar, uint32_t b
                : "memory");
 }
 
+// Before the first copy through a tensor map that lies in global memory
+// (written before the launch, by a copy or a store), order the tensor-map
+// proxy's reads of its 128 bytes after those writes.
+__device__ __forceinline__ void fence_map_acquire(const CUtensorMap* map) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map))
+               : "memory");
+}
+
 // One box of `map` at (x, y, z) into shared memory at `dst` (128-byte
 // aligned); completes `bytes` of the transaction count of `mbar`.
 __device__ __forceinline__ void load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* mbar) {

@@ -125,11 +125,13 @@ def test_multi_stream_bench_configuration(handle, schedule):
     assert len(checked) == 4
 
 
-def test_multi_stream_feature_alignment(handle):
-    """The same sizes with the feature maps 16-byte aligned (TMA-staged
-    propagation tiles) and one float off (global-memory items): each call
-    keeps a graph of its own, and both are bit-exact with the oracle, in
-    either order and again on a repeated call."""
+@pytest.mark.parametrize("schedule", [0, 80])
+def test_multi_stream_alignment(handle, schedule):
+    """The same sizes with frames and feature maps 16-byte aligned (TMA-staged
+    search windows and propagation tiles) and one element off (plain-load
+    staging and global-memory propagation items): each call keeps a graph of
+    its own, and both are bit-exact with the oracle, in either order and again
+    on a repeated call; autotuned and pinned to 8-block strips."""
     sizes = [(128, 160, 24, 8), (96, 128, 16, 4)]
     frames, feats = [], []
     for i, (H, W, C, s) in enumerate(sizes):
@@ -137,19 +139,26 @@ def test_multi_stream_feature_alignment(handle):
         feats.append(synth.features(750 + i, C, H // s, W // s)[0])
     want = [oracle.me_full(fr[0], fr[1], 16, 32, even=True)[0] for fr in frames]
     prop = [oracle.propagate(f, w, 16, s, interp=oracle.BILINEAR) for f, w, (_, _, _, s) in zip(feats, want, sizes)]
+
+    def placed(a, shift, dtype):
+        flat = torch.zeros(a.size + 8, dtype=dtype, device="cuda")
+        flat[shift:shift + a.size] = torch.from_numpy(a.ravel()).to(dtype).cuda()
+        t = flat[shift:shift + a.size].view(a.shape)
+        assert (t.data_ptr() % 16 == 0) == (shift == 0)
+        return t
+
     for shift in (0, 1, 0, 1):
         streams = []
         for fr, f, (H, W, C, s) in zip(frames, feats, sizes):
-            base = torch.zeros(f.size + 4, device="cuda")
-            base[shift:shift + f.size] = torch.from_numpy(f.ravel()).cuda()
-            fin = base[shift:shift + f.size].view(C, H // s, W // s)
-            assert (fin.data_ptr() % 16 == 0) == (shift == 0)
-            streams.append({"ref": torch.from_numpy(fr[0]).cuda(), "cur": torch.from_numpy(fr[1]).cuda(),
+            streams.append({"ref": placed(fr[0].view(np.int16), shift, torch.int16),
+                            "cur": placed(fr[1].view(np.int16), shift, torch.int16),
                             "mv": torch.empty((H // 16, W // 16, 2), dtype=torch.int32, device="cuda"),
-                            "feat": fin, "feat_out": torch.empty((C, H // s, W // s), device="cuda"), "stride": s})
-        handle.multi_stream(streams, 32)
+                            "feat": placed(f, shift, torch.float32),
+                            "feat_out": torch.empty((C, H // s, W // s), device="cuda"), "stride": s})
+        got_sched = handle.multi_stream(streams, 32, schedule=schedule)
         torch.cuda.synchronize()
         assert handle.sync_status() == bm.OK
+        assert schedule == 0 or got_sched == schedule
         for q, w, pw in zip(streams, want, prop):
             got = bm.records_to_numpy(q["mv"])
             for k in ("dx", "dy", "sad"):
