@@ -68,10 +68,18 @@ def prop_bytes_per_pair() -> int:
     return 2 * C * HF * WF * 4 + (H // BLOCK) * (W // BLOCK) * 8
 
 
+def bench_config(world: int) -> dict:
+    """The workload both arms name (the reference arm times a bounded sample of it)."""
+    return {"workload": WORKLOAD, "pairs_per_step": PAIRS, "search": "plain exhaustive",
+            "l2": "inputs larger than L2 (267 MB read + 234 MB written per step); no flush",
+            "parallelism": f"replicas x{world} (independent clips, no collective)"}
+
+
 ME_SOURCES = ("paper_2508_05990_b300/csrc/me_full16.cu", "paper_2508_05990_b300/csrc/full16.cuh",
               "paper_2508_05990_b300/csrc/common.cuh", "paper_2508_05990_b300/csrc/tma.cuh",
               "paper_2508_05990_b300/csrc/tc_common.cuh")
-PROP_SOURCES = ("paper_2508_05990_b300/csrc/propagate.cu", "paper_2508_05990_b300/csrc/prop_common.cuh",
+PROP_SOURCES = ("paper_2508_05990_b300/csrc/propagate.cu", "paper_2508_05990_b300/csrc/prop_tma.cuh",
+                "paper_2508_05990_b300/csrc/prop_common.cuh",
                 "paper_2508_05990_b300/csrc/common.cuh", "paper_2508_05990_b300/csrc/tma.cuh",
                 "paper_2508_05990_b300/csrc/tc_common.cuh")
 
@@ -869,9 +877,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": round(ms_total / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u16 frames (packed 16x2 min), u32 SAD, f32 features",
             "data": "synthetic (seeded pan+rectangles Bayer clip, N(0,1) features)",
-            "config": {"workload": WORKLOAD, "pairs_per_step": PAIRS, "search": "plain exhaustive",
-                       "l2": "inputs larger than L2 (267 MB read + 234 MB written per step); no flush",
-                       "parallelism": f"replicas x{world} (independent clips, no collective)"},
+            "config": bench_config(world),
             "roofline": {"bound": "alu", "kernel": "me_full16_even_kernel<16>", "achieved": round(achieved, 1),
                          "peak": round(peak, 1), "unit": "G pixel-candidates/s", "frac": round(achieved / peak, 4),
                          "clock_samples": clocks.get("samples"),
@@ -943,8 +949,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 2),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16 frames, u64 SAD, f32 features",
         "data": "synthetic (seeded pan+rectangles Bayer clip, N(0,1) features)",
-        "config": {"workload": WORKLOAD, "pairs_per_step": 1,
-                   "sample": "each step = 1 pair of the 1080p clip (of 7), CPU oracle"},
+        "config": bench_config(world),
+        "sample": "each step = 1 pair of the 1080p clip (of 7), CPU oracle",
         "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": "1 pair per step of the 1080p clip, plain C oracle, all host threads"},
         "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
