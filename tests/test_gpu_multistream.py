@@ -164,3 +164,22 @@ def test_multi_stream_alignment(handle, schedule):
             for k in ("dx", "dy", "sad"):
                 np.testing.assert_array_equal(got[k], w[k])
             np.testing.assert_array_equal(q["feat_out"].cpu().numpy().view(np.uint32), pw.view(np.uint32))
+
+
+def test_multi_stream_nearest(handle):
+    """NEAREST propagation through the multi-stream call (global-memory items
+    on every pair): maps equal the oracle's pure copies bit for bit."""
+    end = torch.zeros(len(SIZES), dtype=torch.int64, device="cuda")
+    streams = make(900)
+    handle.multi_stream(streams, 32, interp=bm.INTERP_NEAREST, end_ns=end)
+    torch.cuda.synchronize()
+    assert handle.sync_status() == bm.OK
+    assert (end.cpu().numpy() > 0).all()
+    for q in streams:
+        want, _ = oracle.me_full(q["np"][0], q["np"][1], 16, 32, even=True)
+        got = bm.records_to_numpy(q["mv"])
+        for k in ("dx", "dy", "sad"):
+            np.testing.assert_array_equal(got[k], want[k])
+        if "feat" in q:
+            pw = oracle.propagate(q["feat_np"], want, 16, q["stride"], interp=oracle.NEAREST)
+            np.testing.assert_array_equal(q["feat_out"].cpu().numpy().view(np.uint32), pw.view(np.uint32))
