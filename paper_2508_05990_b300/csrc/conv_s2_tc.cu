@@ -16,16 +16,17 @@
 // Each output row accumulates in one of four rotating TMEM accumulators, so
 // the epilogue of one row overlaps the MMAs of the next ones.
 //
-// Warp roles (416 threads, 448 for layer 1 with TMA):
+// Warp roles (416 threads; 320 for layer 1 with TMA):
 //   warps 0-3   epilogue: TMEM -> registers -> bias, ReLU -> bf16 NHWC
 //               (warp w reads TMEM lanes 32w..32w+31 = pixels of the segment);
 //   warp 4      one thread issues the MMAs and commits them to mbarriers;
-//   warps 5-12  producers in groups taking input rows round-robin: layer 2
+//   warps 5-12  producers in groups taking input rows round-robin (layer 1
+//               with TMA: warps 5-8, two groups of two warps): layer 2
 //               loads the row's 16-byte NHWC chunks and stores them as K-major
 //               core matrices; layer 1 turns each 12-bit Bayer sample v into
 //               the TF32 operand v/2048 - 1 (exact), its MMAs running in
 //               kind::tf32 on the bf16 weights widened exactly to float32;
-//   warp 13     (layer 1 with 16-byte aligned frame rows) one thread copies
+//   warp 9      (layer 1 with 16-byte aligned frame rows) one thread copies
 //               the two raw rows of each staged half-resolution row of both
 //               frames by TMA (one box per frame) into a ring that the
 //               producers convert from,
@@ -59,7 +60,7 @@ struct Roles {
   static constexpr int EPI = 4;
   static constexpr int MMA = EPI;
   static constexpr int PROD0 = MMA + 1;
-  static constexpr int PROD = 8;
+  static constexpr int PROD = SRC == 2 ? 4 : 8;
   static constexpr int TMA = PROD0 + PROD;  // SRC 2 only
   static constexpr int THREADS = (PROD0 + PROD + (SRC == 2 ? 1 : 0)) * 32;
 };
@@ -88,15 +89,16 @@ constexpr uint32_t kWaitLimit = 1u << 22;
 // Ring: NR slots filled by G producer groups taking rows j % G (slot j % NR
 // always belongs to group j % G).  Layer 1 (Bayer frames) has small rows and
 // little work per loaded byte, so it keeps more rows in flight: 8 slots, 8
-// one-warp groups (4 two-warp groups converting TMA-staged rows); layer 2: 4
+// one-warp groups; converting TMA-staged rows, 4 slots, 2 two-warp groups and
+// 4 raw slots, so that three CTAs fit an SM (60 KB, 320 threads); layer 2: 4
 // slots, 2 groups of 4 warps.
 template <int CIN, int SRC>
 struct S2Layout {
   static constexpr int KC = CIN / 8;
-  static constexpr int NR = SRC != 0 ? 8 : 4;
-  static constexpr int G = SRC == 0 ? 2 : (SRC == 1 ? 8 : 4);
+  static constexpr int NR = SRC == 2 ? 4 : (SRC != 0 ? 8 : 4);
+  static constexpr int G = SRC == 0 ? 2 : (SRC == 1 ? 8 : 2);
   static constexpr int GT = Roles<SRC>::PROD * 32 / G;
-  static constexpr int RR = SRC == 2 ? 8 : 0;  // raw ring slots
+  static constexpr int RR = SRC == 2 ? 4 : 0;  // raw ring slots
   static constexpr int SLOT_BYTES = 2 * KC * kNP * 16;
   static constexpr int B_BYTES = 9 * CIN * kN * 2;
   static constexpr int RAW_OFF = B_BYTES + NR * SLOT_BYTES;
@@ -106,7 +108,7 @@ struct S2Layout {
   static constexpr int SMEM = BIAS_OFF + kN * 4;
   static_assert(CIN % 16 == 0, "shape");
   static_assert(B_BYTES % 16 == 0 && SLOT_BYTES % 16 == 0, "alignment");
-  static_assert(SMEM <= 113 * 1024, "two CTAs per SM");
+  static_assert(SMEM <= 113 * 1024, "two CTAs per SM (three for layer 1 with TMA)");
   static_assert(NR % G == 0, "a slot belongs to one group");
   static_assert(RAW_OFF % 128 == 0, "TMA destinations 128-byte aligned");
 };
@@ -143,7 +145,7 @@ __device__ __forceinline__ void raise_abort(volatile int* abort_flag, int* statu
 // SRC 2: the same, raw rows staged by TMA (tm_ref, tm_cur: boxes of
 // 66 chunks of 8 samples x 2 rows over [batch][H][W/8][8]).
 template <int CIN, int SRC>
-__global__ void __launch_bounds__(threads_of<SRC>(), 2)
+__global__ void __launch_bounds__(threads_of<SRC>(), SRC == 2 ? 3 : 2)
     conv3x3s2_rows_tc_kernel(const ConvTcArgs a, const __grid_constant__ CUtensorMap tm_ref,
                              const __grid_constant__ CUtensorMap tm_cur) {
   using L = S2Layout<CIN, SRC>;
