@@ -452,10 +452,12 @@ def leg_multi_stream(h, clips, steps, warmup, peaks, pc_clk_sm, nsm, sm_mhz):
                        "p99": round(float(np.percentile(lat_ms, 99)), 4),
                        "max": round(float(lat_ms.max()), 4),
                        "definition": "first CTA of the step's search launch -> pair's propagated map written"},
-        "schedule": {"blocks_per_strip": sched % 100 // 10,
+        "schedule": {"code": sched, "blocks_per_strip": sched % 100 // 10,
                      "order": {0: "stream order", 1: "largest first", 2: "smallest first"}[sched % 10],
-                     "launches": "per frame size, smallest first: search then propagation" if sched >= 100
+                     "launches": "per frame size, smallest first: search then propagation" if sched % 1000 >= 100
                      else "one search + one propagation launch",
+                     "search_windows": "plain loads" if (sched // 1000) & 1 else "TMA tiles",
+                     "propagation": "global-memory items" if (sched // 1000) & 2 else "TMA-staged tiles",
                      "picked_by": "autotuner (timed graph replays of each candidate)"},
         "separate_launches": {"ms_per_step": round(ms_sep, 4), "launches_per_step": 2 * n,
                               "speedup_of_batched": round(ms_sep / step_ms, 3)},

@@ -310,26 +310,31 @@ bayer_status_t bayer_refine_conv(bayer_me_t h, const float* feat, int n, int Hf,
  * and the propagations in a second one, or, smallest frames first, per class
  * of frame size a search launch followed by that class's propagation launch;
  * the launches are captured as a CUDA graph and replayed on later calls with
- * the same set of sizes.  The first call for a
- * set of sizes also runs an autotuner: it times each launch schedule (blocks
- * per strip 4 or 8; pairs as given or largest first; the per-size launches
- * smallest first) and keeps, among those within 3 % of the fastest step,
- * the one with the lowest median per-pair completion time (the handle's
- * autotune table).  A bilinear propagation with stride < 16 whose feat is
- * 16-byte aligned and Wf a multiple of 4 is staged through shared memory by
- * TMA tile loads (a tensor map per pair, encoded on every call); other maps
- * are read straight from global memory.  Either way the result is the same
- * bit for bit.  A TMA wait that expires records BAYER_ERR_TIMEOUT in the
- * handle's status word (bayer_me_sync_status).
+ * the same set of sizes.  A pair with 16-byte aligned frame rows can have its
+ * search windows staged by TMA tile loads, and a bilinear propagation with
+ * stride < 16 whose feat is 16-byte aligned and Wf a multiple of 4 can be
+ * staged through shared memory by TMA tile loads (tensor maps per pair,
+ * encoded on every call); the schedule decides; other pairs are read with
+ * plain loads.  Either way the result is the same bit for bit.  The first
+ * call for a set of sizes also runs an autotuner: it times each launch
+ * schedule (blocks per strip 4 or 8; pairs as given or largest first; the
+ * per-size launches smallest first), then, for the best of them, plain-load
+ * search windows and global-memory propagation items in place of TMA tiles,
+ * and keeps, among those within 3 % of the fastest step, the one with the
+ * lowest median per-pair completion time (the handle's autotune table).  A TMA wait that expires
+ * records BAYER_ERR_TIMEOUT in the handle's status word
+ * (bayer_me_sync_status).
  *   pairs: HOST array of n descriptors of device buffers (caller-owned).
  *   end_ns: optional device int64 [n]: per pair, nanoseconds from the start
  *     of the search launch until that pair's output (propagated features, or
  *     the MV field without features) was complete.
  *   schedule: optional host int.  In: 0 to let the autotuner choose, or a
- *     schedule code to run that schedule instead (40, 41, 80, 81, 142, 182;
- *     any other value returns BAYER_ERR_INVALID_ARG).  Out: the schedule
- *     run, 100 * (per-size launches) + 10 * blocks per strip + order (0 as
- *     given, 1 largest first, 2 smallest first).
+ *     schedule code to run that schedule instead (40, 41, 80, 81, 142 or 182,
+ *     plus 1000 for plain-load search windows and/or 2000 for global-memory
+ *     propagation items; any other value returns BAYER_ERR_INVALID_ARG).
+ *     Out: the schedule run, 1000 * (plain windows + 2 * global-memory
+ *     propagation) + 100 * (per-size launches) + 10 * blocks per strip +
+ *     order (0 as given, 1 largest first, 2 smallest first).
  * The first call synchronises the device (autotuning); later calls are
  * asynchronous on `stream`. */
 typedef struct {

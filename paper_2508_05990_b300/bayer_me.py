@@ -365,8 +365,10 @@ class Handle:
     def multi_stream(self, pairs, search_range=32, interp=INTERP_BILINEAR, end_ns=None, stream=None, schedule=0):
         """pairs: list of dicts with ref, cur (uint16/int16 [H, W] tensors), mv (int32 [H/16, W/16, 2]) and
         optionally feat, feat_out (float32 [C, Hf, Wf]) and stride.  Returns the schedule the autotuner chose
-        (100 * per-size launches + 10 * blocks per strip + order; order 0 as given, 1 largest first,
-        2 smallest first).  ``schedule``: 0 lets the autotuner choose; a code runs that schedule."""
+        (1000 * (plain-load search windows + 2 * global-memory propagation items) + 100 * per-size launches
+        + 10 * blocks per strip + order; order 0 as given, 1 largest first, 2 smallest first; staging by
+        TMA tiles where a pair allows it unless the thousands say otherwise).  ``schedule``: 0 lets the
+        autotuner choose; a code runs that schedule."""
         arr = (PairDesc * len(pairs))()
         for i, q in enumerate(pairs):
             H, W = q["ref"].shape[-2:]

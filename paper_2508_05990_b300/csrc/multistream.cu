@@ -38,11 +38,15 @@
 // propagation launch, so the small frames' pairs complete early in the step
 // instead of all at its end (a launch boundary per class costs about 1-2 %
 // of the step).
-// Autotuner: on the first call for a set of sizes it times each schedule
-// (NW in {4, 8} x pair order {as given, largest first}, and the classes mode
-// with NW in {4, 8}) with CUDA events and reads each one's per-pair
-// completion times; it keeps the schedule with the lowest median completion
-// time among those whose step takes at most 3 % longer than the fastest.  The
+// Autotuner: on the first call for a set of sizes it times each launch
+// schedule (NW in {4, 8} x pair order {as given, largest first}, and the
+// classes mode with NW in {4, 8}) with CUDA events and reads each one's
+// per-pair completion times; then, for the best of those, the staging
+// choices: search windows by plain loads instead of TMA tiles, and the
+// propagation as global-memory items instead of TMA-staged tiles (each where
+// a pair could take the TMA form).  It keeps the candidate with the lowest
+// median completion time among those whose step takes at most 3 % longer
+// than the fastest.  The
 // graph (counter reset, launches, end times) is then captured once and
 // relaunched with only the descriptor table refreshed.
 #include <algorithm>
@@ -280,10 +284,21 @@ __global__ void __launch_bounds__(256) ms_end_kernel(const unsigned long long* _
 }
 
 struct Config {
-  int nw;       // warps (blocks) per search strip: 4 or 8
-  int order;    // 0: pairs as given, 1: largest first, 2: smallest first
-  int classes;  // 1: a search and a propagation launch per class of frame size, smallest first
+  int nw;          // warps (blocks) per search strip: 4 or 8
+  int order;       // 0: pairs as given, 1: largest first, 2: smallest first
+  int classes;     // 1: a search and a propagation launch per class of frame size, smallest first
+  int win_plain;   // 1: search windows staged by plain loads even where TMA tiles could be used
+  int prop_plain;  // 1: propagation as global-memory items even where TMA tiles could be used
 };
+
+// Schedule code: 1000 * (win_plain + 2 * prop_plain) + 100 * classes + 10 * nw + order.
+int config_code(const Config& c) {
+  return 1000 * (c.win_plain + 2 * c.prop_plain) + 100 * c.classes + 10 * c.nw + c.order;
+}
+Config config_of(int code) {
+  const int base = code % 1000, st = code / 1000;
+  return Config{base % 100 / 10, base % 10, base / 100, st & 1, (st >> 1) & 1};
+}
 
 constexpr int kMaxClasses = 8;
 
@@ -465,11 +480,11 @@ struct PropGeom {
   int quads, tma, tiles_x, tiles, items;
 };
 
-PropGeom prop_geom(const bayer_pair_t& q, int interp) {
+PropGeom prop_geom(const bayer_pair_t& q, int interp, bool allow_tma = true) {
   PropGeom g{};
   if (!q.feat) return g;
   g.quads = (interp == BAYER_INTERP_BILINEAR && q.stride < 16) ? 1 : 0;
-  g.tma = g.quads && (q.Wf % 4) == 0 && (reinterpret_cast<uintptr_t>(q.feat) % 16) == 0 &&
+  g.tma = allow_tma && g.quads && (q.Wf % 4) == 0 && (reinterpret_cast<uintptr_t>(q.feat) % 16) == 0 &&
           (long long)q.Hf * q.Wf <= (1ll << 31) - 256 && tma::encode_fn() != nullptr;
   if (g.tma) {
     g.tiles_x = (q.Wf + prop::kTileW - 1) / prop::kTileW;
@@ -518,7 +533,7 @@ bool build_table(MultiStream* m, const bayer_pair_t* pairs, int n, const Config&
     P.w = q.W / 16;
     P.strips_x = (P.w + cfg.nw - 1) / cfg.nw;
     P.me_items = P.h * P.strips_x;
-    const PropGeom g = prop_geom(q, interp);
+    const PropGeom g = prop_geom(q, interp, !cfg.prop_plain);
     P.quads = g.quads;
     P.tma = g.tma;
     P.tiles_x = g.tiles_x;
@@ -530,8 +545,11 @@ bool build_table(MultiStream* m, const bayer_pair_t* pairs, int n, const Config&
     P.vec = (reinterpret_cast<uintptr_t>(q.ref) % 16 == 0 && reinterpret_cast<uintptr_t>(q.cur) % 16 == 0 &&
              q.pitch % 8 == 0) ? 1 : 0;
     // a map that cannot be encoded leaves the pair on plain-load staging (same launch shape)
-    P.win_tma = P.vec && (cfg.nw == 4 ? encode_strip_maps_nw<4>(range, &m->h_maps[k], q)
-                                      : encode_strip_maps_nw<8>(range, &m->h_maps[k], q)) ? 1 : 0;
+    P.win_tma = !cfg.win_plain && P.vec &&
+                        (cfg.nw == 4 ? encode_strip_maps_nw<4>(range, &m->h_maps[k], q)
+                                     : encode_strip_maps_nw<8>(range, &m->h_maps[k], q))
+                    ? 1
+                    : 0;
     m->h_prefix[k] = me;
     m->h_prefix[(n + 1) + k] = pr;
     me += P.me_items;
@@ -568,10 +586,12 @@ bool build_table(MultiStream* m, const bayer_pair_t* pairs, int n, const Config&
   return true;
 }
 
-// Propagation items of all pairs: the size of the stamp array.
+// Propagation items of all pairs under either propagation staging: the size
+// of the stamp array.
 long long max_items(const bayer_pair_t* pairs, int n, int interp) {
   long long items = 0;
-  for (int i = 0; i < n; ++i) items += prop_geom(pairs[i], interp).items;
+  for (int i = 0; i < n; ++i)
+    items += std::max(prop_geom(pairs[i], interp, true).items, prop_geom(pairs[i], interp, false).items);
   return items;
 }
 
@@ -663,7 +683,9 @@ cudaError_t upload(MultiStream* m, int n, cudaStream_t st) {
 }  // namespace
 
 bool ms_schedule_valid(int code) {
-  return code == 40 || code == 41 || code == 80 || code == 81 || code == 142 || code == 182;
+  if (code < 0 || code >= 4000) return false;
+  const int base = code % 1000;
+  return base == 40 || base == 41 || base == 80 || base == 81 || base == 142 || base == 182;
 }
 
 cudaError_t ms_run(MultiStream* m, const bayer_pair_t* pairs, int n, int range, int interp, long long* end_ns,
@@ -677,7 +699,7 @@ cudaError_t ms_run(MultiStream* m, const bayer_pair_t* pairs, int n, int range, 
   int me_total = 0, pr_total = 0;
   auto it = m->cache.find(key);
   if (it == m->cache.end() && force) {
-    const Config cfg = {force % 100 / 10, force % 10, force / 100};
+    const Config cfg = config_of(force);
     MultiStream::Entry entry;
     entry.cfg = cfg;
     if ((e = cudaEventSynchronize(m->copied)) != cudaSuccess) return e;
@@ -692,45 +714,60 @@ cudaError_t ms_run(MultiStream* m, const bayer_pair_t* pairs, int n, int range, 
     if (e != cudaSuccess) return e;
     it = m->cache.emplace(key, entry).first;
   } else if (it == m->cache.end()) {
-    // autotune: time every schedule on this set of pairs; keep the one with the
-    // lowest median per-pair completion time among those whose step time is
-    // within 3 % of the fastest
-    constexpr int NC = 6;
-    const Config cands[NC] = {{8, 0, 0}, {8, 1, 0}, {4, 0, 0}, {4, 1, 0}, {8, 2, 1}, {4, 2, 1}};
+    // autotune: time every launch schedule on this set of pairs (search and
+    // propagation staged by TMA where the pair allows it), then the plain-load
+    // search windows and the global-memory propagation items for the winner;
+    // keep the candidate with the lowest median per-pair completion time among
+    // those whose step time is within 3 % of the fastest
+    constexpr int NB = 6, NC = NB + 3;
+    Config cands[NC] = {{8, 0, 0}, {8, 1, 0}, {4, 0, 0}, {4, 1, 0}, {8, 2, 1}, {4, 2, 1}};
     float ms_of[NC], p50_of[NC];
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     std::vector<long long> ends(n);
-    for (int ci = 0; ci < NC; ++ci) {
-      const Config& c = cands[ci];
-      if ((e = cudaEventSynchronize(m->copied)) != cudaSuccess) break;
-      if (!build_table(m, pairs, n, c, interp, range, &me_total, &pr_total, &perm)) {
-        e = cudaErrorInvalidValue;
-        break;
-      }
-      if ((e = upload(m, n, st)) != cudaSuccess) break;
-      if ((e = enqueue(m, n, range, interp, c, me_total, pr_total, st)) != cudaSuccess) break;  // warm
+    auto time_cfg = [&](const Config& c, float* ms, float* p50) -> cudaError_t {
+      cudaError_t r = cudaEventSynchronize(m->copied);
+      if (r != cudaSuccess) return r;
+      if (!build_table(m, pairs, n, c, interp, range, &me_total, &pr_total, &perm)) return cudaErrorInvalidValue;
+      if ((r = upload(m, n, st)) != cudaSuccess) return r;
+      if ((r = enqueue(m, n, range, interp, c, me_total, pr_total, st)) != cudaSuccess) return r;  // warm
       cudaEventRecord(e0, st);
-      if ((e = enqueue(m, n, range, interp, c, me_total, pr_total, st)) != cudaSuccess) break;
+      if ((r = enqueue(m, n, range, interp, c, me_total, pr_total, st)) != cudaSuccess) return r;
       cudaEventRecord(e1, st);
-      if ((e = cudaMemcpyAsync(ends.data(), m->d_end, sizeof(long long) * n, cudaMemcpyDeviceToHost, st)) !=
+      if ((r = cudaMemcpyAsync(ends.data(), m->d_end, sizeof(long long) * n, cudaMemcpyDeviceToHost, st)) !=
           cudaSuccess)
-        break;
-      if ((e = cudaStreamSynchronize(st)) != cudaSuccess) break;
-      cudaEventElapsedTime(&ms_of[ci], e0, e1);
+        return r;
+      if ((r = cudaStreamSynchronize(st)) != cudaSuccess) return r;
+      cudaEventElapsedTime(ms, e0, e1);
       std::vector<long long> sorted = ends;
       std::nth_element(sorted.begin(), sorted.begin() + n / 2, sorted.end());
-      p50_of[ci] = (float)sorted[n / 2];
+      *p50 = (float)sorted[n / 2];
+      return cudaSuccess;
+    };
+    auto choose = [&](int count) {
+      float fastest = 1e30f;
+      for (int ci = 0; ci < count; ++ci) fastest = ms_of[ci] < fastest ? ms_of[ci] : fastest;
+      int pick = -1;
+      for (int ci = 0; ci < count; ++ci)
+        if (ms_of[ci] <= 1.03f * fastest && (pick < 0 || p50_of[ci] < p50_of[pick])) pick = ci;
+      return pick;
+    };
+    for (int ci = 0; ci < NB && e == cudaSuccess; ++ci) e = time_cfg(cands[ci], &ms_of[ci], &p50_of[ci]);
+    if (e == cudaSuccess) {
+      const Config w = cands[choose(NB)];
+      for (int v = 1; v <= 3 && e == cudaSuccess; ++v) {
+        Config c = w;
+        c.win_plain = v & 1;
+        c.prop_plain = v >> 1;
+        cands[NB + v - 1] = c;
+        e = time_cfg(c, &ms_of[NB + v - 1], &p50_of[NB + v - 1]);
+      }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (e != cudaSuccess) return e;
-    float fastest = 1e30f;
-    for (int ci = 0; ci < NC; ++ci) fastest = ms_of[ci] < fastest ? ms_of[ci] : fastest;
-    int pick = -1;
-    for (int ci = 0; ci < NC; ++ci)
-      if (ms_of[ci] <= 1.03f * fastest && (pick < 0 || p50_of[ci] < p50_of[pick])) pick = ci;
+    const int pick = choose(NC);
     const Config best = cands[pick];
     // capture the graph of the chosen schedule on the private stream
     MultiStream::Entry entry;
@@ -763,7 +800,7 @@ cudaError_t ms_run(MultiStream* m, const bayer_pair_t* pairs, int n, int range, 
 
 int ms_config_nw(MultiStream* m, const bayer_pair_t* pairs, int n, int range, int interp, int force) {
   auto it = m->cache.find(signature(pairs, n, range, interp) + (force ? ":" + std::to_string(force) : ""));
-  return it == m->cache.end() ? 0 : it->second.cfg.classes * 100 + it->second.cfg.nw * 10 + it->second.cfg.order;
+  return it == m->cache.end() ? 0 : config_code(it->second.cfg);
 }
 
 }  // namespace bme
