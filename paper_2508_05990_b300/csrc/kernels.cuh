@@ -191,6 +191,7 @@ struct Seeded16Args {
   int* list;          // [batch*h*w] global block indices needing the full search
   int* count;         // number of entries in list (zeroed by the caller)
   bool vec2;          // set by launch_seeded16: 32-bit sample-pair loads allowed
+  bool vec16;         // set by launch_seeded16: 16-byte loads of frame rows allowed
 };
 cudaError_t configure_seeded16();  // once per device: shared-memory opt-in
 cudaError_t launch_seeded16(const Seeded16Args& a, cudaStream_t st);

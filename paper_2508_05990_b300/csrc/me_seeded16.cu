@@ -12,8 +12,9 @@
 // blocks are appended to the fallback list (one atomic per warp).  For the
 // confident blocks the warp stages the 24 x 24 windows and the current
 // blocks in its shared memory as packed pixel pairs (the centre is even, so
-// the window starts on a pair; every pair load of the three blocks in flight
-// at once), then lane 10 j + 5 half + v owns candidate row v (5 candidates)
+// the window starts on a pair; with 16-byte aligned frame rows by 16-byte
+// chunks realigned across lanes, else every pair load of the three blocks in
+// flight at once), then lane 10 j + 5 half + v owns candidate row v (5 candidates)
 // of block j over one half of its columns: 30 of 32 lanes carry SADs.  As in
 // the exhaustive search (full16.cuh), SAD = sum(cur) + sum(win) -
 // 2 sum min(cur, win) with min.u16x2 + dp2a per pixel pair; each lane keeps
@@ -70,6 +71,7 @@ __global__ void __launch_bounds__(kSW * 32) seeded16_kernel(const Seeded16Args a
     }
   }
   const bool vec = a.vec2;
+  const bool vec16 = a.vec16;
   // launched as a dependent of the network's last layer: its proposals are
   // read only after this wait (the fallback list's counter was zeroed before
   // the network ran)
@@ -87,7 +89,16 @@ __global__ void __launch_bounds__(kSW * 32) seeded16_kernel(const Seeded16Args a
     py = a.prop[2 * gb + 1];
   }
   uint32_t rc[kPer][kPairsCur / 32];
-  if (vec) {
+  uint4 rc16[kPer];
+  if (vec16) {
+    // 16-byte loads: lane = (row lane / 2, half lane % 2) of each current block
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int x0 = bxy[k] & 0xFFFF, y0 = bxy[k] >> 16;
+      const uint16_t* cur = a.cur + (long long)bp[k] * a.cur_bs + (long long)(y0 + (lane >> 1)) * a.pitch + x0;
+      rc16[k] = gb0 + k < nblk ? __ldg(reinterpret_cast<const uint4*>(cur) + (lane & 1)) : make_uint4(0, 0, 0, 0);
+    }
+  } else if (vec) {
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
       const int x0 = bxy[k] & 0xFFFF, y0 = bxy[k] >> 16;
@@ -136,7 +147,45 @@ __global__ void __launch_bounds__(kSW * 32) seeded16_kernel(const Seeded16Args a
 
   // ---- stage the confident blocks' windows and current blocks
   uint32_t* slots = smem + warp * kPer * kSlot;
-  if (vec) {
+  if (vec16) {
+    // each window row as four 16-byte chunks from the 16-byte aligned column
+    // at or left of its origin (lane = (row, chunk), three rounds of 8 rows);
+    // the origin lies o = 0..3 words into chunk 0, so output chunk c takes
+    // words o..3 of loaded chunk c and 0..o-1 of chunk c + 1 (the next lane)
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int bc = __shfl_sync(0xffffffffu, cpk, k);
+      if (!(conf_mask & (1u << k))) continue;
+      const int x0 = bxy[k] & 0xFFFF, y0 = bxy[k] >> 16;
+      const int cx = (int)(int16_t)(bc & 0xFFFF), cy = bc >> 16;
+      const uint16_t* ref = a.ref + (long long)bp[k] * a.ref_bs;
+      const int wx0 = x0 + cx - 4, wy0 = y0 + cy - 4;  // even; at least -4
+      const int xa = (wx0 >> 3) << 3, o = (wx0 - xa) >> 1;
+      const int ch = lane & 3;
+      uint4 v[kWin / 8];
+#pragma unroll
+      for (int i = 0; i < kWin / 8; ++i) {
+        // a chunk lies wholly inside or outside the frame (W a multiple of 16)
+        const int gy = wy0 + (lane >> 2) + 8 * i, gx = xa + 8 * ch;
+        v[i] = make_uint4(0, 0, 0, 0);
+        if (gy >= 0 && gy < a.H && gx >= 0 && gx < a.W)
+          v[i] = __ldg(reinterpret_cast<const uint4*>(ref + (long long)gy * a.pitch + gx));
+      }
+      uint32_t* wdst = slots + k * kSlot;
+#pragma unroll
+      for (int i = 0; i < kWin / 8; ++i) {
+        const uint32_t n0 = __shfl_down_sync(0xffffffffu, v[i].x, 1), n1 = __shfl_down_sync(0xffffffffu, v[i].y, 1);
+        const uint32_t n2 = __shfl_down_sync(0xffffffffu, v[i].z, 1);
+        uint4 w;
+        w.x = o == 0 ? v[i].x : (o == 1 ? v[i].y : (o == 2 ? v[i].z : v[i].w));
+        w.y = o == 0 ? v[i].y : (o == 1 ? v[i].z : (o == 2 ? v[i].w : n0));
+        w.z = o == 0 ? v[i].z : (o == 1 ? v[i].w : (o == 2 ? n0 : n1));
+        w.w = o == 0 ? v[i].w : (o == 1 ? n0 : (o == 2 ? n1 : n2));
+        if (ch < 3) *reinterpret_cast<uint4*>(wdst + ((lane >> 2) + 8 * i) * kWP + 4 * ch) = w;
+      }
+      reinterpret_cast<uint4*>(wdst + kCurOff)[lane] = rc16[k];  // row lane / 2, words 4 (lane % 2) ..
+    }
+  } else if (vec) {
     uint32_t raw[kPer][kPairsWin / 32];
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
@@ -284,6 +333,8 @@ cudaError_t launch_seeded16(const Seeded16Args& in, cudaStream_t st) {
   Seeded16Args a = in;
   a.vec2 = (reinterpret_cast<uintptr_t>(a.ref) % 4) == 0 && (reinterpret_cast<uintptr_t>(a.cur) % 4) == 0 &&
            a.pitch % 2 == 0 && a.ref_bs % 2 == 0 && a.cur_bs % 2 == 0;
+  a.vec16 = (reinterpret_cast<uintptr_t>(a.ref) % 16) == 0 && (reinterpret_cast<uintptr_t>(a.cur) % 16) == 0 &&
+            a.pitch % 8 == 0 && a.ref_bs % 8 == 0 && a.cur_bs % 8 == 0 && a.W % 16 == 0;
   const long long nblk = (long long)a.batch * a.h * a.w;
   const long long per_cta = (long long)kSW * kPer;
   return tc::launch_dependent(seeded16_kernel, dim3((unsigned)((nblk + per_cta - 1) / per_cta)), dim3(kSW * 32),
