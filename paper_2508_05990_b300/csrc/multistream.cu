@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 4 : 6) ms_me_kernel(const M
                                                                           const int* __restrict__ prefix, int n,
                                                                           MsCounters* ctr, int item0, int* status) {
   using C = Full16Strip<R, NW>;
-  extern __shared__ __align__(16) uint32_t smem[];
+  extern __shared__ __align__(128) uint32_t smem[];  // window and current tile: TMA destinations
   uint32_t* win = smem;
   uint32_t* curt = smem + C::CUR_OFF;
   uint32_t* cs = smem + C::CS_OFF;
