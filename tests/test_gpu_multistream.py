@@ -44,7 +44,7 @@ def make(seed):
     return streams
 
 
-@pytest.mark.parametrize("search_range", [32, 16])
+@pytest.mark.parametrize("search_range", [32, 24, 16, 8])
 def test_multi_stream_exact(handle, search_range):
     end = torch.zeros(len(SIZES), dtype=torch.int64, device="cuda")
     for call, seed in enumerate((300, 400)):
