@@ -53,6 +53,10 @@ constexpr int kN = 32;      // output channels (MMA N)
 constexpr int kNJ = 2 * kM + 1;  // staged input columns per row segment (257)
 constexpr int kNP = 129;    // pixels per parity plane; 129 * 16 B = 16 mod 128 (conflict-free stores)
 constexpr int kAcc = 4;     // TMEM accumulators (output rows in flight)
+// Epilogue transpose buffer: one row of 16 bf16x2 words per pixel, pitch 20
+// words (16-byte stores of a pixel row and 16-byte loads across pixels both
+// take few wavefronts).
+constexpr int kTP = 20;
 // Warp roles: 4 epilogue warps, the MMA warp, 8 producer warps and, for SRC
 // 2, one TMA warp.
 template <int SRC>
@@ -105,7 +109,8 @@ struct S2Layout {
   static constexpr int BAR_OFF = RAW_OFF + RR * kRawSlot;
   static constexpr int NBAR = 2 * NR + 2 * kAcc + 1 + 2 * RR;
   static constexpr int BIAS_OFF = (BAR_OFF + NBAR * 8 + 16 + 15) / 16 * 16;
-  static constexpr int SMEM = BIAS_OFF + kN * 4;
+  static constexpr int TR_OFF = BIAS_OFF + kN * 4;  // epilogue transpose buffers (16-byte aligned)
+  static constexpr int SMEM = TR_OFF + Roles<SRC>::EPI * 32 * kTP * 4;
   static_assert(CIN % 16 == 0, "shape");
   static_assert(B_BYTES % 16 == 0 && SLOT_BYTES % 16 == 0, "alignment");
   static_assert(SMEM <= 113 * 1024, "two CTAs per SM (three for layer 1 with TMA)");
@@ -166,6 +171,7 @@ __global__ void __launch_bounds__(threads_of<SRC>(), SRC == 2 ? 3 : 2)
   uint8_t* sRaw = smem + L::RAW_OFF;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float* sBias = reinterpret_cast<float*>(smem + L::BIAS_OFF);
+  uint32_t* sTr = reinterpret_cast<uint32_t*>(smem + L::TR_OFF);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (tid == 0) {
@@ -526,24 +532,33 @@ __global__ void __launch_bounds__(threads_of<SRC>(), SRC == 2 ? 3 : 2)
         tc::fence_before_sync();
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(&acc_empty[acc]);  // accumulator drained
-        const int ox = runs.seg * kM + quarter * 32 + lane;
-        if (ox < a.Wo) {
 #pragma unroll
-          for (int q4 = 0; q4 < 8; ++q4) {
-            const float4 b4 = *reinterpret_cast<const float4*>(sBias + 4 * q4);
-            v[4 * q4] += b4.x;
-            v[4 * q4 + 1] += b4.y;
-            v[4 * q4 + 2] += b4.z;
-            v[4 * q4 + 3] += b4.w;
-          }
-          const long long opix = ((long long)runs.b * a.Ho + y) * a.Wo + ox;
-          uint4* o4 = reinterpret_cast<uint4*>(a.out + opix * kN);
-#pragma unroll
-          for (int q4 = 0; q4 < 4; ++q4)
-            o4[q4] = make_uint4(tc::bf2_relu(v[8 * q4], v[8 * q4 + 1]), tc::bf2_relu(v[8 * q4 + 2], v[8 * q4 + 3]),
-                                tc::bf2_relu(v[8 * q4 + 4], v[8 * q4 + 5]),
-                                tc::bf2_relu(v[8 * q4 + 6], v[8 * q4 + 7]));
+        for (int q4 = 0; q4 < 8; ++q4) {
+          const float4 b4 = *reinterpret_cast<const float4*>(sBias + 4 * q4);
+          v[4 * q4] += b4.x;
+          v[4 * q4 + 1] += b4.y;
+          v[4 * q4 + 2] += b4.z;
+          v[4 * q4 + 3] += b4.w;
         }
+        // the warp's 32 pixels x 64 bytes are one contiguous NHWC run: each
+        // lane puts its pixel's 64 bytes into the transpose buffer, then the
+        // warp stores the run as four 512-byte rows of 16 bytes per lane
+        uint32_t* tb = sTr + quarter * (32 * kTP);
+#pragma unroll
+        for (int q4 = 0; q4 < 4; ++q4)
+          *reinterpret_cast<uint4*>(tb + lane * kTP + 4 * q4) =
+              make_uint4(tc::bf2_relu(v[8 * q4], v[8 * q4 + 1]), tc::bf2_relu(v[8 * q4 + 2], v[8 * q4 + 3]),
+                         tc::bf2_relu(v[8 * q4 + 4], v[8 * q4 + 5]), tc::bf2_relu(v[8 * q4 + 6], v[8 * q4 + 7]));
+        __syncwarp();
+        const int px0 = runs.seg * kM + quarter * 32;  // the warp's first pixel
+        const long long obase = ((long long)runs.b * a.Ho + y) * a.Wo + px0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int p = 8 * q + (lane >> 2), piece = lane & 3;
+          const uint4 val = *reinterpret_cast<const uint4*>(tb + p * kTP + 4 * piece);
+          if (px0 + p < a.Wo) reinterpret_cast<uint4*>(a.out + (obase + p) * kN)[piece] = val;
+        }
+        __syncwarp();  // the buffer is rewritten by the next row
       }
     }
   }
