@@ -250,12 +250,23 @@ __global__ void __launch_bounds__(threads_of<SRC>(), SRC == 2 ? 3 : 2)
     const int ptid = tid - R::PROD0 * 32;
     const int group = ptid / kGT, gtid = ptid - group * kGT;
     // SRC 2: byte offset in a raw row of the sample pair 2jj + 6 of column
-    // jj = gtid + kGT * i
+    // jj = cl + kGT * i
     constexpr int kConvPer = (kNJ + kGT - 1) / kGT;
+    static_assert(SRC != 2 || kGT == 64, "the column map below covers two warps");
+    // SRC 2: the thread's staged column within each kGT-column stripe.  In
+    // every 8-lane phase of a warp four lanes take even columns (parity
+    // plane 0, chunks h .. h + 3) and four odd ones whose chunks lie two
+    // further on (plane 1 starts 2 mod 8 chunks after plane 0), so the
+    // phase's 16-byte stores hit eight distinct bank groups
+    const int cl = [&] {
+      const int l = gtid & 31, k = l >> 3, r = l & 7;
+      const int half = r < 4 ? 4 * k + r : (4 * k + r - 2) & 15;
+      return 32 * (gtid >> 5) + 2 * half + (r < 4 ? 0 : 1);
+    }();
     int raw_off[SRC == 2 ? kConvPer : 1];
     if (SRC == 2) {
 #pragma unroll
-      for (int i = 0; i < kConvPer; ++i) raw_off[i] = (2 * (gtid + kGT * i) + 6) * 2;
+      for (int i = 0; i < kConvPer; ++i) raw_off[i] = (2 * (cl + kGT * i) + 6) * 2;
     }
     // A staged row is released by the commit of output row o_base + max(0,
     // (t - 1) / 2) (t: its index in the run; the MMA issues an odd row's ky = 0
@@ -329,14 +340,14 @@ __global__ void __launch_bounds__(threads_of<SRC>(), SRC == 2 ? 3 : 2)
             stop = true;
             break;
           }
-          // thread gtid converts columns jj = gtid + kGT * i of both frames;
-          // its raw offsets (kRawOff) are row-independent
+          // thread gtid converts columns jj = cl + kGT * i of both frames;
+          // its raw offsets (raw_off) are row-independent
           const uint8_t* raw = sRaw + s * kRawSlot;
           const int jlo = -c0, jhi = a.Wi - c0;  // staged columns inside the map: [jlo, jhi)
-          uint8_t* dcol = dst + ((gtid & 1) * KC * kNP + (gtid >> 1)) * 16;
+          uint8_t* dcol = dst + ((cl & 1) * KC * kNP + (cl >> 1)) * 16;
 #pragma unroll
           for (int i = 0; i < kConvPer; ++i) {
-            const int jj = gtid + kGT * i;
+            const int jj = cl + kGT * i;
             if (jj < kNJ) {
               const bool in = row_ok && jj >= jlo && jj < jhi;
 #pragma unroll
