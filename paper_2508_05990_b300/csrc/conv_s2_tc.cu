@@ -29,8 +29,9 @@
 //   warp 9      (layer 1 with 16-byte aligned frame rows) one thread copies
 //               the two raw rows of each staged half-resolution row of both
 //               frames by TMA (one box per frame) into a ring that the
-//               producers convert from,
-//               so that they do no global address arithmetic or loads.
+//               producers convert from, four columns per 16-byte word of
+//               each raw row, so that they do no global address arithmetic
+//               or loads.
 //               Otherwise the producers load the frames themselves.
 // Ring of staged rows: full mbarriers, and a slot is free again once the
 // commit that completes an output row covers its last MMA; weights (packed once per
@@ -249,24 +250,20 @@ __global__ void __launch_bounds__(threads_of<SRC>(), SRC == 2 ? 3 : 2)
     // ---- producers: input rows 2ya-1 .. 2yb-1 of each run; group g takes rows j % G == g
     const int ptid = tid - R::PROD0 * 32;
     const int group = ptid / kGT, gtid = ptid - group * kGT;
-    // SRC 2: byte offset in a raw row of the sample pair 2jj + 6 of column
-    // jj = cl + kGT * i
-    constexpr int kConvPer = (kNJ + kGT - 1) / kGT;
-    static_assert(SRC != 2 || kGT == 64, "the column map below covers two warps");
-    // SRC 2: the thread's staged column within each kGT-column stripe.  In
-    // every 8-lane phase of a warp four lanes take even columns (parity
-    // plane 0, chunks h .. h + 3) and four odd ones whose chunks lie two
-    // further on (plane 1 starts 2 mod 8 chunks after plane 0), so the
-    // phase's 16-byte stores hit eight distinct bank groups
-    const int cl = [&] {
-      const int l = gtid & 31, k = l >> 3, r = l & 7;
-      const int half = r < 4 ? 4 * k + r : (4 * k + r - 2) & 15;
-      return 32 * (gtid >> 5) + 2 * half + (r < 4 ? 0 : 1);
-    }();
-    int raw_off[SRC == 2 ? kConvPer : 1];
-    if (SRC == 2) {
+    // SRC 2: staged columns 1 .. 256 form 64 groups of four, jj = 4g + 1 ..
+    // 4g + 4, whose raw samples 8g + 8 .. 8g + 15 are one 16-byte word per
+    // raw row; column 0 (samples 6, 7) is converted on its own.  Task tau =
+    // gtid + kGT k (k = 0, 1) is (frame fr, group g): per 8-lane phase the
+    // eight raw loads read eight consecutive 16-byte words (distinct bank
+    // groups) and the 16-byte stores of one column of the four land on
+    // plane chunks 2g + c + fr * kNP (kNP = 1 mod 8), eight distinct groups
+    static_assert(SRC != 2 || (kGT == 64 && kNJ == 257), "two tasks per thread cover the 128 (frame, group) tasks");
+    int cv_fr[2], cv_g[2];
 #pragma unroll
-      for (int i = 0; i < kConvPer; ++i) raw_off[i] = (2 * (cl + kGT * i) + 6) * 2;
+    for (int k = 0; k < 2; ++k) {
+      const int tau = gtid + kGT * k, l = tau & 31, k8 = l >> 3, r = l & 7;
+      cv_g[k] = 16 * (tau >> 5) + 8 * (k8 >> 1) + r;
+      cv_fr[k] = (r >> 2) ^ (k8 & 1);
     }
     // A staged row is released by the commit of output row o_base + max(0,
     // (t - 1) / 2) (t: its index in the run; the MMA issues an odd row's ky = 0
@@ -340,29 +337,39 @@ __global__ void __launch_bounds__(threads_of<SRC>(), SRC == 2 ? 3 : 2)
             stop = true;
             break;
           }
-          // thread gtid converts columns jj = cl + kGT * i of both frames;
-          // its raw offsets (raw_off) are row-independent
           const uint8_t* raw = sRaw + s * kRawSlot;
           const int jlo = -c0, jhi = a.Wi - c0;  // staged columns inside the map: [jlo, jhi)
-          uint8_t* dcol = dst + ((cl & 1) * KC * kNP + (cl >> 1)) * 16;
 #pragma unroll
-          for (int i = 0; i < kConvPer; ++i) {
-            const int jj = cl + kGT * i;
-            if (jj < kNJ) {
-              const bool in = row_ok && jj >= jlo && jj < jhi;
-#pragma unroll
-              for (int fr = 0; fr < 2; ++fr) {
-                uint4 val = make_uint4(0, 0, 0, 0);
-                if (in) {
-                  const uint8_t* p0 = raw + raw_off[i] + fr * kRawBoxStep;
-                  const uint32_t w0 = *reinterpret_cast<const uint32_t*>(p0);
-                  const uint32_t w1 = *reinterpret_cast<const uint32_t*>(p0 + kRawRowBytes);
-                  val = make_uint4(tf32_sample12(w0 & 0xFFFFu), tf32_sample12(w0 >> 16),
-                                   tf32_sample12(w1 & 0xFFFFu), tf32_sample12(w1 >> 16));
-                }
-                *reinterpret_cast<uint4*>(dcol + (fr * kNP + (kGT / 2) * i) * 16) = val;
-              }
+          for (int k = 0; k < 2; ++k) {
+            const int fr = cv_fr[k], g = cv_g[k];
+            const uint8_t* p0 = raw + fr * kRawBoxStep + 16 * g + 16;
+            uint4 ra = make_uint4(0, 0, 0, 0), rb = make_uint4(0, 0, 0, 0);
+            if (row_ok) {
+              ra = *reinterpret_cast<const uint4*>(p0);
+              rb = *reinterpret_cast<const uint4*>(p0 + kRawRowBytes);
             }
+            const uint32_t wa[4] = {ra.x, ra.y, ra.z, ra.w}, wb[4] = {rb.x, rb.y, rb.z, rb.w};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+              const int jj = 4 * g + 1 + t;
+              uint4 val = make_uint4(0, 0, 0, 0);
+              if (row_ok && jj >= jlo && jj < jhi)  // outside the map: zero operands (not v = 0)
+                val = make_uint4(tf32_sample12(wa[t] & 0xFFFFu), tf32_sample12(wa[t] >> 16),
+                                 tf32_sample12(wb[t] & 0xFFFFu), tf32_sample12(wb[t] >> 16));
+              *reinterpret_cast<uint4*>(dst + (((jj & 1) * KC + fr) * kNP + (jj >> 1)) * 16) = val;
+            }
+          }
+          if (gtid < 2) {  // column 0 of frame gtid: raw samples 6, 7
+            const int fr = gtid;
+            uint4 val = make_uint4(0, 0, 0, 0);
+            if (row_ok && 0 >= jlo && 0 < jhi) {
+              const uint8_t* p0 = raw + fr * kRawBoxStep + 12;
+              const uint32_t w0 = *reinterpret_cast<const uint32_t*>(p0);
+              const uint32_t w1 = *reinterpret_cast<const uint32_t*>(p0 + kRawRowBytes);
+              val = make_uint4(tf32_sample12(w0 & 0xFFFFu), tf32_sample12(w0 >> 16), tf32_sample12(w1 & 0xFFFFu),
+                               tf32_sample12(w1 >> 16));
+            }
+            *reinterpret_cast<uint4*>(dst + (fr * kNP) * 16) = val;
           }
           tc::fence_proxy_async();
           tc::mbar_arrive(&full[slot]);
