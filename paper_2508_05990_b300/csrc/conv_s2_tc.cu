@@ -311,7 +311,8 @@ __global__ void __launch_bounds__(threads_of<SRC>(), SRC == 2 ? 3 : 2)
             const int it = gtid + u * kGT;
             const int p = it / KC, kc = it - p * KC, ix = c0 + p;
             const bool ok = row_ok && it < NITEM && ix >= 0 && ix < a.Wi;
-            v[u] = ok ? __ldg(reinterpret_cast<const uint4*>(a.in + (rowbase + ix) * CIN + kc * 8))
+            // the map's last read: evict-first
+            v[u] = ok ? __ldcs(reinterpret_cast<const uint4*>(a.in + (rowbase + ix) * CIN + kc * 8))
                       : make_uint4(0, 0, 0, 0);
           }
           if (!slot_free()) {
@@ -574,7 +575,9 @@ __global__ void __launch_bounds__(threads_of<SRC>(), SRC == 2 ? 3 : 2)
         for (int q = 0; q < 4; ++q) {
           const int p = 8 * q + (lane >> 2), piece = lane & 3;
           const uint4 val = *reinterpret_cast<const uint4*>(tb + p * kTP + 4 * piece);
-          if (px0 + p < a.Wo) reinterpret_cast<uint4*>(a.out + (obase + p) * kN)[piece] = val;
+          // evict-first: the next layer reads the map once; the frames, which the
+          // refine and fallback searches read after the network, stay in L2
+          if (px0 + p < a.Wo) __stcs(reinterpret_cast<uint4*>(a.out + (obase + p) * kN) + piece, val);
         }
         __syncwarp();  // the buffer is rewritten by the next row
       }
