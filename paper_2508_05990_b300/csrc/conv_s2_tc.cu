@@ -95,7 +95,7 @@ constexpr uint32_t kWaitLimit = 1u << 22;
 // always belongs to group j % G).  Layer 1 (Bayer frames) has small rows and
 // little work per loaded byte, so it keeps more rows in flight: 8 slots, 8
 // one-warp groups; converting TMA-staged rows, 4 slots, 2 two-warp groups and
-// 4 raw slots, so that three CTAs fit an SM (60 KB, 320 threads); layer 2: 4
+// 4 raw slots, so that three CTAs fit an SM (70 KB, 320 threads); layer 2: 4
 // slots, 2 groups of 4 warps.
 template <int CIN, int SRC>
 struct S2Layout {
