@@ -168,6 +168,50 @@ __global__ void __launch_bounds__(256) prop_nhwc4_kernel(const PropArgs a, int c
   }
 }
 
+// NHWC with C % 4 == 0, bilinear, two or more cells per block side: one
+// thread per (2 x 2 quad of cells, 4 channels) of a quad row (grid.x = the
+// row's quads x float4 vectors / 256, grid.y = quad row, grid.z = map).  The
+// quad's cells share one MV, so their 16 taps are the 3 x 3 grid of rows
+// y0 .. y0 + 2 and columns x0 .. x0 + 2, each clamped as for a single cell:
+// 9 float4 loads for 4 outputs, every output bit for bit bilinear_taps /
+// blend of its cell (as in warp_quad); a warp's loads and stores are
+// contiguous runs of the cells' channel vectors.
+__global__ void __launch_bounds__(256) prop_nhwc4_quad_kernel(const PropArgs a, int c4n, int lc4, int qw) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= qw * c4n) return;
+  const int m = blockIdx.z;
+  const int qx = lc4 >= 0 ? t >> lc4 : t / c4n;
+  const int c4 = t - qx * c4n;
+  const int fy = 2 * blockIdx.y, fx = 2 * qx;
+  const bayer_mv_t mv = a.mv[((long long)m * a.mv_h + (fy >> a.lc)) * a.mv_w + (fx >> a.lc)];
+  const Taps tp = bilinear_taps(a.ls, a.Hf, a.Wf, fy, fx, mv);
+  const int oy = (int)mv.dy >> a.ls, ox = (int)mv.dx >> a.ls;
+  const float4* in = reinterpret_cast<const float4*>(a.feat) + (long long)m * a.Hf * a.Wf * c4n + c4;
+  float4 v[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const long long row = (long long)clampi(fy + oy + i, 0, a.Hf - 1) * a.Wf;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) v[i][j] = __ldg(in + (row + clampi(fx + ox + j, 0, a.Wf - 1)) * c4n);
+  }
+  auto quad_blend = [&](int i, int j) {
+    float4 r;
+    r.x = blend(tp, v[i][j].x, v[i][j + 1].x, v[i + 1][j].x, v[i + 1][j + 1].x);
+    r.y = blend(tp, v[i][j].y, v[i][j + 1].y, v[i + 1][j].y, v[i + 1][j + 1].y);
+    r.z = blend(tp, v[i][j].z, v[i][j + 1].z, v[i + 1][j].z, v[i + 1][j + 1].z);
+    r.w = blend(tp, v[i][j].w, v[i][j + 1].w, v[i + 1][j].w, v[i + 1][j + 1].w);
+    return r;
+  };
+  float4* out = reinterpret_cast<float4*>(a.out) + (((long long)m * a.Hf + fy) * a.Wf + fx) * c4n + c4;
+  const bool row2 = fy + 1 < a.Hf, col2 = fx + 1 < a.Wf;
+  __stcs(out, quad_blend(0, 0));
+  if (col2) __stcs(out + c4n, quad_blend(0, 1));
+  if (row2) {
+    __stcs(out + (long long)a.Wf * c4n, quad_blend(1, 0));
+    if (col2) __stcs(out + ((long long)a.Wf + 1) * c4n, quad_blend(1, 1));
+  }
+}
+
 // NHWC, any C: one thread per (map, cell, channel).
 template <int INTERP>
 __global__ void __launch_bounds__(256) prop_nhwc1_kernel(const PropArgs a) {
@@ -238,11 +282,18 @@ cudaError_t launch_propagate(const PropArgs& args, int layout, int interp, cudaS
              (reinterpret_cast<uintptr_t>(a.out) & 15) == 0 && a.n <= 65535 && a.Hf <= 65535 &&
              (long long)a.Hf * a.Wf * (a.C >> 2) < (1ll << 31) - 256) {
     const int c4n = a.C >> 2;
-    dim3 g(blocks_for((long long)a.Wf * c4n, 256), a.Hf, a.n);
-    if (interp == BAYER_INTERP_NEAREST)
-      prop_nhwc4_kernel<BAYER_INTERP_NEAREST><<<g, 256, 0, st>>>(a, c4n, log2_exact(c4n));
-    else
-      prop_nhwc4_kernel<BAYER_INTERP_BILINEAR><<<g, 256, 0, st>>>(a, c4n, log2_exact(c4n));
+    if (interp == BAYER_INTERP_BILINEAR && a.lc >= 1) {
+      // quads: the cells of a 2 x 2 quad share their block's MV
+      const int qw = (a.Wf + 1) / 2;
+      dim3 g(blocks_for((long long)qw * c4n, 256), (a.Hf + 1) / 2, a.n);
+      prop_nhwc4_quad_kernel<<<g, 256, 0, st>>>(a, c4n, log2_exact(c4n), qw);
+    } else {
+      dim3 g(blocks_for((long long)a.Wf * c4n, 256), a.Hf, a.n);
+      if (interp == BAYER_INTERP_NEAREST)
+        prop_nhwc4_kernel<BAYER_INTERP_NEAREST><<<g, 256, 0, st>>>(a, c4n, log2_exact(c4n));
+      else
+        prop_nhwc4_kernel<BAYER_INTERP_BILINEAR><<<g, 256, 0, st>>>(a, c4n, log2_exact(c4n));
+    }
   } else {
     const unsigned g = blocks_for(cells * a.C, 256);
     if (interp == BAYER_INTERP_NEAREST)

@@ -200,7 +200,7 @@ def _records(mv):
 
 
 @pytest.mark.parametrize("C,Hf,Wf,stride", [(64, 64, 64, 4), (256, 136, 240, 8), (7, 20, 36, 2), (3, 9, 13, 4),
-                                          (6, 11, 7, 8), (5, 8, 12, 16)])
+                                          (6, 11, 7, 8), (5, 8, 12, 16), (12, 9, 13, 4), (8, 11, 7, 8)])
 @pytest.mark.parametrize("interp", [bm.INTERP_NEAREST, bm.INTERP_BILINEAR])
 @pytest.mark.parametrize("layout", [bm.LAYOUT_NCHW, bm.LAYOUT_NHWC])
 def test_propagate(handle, C, Hf, Wf, stride, interp, layout):
