@@ -150,17 +150,22 @@ bool seeded16_fast(int block, int phase, int W, int H, int range) {
 
 // Seeded refine on the fast kernels: warp-per-block +-4 refine, compacted list
 // of low-confidence blocks, list-mode exhaustive search of that list.
-// The fallback list (counter, then block indices) for nblk blocks, its counter
-// zeroed on st.
+// The fallback list (counter, then block indices) for nblk blocks.
+bayer_status_t fallback_list_space(bayer_me_s* h, long long nblk) {
+  return grow(h, &h->list, &h->list_bytes, (size_t)(nblk + 1) * sizeof(int));
+}
+
+// The same, its counter zeroed on st.
 bayer_status_t fallback_list(bayer_me_s* h, long long nblk, cudaStream_t st) {
-  bayer_status_t s = grow(h, &h->list, &h->list_bytes, (size_t)(nblk + 1) * sizeof(int));
+  bayer_status_t s = fallback_list_space(h, nblk);
   if (s != BAYER_OK) return s;
   return cuda_status(cudaMemsetAsync(h->list, 0, sizeof(int), st));
 }
 
-// The +-4 refine and the fallback searches; list_ready: fallback_list already
-// ran on st (so that the refine kernel follows the network's last layer
-// directly, as its dependent launch).
+// The +-4 refine and the fallback searches; list_ready: the list has room and
+// its counter is zeroed earlier on st (by the network's first launch), so
+// that the refine kernel follows the network's last layer directly, as its
+// dependent launch.
 bayer_status_t seeded_fast(bayer_me_s* h, const uint16_t* ref, const uint16_t* cur, int W, int H, int pitch,
                            long long rbs, long long cbs, int batch, int range, const float* prop, const float* conf,
                            float thresh, bayer_mv_t* out, uint8_t* fallback, int* n_fallback, cudaStream_t st,
@@ -585,9 +590,10 @@ bayer_status_t bayer_me_estimate_learned(bayer_me_t h, const uint16_t* ref, cons
   if ((s = grow(h, reinterpret_cast<char**>(&h->prop), &h->prop_bytes, nblk * 3 * sizeof(float))) != BAYER_OK) return s;
   float* prop = h->prop;
   float* conf = h->prop + 2 * nblk;
-  if ((s = fallback_list(h, (long long)nblk, st)) != BAYER_OK) return s;
+  // the network's first launch zeroes the fallback list's counter
+  if ((s = fallback_list_space(h, (long long)nblk)) != BAYER_OK) return s;
   bme::CnnFrames fr{ref, cur, W, H, pitch, ref_bs, cur_bs};
-  cudaError_t e = bme::cnn_forward(fr, batch, w_bf16, range, h->cnn_acts, prop, conf, h->d_status, st);
+  cudaError_t e = bme::cnn_forward(fr, batch, w_bf16, range, h->cnn_acts, prop, conf, h->d_status, st, h->list);
   if (e != cudaSuccess) return cuda_status(e);
   return seeded_fast(h, ref, cur, W, H, pitch, ref_bs, cur_bs, batch, range, prop, conf, conf_thresh, mv_out,
                      fallback_out, n_fallback, st, true);

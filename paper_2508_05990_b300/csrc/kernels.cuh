@@ -76,8 +76,11 @@ struct CnnShapes {
 CnnShapes cnn_shapes(int W, int H);
 size_t cnn_act_bytes(int W, int H, int batch);   // bf16 activations of layers 1..4 + packed weights
 size_t cnn_grad_bytes(int W, int H, int batch);  // bf16 pre-activation gradients of layers 1..4
+// zero_word (optional): an int the forward's first launch sets to 0 (the
+// fallback list's counter of a learned search, so that no separate memset
+// sits between the previous kernel and the network).
 cudaError_t cnn_forward(const CnnFrames& fr, int batch, const uint16_t* wbf16, int range, void* acts, float* prop,
-                        float* conf, int* status, cudaStream_t st);
+                        float* conf, int* status, cudaStream_t st, int* zero_word = nullptr);
 cudaError_t cnn_loss_grad(const CnnFrames& fr, int batch, const uint16_t* wbf16, const bayer_mv_t* labels, int range,
                           float neg_weight, void* acts, void* dpre, float* grad, float* loss, int* status,
                           cudaStream_t st);
@@ -107,10 +110,11 @@ cudaError_t configure_conv_tc();
 // Packed weight image of one layer in bytes: cin_op = 32 for layers 2..4, 16
 // for layer 1 (whose TF32 image of 8 planes has the same 9216 bytes).  pack_conv_tc_weights builds all four layers'
 // images in one launch: layer l from the [32][cin][3][3] bf16 block at
-// w + w_off[l], written at byte img_off[l] (256-byte aligned) of img.
+// w + w_off[l], written at byte img_off[l] (256-byte aligned) of img;
+// zero_word (optional) is set to 0 by the same launch.
 size_t conv_tc_weight_bytes(int cin_op);
 cudaError_t pack_conv_tc_weights(const uint16_t* w, const int* w_off, const size_t* img_off, uint16_t* img,
-                                 cudaStream_t st);
+                                 int* zero_word, cudaStream_t st);
 cudaError_t launch_conv_tc(const ConvTcArgs& a, int layer, bool head, cudaStream_t st);  // layers 3, 4
 // Inference: layers 3 and 4 and the head in one kernel (the layer-3 map stays
 // in shared memory); l3 describes layer 3 (and carries the head's fields),
