@@ -85,8 +85,13 @@ struct PackArgs {
   int* zero_word;  // optional: set to 0 (a counter that kernels after the network fill)
 };
 
+// Launched as a dependent of whatever precedes it on the stream (its launch
+// overlaps that kernel's last CTAs); it reads the weights only after the wait,
+// since the kernel before may have written them (an optimizer step).
 __global__ void pack_conv_tc_weights_kernel(const PackArgs pa, __nv_bfloat16* __restrict__ img) {
   constexpr int kL1 = kN * 9 * 8, kL = kN * 9 * 32;
+  tc::grid_dep_wait();
+  tc::grid_dep_launch();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0 && pa.zero_word) *pa.zero_word = 0;
   if (i < kL1) {
@@ -479,8 +484,8 @@ cudaError_t pack_conv_tc_weights(const uint16_t* w, const int* w_off, const size
     pa.img_off[l] = (unsigned)img_off[l];
   }
   const int n = kN * 9 * 8 + 3 * kN * 9 * 32;
-  pack_conv_tc_weights_kernel<<<(n + 255) / 256, 256, 0, st>>>(pa, reinterpret_cast<__nv_bfloat16*>(img));
-  return cudaGetLastError();
+  return tc::launch_dependent(pack_conv_tc_weights_kernel, dim3((n + 255) / 256), dim3(256), 0, st, pa,
+                              reinterpret_cast<__nv_bfloat16*>(img));
 }
 
 cudaError_t configure_conv_tc() {
