@@ -9,7 +9,8 @@
 // with 16-byte aligned rows are staged by two TMA tile loads (window and
 // current tile, as in the single-pair search) from tensor maps per pair that
 // the host encodes for the schedule's strip width into the map table on
-// every call; other frames by 16-byte or pair-word loads.  The
+// every call, unless the schedule asks for plain loads; other frames by
+// 16-byte or pair-word loads.  The
 // hardware block scheduler balances the strips (a persistent variant with an
 // atomic work queue measured slower once the search itself got cheaper).
 // Completion times, from %globaltimer, relative to the search launch's start
@@ -24,10 +25,10 @@
 // Propagation: one CTA (288 threads) per item, the pair found by binary
 // search in a second prefix table; the CTA warps part of the pair's NCHW
 // feature map by its MV field.  Bilinear with two or more cells per block
-// side, on a map whose rows and base allow TMA loads: an item is a tile of
-// 16 x 64 cells and 16 channels staged through shared memory by TMA loads
-// (prop_tma.cuh), from a tensor map per pair that the host encodes into the
-// descriptor table on every call.  Otherwise an item is a chunk of 4
+// side, on a map whose rows and base allow TMA loads (and a schedule that
+// takes them): an item is a tile of 16 x 64 cells and 16 channels staged
+// through shared memory by TMA loads (prop_tma.cuh), from a tensor map per
+// pair that the host encodes into the map table on every call.  Otherwise an item is a chunk of 4
 // channels and a tile of 256 units on the first 256 threads, straight from
 // global memory (prop_common.cuh); a unit is a 2 x 2 quad of cells sharing
 // one MV (bilinear, two or more cells per block side) or one cell.  Its CTAs
@@ -46,9 +47,9 @@
 // propagation as global-memory items instead of TMA-staged tiles (each where
 // a pair could take the TMA form).  It keeps the candidate with the lowest
 // median completion time among those whose step takes at most 3 % longer
-// than the fastest.  The
-// graph (counter reset, launches, end times) is then captured once and
-// relaunched with only the descriptor table refreshed.
+// than the fastest.  The graph (counter reset, launches, end times) is then
+// captured once and relaunched with only the descriptor and tensor-map tables
+// refreshed.
 #include <algorithm>
 #include <map>
 #include <string>
