@@ -362,6 +362,19 @@ bool encode_strip_maps_nw(int range, MsMaps* mp, const bayer_pair_t& q) {
 
 }  // namespace
 
+// What one slot's tensor maps were encoded from: a slot is re-encoded only
+// when its pair's buffers, sizes or staging choice change.
+struct MapKey {
+  const void* ref = nullptr;
+  const void* cur = nullptr;
+  const void* feat = nullptr;
+  int W = -1, H = 0, pitch = 0, C = 0, Hf = 0, Wf = 0, nw = 0, range = 0, win = 0, prop = 0;
+  bool operator==(const MapKey& o) const {
+    return ref == o.ref && cur == o.cur && feat == o.feat && W == o.W && H == o.H && pitch == o.pitch && C == o.C &&
+           Hf == o.Hf && Wf == o.Wf && nw == o.nw && range == o.range && win == o.win && prop == o.prop;
+  }
+};
+
 // Per-handle state: device tables, counters, the autotune table and cached
 // graphs (one per set of frame sizes and schedule).
 struct MultiStream {
@@ -384,6 +397,8 @@ struct MultiStream {
     cudaGraphExec_t exec = nullptr;
   };
   std::map<std::string, Entry> cache;  // autotune table + graphs
+  std::vector<MapKey> map_keys;        // [cap] what h_maps[k] holds
+  std::vector<int> map_win;            // [cap] its search maps could be encoded
   cudaStream_t capture = nullptr;
   Classes classes;  // of the last table built
 };
@@ -469,6 +484,8 @@ cudaError_t ensure_capacity(MultiStream* m, int n) {
   if ((e = cudaMallocHost(&m->h_maps, sizeof(MsMaps) * c)) != cudaSuccess) return e;
   if ((e = cudaMallocHost(&m->h_prefix, sizeof(int) * 2 * (c + 1))) != cudaSuccess) return e;
   m->cap = c;
+  m->map_keys.assign(c, MapKey{});
+  m->map_win.assign(c, 0);
   return cudaSuccess;
 }
 
@@ -540,17 +557,35 @@ bool build_table(MultiStream* m, const bayer_pair_t* pairs, int n, const Config&
     P.tiles_x = g.tiles_x;
     P.prop_tiles = g.tiles;
     P.pr_items = g.items;
-    m->h_maps[k] = MsMaps{};
-    if (g.tma && !tma::encode_f32_planes(&m->h_maps[k].feat, q.feat, q.Wf, q.Hf, q.C, prop::kBW, prop::kRH))
-      return false;
     P.vec = (reinterpret_cast<uintptr_t>(q.ref) % 16 == 0 && reinterpret_cast<uintptr_t>(q.cur) % 16 == 0 &&
              q.pitch % 8 == 0) ? 1 : 0;
-    // a map that cannot be encoded leaves the pair on plain-load staging (same launch shape)
-    P.win_tma = !cfg.win_plain && P.vec &&
-                        (cfg.nw == 4 ? encode_strip_maps_nw<4>(range, &m->h_maps[k], q)
-                                     : encode_strip_maps_nw<8>(range, &m->h_maps[k], q))
-                    ? 1
-                    : 0;
+    MapKey key;
+    key.ref = q.ref;
+    key.cur = q.cur;
+    key.feat = q.feat;
+    key.W = q.W;
+    key.H = q.H;
+    key.pitch = q.pitch;
+    key.C = q.C;
+    key.Hf = q.Hf;
+    key.Wf = q.Wf;
+    key.nw = cfg.nw;
+    key.range = range;
+    key.win = !cfg.win_plain && P.vec;
+    key.prop = g.tma;
+    if (!(m->map_keys[k] == key)) {
+      m->map_keys[k] = MapKey{};
+      m->h_maps[k] = MsMaps{};
+      if (g.tma && !tma::encode_f32_planes(&m->h_maps[k].feat, q.feat, q.Wf, q.Hf, q.C, prop::kBW, prop::kRH))
+        return false;
+      // a map that cannot be encoded leaves the pair on plain-load staging (same launch shape)
+      m->map_win[k] = key.win && (cfg.nw == 4 ? encode_strip_maps_nw<4>(range, &m->h_maps[k], q)
+                                               : encode_strip_maps_nw<8>(range, &m->h_maps[k], q))
+                          ? 1
+                          : 0;
+      m->map_keys[k] = key;
+    }
+    P.win_tma = m->map_win[k];
     m->h_prefix[k] = me;
     m->h_prefix[(n + 1) + k] = pr;
     me += P.me_items;
