@@ -284,6 +284,13 @@ __global__ void __launch_bounds__(256) ms_end_kernel(const unsigned long long* _
   }
 }
 
+// end_ns[perm[k]] = end[k]: schedule order back to the caller's.
+__global__ void ms_scatter_kernel(const long long* __restrict__ end, const int* __restrict__ perm,
+                                  long long* __restrict__ end_ns, int n) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) end_ns[perm[k]] = end[k];
+}
+
 struct Config {
   int nw;          // warps (blocks) per search strip: 4 or 8
   int order;       // 0: pairs as given, 1: largest first, 2: smallest first
@@ -382,7 +389,7 @@ struct MultiStream {
   int* status = nullptr;  // the handle's device status word (bounded waits record BAYER_ERR_TIMEOUT)
   MsPair* d_pairs = nullptr;
   MsMaps* d_maps = nullptr;  // [n] tensor maps of the TMA-staged pairs' frames and feature maps
-  int* d_prefix = nullptr;  // [2 * (n + 1)]: search prefix, then propagation prefix
+  int* d_prefix = nullptr;  // [3 * (n + 1)]: search prefix, propagation prefix, caller index per slot
   unsigned long long* d_stamp = nullptr;  // end time (%globaltimer) of every propagation item
   long long stamp_cap = 0;
   MsCounters* d_ctr = nullptr;
@@ -478,11 +485,11 @@ cudaError_t ensure_capacity(MultiStream* m, int n) {
   const int c = n < 64 ? 64 : n;
   if ((e = cudaMalloc(&m->d_pairs, sizeof(MsPair) * c)) != cudaSuccess) return e;
   if ((e = cudaMalloc(&m->d_maps, sizeof(MsMaps) * c)) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&m->d_prefix, sizeof(int) * 2 * (c + 1))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&m->d_prefix, sizeof(int) * 3 * (c + 1))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&m->d_end, sizeof(long long) * c)) != cudaSuccess) return e;
   if ((e = cudaMallocHost(&m->h_pairs, sizeof(MsPair) * c)) != cudaSuccess) return e;
   if ((e = cudaMallocHost(&m->h_maps, sizeof(MsMaps) * c)) != cudaSuccess) return e;
-  if ((e = cudaMallocHost(&m->h_prefix, sizeof(int) * 2 * (c + 1))) != cudaSuccess) return e;
+  if ((e = cudaMallocHost(&m->h_prefix, sizeof(int) * 3 * (c + 1))) != cudaSuccess) return e;
   m->cap = c;
   m->map_keys.assign(c, MapKey{});
   m->map_win.assign(c, 0);
@@ -588,6 +595,7 @@ bool build_table(MultiStream* m, const bayer_pair_t* pairs, int n, const Config&
     P.win_tma = m->map_win[k];
     m->h_prefix[k] = me;
     m->h_prefix[(n + 1) + k] = pr;
+    m->h_prefix[2 * (n + 1) + k] = (*perm)[k];  // the caller's index of slot k
     me += P.me_items;
     pr += P.pr_items;
   }
@@ -711,7 +719,7 @@ cudaError_t upload(MultiStream* m, int n, cudaStream_t st) {
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(m->d_maps, m->h_maps, sizeof(MsMaps) * n, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(m->d_prefix, m->h_prefix, sizeof(int) * 2 * (n + 1), cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyAsync(m->d_prefix, m->h_prefix, sizeof(int) * 3 * (n + 1), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaEventRecord(m->copied, st);
   return e;
 }
@@ -828,8 +836,8 @@ cudaError_t ms_run(MultiStream* m, const bayer_pair_t* pairs, int n, int range, 
   if ((e = cudaGraphLaunch(it->second.exec, st)) != cudaSuccess) return e;
   if (end_ns) {
     // end times are in schedule order; scatter them back to the caller's order
-    for (int k = 0; k < n && e == cudaSuccess; ++k)
-      e = cudaMemcpyAsync(end_ns + perm[k], m->d_end + k, sizeof(long long), cudaMemcpyDeviceToDevice, st);
+    ms_scatter_kernel<<<(n + 255) / 256, 256, 0, st>>>(m->d_end, m->d_prefix + 2 * (n + 1), end_ns, n);
+    e = cudaGetLastError();
   }
   return e;
 }
