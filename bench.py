@@ -143,6 +143,29 @@ def ms_prop_bytes_per_step() -> int:
                for hh, ww in MS_SIZES)
 
 
+def ms_launches_per_step(sched: int) -> int:
+    """Kernel launches of one multi-stream call under schedule code `sched`: a
+    search and a propagation launch per class of frame size (the library's rule:
+    runs of equal sizes, smallest first, merged until a class holds an eighth of
+    the search strips; at most 8), or one of each; then the end-time kernel and
+    the scatter of the end times."""
+    base = sched % 1000
+    if base < 100:
+        return 2 + 2
+    nw = base % 100 // 10
+    sizes = sorted(MS_SIZES, key=lambda hw: hw[0] * hw[1])
+    strips = [(hh // BLOCK) * (-(-(ww // BLOCK) // nw)) for hh, ww in sizes]
+    min_items = -(-sum(strips) // 8)
+    classes, acc = 0, 0
+    for k, st in enumerate(strips):
+        acc += st
+        last = k + 1 == len(strips)
+        if last or (sizes[k + 1] != sizes[k] and (acc >= min_items and classes < 7)):
+            classes += 1
+            acc = 0
+    return 2 * classes + 2
+
+
 def refine_flops_per_frame() -> int:
     """Multiply-adds x 2 of the three 3x3 refine convs (C -> hidden -> hidden -> C) on one map."""
     hf, wf = K4_H // K4_STRIDE, K4_W // K4_STRIDE
@@ -468,7 +491,7 @@ def leg_multi_stream(h, clips, steps, warmup, peaks, pc_clk_sm, nsm, sm_mhz):
                      "peak_source": "measured packed min.u16x2 + dp2a rate x SMs x median SM clock; " + (
                          "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks
                          else "fallback 6400 GB/s (MEASURED_PEAKS.json absent)")},
-        "gpu_launches": 2 * steps,
+        "gpu_launches": ms_launches_per_step(sched) * steps,
         "l2": "inputs larger than L2 (2.2 GB of feature maps per step); no flush",
     }
 
@@ -682,7 +705,8 @@ def leg_refine_4k(h, clip, steps, warmup, peaks):
                                      else "fallback 1400 TFLOP/s sustained (MEASURED_PEAKS.json absent)"),
                      "fp32_simt_tflops": round(flops / (rf32 / 1e3) / 1e12, 1)},
         "bf16_vs_fp32_normwise": round(diff, 6),
-        "gpu_launches": 5 * steps,
+        # search, propagation, then per refine call three weight packs and three convs
+        "gpu_launches": 8 * steps,
     }
 
 
@@ -794,7 +818,8 @@ def run_ours(args):
             "mean_block_rel_regret": round(float(((sad_l - sad_plain) / np.maximum(sad_plain, 1)).mean()), 5),
             "search": "proposal CNN (BF16, tcgen05) + +-4 refine; exhaustive +-32 where conf < 0.5",
             "weights": os.path.relpath(WEIGHTS, ROOT) + " (4,000 training pairs)",
-            "gpu_launches": args.steps * 8,
+            # weight pack, layers 1 and 2, layers 3-4 + head, refine, fallback search, propagation
+            "gpu_launches": args.steps * 7,
         }
         if os.path.exists(WEIGHTS_2000):
             # the configured training scale: same clip, same timing
