@@ -575,12 +575,17 @@ def leg_ragged(h, steps, warmup, peak_gpcs):
     frame (exhaustive block 16 +-32, its last block row 8 rows high) beside the
     1920x1088 workload, and the paper's 720x960 runtime resolution (standard
     pyramid, EVEN; 720 is no multiple of 64 or 32) beside 768x960.  Seven pairs
-    per launch, search alone; G pixel-candidates/s count in-frame pixels."""
+    per launch, search alone; G pixel-candidates/s count in-frame pixels.  With
+    the shipped proposal weights, also the learned-seeded search (network, +-4
+    refine, fallback) on 1920x1080 beside 1920x1088."""
     import torch
     from paper_2508_05990_b300 import bayer_me as bm
     from paper_2508_05990_b300 import synth
     std = bm.C2F_PRESETS["standard"]
     out = {}
+    wbf = None
+    if os.path.exists(WEIGHTS):
+        wbf = bm.to_bf16_bits(torch.from_numpy(np.load(WEIGHTS)["theta"].astype(np.float32)).cuda()).contiguous()
     for name, Hh, Ww, mode in (("full_1920x1080", 1080, 1920, bm.MODE_FULL), ("full_1920x1088", 1088, 1920, bm.MODE_FULL),
                                ("c2f_standard_720x960", 720, 960, bm.MODE_C2F),
                                ("c2f_standard_768x960", 768, 960, bm.MODE_C2F)):
@@ -603,6 +608,26 @@ def leg_ragged(h, steps, warmup, peak_gpcs):
         pc = PAIRS * (Hh * Ww * (2 * (RANGE // 2) + 1) ** 2 if mode == bm.MODE_FULL else c2f_pc_in_frame(std, Hh, Ww))
         out[name] = {"me_ms": round(ms, 4), "frames_per_s": round(PAIRS / (ms / 1e3), 1),
                      "gpc_per_s": round(pc / (ms / 1e3) / 1e9, 1), "frac_of_alu_peak": round(pc / (ms / 1e3) / peak_gpcs, 4)}
+    for Hh in ((1080, 1088) if wbf is not None else ()):
+        frames = torch.from_numpy(synth.pan_clip(RAGGED_SEED, Hh, 1920, n_frames=T)).cuda()
+        mv = torch.empty((PAIRS, -(-Hh // BLOCK), 1920 // BLOCK, 2), dtype=torch.int32, device="cuda")
+        nfb = torch.zeros(1, dtype=torch.int32, device="cuda")
+
+        def run():
+            h.estimate_learned(frames, frames[1:], wbf, RANGE, 0.5, batch=PAIRS, ref_batch_stride=Hh * 1920,
+                               cur_batch_stride=Hh * 1920, out=mv, n_fallback=nfb)
+        for _ in range(warmup):
+            run()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(steps):
+            run()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[f"learned_1920x{Hh}"] = {"search_ms": round(ms, 4), "frames_per_s": round(PAIRS / (ms / 1e3), 1),
+                                     "fallback_frac": round(int(nfb.item()) / mv[..., 0].numel(), 4)}
     if h.sync_status() != bm.OK:
         raise RuntimeError("device status after the ragged-frame leg")
     out["ratio_1080_vs_1088"] = round(out["full_1920x1080"]["gpc_per_s"] / out["full_1920x1088"]["gpc_per_s"], 4)

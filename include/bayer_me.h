@@ -223,8 +223,13 @@ bayer_status_t bayer_probe_alu(bayer_me_t h, int variant, double* pc_per_clk_per
  *   z = head 1x1 conv 32 -> 12 + bias; channel 3*(2*sy + sx) + q of L4 cell
  *       (i, k) is quantity q of block (2i + sy, 2k + sx)
  *   dx = range * tanh(z_0), dy = range * tanh(z_1), conf = sigmoid(z_2)
- * Activations are bfloat16, accumulation float32.  W and H must be multiples
- * of 32 (the L4 grid is then exactly half the 16x16 block grid).
+ * Activations are bfloat16, accumulation float32.  Each layer has its natural
+ * size ceil(n / 2) of its input's n (the last row or column may read the zero
+ * pad), so the depth-to-space output has 2 * ceil(H / 32) block rows; the
+ * block grid is its top ceil(H / 16) rows (one fewer where ceil(H / 16) is
+ * odd, e.g. H = 720 or 2160).  W must be a multiple of 32; H a multiple of 8
+ * for the forward and the learned search (1080 included, whose last block row
+ * is 8 rows high), of 32 for the loss (BAYER_ERR_UNSUPPORTED otherwise).
  * Loss (mean over the blocks of the batch): BerHu_4(dx - dx*) +
  * BerHu_4(dy - dy*) - t log(conf) - w_neg (1 - t) log(1 - conf), with
  * BerHu_c(e) = |e| for |e| <= c, else (e^2 + c^2) / (2c); t = 1 where the
@@ -244,8 +249,8 @@ bayer_status_t bayer_probe_alu(bayer_me_t h, int variant, double* pc_per_clk_per
 #define BAYER_CNN_NPARAMS 30476
 
 /* Network forward on `batch` frame pairs (strides as in bayer_me_params_t):
- * prop_dxdy [batch][H/16][W/16][2] and conf [batch][H/16][W/16] (device
- * float32).  Activations use the handle's workspace. */
+ * prop_dxdy [batch][h][W/16][2] and conf [batch][h][W/16], h = ceil(H / 16)
+ * (device float32).  Activations use the handle's workspace. */
 bayer_status_t bayer_cnn_forward(bayer_me_t h, const uint16_t* ref, const uint16_t* cur, int W, int H, int pitch,
                                  int batch, long long ref_batch_stride, long long cur_batch_stride,
                                  const uint16_t* w_bf16, int range, float* prop_dxdy, float* conf, void* stream);
@@ -270,7 +275,9 @@ bayer_status_t bayer_cnn_adamw(bayer_me_t h, float* w, uint16_t* w_bf16, const f
 
 /* Learned-seeded search: network forward, +-4 refine of the blocks with
  * conf >= conf_thresh, exhaustive +-range search of the others (block 16,
- * EVEN phase, range in {8, 16, 24, 32}).  mv_out [batch][H/16][W/16];
+ * EVEN phase, range in {8, 16, 24, 32}).  mv_out [batch][ceil(H/16)][W/16]
+ * (a last block row clipped by the frame is searched over its rows in the
+ * frame, as in the exhaustive search);
  * fallback_out (optional) 1 where the full search ran; n_fallback (optional,
  * device int) the number of such blocks.  The result is exactly the SEEDED
  * mode of bayer_me_estimate_ex given the network's proposals. */

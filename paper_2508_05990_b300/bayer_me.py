@@ -300,10 +300,11 @@ class Handle:
     # -- learned proposal network and learned-seeded search -----------------
     def cnn_forward(self, ref, cur, w_bf16, search_range=32, batch=1, ref_batch_stride=0, cur_batch_stride=0,
                     prop=None, conf=None, stream=None):
-        """Proposals [batch, h, w, 2] and confidences [batch, h, w] (float32 tensors)."""
+        """Proposals [batch, h, w, 2] and confidences [batch, h, w] (float32 tensors);
+        h = ceil(H / 16), w = W / 16."""
         import torch
         H, W = ref.shape[-2:]
-        h, w = H // 16, W // 16
+        h, w = grid_shape(H, W, 16)
         if prop is None:
             prop = torch.empty((batch, h, w, 2), dtype=torch.float32, device=ref.device)
         if conf is None:
@@ -336,12 +337,14 @@ class Handle:
 
     def estimate_learned(self, ref, cur, w_bf16, search_range=32, conf_thresh=0.5, batch=1, ref_batch_stride=0,
                          cur_batch_stride=0, out=None, fallback=None, n_fallback=None, stream=None):
-        """Learned-seeded search; returns the [batch, h, w, 2] int32 record tensor."""
+        """Learned-seeded search; returns the [batch, h, w, 2] int32 record tensor
+        (h = ceil(H / 16): a last block row clipped by the frame counts)."""
         import torch
         H, W = ref.shape[-2:]
+        h, w = grid_shape(H, W, 16)
         if out is None:
-            out = torch.empty((batch, H // 16, W // 16, 2), dtype=torch.int32, device=ref.device)
-        _check_out(out, batch * (H // 16) * (W // 16) * 2, torch.int32, ref.device, "estimate_learned")
+            out = torch.empty((batch, h, w, 2), dtype=torch.int32, device=ref.device)
+        _check_out(out, batch * h * w * 2, torch.int32, ref.device, "estimate_learned")
         _check(self._lib.bayer_me_estimate_learned(self._h, _ptr(ref), _ptr(cur), W, H, W, batch, ref_batch_stride,
                                                    cur_batch_stride, _ptr(w_bf16), search_range, float(conf_thresh),
                                                    _ptr(out), _ptr(fallback), _ptr(n_fallback), _stream(stream)),

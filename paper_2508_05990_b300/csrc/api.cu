@@ -144,8 +144,7 @@ bayer_status_t full_search(const uint16_t* ref, const uint16_t* cur, int W, int 
 }
 
 bool seeded16_fast(int block, int phase, int W, int H, int range) {
-  return block == 16 && phase == BAYER_PHASE_EVEN && (W % 16) == 0 && (H % 16) == 0 &&
-         bme::full16_even_supported(range);
+  return block == 16 && phase == BAYER_PHASE_EVEN && (W % 16) == 0 && bme::full16_even_supported(range);
 }
 
 // Seeded refine on the fast kernels: warp-per-block +-4 refine, compacted list
@@ -170,7 +169,7 @@ bayer_status_t seeded_fast(bayer_me_s* h, const uint16_t* ref, const uint16_t* c
                            long long rbs, long long cbs, int batch, int range, const float* prop, const float* conf,
                            float thresh, bayer_mv_t* out, uint8_t* fallback, int* n_fallback, cudaStream_t st,
                            bool list_ready = false) {
-  const int hb = H / 16, wb = W / 16;
+  const int hb = (H + 15) / 16, wb = W / 16;  // a last block row clipped by the frame counts
   const long long nblk = (long long)batch * hb * wb;
   if (!list_ready) {
     bayer_status_t s = fallback_list(h, nblk, st);
@@ -204,11 +203,15 @@ bayer_status_t seeded_fast(bayer_me_s* h, const uint16_t* ref, const uint16_t* c
   return cuda_status(e);
 }
 
+// Frames for the network: W a multiple of 32; H a multiple of 32 for training
+// (the loss covers the network's whole 2 H4 x 2 W4 block grid), of 8 for
+// inference (the layers take their natural sizes, the proposals are cropped
+// to the ceil(H / 16) block rows).
 bayer_status_t check_cnn_frames(const void* ref, const void* cur, int W, int H, int pitch, int batch, long long rbs,
-                                long long cbs) {
+                                long long cbs, bool infer) {
   bayer_status_t s = check_frames(ref, cur, W, H, pitch, 16);
   if (s != BAYER_OK) return s;
-  if ((W % 32) != 0 || (H % 32) != 0) return BAYER_ERR_UNSUPPORTED;
+  if ((W % 32) != 0 || (H % (infer ? 8 : 32)) != 0) return BAYER_ERR_UNSUPPORTED;
   if (batch < 1 || batch > 65535 || rbs < 0 || cbs < 0) return BAYER_ERR_INVALID_ARG;
   return BAYER_OK;
 }
@@ -529,7 +532,7 @@ bayer_status_t bayer_cnn_forward(bayer_me_t h, const uint16_t* ref, const uint16
                                  float* prop_dxdy, float* conf, void* stream) {
   NvtxRange nvtx_range("bayer_cnn_forward");
   if (!h || !w_bf16 || !prop_dxdy || !conf || range < 1 || range > 510) return BAYER_ERR_INVALID_ARG;
-  bayer_status_t s = check_cnn_frames(ref, cur, W, H, pitch, batch, ref_bs, cur_bs);
+  bayer_status_t s = check_cnn_frames(ref, cur, W, H, pitch, batch, ref_bs, cur_bs, true);
   if (s != BAYER_OK) return s;
   DeviceGuard g(h->device);
   if ((s = grow(h, reinterpret_cast<char**>(&h->cnn_acts), &h->cnn_acts_bytes, bme::cnn_act_bytes(W, H, batch))) !=
@@ -547,7 +550,7 @@ bayer_status_t bayer_cnn_loss_grad(bayer_me_t h, const uint16_t* ref, const uint
   NvtxRange nvtx_range("bayer_cnn_loss_grad");
   if (!h || !w_bf16 || !labels || !grad || !loss || range < 1 || range > 510) return BAYER_ERR_INVALID_ARG;
   if (!(neg_weight > 0.f)) return BAYER_ERR_INVALID_ARG;
-  bayer_status_t s = check_cnn_frames(ref, cur, W, H, pitch, batch, ref_bs, cur_bs);
+  bayer_status_t s = check_cnn_frames(ref, cur, W, H, pitch, batch, ref_bs, cur_bs, false);
   if (s != BAYER_OK) return s;
   DeviceGuard g(h->device);
   if ((s = grow(h, reinterpret_cast<char**>(&h->cnn_acts), &h->cnn_acts_bytes, bme::cnn_act_bytes(W, H, batch))) !=
@@ -578,12 +581,12 @@ bayer_status_t bayer_me_estimate_learned(bayer_me_t h, const uint16_t* ref, cons
                                          uint8_t* fallback_out, int* n_fallback, void* stream) {
   NvtxRange nvtx_range("bayer_me_estimate_learned");
   if (!h || !w_bf16 || !mv_out) return BAYER_ERR_INVALID_ARG;
-  bayer_status_t s = check_cnn_frames(ref, cur, W, H, pitch, batch, ref_bs, cur_bs);
+  bayer_status_t s = check_cnn_frames(ref, cur, W, H, pitch, batch, ref_bs, cur_bs, true);
   if (s != BAYER_OK) return s;
   if (!bme::full16_even_supported(range)) return BAYER_ERR_UNSUPPORTED;
   DeviceGuard g(h->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const size_t nblk = (size_t)batch * (H / 16) * (W / 16);
+  const size_t nblk = (size_t)batch * ((H + 15) / 16) * (W / 16);
   if ((s = grow(h, reinterpret_cast<char**>(&h->cnn_acts), &h->cnn_acts_bytes, bme::cnn_act_bytes(W, H, batch))) !=
       BAYER_OK)
     return s;

@@ -213,9 +213,11 @@ __global__ void __launch_bounds__(kM) conv3x3_tc_kernel(const ConvTcArgs a) {
         // the head sees the bf16 activation, as it would read it back from memory
 #pragma unroll
         for (int j = 0; j < 32; ++j) v[j] = __bfloat162float(__float2bfloat16_rn(v[j]));
-        const int hb = 2 * a.Ho, wb = 2 * a.Wo;
+        // the block grid: ceil(H / 16) rows (the network's 2 Ho rows cropped), 2 Wo columns
+        const int hb = (a.fr.H + 15) / 16, wb = 2 * a.Wo;
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
+          if (2 * oy + (s >> 1) >= hb) continue;
           float z[3];
 #pragma unroll
           for (int q = 0; q < 3; ++q) {
@@ -410,7 +412,7 @@ __global__ void __launch_bounds__(k34Threads) conv34_head_tc_kernel(const Conv34
   }
   ok &= tc::mbar_wait(&mbar[2], 0, kWaitLimit);
   tc::fence_after_sync();
-  const int hb = 2 * c.H4, wb = 2 * c.W4;
+  const int hb = (a.fr.H + 15) / 16, wb = 2 * c.W4;  // the block grid (2 H4 rows cropped to ceil(H / 16))
   {
     // warps 0-3: layer-4 row u0, warps 4-7: row u0 + 1
     const int v2 = half;
@@ -424,6 +426,7 @@ __global__ void __launch_bounds__(k34Threads) conv34_head_tc_kernel(const Conv34
         v[jj] = __bfloat162float(__float2bfloat16_rn(fmaxf(v[jj] + sBias[kN + jj], 0.f)));
 #pragma unroll
       for (int s = 0; s < 4; ++s) {
+        if (2 * y4 + (s >> 1) >= hb) continue;
         float z[3];
 #pragma unroll
         for (int q = 0; q < 3; ++q) {

@@ -120,10 +120,12 @@ struct Full16WinSums {
 // accumulated by one warp from a staged window (wbase: the block's window
 // origin, row pitch P words) and current block (cbase, row pitch PC words).
 // Lane v owns candidate row v (lanes past the last row repeat it).  With
-// SUMS the lane also gathers its window sums into S.
-template <int R, int P, int PC, bool SUMS = false>
+// SUMS the lane also gathers its window sums into S.  With CLIP the loop
+// runs over the block's bh rows only (a last block row clipped by the frame),
+// so that the window sums cover the rows the SAD covers.
+template <int R, int P, int PC, bool SUMS = false, bool CLIP = false>
 __device__ __forceinline__ void full16_accumulate(const uint32_t* wbase, const uint32_t* cbase, int lane,
-                                                  Full16Acc<R>& A, Full16WinSums<R>& S) {
+                                                  Full16Acc<R>& A, Full16WinSums<R>& S, int bh = 16) {
   constexpr int NU = 2 * R + 1, SPANW = 8 + 2 * R;
   const int v = lane < NU ? lane : NU - 1;
   const int eps = (lane >> 2) & 1;  // row rotation for conflict-free loads
@@ -139,9 +141,16 @@ __device__ __forceinline__ void full16_accumulate(const uint32_t* wbase, const u
     S.scn = 0;
   }
 
+  const int rows = CLIP ? bh : 16;
 #pragma unroll 1
-  for (int i = 0; i < 16; ++i) {
-    const int r = (i + eps) & 15;
+  for (int i = 0; i < rows; ++i) {
+    int r;
+    if constexpr (CLIP) {
+      r = i + eps;
+      r = r >= bh ? r - bh : r;
+    } else {
+      r = (i + eps) & 15;
+    }
     uint32_t c[8];
     const uint4* cp = reinterpret_cast<const uint4*>(cbase + r * PC);
 #pragma unroll

@@ -188,7 +188,8 @@ __device__ __forceinline__ void list_stage(const uint16_t* __restrict__ ref, con
             raw[j] = __ldg(reinterpret_cast<const uint4*>(ref + (long long)gy * pitch + gx));
         } else if (e < NT) {
           const int f = e - NW, ry = f >> 1, cx = f & 1;
-          raw[j] = __ldg(reinterpret_cast<const uint4*>(cur + (long long)(y0 + ry) * pitch + x0 + 8 * cx));
+          if (y0 + ry < H)  // a clipped last block row keeps zero rows below the frame
+            raw[j] = __ldg(reinterpret_cast<const uint4*>(cur + (long long)(y0 + ry) * pitch + x0 + 8 * cx));
         }
       }
 #pragma unroll
@@ -222,7 +223,10 @@ __device__ __forceinline__ void list_where(int gb, int h, int w, int& pair, int&
   x0 = (rem - by * w) * 16;
 }
 
-template <int R, bool TMA>
+// CLIP: the frame height is no multiple of 16; a block of the last block row
+// runs over its bh = H - y0 rows (the current rows below the frame are staged
+// as zeros: TMA fills them, the plain loads skip them).
+template <int R, bool TMA, bool CLIP>
 __global__ void __launch_bounds__(kLW * 32) me_full16_list_kernel(const __grid_constant__ CUtensorMap tm_ref,
                                                                    const __grid_constant__ CUtensorMap tm_cur,
                                                                    const uint16_t* __restrict__ ref_base,
@@ -281,7 +285,8 @@ __global__ void __launch_bounds__(kLW * 32) me_full16_list_kernel(const __grid_c
     }
     Full16Acc<R> A;
     Full16WinSums<R> S;
-    full16_accumulate<R, C::P, C::PC, true>(win, curt, lane, A, S);
+    const int bh = CLIP && y0 + 16 > H ? H - y0 : 16;
+    full16_accumulate<R, C::P, C::PC, true, CLIP>(win, curt, lane, A, S, bh);
     const int gn = gi + step;
     int pn = 0, xn = 0, yn = 0;
     if constexpr (TMA) {
@@ -301,7 +306,7 @@ __global__ void __launch_bounds__(kLW * 32) me_full16_list_kernel(const __grid_c
         tma::load_3d(curt, &tm_cur, xn, yn, pn, &mbar[warp]);
       }
     }
-    const uint64_t best = warp_min_u64(full16_select<R>(A, lane, x0, y0, W, H));
+    const uint64_t best = warp_min_u64(full16_select<R>(A, lane, x0, y0, W, H, bh));
     if (lane == 0) out[gb] = key_to_mv(best);
   }
 }
@@ -319,23 +324,26 @@ cudaError_t launch_list_r(const uint16_t* ref, const uint16_t* cur, int W, int H
   const bool use_tma = vec_ok &&
                        tma::encode_u16_frames(&tref, ref, W, H, batch, pitch, ref_bs, C::BOX_W, C::WIN_H) &&
                        tma::encode_u16_frames(&tcur, cur, W, H, batch, pitch, cur_bs, 16, 16);
-  const int per_sm = use_tma ? tc::ctas_per_sm(me_full16_list_kernel<R, true>, kLW * 32, (int)C::SMEM, 0)
-                             : tc::ctas_per_sm(me_full16_list_kernel<R, false>, kLW * 32, (int)C::SMEM, 0);
+  const bool clip = H % 16 != 0;
+  auto kern = use_tma ? (clip ? me_full16_list_kernel<R, true, true> : me_full16_list_kernel<R, true, false>)
+                      : (clip ? me_full16_list_kernel<R, false, true> : me_full16_list_kernel<R, false, false>);
+  const int per_sm = tc::ctas_per_sm(kern, kLW * 32, (int)C::SMEM, 0);
   int grid = (max_count + kLW - 1) / kLW;
   if (grid > per_sm * nsm) grid = per_sm * nsm;
   if (grid < 1) grid = 1;
-  if (use_tma)
-    return tc::launch_dependent(me_full16_list_kernel<R, true>, dim3(grid), dim3(kLW * 32), C::SMEM, st, tref, tcur,
-                                ref, cur, W, H, pitch, ref_bs, cur_bs, h, w, list, count, out, vec_ok, status);
-  return tc::launch_dependent(me_full16_list_kernel<R, false>, dim3(grid), dim3(kLW * 32), C::SMEM, st, tref, tcur,
-                              ref, cur, W, H, pitch, ref_bs, cur_bs, h, w, list, count, out, vec_ok, status);
+  return tc::launch_dependent(kern, dim3(grid), dim3(kLW * 32), C::SMEM, st, tref, tcur, ref, cur, W, H, pitch,
+                              ref_bs, cur_bs, h, w, list, count, out, vec_ok, status);
 }
 
 template <int R>
 cudaError_t configure_list_r() {
   cudaError_t e = cudaSuccess;
-  for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
-    const void* fn = v ? (const void*)me_full16_list_kernel<R, true> : (const void*)me_full16_list_kernel<R, false>;
+  const void* fns[4] = {(const void*)me_full16_list_kernel<R, true, false>,
+                        (const void*)me_full16_list_kernel<R, false, false>,
+                        (const void*)me_full16_list_kernel<R, true, true>,
+                        (const void*)me_full16_list_kernel<R, false, true>};
+  for (int v = 0; v < 4 && e == cudaSuccess; ++v) {
+    const void* fn = fns[v];
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Full16List<R>::SMEM);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   }

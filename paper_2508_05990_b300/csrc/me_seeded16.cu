@@ -43,6 +43,11 @@ constexpr size_t kSmem = (size_t)kSW * kPer * kSlot * sizeof(uint32_t);
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
+// CLIP: the frame height is no multiple of 16, so the last block row is
+// clipped to bh = H - y0 rows: its current rows below the frame stay zero
+// (min(win, 0) adds nothing), its window sums weigh only rows < bh, and its
+// candidates are valid while y0 + dy + bh <= H.
+template <bool CLIP>
 __global__ void __launch_bounds__(kSW * 32) seeded16_kernel(const Seeded16Args a) {
   extern __shared__ __align__(16) uint32_t smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -96,7 +101,8 @@ __global__ void __launch_bounds__(kSW * 32) seeded16_kernel(const Seeded16Args a
     for (int k = 0; k < kPer; ++k) {
       const int x0 = bxy[k] & 0xFFFF, y0 = bxy[k] >> 16;
       const uint16_t* cur = a.cur + (long long)bp[k] * a.cur_bs + (long long)(y0 + (lane >> 1)) * a.pitch + x0;
-      rc16[k] = gb0 + k < nblk ? __ldg(reinterpret_cast<const uint4*>(cur) + (lane & 1)) : make_uint4(0, 0, 0, 0);
+      const bool in = gb0 + k < nblk && (!CLIP || y0 + (lane >> 1) < a.H);
+      rc16[k] = in ? __ldg(reinterpret_cast<const uint4*>(cur) + (lane & 1)) : make_uint4(0, 0, 0, 0);
     }
   } else if (vec) {
 #pragma unroll
@@ -106,8 +112,8 @@ __global__ void __launch_bounds__(kSW * 32) seeded16_kernel(const Seeded16Args a
 #pragma unroll
       for (int i = 0; i < kPairsCur / 32; ++i) {
         const int f = lane + 32 * i;
-        rc[k][i] = gb0 + k < nblk ? __ldg(reinterpret_cast<const uint32_t*>(cur + (f >> 3) * a.pitch + 2 * (f & 7)))
-                                  : 0u;
+        const bool in = gb0 + k < nblk && (!CLIP || y0 + (f >> 3) < a.H);
+        rc[k][i] = in ? __ldg(reinterpret_cast<const uint32_t*>(cur + (f >> 3) * a.pitch + 2 * (f & 7))) : 0u;
       }
     }
   }
@@ -130,7 +136,8 @@ __global__ void __launch_bounds__(kSW * 32) seeded16_kernel(const Seeded16Args a
       int cx = 2 * (int)roundf(qx * 0.5f);
       int cy = 2 * (int)roundf(qy * 0.5f);
       cx = clampi(clampi(cx, -a.range, a.range), -x0, a.W - 16 - x0);
-      cy = clampi(clampi(cy, -a.range, a.range), -y0, a.H - 16 - y0);
+      const int bh = CLIP && y0 + 16 > a.H ? a.H - y0 : 16;
+      cy = clampi(clampi(cy, -a.range, a.range), -y0, a.H - bh - y0);
       cpk = (int)(((unsigned)cx & 0xFFFFu) | ((unsigned)cy << 16));
       confident = true;
     }
@@ -238,7 +245,8 @@ __global__ void __launch_bounds__(kSW * 32) seeded16_kernel(const Seeded16Args a
       }
       for (int e = lane; e < kPairsCur; e += 32) {
         const uint16_t* cp = cur + (long long)(y0 + (e >> 3)) * a.pitch + x0 + 2 * (e & 7);
-        slots[k * kSlot + kCurOff + e] = (uint32_t)__ldg(cp) | ((uint32_t)__ldg(cp + 1) << 16);
+        slots[k * kSlot + kCurOff + e] =
+            (!CLIP || y0 + (e >> 3) < a.H) ? (uint32_t)__ldg(cp) | ((uint32_t)__ldg(cp + 1) << 16) : 0u;
       }
     }
   }
@@ -251,6 +259,7 @@ __global__ void __launch_bounds__(kSW * 32) seeded16_kernel(const Seeded16Args a
   const int mxy = jj == 0 ? bxy[0] : (jj == 1 ? bxy[1] : bxy[2]);
   const bool live = j < kPer && (conf_mask & (1u << j));
   uint32_t acc[5] = {0, 0, 0, 0, 0};
+  const int bhj = CLIP && (mxy >> 16) + 16 > a.H ? a.H - (mxy >> 16) : 16;  // the block's rows in the frame
   if (live) {
     // half hh: current words 4 hh .. 4 hh + 3, window words 4 hh .. 4 hh + 7 of rows 2 v + r
     const uint32_t* wb = slots + j * kSlot + 2 * v * kWP + 4 * hh;
@@ -279,8 +288,11 @@ __global__ void __launch_bounds__(kSW * 32) seeded16_kernel(const Seeded16Args a
       for (int u = 0; u < 5; ++u)
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) acc[u] = dp2a_lo(min_u16x2(w[u + cc], c[cc]), 0x0202u, acc[u]);
+      {
+        const uint32_t wt = !CLIP || r < bhj ? 0x0101u : 0u;  // window rows past the block's own add nothing
 #pragma unroll
-      for (int t = 0; t < 8; ++t) tw[t] = dp2a_lo(w[t], 0x0101u, tw[t]);
+        for (int t = 0; t < 8; ++t) tw[t] = dp2a_lo(w[t], wt, tw[t]);
+      }
 #pragma unroll
       for (int t = 0; t < 4; ++t) pc[t] += c[t];
     }
@@ -307,7 +319,7 @@ __global__ void __launch_bounds__(kSW * 32) seeded16_kernel(const Seeded16Args a
     for (int u = 0; u < 5; ++u) {
       const int dx = cx + 2 * (u - 2);
       const bool ok = abs(dx) <= a.range && abs(dy) <= a.range && x0 + dx >= 0 && x0 + dx + 16 <= a.W &&
-                      y0 + dy >= 0 && y0 + dy + 16 <= a.H;
+                      y0 + dy >= 0 && y0 + dy + bhj <= a.H;
       const uint64_t k = ok ? make_key(acc[u], dx, dy) : kInvalidKey;
       key = k < key ? k : key;
     }
@@ -324,8 +336,12 @@ __global__ void __launch_bounds__(kSW * 32) seeded16_kernel(const Seeded16Args a
 }  // namespace
 
 cudaError_t configure_seeded16() {
-  cudaError_t e = cudaFuncSetAttribute(seeded16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(seeded16_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  cudaError_t e = cudaSuccess;
+  for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+    const void* fn = v ? (const void*)seeded16_kernel<true> : (const void*)seeded16_kernel<false>;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  }
   return e;
 }
 
@@ -337,8 +353,9 @@ cudaError_t launch_seeded16(const Seeded16Args& in, cudaStream_t st) {
             a.pitch % 8 == 0 && a.ref_bs % 8 == 0 && a.cur_bs % 8 == 0 && a.W % 16 == 0;
   const long long nblk = (long long)a.batch * a.h * a.w;
   const long long per_cta = (long long)kSW * kPer;
-  return tc::launch_dependent(seeded16_kernel, dim3((unsigned)((nblk + per_cta - 1) / per_cta)), dim3(kSW * 32),
-                              kSmem, st, a);
+  const dim3 grid((unsigned)((nblk + per_cta - 1) / per_cta));
+  if (a.H % 16) return tc::launch_dependent(seeded16_kernel<true>, grid, dim3(kSW * 32), kSmem, st, a);
+  return tc::launch_dependent(seeded16_kernel<false>, grid, dim3(kSW * 32), kSmem, st, a);
 }
 
 }  // namespace bme

@@ -65,21 +65,30 @@ def rel(a, b):
 
 
 def check_forward(prop, conf, theta, ref, cur, R=32):
-    """Every block's outputs against both oracles (see the module docstring)."""
+    """Every block's outputs against both oracles (see the module docstring).
+    The network's 2 ceil(H/32) block rows are cropped to the block grid's
+    ceil(H/16) (the header's definition), which the GPU's outputs have."""
+    h, w = conf.shape
+    assert h == -(-ref.shape[0] // 16) and w == ref.shape[1] // 16
     z, mz, _ = fb.cnn_logits(theta, ref, cur, R)
     zb, _, _ = fb.cnn_logits(theta, ref, cur, R, act_round="bf16")
+    z, mz, zb = z[:, :h, :w], mz[:, :h, :w], zb[:, :h, :w]
     ok = fb.outputs_within(prop, conf, z, fb.TOL_BF16 * mz, R)
     assert ok.all(), ("vs exact", np.argwhere(~ok)[:5])
     ok = fb.outputs_within(prop, conf, zb, fb.TOL_CNN_SAME_ROUNDING * mz, R)
     assert ok.all(), ("vs bf16-rounded", np.argwhere(~ok)[:5])
 
 
-@pytest.mark.parametrize("shape", [(128, 192), (1088, 1920), (64, 2048), (96, 2080)])
+@pytest.mark.parametrize("shape", [(128, 192), (1088, 1920), (64, 2048), (96, 2080), (1080, 1920), (720, 1280),
+                                   (72, 2080)])
 def test_cnn_forward_matches_oracle(handle, shape):
     """128x192 and 1088x1920: layers 3, 4 and the head in one kernel; 64x2048:
     its widest case (layer-3 rows of 128 pixels); 96x2080: layer-3 rows of 130
     pixels, so the per-tile layer-3 and layer-4 kernels run instead (and H4 = 3
-    leaves the last layer-4 row pair half outside the map)."""
+    leaves the last layer-4 row pair half outside the map).  Heights that are
+    no multiple of 32: 1080 (layer 2's 135 rows make layer 3 read its zero pad
+    row; 68 block rows, the last 8 pixels high), 720 (46 network block rows
+    cropped to 45) and 72 with the per-tile kernels (6 rows cropped to 5)."""
     H, W = shape
     ref, cur = synth.pan_clip(90, H, W, n_frames=2, rect_size=(16, 64))
     _, wbf, theta = weights(3)
@@ -185,14 +194,17 @@ def test_learned_equals_seeded_mode_on_network_proposals(handle):
     assert int(nfb.item()) == int(fb.sum().item())
 
 
+@pytest.mark.parametrize("H", [224, 216, 210])
 @pytest.mark.parametrize("mode", ["all_fallback", "at_optimum", "mixed", "mixed_odd_pitch"])
-def test_seeded_fast_path_vs_oracle(handle, mode):
+def test_seeded_fast_path_vs_oracle(handle, mode, H):
     """SEEDED mode (block 16, EVEN, +-32) vs the oracle on a 14 x 20-block frame
     (the second CTA of 256 blocks is partial); "mixed_odd_pitch" stores the
-    frames with a row pitch of 321 samples, which rules out paired loads."""
-    H, W = 224, 320
+    frames with a row pitch of 321 samples, which rules out paired loads.
+    H = 216 and 210: the last block row is clipped to 8 and 2 rows (the
+    refine's and the fallback list kernel's clipped forms)."""
+    W = 320
     frames = synth.pan_clip(94, H, W, n_frames=2, rect_size=(16, 64))
-    h, w = H // 16, W // 16
+    h, w = -(-H // 16), W // 16
     full, _ = oracle.me_full(frames[0], frames[1], 16, 32, even=True)
     if mode == "all_fallback":
         pdx = pdy = np.zeros((h, w), np.float32)
@@ -250,3 +262,42 @@ def test_learned_1080p_clip_as_benchmarked(handle):
         for k in ("dx", "dy", "sad"):
             np.testing.assert_array_equal(g[k], ref_field[k])
         np.testing.assert_array_equal(fb[t].cpu().numpy(), ref_fb)
+
+
+def test_learned_1920x1080(handle):
+    """The learned-seeded search on real 1080-row frames (the last block row 8
+    rows high, the network's layer 3 reading its zero pad row): equal to SEEDED
+    mode on the network's own proposals bit for bit, and to the oracle's
+    seeded search given those proposals for two pairs; the network's outputs
+    for the first pair within the forward bounds."""
+    import os
+    H, W = 1080, 1920
+    frames = synth.pan_clip(synth.WORKLOADS["1080p"]["seed"], H, W, n_frames=4)
+    d = dev(frames)
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2508_05990_b300",
+                        "weights", "proposal_1080p_r32.npz")
+    theta32 = torch.from_numpy(np.load(path)["theta"].astype(np.float32)).cuda()
+    wbf = bm.to_bf16_bits(theta32).contiguous()
+    kw = dict(batch=3, ref_batch_stride=H * W, cur_batch_stride=H * W)
+    h, w = 68, 120
+    fbk = torch.empty((3, h, w), dtype=torch.uint8, device="cuda")
+    got = handle.estimate_learned(d, d[1:], wbf, 32, 0.5, fallback=fbk, **kw)
+    assert tuple(got.shape) == (3, h, w, 2)
+    prop, conf = handle.cnn_forward(d, d[1:], wbf, 32, **kw)
+    fb2 = torch.empty_like(fbk)
+    want = handle.estimate_ex(d, d[1:], mode=bm.MODE_SEEDED, search_range=32, prop_dxdy=prop, conf=conf,
+                              fallback=fb2, **kw)
+    torch.cuda.synchronize()
+    assert handle.sync_status() == bm.OK
+    assert torch.equal(got, want) and torch.equal(fbk, fb2)
+    last = fbk[:, -1].cpu().numpy()
+    assert last.any() and not last.all(), "the clipped block row should hold refined and fallback blocks"
+    p, c = prop.cpu().numpy(), conf.cpu().numpy()
+    for t in (0, 2):
+        ref_field, ref_fb, _ = oracle.me_seeded(frames[t], frames[t + 1], 16, 32, p[t, ..., 0], p[t, ..., 1], c[t])
+        g = bm.records_to_numpy(got[t])
+        for k in ("dx", "dy", "sad"):
+            np.testing.assert_array_equal(g[k], ref_field[k])
+        np.testing.assert_array_equal(fbk[t].cpu().numpy(), ref_fb)
+    theta_bf = theta32.to(torch.bfloat16).double().cpu().numpy()
+    check_forward(p[0], c[0], theta_bf, frames[0], frames[1])

@@ -37,6 +37,22 @@ def torch_forward(theta, ref, cur, R):
     return R * torch.tanh(z[0]), R * torch.tanh(z[1]), torch.sigmoid(z[2]), p
 
 
+@pytest.mark.parametrize("H,W", [(40, 96), (72, 64)])
+def test_forward_matches_torch_off_multiples_of_32(H, W):
+    """Heights that are no multiple of 32 (the learned search's 1080-row and
+    720-row case in small): every layer takes its natural ceil(n / 2) size,
+    torch's stride-2 conv with padding 1 included, and the depth-to-space
+    output has 2 ceil(H / 32) >= ceil(H / 16) block rows."""
+    ref, cur = synth.pan_clip(5, H, W, n_frames=2, rect_size=(8, 16))
+    theta = synth.he_normal_params(14, shapes()).astype(np.float64)
+    dx, dy, conf, _ = cnn.forward(theta, ref, cur, 32)
+    tdx, tdy, tconf, _ = torch_forward(theta, ref, cur, 32)
+    assert dx.shape == (2 * (-(-H // 32)), W // 16) and dx.shape[0] >= -(-H // 16)
+    np.testing.assert_allclose(dx, tdx.detach().numpy(), rtol=1e-10, atol=1e-10)
+    np.testing.assert_allclose(dy, tdy.detach().numpy(), rtol=1e-10, atol=1e-10)
+    np.testing.assert_allclose(conf, tconf.detach().numpy(), rtol=1e-10, atol=1e-12)
+
+
 def test_forward_and_gradient_match_torch_autograd():
     ref, cur = synth.pan_clip(3, 64, 96, n_frames=2, rect_size=(8, 24))
     theta = synth.he_normal_params(11, shapes()).astype(np.float64)
