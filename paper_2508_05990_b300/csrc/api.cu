@@ -34,7 +34,7 @@ struct bayer_me_s {
   size_t cnn_dpre_bytes = 0;
   float* prop = nullptr;  // [blocks][2] proposals, then [blocks] confidences
   size_t prop_bytes = 0;
-  int* list = nullptr;    // [1 + blocks]: count, then block indices
+  int* list = nullptr;    // [2 + 2 blocks]: two counts, then the two fallback lists
   size_t list_bytes = 0;
   // refine convolution
   void* ref_w = nullptr;  // bf16 weights and biases
@@ -149,16 +149,18 @@ bool seeded16_fast(int block, int phase, int W, int H, int range) {
 
 // Seeded refine on the fast kernels: warp-per-block +-4 refine, compacted list
 // of low-confidence blocks, list-mode exhaustive search of that list.
-// The fallback list (counter, then block indices) for nblk blocks.
+// The fallback lists for nblk blocks: two counters, then the block indices
+// of every fallback block, then those of the clipped last block row (frames
+// whose height is no multiple of 16) again.
 bayer_status_t fallback_list_space(bayer_me_s* h, long long nblk) {
-  return grow(h, &h->list, &h->list_bytes, (size_t)(nblk + 1) * sizeof(int));
+  return grow(h, &h->list, &h->list_bytes, (size_t)(2 * nblk + 2) * sizeof(int));
 }
 
-// The same, its counter zeroed on st.
+// The same, its counters zeroed on st.
 bayer_status_t fallback_list(bayer_me_s* h, long long nblk, cudaStream_t st) {
   bayer_status_t s = fallback_list_space(h, nblk);
   if (s != BAYER_OK) return s;
-  return cuda_status(cudaMemsetAsync(h->list, 0, sizeof(int), st));
+  return cuda_status(cudaMemsetAsync(h->list, 0, 2 * sizeof(int), st));
 }
 
 // The +-4 refine and the fallback searches; list_ready: the list has room and
@@ -194,12 +196,21 @@ bayer_status_t seeded_fast(bayer_me_s* h, const uint16_t* ref, const uint16_t* c
   a.out = out;
   a.fallback = fallback;
   a.count = h->list;
-  a.list = h->list + 1;
+  a.count2 = h->list + 1;
+  a.list = h->list + 2;
+  a.list2 = h->list + 2 + nblk;
   if (e == cudaSuccess) e = bme::launch_seeded16(a, st);
+  // every fallback block as 16 rows (the clipped row's results are then
+  // replaced), then the clipped row's over its rows in the frame: the clipped
+  // form of the list kernel is slower for every block, so it runs only there
   if (e == cudaSuccess)
-    e = bme::launch_full16_list(ref, cur, W, H, pitch, rbs, cbs, batch, hb, wb, range, h->list + 1, h->list, (int)nblk,
-                                out, h->d_status, st);
-  if (e == cudaSuccess && n_fallback) e = cudaMemcpyAsync(n_fallback, h->list, sizeof(int), cudaMemcpyDeviceToDevice, st);
+    e = bme::launch_full16_list(ref, cur, W, H, pitch, rbs, cbs, batch, hb, wb, range, a.list, a.count, (int)nblk,
+                                false, out, h->d_status, st);
+  if (e == cudaSuccess && H % 16)
+    e = bme::launch_full16_list(ref, cur, W, H, pitch, rbs, cbs, batch, hb, wb, range, a.list2, a.count2,
+                                batch * wb, true, out, h->d_status, st);
+  if (e == cudaSuccess && n_fallback)
+    e = cudaMemcpyAsync(n_fallback, a.count, sizeof(int), cudaMemcpyDeviceToDevice, st);
   return cuda_status(e);
 }
 

@@ -225,7 +225,7 @@ size_t wimg_all_bytes() { return wimg_bytes() + (conv_dx_weight_bytes() + 255) /
 // the head (activations of layer 4 are then not stored); otherwise all four
 // layers' activations are written.
 cudaError_t cnn_forward_acts(const CnnFrames& fr, int batch, const uint16_t* wbf16, void* acts, int* status, bool head,
-                             int range, float* prop, float* conf, cudaStream_t st, int* zero_word = nullptr) {
+                             int range, float* prop, float* conf, cudaStream_t st, int* zero_words = nullptr) {
   const CnnShapes s = cnn_shapes(fr.W, fr.H);
   const __nv_bfloat16* w = reinterpret_cast<const __nv_bfloat16*>(wbf16);
   __nv_bfloat16* a[5];
@@ -242,7 +242,7 @@ cudaError_t cnn_forward_acts(const CnnFrames& fr, int batch, const uint16_t* wbf
     wimg[l] = reinterpret_cast<const uint4*>(img + off);
     off += (conv_tc_weight_bytes(l == 1 ? 16 : 32) + 255) / 256 * 256;
   }
-  cudaError_t e0 = pack_conv_tc_weights(wbf16, woff + 1, img_off, reinterpret_cast<uint16_t*>(img), zero_word, st);
+  cudaError_t e0 = pack_conv_tc_weights(wbf16, woff + 1, img_off, reinterpret_cast<uint16_t*>(img), zero_words, st);
   if (e0 != cudaSuccess) return e0;
   const bool vec = (reinterpret_cast<uintptr_t>(fr.ref) % 16) == 0 && (reinterpret_cast<uintptr_t>(fr.cur) % 16) == 0 &&
                    fr.pitch % 8 == 0 && fr.ref_bs % 8 == 0 && fr.cur_bs % 8 == 0 && s.W[0] % 4 == 0;
@@ -286,8 +286,8 @@ size_t cnn_grad_bytes(int W, int H, int batch) {
 }
 
 cudaError_t cnn_forward(const CnnFrames& fr, int batch, const uint16_t* wbf16, int range, void* acts, float* prop,
-                        float* conf, int* status, cudaStream_t st, int* zero_word) {
-  return cnn_forward_acts(fr, batch, wbf16, acts, status, true, range, prop, conf, st, zero_word);
+                        float* conf, int* status, cudaStream_t st, int* zero_words) {
+  return cnn_forward_acts(fr, batch, wbf16, acts, status, true, range, prop, conf, st, zero_words);
 }
 
 cudaError_t cnn_loss_grad(const CnnFrames& fr, int batch, const uint16_t* wbf16, const bayer_mv_t* labels, int range,

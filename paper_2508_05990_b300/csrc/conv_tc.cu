@@ -82,7 +82,7 @@ struct PackArgs {
   const __nv_bfloat16* w;
   int w_off[4];
   unsigned img_off[4];
-  int* zero_word;  // optional: set to 0 (a counter that kernels after the network fill)
+  int* zero_words;  // optional: two ints set to 0 (counters that kernels after the network fill)
 };
 
 // Launched as a dependent of whatever precedes it on the stream (its launch
@@ -93,7 +93,7 @@ __global__ void pack_conv_tc_weights_kernel(const PackArgs pa, __nv_bfloat16* __
   tc::grid_dep_wait();
   tc::grid_dep_launch();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i == 0 && pa.zero_word) *pa.zero_word = 0;
+  if (i == 0 && pa.zero_words) pa.zero_words[0] = pa.zero_words[1] = 0;
   if (i < kL1) {
     const int n = i / 72, k = i - n * 72;
     const int tap = k / 8, ci = k - tap * 8;
@@ -478,9 +478,9 @@ cudaError_t configure_t() {
 size_t conv_tc_weight_bytes(int cin_op) { return (size_t)9 * cin_op * kN * 2; }
 
 cudaError_t pack_conv_tc_weights(const uint16_t* w, const int* w_off, const size_t* img_off, uint16_t* img,
-                                 int* zero_word, cudaStream_t st) {
+                                 int* zero_words, cudaStream_t st) {
   PackArgs pa;
-  pa.zero_word = zero_word;
+  pa.zero_words = zero_words;
   pa.w = reinterpret_cast<const __nv_bfloat16*>(w);
   for (int l = 0; l < 4; ++l) {
     pa.w_off[l] = w_off[l];

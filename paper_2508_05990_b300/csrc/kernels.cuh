@@ -76,11 +76,11 @@ struct CnnShapes {
 CnnShapes cnn_shapes(int W, int H);
 size_t cnn_act_bytes(int W, int H, int batch);   // bf16 activations of layers 1..4 + packed weights
 size_t cnn_grad_bytes(int W, int H, int batch);  // bf16 pre-activation gradients of layers 1..4
-// zero_word (optional): an int the forward's first launch sets to 0 (the
-// fallback list's counter of a learned search, so that no separate memset
+// zero_words (optional): two ints the forward's first launch sets to 0 (the
+// fallback lists' counters of a learned search, so that no separate memset
 // sits between the previous kernel and the network).
 cudaError_t cnn_forward(const CnnFrames& fr, int batch, const uint16_t* wbf16, int range, void* acts, float* prop,
-                        float* conf, int* status, cudaStream_t st, int* zero_word = nullptr);
+                        float* conf, int* status, cudaStream_t st, int* zero_words = nullptr);
 cudaError_t cnn_loss_grad(const CnnFrames& fr, int batch, const uint16_t* wbf16, const bayer_mv_t* labels, int range,
                           float neg_weight, void* acts, void* dpre, float* grad, float* loss, int* status,
                           cudaStream_t st);
@@ -194,14 +194,19 @@ struct Seeded16Args {
   uint8_t* fallback;  // optional
   int* list;          // [batch*h*w] global block indices needing the full search
   int* count;         // number of entries in list (zeroed by the caller)
+  int* list2;         // H % 16 != 0: the entries of list in the clipped last block row, again
+  int* count2;        // number of entries in list2 (zeroed by the caller)
   bool vec2;          // set by launch_seeded16: 32-bit sample-pair loads allowed
   bool vec16;         // set by launch_seeded16: 16-byte loads of frame rows allowed
 };
 cudaError_t configure_seeded16();  // once per device: shared-memory opt-in
 cudaError_t launch_seeded16(const Seeded16Args& a, cudaStream_t st);
+// clip: the list holds blocks of a last block row clipped by the frame
+// (H % 16 != 0), searched over their rows in the frame; without it every
+// block is searched as 16 rows (the rows below the frame read as zeros).
 cudaError_t launch_full16_list(const uint16_t* ref, const uint16_t* cur, int W, int H, int pitch, long long ref_bs,
                                long long cur_bs, int batch, int h, int w, int range, const int* list, const int* count,
-                               int max_count, bayer_mv_t* out, int* status, cudaStream_t st);
+                               int max_count, bool clip, bayer_mv_t* out, int* status, cudaStream_t st);
 cudaError_t configure_full16_list();
 
 // Multi-stream search + propagation (multistream.cu); status: the handle's

@@ -223,9 +223,11 @@ __device__ __forceinline__ void list_where(int gb, int h, int w, int& pair, int&
   x0 = (rem - by * w) * 16;
 }
 
-// CLIP: the frame height is no multiple of 16; a block of the last block row
-// runs over its bh = H - y0 rows (the current rows below the frame are staged
-// as zeros: TMA fills them, the plain loads skip them).
+// CLIP: a block of a last block row clipped by the frame (H % 16 != 0) runs
+// over its bh = H - y0 rows (the current rows below the frame are staged as
+// zeros: TMA fills them, the plain loads skip them).  This form makes every
+// block slower (list search of the 1080p clip's fallback blocks: 127.6 ->
+// ~150 us), so it only runs a second list of the clipped row's blocks.
 template <int R, bool TMA, bool CLIP>
 __global__ void __launch_bounds__(kLW * 32) me_full16_list_kernel(const __grid_constant__ CUtensorMap tm_ref,
                                                                    const __grid_constant__ CUtensorMap tm_cur,
@@ -248,8 +250,10 @@ __global__ void __launch_bounds__(kLW * 32) me_full16_list_kernel(const __grid_c
   tc::grid_dep_wait();
   tc::grid_dep_launch();
   const int n = *count;
+  // warp-major: consecutive entries go to different CTAs, so that a partial
+  // last round (or a short list) spreads over every SM
   const int step = gridDim.x * kLW;
-  int gi = blockIdx.x * kLW + warp;
+  int gi = warp * gridDim.x + blockIdx.x;
 
   if constexpr (TMA) {
     if (lane == 0) {
@@ -314,7 +318,7 @@ __global__ void __launch_bounds__(kLW * 32) me_full16_list_kernel(const __grid_c
 template <int R>
 cudaError_t launch_list_r(const uint16_t* ref, const uint16_t* cur, int W, int H, int pitch, long long ref_bs,
                           long long cur_bs, int batch, int h, int w, const int* list, const int* count, int max_count,
-                          bayer_mv_t* out, int* status, cudaStream_t st) {
+                          bool clip, bayer_mv_t* out, int* status, cudaStream_t st) {
   using C = Full16List<R>;
   int dev = 0, nsm = 148;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -324,11 +328,10 @@ cudaError_t launch_list_r(const uint16_t* ref, const uint16_t* cur, int W, int H
   const bool use_tma = vec_ok &&
                        tma::encode_u16_frames(&tref, ref, W, H, batch, pitch, ref_bs, C::BOX_W, C::WIN_H) &&
                        tma::encode_u16_frames(&tcur, cur, W, H, batch, pitch, cur_bs, 16, 16);
-  const bool clip = H % 16 != 0;
   auto kern = use_tma ? (clip ? me_full16_list_kernel<R, true, true> : me_full16_list_kernel<R, true, false>)
                       : (clip ? me_full16_list_kernel<R, false, true> : me_full16_list_kernel<R, false, false>);
   const int per_sm = tc::ctas_per_sm(kern, kLW * 32, (int)C::SMEM, 0);
-  int grid = (max_count + kLW - 1) / kLW;
+  int grid = max_count;
   if (grid > per_sm * nsm) grid = per_sm * nsm;
   if (grid < 1) grid = 1;
   return tc::launch_dependent(kern, dim3(grid), dim3(kLW * 32), C::SMEM, st, tref, tcur, ref, cur, W, H, pitch,
@@ -381,20 +384,20 @@ cudaError_t configure_full16_list() {
 
 cudaError_t launch_full16_list(const uint16_t* ref, const uint16_t* cur, int W, int H, int pitch, long long ref_bs,
                                long long cur_bs, int batch, int h, int w, int range, const int* list, const int* count,
-                               int max_count, bayer_mv_t* out, int* status, cudaStream_t st) {
+                               int max_count, bool clip, bayer_mv_t* out, int* status, cudaStream_t st) {
   switch (range) {
     case 8:
-      return launch_list_r<4>(ref, cur, W, H, pitch, ref_bs, cur_bs, batch, h, w, list, count, max_count, out, status,
-                              st);
+      return launch_list_r<4>(ref, cur, W, H, pitch, ref_bs, cur_bs, batch, h, w, list, count, max_count, clip,
+                              out, status, st);
     case 16:
-      return launch_list_r<8>(ref, cur, W, H, pitch, ref_bs, cur_bs, batch, h, w, list, count, max_count, out, status,
-                              st);
+      return launch_list_r<8>(ref, cur, W, H, pitch, ref_bs, cur_bs, batch, h, w, list, count, max_count, clip,
+                              out, status, st);
     case 24:
-      return launch_list_r<12>(ref, cur, W, H, pitch, ref_bs, cur_bs, batch, h, w, list, count, max_count, out, status,
-                               st);
+      return launch_list_r<12>(ref, cur, W, H, pitch, ref_bs, cur_bs, batch, h, w, list, count, max_count, clip,
+                               out, status, st);
     case 32:
-      return launch_list_r<16>(ref, cur, W, H, pitch, ref_bs, cur_bs, batch, h, w, list, count, max_count, out, status,
-                               st);
+      return launch_list_r<16>(ref, cur, W, H, pitch, ref_bs, cur_bs, batch, h, w, list, count, max_count, clip,
+                               out, status, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -7,6 +7,12 @@
 // with |dx|, |dy| <= range and the displaced block inside the frame are
 // evaluated.  Argmin with the (sad, |dx|+|dy|, dy, dx) key as everywhere else.
 //
+// Frames whose height is no multiple of 16 (the CLIP instance): the last
+// block row is clipped to its rows in the frame; its fallback blocks are also
+// appended to a second list, which a list search in the clipped form runs
+// after the list search of the first (whose 16-row results for those blocks
+// it overwrites).
+//
 // Mapping: one warp per three consecutive blocks, 10 lanes per block.
 // Lanes 0-2 read the blocks' confidences and proposals; low-confidence
 // blocks are appended to the fallback list (one atomic per warp).  For the
@@ -148,6 +154,19 @@ __global__ void __launch_bounds__(kSW * 32) seeded16_kernel(const Seeded16Args a
     if (lane == 0) base = atomicAdd(a.count, __popc(m));
     base = __shfl_sync(0xffffffffu, base, 0);
     if (fb) a.list[base + __popc(m & ((1u << lane) - 1u))] = (int)(gb0 + lane);
+    if constexpr (CLIP) {
+      // fallback blocks of the clipped last block row go to the second list as
+      // well: the list search runs them again over their rows in the frame
+      const int my0 = (lane == 0 ? bxy[0] : (lane == 1 ? bxy[1] : bxy[2])) >> 16;
+      const bool clipped = fb && my0 + 16 > a.H;
+      const unsigned m2 = __ballot_sync(0xffffffffu, clipped);
+      if (m2) {
+        int base2 = 0;
+        if (lane == 0) base2 = atomicAdd(a.count2, __popc(m2));
+        base2 = __shfl_sync(0xffffffffu, base2, 0);
+        if (clipped) a.list2[base2 + __popc(m2 & ((1u << lane) - 1u))] = (int)(gb0 + lane);
+      }
+    }
   }
   const unsigned conf_mask = __ballot_sync(0xffffffffu, confident);
   if (conf_mask == 0) return;
