@@ -301,3 +301,28 @@ def test_learned_1920x1080(handle):
         np.testing.assert_array_equal(fbk[t].cpu().numpy(), ref_fb)
     theta_bf = theta32.to(torch.bfloat16).double().cpu().numpy()
     check_forward(p[0], c[0], theta_bf, frames[0], frames[1])
+
+
+def test_network_size_rules(handle):
+    """Inference takes H % 8 == 0 and W % 32 == 0; the loss keeps H % 32 == 0;
+    other sizes return BAYER_ERR_UNSUPPORTED and launch nothing."""
+    _, wbf, _ = weights(6)
+    f = torch.zeros((2, 1084, 1920), dtype=torch.int16, device="cuda")  # 1084 % 8 == 4
+    for call in (lambda: handle.cnn_forward(f[0], f[1], wbf, 32),
+                 lambda: handle.estimate_learned(f[0], f[1], wbf, 32, 0.5)):
+        with pytest.raises(bm.BayerError) as e:
+            call()
+        assert e.value.status == bm.ERR_UNSUPPORTED
+    g = torch.zeros((2, 1080, 1936), dtype=torch.int16, device="cuda")  # 1936 % 32 == 16
+    with pytest.raises(bm.BayerError) as e:
+        handle.cnn_forward(g[0], g[1], wbf, 32)
+    assert e.value.status == bm.ERR_UNSUPPORTED
+    k = torch.zeros((2, 1080, 1920), dtype=torch.int16, device="cuda")
+    labels = torch.zeros((1, 68, 120, 2), dtype=torch.int32, device="cuda")
+    with pytest.raises(bm.BayerError) as e:
+        handle.cnn_loss_grad(k[0], k[1], wbf, labels, 32)
+    assert e.value.status == bm.ERR_UNSUPPORTED
+    prop, conf = handle.cnn_forward(k[0], k[1], wbf, 32)  # 1080 rows: accepted, 68 block rows
+    assert tuple(conf.shape) == (1, 68, 120)
+    torch.cuda.synchronize()
+    assert handle.sync_status() == bm.OK
