@@ -310,9 +310,11 @@ bayer_status_t bayer_refine_conv(bayer_me_t h, const float* feat, int n, int Hf,
  * Many camera streams at once (not in the paper; its batch dimension, Sec. 4.1
  * "CUDA Settings", extended to frame pairs of different sizes).  One frame pair
  * per entry: exhaustive EVEN search (block 16, +-range, range in
- * {8, 16, 24, 32}; W and H multiples of 16), then, where feat is not NULL,
- * propagation of that pair's NCHW feature map as in bayer_feat_propagate
- * (stride divides 16; Hf*stride/16 == H/16 and Wf*stride/16 == W/16).
+ * {8, 16, 24, 32}; W a multiple of 16, H even: a last block row clipped by
+ * the frame, e.g. H = 1080, is searched over its rows in the frame), then,
+ * where feat is not NULL, propagation of that pair's NCHW feature map as in
+ * bayer_feat_propagate (stride divides 16; Wf == W / stride and
+ * Hf == ceil(H / stride)).  mv_out holds ceil(H/16) x W/16 records.
  * The searches run in one launch (one CTA per strip of blocks of any pair)
  * and the propagations in a second one, or, smallest frames first, per class
  * of frame size a search launch followed by that class's propagation launch;
@@ -348,7 +350,7 @@ typedef struct {
   const uint16_t* ref; /* device frame, H rows of `pitch` elements */
   const uint16_t* cur;
   int W, H, pitch;
-  bayer_mv_t* mv_out;  /* device [H/16][W/16] */
+  bayer_mv_t* mv_out;  /* device [ceil(H/16)][W/16] */
   const float* feat;   /* device NCHW [C][Hf][Wf], or NULL */
   float* feat_out;     /* device, like feat */
   int C, Hf, Wf, stride;

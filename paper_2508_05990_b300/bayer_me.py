@@ -366,17 +366,21 @@ class Handle:
         return out
 
     def multi_stream(self, pairs, search_range=32, interp=INTERP_BILINEAR, end_ns=None, stream=None, schedule=0):
-        """pairs: list of dicts with ref, cur (uint16/int16 [H, W] tensors), mv (int32 [H/16, W/16, 2]) and
-        optionally feat, feat_out (float32 [C, Hf, Wf]) and stride.  Returns the schedule the autotuner chose
+        """pairs: list of dicts with ref, cur (uint16/int16 [H, W] tensors; W a multiple of 16, H even), mv
+        (int32 [ceil(H/16), W/16, 2]) and optionally feat, feat_out (float32 [C, Hf, Wf], Wf = W / stride,
+        Hf = ceil(H / stride)) and stride.  Returns the schedule the autotuner chose
         (1000 * (plain-load search windows + 2 * global-memory propagation items) + 100 * per-size launches
         + 10 * blocks per strip + order; order 0 as given, 1 largest first, 2 smallest first; staging by
         TMA tiles where a pair allows it unless the thousands say otherwise).  ``schedule``: 0 lets the
         autotuner choose; a code runs that schedule."""
+        import torch
         arr = (PairDesc * len(pairs))()
         for i, q in enumerate(pairs):
             H, W = q["ref"].shape[-2:]
             d = arr[i]
             d.ref, d.cur, d.W, d.H, d.pitch = q["ref"].data_ptr(), q["cur"].data_ptr(), W, H, W
+            h, w = grid_shape(H, W, 16)
+            _check_out(q["mv"], h * w * 2, torch.int32, q["ref"].device, "multi_stream")
             d.mv_out = q["mv"].data_ptr()
             if q.get("feat") is not None:
                 C, Hf, Wf = q["feat"].shape[-3:]

@@ -692,13 +692,12 @@ bayer_status_t bayer_me_multi_stream(bayer_me_t h, const bayer_pair_t* pairs, in
   for (int i = 0; i < n; ++i) {
     const bayer_pair_t& q = pairs[i];
     if (!q.ref || !q.cur || !q.mv_out) return BAYER_ERR_INVALID_ARG;
-    if (q.W < 16 || q.H < 16 || (q.W % 16) || (q.H % 16) || q.pitch < q.W || q.W > 32767 || q.H > 32767)
+    if (q.W < 16 || q.H < 16 || (q.W % 16) || (q.H & 1) || q.pitch < q.W || q.W > 32767 || q.H > 32767)
       return BAYER_ERR_INVALID_ARG;
     if (q.feat) {
       if (!q.feat_out || q.C < 1 || q.stride < 1 || 16 % q.stride) return BAYER_ERR_INVALID_ARG;
-      if (q.Hf * q.stride / 16 != q.H / 16 || q.Wf * q.stride / 16 != q.W / 16 || (q.Hf * q.stride) % 16 ||
-          (q.Wf * q.stride) % 16)
-        return BAYER_ERR_INVALID_ARG;
+      // the map covers the frame: Wf = W / stride, Hf = ceil(H / stride)
+      if ((long long)q.Wf * q.stride != q.W || q.Hf != (q.H + q.stride - 1) / q.stride) return BAYER_ERR_INVALID_ARG;
       const size_t bytes = (size_t)q.C * q.Hf * q.Wf * sizeof(float);
       const char* fb = reinterpret_cast<const char*>(q.feat);
       const char* ob = reinterpret_cast<const char*>(q.feat_out);

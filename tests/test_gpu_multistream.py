@@ -16,8 +16,10 @@ pytestmark = pytest.mark.gpu
 # 16-channel chunk, one at stride 4 where pan offsets pass the staged halo),
 # global-memory items at stride 16 and where Wf % 4 != 0, and a pair without
 # features
+# (H, W, C, stride); 72, 136 and 90 rows clip the last block row to 8, 8 and
+# 10 rows (feature maps of ceil(H / stride) rows)
 SIZES = [(128, 160, 32, 8), (128, 160, 16, 4), (272, 480, 32, 8), (96, 64, 8, 16), (64, 96, 0, 8),
-         (64, 48, 20, 8), (160, 128, 20, 4)]
+         (64, 48, 20, 8), (160, 128, 20, 4), (72, 96, 8, 8), (136, 128, 16, 4), (90, 64, 4, 2)]
 
 
 @pytest.fixture(scope="module")
@@ -36,10 +38,11 @@ def make(seed):
     for i, (H, W, C, s) in enumerate(SIZES):
         fr = synth.pan_clip(seed + i, H, W, n_frames=2, rect_size=(8, 48))
         q = {"np": fr, "ref": torch.from_numpy(fr[0]).cuda(), "cur": torch.from_numpy(fr[1]).cuda(),
-             "mv": torch.empty((H // 16, W // 16, 2), dtype=torch.int32, device="cuda"), "stride": s}
+             "mv": torch.empty((-(-H // 16), W // 16, 2), dtype=torch.int32, device="cuda"), "stride": s}
         if C:
-            f = synth.features(seed + 50 + i, C, H // s, W // s)[0]
-            q.update(feat_np=f, feat=torch.from_numpy(f).cuda(), feat_out=torch.empty((C, H // s, W // s), device="cuda"))
+            Hf = -(-H // s)
+            f = synth.features(seed + 50 + i, C, Hf, W // s)[0]
+            q.update(feat_np=f, feat=torch.from_numpy(f).cuda(), feat_out=torch.empty((C, Hf, W // s), device="cuda"))
         streams.append(q)
     return streams
 
@@ -68,10 +71,20 @@ def test_multi_stream_exact(handle, search_range):
 
 
 def test_multi_stream_rejects_bad_sizes(handle):
-    fr = torch.zeros((40, 64), dtype=torch.int16, device="cuda")
-    mv = torch.empty((2, 4, 2), dtype=torch.int32, device="cuda")
+    fr = torch.zeros((41, 64), dtype=torch.int16, device="cuda")
+    mv = torch.empty((3, 4, 2), dtype=torch.int32, device="cuda")
     with pytest.raises(bm.BayerError):
-        handle.multi_stream([{"ref": fr, "cur": fr, "mv": mv}], 32)  # H not a multiple of 16
+        handle.multi_stream([{"ref": fr, "cur": fr, "mv": mv}], 32)  # odd H
+    fw = torch.zeros((32, 72), dtype=torch.int16, device="cuda")
+    with pytest.raises(bm.BayerError):
+        handle.multi_stream([{"ref": fw, "cur": fw, "mv": torch.empty((2, 5, 2), dtype=torch.int32, device="cuda")}],
+                            32)  # W not a multiple of 16
+    fc = torch.zeros((72, 64), dtype=torch.int16, device="cuda")
+    feat = torch.zeros((4, 8, 8), device="cuda")  # 72 rows at stride 8 need Hf = 9
+    with pytest.raises(bm.BayerError):
+        handle.multi_stream([{"ref": fc, "cur": fc, "mv": torch.empty((5, 4, 2), dtype=torch.int32, device="cuda"),
+                              "feat": feat, "feat_out": torch.empty_like(feat), "stride": 8}], 32)
+    mv = torch.empty((2, 4, 2), dtype=torch.int32, device="cuda")
     gr = torch.zeros((32, 64), dtype=torch.int16, device="cuda")
     with pytest.raises(bm.BayerError) as err:
         handle.multi_stream([{"ref": gr, "cur": gr, "mv": mv}], 32, schedule=43)  # no such schedule
@@ -188,3 +201,37 @@ def test_multi_stream_nearest(handle):
         if "feat" in q:
             pw = oracle.propagate(q["feat_np"], want, 16, q["stride"], interp=oracle.NEAREST)
             np.testing.assert_array_equal(q["feat_out"].cpu().numpy().view(np.uint32), pw.view(np.uint32))
+
+
+def test_multi_stream_1920x1080(handle):
+    """Camera-sized frames whose height is no multiple of 16 in one call: 1920x1080
+    (last block row 8 rows high, 135-row stride-8 map), 1280x720 and 640x480.
+    Every pair equals the single-pair search and propagation bit for bit; the
+    1080-row pair equals the oracle (MV field and map)."""
+    sizes = [(1080, 1920), (720, 1280), (480, 640)]
+    C, s = 32, 8
+    streams = []
+    for i, (H, W) in enumerate(sizes):
+        fr = synth.pan_clip(700 + i, H, W, n_frames=2)
+        Hf = -(-H // s)
+        f = synth.features(710 + i, C, Hf, W // s)[0]
+        streams.append({"np": fr, "ref": torch.from_numpy(fr[0]).cuda(), "cur": torch.from_numpy(fr[1]).cuda(),
+                        "mv": torch.empty((-(-H // 16), W // 16, 2), dtype=torch.int32, device="cuda"),
+                        "feat_np": f, "feat": torch.from_numpy(f).cuda(),
+                        "feat_out": torch.empty((C, Hf, W // s), device="cuda"), "stride": s})
+    handle.multi_stream(streams, 32)
+    torch.cuda.synchronize()
+    assert handle.sync_status() == bm.OK
+    for q in streams:
+        single = handle.estimate(q["ref"], q["cur"], 16, 32)
+        prop = handle.feat_propagate(q["feat"], single, 16, s)
+        torch.cuda.synchronize()
+        assert torch.equal(q["mv"], single)
+        assert torch.equal(q["feat_out"].view(torch.int32), prop[0].view(torch.int32))
+    q = streams[0]
+    want, _ = oracle.me_full(q["np"][0], q["np"][1], 16, 32, even=True)
+    got = bm.records_to_numpy(q["mv"])
+    for k in ("dx", "dy", "sad"):
+        np.testing.assert_array_equal(got[k], want[k])
+    pw = oracle.propagate(q["feat_np"], want, 16, s, interp=oracle.BILINEAR)
+    np.testing.assert_array_equal(q["feat_out"].cpu().numpy().view(np.uint32), pw.view(np.uint32))
