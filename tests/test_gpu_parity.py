@@ -249,9 +249,11 @@ def test_propagate_4k_full(handle, layout):
 # end-to-end host path, argument errors, probe
 # ----------------------------------------------------------------------------
 
-def test_clip_process_host(handle):
-    frames = synth.pan_clip(60, 272, 480, n_frames=4)
-    feats = synth.features(61, 32, 34, 60, n=3)
+@pytest.mark.parametrize("H", [272, 264])
+def test_clip_process_host(handle, H):
+    """The host-buffer path; 264 rows clip the last block row to 8 (33-row maps)."""
+    frames = synth.pan_clip(60, H, 480, n_frames=4)
+    feats = synth.features(61, 32, -(-H // 8), 60, n=3)
     mv, fo = handle.clip_process_host(frames, feats, block=16, search_range=32, stride=8)
     for t in range(3):
         ref_field, _ = oracle.me_full(frames[t], frames[t + 1], 16, 32, even=True)
